@@ -1,0 +1,387 @@
+"""Pins for the CPU oracle (CPU only).
+
+The oracle states Eq. (eq:dnf) (Sec. 2) in the i-k-j order of Fig. ip.c.  The
+paper prints no worked numeric example, so these tests pin it to what the
+mathematics fixes instead: exact integer arithmetic, identity and permutation
+matrices, the transpose identity, associativity on integers, exact rational
+evaluation within Higham's dot-product bound, the n = 1 and n = 0 special
+cases, and the dimension-lifted loop orders of Sec. 3.1 (Figs. ip_rows.c,
+ip_cols.c), which visit the same products in the same order per element.
+
+Each pin is also run against deliberately broken variants of the oracle
+(dropped term, wrong sign, transposed operand, swapped operands, off-by-one
+index) to show that every such mistake fails at least one pin.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2306_11148_b300 import inputs
+
+RNG = np.random.default_rng(1234)
+SHAPES = [(1, 1, 1), (3, 5, 7), (17, 33, 9), (64, 64, 64), (31, 129, 15), (8, 1, 8)]
+
+
+# --------------------------------------------------------------------------
+# Pin checks, written as predicates over a GEMM function f(A, B) -> C so that
+# the same checks can be run on the oracle and on broken variants of it.
+# --------------------------------------------------------------------------
+
+def pin_integer_exact(f, m=17, n=33, p=9, seed=0):
+    A, B = inputs.integer_pair(m, n, p, seed=seed)
+    A = A.numpy()
+    B = B.numpy()
+    exact = A.astype(np.int64) @ B.astype(np.int64)   # integer arithmetic, exact
+    C = f(A, B)
+    return C.shape == exact.shape and np.array_equal(C, exact.astype(np.float64))
+
+
+def pin_identity_permutation(f, n=12, seed=3):
+    rng = np.random.default_rng(seed)
+    A = rng.uniform(-1, 1, (n, n + 3))
+    I_l = np.eye(n)
+    I_r = np.eye(n + 3)
+    perm = rng.permutation(n)
+    P = np.eye(n)[perm]                        # (P A)[i] = A[perm[i]]
+    q = rng.permutation(n + 3)
+    Q = np.eye(n + 3)[:, q]                    # (A Q)[:, j] = A[:, q[j]]
+    return (np.array_equal(f(I_l, A), A) and np.array_equal(f(A, I_r), A)
+            and np.array_equal(f(P, A), A[perm]) and np.array_equal(f(A, Q), A[:, q]))
+
+
+def pin_transpose(f, m=7, n=11, p=5, seed=5):
+    rng = np.random.default_rng(seed)
+    A = rng.uniform(-1, 1, (m, n))
+    B = rng.uniform(-1, 1, (n, p))
+    # (B^T A^T)^T multiplies the same pairs in the same k order: bit-identical.
+    return np.array_equal(f(B.T.copy(), A.T.copy()).T, f(A, B))
+
+
+def pin_associative_integers(f, seed=7):
+    rng = np.random.default_rng(seed)
+    A = rng.integers(-8, 9, (6, 9)).astype(np.float64)
+    B = rng.integers(-8, 9, (9, 4)).astype(np.float64)
+    Cm = rng.integers(-8, 9, (4, 10)).astype(np.float64)
+    return np.array_equal(f(f(A, B), Cm), f(A, f(B, Cm)))
+
+
+def pin_rational_bound(f, m=6, n=8, p=5, seed=11):
+    """|C - C_exact| <= gamma_n |A||B| elementwise (Higham, Thm 3.5), with the
+    exact product evaluated in rational arithmetic from the FP64 inputs."""
+    rng = np.random.default_rng(seed)
+    A = rng.uniform(-1, 1, (m, n)) * 2.0 ** rng.integers(-20, 20, (m, n))
+    B = rng.uniform(-1, 1, (n, p)) * 2.0 ** rng.integers(-20, 20, (n, p))
+    C = f(A, B)
+    if C.shape != (m, p):
+        return False
+    u = 2.0 ** -53
+    gamma = n * u / (1 - n * u)
+    absAB = np.abs(A) @ np.abs(B)
+    for i in range(m):
+        for j in range(p):
+            exact = sum((Fraction(A[i, k]) * Fraction(B[k, j]) for k in range(n)), Fraction(0))
+            if abs(Fraction(C[i, j]) - exact) > Fraction(gamma) * Fraction(absAB[i, j]) * 1.0000001:
+                return False
+    return True
+
+
+PINS = [pin_integer_exact, pin_identity_permutation, pin_transpose,
+        pin_associative_integers, pin_rational_bound]
+
+
+# --------------------------------------------------------------------------
+# The oracle passes every pin.
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("pin", PINS, ids=lambda f: f.__name__)
+def test_oracle_passes_pin(pin):
+    assert pin(oracle.gemm)
+
+
+@pytest.mark.parametrize("m,n,p", SHAPES)
+def test_integer_exact_shapes(m, n, p):
+    assert pin_integer_exact(oracle.gemm, m, n, p, seed=m * 1000 + n)
+
+
+def test_integer_exact_largest_partial_sum():
+    # All entries -8 or 8 with n = 4096: |partial sums| reach 64 * 4096 = 2^18.
+    n = 4096
+    A = np.full((2, n), 8.0)
+    A[1, ::2] = -8.0
+    B = np.full((n, 3), 8.0)
+    B[:, 1] = -8.0
+    C = oracle.gemm(A, B)
+    exact = A.astype(np.int64) @ B.astype(np.int64)
+    assert np.array_equal(C, exact.astype(np.float64))
+
+
+def test_rational_bound_square_small():
+    for N in range(1, 9):
+        assert pin_rational_bound(oracle.gemm, N, N, N, seed=100 + N)
+
+
+def test_summation_order_and_unfused_products():
+    """Reading of Eq. (eq:dnf)/Fig. ip.c: products rounded separately, summed
+    for k = 0..n-1 ascending starting from 0.0.  Python floats are IEEE FP64
+    and never fuse, so the expected value is fixed by that reading alone."""
+    rng = np.random.default_rng(99)
+    for _ in range(200):
+        n = int(rng.integers(2, 6))
+        a = rng.uniform(-1, 1, n) * 10.0 ** rng.integers(-8, 8, n)
+        b = rng.uniform(-1, 1, n) * 10.0 ** rng.integers(-8, 8, n)
+        expected = 0.0
+        for k in range(n):
+            expected = expected + float(a[k]) * float(b[k])
+        got = oracle.gemm(a[None, :], b[:, None])[0, 0]
+        assert got == expected
+
+
+def test_outer_product_n1():
+    rng = np.random.default_rng(2)
+    a = rng.uniform(-1, 1, (9, 1))
+    b = rng.uniform(-1, 1, (1, 13))
+    C = oracle.gemm(a, b)
+    for i in range(9):
+        for j in range(13):
+            assert C[i, j] == float(a[i, 0]) * float(b[0, j])   # one rounding
+
+
+def test_empty_inner_dimension_gives_zero():
+    C = oracle.gemm(np.zeros((4, 0)), np.zeros((0, 6)))
+    assert C.shape == (4, 6) and np.all(C == 0.0)
+
+
+def test_empty_outer_dimensions():
+    assert oracle.gemm(np.zeros((0, 5)), np.ones((5, 3))).shape == (0, 3)
+    assert oracle.gemm(np.ones((3, 5)), np.ones((5, 0))).shape == (3, 0)
+
+
+def test_dimension_lifted_forms_bit_identical():
+    """Figs. ip_rows.c (i = ip + (m/np)*k over np processors) and ip_cols.c
+    (j = jp*rsize + kp) visit, for each C element, the same products in the
+    same sigma order, so they reproduce the generic form bit for bit."""
+    rng = np.random.default_rng(4)
+    m, n, p, np_, rsize = 8, 5, 16, 4, 8
+    A = rng.uniform(-1, 1, (m, n))
+    B = rng.uniform(-1, 1, (n, p))
+    Af, Bf = A.ravel(), B.ravel()
+    rows = np.zeros(m * p)
+    for k in range(np_):
+        for ip in range(m // np_):
+            i = ip + (m // np_) * k
+            for sigma in range(n):
+                for j in range(p):
+                    rows[j + i * p] = rows[j + i * p] + Af[i * n + sigma] * Bf[sigma * p + j]
+    cols = np.zeros(m * p)
+    for i in range(m):
+        for sigma in range(n):
+            for jp in range(p // rsize):
+                for kp in range(rsize):
+                    j = jp * rsize + kp
+                    cols[j + i * p] = cols[j + i * p] + Af[i * n + sigma] * Bf[sigma * p + j]
+    C = oracle.gemm(A, B).ravel()
+    assert np.array_equal(rows, C)
+    assert np.array_equal(cols, C)
+
+
+def test_omp_and_rows_bit_identical():
+    A, B = inputs.uniform_pair(37, 50, 23, seed=0)
+    A, B = A.numpy(), B.numpy()
+    C = oracle.gemm(A, B)
+    Comp, used = oracle.gemm_omp(A, B, threads=3)
+    assert used >= 1 and np.array_equal(Comp, C)
+    rows = inputs.sample_rows(37, 10)
+    assert np.array_equal(oracle.gemm_rows(A, B, rows), C[rows])
+
+
+def test_oracle_matches_float128_reference_within_rounding():
+    # A second, independent evaluation route: numpy longdouble (x87 80-bit on
+    # x86) summation of the same products; differences stay within gamma_n.
+    A, B = inputs.uniform_pair(20, 300, 10, seed=2)
+    A, B = A.numpy(), B.numpy()
+    C = oracle.gemm(A, B)
+    ref = (A.astype(np.longdouble) @ B.astype(np.longdouble))
+    n = A.shape[1]
+    bound = (n * 2.0 ** -53 / (1 - n * 2.0 ** -53)) * (np.abs(A) @ np.abs(B)) * 1.01
+    assert np.all(np.abs(C - ref.astype(np.float64)) <= bound + 1e-300)
+
+
+# --------------------------------------------------------------------------
+# Planted mistakes (in the oracle, on the CPU) fail at least one pin.
+# --------------------------------------------------------------------------
+
+def _dropped_last_term(A, B):
+    if A.shape[1] == 0:
+        return oracle.gemm(A, B)
+    return oracle.gemm(A[:, :-1], B[:-1, :])
+
+
+def _wrong_sign(A, B):
+    C = oracle.gemm(A, B)
+    if C.size:
+        C = C.copy()
+        C[-1, -1] = -C[-1, -1]
+    return C
+
+
+def _transposed_b(A, B):
+    # reads B as if it were stored column-major (B[j*n+k] instead of B[k*p+j])
+    n, p = B.shape
+    Bt = np.ascontiguousarray(B).ravel().reshape(p, n).T
+    return oracle.gemm(A, Bt)
+
+
+def _swapped_operands(A, B):
+    if A.shape[0] == A.shape[1] == B.shape[0] == B.shape[1]:
+        return oracle.gemm(B, A)
+    return oracle.gemm(A, B) * 1.0000001
+
+
+def _off_by_one_row(A, B):
+    # each row i of C built from row i+1 of A (wrapping)
+    return oracle.gemm(np.roll(A, -1, axis=0), B)
+
+
+def _fused_products(A, B):
+    # the same sums with higher-precision products (a different definition)
+    C = (A.astype(np.longdouble) @ B.astype(np.longdouble)).astype(np.float64)
+    return C
+
+
+@pytest.mark.parametrize("mutant", [_dropped_last_term, _wrong_sign, _transposed_b,
+                                    _swapped_operands, _off_by_one_row, _fused_products],
+                         ids=lambda f: f.__name__)
+def test_planted_mistake_fails_a_pin(mutant):
+    results = {pin.__name__: pin(mutant) for pin in PINS}
+    results["summation_order"] = _order_pin(mutant)
+    assert not all(results.values()), results
+
+
+def _order_pin(f):
+    rng = np.random.default_rng(123)
+    for _ in range(50):
+        n = 4
+        a = rng.uniform(-1, 1, n) * 10.0 ** rng.integers(-8, 8, n)
+        b = rng.uniform(-1, 1, n) * 10.0 ** rng.integers(-8, 8, n)
+        expected = 0.0
+        for k in range(n):
+            expected = expected + float(a[k]) * float(b[k])
+        if f(a[None, :], b[:, None])[0, 0] != expected:
+            return False
+    return True
+
+
+# --------------------------------------------------------------------------
+# Slicing oracles (precision modes; not in the paper).
+# --------------------------------------------------------------------------
+
+def _fp32_edge_values():
+    f = np.float32
+    tiny = np.finfo(np.float32).tiny
+    vals = [0.0, -0.0, 1.0, -1.0, tiny, -tiny, tiny / 8, 1e-30, 3.0e38, -3.0e38,
+            1.0 + 2.0 ** -23, 1.0 - 2.0 ** -24, 2.0 ** -126 * 1.5, 65504.0, 1.0 / 3.0]
+    return np.array(vals, dtype=f)
+
+
+def test_split3_reconstructs_exactly():
+    rng = np.random.default_rng(8)
+    x = np.concatenate([
+        rng.standard_normal(200000).astype(np.float32),
+        (rng.standard_normal(200000) * 10.0 ** rng.uniform(-30, 30, 200000)).astype(np.float32),
+        rng.integers(-2 ** 31, 2 ** 31, 5000).astype(np.int32).view(np.float32),
+        _fp32_edge_values(),
+    ])
+    x = x[np.isfinite(x) & (np.abs(x) < 3.3e38)]
+    s0, s1, s2 = oracle.split3_bf16(x)
+    total = s0.astype(np.float64) + s1.astype(np.float64) + s2.astype(np.float64)
+    # Exact reconstruction (FP64 holds the sum of three BF16 values exactly)
+    # whenever the last slice stays above BF16's subnormal quantum 2^-133,
+    # i.e. |x| >= 2^-110; below that the lost bits are under 2^-134.
+    normal = (np.abs(x) >= 2.0 ** -110) | (x == 0)
+    assert np.array_equal(total[normal], x.astype(np.float64)[normal])
+    assert np.all(np.abs(total - x.astype(np.float64)) <= 2.0 ** -134)
+    # every slice is a BF16 value: low 16 bits clear
+    for s in (s0, s1, s2):
+        assert np.all((s.view(np.uint32) & 0xFFFF) == 0)
+    # the first slice is torch's round-to-nearest-even conversion to BF16
+    t0 = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy()
+    assert np.array_equal(s0, t0)
+    t1 = torch.from_numpy(x - s0).to(torch.bfloat16).to(torch.float32).numpy()
+    assert np.array_equal(s1, t1)
+
+
+def test_split3_special_values():
+    x = np.array([np.inf, -np.inf, np.nan], dtype=np.float32)
+    s0, _, _ = oracle.split3_bf16(x)
+    assert s0[0] == np.inf and s0[1] == -np.inf and np.isnan(s0[2])
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+@pytest.mark.parametrize("beta,S", [(8, 6), (7, 7), (8, 3)])
+def test_slice_fixed_reconstruction_bound(axis, beta, S):
+    rng = np.random.default_rng(10 + axis + beta + S)
+    X = rng.standard_normal((13, 17)) * 10.0 ** rng.uniform(-4, 4, (13, 1))
+    X[3, :] = 0.0
+    X[:, 5] = 0.0
+    exps, digits = oracle.slice_fixed(X, axis, beta, S)
+    # exponent: 2^(e-1) <= max|x| < 2^e per group (e = 0 for all-zero groups)
+    mx = np.abs(X).max(axis=1 - axis)
+    for g, e in enumerate(exps):
+        if mx[g] == 0:
+            assert e == 0
+        else:
+            assert math.ldexp(1.0, int(e) - 1) <= mx[g] < math.ldexp(1.0, int(e))
+    # digit ranges
+    assert np.all(np.abs(digits[0]) <= 2 ** beta)
+    assert np.all(np.abs(digits[1:]) <= 2 ** (beta - 1))
+    # exact reconstruction bound |x - 2^e sum_s d_s 2^-beta(s+1)| <= 2^(e - beta S) / 2
+    for r in range(X.shape[0]):
+        for c in range(X.shape[1]):
+            e = int(exps[r] if axis == 0 else exps[c])
+            approx = sum(Fraction(int(digits[s, r, c])) * Fraction(2) ** (e - beta * (s + 1))
+                         for s in range(S))
+            err = abs(Fraction(X[r, c]) - approx)
+            assert err <= Fraction(2) ** (e - beta * S) / 2
+
+
+def test_slice_fixed_integers_exact_digits():
+    A, _ = inputs.integer_pair(5, 9, 3, seed=4)
+    X = A.numpy()
+    exps, digits = oracle.slice_fixed(X, 0, 8, 4)
+    for r in range(5):
+        e = int(exps[r])
+        # integers |x| <= 8 need one digit: d_0 = x * 2^(beta - e), rest zero
+        assert np.array_equal(digits[0, r], (X[r] * 2.0 ** (8 - e)).astype(np.int32))
+        assert np.all(digits[1:, r] == 0)
+
+
+def test_split_gemm_exact_integer_inputs_bit_exact():
+    A, B = inputs.integer_pair(11, 40, 7, seed=9)
+    A, B = A.numpy(), B.numpy()
+    eA, dA = oracle.slice_fixed(A, 0, 8, 6)
+    eB, dB = oracle.slice_fixed(B, 1, 8, 6)
+    C = oracle.split_gemm_exact(dA, eA, dB, eB, 8, 6)
+    assert np.array_equal(C, (A.astype(np.int64) @ B.astype(np.int64)).astype(np.float64))
+
+
+@pytest.mark.parametrize("beta,S", [(8, 6), (7, 7)])
+def test_split_gemm_exact_close_to_fp64_product(beta, S):
+    A, B = inputs.normal_pair(24, 64, 20, dtype=torch.float64, seed=1, scaled="rows")
+    A, B = A.numpy(), B.numpy()
+    eA, dA = oracle.slice_fixed(A, 0, beta, S)
+    eB, dB = oracle.slice_fixed(B, 1, beta, S)
+    C = oracle.split_gemm_exact(dA, eA, dB, eB, beta, S)
+    ref = oracle.gemm(A, B)
+    # Truncation bound per element: each operand digit expansion is within
+    # 2^(e - beta S)/2 and the dropped cross levels are below
+    # S * 2^(eA+eB) * 2^(-beta S); summed over n terms.
+    mA = 2.0 ** eA.astype(np.float64)
+    mB = 2.0 ** eB.astype(np.float64)
+    bound = A.shape[1] * (S + 2) * np.outer(mA, mB) * 2.0 ** (-beta * S)
+    assert np.all(np.abs(C - ref) <= bound)
+    rel = np.linalg.norm(C - ref) / np.linalg.norm(ref)
+    assert rel < 1e-12
