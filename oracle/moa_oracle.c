@@ -137,16 +137,18 @@ void moa_oracle_split3_bf16(int64_t count, const float* x,
 /* slicing in the manner of Ozaki, Ogita, Oishi & Rump (2012).               */
 /* Each group (a row of A, or a column of B) gets the exponent e such that   */
 /* max|x| over the group lies in [2^(e-1), 2^e) (e = 0 for an all-zero       */
-/* group).  Each x of the group is scaled to t = x * 2^-e, |t| < 1, and cut  */
-/* into S signed integer digits of radix 2^beta, nearest first:              */
-/*   t <- t*2^beta; d_s = rint(t); t <- t - d_s      (s = 0..S-1)            */
-/* so that x = 2^e * sum_s d_s 2^(-beta(s+1)) + 2^e * 2^(-beta S) * t_rest, */
-/* |t_rest| <= 1/2.  |d_0| <= 2^beta and |d_s| <= 2^(beta-1) for s >= 1.     */
+/* group).  Each x of the group is scaled to X = x * 2^(beta*S - e), so      */
+/* |X| < 2^(beta*S), and rounded once to the nearest integer D (ties to      */
+/* even).  D is then written in balanced radix 2^beta with S digits:         */
+/*   D = sum_{s=0}^{S-1} d_s 2^(beta(S-1-s)),                                */
+/*   d_s in [-2^(beta-1), 2^(beta-1)) for s >= 1 (taken from the bottom),   */
+/*   |d_0| <= 2^beta,                                                        */
+/* so that |x - 2^e sum_s d_s 2^(-beta(s+1))| <= 2^(e - beta S) / 2.         */
 /* ------------------------------------------------------------------------ */
 
 /* X is rows x cols row-major.  axis 0: one exponent per row (length rows);
  * axis 1: one exponent per column (length cols).  digits is S x rows x cols
- * (slice-major), int32. */
+ * (slice-major), int32.  Requires beta * S <= 60. */
 void moa_oracle_slice_fixed(int64_t rows, int64_t cols, const double* X,
                             int axis, int beta, int S,
                             int32_t* exps, int32_t* digits)
@@ -164,17 +166,23 @@ void moa_oracle_slice_fixed(int64_t rows, int64_t cols, const double* X,
         if (mu != 0.0) (void)frexp(mu, &e);     /* mu = f * 2^e, f in [1/2, 1) */
         exps[g] = e;
     }
-    const double radix = ldexp(1.0, beta);
+    const int64_t radix = (int64_t)1 << beta;
+    const int64_t half = radix / 2;
     for (int64_t r = 0; r < rows; ++r) {
         for (int64_t c = 0; c < cols; ++c) {
             const int e = axis == 0 ? exps[r] : exps[c];
-            double t = ldexp(X[r * cols + c], -e);
-            for (int s = 0; s < S; ++s) {
-                t = t * radix;
-                const double d = rint(t);
-                t = t - d;
-                digits[((int64_t)s * rows + r) * cols + c] = (int32_t)d;
+            /* x * 2^(beta S - e) is exact (|X| < 2^60, no overflow; a result
+             * in the subnormal range rounds to 0 below anyway), and rint in
+             * the default rounding mode rounds half to even. */
+            int64_t D = (int64_t)rint(ldexp(X[r * cols + c], beta * S - e));
+            for (int s = S - 1; s >= 1; --s) {
+                int64_t low = D % radix;               /* C remainder: sign of D */
+                if (low < 0) low += radix;             /* now in [0, radix) */
+                if (low >= half) low -= radix;         /* balanced: [-half, half) */
+                digits[((int64_t)s * rows + r) * cols + c] = (int32_t)low;
+                D = (D - low) / radix;                 /* exact division */
             }
+            digits[((int64_t)0 * rows + r) * cols + c] = (int32_t)D;
         }
     }
 }

@@ -321,7 +321,7 @@ def test_split3_special_values():
 
 
 @pytest.mark.parametrize("axis", [0, 1])
-@pytest.mark.parametrize("beta,S", [(8, 6), (7, 7), (8, 3)])
+@pytest.mark.parametrize("beta,S", [(8, 6), (7, 7), (8, 3), (8, 7)])
 def test_slice_fixed_reconstruction_bound(axis, beta, S):
     rng = np.random.default_rng(10 + axis + beta + S)
     X = rng.standard_normal((13, 17)) * 10.0 ** rng.uniform(-4, 4, (13, 1))
@@ -335,9 +335,9 @@ def test_slice_fixed_reconstruction_bound(axis, beta, S):
             assert e == 0
         else:
             assert math.ldexp(1.0, int(e) - 1) <= mx[g] < math.ldexp(1.0, int(e))
-    # digit ranges
+    # digit ranges: |d_0| <= 2^beta, d_s in [-2^(beta-1), 2^(beta-1)) for s >= 1
     assert np.all(np.abs(digits[0]) <= 2 ** beta)
-    assert np.all(np.abs(digits[1:]) <= 2 ** (beta - 1))
+    assert np.all(digits[1:] >= -2 ** (beta - 1)) and np.all(digits[1:] < 2 ** (beta - 1))
     # exact reconstruction bound |x - 2^e sum_s d_s 2^-beta(s+1)| <= 2^(e - beta S) / 2
     for r in range(X.shape[0]):
         for c in range(X.shape[1]):
@@ -385,3 +385,34 @@ def test_split_gemm_exact_close_to_fp64_product(beta, S):
     assert np.all(np.abs(C - ref) <= bound)
     rel = np.linalg.norm(C - ref) / np.linalg.norm(ref)
     assert rel < 1e-12
+
+
+def _digits_by_fractions(x, e, beta, S):
+    """Exact-rational route: D = round-half-even(x * 2^(beta S - e)), then
+    balanced base-2^beta digits taken from the bottom."""
+    D = round(Fraction(x) * Fraction(2) ** (beta * S - e))   # Fraction.__round__: half to even
+    out = [0] * S
+    radix, half = 2 ** beta, 2 ** (beta - 1)
+    for s in range(S - 1, 0, -1):
+        low = D % radix
+        if low >= half:
+            low -= radix
+        out[s] = low
+        D = (D - low) // radix
+    out[0] = D
+    return out
+
+
+def test_slice_fixed_matches_exact_rational_route():
+    rng = np.random.default_rng(21)
+    X = rng.standard_normal((9, 11)) * 10.0 ** rng.uniform(-6, 6, (9, 11))
+    # exact ties: values whose scaled form ends in exactly one half unit
+    X[0, 0] = 1.0 + 2.0 ** -48          # with e = 1, beta S = 48: X = 2^47 + 0.5
+    X[0, 1] = -(1.0 + 3 * 2.0 ** -48)
+    X[1, :] = 2.0 ** -1074              # subnormal row
+    for beta, S in [(8, 6), (7, 7), (8, 3)]:
+        exps, digits = oracle.slice_fixed(X, 0, beta, S)
+        for r in range(X.shape[0]):
+            for c in range(X.shape[1]):
+                want = _digits_by_fractions(X[r, c], int(exps[r]), beta, S)
+                assert [int(digits[s, r, c]) for s in range(S)] == want
