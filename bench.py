@@ -1,0 +1,460 @@
+#!/usr/bin/env python
+"""Benchmark of the B300-native MoA ONF GEMM (Eq. eq:dnf).
+
+Default workload: the square FP32 ONF GEMM at N = 8192 (uniform[-1,1) inputs,
+seed 0) on the FP32-via-TF32 tensor-core path, one GEMM per step; the other
+precision modes are measured on the same inputs and reported under "modes".
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl moa|reference]
+                  [--workload square|split_f32|split_f64|bf16|f64] [--n N]
+
+Under torchrun (N > 1) every rank runs its own replica of the workload (the
+GEMM is not sharded: replicas only); timing is the max over ranks and the
+value is the total over ranks.  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}
+# Dense tensor rates relative to BF16 (nominal datasheet figures).
+NOMINAL_RATIO = {"bf16": 1.0, "tf32": 1.1 / 2.25, "fp8": 2.0}
+
+
+def load_peaks():
+    try:
+        with open(MEASURED) as f:
+            d = json.load(f)
+        d["source"] = "measured"
+        return d
+    except Exception:
+        d = dict(FALLBACK)
+        d["source"] = "fallback"
+        return d
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="moa_clocks_", suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_identity(dev):
+    import torch
+    props = torch.cuda.get_device_properties(dev)
+    try:
+        return f"{props.pci_domain_id:08x}:{props.pci_bus_id:02x}:{props.pci_device_id:02x}.0"
+    except Exception:
+        return None
+
+
+class Energy:
+    """NVML total-energy counter (mJ) of the device."""
+
+    def __init__(self, pci):
+        self.h = None
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            self.nv = pynvml
+            if pci:
+                self.h = pynvml.nvmlDeviceGetHandleByPciBusId(pci.encode())
+            else:
+                self.h = pynvml.nvmlDeviceGetHandleByIndex(0)
+        except Exception:
+            self.h = None
+
+    def read_j(self):
+        if self.h is None:
+            return None
+        try:
+            return self.nv.nvmlDeviceGetTotalEnergyConsumption(self.h) / 1000.0
+        except Exception:
+            return None
+
+
+# ------------------------------------------------------------------ distributed
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ workloads
+MODE_OF = {"square": "tf32", "bf16": "bf16", "split_f32": "f32_split",
+           "split_f64": "f64_split_f32in", "f64": "f64", "simt": "f32_simt"}
+
+
+def make_inputs(mode, N):
+    import torch
+    from paper_2306_11148_b300 import inputs, moa
+    dt = moa.MODES[mode]
+    if mode in ("f32_split", "f64_split_f32in"):
+        A, B = inputs.normal_pair(N, N, N, dtype=torch.float32, seed=0)
+    else:
+        A, B = inputs.square_uniform(N, moa.in_dtype(dt), seed=0)
+    return dt, A, B
+
+
+def time_device(fn, steps, warmup, stream, ws):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        fn()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    return ev0.elapsed_time(ev1) / 1000.0
+
+
+def bench_mode(mode, N, steps, warmup, ws, stream, want_energy=False, energy=None,
+               want_e2e=False):
+    import torch
+    from paper_2306_11148_b300 import moa
+    dt, A, B = make_inputs(mode, N)
+    Ad, Bd = A.cuda(), B.cuda()
+    C = torch.empty((N, N), dtype=moa.out_dtype(dt), device="cuda")
+    wspace = moa.Workspace(torch.device("cuda"))
+    need = moa.moa_gemm_workspace_size(N, N, N, dt, 0)
+    wptr, wbytes = wspace.get(need)
+    sh = int(stream.cuda_stream)
+    st = moa.moa_stats()
+
+    def step():
+        rc = moa.moa_gemm_ex(N, N, N, dt, Ad.data_ptr(), Bd.data_ptr(), C.data_ptr(), 0, wptr,
+                             wbytes, sh, st)
+        if rc != 0:
+            raise moa.MoaError(rc, moa.last_error())
+
+    with torch.cuda.stream(stream):
+        t = time_device(step, steps, warmup, stream, ws)
+    moa.check(moa.moa_sync_status(sh))
+    out = {"mode": mode, "N": N, "seconds": t, "steps": steps,
+           "flops_per_step": 2.0 * N ** 3, "kernels_per_step": int(st.kernels),
+           "tile": [int(st.block_m), int(st.block_n), int(st.block_k)],
+           "products": int(st.products), "slices": int(st.slices)}
+    if want_energy and energy is not None and energy.h is not None:
+        per = t / steps
+        reps = max(3, int(math.ceil(1.5 / max(per, 1e-6))))
+        torch.cuda.synchronize()
+        j0 = energy.read_j()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for _ in range(reps):
+                step()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        j1 = energy.read_j()
+        if j0 is not None and j1 is not None:
+            out["energy"] = {"j_per_gemm": (j1 - j0) / reps, "window_s": t1 - t0, "reps": reps,
+                             "avg_w": (j1 - j0) / (t1 - t0)}
+    if want_e2e:
+        out["e2e"] = bench_e2e(dt, A, B, C, N, max(2, min(steps, 5)), 1, stream, ws)
+    # oracle spot check of a few rows (cheap) to tie the timed output to parity
+    try:
+        import numpy as np
+
+        import oracle
+        rows = np.array([0, N // 3, N - 1], dtype=np.int64)
+        ref = oracle.gemm_rows(A.double().numpy(), B.double().numpy(), rows)
+        got = C[torch.from_numpy(rows).cuda()].cpu().double().numpy()
+        out["rel_err_sampled_rows"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    except Exception as e:  # pragma: no cover - informational only
+        out["rel_err_sampled_rows"] = f"unavailable: {e}"
+    del Ad, Bd, C
+    return out
+
+
+def bench_e2e(dt, A, B, C, N, steps, warmup, stream, ws):
+    """Same GEMM through the C ABI with host buffers: H2D of A and B from pinned
+    memory, the GEMM, and D2H of C, all inside the timed region."""
+    import torch
+    from paper_2306_11148_b300 import moa
+    Ah = A.pin_memory()
+    Bh = B.pin_memory()
+    Ch = torch.empty(C.shape, dtype=C.dtype, pin_memory=True)
+    Ad = torch.empty_like(A, device="cuda")
+    Bd = torch.empty_like(B, device="cuda")
+    wspace = moa.Workspace(torch.device("cuda"))
+    wptr, wbytes = wspace.get(moa.moa_gemm_workspace_size(N, N, N, dt, 0))
+    sh = int(stream.cuda_stream)
+
+    def step():
+        Ad.copy_(Ah, non_blocking=True)
+        Bd.copy_(Bh, non_blocking=True)
+        moa.check(moa.moa_gemm_ex(N, N, N, dt, Ad.data_ptr(), Bd.data_ptr(), C.data_ptr(), 0,
+                                  wptr, wbytes, sh, None))
+        Ch.copy_(C, non_blocking=True)
+
+    with torch.cuda.stream(stream):
+        t = time_device(step, steps, warmup, stream, ws)
+    h2d = A.numel() * A.element_size() + B.numel() * B.element_size()
+    d2h = C.numel() * C.element_size()
+    return {"seconds": t, "steps": steps, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+def cpu_baseline(N, dtype_name, seconds_target=8.0):
+    """The oracle, as it stands, on sampled rows of the same N^3 problem, all
+    host cores (OpenMP over rows); TFLOP/s of algorithmic work."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2306_11148_b300 import inputs
+    tdt = torch.float32 if dtype_name != "f64" else torch.float64
+    A, B = inputs.square_uniform(N, tdt, seed=0)
+    A = A.double().numpy()
+    B = B.double().numpy()
+    rows = 8
+    cores = os.cpu_count() or 1
+    while True:
+        idx = inputs.sample_rows(N, rows, seed=1)
+        t0 = time.perf_counter()
+        _, used = oracle.gemm_omp(A[idx], B, threads=0)
+        dt = time.perf_counter() - t0
+        if dt > seconds_target / 4 or rows >= N:
+            break
+        rows = min(N, rows * 4)
+    flops = 2.0 * rows * N * N
+    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": int(used), "kind": "oracle",
+            "sample": f"{rows} of {N} rows of the N={N} FP64 ONF GEMM (i-k-j loop, OpenMP over "
+                      f"rows), {dt:.2f} s", "host_cores": cores}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    N = args.n
+    per_step = []
+    for _ in range(args.warmup):
+        cpu_baseline(N, "f32", seconds_target=2.0)
+    for _ in range(args.steps):
+        per_step.append(cpu_baseline(N, "f32", seconds_target=4.0))
+    v = sum(x["value"] for x in per_step) / len(per_step)
+    line = {"impl": "reference", "metric": "GEMM TFLOP/s", "value": v, "unit": "TFLOP/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"square ONF GEMM N={N} (FP32 inputs), CPU oracle on "
+                                   "sampled rows", "N": N},
+            "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": per_step[0]["cores"],
+                             "kind": "oracle", "sample": per_step[0]["sample"]},
+            "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="moa", choices=["moa", "reference"])
+    ap.add_argument("--workload", default="square", choices=list(MODE_OF))
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--no-extras", action="store_true", help="skip the other-mode measurements")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    import torch
+    from paper_2306_11148_b300 import build as moa_build
+    from paper_2306_11148_b300 import moa
+    if rank == 0 and not os.path.exists(moa.LIB_PATH):
+        moa_build.build()
+    barrier(ws)
+    torch.cuda.set_device(local)
+    moa.lib()
+    peaks = load_peaks()
+    pci = gpu_identity(local)
+    energy = Energy(pci)
+    stream = torch.cuda.Stream()
+    mode = MODE_OF[args.workload]
+    N = args.n
+
+    clocks = ClockSampler(pci)
+    clocks.start()
+    main_res = bench_mode(mode, N, args.steps, args.warmup, ws, stream, want_energy=True,
+                          energy=energy, want_e2e=True)
+    clk = clocks.stop()
+
+    t_max = max_over_ranks(main_res["seconds"], ws)
+    total_flops = main_res["flops_per_step"] * args.steps * ws
+    value = total_flops / t_max / 1e12
+    ms_per_step = t_max / args.steps * 1e3
+
+    e2e = main_res.get("e2e", {})
+    e2e_t = max_over_ranks(e2e.get("seconds", float("nan")), ws)
+    e2e_val = main_res["flops_per_step"] * e2e.get("steps", 1) * ws / e2e_t / 1e12
+
+    # roofline of the dominant kernel (the tensor-core GEMM): algorithmic
+    # flops per launch / average launch duration (one GEMM kernel per step on
+    # aligned shapes; pre-pass kernels of split modes are small HBM passes).
+    kdtype = {"tf32": "tf32", "bf16": "bf16", "f32_split": "bf16",
+              "f64_split_f32in": "bf16"}.get(mode)
+    if kdtype:
+        peak = peaks["bf16_tflops"] * NOMINAL_RATIO[kdtype]
+        achieved = main_res["flops_per_step"] * max(1, main_res["products"]) / \
+            (main_res["seconds"] / args.steps) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{peaks['source']} bf16 x nominal {kdtype}/bf16 ratio",
+                "kernel": "dense_tc_kernel" if mode in ("tf32", "bf16") else "split_gemm_kernel"}
+    else:
+        roof = {"bound": "alu", "achieved": value / ws, "peak": None, "unit": "TFLOP/s",
+                "frac": None, "traffic": None}
+
+    modes = {}
+    if not args.no_extras and rank == 0 and ws == 1:
+        for m2, n2 in [("bf16", N), ("f32_split", N), ("f64_split_f32in", N), ("f32_simt", N // 2),
+                       ("f64", N // 4)]:
+            if m2 == mode:
+                continue
+            try:
+                r = bench_mode(m2, n2, 3, 2, 1, stream, want_energy=(n2 == N), energy=energy)
+                r["tflops"] = r["flops_per_step"] * r["steps"] / r["seconds"] / 1e12
+                modes[m2] = r
+            except Exception as e:  # report, do not hide
+                modes[m2] = {"error": str(e)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(N, "f32")
+
+    if rank == 0:
+        line = {
+            "metric": "GEMM TFLOP/s (FP32 ONF GEMM, TF32 tensor path)",
+            "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"tf32": "tf32", "bf16": "bf16", "f32_split": "bf16x6",
+                      "f64_split_f32in": "bf16-digits", "f64": "f64",
+                      "f32_simt": "f32"}[mode],
+            "data": "synthetic",
+            "config": {"workload": f"square ONF GEMM m=n=p={N}, FP32 row-major "
+                                   f"uniform[-1,1) seed 0, mode {mode}",
+                       "N": N, "mode": mode, "parallelism": f"replicas x{ws}",
+                       "l2": "inputs larger than L2 (3 x N^2 x 4 B)"},
+            "rel_err_sampled_rows": main_res.get("rel_err_sampled_rows"),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": "TFLOP/s",
+                    "h2d_bytes_per_step": e2e.get("h2d_bytes_per_step"),
+                    "d2h_bytes_per_step": e2e.get("d2h_bytes_per_step")},
+            "gpu_launches": main_res["kernels_per_step"] * args.steps,
+            "clocks": clk,
+            "energy": main_res.get("energy"),
+            "tile": main_res["tile"],
+            "modes": modes,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

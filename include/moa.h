@@ -1,0 +1,151 @@
+/*
+ * moa.h -- C ABI of the B300-native MoA ONF GEMM library (libmoa.so).
+ *
+ * The operation (Mullin, "From array algebra to energy efficiency on GPUs",
+ * Sec. 2, Eq. (eq:dnf) and its address form):
+ *
+ *     C[(i*p) + j] := sum_{k=0}^{n-1} A[(i*n) + k] * B[(k*p) + j]
+ *     0 <= i < m,  0 <= j < p,  0 <= k < n          (Eqs. (eq:shapes), (eq:indices))
+ *
+ * Layout: A is m x n, B is n x p and C is m x p, each a dense row-major array
+ * starting at the given pointer (the gamma_row layout of the Appendix); there
+ * are no leading-dimension arguments.  C is assigned, not accumulated into:
+ * callers need not clear it.
+ *
+ * Memory: A, B, C, workspaces and the serving arena are DEVICE pointers owned
+ * by the caller (allocate them with cudaMalloc or PyTorch).  The library
+ * allocates device memory in exactly two places, both documented below:
+ * moa_gemm()'s internal workspace and nothing else.  Streams are passed as
+ * `void*` holding a cudaStream_t (NULL = the legacy default stream).
+ *
+ * Errors: every entry point returns a moa_status.  Argument errors are
+ * detected on the host before anything is launched and leave C untouched;
+ * moa_last_error() then gives a message (thread-local).  Launches are
+ * asynchronous on the given stream; a device-side failure (a pipeline wait
+ * that ran past its time limit) is recorded in a per-device status word and
+ * reported by moa_sync_status().
+ *
+ * Precision modes (moa_dtype): see the enum.  Tolerances the test suite
+ * holds each mode to, as relative Frobenius error against the FP64 oracle:
+ * MOA_F64 1e-12, MOA_F64_SPLIT_* 1e-12, MOA_F32_SPLIT 1e-5, MOA_F32_TF32
+ * 5e-3, MOA_BF16 1e-2 (and bit-exact on integer-valued inputs in {-8..8}
+ * for every mode).
+ */
+#ifndef MOA_H_
+#define MOA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MOA_OK = 0,
+    MOA_ERR_ARG = -1,         /* negative size, NULL pointer with nonzero size, bad count */
+    MOA_ERR_DTYPE = -2,       /* unknown moa_dtype or unsupported slice count */
+    MOA_ERR_ALIGN = -3,       /* pointer not aligned to its element size */
+    MOA_ERR_WORKSPACE = -4,   /* workspace NULL or smaller than the *_workspace_size query */
+    MOA_ERR_NONFINITE = -5,   /* split modes: an input is NaN or +-Inf (seen by the pre-pass) */
+    MOA_ERR_CUDA = -6,        /* a CUDA runtime/driver call failed (see moa_last_error) */
+    MOA_ERR_TIMEOUT = -7,     /* a device pipeline wait ran past its limit; results invalid */
+    MOA_ERR_BUDGET = -8,      /* serving: the request alone exceeds the arena */
+    MOA_ERR_REJECTED = -9,    /* serving: rejected by the admission policy */
+    MOA_ERR_BUSY = -10,       /* serving: queue full */
+    MOA_ERR_UNSUPPORTED = -11 /* device is not sm_103 / sm_100 class */
+} moa_status;
+
+typedef enum {
+    MOA_F64 = 0,              /* A,B,C FP64.  Native FP64 arithmetic (DFMA).                  */
+    MOA_F32_TF32 = 1,         /* A,B,C FP32.  tcgen05 kind::tf32, FP32 accumulation.         */
+    MOA_F32_SIMT = 2,         /* A,B,C FP32.  Plain FP32 FFMA (comparison path).             */
+    MOA_BF16 = 3,             /* A,B BF16, C FP32.  tcgen05 kind::f16, FP32 accumulation.    */
+    MOA_F32_SPLIT = 4,        /* A,B,C FP32.  3 BF16 slices each, 6 slice products, FP32 acc.*/
+    MOA_F64_SPLIT_F32IN = 5,  /* A,B FP32, C FP64.  Integer-digit BF16 slices, exact         */
+                              /*   chunked accumulation, FP64 recombination.                 */
+    MOA_F64_SPLIT_F64IN = 6   /* A,B,C FP64.  As above with FP64 inputs.                     */
+} moa_dtype;
+
+/* Optional per-call report (may be NULL). */
+typedef struct {
+    int32_t block_m, block_n, block_k;   /* tile chosen by the planner */
+    int32_t slices;                      /* slices per operand (split modes), else 1 */
+    int32_t products;                    /* slice products issued per K block, else 1 */
+    int32_t grid;                        /* CTAs launched for the main kernel */
+    int64_t tiles;                       /* output tiles */
+    int32_t kernels;                     /* kernel launches made by this call */
+    int32_t padded;                      /* 1 if operands were copied to padded pitches */
+} moa_stats;
+
+/* ---------------------------------------------------------------------- */
+/* Single GEMM                                                             */
+/* ---------------------------------------------------------------------- */
+
+/* C := A . B on the legacy default stream, using a library-owned workspace
+ * that grows on demand (cudaMalloc) and is freed by moa_shutdown().  This is
+ * the one entry point that allocates device memory.  Split modes use their
+ * default slice count.  Asynchronous: synchronise (or moa_sync_status) before
+ * reading C on the host.
+ * m == 0 or p == 0: MOA_OK, nothing launched.  n == 0: C := 0. */
+int moa_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt,
+             const void* A, const void* B, void* C);
+
+/* Bytes of workspace moa_gemm_ex needs for this problem (0 if none).
+ * slices: split modes only (0 = default); ignored otherwise. */
+size_t moa_gemm_workspace_size(int64_t m, int64_t n, int64_t p, moa_dtype dt, int slices);
+
+/* C := A . B on `stream` with a caller-provided device workspace of at least
+ * moa_gemm_workspace_size(...) bytes (ws may be NULL when that size is 0).
+ * Allocates nothing.  stats may be NULL. */
+int moa_gemm_ex(int64_t m, int64_t n, int64_t p, moa_dtype dt,
+                const void* A, const void* B, void* C, int slices,
+                void* ws, size_t ws_bytes, void* stream, moa_stats* stats);
+
+/* ---------------------------------------------------------------------- */
+/* Grouped GEMM: `count` independent problems of any shapes in one          */
+/* persistent launch (the batching pattern).                                */
+/* ---------------------------------------------------------------------- */
+
+typedef struct {
+    int64_t m, n, p;
+    moa_dtype dt;             /* MOA_BF16 or MOA_F32_TF32; all descriptors of one call share it */
+    const void* A;
+    const void* B;
+    void* C;
+} moa_gemm_desc;
+
+size_t moa_gemm_grouped_workspace_size(int count, const moa_gemm_desc* descs);
+
+int moa_gemm_grouped(int count, const moa_gemm_desc* descs,
+                     void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Status and housekeeping                                                 */
+/* ---------------------------------------------------------------------- */
+
+/* Synchronises `stream`, then returns and clears the current device's
+ * status word: MOA_OK, MOA_ERR_TIMEOUT (a kernel gave up on a pipeline
+ * wait), MOA_ERR_NONFINITE (a split pre-pass saw NaN/Inf) or MOA_ERR_CUDA
+ * (the synchronisation itself failed). */
+int moa_sync_status(void* stream);
+
+/* Thread-local message describing the last non-OK status of this thread. */
+const char* moa_last_error(void);
+
+/* Per-wait time limit of device pipeline waits, in nanoseconds
+ * (default 2e9; also read from the MOA_WAIT_LIMIT_NS environment variable).
+ * Returns the previous value. */
+uint64_t moa_set_wait_limit_ns(uint64_t ns);
+
+/* Library version string. */
+const char* moa_version(void);
+
+/* Frees moa_gemm()'s internal workspace on every device that has one. */
+void moa_shutdown(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MOA_H_ */

@@ -1,0 +1,234 @@
+// api.cu -- the C ABI entry points of libmoa.so for single GEMMs (include/moa.h):
+// argument validation, workspace sizing, the padding of row pitches that TMA
+// cannot address, and dispatch to the kernels of each precision mode.
+//
+// The operation is Eq. (eq:dnf) of Sec. 2 over the row-major shapes of
+// Eqs. (eq:shapes)/(eq:indices); C is assigned (callers need not clear it).
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <mutex>
+#include <string>
+
+#include "internal.h"
+#include "split.h"
+
+namespace moa {
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool valid_dtype(int dt) { return dt >= MOA_F64 && dt <= MOA_F64_SPLIT_F64IN; }
+
+int in_size(moa_dtype dt) {
+    switch (dt) {
+        case MOA_F64:
+        case MOA_F64_SPLIT_F64IN:
+            return 8;
+        case MOA_BF16:
+            return 2;
+        default:
+            return 4;
+    }
+}
+
+int out_size(moa_dtype dt) {
+    switch (dt) {
+        case MOA_F64:
+        case MOA_F64_SPLIT_F32IN:
+        case MOA_F64_SPLIT_F64IN:
+            return 8;
+        default:
+            return 4;
+    }
+}
+
+bool is_tc_dense(moa_dtype dt) { return dt == MOA_BF16 || dt == MOA_F32_TF32; }
+
+// Elements per 16 bytes: TMA needs row pitches that are multiples of 16 bytes.
+int64_t tma_pitch(int64_t cols, int esize) { return round_up(cols, 16 / esize); }
+
+struct DenseWs {
+    bool pad_a, pad_b;
+    int64_t lda, ldb;
+    size_t a_bytes, b_bytes, total;
+};
+
+DenseWs dense_ws(int64_t m, int64_t n, int64_t p, moa_dtype dt) {
+    DenseWs w{};
+    const int es = in_size(dt);
+    w.lda = tma_pitch(n, es);
+    w.ldb = tma_pitch(p, es);
+    w.pad_a = w.lda != n;
+    w.pad_b = w.ldb != p;
+    w.a_bytes = w.pad_a ? align_up(static_cast<size_t>(m) * w.lda * es) : 0;
+    w.b_bytes = w.pad_b ? align_up(static_cast<size_t>(n) * w.ldb * es) : 0;
+    w.total = w.a_bytes + w.b_bytes;
+    if (!w.pad_a) w.lda = n;
+    if (!w.pad_b) w.ldb = p;
+    return w;
+}
+
+int validate(int64_t m, int64_t n, int64_t p, int dt, const void* A, const void* B, const void* C) {
+    if (!valid_dtype(dt)) return fail(MOA_ERR_DTYPE, "unknown moa_dtype");
+    if (m < 0 || n < 0 || p < 0) return fail(MOA_ERR_ARG, "negative dimension");
+    if (m > (int64_t(1) << 31) || n > (int64_t(1) << 31) || p > (int64_t(1) << 31))
+        return fail(MOA_ERR_ARG, "dimension above 2^31");
+    const moa_dtype d = static_cast<moa_dtype>(dt);
+    if (m > 0 && p > 0 && C == nullptr) return fail(MOA_ERR_ARG, "C is NULL");
+    if (m > 0 && p > 0 && n > 0 && (A == nullptr || B == nullptr))
+        return fail(MOA_ERR_ARG, "A or B is NULL");
+    const uintptr_t ia = reinterpret_cast<uintptr_t>(A), ib = reinterpret_cast<uintptr_t>(B),
+                    ic = reinterpret_cast<uintptr_t>(C);
+    if (ia % in_size(d) || ib % in_size(d) || ic % out_size(d))
+        return fail(MOA_ERR_ALIGN, "pointer not aligned to its element size");
+    if ((is_tc_dense(d) || is_split(d)) && m > 0 && n > 0 && p > 0 && (ia % 16 || ib % 16))
+        return fail(MOA_ERR_ALIGN, "tensor-core modes need 16-byte aligned A and B");
+    return MOA_OK;
+}
+
+// Library-owned workspace of moa_gemm(), one per device.
+std::mutex g_ws_mu;
+constexpr int kMaxDev = 64;
+void* g_ws[kMaxDev] = {nullptr};
+size_t g_ws_bytes[kMaxDev] = {0};
+
+}  // namespace
+
+size_t workspace_bytes(int64_t m, int64_t n, int64_t p, moa_dtype dt, int slices) {
+    if (m <= 0 || p <= 0 || n <= 0) return 0;
+    if (is_tc_dense(dt)) return dense_ws(m, n, p, dt).total;
+    if (is_split(dt)) return split_workspace_bytes(m, n, p, dt, slices);
+    return 0;
+}
+
+int gemm_ex(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const void* B, void* C,
+            int slices, void* ws, size_t ws_bytes, cudaStream_t s, moa_stats* st) {
+    int rc = validate(m, n, p, dt, A, B, C);
+    if (rc != MOA_OK) return rc;
+    if (st) {
+        *st = moa_stats{};
+        st->slices = 1;
+        st->products = 1;
+    }
+    if (m == 0 || p == 0) return MOA_OK;
+    if (n == 0) {
+        cudaError_t e = cudaMemsetAsync(C, 0, static_cast<size_t>(m) * p * out_size(dt), s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(C)");
+        if (st) st->kernels = 1;
+        return MOA_OK;
+    }
+    const size_t need = workspace_bytes(m, n, p, dt, slices);
+    if (need > 0 && (ws == nullptr || ws_bytes < need)) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "workspace of %zu bytes needed, %zu given", need,
+                      ws ? ws_bytes : size_t(0));
+        return fail(MOA_ERR_WORKSPACE, buf);
+    }
+    if (ws && reinterpret_cast<uintptr_t>(ws) % kAlign)
+        return fail(MOA_ERR_ALIGN, "workspace must be 256-byte aligned");
+    switch (dt) {
+        case MOA_F64:
+            if (st) st->kernels = 1;
+            return simt_f64_launch(m, n, p, static_cast<const double*>(A),
+                                   static_cast<const double*>(B), static_cast<double*>(C), s);
+        case MOA_F32_SIMT:
+            if (st) st->kernels = 1;
+            return simt_f32_launch(m, n, p, static_cast<const float*>(A),
+                                   static_cast<const float*>(B), static_cast<float*>(C), s);
+        case MOA_BF16:
+        case MOA_F32_TF32: {
+            const DenseWs w = dense_ws(m, n, p, dt);
+            const int es = in_size(dt);
+            const void* a = A;
+            const void* b = B;
+            uint8_t* base = static_cast<uint8_t*>(ws);
+            int kernels = 0;
+            if (w.pad_a) {
+                rc = pad_copy_launch(A, base, m, n, w.lda, es, s);
+                if (rc != MOA_OK) return rc;
+                a = base;
+                ++kernels;
+            }
+            if (w.pad_b) {
+                rc = pad_copy_launch(B, base + w.a_bytes, n, p, w.ldb, es, s);
+                if (rc != MOA_OK) return rc;
+                b = base + w.a_bytes;
+                ++kernels;
+            }
+            rc = dense_tc_launch(dt == MOA_BF16, m, n, p, a, w.lda, b, w.ldb,
+                                 static_cast<float*>(C), s, st);
+            if (st) {
+                st->kernels += kernels;
+                st->padded = (w.pad_a || w.pad_b) ? 1 : 0;
+            }
+            return rc;
+        }
+        default:
+            return split_gemm(m, n, p, dt, A, B, C, slices, ws, ws_bytes, s, st);
+    }
+}
+
+}  // namespace moa
+
+extern "C" {
+
+size_t moa_gemm_workspace_size(int64_t m, int64_t n, int64_t p, moa_dtype dt, int slices) {
+    if (!moa::valid_dtype(dt) || m < 0 || n < 0 || p < 0) return 0;
+    return moa::workspace_bytes(m, n, p, dt, slices);
+}
+
+int moa_gemm_ex(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const void* B,
+                void* C, int slices, void* ws, size_t ws_bytes, void* stream, moa_stats* stats) {
+    return moa::gemm_ex(m, n, p, dt, A, B, C, slices, ws, ws_bytes,
+                        static_cast<cudaStream_t>(stream), stats);
+}
+
+int moa_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const void* B, void* C) {
+    int rc = moa::validate(m, n, p, dt, A, B, C);
+    if (rc != MOA_OK) return rc;
+    const size_t need = moa::workspace_bytes(m, n, p, dt, 0);
+    void* ws = nullptr;
+    if (need > 0) {
+        int d = 0;
+        cudaError_t e = cudaGetDevice(&d);
+        if (e != cudaSuccess) return moa::cuda_fail(e, "cudaGetDevice");
+        if (d < 0 || d >= moa::kMaxDev) return moa::fail(MOA_ERR_CUDA, "device index out of range");
+        std::lock_guard<std::mutex> lk(moa::g_ws_mu);
+        if (moa::g_ws_bytes[d] < need) {
+            if (moa::g_ws[d]) {
+                // The legacy default stream orders this after earlier work.
+                cudaStreamSynchronize(nullptr);
+                cudaFree(moa::g_ws[d]);
+                moa::g_ws[d] = nullptr;
+                moa::g_ws_bytes[d] = 0;
+            }
+            e = cudaMalloc(&moa::g_ws[d], need);
+            if (e != cudaSuccess) return moa::cuda_fail(e, "cudaMalloc(moa_gemm workspace)");
+            moa::g_ws_bytes[d] = need;
+        }
+        ws = moa::g_ws[d];
+        return moa::gemm_ex(m, n, p, dt, A, B, C, 0, ws, moa::g_ws_bytes[d], nullptr, nullptr);
+    }
+    return moa::gemm_ex(m, n, p, dt, A, B, C, 0, nullptr, 0, nullptr, nullptr);
+}
+
+void moa_shutdown(void) {
+    std::lock_guard<std::mutex> lk(moa::g_ws_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (int d = 0; d < moa::kMaxDev; ++d) {
+        if (moa::g_ws[d]) {
+            cudaSetDevice(d);
+            cudaDeviceSynchronize();
+            cudaFree(moa::g_ws[d]);
+            moa::g_ws[d] = nullptr;
+            moa::g_ws_bytes[d] = 0;
+        }
+    }
+    cudaSetDevice(cur);
+}
+
+}  // extern "C"

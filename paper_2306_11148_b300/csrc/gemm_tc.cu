@@ -1,0 +1,336 @@
+// gemm_tc.cu -- dense ONF GEMM on the 5th-generation tensor cores (tcgen05).
+//
+// C[(i*p)+j] := sum_k A[(i*n)+k] * B[(k*p)+j]   (Eq. (eq:dnf), Sec. 2)
+//
+// Dimension lifting (Sec. 3.1) mapped onto the B300:
+//   * the i loop is split into 128-row tiles (one tile row per TMEM lane), the
+//     j loop into BLOCK_N-column tiles (the MMA N extent), so that each output
+//     tile is an independent block product (Fig. fig:omega);
+//   * the sigma (k) loop is split into K blocks of 128 bytes of operand each,
+//     summed into the same TMEM accumulator (the "extra summation loop" that
+//     closes Sec. 3.1);
+//   * output tiles are dealt round-robin to persistent CTAs, one per SM, in a
+//     grouped raster order so that neighbouring CTAs share A rows and B
+//     columns in L2 (the L2-level lift of Sec. 3.4).
+// Both operands are read exactly as the ONF lays them out: A row strips are
+// K-major (contiguous in k), B row strips are MN-major (contiguous in j, the
+// "row of B" of Fig. fig:mm).  TMA stages them into 128-byte-swizzled shared
+// memory; one thread issues tcgen05.mma; four epilogue warps drain the TMEM
+// accumulator (double-buffered, so the next tile's MMAs overlap the stores).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace moa {
+namespace {
+
+struct DenseArgs {
+    float* C;
+    int64_t m, n, p;
+    int tiles_m, tiles_n, num_kb;
+    int group_m;
+    int vec_ok;
+    uint64_t wait_limit_ns;
+    int* status;
+};
+
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int group_m, int& tm,
+                                            int& tn) {
+    const int per_group = group_m * tiles_n;
+    const int g = t / per_group;
+    const int first_m = g * group_m;
+    const int gsize = min(tiles_m - first_m, group_m);
+    const int r = t - g * per_group;
+    tm = first_m + r % gsize;
+    tn = r / gsize;
+}
+
+template <int ESIZE, int BLOCK_N, int STAGES>
+struct DenseCfg {
+    static constexpr int BLOCK_M = 128;
+    static constexpr int BK = 128 / ESIZE;          // K elements per stage (128 bytes)
+    static constexpr int MMA_K = 32 / ESIZE;        // K per tcgen05.mma (32 bytes)
+    static constexpr int CHUNK_N = 128 / ESIZE;     // B columns per 128-byte swizzle row
+    static constexpr int CHUNK_BYTES = BK * 128;    // one B column chunk: BK rows x 128 B
+    static constexpr int A_BYTES = BLOCK_M * 128;
+    static constexpr int B_BYTES = BLOCK_N * BK * ESIZE;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int TMEM_COLS = 2 * BLOCK_N <= 32 ? 32 : (2 * BLOCK_N <= 64 ? 64 : (2 * BLOCK_N <= 128 ? 128 : (2 * BLOCK_N <= 256 ? 256 : 512)));
+    static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + 256;
+    static constexpr uint32_t IDESC = make_idesc(ESIZE == 2 ? 1u : 2u, BLOCK_M, BLOCK_N, 0u, 1u);
+};
+
+template <int ESIZE, int BLOCK_N, int STAGES>
+__global__ void __launch_bounds__(192, 1)
+    dense_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    const DenseArgs args) {
+    using Cfg = DenseCfg<ESIZE, BLOCK_N, STAGES>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                               ~static_cast<uintptr_t>(1023));
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + STAGES * Cfg::A_BYTES;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + STAGES * Cfg::B_BYTES);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + STAGES;
+    uint64_t* tfull = bars + 2 * STAGES;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* drain = tempty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    CtaCtl* ctl = reinterpret_cast<CtaCtl*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const uint64_t limit = args.wait_limit_ns;
+    int* status = args.status;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], 4);
+        }
+        mbar_init(drain, 1);
+        ctl->abort = 0;
+        fence_barrier_init();
+    }
+    if (warp == 0 && lane == 0) {
+        prefetch_tmap(&tmA);
+        prefetch_tmap(&tmB);
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    const int num_tiles = args.tiles_m * args.tiles_n;
+    const int num_kb = args.num_kb;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer
+            int stage = 0;
+            uint32_t phase = 0;
+            long issued = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+                int tm, tn;
+                tile_coords(t, args.tiles_m, args.tiles_n, args.group_m, tm, tn);
+                for (int kb = 0; kb < num_kb; ++kb) {
+                    if (!mbar_wait(&empty[stage], phase ^ 1u, ctl, limit, status)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[stage], Cfg::STAGE_BYTES);
+                    tma_load_2d(sA + stage * Cfg::A_BYTES, &tmA, &full[stage], kb * Cfg::BK,
+                                tm * Cfg::BLOCK_M);
+#pragma unroll
+                    for (int c = 0; c < BLOCK_N / Cfg::CHUNK_N; ++c)
+                        tma_load_2d(sB + stage * Cfg::B_BYTES + c * Cfg::CHUNK_BYTES, &tmB,
+                                    &full[stage], tn * BLOCK_N + c * Cfg::CHUNK_N, kb * Cfg::BK);
+                    ++issued;
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                // Let the loads already in flight land before the CTA exits.
+                CtaCtl local{0};
+                const long outstanding = issued < STAGES ? issued : STAGES;
+                for (long q = 1; q <= outstanding; ++q) {
+                    const long idx = issued - q;
+                    mbar_wait(&full[idx % STAGES], static_cast<uint32_t>((idx / STAGES) & 1), &local,
+                              limit, status);
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer
+            int stage = 0;
+            uint32_t phase = 0;
+            int local_t = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x, ++local_t) {
+                const int acc = local_t & 1;
+                const uint32_t acc_phase = static_cast<uint32_t>(local_t >> 1) & 1u;
+                if (!mbar_wait(&tempty[acc], acc_phase ^ 1u, ctl, limit, status)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem_base + static_cast<uint32_t>(acc * BLOCK_N);
+                for (int kb = 0; kb < num_kb; ++kb) {
+                    if (!mbar_wait(&full[stage], phase, ctl, limit, status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t adesc =
+                        smem_desc_sw128(smem_u32(sA + stage * Cfg::A_BYTES), 16, 1024);
+                    const uint64_t bdesc = smem_desc_sw128(smem_u32(sB + stage * Cfg::B_BYTES),
+                                                           Cfg::CHUNK_BYTES, 1024);
+#pragma unroll
+                    for (int k = 0; k < Cfg::BK / Cfg::MMA_K; ++k) {
+                        const uint64_t a_off = static_cast<uint64_t>((k * 32) >> 4);
+                        const uint64_t b_off = static_cast<uint64_t>((k * Cfg::MMA_K * 128) >> 4);
+                        if constexpr (ESIZE == 2)
+                            mma_f16(d, adesc + a_off, bdesc + b_off, Cfg::IDESC, (kb | k) != 0);
+                        else
+                            mma_tf32(d, adesc + a_off, bdesc + b_off, Cfg::IDESC, (kb | k) != 0);
+                    }
+                    mma_commit(&empty[stage]);
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(&tfull[acc]);
+            }
+            // Every MMA issued above must finish before TMEM is released.
+            mma_commit(drain);
+            CtaCtl local{0};
+            mbar_wait(drain, 0, &local, limit, status);
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue: warps 2..5, TMEM lane quadrant = warp % 4
+        const int q = warp & 3;
+        int local_t = 0;
+        for (int t = blockIdx.x; t < num_tiles; t += gridDim.x, ++local_t) {
+            const int acc = local_t & 1;
+            const uint32_t acc_phase = static_cast<uint32_t>(local_t >> 1) & 1u;
+            bool ok = mbar_wait(&tfull[acc], acc_phase, ctl, limit, status);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            tc_fence_after();
+            int tm, tn;
+            tile_coords(t, args.tiles_m, args.tiles_n, args.group_m, tm, tn);
+            const int64_t row = static_cast<int64_t>(tm) * Cfg::BLOCK_M + q * 32 + lane;
+            const bool row_ok = row < args.m;
+            float* crow = args.C + row * args.p;
+#pragma unroll 1
+            for (int c = 0; c < BLOCK_N / 32; ++c) {
+                uint32_t r[32];
+                tmem_ld32(tmem_base + (static_cast<uint32_t>(q * 32) << 16) +
+                              static_cast<uint32_t>(acc * BLOCK_N + c * 32),
+                          r);
+                tmem_ld_wait();
+                const int64_t col0 = static_cast<int64_t>(tn) * BLOCK_N + c * 32;
+                if (row_ok) {
+                    if (args.vec_ok && col0 + 32 <= args.p) {
+                        float4* dst = reinterpret_cast<float4*>(crow + col0);
+#pragma unroll
+                        for (int v = 0; v < 8; ++v)
+                            dst[v] = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
+                                                 __uint_as_float(r[4 * v + 2]),
+                                                 __uint_as_float(r[4 * v + 3]));
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < 32; ++v)
+                            if (col0 + v < args.p) crow[col0 + v] = __uint_as_float(r[v]);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[acc]);
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, Cfg::TMEM_COLS);
+    }
+}
+
+template <int ESIZE, int BLOCK_N, int STAGES>
+int launch_cfg(int64_t m, int64_t n, int64_t p, const void* A, int64_t lda, const void* B,
+               int64_t ldb, float* C, cudaStream_t s, moa_stats* st) {
+    using Cfg = DenseCfg<ESIZE, BLOCK_N, STAGES>;
+    const CUtensorMapDataType dt =
+        ESIZE == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    CUtensorMap tmA, tmB;
+    int rc = make_tmap_2d(&tmA, dt, A, static_cast<uint64_t>(n), static_cast<uint64_t>(m),
+                          static_cast<uint64_t>(lda) * ESIZE, Cfg::BK, Cfg::BLOCK_M);
+    if (rc != MOA_OK) return rc;
+    rc = make_tmap_2d(&tmB, dt, B, static_cast<uint64_t>(p), static_cast<uint64_t>(n),
+                      static_cast<uint64_t>(ldb) * ESIZE, Cfg::CHUNK_N, Cfg::BK);
+    if (rc != MOA_OK) return rc;
+
+    DenseArgs args;
+    args.C = C;
+    args.m = m;
+    args.n = n;
+    args.p = p;
+    args.tiles_m = static_cast<int>(ceil_div(m, Cfg::BLOCK_M));
+    args.tiles_n = static_cast<int>(ceil_div(p, BLOCK_N));
+    args.num_kb = static_cast<int>(ceil_div(n, Cfg::BK));
+    args.group_m = 16;
+    args.vec_ok = (p % 4 == 0) && (reinterpret_cast<uintptr_t>(C) % 16 == 0);
+    args.wait_limit_ns = wait_limit_ns();
+    args.status = device_status_ptr();
+    if (!args.status) return MOA_ERR_CUDA;
+
+    auto kern = dense_tc_kernel<ESIZE, BLOCK_N, STAGES>;
+    static bool attr_set = false;   // per instantiation; the attribute is per device function
+    if (!attr_set) {
+        cudaError_t e =
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dense_tc)");
+        attr_set = true;
+    }
+    const long tiles = static_cast<long>(args.tiles_m) * args.tiles_n;
+    const int grid = static_cast<int>(std::min<long>(tiles, num_sms()));
+    dense_tc_kernel<ESIZE, BLOCK_N, STAGES><<<grid, 192, Cfg::SMEM, s>>>(tmA, tmB, args);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "dense_tc_kernel launch");
+    if (st) {
+        st->block_m = Cfg::BLOCK_M;
+        st->block_n = BLOCK_N;
+        st->block_k = Cfg::BK;
+        st->grid = grid;
+        st->tiles = tiles;
+        st->kernels += 1;
+    }
+    return MOA_OK;
+}
+
+}  // namespace
+
+int dense_tc_launch(bool in_bf16, int64_t m, int64_t n, int64_t p, const void* A, int64_t lda,
+                    const void* B, int64_t ldb, float* C, cudaStream_t s, moa_stats* st) {
+    // Tile planner: the widest N tile (fewest A re-reads) unless that leaves
+    // most SMs idle, in which case narrower tiles spread the work.
+    const long tiles256 = ceil_div(m, 128) * ceil_div(p, 256);
+    const long tiles128 = ceil_div(m, 128) * ceil_div(p, 128);
+    const int sms = num_sms();
+    int bn = 256;
+    if (tiles256 < sms && tiles128 > tiles256) bn = 128;
+    if (bn == 128 && tiles128 < sms && p <= 64) bn = 64;
+    if (in_bf16) {
+        if (bn == 256) return launch_cfg<2, 256, 4>(m, n, p, A, lda, B, ldb, C, s, st);
+        if (bn == 128) return launch_cfg<2, 128, 6>(m, n, p, A, lda, B, ldb, C, s, st);
+        return launch_cfg<2, 64, 8>(m, n, p, A, lda, B, ldb, C, s, st);
+    }
+    if (bn == 256) return launch_cfg<4, 256, 4>(m, n, p, A, lda, B, ldb, C, s, st);
+    if (bn == 128) return launch_cfg<4, 128, 6>(m, n, p, A, lda, B, ldb, C, s, st);
+    return launch_cfg<4, 64, 8>(m, n, p, A, lda, B, ldb, C, s, st);
+}
+
+}  // namespace moa

@@ -1,0 +1,59 @@
+// internal.h -- declarations shared by the translation units of libmoa.so
+// (not part of the public ABI; see include/moa.h for that).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "moa.h"
+
+namespace moa {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+int fail(int status, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+// Per-device status word (device address), created on first use.
+int* device_status_ptr();
+uint64_t wait_limit_ns();
+int num_sms();
+
+// ------------------------------------------------------------------ TMA maps
+// 2-D tiled map over a row-major matrix of `outer` rows x `inner` columns with
+// a row pitch of `pitch_bytes`; box = box_outer rows x box_inner columns,
+// 128-byte swizzle, zero fill out of bounds.
+int make_tmap_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uint64_t inner,
+                 uint64_t outer, uint64_t pitch_bytes, uint32_t box_inner, uint32_t box_outer);
+// 3-D variant: `depth` matrices of outer x inner, matrix pitch `plane_bytes`.
+int make_tmap_3d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uint64_t inner,
+                 uint64_t outer, uint64_t depth, uint64_t pitch_bytes, uint64_t plane_bytes,
+                 uint32_t box_inner, uint32_t box_outer);
+
+// ------------------------------------------------------------------ kernels
+// Dense tcgen05 GEMM, A (m x n, row pitch lda elements), B (n x p, pitch ldb),
+// C (m x p, FP32, pitch p).  in_bf16: operands are BF16, else FP32 (TF32 MMA).
+struct TileChoice {
+    int block_n;     // 64, 128 or 256
+};
+int dense_tc_launch(bool in_bf16, int64_t m, int64_t n, int64_t p, const void* A, int64_t lda,
+                    const void* B, int64_t ldb, float* C, cudaStream_t s, moa_stats* st);
+
+// SIMT kernels (no tensor cores).
+int simt_f64_launch(int64_t m, int64_t n, int64_t p, const double* A, const double* B, double* C,
+                    cudaStream_t s);
+int simt_f32_launch(int64_t m, int64_t n, int64_t p, const float* A, const float* B, float* C,
+                    cudaStream_t s);
+
+// Copy a rows x cols row-major matrix into a buffer with row pitch ld >= cols
+// (elements), zero-filling the padding columns.
+int pad_copy_launch(const void* src, void* dst, int64_t rows, int64_t cols, int64_t ld,
+                    int esize, cudaStream_t s);
+
+inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+inline int64_t ceil_div(int64_t x, int64_t a) { return (x + a - 1) / a; }
+
+}  // namespace moa

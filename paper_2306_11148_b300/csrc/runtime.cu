@@ -1,0 +1,227 @@
+// runtime.cu -- host runtime shared by every entry point: error reporting,
+// the per-device status word, device properties, TMA descriptor encoding
+// (driver entry point fetched at run time, so no link against libcuda), and
+// the padding copy used when a row pitch is not a multiple of 16 bytes.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace moa {
+
+namespace {
+thread_local std::string g_last_error;
+std::mutex g_mu;
+uint64_t g_wait_limit_ns = 0;
+constexpr int kMaxDevices = 64;
+int* g_status[kMaxDevices] = {nullptr};
+int g_sms[kMaxDevices] = {0};
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+int current_device() {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess) return -1;
+    return d;
+}
+}  // namespace
+
+// Per-device status word: a file-scope device variable; host code only ever
+// uses the address cudaGetSymbolAddress gives for the current device.
+__device__ int g_moa_device_status;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int fail(int status, const std::string& msg) {
+    g_last_error = msg;
+    return status;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return MOA_ERR_CUDA;
+}
+
+int* device_status_ptr() {
+    const int d = current_device();
+    if (d < 0 || d >= kMaxDevices) {
+        set_error("no current CUDA device");
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_status[d]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_moa_device_status);
+        if (e != cudaSuccess) {
+            cuda_fail(e, "cudaGetSymbolAddress(status)");
+            return nullptr;
+        }
+        g_status[d] = static_cast<int*>(p);
+    }
+    return g_status[d];
+}
+
+int num_sms() {
+    const int d = current_device();
+    if (d < 0 || d >= kMaxDevices) return 1;
+    if (g_sms[d] == 0) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d);
+        g_sms[d] = v > 0 ? v : 1;
+    }
+    return g_sms[d];
+}
+
+uint64_t wait_limit_ns() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_wait_limit_ns == 0) {
+        const char* env = std::getenv("MOA_WAIT_LIMIT_NS");
+        g_wait_limit_ns = env ? std::strtoull(env, nullptr, 10) : 0;
+        if (g_wait_limit_ns == 0) g_wait_limit_ns = 2000000000ull;
+    }
+    return g_wait_limit_ns;
+}
+
+static int get_encode() {
+    if (g_encode) return MOA_OK;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+        return fail(MOA_ERR_CUDA, "cuTensorMapEncodeTiled entry point unavailable");
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    return MOA_OK;
+}
+
+int make_tmap_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uint64_t inner,
+                 uint64_t outer, uint64_t pitch_bytes, uint32_t box_inner, uint32_t box_outer) {
+    int rc = get_encode();
+    if (rc != MOA_OK) return rc;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {pitch_bytes};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        char buf[256];
+        std::snprintf(buf, sizeof buf,
+                      "cuTensorMapEncodeTiled(2d) failed (%d): inner=%llu outer=%llu pitch=%llu "
+                      "box=%ux%u",
+                      static_cast<int>(r), static_cast<unsigned long long>(inner),
+                      static_cast<unsigned long long>(outer),
+                      static_cast<unsigned long long>(pitch_bytes), box_inner, box_outer);
+        return fail(MOA_ERR_CUDA, buf);
+    }
+    return MOA_OK;
+}
+
+int make_tmap_3d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uint64_t inner,
+                 uint64_t outer, uint64_t depth, uint64_t pitch_bytes, uint64_t plane_bytes,
+                 uint32_t box_inner, uint32_t box_outer) {
+    int rc = get_encode();
+    if (rc != MOA_OK) return rc;
+    cuuint64_t dims[3] = {inner, outer, depth};
+    cuuint64_t strides[2] = {pitch_bytes, plane_bytes};
+    cuuint32_t box[3] = {box_inner, box_outer, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = g_encode(map, dt, 3, const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        char buf[256];
+        std::snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled(3d) failed (%d)", static_cast<int>(r));
+        return fail(MOA_ERR_CUDA, buf);
+    }
+    return MOA_OK;
+}
+
+// ------------------------------------------------------------------ padding copy
+namespace {
+template <typename T>
+__global__ void pad_copy_kernel(const T* __restrict__ src, T* __restrict__ dst, int64_t rows,
+                                int64_t cols, int64_t ld) {
+    const int64_t total = rows * ld;
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t r = e / ld, c = e % ld;
+        dst[e] = c < cols ? src[r * cols + c] : T(0);
+    }
+}
+}  // namespace
+
+int pad_copy_launch(const void* src, void* dst, int64_t rows, int64_t cols, int64_t ld, int esize,
+                    cudaStream_t s) {
+    const int64_t total = rows * ld;
+    if (total == 0) return MOA_OK;
+    const int threads = 256;
+    const int64_t want = ceil_div(total, threads);
+    const int blocks = static_cast<int>(want < 8L * num_sms() ? want : 8L * num_sms());
+    switch (esize) {
+        case 2:
+            pad_copy_kernel<uint16_t><<<blocks, threads, 0, s>>>(
+                static_cast<const uint16_t*>(src), static_cast<uint16_t*>(dst), rows, cols, ld);
+            break;
+        case 4:
+            pad_copy_kernel<uint32_t><<<blocks, threads, 0, s>>>(
+                static_cast<const uint32_t*>(src), static_cast<uint32_t*>(dst), rows, cols, ld);
+            break;
+        case 8:
+            pad_copy_kernel<uint64_t><<<blocks, threads, 0, s>>>(
+                static_cast<const uint64_t*>(src), static_cast<uint64_t*>(dst), rows, cols, ld);
+            break;
+        default:
+            return fail(MOA_ERR_ARG, "pad_copy: bad element size");
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "pad_copy_kernel launch");
+    return MOA_OK;
+}
+
+}  // namespace moa
+
+// ------------------------------------------------------------------ public housekeeping
+extern "C" {
+
+const char* moa_last_error(void) { return moa::g_last_error.c_str(); }
+
+uint64_t moa_set_wait_limit_ns(uint64_t ns) {
+    const uint64_t prev = moa::wait_limit_ns();
+    std::lock_guard<std::mutex> lk(moa::g_mu);
+    moa::g_wait_limit_ns = ns ? ns : 2000000000ull;
+    return prev;
+}
+
+const char* moa_version(void) { return "moa-b300 0.1.0 (sm_103a)"; }
+
+int moa_sync_status(void* stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return moa::cuda_fail(e, "cudaStreamSynchronize");
+    int* dev = moa::device_status_ptr();
+    if (!dev) return MOA_ERR_CUDA;
+    int v = 0;
+    e = cudaMemcpy(&v, dev, sizeof v, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return moa::cuda_fail(e, "read status word");
+    if (v != moa::kDevOk) {
+        const int zero = 0;
+        cudaMemcpy(dev, &zero, sizeof zero, cudaMemcpyHostToDevice);
+        if (v == moa::kDevTimeout)
+            return moa::fail(MOA_ERR_TIMEOUT, "a device pipeline wait exceeded its time limit");
+        if (v == moa::kDevNonFinite)
+            return moa::fail(MOA_ERR_NONFINITE, "split pre-pass found a NaN or Inf input");
+        return moa::fail(MOA_ERR_CUDA, "unknown device status");
+    }
+    return MOA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,781 @@
+// split.cu -- split-precision ONF GEMM: the bulk of the products run as BF16
+// slice products on the tcgen05 tensor cores, accumulated in FP32 TMEM, and are
+// recombined to FP32 accuracy (MOA_F32_SPLIT) or FP64 accuracy (MOA_F64_SPLIT_*).
+//
+// The result is still Eq. (eq:dnf) of Sec. 2, C[(i*p)+j] := sum_k A[(i*n)+k] *
+// B[(k*p)+j]; the slicing is not in the paper (it is the "Precision" pattern of
+// this library):
+//
+// * FP32 accuracy (Henry, Tang & Heinecke 2019): every FP32 x is split as
+//   x = s0 + s1 + s2, s_t = RN_bf16(x - s0 - ... - s_{t-1}); the six slice
+//   products with t + u <= 2 are summed into one FP32 accumulator.
+// * FP64 accuracy (error-free digit slicing in the manner of Ozaki, Ogita,
+//   Oishi & Rump 2012): each row i of A gets the exponent eA_i with
+//   max_k |A[i,k]| in [2^(eA_i - 1), 2^eA_i), each column j of B likewise eB_j;
+//   x * 2^(8S - e) is rounded once to an integer D and written as S balanced
+//   base-256 digits (|d_0| <= 256, d_s in [-128, 128) for s >= 1), each exactly
+//   a BF16 value.  Level L = s + t of the triangular product (s + t <= S - 1)
+//   is summed over chunks of K short enough that every FP32 partial sum is an
+//   integer below 2^24, hence exact; each chunk is flushed into an int32
+//   running sum, folded at the level's end into an int64 fixed-point total in
+//   TMEM, which the epilogue converts to FP64 once and scales by
+//   2^(eA_i + eB_j - 8(S+1) + drop).
+//
+// Kernel layout (one persistent CTA per SM, 320 threads): warp 0 issues TMA
+// loads of (A slice, B slice) K blocks; warp 1 issues tcgen05.mma into one of
+// two TMEM chunk accumulators; warps 2..9 (two per TMEM lane quadrant, 64
+// columns each) flush chunks and write C.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+
+#include "internal.h"
+#include "ptx.cuh"
+#include "split.h"
+
+namespace moa {
+
+// ====================================================================== pre-passes
+namespace {
+
+// FP32 -> three BF16 slices, zero-padded to row pitch ld; flags NaN/Inf (and
+// values whose leading slice overflows BF16) in the status word.
+__global__ void split3_kernel(const float* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
+                              __nv_bfloat16* __restrict__ out, int64_t plane, int* status) {
+    const int64_t total = rows * ld;
+    bool bad = false;
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t r = e / ld, c = e - r * ld;
+        __nv_bfloat16 s0 = __float2bfloat16_rn(0.f), s1 = s0, s2 = s0;
+        if (c < cols) {
+            const float x = X[r * cols + c];
+            s0 = __float2bfloat16_rn(x);
+            const float a = __bfloat162float(s0);
+            const float r1 = __fsub_rn(x, a);
+            s1 = __float2bfloat16_rn(r1);
+            const float r2 = __fsub_rn(r1, __bfloat162float(s1));
+            s2 = __float2bfloat16_rn(r2);
+            bad |= !isfinite(x) || !isfinite(a);
+        }
+        out[e] = s0;
+        out[plane + e] = s1;
+        out[2 * plane + e] = s2;
+    }
+    if (bad) atomicCAS(status, kDevOk, kDevNonFinite);
+}
+
+template <typename T>
+struct Bits;
+template <>
+struct Bits<double> {
+    using U = unsigned long long;
+    static constexpr U kAbsMask = 0x7FFFFFFFFFFFFFFFull;
+    static constexpr U kInf = 0x7FF0000000000000ull;
+    __device__ static U abs_bits(double x) {
+        return static_cast<U>(__double_as_longlong(x)) & kAbsMask;
+    }
+    // frexp exponent of the non-negative value with bit pattern M (0 for 0).
+    __device__ static int frexp_exp(U M) {
+        if (M == 0) return 0;
+        const int ex = static_cast<int>(M >> 52);
+        if (ex > 0) return ex - 1022;
+        return (64 - __clzll(static_cast<long long>(M))) - 1074;
+    }
+    // round-half-even(x * 2^k) as an integer; requires |x| * 2^k < 2^62.
+    __device__ static long long round_scaled(double x, int k) {
+        const U b = static_cast<U>(__double_as_longlong(x));
+        const bool neg = (b >> 63) != 0;
+        const int ex = static_cast<int>((b >> 52) & 0x7FF);
+        U mant = b & 0xFFFFFFFFFFFFFull;
+        int E;
+        if (ex == 0) {
+            E = -1074;
+        } else {
+            mant |= 1ull << 52;
+            E = ex - 1075;
+        }
+        if (mant == 0) return 0;
+        const int sh = E + k;
+        U D;
+        if (sh >= 0) {
+            D = mant << sh;
+        } else {
+            const int kk = -sh;
+            if (kk > 54) {
+                D = 0;
+            } else {
+                const U q = mant >> kk;
+                const U rem = mant & ((1ull << kk) - 1);
+                const U half = 1ull << (kk - 1);
+                D = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+            }
+        }
+        return neg ? -static_cast<long long>(D) : static_cast<long long>(D);
+    }
+};
+template <>
+struct Bits<float> {
+    using U = unsigned int;
+    static constexpr U kAbsMask = 0x7FFFFFFFu;
+    static constexpr U kInf = 0x7F800000u;
+    __device__ static U abs_bits(float x) { return __float_as_uint(x) & kAbsMask; }
+    __device__ static int frexp_exp(U M) {
+        if (M == 0) return 0;
+        const int ex = static_cast<int>(M >> 23);
+        if (ex > 0) return ex - 126;
+        return (32 - __clz(static_cast<int>(M))) - 149;
+    }
+    __device__ static long long round_scaled(float x, int k) {
+        const U b = __float_as_uint(x);
+        const bool neg = (b >> 31) != 0;
+        const int ex = static_cast<int>((b >> 23) & 0xFF);
+        unsigned long long mant = b & 0x7FFFFFu;
+        int E;
+        if (ex == 0) {
+            E = -149;
+        } else {
+            mant |= 1ull << 23;
+            E = ex - 150;
+        }
+        if (mant == 0) return 0;
+        const int sh = E + k;
+        unsigned long long D;
+        if (sh >= 0) {
+            D = mant << sh;
+        } else {
+            const int kk = -sh;
+            if (kk > 25) {
+                D = 0;
+            } else {
+                const unsigned long long q = mant >> kk;
+                const unsigned long long rem = mant & ((1ull << kk) - 1);
+                const unsigned long long half = 1ull << (kk - 1);
+                D = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+            }
+        }
+        return neg ? -static_cast<long long>(D) : static_cast<long long>(D);
+    }
+};
+
+// One warp per row: exponent of max |A[i,:]|.
+template <typename T>
+__global__ void row_exp_kernel(const T* __restrict__ X, int64_t rows, int64_t cols,
+                               int* __restrict__ e_out, int* status) {
+    using B = Bits<T>;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    bool bad = false;
+    for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5);
+         r < rows; r += warps) {
+        typename B::U mx = 0;
+        for (int64_t c = lane; c < cols; c += 32) mx = max(mx, B::abs_bits(X[r * cols + c]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const typename B::U other = __shfl_xor_sync(0xffffffffu, mx, o);
+            mx = max(mx, other);
+        }
+        if (lane == 0) {
+            bad |= mx >= B::kInf;
+            e_out[r] = B::frexp_exp(mx);
+        }
+    }
+    if (bad) atomicCAS(status, kDevOk, kDevNonFinite);
+}
+
+// Column maxima of |B| (bit patterns), by atomicMax over row chunks.
+template <typename T>
+__global__ void col_max_kernel(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t chunk,
+                               typename Bits<T>::U* __restrict__ cmax) {
+    using B = Bits<T>;
+    const int64_t c = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (c >= cols) return;
+    const int64_t r0 = blockIdx.y * chunk;
+    const int64_t r1 = min(rows, r0 + chunk);
+    typename B::U mx = 0;
+    for (int64_t r = r0; r < r1; ++r) mx = max(mx, B::abs_bits(X[r * cols + c]));
+    atomicMax(&cmax[c], mx);
+}
+
+template <typename T>
+__global__ void col_exp_kernel(const typename Bits<T>::U* __restrict__ cmax, int64_t cols,
+                               int* __restrict__ e_out, int* status) {
+    using B = Bits<T>;
+    const int64_t c = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (c >= cols) return;
+    const typename B::U M = cmax[c];
+    if (M >= B::kInf) atomicCAS(status, kDevOk, kDevNonFinite);
+    e_out[c] = B::frexp_exp(M);
+}
+
+// Integer digits of every element into S BF16 planes (row pitch ld, zero pad).
+// axis 0: exponent per row (e[r]); axis 1: per column (e[c]).
+template <typename T>
+__global__ void digits_kernel(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
+                              const int* __restrict__ e, int axis, int S,
+                              __nv_bfloat16* __restrict__ out, int64_t plane) {
+    const int64_t total = rows * ld;
+    constexpr long long radix = 1ll << kBeta;
+    constexpr long long half = radix / 2;
+    for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+         idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t r = idx / ld, c = idx - r * ld;
+        long long D = 0;
+        if (c < cols) {
+            const int ex = axis == 0 ? e[r] : e[c];
+            D = Bits<T>::round_scaled(X[r * cols + c], kBeta * S - ex);
+        }
+        for (int s = S - 1; s >= 1; --s) {
+            long long low = D & (radix - 1);
+            if (low >= half) low -= radix;
+            out[s * plane + idx] = __float2bfloat16_rn(static_cast<float>(low));
+            D = (D - low) >> kBeta;
+        }
+        out[idx] = __float2bfloat16_rn(static_cast<float>(D));
+    }
+}
+
+int grid_for(int64_t total, int threads) {
+    const int64_t want = ceil_div(total, threads);
+    const int64_t cap = 16L * num_sms();
+    return static_cast<int>(std::max<int64_t>(1, std::min(want, cap)));
+}
+
+}  // namespace
+
+// ====================================================================== slice GEMM
+namespace {
+
+constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 6;
+constexpr int kABytes = kBM * 128;                 // 128 rows x 64 BF16
+constexpr int kBChunkBytes = kBK * 128;            // 64 rows x 64 BF16
+constexpr int kBBytes = 2 * kBChunkBytes;          // 128 columns
+constexpr int kStageBytes = kABytes + kBBytes;
+constexpr int kSplitSmem = 1024 + kStages * kStageBytes + 256;
+constexpr int kSplitThreads = 320;
+constexpr uint32_t kSplitIdesc = make_idesc(1u, kBM, kBN, 0u, 1u);
+constexpr int kMaxLevels = 8;
+
+struct SplitArgs {
+    void* C;
+    int64_t m, n, p;
+    int tiles_m, tiles_n, num_kb;
+    int group_m;
+    int f64;            // 0: FP32-accuracy (one level of 6 pairs); 1: FP64-accuracy levels
+    int levels;         // number of levels
+    int kc[kMaxLevels]; // chunk length per level, in K blocks
+    int S;
+    int drop;           // fixed-point bits dropped from the int64 total (FP64 mode)
+    const int* eA;
+    const int* eB;
+    int vec_ok;
+    uint64_t wait_limit_ns;
+    int* status;
+};
+
+__device__ __forceinline__ void split_tile_coords(int t, int tiles_m, int tiles_n, int group_m,
+                                                  int& tm, int& tn) {
+    const int per_group = group_m * tiles_n;
+    const int g = t / per_group;
+    const int first_m = g * group_m;
+    const int gsize = min(tiles_m - first_m, group_m);
+    const int r = t - g * per_group;
+    tm = first_m + r % gsize;
+    tn = r / gsize;
+}
+
+// Pairs (slice of A, slice of B) of one level.  FP32 mode: the six products
+// with t + u <= 2, larger first.  FP64 mode: level L holds (s, L - s).
+__device__ __forceinline__ int level_pairs(const SplitArgs& a, int L) {
+    return a.f64 ? L + 1 : 6;
+}
+__device__ __forceinline__ void pair_at(const SplitArgs& a, int L, int q, int& s, int& t) {
+    if (a.f64) {
+        s = q;
+        t = L - q;
+    } else {
+        // (0,0) (0,1) (1,0) (0,2) (1,1) (2,0), one nibble per pair
+        s = (0x210100 >> (4 * q)) & 15;
+        t = (0x012010 >> (4 * q)) & 15;
+    }
+}
+
+__global__ void __launch_bounds__(kSplitThreads, 1)
+    split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                      const SplitArgs args) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                               ~static_cast<uintptr_t>(1023));
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + kStages * kABytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kStages * kBBytes);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + kStages;
+    uint64_t* tfull = bars + 2 * kStages;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* drain = tempty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    CtaCtl* ctl = reinterpret_cast<CtaCtl*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const uint64_t limit = args.wait_limit_ns;
+    int* status = args.status;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 8);
+        }
+        mbar_init(drain, 1);
+        ctl->abort = 0;
+        fence_barrier_init();
+    }
+    if (warp == 0 && lane == 0) {
+        prefetch_tmap(&tmA);
+        prefetch_tmap(&tmB);
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    const int num_tiles = args.tiles_m * args.tiles_n;
+    const int num_kb = args.num_kb;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer: (tile, level, chunk, kb, pair)
+            int stage = 0;
+            uint32_t phase = 0;
+            long issued = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+                int tm, tn;
+                split_tile_coords(t, args.tiles_m, args.tiles_n, args.group_m, tm, tn);
+                for (int L = 0; L < args.levels && ok; ++L) {
+                    const int np = level_pairs(args, L);
+                    for (int kb = 0; kb < num_kb && ok; ++kb) {
+                        for (int q = 0; q < np; ++q) {
+                            int s, u;
+                            pair_at(args, L, q, s, u);
+                            if (!mbar_wait(&empty[stage], phase ^ 1u, ctl, limit, status)) {
+                                ok = false;
+                                break;
+                            }
+                            mbar_arrive_expect_tx(&full[stage], kStageBytes);
+                            tma_load_3d(sA + stage * kABytes, &tmA, &full[stage], kb * kBK,
+                                        tm * kBM, s);
+                            tma_load_3d(sB + stage * kBBytes, &tmB, &full[stage], tn * kBN,
+                                        kb * kBK, u);
+                            tma_load_3d(sB + stage * kBBytes + kBChunkBytes, &tmB, &full[stage],
+                                        tn * kBN + 64, kb * kBK, u);
+                            ++issued;
+                            if (++stage == kStages) {
+                                stage = 0;
+                                phase ^= 1u;
+                            }
+                        }
+                    }
+                }
+            }
+            if (!ok) {
+                CtaCtl local{0};
+                const long outstanding = issued < kStages ? issued : kStages;
+                for (long q = 1; q <= outstanding; ++q) {
+                    const long idx = issued - q;
+                    mbar_wait(&full[idx % kStages], static_cast<uint32_t>((idx / kStages) & 1),
+                              &local, limit, status);
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer: one TMEM chunk accumulator per chunk
+            int stage = 0;
+            uint32_t phase = 0;
+            long cnt = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+                for (int L = 0; L < args.levels && ok; ++L) {
+                    const int np = level_pairs(args, L);
+                    const int kc = args.kc[L];
+                    for (int kb0 = 0; kb0 < num_kb && ok; kb0 += kc, ++cnt) {
+                        const int buf = static_cast<int>(cnt & 1);
+                        const uint32_t bph = static_cast<uint32_t>((cnt >> 1) & 1);
+                        if (!mbar_wait(&tempty[buf], bph ^ 1u, ctl, limit, status)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t d = tmem_base + static_cast<uint32_t>(buf * kBN);
+                        const int kb1 = min(num_kb, kb0 + kc);
+                        bool first = true;
+                        for (int kb = kb0; kb < kb1 && ok; ++kb) {
+                            for (int q = 0; q < np; ++q) {
+                                if (!mbar_wait(&full[stage], phase, ctl, limit, status)) {
+                                    ok = false;
+                                    break;
+                                }
+                                tc_fence_after();
+                                const uint64_t adesc =
+                                    smem_desc_sw128(smem_u32(sA + stage * kABytes), 16, 1024);
+                                const uint64_t bdesc = smem_desc_sw128(
+                                    smem_u32(sB + stage * kBBytes), kBChunkBytes, 1024);
+#pragma unroll
+                                for (int k = 0; k < kBK / 16; ++k) {
+                                    mma_f16(d, adesc + static_cast<uint64_t>((k * 32) >> 4),
+                                            bdesc + static_cast<uint64_t>((k * 16 * 128) >> 4),
+                                            kSplitIdesc, (first && k == 0) ? 0u : 1u);
+                                }
+                                first = false;
+                                mma_commit(&empty[stage]);
+                                if (++stage == kStages) {
+                                    stage = 0;
+                                    phase ^= 1u;
+                                }
+                            }
+                        }
+                        if (!ok) break;
+                        mma_commit(&tfull[buf]);
+                    }
+                }
+            }
+            mma_commit(drain);
+            CtaCtl local{0};
+            mbar_wait(drain, 0, &local, limit, status);
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue: warps 2..9; quadrant q = warp % 4, column half h
+        const int q = warp & 3;
+        const int h = (warp - 2) >> 2;
+        const uint32_t lane_base = static_cast<uint32_t>(q * 32) << 16;
+        long cnt = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+            int tm, tn;
+            split_tile_coords(t, args.tiles_m, args.tiles_n, args.group_m, tm, tn);
+            const int64_t row = static_cast<int64_t>(tm) * kBM + q * 32 + lane;
+            const int64_t col_base = static_cast<int64_t>(tn) * kBN + h * 64;
+            if (args.f64) {
+                // zero the int64 fixed-point total: TMEM columns 256 + 128h .. +128
+                uint32_t z[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) z[i] = 0u;
+#pragma unroll
+                for (int g = 0; g < 4; ++g)
+                    tmem_st32(tmem_base + lane_base + 256u + 128u * h + 32u * g, z);
+                tmem_st_wait();
+            }
+            // Running sum per element: FP32 bits (FP32 mode) or the exact
+            // int32 sum of the current level (FP64 mode); 0 is zero in both.
+            uint32_t acc[64];
+#pragma unroll
+            for (int i = 0; i < 64; ++i) acc[i] = 0u;
+            for (int L = 0; L < args.levels && ok; ++L) {
+                const int kc = args.kc[L];
+                int since_fold = 0;
+                for (int kb0 = 0; kb0 < num_kb; kb0 += kc, ++cnt) {
+                    const int buf = static_cast<int>(cnt & 1);
+                    const uint32_t bph = static_cast<uint32_t>((cnt >> 1) & 1);
+                    ok = mbar_wait(&tfull[buf], bph, ctl, limit, status);
+                    if (!__all_sync(0xffffffffu, ok)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+#pragma unroll
+                    for (int g = 0; g < 2; ++g) {
+                        uint32_t r[32];
+                        tmem_ld32(tmem_base + lane_base + static_cast<uint32_t>(buf * kBN + h * 64 + g * 32), r);
+                        tmem_ld_wait();
+                        if (args.f64) {
+#pragma unroll
+                            for (int i = 0; i < 32; ++i)
+                                acc[g * 32 + i] = static_cast<uint32_t>(
+                                    static_cast<int>(acc[g * 32 + i]) + __float2int_rn(__uint_as_float(r[i])));
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 32; ++i)
+                                acc[g * 32 + i] = __float_as_uint(__uint_as_float(acc[g * 32 + i]) +
+                                                                  __uint_as_float(r[i]));
+                        }
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tempty[buf]);
+                    ++since_fold;
+                    const bool level_end = kb0 + kc >= num_kb;
+                    if (args.f64 && (level_end || since_fold == 64)) {
+                        // fold the level's exact sum into the int64 total:
+                        // T += round(R * 2^(8(S-1-L) - drop))
+                        const int sh = kBeta * (args.S - 1 - L) - args.drop;
+#pragma unroll
+                        for (int g = 0; g < 4; ++g) {
+                            uint32_t r[32];
+                            const uint32_t ta = tmem_base + lane_base + 256u + 128u * h + 32u * g;
+                            tmem_ld32(ta, r);
+                            tmem_ld_wait();
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) {
+                                long long v = static_cast<int>(acc[g * 16 + i]);
+                                if (sh >= 0)
+                                    v = v * (1ll << sh);
+                                else
+                                    v = (v + (1ll << (-sh - 1))) >> (-sh);
+                                long long tot = static_cast<long long>(
+                                    (static_cast<unsigned long long>(r[2 * i + 1]) << 32) | r[2 * i]);
+                                tot += v;
+                                r[2 * i] = static_cast<uint32_t>(tot);
+                                r[2 * i + 1] = static_cast<uint32_t>(static_cast<unsigned long long>(tot) >> 32);
+                            }
+                            tmem_st32(ta, r);
+                            tmem_st_wait();
+                        }
+#pragma unroll
+                        for (int i = 0; i < 64; ++i) acc[i] = 0u;
+                        since_fold = 0;
+                    }
+                }
+            }
+            if (!ok) break;
+            // ---------------- store the tile
+            const bool row_ok = row < args.m;
+            if (args.f64) {
+                double* crow = static_cast<double*>(args.C) + row * args.p;
+                const int er = row_ok ? args.eA[row] : 0;
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    uint32_t r[32];
+                    tmem_ld32(tmem_base + lane_base + 256u + 128u * h + 32u * g, r);
+                    tmem_ld_wait();
+                    if (row_ok) {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const int64_t col = col_base + g * 16 + i;
+                            if (col < args.p) {
+                                const long long tot = static_cast<long long>(
+                                    (static_cast<unsigned long long>(r[2 * i + 1]) << 32) | r[2 * i]);
+                                const int ex = er + args.eB[col] - kBeta * (args.S + 1) + args.drop;
+                                crow[col] = ldexp(__ll2double_rn(tot), ex);
+                            }
+                        }
+                    }
+                }
+            } else if (row_ok) {
+                float* crow = static_cast<float*>(args.C) + row * args.p;
+                if (args.vec_ok && col_base + 64 <= args.p) {
+                    float4* dst = reinterpret_cast<float4*>(crow + col_base);
+#pragma unroll
+                    for (int v = 0; v < 16; ++v)
+                        dst[v] = make_float4(__uint_as_float(acc[4 * v]), __uint_as_float(acc[4 * v + 1]),
+                                             __uint_as_float(acc[4 * v + 2]), __uint_as_float(acc[4 * v + 3]));
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 64; ++i)
+                        if (col_base + i < args.p) crow[col_base + i] = __uint_as_float(acc[i]);
+                }
+            }
+            tc_fence_before();
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, 512);
+    }
+}
+
+}  // namespace
+
+// ====================================================================== host side
+int split_slices(moa_dtype dt, int slices) {
+    if (dt == MOA_F32_SPLIT) return (slices == 0 || slices == 3) ? 3 : -1;
+    if (slices == 0) return kDefaultSlices;
+    if (slices < kMinSlices || slices > kMaxSlices) return -1;
+    return slices;
+}
+
+SplitLayout split_layout(int64_t m, int64_t n, int64_t p, moa_dtype dt, int S) {
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    SplitLayout L{};
+    L.S = S;
+    L.lda = round_up(n, 8);
+    L.ldb = round_up(p, 8);
+    size_t off = 0;
+    L.a_off = off;
+    off += al(static_cast<size_t>(S) * m * L.lda * 2);
+    L.b_off = off;
+    off += al(static_cast<size_t>(S) * n * L.ldb * 2);
+    if (dt != MOA_F32_SPLIT) {
+        L.ea_off = off;
+        off += al(static_cast<size_t>(m) * 4);
+        L.eb_off = off;
+        off += al(static_cast<size_t>(p) * 4);
+        L.cmax_off = off;
+        off += al(static_cast<size_t>(p) * 8);
+    }
+    L.total = off;
+    return L;
+}
+
+size_t split_workspace_bytes(int64_t m, int64_t n, int64_t p, moa_dtype dt, int slices) {
+    const int S = split_slices(dt, slices);
+    if (S < 0) return 0;
+    return split_layout(m, n, p, dt, S).total;
+}
+
+static int launch_split_gemm(const SplitArgs& a, const CUtensorMap& tmA, const CUtensorMap& tmB,
+                             cudaStream_t s, moa_stats* st) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSplitSmem);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(split_gemm)");
+        attr_set = true;
+    }
+    const long tiles = static_cast<long>(a.tiles_m) * a.tiles_n;
+    const int grid = static_cast<int>(std::min<long>(tiles, num_sms()));
+    split_gemm_kernel<<<grid, kSplitThreads, kSplitSmem, s>>>(tmA, tmB, a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "split_gemm_kernel launch");
+    if (st) {
+        st->block_m = kBM;
+        st->block_n = kBN;
+        st->block_k = kBK;
+        st->grid = grid;
+        st->tiles = tiles;
+    }
+    return MOA_OK;
+}
+
+int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const void* B,
+               void* C, int slices, void* ws, size_t ws_bytes, cudaStream_t s, moa_stats* st) {
+    const int S = split_slices(dt, slices);
+    if (S < 0) return fail(MOA_ERR_DTYPE, "slice count not supported for this mode");
+    const SplitLayout L = split_layout(m, n, p, dt, S);
+    if (ws_bytes < L.total) return fail(MOA_ERR_WORKSPACE, "workspace too small for split mode");
+    int* status = device_status_ptr();
+    if (!status) return MOA_ERR_CUDA;
+    uint8_t* base = static_cast<uint8_t*>(ws);
+    __nv_bfloat16* a_sl = reinterpret_cast<__nv_bfloat16*>(base + L.a_off);
+    __nv_bfloat16* b_sl = reinterpret_cast<__nv_bfloat16*>(base + L.b_off);
+    const int64_t a_plane = m * L.lda, b_plane = n * L.ldb;
+    int kernels = 0;
+
+    SplitArgs a{};
+    a.C = C;
+    a.m = m;
+    a.n = n;
+    a.p = p;
+    a.tiles_m = static_cast<int>(ceil_div(m, kBM));
+    a.tiles_n = static_cast<int>(ceil_div(p, kBN));
+    a.num_kb = static_cast<int>(ceil_div(n, kBK));
+    a.group_m = 16;
+    a.S = S;
+    a.wait_limit_ns = wait_limit_ns();
+    a.status = status;
+    a.vec_ok = (p % 4 == 0) && (reinterpret_cast<uintptr_t>(C) % 16 == 0);
+
+    if (dt == MOA_F32_SPLIT) {
+        split3_kernel<<<grid_for(a_plane, 256), 256, 0, s>>>(static_cast<const float*>(A), m, n,
+                                                             L.lda, a_sl, a_plane, status);
+        split3_kernel<<<grid_for(b_plane, 256), 256, 0, s>>>(static_cast<const float*>(B), n, p,
+                                                             L.ldb, b_sl, b_plane, status);
+        kernels += 2;
+        a.f64 = 0;
+        a.levels = 1;
+        a.kc[0] = 16;   // flush the FP32 accumulator every 1024 k
+        a.drop = 0;
+    } else {
+        int* eA = reinterpret_cast<int*>(base + L.ea_off);
+        int* eB = reinterpret_cast<int*>(base + L.eb_off);
+        void* cmax = base + L.cmax_off;
+        const bool in64 = dt == MOA_F64_SPLIT_F64IN;
+        cudaError_t e = cudaMemsetAsync(cmax, 0, static_cast<size_t>(p) * 8, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(colmax)");
+        const int rows_per_block = 8;   // 8 warps of 32 threads
+        const int64_t rblocks = std::min<int64_t>(ceil_div(m, rows_per_block), 16L * num_sms());
+        const int64_t chunk = 256;
+        dim3 cgrid(static_cast<unsigned>(ceil_div(p, 256)), static_cast<unsigned>(ceil_div(n, chunk)));
+        if (cgrid.y > 65535) return fail(MOA_ERR_ARG, "n too large for the column-max grid");
+        if (in64) {
+            const double* Ad = static_cast<const double*>(A);
+            const double* Bd = static_cast<const double*>(B);
+            row_exp_kernel<double><<<static_cast<int>(rblocks), 256, 0, s>>>(Ad, m, n, eA, status);
+            col_max_kernel<double><<<cgrid, 256, 0, s>>>(Bd, n, p, chunk,
+                                                         static_cast<unsigned long long*>(cmax));
+            col_exp_kernel<double><<<static_cast<int>(ceil_div(p, 256)), 256, 0, s>>>(
+                static_cast<const unsigned long long*>(cmax), p, eB, status);
+            digits_kernel<double><<<grid_for(a_plane, 256), 256, 0, s>>>(Ad, m, n, L.lda, eA, 0, S,
+                                                                          a_sl, a_plane);
+            digits_kernel<double><<<grid_for(b_plane, 256), 256, 0, s>>>(Bd, n, p, L.ldb, eB, 1, S,
+                                                                          b_sl, b_plane);
+        } else {
+            const float* Af = static_cast<const float*>(A);
+            const float* Bf = static_cast<const float*>(B);
+            row_exp_kernel<float><<<static_cast<int>(rblocks), 256, 0, s>>>(Af, m, n, eA, status);
+            col_max_kernel<float><<<cgrid, 256, 0, s>>>(Bf, n, p, chunk,
+                                                        static_cast<unsigned int*>(cmax));
+            col_exp_kernel<float><<<static_cast<int>(ceil_div(p, 256)), 256, 0, s>>>(
+                static_cast<const unsigned int*>(cmax), p, eB, status);
+            digits_kernel<float><<<grid_for(a_plane, 256), 256, 0, s>>>(Af, m, n, L.lda, eA, 0, S,
+                                                                        a_sl, a_plane);
+            digits_kernel<float><<<grid_for(b_plane, 256), 256, 0, s>>>(Bf, n, p, L.ldb, eB, 1, S,
+                                                                        b_sl, b_plane);
+        }
+        kernels += 6;
+        a.f64 = 1;
+        a.levels = S;
+        a.eA = eA;
+        a.eB = eB;
+        // Chunk lengths: every FP32 partial sum of a level must stay an
+        // integer of magnitude <= 2^24.  Per k, level 0 adds at most 2^16
+        // (|d_0| <= 256) and level L >= 1 at most (L + 3) * 2^14.
+        for (int lev = 0; lev < S; ++lev) {
+            const long long per_k = lev == 0 ? (1ll << 16) : static_cast<long long>(lev + 3) << 14;
+            const long long kmax = (1ll << 24) / per_k;
+            a.kc[lev] = static_cast<int>(std::max(1ll, kmax / kBK));
+        }
+        // int64 total: |T| <= n * 2^(8(S+1)) * 1.01 in units of the finest
+        // level before dropping `drop` bits; keep it below 2^62.
+        int nbits = 0;
+        while ((1ll << nbits) < n) ++nbits;
+        a.drop = std::max(0, nbits + kBeta * (S + 1) + 1 - 62);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "split pre-pass launch");
+
+    CUtensorMap tmA, tmB;
+    int rc = make_tmap_3d(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, a_sl, static_cast<uint64_t>(n),
+                          static_cast<uint64_t>(m), static_cast<uint64_t>(S),
+                          static_cast<uint64_t>(L.lda) * 2, static_cast<uint64_t>(a_plane) * 2, 64,
+                          kBM);
+    if (rc != MOA_OK) return rc;
+    rc = make_tmap_3d(&tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, b_sl, static_cast<uint64_t>(p),
+                      static_cast<uint64_t>(n), static_cast<uint64_t>(S),
+                      static_cast<uint64_t>(L.ldb) * 2, static_cast<uint64_t>(b_plane) * 2, 64, kBK);
+    if (rc != MOA_OK) return rc;
+    rc = launch_split_gemm(a, tmA, tmB, s, st);
+    if (st) {
+        st->slices = S;
+        st->products = dt == MOA_F32_SPLIT ? 6 : S * (S + 1) / 2;
+        st->kernels = kernels + 1;
+    }
+    return rc;
+}
+
+}  // namespace moa

@@ -1,0 +1,37 @@
+// split.h -- the split-precision modes (MOA_F32_SPLIT, MOA_F64_SPLIT_*),
+// internal to libmoa.so.
+#pragma once
+#include "internal.h"
+
+namespace moa {
+
+inline bool is_split(moa_dtype dt) {
+    return dt == MOA_F32_SPLIT || dt == MOA_F64_SPLIT_F32IN || dt == MOA_F64_SPLIT_F64IN;
+}
+
+// Digit radix 2^kBeta of the FP64-accuracy mode and its slice-count limits.
+constexpr int kBeta = 8;
+constexpr int kMinSlices = 3;
+constexpr int kMaxSlices = 7;
+constexpr int kDefaultSlices = 6;
+
+// Resolves the `slices` argument (0 = default); -1 if not allowed for dt.
+int split_slices(moa_dtype dt, int slices);
+
+size_t split_workspace_bytes(int64_t m, int64_t n, int64_t p, moa_dtype dt, int slices);
+
+int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const void* B,
+               void* C, int slices, void* ws, size_t ws_bytes, cudaStream_t s, moa_stats* st);
+
+// Workspace layout of a split call (byte offsets from the workspace base).
+struct SplitLayout {
+    int S;                 // slices per operand
+    int64_t lda, ldb;      // padded row pitches of the slice planes (elements)
+    size_t a_off, b_off;   // slice planes: S x m x lda and S x n x ldb BF16
+    size_t ea_off, eb_off; // FP64-accuracy: per-row / per-column exponents (int32)
+    size_t cmax_off;       // FP64-accuracy: per-column max |B| bit patterns (uint64)
+    size_t total;
+};
+SplitLayout split_layout(int64_t m, int64_t n, int64_t p, moa_dtype dt, int S);
+
+}  // namespace moa

@@ -1,0 +1,220 @@
+"""Thin ctypes binding over libmoa.so (the C ABI declared in include/moa.h).
+
+Every function here only marshals arguments: device memory comes from
+PyTorch tensors, streams from ``torch.cuda.Stream``, and every step of the
+GEMM runs in the library's CUDA kernels.  If libmoa.so is missing or cannot
+be loaded, :func:`lib` raises -- there is no CPU fallback.
+
+Low-level names mirror the C ABI (``moa_gemm``, ``moa_gemm_ex``,
+``moa_gemm_workspace_size``, ``moa_gemm_grouped``, ``moa_sync_status`` ...);
+:func:`gemm` and :func:`gemm_grouped` are convenience wrappers over them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmoa.so")
+
+# moa_status
+MOA_OK = 0
+MOA_ERR_ARG = -1
+MOA_ERR_DTYPE = -2
+MOA_ERR_ALIGN = -3
+MOA_ERR_WORKSPACE = -4
+MOA_ERR_NONFINITE = -5
+MOA_ERR_CUDA = -6
+MOA_ERR_TIMEOUT = -7
+MOA_ERR_BUDGET = -8
+MOA_ERR_REJECTED = -9
+MOA_ERR_BUSY = -10
+MOA_ERR_UNSUPPORTED = -11
+
+# moa_dtype
+MOA_F64 = 0
+MOA_F32_TF32 = 1
+MOA_F32_SIMT = 2
+MOA_BF16 = 3
+MOA_F32_SPLIT = 4
+MOA_F64_SPLIT_F32IN = 5
+MOA_F64_SPLIT_F64IN = 6
+
+MODES = {
+    "f64": MOA_F64, "tf32": MOA_F32_TF32, "f32_simt": MOA_F32_SIMT, "bf16": MOA_BF16,
+    "f32_split": MOA_F32_SPLIT, "f64_split_f32in": MOA_F64_SPLIT_F32IN,
+    "f64_split_f64in": MOA_F64_SPLIT_F64IN,
+}
+
+
+class moa_stats(ctypes.Structure):
+    _fields_ = [("block_m", ctypes.c_int32), ("block_n", ctypes.c_int32),
+                ("block_k", ctypes.c_int32), ("slices", ctypes.c_int32),
+                ("products", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("tiles", ctypes.c_int64), ("kernels", ctypes.c_int32),
+                ("padded", ctypes.c_int32)]
+
+
+class moa_gemm_desc(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("p", ctypes.c_int64),
+                ("dt", ctypes.c_int), ("A", ctypes.c_void_p), ("B", ctypes.c_void_p),
+                ("C", ctypes.c_void_p)]
+
+
+class MoaError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"moa status {status}: {msg}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+_i64 = ctypes.c_int64
+_vp = ctypes.c_void_p
+_sz = ctypes.c_size_t
+
+# Symbols the library exports (the declarations of include/moa.h).
+EXPORTS = {
+    "moa_gemm": (ctypes.c_int, [_i64, _i64, _i64, ctypes.c_int, _vp, _vp, _vp]),
+    "moa_gemm_workspace_size": (_sz, [_i64, _i64, _i64, ctypes.c_int, ctypes.c_int]),
+    "moa_gemm_ex": (ctypes.c_int, [_i64, _i64, _i64, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int,
+                                   _vp, _sz, _vp, ctypes.POINTER(moa_stats)]),
+    "moa_gemm_grouped_workspace_size": (_sz, [ctypes.c_int, ctypes.POINTER(moa_gemm_desc)]),
+    "moa_gemm_grouped": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(moa_gemm_desc), _vp, _sz,
+                                        _vp]),
+    "moa_sync_status": (ctypes.c_int, [_vp]),
+    "moa_last_error": (ctypes.c_char_p, []),
+    "moa_set_wait_limit_ns": (ctypes.c_uint64, [ctypes.c_uint64]),
+    "moa_version": (ctypes.c_char_p, []),
+    "moa_shutdown": (None, []),
+}
+
+
+def lib():
+    """Loads libmoa.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libmoa.so not built ({LIB_PATH}); run "
+                                   "`python -m paper_2306_11148_b300.build`")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in EXPORTS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().moa_last_error().decode()
+
+
+def check(status: int):
+    if status != MOA_OK:
+        raise MoaError(status, last_error())
+    return status
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------- raw ABI
+def moa_gemm(m, n, p, dt, A, B, C) -> int:
+    return lib().moa_gemm(m, n, p, dt, A, B, C)
+
+
+def moa_gemm_workspace_size(m, n, p, dt, slices=0) -> int:
+    return int(lib().moa_gemm_workspace_size(m, n, p, dt, slices))
+
+
+def moa_gemm_ex(m, n, p, dt, A, B, C, slices, ws, ws_bytes, stream, stats=None) -> int:
+    return lib().moa_gemm_ex(m, n, p, dt, A, B, C, slices, ws, ws_bytes, stream,
+                             ctypes.byref(stats) if stats is not None else None)
+
+
+def moa_sync_status(stream=0) -> int:
+    return lib().moa_sync_status(stream)
+
+
+def moa_set_wait_limit_ns(ns: int) -> int:
+    return int(lib().moa_set_wait_limit_ns(ns))
+
+
+def moa_version() -> str:
+    return lib().moa_version().decode()
+
+
+# ---------------------------------------------------------------- torch helpers
+def out_dtype(dt: int):
+    import torch
+    return torch.float64 if dt in (MOA_F64, MOA_F64_SPLIT_F32IN, MOA_F64_SPLIT_F64IN) \
+        else torch.float32
+
+
+def in_dtype(dt: int):
+    import torch
+    if dt in (MOA_F64, MOA_F64_SPLIT_F64IN):
+        return torch.float64
+    if dt == MOA_BF16:
+        return torch.bfloat16
+    return torch.float32
+
+
+class Workspace:
+    """A growable device workspace owned by PyTorch (256-byte aligned)."""
+
+    def __init__(self, device=None):
+        self.buf = None
+        self.device = device
+
+    def get(self, nbytes: int):
+        import torch
+        if nbytes == 0:
+            return 0, 0
+        if self.buf is None or self.buf.numel() < nbytes + 256:
+            self.buf = torch.empty(nbytes + 256, dtype=torch.uint8,
+                                   device=self.device or torch.device("cuda"))
+        base = self.buf.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        return aligned, nbytes
+
+
+_default_ws = {}
+
+
+def gemm(A, B, dt: int, C=None, slices: int = 0, stream=None, workspace: Workspace | None = None,
+         stats: bool = False):
+    """C := A . B through moa_gemm_ex on torch CUDA tensors (row-major, contiguous)."""
+    import torch
+    if A.dim() != 2 or B.dim() != 2 or A.shape[1] != B.shape[0]:
+        raise ValueError("A must be m x n and B n x p")
+    if not (A.is_contiguous() and B.is_contiguous()):
+        raise ValueError("A and B must be contiguous row-major tensors")
+    m, n = A.shape
+    p = B.shape[1]
+    if C is None:
+        C = torch.empty((m, p), dtype=out_dtype(dt), device=A.device)
+    if workspace is None:
+        workspace = _default_ws.setdefault(A.device, Workspace(A.device))
+    need = moa_gemm_workspace_size(m, n, p, dt, slices)
+    ws, wsb = workspace.get(need)
+    st = moa_stats() if stats else None
+    check(moa_gemm_ex(m, n, p, dt, _ptr(A), _ptr(B), _ptr(C), slices, ws, wsb,
+                      _stream_handle(stream), st))
+    return (C, st) if stats else C
+
+
+def sync_status(stream=None):
+    check(moa_sync_status(_stream_handle(stream)))

@@ -1,0 +1,108 @@
+"""The C-ABI boundary on the CPU: the library loads, exports every function
+that include/moa.h declares, and rejects bad arguments on the host before
+launching anything (no GPU is needed for any of these calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2306_11148_b300 import build as moa_build
+from paper_2306_11148_b300 import moa
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    moa_build.build()
+    return moa.lib()
+
+
+def _declared_functions():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for mt in re.finditer(r"\b(moa_[a-z0-9_]+)\s*\(", text):
+            names.add(mt.group(1))
+    return names
+
+
+def test_every_declared_symbol_is_exported(L):
+    declared = _declared_functions()
+    assert "moa_gemm" in declared and "moa_gemm_grouped" in declared
+    for name in sorted(declared):
+        assert hasattr(L, name), f"{name} declared in include/ but not exported"
+
+
+def test_binding_covers_declared_symbols(L):
+    assert _declared_functions() <= set(moa.EXPORTS)
+
+
+def test_version(L):
+    assert "sm_103a" in moa.moa_version()
+
+
+@pytest.mark.parametrize("m,n,p", [(-1, 4, 4), (4, -1, 4), (4, 4, -1)])
+def test_negative_dimensions_rejected(L, m, n, p):
+    rc = moa.moa_gemm_ex(m, n, p, moa.MOA_F32_TF32, 16, 16, 16, 0, None, 0, None)
+    assert rc == moa.MOA_ERR_ARG
+    assert "negative" in moa.last_error()
+
+
+def test_unknown_dtype_rejected(L):
+    assert moa.moa_gemm_ex(4, 4, 4, 99, 16, 16, 16, 0, None, 0, None) == moa.MOA_ERR_DTYPE
+
+
+def test_null_pointers_rejected(L):
+    assert moa.moa_gemm_ex(4, 4, 4, moa.MOA_F64, None, 16, 16, 0, None, 0, None) == moa.MOA_ERR_ARG
+    assert moa.moa_gemm_ex(4, 4, 4, moa.MOA_F64, 16, 16, None, 0, None, 0, None) == moa.MOA_ERR_ARG
+
+
+def test_misaligned_pointers_rejected(L):
+    assert moa.moa_gemm_ex(4, 4, 4, moa.MOA_F64, 8 + 4, 16, 16, 0, None, 0, None) == moa.MOA_ERR_ALIGN
+    # tensor-core modes need 16-byte aligned operands
+    assert moa.moa_gemm_ex(4, 4, 4, moa.MOA_F32_TF32, 16 + 4, 16, 16, 0, None, 0, None) == \
+        moa.MOA_ERR_ALIGN
+
+
+def test_missing_workspace_rejected(L):
+    # n = 5 needs padded copies for TMA (20-byte rows)
+    need = moa.moa_gemm_workspace_size(8, 5, 8, moa.MOA_F32_TF32, 0)
+    assert need > 0
+    rc = moa.moa_gemm_ex(8, 5, 8, moa.MOA_F32_TF32, 256, 512, 1024, 0, None, 0, None)
+    assert rc == moa.MOA_ERR_WORKSPACE
+    for dt in (moa.MOA_F32_SPLIT, moa.MOA_F64_SPLIT_F32IN, moa.MOA_F64_SPLIT_F64IN):
+        assert moa.moa_gemm_workspace_size(64, 64, 64, dt, 0) > 0
+        rc = moa.moa_gemm_ex(64, 64, 64, dt, 256, 512, 1024, 0, None, 0, None)
+        assert rc == moa.MOA_ERR_WORKSPACE
+
+
+def test_workspace_sizes(L):
+    # aligned dense shapes need none; split modes hold S slice planes
+    assert moa.moa_gemm_workspace_size(256, 256, 256, moa.MOA_BF16, 0) == 0
+    assert moa.moa_gemm_workspace_size(256, 256, 256, moa.MOA_F64, 0) == 0
+    s3 = moa.moa_gemm_workspace_size(256, 256, 256, moa.MOA_F32_SPLIT, 0)
+    assert s3 >= 3 * 2 * (256 * 256 * 2)
+    s6 = moa.moa_gemm_workspace_size(256, 256, 256, moa.MOA_F64_SPLIT_F32IN, 0)
+    s7 = moa.moa_gemm_workspace_size(256, 256, 256, moa.MOA_F64_SPLIT_F32IN, 7)
+    assert s7 > s6 >= 6 * 2 * (256 * 256 * 2)
+    # unsupported slice counts report 0 and are rejected by the call
+    assert moa.moa_gemm_workspace_size(256, 256, 256, moa.MOA_F64_SPLIT_F32IN, 9) == 0
+    assert moa.moa_gemm_ex(64, 64, 64, moa.MOA_F64_SPLIT_F32IN, 256, 512, 1024, 9, 4096, 1 << 20,
+                           None) == moa.MOA_ERR_DTYPE
+
+
+def test_empty_problems_are_noops(L):
+    # m == 0 or p == 0: nothing to do, nothing launched (works without a GPU)
+    assert moa.moa_gemm_ex(0, 5, 5, moa.MOA_F64, None, None, None, 0, None, 0, None) == moa.MOA_OK
+    assert moa.moa_gemm_ex(5, 5, 0, moa.MOA_F64, None, None, None, 0, None, 0, None) == moa.MOA_OK
+
+
+def test_grouped_argument_errors(L):
+    assert L.moa_gemm_grouped(-1, None, None, 0, None) == moa.MOA_ERR_ARG
+    assert L.moa_gemm_grouped(0, None, None, 0, None) == moa.MOA_OK
+    assert L.moa_gemm_grouped(2, None, None, 0, None) == moa.MOA_ERR_ARG

@@ -1,0 +1,180 @@
+"""GPU parity of every precision mode of the ONF GEMM against the FP64 oracle.
+
+C[(i*p)+j] := sum_k A[(i*n)+k] * B[(k*p)+j]  (Eq. eq:dnf, Sec. 2).
+
+Two kinds of check per mode, through the C ABI (moa_gemm_ex):
+* integer-valued inputs in {-8..8}: every partial sum is an integer below
+  2^24, so every mode must be bit-exact against the oracle;
+* random inputs (the workloads' distributions): relative Frobenius error
+  against the oracle within the mode's stated tolerance.
+Shapes span several 128-row tiles, ragged M/N/K tails, single rows/columns and
+row pitches that are not a multiple of 16 bytes (padded by the library).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2306_11148_b300 import inputs
+from paper_2306_11148_b300 import moa
+
+pytestmark = pytest.mark.gpu
+
+# Relative Frobenius tolerance per mode against the FP64 oracle.
+TOL = {
+    moa.MOA_F64: 1e-12,
+    moa.MOA_F32_TF32: 5e-3,
+    moa.MOA_F32_SIMT: 1e-5,
+    moa.MOA_BF16: 1e-2,
+    moa.MOA_F32_SPLIT: 1e-5,
+    moa.MOA_F64_SPLIT_F32IN: 1e-12,
+    moa.MOA_F64_SPLIT_F64IN: 1e-12,
+}
+ALL_MODES = list(TOL)
+NAMES = {v: k for k, v in moa.MODES.items()}
+
+SHAPES = [
+    (1, 1, 1),
+    (15, 17, 31),
+    (33, 127, 129),
+    (128, 64, 128),
+    (129, 65, 257),
+    (256, 256, 256),
+    (300, 200, 520),
+    (257, 1000, 200),
+    (64, 4096, 96),
+]
+
+
+def _rel(C, ref):
+    den = np.linalg.norm(ref)
+    return np.linalg.norm(C - ref) / (den if den > 0 else 1.0)
+
+
+def _run(A, B, dt, slices=0):
+    C = moa.gemm(A.cuda(), B.cuda(), dt, slices=slices)
+    moa.sync_status()
+    return C.cpu().double().numpy()
+
+
+@pytest.mark.parametrize("dt", ALL_MODES, ids=lambda d: NAMES[d])
+@pytest.mark.parametrize("m,n,p", SHAPES)
+def test_integer_inputs_bit_exact(dt, m, n, p):
+    A, B = inputs.integer_pair(m, n, p, dtype=moa.in_dtype(dt), seed=m + 7 * n + 13 * p)
+    C = _run(A, B, dt)
+    ref = oracle.gemm(A.double().numpy(), B.double().numpy())
+    assert np.array_equal(C, ref), f"max diff {np.abs(C - ref).max()}"
+
+
+@pytest.mark.parametrize("dt", ALL_MODES, ids=lambda d: NAMES[d])
+@pytest.mark.parametrize("m,n,p", SHAPES)
+def test_uniform_inputs_within_tolerance(dt, m, n, p):
+    A, B = inputs.uniform_pair(m, n, p, dtype=moa.in_dtype(dt), seed=1)
+    C = _run(A, B, dt)
+    ref = oracle.gemm(A.double().numpy(), B.double().numpy())
+    assert _rel(C, ref) <= TOL[dt]
+
+
+@pytest.mark.parametrize("dt", [moa.MOA_F32_SPLIT, moa.MOA_F64_SPLIT_F32IN, moa.MOA_F32_TF32],
+                         ids=lambda d: NAMES[d])
+@pytest.mark.parametrize("scaled", [None, "rows", "rowcol"])
+def test_normal_scaled_inputs(dt, scaled):
+    A, B = inputs.normal_pair(200, 1536, 160, dtype=torch.float32, seed=3, scaled=scaled)
+    C = _run(A, B, dt)
+    ref = oracle.gemm(A.double().numpy(), B.double().numpy())
+    assert _rel(C, ref) <= TOL[dt]
+
+
+@pytest.mark.parametrize("S", [3, 4, 5, 6, 7])
+def test_f64_split_matches_exact_slice_product(S):
+    """The FP64-accuracy mode reaches the exact triangular slice product of
+    the oracle's digits, up to the final FP64 rounding and the int64 total's
+    dropped low bits (relative 2^-48 of the scale)."""
+    A, B = inputs.normal_pair(130, 700, 140, dtype=torch.float64, seed=5, scaled="rows")
+    C = _run(A, B, moa.MOA_F64_SPLIT_F64IN, slices=S)
+    eA, dA = oracle.slice_fixed(A.numpy(), 0, 8, S)
+    eB, dB = oracle.slice_fixed(B.numpy(), 1, 8, S)
+    exact = oracle.split_gemm_exact(dA, eA, dB, eB, 8, S)
+    scale = np.outer(2.0 ** eA.astype(np.float64), 2.0 ** eB.astype(np.float64))
+    assert np.all(np.abs(C - exact) <= scale * 2.0 ** -46 + np.abs(exact) * 2.0 ** -52)
+
+
+def test_f32_split_slices_match_oracle_split():
+    """The FP32-accuracy mode's result equals the six-product sum of the
+    oracle's BF16 slices to FP32 accumulation accuracy."""
+    A, B = inputs.normal_pair(96, 512, 80, dtype=torch.float32, seed=8)
+    s = oracle.split3_bf16(A.numpy())
+    t = oracle.split3_bf16(B.numpy())
+    pairs = [(0, 0), (0, 1), (1, 0), (0, 2), (1, 1), (2, 0)]
+    six = sum(oracle.gemm(s[i], t[j]) for i, j in pairs)
+    C = _run(A, B, moa.MOA_F32_SPLIT)
+    assert _rel(C, six) <= 2e-6
+
+
+def test_zero_inner_dimension_gives_zero():
+    for dt in ALL_MODES:
+        C = torch.full((5, 7), 3.0, dtype=moa.out_dtype(dt), device="cuda")
+        A = torch.empty((5, 0), dtype=moa.in_dtype(dt), device="cuda")
+        B = torch.empty((0, 7), dtype=moa.in_dtype(dt), device="cuda")
+        moa.gemm(A, B, dt, C=C)
+        moa.sync_status()
+        assert torch.all(C == 0)
+
+
+def test_empty_outer_dimensions_touch_nothing():
+    for dt in ALL_MODES:
+        A = torch.ones((0, 5), dtype=moa.in_dtype(dt), device="cuda")
+        B = torch.ones((5, 3), dtype=moa.in_dtype(dt), device="cuda")
+        C = moa.gemm(A, B, dt)
+        assert C.shape == (0, 3)
+
+
+def test_nonfinite_input_reported_by_split_modes():
+    for dt in (moa.MOA_F32_SPLIT, moa.MOA_F64_SPLIT_F32IN):
+        A, B = inputs.uniform_pair(64, 64, 64, dtype=torch.float32, seed=2)
+        A[3, 5] = float("nan")
+        moa.gemm(A.cuda(), B.cuda(), dt)
+        assert moa.moa_sync_status(moa._stream_handle(None)) == moa.MOA_ERR_NONFINITE
+        moa.sync_status()   # cleared
+
+
+def test_plain_moa_gemm_entry_point():
+    """moa_gemm (library-owned workspace, legacy default stream)."""
+    A, B = inputs.uniform_pair(77, 131, 45, dtype=torch.float32, seed=4)
+    Ad, Bd = A.cuda(), B.cuda()
+    ref = oracle.gemm(A.double().numpy(), B.double().numpy())
+    for dt in (moa.MOA_F32_TF32, moa.MOA_F32_SPLIT, moa.MOA_F64_SPLIT_F32IN):
+        C = torch.empty((77, 45), dtype=moa.out_dtype(dt), device="cuda")
+        torch.cuda.synchronize()
+        moa.check(moa.moa_gemm(77, 131, 45, dt, Ad.data_ptr(), Bd.data_ptr(), C.data_ptr()))
+        moa.check(moa.moa_sync_status(0))
+        assert _rel(C.cpu().double().numpy(), ref) <= TOL[dt]
+
+
+def test_deterministic_repeat():
+    """Two runs give bit-identical results (catches pipeline races)."""
+    A, B = inputs.uniform_pair(384, 2048, 512, dtype=torch.float32, seed=6)
+    Ad, Bd = A.cuda(), B.cuda()
+    for dt in (moa.MOA_F32_TF32, moa.MOA_F32_SPLIT, moa.MOA_F64_SPLIT_F32IN):
+        c1 = moa.gemm(Ad, Bd, dt).clone()
+        c2 = moa.gemm(Ad, Bd, dt)
+        torch.cuda.synchronize()
+        assert torch.equal(c1, c2)
+
+
+@pytest.mark.parametrize("dt,N", [(moa.MOA_F32_TF32, 8192), (moa.MOA_BF16, 8192),
+                                  (moa.MOA_F32_SPLIT, 8192), (moa.MOA_F64_SPLIT_F32IN, 8192),
+                                  (moa.MOA_F64, 2048), (moa.MOA_F32_SIMT, 4096)],
+                         ids=lambda x: NAMES.get(x, str(x)) if isinstance(x, int) and x < 10 else str(x))
+def test_full_size_sampled_rows(dt, N):
+    """Workload sizes: 64 seed-chosen rows recomputed by the oracle."""
+    if dt in (moa.MOA_F64,):
+        A, B = inputs.square_uniform(N, torch.float64)
+    else:
+        A, B = inputs.normal_pair(N, N, N, dtype=moa.in_dtype(dt), seed=0)
+    C = moa.gemm(A.cuda(), B.cuda(), dt)
+    moa.sync_status()
+    rows = inputs.sample_rows(N, 64)
+    got = C[torch.from_numpy(rows).cuda()].cpu().double().numpy()
+    ref = oracle.gemm_rows(A.double().numpy(), B.double().numpy(), rows)
+    assert _rel(got, ref) <= TOL[dt]
