@@ -32,6 +32,10 @@ MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}
 # Dense tensor rates relative to BF16 (nominal datasheet figures).
 NOMINAL_RATIO = {"bf16": 1.0, "tf32": 1.1 / 2.25, "fp8": 2.0}
+# DRAM traffic (read + write bytes) per launch of the dominant kernel from one
+# ncu capture, keyed by (mode, N); see profiles/.  Remove an entry when its
+# kernel changes.
+TRAFFIC = {("tf32", 8192): 2.276975e9 + 0.255525e9}
 
 
 def load_peaks():
@@ -104,29 +108,54 @@ class ClockSampler:
 
 
 def gpu_identity(dev):
+    """(PCI bus id as NVML prints it, NVML-style UUID) of a torch device."""
     import torch
     props = torch.cuda.get_device_properties(dev)
+    pci = uuid = None
     try:
-        return f"{props.pci_domain_id:08x}:{props.pci_bus_id:02x}:{props.pci_device_id:02x}.0"
+        pci = f"{props.pci_domain_id:08X}:{props.pci_bus_id:02X}:{props.pci_device_id:02X}.0"
     except Exception:
-        return None
+        pass
+    try:
+        uuid = "GPU-" + str(props.uuid)
+    except Exception:
+        pass
+    return pci, uuid
 
 
 class Energy:
-    """NVML total-energy counter (mJ) of the device."""
+    """NVML total-energy counter (mJ) of the device, found by PCI bus id, then
+    by UUID, then as the only visible device."""
 
-    def __init__(self, pci):
+    def __init__(self, pci, uuid=None):
         self.h = None
+        self.why = None
         try:
             import pynvml
             pynvml.nvmlInit()
             self.nv = pynvml
-            if pci:
-                self.h = pynvml.nvmlDeviceGetHandleByPciBusId(pci.encode())
-            else:
-                self.h = pynvml.nvmlDeviceGetHandleByIndex(0)
-        except Exception:
-            self.h = None
+        except Exception as e:
+            self.why = f"nvmlInit: {e}"
+            return
+        tries = []
+        if pci:
+            tries += [lambda: pynvml.nvmlDeviceGetHandleByPciBusId(pci),
+                      lambda: pynvml.nvmlDeviceGetHandleByPciBusId(pci.encode())]
+        if uuid:
+            tries += [lambda: pynvml.nvmlDeviceGetHandleByUUID(uuid)]
+        tries += [lambda: pynvml.nvmlDeviceGetHandleByIndex(0)
+                  if pynvml.nvmlDeviceGetCount() == 1 else None]
+        errs = []
+        for t in tries:
+            try:
+                h = t()
+                if h is not None:
+                    pynvml.nvmlDeviceGetTotalEnergyConsumption(h)
+                    self.h = h
+                    return
+            except Exception as e:
+                errs.append(str(e))
+        self.why = "; ".join(errs) or "no handle"
 
     def read_j(self):
         if self.h is None:
@@ -182,10 +211,10 @@ def make_inputs(mode, N):
     return dt, A, B
 
 
-def time_device(fn, steps, warmup, stream, ws):
+def time_device(fn, steps, warmup, stream, ws, warm_fn=None):
     import torch
     for _ in range(warmup):
-        fn()
+        (warm_fn or fn)()
     torch.cuda.synchronize()
     barrier(ws)
     torch.cuda.synchronize()
@@ -201,7 +230,7 @@ def time_device(fn, steps, warmup, stream, ws):
 
 
 def bench_mode(mode, N, steps, warmup, ws, stream, want_energy=False, energy=None,
-               want_e2e=False):
+               want_e2e=False, check_rows=True):
     import torch
     from paper_2306_11148_b300 import moa
     dt, A, B = make_inputs(mode, N)
@@ -219,10 +248,27 @@ def bench_mode(mode, N, steps, warmup, ws, stream, want_energy=False, energy=Non
         if rc != 0:
             raise moa.MoaError(rc, moa.last_error())
 
+    # Per-step CUDA events around the main GEMM kernel only (recorded by the
+    # library on this stream immediately before and after that launch).
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    for a, b in kev:
+        a.record(stream)
+        b.record(stream)
+    idx = [0]
+
+    def step_timed():
+        a, b = kev[idx[0]]
+        moa.lib().moa_profile_events(a.cuda_event, b.cuda_event)
+        step()
+        idx[0] += 1
+
     with torch.cuda.stream(stream):
-        t = time_device(step, steps, warmup, stream, ws)
+        t = time_device(step_timed, steps, warmup, stream, ws, warm_fn=step)
+    moa.lib().moa_profile_events(None, None)
+    kernel_s = sum(a.elapsed_time(b) for a, b in kev) / 1000.0
     moa.check(moa.moa_sync_status(sh))
-    out = {"mode": mode, "N": N, "seconds": t, "steps": steps,
+    out = {"mode": mode, "N": N, "seconds": t, "kernel_seconds": kernel_s, "steps": steps,
            "flops_per_step": 2.0 * N ** 3, "kernels_per_step": int(st.kernels),
            "tile": [int(st.block_m), int(st.block_n), int(st.block_k)],
            "products": int(st.products), "slices": int(st.slices)}
@@ -245,6 +291,8 @@ def bench_mode(mode, N, steps, warmup, ws, stream, want_energy=False, energy=Non
         out["e2e"] = bench_e2e(dt, A, B, C, N, max(2, min(steps, 5)), 1, stream, ws)
     # oracle spot check of a few rows (cheap) to tie the timed output to parity
     try:
+        if not check_rows:
+            raise RuntimeError("skipped")
         import numpy as np
 
         import oracle
@@ -349,7 +397,11 @@ def main():
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--no-extras", action="store_true", help="skip the other-mode measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--profile", action="store_true",
+                    help="timed GEMM steps only (no energy window, e2e, extras, CPU baseline)")
     args = ap.parse_args()
+    if args.profile:
+        args.no_extras = args.no_cpu = True
     args.warmup = max(args.warmup, 3)
 
     ws, rank, local = dist_setup()
@@ -369,16 +421,17 @@ def main():
     torch.cuda.set_device(local)
     moa.lib()
     peaks = load_peaks()
-    pci = gpu_identity(local)
-    energy = Energy(pci)
+    pci, uuid = gpu_identity(local)
+    energy = Energy(pci, uuid)
     stream = torch.cuda.Stream()
     mode = MODE_OF[args.workload]
     N = args.n
 
     clocks = ClockSampler(pci)
     clocks.start()
-    main_res = bench_mode(mode, N, args.steps, args.warmup, ws, stream, want_energy=True,
-                          energy=energy, want_e2e=True)
+    main_res = bench_mode(mode, N, args.steps, args.warmup, ws, stream,
+                          want_energy=not args.profile, energy=energy, want_e2e=not args.profile,
+                          check_rows=not args.profile)
     clk = clocks.stop()
 
     t_max = max_over_ranks(main_res["seconds"], ws)
@@ -397,10 +450,13 @@ def main():
               "f64_split_f32in": "bf16"}.get(mode)
     if kdtype:
         peak = peaks["bf16_tflops"] * NOMINAL_RATIO[kdtype]
+        # tensor work per launch = products x 2N^3 (one slice product per
+        # product for split modes); duration = main kernel's CUDA-event time
         achieved = main_res["flops_per_step"] * max(1, main_res["products"]) / \
-            (main_res["seconds"] / args.steps) / 1e12
+            (main_res["kernel_seconds"] / args.steps) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": TRAFFIC.get((mode, N)),
+                "kernel_ms": main_res["kernel_seconds"] / args.steps * 1e3,
                 "peak_source": f"{peaks['source']} bf16 x nominal {kdtype}/bf16 ratio",
                 "kernel": "dense_tc_kernel" if mode in ("tf32", "bf16") else "split_gemm_kernel"}
     else:
@@ -446,7 +502,7 @@ def main():
                     "d2h_bytes_per_step": e2e.get("d2h_bytes_per_step")},
             "gpu_launches": main_res["kernels_per_step"] * args.steps,
             "clocks": clk,
-            "energy": main_res.get("energy"),
+            "energy": main_res.get("energy") or {"unavailable": energy.why},
             "tile": main_res["tile"],
             "modes": modes,
         }

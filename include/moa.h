@@ -138,6 +138,13 @@ const char* moa_last_error(void);
  * Returns the previous value. */
 uint64_t moa_set_wait_limit_ns(uint64_t ns);
 
+/* Profiling hook for the calling thread: when both are non-NULL cudaEvent_t
+ * handles, every later GEMM call of this thread records `start_event`
+ * immediately before its main kernel (the tensor-core or CUDA-core GEMM, not
+ * the pre-passes) and `stop_event` immediately after it, on the call's stream.
+ * Pass NULL, NULL to stop.  The events stay owned by the caller.  Returns MOA_OK. */
+int moa_profile_events(void* start_event, void* stop_event);
+
 /* Library version string. */
 const char* moa_version(void);
 

@@ -51,23 +51,32 @@ bool is_tc_dense(moa_dtype dt) { return dt == MOA_BF16 || dt == MOA_F32_TF32; }
 int64_t tma_pitch(int64_t cols, int esize) { return round_up(cols, 16 / esize); }
 
 struct DenseWs {
-    bool pad_a, pad_b;
+    bool pad_a, pad_b, trans_b;
     int64_t lda, ldb;
     size_t a_bytes, b_bytes, total;
 };
 
+// BF16: A and B are read in place unless a row pitch is not a multiple of 16
+// bytes (then copied to a padded pitch).  TF32: B is always transposed into
+// the workspace (p x round_up(n, 4)), because the TF32 MMA reads K-major B only.
 DenseWs dense_ws(int64_t m, int64_t n, int64_t p, moa_dtype dt) {
     DenseWs w{};
     const int es = in_size(dt);
     w.lda = tma_pitch(n, es);
-    w.ldb = tma_pitch(p, es);
     w.pad_a = w.lda != n;
-    w.pad_b = w.ldb != p;
     w.a_bytes = w.pad_a ? align_up(static_cast<size_t>(m) * w.lda * es) : 0;
-    w.b_bytes = w.pad_b ? align_up(static_cast<size_t>(n) * w.ldb * es) : 0;
-    w.total = w.a_bytes + w.b_bytes;
     if (!w.pad_a) w.lda = n;
-    if (!w.pad_b) w.ldb = p;
+    if (dt == MOA_F32_TF32) {
+        w.trans_b = true;
+        w.ldb = tma_pitch(n, es);
+        w.b_bytes = align_up(static_cast<size_t>(p) * w.ldb * es);
+    } else {
+        w.ldb = tma_pitch(p, es);
+        w.pad_b = w.ldb != p;
+        w.b_bytes = w.pad_b ? align_up(static_cast<size_t>(n) * w.ldb * es) : 0;
+        if (!w.pad_b) w.ldb = p;
+    }
+    w.total = w.a_bytes + w.b_bytes;
     return w;
 }
 
@@ -152,7 +161,13 @@ int gemm_ex(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const 
                 a = base;
                 ++kernels;
             }
-            if (w.pad_b) {
+            if (w.trans_b) {
+                rc = transpose_pad_launch(static_cast<const float*>(B), n, p,
+                                          reinterpret_cast<float*>(base + w.a_bytes), w.ldb, s);
+                if (rc != MOA_OK) return rc;
+                b = base + w.a_bytes;
+                ++kernels;
+            } else if (w.pad_b) {
                 rc = pad_copy_launch(B, base + w.a_bytes, n, p, w.ldb, es, s);
                 if (rc != MOA_OK) return rc;
                 b = base + w.a_bytes;

@@ -88,8 +88,10 @@ int launch_simt(int64_t m, int64_t n, int64_t p, const T* A, const T* B, T* C, c
     const int64_t gx = ceil_div(p, BN), gy = ceil_div(m, BM);
     if (gy > 65535) return fail(MOA_ERR_ARG, "m too large for the SIMT grid");
     dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(gy));
+    prof_begin(s);
     simt_gemm_kernel<T, BM, BN, BK, TM, TN><<<grid, (BM / TM) * (BN / TN), 0, s>>>(A, B, C, m, n, p);
     cudaError_t e = cudaGetLastError();
+    prof_end(s);
     if (e != cudaSuccess) return cuda_fail(e, "simt_gemm_kernel launch");
     return MOA_OK;
 }

@@ -50,7 +50,7 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
     tn = r / gsize;
 }
 
-template <int ESIZE, int BLOCK_N, int STAGES>
+template <int ESIZE, int BLOCK_N, int STAGES, int BKM>
 struct DenseCfg {
     static constexpr int BLOCK_M = 128;
     static constexpr int BK = 128 / ESIZE;          // K elements per stage (128 bytes)
@@ -62,14 +62,18 @@ struct DenseCfg {
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int TMEM_COLS = 2 * BLOCK_N <= 32 ? 32 : (2 * BLOCK_N <= 64 ? 64 : (2 * BLOCK_N <= 128 ? 128 : (2 * BLOCK_N <= 256 ? 256 : 512)));
     static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + 256;
-    static constexpr uint32_t IDESC = make_idesc(ESIZE == 2 ? 1u : 2u, BLOCK_M, BLOCK_N, 0u, 1u);
+    static constexpr uint32_t IDESC =
+        make_idesc(ESIZE == 2 ? 1u : 2u, BLOCK_M, BLOCK_N, 0u, BKM ? 0u : 1u);
 };
 
-template <int ESIZE, int BLOCK_N, int STAGES>
+// BKM = 0: B staged MN-major (row-major n x p, contiguous in j).
+// BKM = 1: B staged K-major from its transpose (p x n), for the TF32 kind,
+//          whose MMA does not read MN-major operands.
+template <int ESIZE, int BLOCK_N, int STAGES, int BKM>
 __global__ void __launch_bounds__(192, 1)
     dense_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const DenseArgs args) {
-    using Cfg = DenseCfg<ESIZE, BLOCK_N, STAGES>;
+    using Cfg = DenseCfg<ESIZE, BLOCK_N, STAGES, BKM>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                ~static_cast<uintptr_t>(1023));
@@ -136,10 +140,15 @@ __global__ void __launch_bounds__(192, 1)
                     mbar_arrive_expect_tx(&full[stage], Cfg::STAGE_BYTES);
                     tma_load_2d(sA + stage * Cfg::A_BYTES, &tmA, &full[stage], kb * Cfg::BK,
                                 tm * Cfg::BLOCK_M);
+                    if constexpr (BKM) {
+                        tma_load_2d(sB + stage * Cfg::B_BYTES, &tmB, &full[stage], kb * Cfg::BK,
+                                    tn * BLOCK_N);
+                    } else {
 #pragma unroll
-                    for (int c = 0; c < BLOCK_N / Cfg::CHUNK_N; ++c)
-                        tma_load_2d(sB + stage * Cfg::B_BYTES + c * Cfg::CHUNK_BYTES, &tmB,
-                                    &full[stage], tn * BLOCK_N + c * Cfg::CHUNK_N, kb * Cfg::BK);
+                        for (int c = 0; c < BLOCK_N / Cfg::CHUNK_N; ++c)
+                            tma_load_2d(sB + stage * Cfg::B_BYTES + c * Cfg::CHUNK_BYTES, &tmB,
+                                        &full[stage], tn * BLOCK_N + c * Cfg::CHUNK_N, kb * Cfg::BK);
+                    }
                     ++issued;
                     if (++stage == STAGES) {
                         stage = 0;
@@ -184,11 +193,12 @@ __global__ void __launch_bounds__(192, 1)
                     const uint64_t adesc =
                         smem_desc_sw128(smem_u32(sA + stage * Cfg::A_BYTES), 16, 1024);
                     const uint64_t bdesc = smem_desc_sw128(smem_u32(sB + stage * Cfg::B_BYTES),
-                                                           Cfg::CHUNK_BYTES, 1024);
+                                                           BKM ? 16 : Cfg::CHUNK_BYTES, 1024);
 #pragma unroll
                     for (int k = 0; k < Cfg::BK / Cfg::MMA_K; ++k) {
                         const uint64_t a_off = static_cast<uint64_t>((k * 32) >> 4);
-                        const uint64_t b_off = static_cast<uint64_t>((k * Cfg::MMA_K * 128) >> 4);
+                        const uint64_t b_off = BKM ? a_off
+                                                   : static_cast<uint64_t>((k * Cfg::MMA_K * 128) >> 4);
                         if constexpr (ESIZE == 2)
                             mma_f16(d, adesc + a_off, bdesc + b_off, Cfg::IDESC, (kb | k) != 0);
                         else
@@ -259,18 +269,22 @@ __global__ void __launch_bounds__(192, 1)
     }
 }
 
-template <int ESIZE, int BLOCK_N, int STAGES>
+template <int ESIZE, int BLOCK_N, int STAGES, int BKM>
 int launch_cfg(int64_t m, int64_t n, int64_t p, const void* A, int64_t lda, const void* B,
                int64_t ldb, float* C, cudaStream_t s, moa_stats* st) {
-    using Cfg = DenseCfg<ESIZE, BLOCK_N, STAGES>;
+    using Cfg = DenseCfg<ESIZE, BLOCK_N, STAGES, BKM>;
     const CUtensorMapDataType dt =
         ESIZE == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     CUtensorMap tmA, tmB;
     int rc = make_tmap_2d(&tmA, dt, A, static_cast<uint64_t>(n), static_cast<uint64_t>(m),
                           static_cast<uint64_t>(lda) * ESIZE, Cfg::BK, Cfg::BLOCK_M);
     if (rc != MOA_OK) return rc;
-    rc = make_tmap_2d(&tmB, dt, B, static_cast<uint64_t>(p), static_cast<uint64_t>(n),
-                      static_cast<uint64_t>(ldb) * ESIZE, Cfg::CHUNK_N, Cfg::BK);
+    if (BKM)   // B^T: p rows of n (pitch ldb), box = BLOCK_N rows x 128 bytes
+        rc = make_tmap_2d(&tmB, dt, B, static_cast<uint64_t>(n), static_cast<uint64_t>(p),
+                          static_cast<uint64_t>(ldb) * ESIZE, Cfg::BK, BLOCK_N);
+    else
+        rc = make_tmap_2d(&tmB, dt, B, static_cast<uint64_t>(p), static_cast<uint64_t>(n),
+                          static_cast<uint64_t>(ldb) * ESIZE, Cfg::CHUNK_N, Cfg::BK);
     if (rc != MOA_OK) return rc;
 
     DenseArgs args;
@@ -287,7 +301,7 @@ int launch_cfg(int64_t m, int64_t n, int64_t p, const void* A, int64_t lda, cons
     args.status = device_status_ptr();
     if (!args.status) return MOA_ERR_CUDA;
 
-    auto kern = dense_tc_kernel<ESIZE, BLOCK_N, STAGES>;
+    auto kern = dense_tc_kernel<ESIZE, BLOCK_N, STAGES, BKM>;
     static bool attr_set = false;   // per instantiation; the attribute is per device function
     if (!attr_set) {
         cudaError_t e =
@@ -297,8 +311,10 @@ int launch_cfg(int64_t m, int64_t n, int64_t p, const void* A, int64_t lda, cons
     }
     const long tiles = static_cast<long>(args.tiles_m) * args.tiles_n;
     const int grid = static_cast<int>(std::min<long>(tiles, num_sms()));
-    dense_tc_kernel<ESIZE, BLOCK_N, STAGES><<<grid, 192, Cfg::SMEM, s>>>(tmA, tmB, args);
+    prof_begin(s);
+    dense_tc_kernel<ESIZE, BLOCK_N, STAGES, BKM><<<grid, 192, Cfg::SMEM, s>>>(tmA, tmB, args);
     cudaError_t e = cudaGetLastError();
+    prof_end(s);
     if (e != cudaSuccess) return cuda_fail(e, "dense_tc_kernel launch");
     if (st) {
         st->block_m = Cfg::BLOCK_M;
@@ -324,13 +340,14 @@ int dense_tc_launch(bool in_bf16, int64_t m, int64_t n, int64_t p, const void* A
     if (tiles256 < sms && tiles128 > tiles256) bn = 128;
     if (bn == 128 && tiles128 < sms && p <= 64) bn = 64;
     if (in_bf16) {
-        if (bn == 256) return launch_cfg<2, 256, 4>(m, n, p, A, lda, B, ldb, C, s, st);
-        if (bn == 128) return launch_cfg<2, 128, 6>(m, n, p, A, lda, B, ldb, C, s, st);
-        return launch_cfg<2, 64, 8>(m, n, p, A, lda, B, ldb, C, s, st);
+        if (bn == 256) return launch_cfg<2, 256, 4, 0>(m, n, p, A, lda, B, ldb, C, s, st);
+        if (bn == 128) return launch_cfg<2, 128, 6, 0>(m, n, p, A, lda, B, ldb, C, s, st);
+        return launch_cfg<2, 64, 8, 0>(m, n, p, A, lda, B, ldb, C, s, st);
     }
-    if (bn == 256) return launch_cfg<4, 256, 4>(m, n, p, A, lda, B, ldb, C, s, st);
-    if (bn == 128) return launch_cfg<4, 128, 6>(m, n, p, A, lda, B, ldb, C, s, st);
-    return launch_cfg<4, 64, 8>(m, n, p, A, lda, B, ldb, C, s, st);
+    // TF32: B is passed transposed (p x n, row pitch ldb), K-major.
+    if (bn == 256) return launch_cfg<4, 256, 4, 1>(m, n, p, A, lda, B, ldb, C, s, st);
+    if (bn == 128) return launch_cfg<4, 128, 6, 1>(m, n, p, A, lda, B, ldb, C, s, st);
+    return launch_cfg<4, 64, 8, 1>(m, n, p, A, lda, B, ldb, C, s, st);
 }
 
 }  // namespace moa

@@ -17,6 +17,11 @@ void set_error(const std::string& msg);
 int fail(int status, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 
+// Optional per-thread profiling events (moa_profile_events): recorded on the
+// call's stream immediately before and after the main GEMM kernel.
+void prof_begin(cudaStream_t s);
+void prof_end(cudaStream_t s);
+
 // Per-device status word (device address), created on first use.
 int* device_status_ptr();
 uint64_t wait_limit_ns();
@@ -34,8 +39,9 @@ int make_tmap_3d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uin
                  uint32_t box_inner, uint32_t box_outer);
 
 // ------------------------------------------------------------------ kernels
-// Dense tcgen05 GEMM, A (m x n, row pitch lda elements), B (n x p, pitch ldb),
-// C (m x p, FP32, pitch p).  in_bf16: operands are BF16, else FP32 (TF32 MMA).
+// Dense tcgen05 GEMM, A (m x n, row pitch lda elements), C (m x p, FP32,
+// pitch p).  in_bf16: BF16 operands, B given as n x p (pitch ldb).  Else FP32
+// operands on the TF32 kind, B given TRANSPOSED as p x n (pitch ldb).
 struct TileChoice {
     int block_n;     // 64, 128 or 256
 };
@@ -47,6 +53,11 @@ int simt_f64_launch(int64_t m, int64_t n, int64_t p, const double* A, const doub
                     cudaStream_t s);
 int simt_f32_launch(int64_t m, int64_t n, int64_t p, const float* A, const float* B, float* C,
                     cudaStream_t s);
+
+// Bt (cols x ld, row-major) := transpose of X (rows x cols), zero-filling
+// Bt[:, rows:ld].  FP32.
+int transpose_pad_launch(const float* X, int64_t rows, int64_t cols, float* Xt, int64_t ld,
+                         cudaStream_t s);
 
 // Copy a rows x cols row-major matrix into a buffer with row pitch ld >= cols
 // (elements), zero-filling the padding columns.

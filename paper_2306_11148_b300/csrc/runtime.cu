@@ -25,6 +25,8 @@ constexpr int kMaxDevices = 64;
 int* g_status[kMaxDevices] = {nullptr};
 int g_sms[kMaxDevices] = {0};
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+thread_local cudaEvent_t g_prof_start = nullptr;
+thread_local cudaEvent_t g_prof_stop = nullptr;
 
 int current_device() {
     int d = 0;
@@ -38,6 +40,13 @@ int current_device() {
 __device__ int g_moa_device_status;
 
 void set_error(const std::string& msg) { g_last_error = msg; }
+
+void prof_begin(cudaStream_t s) {
+    if (g_prof_start) cudaEventRecord(g_prof_start, s);
+}
+void prof_end(cudaStream_t s) {
+    if (g_prof_stop) cudaEventRecord(g_prof_stop, s);
+}
 
 int fail(int status, const std::string& msg) {
     g_last_error = msg;
@@ -187,6 +196,82 @@ int pad_copy_launch(const void* src, void* dst, int64_t rows, int64_t cols, int6
     return MOA_OK;
 }
 
+// ------------------------------------------------------------------ transpose
+namespace {
+// 64 x 64 tiles through shared memory, 256 threads.  Reads rows of X and
+// writes rows of Xt, 16 bytes per access when both pitches allow it.
+template <bool VEC>
+__global__ void __launch_bounds__(256)
+    transpose_pad_kernel(const float* __restrict__ X, int64_t rows, int64_t cols,
+                         float* __restrict__ Xt, int64_t ld) {
+    __shared__ float tile[64][65];
+    const int64_t c0 = static_cast<int64_t>(blockIdx.x) * 64;   // column block of X
+    const int64_t r0 = static_cast<int64_t>(blockIdx.y) * 64;   // row block of X (< ld)
+    const int t = threadIdx.x;
+    if (VEC) {
+        // 64 rows x 16 float4: thread t loads rows (t / 16) + 16 q, float4 (t % 16)
+        const int cv = (t & 15) * 4;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int rr = (t >> 4) + 16 * q;
+            const int64_t r = r0 + rr, c = c0 + cv;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r < rows && c + 3 < cols) {
+                v = *reinterpret_cast<const float4*>(X + r * cols + c);
+            } else if (r < rows) {
+                if (c < cols) v.x = X[r * cols + c];
+                if (c + 1 < cols) v.y = X[r * cols + c + 1];
+                if (c + 2 < cols) v.z = X[r * cols + c + 2];
+            }
+            tile[rr][cv] = v.x;
+            tile[rr][cv + 1] = v.y;
+            tile[rr][cv + 2] = v.z;
+            tile[rr][cv + 3] = v.w;
+        }
+        __syncthreads();
+        // Xt rows c0 .. c0+63, each 64 values r0 .. r0+63 as 16 float4
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int cc = (t >> 4) + 16 * q;
+            const int rv = (t & 15) * 4;
+            const int64_t c = c0 + cc, r = r0 + rv;
+            if (c >= cols || r >= ld) continue;
+            const float4 v = make_float4(tile[rv][cc], tile[rv + 1][cc], tile[rv + 2][cc],
+                                         tile[rv + 3][cc]);
+            *reinterpret_cast<float4*>(Xt + c * ld + r) = v;   // ld % 4 == 0, r % 4 == 0
+        }
+    } else {
+        for (int e = t; e < 64 * 64; e += 256) {
+            const int rr = e >> 6, cc = e & 63;
+            const int64_t r = r0 + rr, c = c0 + cc;
+            tile[rr][cc] = (r < rows && c < cols) ? X[r * cols + c] : 0.f;
+        }
+        __syncthreads();
+        for (int e = t; e < 64 * 64; e += 256) {
+            const int cc = e >> 6, rr = e & 63;
+            const int64_t c = c0 + cc, r = r0 + rr;
+            if (c < cols && r < ld) Xt[c * ld + r] = tile[rr][cc];
+        }
+    }
+}
+}  // namespace
+
+int transpose_pad_launch(const float* X, int64_t rows, int64_t cols, float* Xt, int64_t ld,
+                         cudaStream_t s) {
+    const int64_t gx = ceil_div(cols, 64), gy = ceil_div(ld, 64);
+    if (gy > 65535) return fail(MOA_ERR_ARG, "transpose: too many rows");
+    dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>(gy));
+    const bool vec = (cols % 4 == 0) && (ld % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0) &&
+                     (reinterpret_cast<uintptr_t>(Xt) % 16 == 0);
+    if (vec)
+        transpose_pad_kernel<true><<<grid, 256, 0, s>>>(X, rows, cols, Xt, ld);
+    else
+        transpose_pad_kernel<false><<<grid, 256, 0, s>>>(X, rows, cols, Xt, ld);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "transpose_pad_kernel launch");
+    return MOA_OK;
+}
+
 }  // namespace moa
 
 // ------------------------------------------------------------------ public housekeeping
@@ -202,6 +287,12 @@ uint64_t moa_set_wait_limit_ns(uint64_t ns) {
 }
 
 const char* moa_version(void) { return "moa-b300 0.1.0 (sm_103a)"; }
+
+int moa_profile_events(void* start_event, void* stop_event) {
+    moa::g_prof_start = static_cast<cudaEvent_t>(start_event);
+    moa::g_prof_stop = static_cast<cudaEvent_t>(stop_event);
+    return MOA_OK;
+}
 
 int moa_sync_status(void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -31,6 +31,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 
 #include "internal.h"
 #include "ptx.cuh"
@@ -602,6 +603,16 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
 }  // namespace
 
 // ====================================================================== host side
+static int f32_split_chunk_kb() {
+    static int kb = 0;
+    if (kb == 0) {
+        const char* env = std::getenv("MOA_F32_SPLIT_CHUNK_K");
+        const long k = env ? std::strtol(env, nullptr, 10) : 256;
+        kb = static_cast<int>(std::max<long>(1, (k + kBK - 1) / kBK));
+    }
+    return kb;
+}
+
 int split_slices(moa_dtype dt, int slices) {
     if (dt == MOA_F32_SPLIT) return (slices == 0 || slices == 3) ? 3 : -1;
     if (slices == 0) return kDefaultSlices;
@@ -649,8 +660,10 @@ static int launch_split_gemm(const SplitArgs& a, const CUtensorMap& tmA, const C
     }
     const long tiles = static_cast<long>(a.tiles_m) * a.tiles_n;
     const int grid = static_cast<int>(std::min<long>(tiles, num_sms()));
+    prof_begin(s);
     split_gemm_kernel<<<grid, kSplitThreads, kSplitSmem, s>>>(tmA, tmB, a);
     cudaError_t e = cudaGetLastError();
+    prof_end(s);
     if (e != cudaSuccess) return cuda_fail(e, "split_gemm_kernel launch");
     if (st) {
         st->block_m = kBM;
@@ -698,7 +711,10 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
         kernels += 2;
         a.f64 = 0;
         a.levels = 1;
-        a.kc[0] = 16;   // flush the FP32 accumulator every 1024 k
+        // Flush the FP32 TMEM accumulator into the epilogue's FP32 running sum
+        // every kc K blocks: shorter chunks bound the accumulation error of
+        // the tensor core's FP32 adds (MOA_F32_SPLIT_CHUNK_K, default 256).
+        a.kc[0] = f32_split_chunk_kb();
         a.drop = 0;
     } else {
         int* eA = reinterpret_cast<int*>(base + L.ea_off);

@@ -88,6 +88,7 @@ EXPORTS = {
     "moa_last_error": (ctypes.c_char_p, []),
     "moa_set_wait_limit_ns": (ctypes.c_uint64, [ctypes.c_uint64]),
     "moa_version": (ctypes.c_char_p, []),
+    "moa_profile_events": (ctypes.c_int, [_vp, _vp]),
     "moa_shutdown": (None, []),
 }
 

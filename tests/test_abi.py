@@ -84,6 +84,8 @@ def test_missing_workspace_rejected(L):
 def test_workspace_sizes(L):
     # aligned dense shapes need none; split modes hold S slice planes
     assert moa.moa_gemm_workspace_size(256, 256, 256, moa.MOA_BF16, 0) == 0
+    # TF32 stages B transposed (K-major) in the workspace
+    assert moa.moa_gemm_workspace_size(256, 256, 256, moa.MOA_F32_TF32, 0) == 256 * 256 * 4
     assert moa.moa_gemm_workspace_size(256, 256, 256, moa.MOA_F64, 0) == 0
     s3 = moa.moa_gemm_workspace_size(256, 256, 256, moa.MOA_F32_SPLIT, 0)
     assert s3 >= 3 * 2 * (256 * 256 * 2)
