@@ -84,6 +84,7 @@ EXPORTS = {
     "moa_gemm_grouped_workspace_size": (_sz, [ctypes.c_int, ctypes.POINTER(moa_gemm_desc)]),
     "moa_gemm_grouped": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(moa_gemm_desc), _vp, _sz,
                                         _vp]),
+    "moa_gemm_f32split_noalloc": (ctypes.c_int, [_i64, _i64, _i64, _vp, _vp, _vp, _vp]),
     "moa_sync_status": (ctypes.c_int, [_vp]),
     "moa_last_error": (ctypes.c_char_p, []),
     "moa_set_wait_limit_ns": (ctypes.c_uint64, [ctypes.c_uint64]),
