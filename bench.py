@@ -123,45 +123,98 @@ def gpu_identity(dev):
     return pci, uuid
 
 
+class _NvmlCtypes:
+    """Minimal ctypes view of libnvidia-ml (used when the pynvml module is absent)."""
+
+    def __init__(self):
+        import ctypes
+        self.c = ctypes
+        self.L = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.L.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit_v2 failed")
+
+    def by_pci(self, pci):
+        h = self.c.c_void_p()
+        rc = self.L.nvmlDeviceGetHandleByPciBusId_v2(pci.encode(), self.c.byref(h))
+        if rc != 0:
+            raise RuntimeError(f"nvmlDeviceGetHandleByPciBusId_v2 rc={rc}")
+        return h
+
+    def by_index(self, i):
+        h = self.c.c_void_p()
+        rc = self.L.nvmlDeviceGetHandleByIndex_v2(i, self.c.byref(h))
+        if rc != 0:
+            raise RuntimeError(f"nvmlDeviceGetHandleByIndex_v2 rc={rc}")
+        return h
+
+    def count(self):
+        n = self.c.c_uint()
+        self.L.nvmlDeviceGetCount_v2(self.c.byref(n))
+        return n.value
+
+    def energy_mj(self, h):
+        v = self.c.c_ulonglong()
+        rc = self.L.nvmlDeviceGetTotalEnergyConsumption(h, self.c.byref(v))
+        if rc != 0:
+            raise RuntimeError(f"nvmlDeviceGetTotalEnergyConsumption rc={rc}")
+        return v.value
+
+
 class Energy:
     """NVML total-energy counter (mJ) of the device, found by PCI bus id, then
-    by UUID, then as the only visible device."""
+    by UUID, then as the only visible device (pynvml, else libnvidia-ml via
+    ctypes)."""
 
     def __init__(self, pci, uuid=None):
         self.h = None
         self.why = None
+        self.read = None
+        errs = []
         try:
             import pynvml
             pynvml.nvmlInit()
-            self.nv = pynvml
+            tries = []
+            if pci:
+                tries += [lambda: pynvml.nvmlDeviceGetHandleByPciBusId(pci)]
+            if uuid:
+                tries += [lambda: pynvml.nvmlDeviceGetHandleByUUID(uuid)]
+            tries += [lambda: pynvml.nvmlDeviceGetHandleByIndex(0)
+                      if pynvml.nvmlDeviceGetCount() == 1 else None]
+            for t in tries:
+                try:
+                    h = t()
+                    if h is not None:
+                        pynvml.nvmlDeviceGetTotalEnergyConsumption(h)
+                        self.h = h
+                        self.read = lambda: pynvml.nvmlDeviceGetTotalEnergyConsumption(self.h)
+                        return
+                except Exception as e:
+                    errs.append(str(e))
         except Exception as e:
-            self.why = f"nvmlInit: {e}"
-            return
-        tries = []
-        if pci:
-            tries += [lambda: pynvml.nvmlDeviceGetHandleByPciBusId(pci),
-                      lambda: pynvml.nvmlDeviceGetHandleByPciBusId(pci.encode())]
-        if uuid:
-            tries += [lambda: pynvml.nvmlDeviceGetHandleByUUID(uuid)]
-        tries += [lambda: pynvml.nvmlDeviceGetHandleByIndex(0)
-                  if pynvml.nvmlDeviceGetCount() == 1 else None]
-        errs = []
-        for t in tries:
-            try:
-                h = t()
-                if h is not None:
-                    pynvml.nvmlDeviceGetTotalEnergyConsumption(h)
-                    self.h = h
-                    return
-            except Exception as e:
-                errs.append(str(e))
+            errs.append(f"pynvml: {e}")
+        try:
+            nv = _NvmlCtypes()
+            tries = ([lambda: nv.by_pci(pci)] if pci else []) + \
+                [lambda: nv.by_index(0) if nv.count() == 1 else None]
+            for t in tries:
+                try:
+                    h = t()
+                    if h is not None:
+                        nv.energy_mj(h)
+                        self.h = h
+                        self.read = lambda: nv.energy_mj(self.h)
+                        return
+                except Exception as e:
+                    errs.append(str(e))
+        except Exception as e:
+            errs.append(f"libnvidia-ml: {e}")
         self.why = "; ".join(errs) or "no handle"
 
     def read_j(self):
         if self.h is None:
             return None
         try:
-            return self.nv.nvmlDeviceGetTotalEnergyConsumption(self.h) / 1000.0
+            return self.read() / 1000.0
         except Exception:
             return None
 
@@ -197,7 +250,8 @@ def max_over_ranks(x, ws):
 
 # ------------------------------------------------------------------ workloads
 MODE_OF = {"square": "tf32", "bf16": "bf16", "split_f32": "f32_split",
-           "split_f64": "f64_split_f32in", "f64": "f64", "simt": "f32_simt"}
+           "split_f64": "f64_split_f32in", "f64": "f64", "simt": "f32_simt",
+           "grouped": "grouped"}
 
 
 def make_inputs(mode, N):
@@ -362,6 +416,70 @@ def cpu_baseline(N, dtype_name, seconds_target=8.0):
                       f"rows), {dt:.2f} s", "host_cores": cores}
 
 
+def bench_grouped(steps, warmup, ws, stream, count=512):
+    """Grouped batch: `count` BF16 GEMMs (m, n, p log-uniform in [32, 2048],
+    multiples of 16, FP32 out) in one moa_gemm_grouped launch per step, and the
+    same problems as `count` separate moa_gemm_ex launches."""
+    import torch
+    from paper_2306_11148_b300 import inputs, moa
+    shapes = inputs.grouped_shapes(count, seed=0)
+    probs = []
+    flops = 0.0
+    nbytes = 0
+    for i, (m, n, p) in enumerate(shapes):
+        A, B = inputs.uniform_pair(m, n, p, dtype=torch.bfloat16, seed=1000 + i)
+        C = torch.empty((m, p), dtype=torch.float32, device="cuda")
+        probs.append((A.cuda(), B.cuda(), C, moa.MOA_BF16))
+        flops += 2.0 * m * n * p
+        nbytes += 2 * (m * n + n * p) + 4 * m * p
+    descs = moa.make_descs(probs)
+    wspace = moa.Workspace(torch.device("cuda"))
+    L = moa.lib()
+    need = int(L.moa_gemm_grouped_workspace_size(len(probs), descs))
+    wptr, wbytes = wspace.get(need)
+    sh = int(stream.cuda_stream)
+
+    def step():
+        moa.check(L.moa_gemm_grouped(len(probs), descs, wptr, wbytes, sh))
+
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    for a, b in kev:
+        a.record(stream)
+        b.record(stream)
+    idx = [0]
+
+    def step_timed():
+        a, b = kev[idx[0]]
+        L.moa_profile_events(a.cuda_event, b.cuda_event)
+        step()
+        idx[0] += 1
+
+    with torch.cuda.stream(stream):
+        t = time_device(step_timed, steps, warmup, stream, ws, warm_fn=step)
+    L.moa_profile_events(None, None)
+    kernel_s = sum(a.elapsed_time(b) for a, b in kev) / 1000.0
+    moa.check(moa.moa_sync_status(sh))
+
+    sws = moa.Workspace(torch.device("cuda"))
+
+    def separate():
+        for A, B, C, dt in probs:
+            m, n = A.shape
+            p = B.shape[1]
+            w, wb = sws.get(moa.moa_gemm_workspace_size(m, n, p, dt, 0))
+            moa.check(moa.moa_gemm_ex(m, n, p, dt, A.data_ptr(), B.data_ptr(), C.data_ptr(), 0,
+                                      w, wb, sh, None))
+
+    nsep = max(2, steps // 2)
+    with torch.cuda.stream(stream):
+        t_sep = time_device(separate, nsep, 2, stream, ws)
+    return {"seconds": t, "kernel_seconds": kernel_s, "steps": steps, "flops_per_step": flops,
+            "bytes_per_step": nbytes, "count": count,
+            "separate_seconds_per_step": t_sep / nsep, "kernels_per_step": 1,
+            "products": 1, "tile": [128, 0, 64]}
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args, ws, rank):
     if rank != 0:
@@ -429,9 +547,12 @@ def main():
 
     clocks = ClockSampler(pci)
     clocks.start()
-    main_res = bench_mode(mode, N, args.steps, args.warmup, ws, stream,
-                          want_energy=not args.profile, energy=energy, want_e2e=not args.profile,
-                          check_rows=not args.profile)
+    if mode == "grouped":
+        main_res = bench_grouped(args.steps, args.warmup, ws, stream)
+    else:
+        main_res = bench_mode(mode, N, args.steps, args.warmup, ws, stream,
+                              want_energy=not args.profile, energy=energy,
+                              want_e2e=not args.profile, check_rows=not args.profile)
     clk = clocks.stop()
 
     t_max = max_over_ranks(main_res["seconds"], ws)
@@ -443,28 +564,46 @@ def main():
     e2e_t = max_over_ranks(e2e.get("seconds", float("nan")), ws)
     e2e_val = main_res["flops_per_step"] * e2e.get("steps", 1) * ws / e2e_t / 1e12
 
-    # roofline of the dominant kernel (the tensor-core GEMM): algorithmic
-    # flops per launch / average launch duration (one GEMM kernel per step on
-    # aligned shapes; pre-pass kernels of split modes are small HBM passes).
+    # roofline of the dominant kernel: algorithmic flops (or bytes) per launch
+    # / that kernel's own CUDA-event duration, recorded by the library on the
+    # launching stream.
     kdtype = {"tf32": "tf32", "bf16": "bf16", "f32_split": "bf16",
-              "f64_split_f32in": "bf16"}.get(mode)
-    if kdtype:
+              "f64_split_f32in": "bf16", "grouped": "bf16"}.get(mode)
+    kernel_ms = main_res["kernel_seconds"] / args.steps * 1e3
+    if mode == "grouped":
+        # mixed: small problems are HBM-bound, large ones tensor-bound; the
+        # bound of the batch is max(flops / tensor peak, bytes / HBM peak)
+        peak_t = peaks["bf16_tflops"]
+        t_tensor = main_res["flops_per_step"] / (peak_t * 1e12)
+        t_hbm = main_res["bytes_per_step"] / (peaks["hbm_gbs"] * 1e9)
+        if t_tensor >= t_hbm:
+            achieved = main_res["flops_per_step"] / (kernel_ms / 1e3) / 1e12
+            roof = {"bound": "tensor", "achieved": achieved, "peak": peak_t, "unit": "TFLOP/s",
+                    "frac": achieved / peak_t}
+        else:
+            achieved = main_res["bytes_per_step"] / (kernel_ms / 1e3) / 1e9
+            roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"]}
+        roof.update({"traffic": TRAFFIC.get((mode, N)), "kernel_ms": kernel_ms,
+                     "kernel": "grouped_tc_kernel",
+                     "bound_times_ms": {"tensor": t_tensor * 1e3, "hbm": t_hbm * 1e3},
+                     "peak_source": peaks["source"]})
+    elif kdtype:
         peak = peaks["bf16_tflops"] * NOMINAL_RATIO[kdtype]
-        # tensor work per launch = products x 2N^3 (one slice product per
-        # product for split modes); duration = main kernel's CUDA-event time
+        # tensor work per launch = products x 2N^3 (one per slice product)
         achieved = main_res["flops_per_step"] * max(1, main_res["products"]) / \
-            (main_res["kernel_seconds"] / args.steps) / 1e12
+            (kernel_ms / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": TRAFFIC.get((mode, N)),
-                "kernel_ms": main_res["kernel_seconds"] / args.steps * 1e3,
+                "kernel_ms": kernel_ms,
                 "peak_source": f"{peaks['source']} bf16 x nominal {kdtype}/bf16 ratio",
                 "kernel": "dense_tc_kernel" if mode in ("tf32", "bf16") else "split_gemm_kernel"}
     else:
         roof = {"bound": "alu", "achieved": value / ws, "peak": None, "unit": "TFLOP/s",
-                "frac": None, "traffic": None}
+                "frac": None, "traffic": None, "kernel_ms": kernel_ms}
 
     modes = {}
-    if not args.no_extras and rank == 0 and ws == 1:
+    if not args.no_extras and rank == 0 and ws == 1 and mode != "grouped":
         for m2, n2 in [("bf16", N), ("f32_split", N), ("f64_split_f32in", N), ("f32_simt", N // 2),
                        ("f64", N // 4)]:
             if m2 == mode:
@@ -477,23 +616,36 @@ def main():
                 modes[m2] = {"error": str(e)}
 
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu:
+    if rank == 0 and ws == 1 and not args.no_cpu and mode != "grouped":
         cpu = cpu_baseline(N, "f32")
 
     if rank == 0:
+        if mode == "grouped":
+            metric = "GEMM TFLOP/s (512 grouped BF16 GEMMs, one persistent launch)"
+            config = {"workload": "512 ONF GEMMs, m,n,p log-uniform in [32,2048] rounded to 16, "
+                                  "BF16 in (uniform[-1,1) seeds 1000+i), FP32 out, one "
+                                  "moa_gemm_grouped launch per step",
+                      "count": main_res["count"], "parallelism": f"replicas x{ws}",
+                      "l2": "operands ~0.96 GB per step, larger than L2",
+                      "separate_launches_ms": main_res["separate_seconds_per_step"] * 1e3,
+                      "separate_tflops": main_res["flops_per_step"] /
+                      main_res["separate_seconds_per_step"] / 1e12}
+        else:
+            metric = "GEMM TFLOP/s (FP32 ONF GEMM, TF32 tensor path)" if mode == "tf32" else \
+                f"GEMM TFLOP/s (ONF GEMM, {mode} path)"
+            config = {"workload": f"square ONF GEMM m=n=p={N}, row-major, seed 0, mode {mode}",
+                      "N": N, "mode": mode, "parallelism": f"replicas x{ws}",
+                      "l2": "inputs larger than L2 (3 x N^2 elements)"}
         line = {
-            "metric": "GEMM TFLOP/s (FP32 ONF GEMM, TF32 tensor path)",
+            "metric": metric,
             "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"tf32": "tf32", "bf16": "bf16", "f32_split": "bf16x6",
                       "f64_split_f32in": "bf16-digits", "f64": "f64",
-                      "f32_simt": "f32"}[mode],
+                      "f32_simt": "f32", "grouped": "bf16"}[mode],
             "data": "synthetic",
-            "config": {"workload": f"square ONF GEMM m=n=p={N}, FP32 row-major "
-                                   f"uniform[-1,1) seed 0, mode {mode}",
-                       "N": N, "mode": mode, "parallelism": f"replicas x{ws}",
-                       "l2": "inputs larger than L2 (3 x N^2 x 4 B)"},
+            "config": config,
             "rel_err_sampled_rows": main_res.get("rel_err_sampled_rows"),
             "roofline": roof,
             "cpu_baseline": cpu,

@@ -109,14 +109,27 @@ int moa_gemm_ex(int64_t m, int64_t n, int64_t p, moa_dtype dt,
 
 typedef struct {
     int64_t m, n, p;
-    moa_dtype dt;             /* MOA_BF16 or MOA_F32_TF32; all descriptors of one call share it */
+    moa_dtype dt;             /* any mode; BF16 problems take the persistent path */
     const void* A;
     const void* B;
     void* C;
 } moa_gemm_desc;
 
+/* Workspace bytes for moa_gemm_grouped with these descriptors (device tables
+ * of the persistent launch, plus scratch for problems it does not take). */
 size_t moa_gemm_grouped_workspace_size(int count, const moa_gemm_desc* descs);
 
+/* Every C_g := A_g . B_g of `descs` (Eq. eq:dnf per problem) on `stream`.
+ * BF16 problems with 16-byte row pitches and 16-byte aligned A, B run in ONE
+ * persistent tcgen05 launch: each problem gets a tile width from a shape cost
+ * model, all output tiles are dealt to the SMs longest-first, and per-problem
+ * TMA descriptors live in `ws`.  Other problems (other dtypes, unaligned
+ * pitches) run one by one on the same stream.  A call that repeats the
+ * previous call of the same thread (identical descriptors, same `ws`, same
+ * device) reuses the tables already in `ws`, so callers must not modify `ws`
+ * between such calls.  Host-side tables are staged in pinned host memory
+ * owned by the library (per thread).  Errors: MOA_ERR_ARG / MOA_ERR_DTYPE for a
+ * bad descriptor (nothing launched), MOA_ERR_WORKSPACE if ws is too small. */
 int moa_gemm_grouped(int count, const moa_gemm_desc* descs,
                      void* ws, size_t ws_bytes, void* stream);
 

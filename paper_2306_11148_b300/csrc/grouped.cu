@@ -1,38 +1,554 @@
 // grouped.cu -- moa_gemm_grouped: `count` independent ONF GEMMs of arbitrary
-// shapes (Eq. (eq:dnf) per problem).  This first version validates every
-// descriptor and issues the problems one after another on the stream.
+// shapes (Eq. (eq:dnf) per problem) in ONE persistent tcgen05 launch.
+//
+// Batching pattern: every problem g gets its own tile width BN_g in {64, 128,
+// 256} from a shape-driven cost model (the paper's block sizes chosen from
+// "the static information of types and shapes", Sec. 3.4).  Its output tiles
+// (128 x BN_g) enter one work list; the host deals the list to the persistent
+// CTAs longest-processing-time first (each tile to the least-loaded CTA), so
+// heavy-tailed size mixes stay balanced.  Per-problem TMA descriptors live in
+// the workspace (global memory); the MMA N extent is a runtime field of the
+// instruction descriptor, so one kernel binary serves every tile width.
+//
+// The persistent path takes BF16 problems whose rows are 16-byte multiples
+// (n % 8 == 0, p % 8 == 0) and 16-byte aligned A and B.  Other problems of the
+// call (other dtypes, unaligned pitches) are issued one by one through the
+// single-GEMM path on the same stream, with the workspace tail as scratch.
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <queue>
+#include <vector>
+
 #include "internal.h"
+#include "ptx.cuh"
 
 namespace moa {
 int gemm_ex(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const void* B, void* C,
             int slices, void* ws, size_t ws_bytes, cudaStream_t s, moa_stats* st);
 size_t workspace_bytes(int64_t m, int64_t n, int64_t p, moa_dtype dt, int slices);
+
+namespace {
+
+constexpr int kGBM = 128, kGBK = 64, kGStages = 4;
+constexpr int kGABytes = kGBM * 128;                    // 128 rows x 64 BF16
+constexpr int kGBChunk = kGBK * 128;                    // 64 rows x 64 BF16 columns
+constexpr int kGStageBytes = kGABytes + 4 * kGBChunk;   // room for BN = 256
+constexpr int kGSmem = 1024 + kGStages * kGStageBytes + 256;
+
+struct GroupDev {
+    float* C;
+    int m, n, p;
+    int bn;        // tile width: 64, 128 or 256
+    int tiles_n;
+    int num_kb;
+    int vec_ok;
+    int pad;
+};
+
+struct GroupedArgs {
+    const CUtensorMap* maps;   // 2 per problem: A, B (64-byte aligned, global memory)
+    const GroupDev* groups;
+    const int4* tiles;         // (group, tm, tn, 0) per tile, grouped by CTA
+    const int* cta_begin;      // grid + 1 offsets into tiles
+    uint64_t wait_limit_ns;
+    int* status;
+};
+
+__global__ void __launch_bounds__(192, 1) grouped_tc_kernel(const GroupedArgs args) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                               ~static_cast<uintptr_t>(1023));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kGStages * kGStageBytes);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + kGStages;
+    uint64_t* tfull = bars + 2 * kGStages;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* drain = tempty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    CtaCtl* ctl = reinterpret_cast<CtaCtl*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const uint64_t limit = args.wait_limit_ns;
+    int* status = args.status;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kGStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], 4);
+        }
+        mbar_init(drain, 1);
+        ctl->abort = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const int t0 = args.cta_begin[blockIdx.x];
+    const int t1 = args.cta_begin[blockIdx.x + 1];
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer
+            int stage = 0;
+            uint32_t phase = 0;
+            long issued = 0;
+            bool ok = true;
+            for (int t = t0; t < t1 && ok; ++t) {
+                const int4 tl = args.tiles[t];
+                const GroupDev g = args.groups[tl.x];
+                const CUtensorMap* mA = args.maps + 2 * tl.x;
+                const CUtensorMap* mB = mA + 1;
+                const uint32_t bytes = kGABytes + static_cast<uint32_t>(g.bn) * kGBK * 2;
+                for (int kb = 0; kb < g.num_kb; ++kb) {
+                    if (!mbar_wait(&empty[stage], phase ^ 1u, ctl, limit, status)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* sa = smem + stage * kGStageBytes;
+                    mbar_arrive_expect_tx(&full[stage], bytes);
+                    tma_load_2d(sa, mA, &full[stage], kb * kGBK, tl.y * kGBM);
+                    for (int c = 0; c < g.bn / 64; ++c)
+                        tma_load_2d(sa + kGABytes + c * kGBChunk, mB, &full[stage],
+                                    tl.z * g.bn + c * 64, kb * kGBK);
+                    ++issued;
+                    if (++stage == kGStages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                // Let the loads already in flight land before the CTA exits.
+                CtaCtl local{0};
+                const long outstanding = issued < kGStages ? issued : kGStages;
+                for (long q = 1; q <= outstanding; ++q) {
+                    const long idx = issued - q;
+                    mbar_wait(&full[idx % kGStages], static_cast<uint32_t>((idx / kGStages) & 1),
+                              &local, limit, status);
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer, runtime N per tile
+            int stage = 0;
+            uint32_t phase = 0;
+            int local_t = 0;
+            bool ok = true;
+            for (int t = t0; t < t1 && ok; ++t, ++local_t) {
+                const int4 tl = args.tiles[t];
+                const int bn = args.groups[tl.x].bn;
+                const int num_kb = args.groups[tl.x].num_kb;
+                const uint32_t idesc = make_idesc(1u, kGBM, static_cast<uint32_t>(bn), 0u, 1u);
+                const int acc = local_t & 1;
+                const uint32_t acc_phase = static_cast<uint32_t>(local_t >> 1) & 1u;
+                if (!mbar_wait(&tempty[acc], acc_phase ^ 1u, ctl, limit, status)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem_base + static_cast<uint32_t>(acc * 256);
+                for (int kb = 0; kb < num_kb; ++kb) {
+                    if (!mbar_wait(&full[stage], phase, ctl, limit, status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    uint8_t* sa = smem + stage * kGStageBytes;
+                    const uint64_t adesc = smem_desc_sw128(smem_u32(sa), 16, 1024);
+                    const uint64_t bdesc = smem_desc_sw128(smem_u32(sa + kGABytes), kGBChunk, 1024);
+#pragma unroll
+                    for (int k = 0; k < kGBK / 16; ++k)
+                        mma_f16(d, adesc + static_cast<uint64_t>((k * 32) >> 4),
+                                bdesc + static_cast<uint64_t>((k * 16 * 128) >> 4), idesc,
+                                (kb | k) != 0);
+                    mma_commit(&empty[stage]);
+                    if (++stage == kGStages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(&tfull[acc]);
+            }
+            // Every MMA issued above must finish before TMEM is released.
+            mma_commit(drain);
+            CtaCtl local{0};
+            mbar_wait(drain, 0, &local, limit, status);
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue: warps 2..5, TMEM lane quadrant = warp % 4
+        const int q = warp & 3;
+        int local_t = 0;
+        for (int t = t0; t < t1; ++t, ++local_t) {
+            const int acc = local_t & 1;
+            const uint32_t acc_phase = static_cast<uint32_t>(local_t >> 1) & 1u;
+            bool ok = mbar_wait(&tfull[acc], acc_phase, ctl, limit, status);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            tc_fence_after();
+            const int4 tl = args.tiles[t];
+            const GroupDev g = args.groups[tl.x];
+            const int64_t row = static_cast<int64_t>(tl.y) * kGBM + q * 32 + lane;
+            const bool row_ok = row < g.m;
+            float* crow = g.C + row * g.p;
+            for (int c = 0; c < g.bn / 32; ++c) {
+                uint32_t r[32];
+                tmem_ld32(tmem_base + (static_cast<uint32_t>(q * 32) << 16) +
+                              static_cast<uint32_t>(acc * 256 + c * 32),
+                          r);
+                tmem_ld_wait();
+                const int64_t col0 = static_cast<int64_t>(tl.z) * g.bn + c * 32;
+                if (row_ok) {
+                    if (g.vec_ok && col0 + 32 <= g.p) {
+                        float4* dst = reinterpret_cast<float4*>(crow + col0);
+#pragma unroll
+                        for (int v = 0; v < 8; ++v)
+                            dst[v] = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
+                                                 __uint_as_float(r[4 * v + 2]),
+                                                 __uint_as_float(r[4 * v + 3]));
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < 32; ++v)
+                            if (col0 + v < g.p) crow[col0 + v] = __uint_as_float(r[v]);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[acc]);
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, 512);
+    }
+}
+
+// ------------------------------------------------------------------ planning
+// Cost of one output tile in units of "one K block of a 128 x 256 tile at full
+// tensor rate": MMA work bn/256 per K block, divided by the width's MMA
+// efficiency (narrow tiles re-read A from shared memory for fewer columns and
+// are shared-memory bound), plus a fixed share per tile for the TMEM drain,
+// the stores and the pipeline fill.
+constexpr double kTileOverheadKb = 3.0;
+
+double mma_eff(int bn) { return bn >= 256 ? 1.0 : (bn >= 128 ? 0.9 : 0.67); }
+
+double tile_cost(int64_t n, int bn) {
+    return static_cast<double>(ceil_div(n, kGBK)) * (bn / 256.0) / mma_eff(bn) + kTileOverheadKb;
+}
+
+bool persistent_ok(const moa_gemm_desc& d) {
+    return d.dt == MOA_BF16 && d.m > 0 && d.p > 0 && d.n > 0 && d.n % 8 == 0 && d.p % 8 == 0 &&
+           reinterpret_cast<uintptr_t>(d.A) % 16 == 0 && reinterpret_cast<uintptr_t>(d.B) % 16 == 0 &&
+           reinterpret_cast<uintptr_t>(d.C) % 4 == 0 && d.m < (int64_t(1) << 31) &&
+           d.n < (int64_t(1) << 31) && d.p < (int64_t(1) << 31);
+}
+
+// Tile width of one problem (the block size chosen from the static shapes,
+// Sec. 3.4): the width with the least total tile cost.  The balance of all
+// tiles over the SMs is left to the LPT dealing of the work list.
+int plan_bn(const moa_gemm_desc& d) {
+    const int64_t tiles_m = ceil_div(d.m, kGBM);
+    int best = 256;
+    double best_cost = 1e300;
+    for (int bn : {256, 128, 64}) {
+        const double cost = static_cast<double>(tiles_m * ceil_div(d.p, bn)) * tile_cost(d.n, bn);
+        if (cost < best_cost * 0.999) {
+            best_cost = cost;
+            best = bn;
+        }
+    }
+    return best;
+}
+
+struct Layout {
+    size_t maps_off, groups_off, tiles_off, begin_off, total;
+};
+
+Layout layout_for(int G, long T, int grid) {
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    Layout L{};
+    size_t off = 0;
+    L.maps_off = off;
+    off += al(static_cast<size_t>(2) * G * sizeof(CUtensorMap));
+    L.groups_off = off;
+    off += al(static_cast<size_t>(G) * sizeof(GroupDev));
+    L.tiles_off = off;
+    off += al(static_cast<size_t>(T) * sizeof(int4));
+    L.begin_off = off;
+    off += al(static_cast<size_t>(grid + 1) * sizeof(int));
+    L.total = off;
+    return L;
+}
+
+// Pinned host staging for the per-call tables: a ring of buffers per thread,
+// each guarded by an event recorded after the copy that reads it, so a call
+// only waits when it laps a copy that has not finished.
+struct Staging {
+    static constexpr int kRing = 4;
+    void* p[kRing] = {nullptr};
+    size_t bytes[kRing] = {0};
+    cudaEvent_t ev[kRing] = {nullptr};
+    int next = 0;
+    ~Staging() {
+        for (int i = 0; i < kRing; ++i) {
+            if (ev[i]) {
+                cudaEventSynchronize(ev[i]);
+                cudaEventDestroy(ev[i]);
+            }
+            if (p[i]) cudaFreeHost(p[i]);
+        }
+    }
+    void* get(size_t n, int* slot) {
+        const int i = next;
+        next = (next + 1) % kRing;
+        if (ev[i]) {
+            cudaEventSynchronize(ev[i]);
+        } else if (cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) != cudaSuccess) {
+            return nullptr;
+        }
+        if (n > bytes[i]) {
+            if (p[i]) cudaFreeHost(p[i]);
+            p[i] = nullptr;
+            bytes[i] = 0;
+            if (cudaHostAlloc(&p[i], n, cudaHostAllocDefault) != cudaSuccess) return nullptr;
+            bytes[i] = n;
+        }
+        *slot = i;
+        return p[i];
+    }
+    void release(int slot, cudaStream_t s) { cudaEventRecord(ev[slot], s); }
+};
+thread_local Staging t_staging;
+
+// The last persistent plan of this thread: when a call repeats it (same
+// descriptors, same workspace, same device) the device tables written by that
+// call are still in the workspace and the launch reuses them.
+struct PlanCache {
+    std::vector<moa_gemm_desc> descs;
+    void* ws = nullptr;
+    int device = -1;
+    int grid = 0;
+    bool valid = false;
+};
+thread_local PlanCache t_plan;
+
+bool same_descs(const std::vector<moa_gemm_desc>& a, int count, const moa_gemm_desc* d) {
+    if (static_cast<int>(a.size()) != count) return false;
+    return std::memcmp(a.data(), d, sizeof(moa_gemm_desc) * count) == 0;
+}
+
+int launch_kernel(uint8_t* dev, const Layout& L, int grid, cudaStream_t s) {
+    GroupedArgs a;
+    a.maps = reinterpret_cast<const CUtensorMap*>(dev + L.maps_off);
+    a.groups = reinterpret_cast<const GroupDev*>(dev + L.groups_off);
+    a.tiles = reinterpret_cast<const int4*>(dev + L.tiles_off);
+    a.cta_begin = reinterpret_cast<const int*>(dev + L.begin_off);
+    a.wait_limit_ns = wait_limit_ns();
+    a.status = device_status_ptr();
+    if (!a.status) return MOA_ERR_CUDA;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(grouped_tc_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(grouped)");
+        attr_set = true;
+    }
+    prof_begin(s);
+    grouped_tc_kernel<<<grid, 192, kGSmem, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    prof_end(s);
+    if (e != cudaSuccess) return cuda_fail(e, "grouped_tc_kernel launch");
+    return MOA_OK;
+}
+
+}  // namespace
+
+int grouped_plan_bn(int64_t m, int64_t n, int64_t p) {
+    moa_gemm_desc d{};
+    d.m = m;
+    d.n = n;
+    d.p = p;
+    d.dt = MOA_BF16;
+    return plan_bn(d);
+}
+
+size_t grouped_workspace(int count, const moa_gemm_desc* d) {
+    int G = 0;
+    long T = 0;
+    size_t side = 0;
+    for (int g = 0; g < count; ++g) {
+        if (persistent_ok(d[g])) {
+            ++G;
+            T += ceil_div(d[g].m, kGBM) * ceil_div(d[g].p, plan_bn(d[g]));
+        } else if (d[g].m >= 0 && d[g].n >= 0 && d[g].p >= 0) {
+            side = std::max(side, workspace_bytes(d[g].m, d[g].n, d[g].p, d[g].dt, 0));
+        }
+    }
+    size_t main = 0;
+    if (G > 0) main = layout_for(G, T, static_cast<int>(std::min<long>(T, num_sms()))).total;
+    return main + side;
+}
+
+int grouped_launch(int count, const moa_gemm_desc* d, void* ws, size_t ws_bytes, cudaStream_t s,
+                   bool allow_cache) {
+    const int sms = num_sms();
+    std::vector<int> idx;
+    std::vector<int> bn;
+    long T = 0;
+    for (int g = 0; g < count; ++g) {
+        const moa_gemm_desc& x = d[g];
+        if (x.dt < MOA_F64 || x.dt > MOA_F64_SPLIT_F64IN)
+            return fail(MOA_ERR_DTYPE, "unknown dtype in descriptor");
+        if (x.m < 0 || x.n < 0 || x.p < 0) return fail(MOA_ERR_ARG, "negative dimension in descriptor");
+        if (x.m > 0 && x.p > 0 && x.C == nullptr) return fail(MOA_ERR_ARG, "descriptor C is NULL");
+        if (x.m > 0 && x.p > 0 && x.n > 0 && (x.A == nullptr || x.B == nullptr))
+            return fail(MOA_ERR_ARG, "descriptor A or B is NULL");
+        if (persistent_ok(x)) {
+            idx.push_back(g);
+            bn.push_back(plan_bn(x));
+            T += ceil_div(x.m, kGBM) * ceil_div(x.p, bn.back());
+        }
+    }
+    const size_t need = grouped_workspace(count, d);
+    if (need > 0 && (ws == nullptr || ws_bytes < need))
+        return fail(MOA_ERR_WORKSPACE, "grouped workspace too small");
+    if (ws && reinterpret_cast<uintptr_t>(ws) % 256)
+        return fail(MOA_ERR_ALIGN, "workspace must be 256-byte aligned");
+    if (T > (1L << 30)) return fail(MOA_ERR_ARG, "too many tiles in one grouped call");
+    size_t main_bytes = 0;
+    int device = -1;
+    cudaGetDevice(&device);
+    if (!idx.empty()) {
+        const int G = static_cast<int>(idx.size());
+        const int grid = static_cast<int>(std::min<long>(T, sms));
+        const Layout L = layout_for(G, T, grid);
+        main_bytes = L.total;
+        uint8_t* dev = static_cast<uint8_t*>(ws);
+        if (allow_cache && t_plan.valid && t_plan.ws == ws && t_plan.device == device &&
+            t_plan.grid == grid && same_descs(t_plan.descs, count, d)) {
+            const int rc = launch_kernel(dev, L, grid, s);
+            if (rc != MOA_OK) return rc;
+        } else {
+            t_plan.valid = false;
+            int slot = 0;
+            uint8_t* host = static_cast<uint8_t*>(t_staging.get(L.total, &slot));
+            if (!host) return fail(MOA_ERR_CUDA, "pinned staging buffer unavailable");
+            CUtensorMap* maps = reinterpret_cast<CUtensorMap*>(host + L.maps_off);
+            GroupDev* groups = reinterpret_cast<GroupDev*>(host + L.groups_off);
+            int4* tiles = reinterpret_cast<int4*>(host + L.tiles_off);
+            int* begin = reinterpret_cast<int*>(host + L.begin_off);
+            struct Tile {
+                double cost;
+                int g, tm, tn;
+            };
+            std::vector<Tile> all;
+            all.reserve(static_cast<size_t>(T));
+            for (int i = 0; i < G; ++i) {
+                const moa_gemm_desc& x = d[idx[i]];
+                GroupDev& gd = groups[i];
+                gd.C = static_cast<float*>(x.C);
+                gd.m = static_cast<int>(x.m);
+                gd.n = static_cast<int>(x.n);
+                gd.p = static_cast<int>(x.p);
+                gd.bn = bn[i];
+                gd.tiles_n = static_cast<int>(ceil_div(x.p, gd.bn));
+                gd.num_kb = static_cast<int>(ceil_div(x.n, kGBK));
+                gd.vec_ok = (x.p % 4 == 0) && (reinterpret_cast<uintptr_t>(x.C) % 16 == 0);
+                gd.pad = 0;
+                int rc = make_tmap_2d(&maps[2 * i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, x.A,
+                                      static_cast<uint64_t>(x.n), static_cast<uint64_t>(x.m),
+                                      static_cast<uint64_t>(x.n) * 2, kGBK, kGBM);
+                if (rc != MOA_OK) return rc;
+                rc = make_tmap_2d(&maps[2 * i + 1], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, x.B,
+                                  static_cast<uint64_t>(x.p), static_cast<uint64_t>(x.n),
+                                  static_cast<uint64_t>(x.p) * 2, 64, kGBK);
+                if (rc != MOA_OK) return rc;
+                const double cost = tile_cost(x.n, gd.bn);
+                const int tm_n = static_cast<int>(ceil_div(x.m, kGBM));
+                for (int tm = 0; tm < tm_n; ++tm)
+                    for (int tn = 0; tn < gd.tiles_n; ++tn) all.push_back({cost, i, tm, tn});
+            }
+            // longest processing time first, each tile onto the least-loaded CTA
+            std::stable_sort(all.begin(), all.end(),
+                             [](const Tile& a, const Tile& b) { return a.cost > b.cost; });
+            using Load = std::pair<double, int>;
+            std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+            for (int c = 0; c < grid; ++c) heap.push({0.0, c});
+            std::vector<std::vector<int>> per_cta(grid);
+            for (size_t t = 0; t < all.size(); ++t) {
+                Load l = heap.top();
+                heap.pop();
+                per_cta[l.second].push_back(static_cast<int>(t));
+                l.first += all[t].cost;
+                heap.push(l);
+            }
+            int pos = 0;
+            for (int c = 0; c < grid; ++c) {
+                begin[c] = pos;
+                for (int t : per_cta[c]) tiles[pos++] = make_int4(all[t].g, all[t].tm, all[t].tn, 0);
+            }
+            begin[grid] = pos;
+            cudaError_t e = cudaMemcpyAsync(dev, host, L.total, cudaMemcpyHostToDevice, s);
+            t_staging.release(slot, s);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(grouped tables)");
+            const int rc = launch_kernel(dev, L, grid, s);
+            if (rc != MOA_OK) return rc;
+            if (allow_cache) {
+                t_plan.descs.assign(d, d + count);
+                t_plan.ws = ws;
+                t_plan.device = device;
+                t_plan.grid = grid;
+                t_plan.valid = true;
+            }
+        }
+    }
+    // problems outside the persistent path, one by one on the same stream
+    uint8_t* side = static_cast<uint8_t*>(ws) + main_bytes;
+    const size_t side_bytes = ws ? ws_bytes - main_bytes : 0;
+    for (int g = 0; g < count; ++g) {
+        if (persistent_ok(d[g])) continue;
+        const int rc = gemm_ex(d[g].m, d[g].n, d[g].p, d[g].dt, d[g].A, d[g].B, d[g].C, 0,
+                               side_bytes ? side : nullptr, side_bytes, s, nullptr);
+        if (rc != MOA_OK) return rc;
+    }
+    return MOA_OK;
+}
+
 }  // namespace moa
 
 extern "C" {
 
 size_t moa_gemm_grouped_workspace_size(int count, const moa_gemm_desc* d) {
     if (count <= 0 || d == nullptr) return 0;
-    size_t mx = 0;
-    for (int g = 0; g < count; ++g) {
-        const size_t w = moa::workspace_bytes(d[g].m, d[g].n, d[g].p, d[g].dt, 0);
-        if (w > mx) mx = w;
-    }
-    return mx;
+    return moa::grouped_workspace(count, d);
 }
 
 int moa_gemm_grouped(int count, const moa_gemm_desc* d, void* ws, size_t ws_bytes, void* stream) {
     if (count < 0) return moa::fail(MOA_ERR_ARG, "negative count");
     if (count == 0) return MOA_OK;
     if (d == nullptr) return moa::fail(MOA_ERR_ARG, "descriptor array is NULL");
-    for (int g = 0; g < count; ++g) {
-        const int rc = moa::gemm_ex(d[g].m, d[g].n, d[g].p, d[g].dt, d[g].A, d[g].B, d[g].C, 0, ws,
-                                    ws_bytes, static_cast<cudaStream_t>(stream), nullptr);
-        if (rc != MOA_OK) return rc;
-    }
-    return MOA_OK;
+    return moa::grouped_launch(count, d, ws, ws_bytes, static_cast<cudaStream_t>(stream), true);
 }
 
 }  // extern "C"

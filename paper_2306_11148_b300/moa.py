@@ -220,3 +220,31 @@ def gemm(A, B, dt: int, C=None, slices: int = 0, stream=None, workspace: Workspa
 
 def sync_status(stream=None):
     check(moa_sync_status(_stream_handle(stream)))
+
+
+def make_descs(problems):
+    """ctypes array of moa_gemm_desc from [(A, B, C, dt), ...] torch tensors."""
+    arr = (moa_gemm_desc * len(problems))()
+    for i, (A, B, C, dt) in enumerate(problems):
+        arr[i].m, arr[i].n = A.shape
+        arr[i].p = B.shape[1]
+        arr[i].dt = dt
+        arr[i].A = _ptr(A)
+        arr[i].B = _ptr(B)
+        arr[i].C = _ptr(C)
+    return arr
+
+
+def gemm_grouped(problems, stream=None, workspace: Workspace | None = None, descs=None):
+    """Every C := A . B of ``problems`` ([(A, B, C, dt), ...]) in one
+    moa_gemm_grouped call.  ``descs`` may pass a prebuilt make_descs() array."""
+    if not problems:
+        return
+    if descs is None:
+        descs = make_descs(problems)
+    dev = problems[0][0].device
+    if workspace is None:
+        workspace = _default_ws.setdefault(dev, Workspace(dev))
+    need = int(lib().moa_gemm_grouped_workspace_size(len(problems), descs))
+    ws, wsb = workspace.get(need)
+    check(lib().moa_gemm_grouped(len(problems), descs, ws, wsb, _stream_handle(stream)))
