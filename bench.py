@@ -251,7 +251,7 @@ def max_over_ranks(x, ws):
 # ------------------------------------------------------------------ workloads
 MODE_OF = {"square": "tf32", "bf16": "bf16", "split_f32": "f32_split",
            "split_f64": "f64_split_f32in", "f64": "f64", "simt": "f32_simt",
-           "grouped": "grouped"}
+           "grouped": "grouped", "serve": "serve"}
 
 
 def make_inputs(mode, N):
@@ -480,6 +480,94 @@ def bench_grouped(steps, warmup, ws, stream, count=512):
             "products": 1, "tile": [128, 0, 64]}
 
 
+def serve_run(srv, pool, arrivals, cring):
+    """Submits `arrivals` [(t, pool index)] at their times; returns the
+    completions and the submit results."""
+    from paper_2306_11148_b300 import moa
+    t0 = time.perf_counter()
+    codes = []
+    ring_pos = {}
+    for t, i in arrivals:
+        delay = t - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        A, B, dt, flops = pool[i]
+        k = ring_pos.get(i, 0)
+        ring_pos[i] = (k + 1) % len(cring[i])
+        rc, tk = srv.submit(A, B, cring[i][k], dt)
+        codes.append((rc, tk, i))
+    submitted = [c for c in codes if c[0] == moa.MOA_OK]
+    got = {}
+    deadline = time.perf_counter() + 120
+    while len(got) < len(submitted) and time.perf_counter() < deadline:
+        for c in srv.poll():
+            got[c[0]] = c
+        time.sleep(0.001)
+    wall = time.perf_counter() - t0
+    return codes, got, wall
+
+
+def bench_serve(rate, seconds, pool_size=64, ring=8, seed=0):
+    """Serving stream: Poisson arrivals of GEMM requests (m, p log-uniform in
+    [64, 4096], n in [64, 8192], multiples of 16), each tagged FP32-accuracy
+    (split BF16) or FP64-accuracy (digit slices) with probability 1/2, FP32
+    N(0,1) operands resident on the device, 64 GB arena.  Operands come from a
+    pool of `pool_size` requests; arrival i uses pool entry i % pool_size and
+    one of `ring` output buffers of that entry."""
+    import numpy as np
+    import torch
+    from paper_2306_11148_b300 import inputs, moa
+    shapes = inputs.serve_arrivals(rate=pool_size / 1.0, seconds=1.0 + 1e-9, seed=seed + 1)
+    shapes = shapes[:pool_size]
+    pool = []
+    cring = []
+    for j, (_, m, n, p, tag) in enumerate(shapes):
+        A, B = inputs.normal_pair(m, n, p, dtype=torch.float32, seed=seed + 100 + j)
+        dt = moa.MOA_F32_SPLIT if tag == "f32" else moa.MOA_F64_SPLIT_F32IN
+        pool.append((A.cuda(), B.cuda(), dt, 2.0 * m * n * p))
+        cring.append([torch.empty((m, p), dtype=moa.out_dtype(dt), device="cuda")
+                      for _ in range(ring)])
+    arr = inputs.serve_arrivals(rate=rate, seconds=seconds, seed=seed)
+    arrivals = [(t, i % len(pool)) for i, (t, *_rest) in enumerate(arr)]
+    srv = moa.Server(arena_bytes=64 << 30, max_inflight=32, n_streams=8,
+                     queue_capacity=pool_size * ring // 2 - 32, queue_deadline_s=2.0)
+    try:
+        codes, got, wall = serve_run(srv, pool, arrivals, cring)
+        st = srv.stats()
+    finally:
+        srv.close()
+    done_ok = [c for c in got.values() if c[1] == moa.MOA_OK]
+    flops = sum(pool[i][3] for rc, tk, i in codes if rc == moa.MOA_OK and tk in got
+                and got[tk][1] == moa.MOA_OK)
+    span = (max(c[4] for c in done_ok) - min(c[2] for c in done_ok)) if done_ok else float("nan")
+    # parity spot check: the last outputs of a few pool entries vs the same GEMM alone
+    torch.cuda.synchronize()
+    mism = 0
+    checked = 0
+    for i in range(0, len(pool), 16):
+        last = None
+        for rc, tk, j in codes:
+            if j == i and rc == moa.MOA_OK and tk in got and got[tk][1] == moa.MOA_OK:
+                last = tk
+        if last is None:
+            continue
+        k = (sum(1 for _, _, j in codes if j == i) - 1) % ring
+        A, B, dt, _ = pool[i]
+        alone = moa.gemm(A, B, dt)
+        torch.cuda.synchronize()
+        checked += 1
+        mism += 0 if torch.equal(alone, cring[i][k]) else 1
+    return {"rate": rate, "seconds": seconds, "offered": len(arrivals),
+            "submitted": st["submitted"], "completed": st["completed"],
+            "rejected": st["rejected"], "busy": sum(1 for c in codes if c[0] == moa.MOA_ERR_BUSY),
+            "failed": st["failed"], "served_per_s": len(done_ok) / span if done_ok else 0.0,
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+            "mean_ms": st["mean_ms"], "batches": st["batches"],
+            "inflight_peak": st["inflight_peak"], "arena_peak_gb": st["arena_peak"] / 1e9,
+            "tflops_served": flops / span / 1e12 if done_ok else 0.0, "wall_s": wall,
+            "alone_vs_mix_checked": checked, "alone_vs_mix_mismatch": mism}
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args, ws, rank):
     if rank != 0:
@@ -513,6 +601,8 @@ def main():
     ap.add_argument("--impl", default="moa", choices=["moa", "reference"])
     ap.add_argument("--workload", default="square", choices=list(MODE_OF))
     ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--no-extras", action="store_true", help="skip the other-mode measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--profile", action="store_true",
@@ -544,6 +634,32 @@ def main():
     stream = torch.cuda.Stream()
     mode = MODE_OF[args.workload]
     N = args.n
+
+    if mode == "serve":
+        clocks = ClockSampler(pci)
+        clocks.start()
+        sat = bench_serve(args.serve_rate, args.serve_seconds)
+        clk = clocks.stop()
+        cap = sat["served_per_s"]
+        light = None
+        if cap > 0 and cap < 0.95 * args.serve_rate:
+            light = bench_serve(0.7 * cap, args.serve_seconds)
+        if rank == 0:
+            line = {"metric": "served GEMM requests/s (continuous batching), p50/p99 latency",
+                    "value": sat["served_per_s"] * ws, "unit": "req/s", "n_gpus": ws,
+                    "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak",
+                    "vs_baseline": None, "dtype": "bf16-slices", "data": "synthetic",
+                    "config": {"workload": f"Poisson arrivals {args.serve_rate}/s for "
+                                           f"{args.serve_seconds} s; m,p logU[64,4096], n "
+                                           "logU[64,8192]; FP32-acc or FP64-acc split requests; "
+                                           "64 GB arena; 32 in flight; 8 streams",
+                               "parallelism": f"replicas x{ws}"},
+                    "saturated": sat, "at_70pct_capacity": light, "clocks": clk}
+            print(json.dumps(line), flush=True)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
 
     clocks = ClockSampler(pci)
     clocks.start()

@@ -134,6 +134,64 @@ int moa_gemm_grouped(int count, const moa_gemm_desc* descs,
                      void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------- */
+/* Serving: a continuous-batching GEMM server (the serving pattern).        */
+/* ---------------------------------------------------------------------- */
+
+typedef struct moa_server moa_server;
+
+typedef struct {
+    void* arena;              /* caller-owned device memory for request workspaces */
+    size_t arena_bytes;       /* the HBM budget: admitted workspaces never exceed it */
+    int max_inflight;         /* most requests on the GPU at once (> 0) */
+    int n_streams;            /* CUDA streams the server launches on (1..64) */
+    int queue_capacity;       /* most queued requests; submit returns MOA_ERR_BUSY beyond (0 = 65536) */
+    double queue_deadline_s;  /* a request queued longer is rejected (0 = never) */
+} moa_serve_config;
+
+typedef struct {
+    uint64_t ticket;
+    int status;               /* MOA_OK, MOA_ERR_REJECTED (deadline) or a launch error */
+    moa_dtype dt;
+    int64_t m, n, p;
+    double t_submit, t_start, t_done;   /* steady-clock seconds */
+} moa_completion;
+
+typedef struct {
+    uint64_t submitted, admitted, completed, rejected, failed, batches;
+    uint64_t queued, inflight;
+    int inflight_peak;
+    size_t arena_peak, arena_used;
+    double p50_ms, p99_ms, max_ms, mean_ms;   /* submit -> done, completed requests */
+} moa_serve_counters;
+
+/* Starts a server on the current device: creates its streams and a scheduler
+ * thread.  The arena (256-byte aligned) stays owned by the caller and must
+ * outlive the server.  MOA_ERR_ARG / MOA_ERR_ALIGN on a bad config. */
+int moa_serve_create(const moa_serve_config* cfg, moa_server** out);
+
+/* Queues C := A . B (any moa_dtype; operands and C are device memory that
+ * stays resident and valid until the ticket completes).  Non-blocking.  A
+ * scheduler thread admits queued requests in FIFO order while fewer than
+ * max_inflight run and the request's workspace fits in the free arena; the
+ * requests admitted in one pass form a batch (its BF16 requests share one
+ * grouped persistent launch) spread over the server's streams, so requests
+ * arriving while others run overlap with them on the device.  Returns MOA_OK
+ * (queued), MOA_ERR_BUDGET (the workspace alone exceeds the arena),
+ * MOA_ERR_BUSY (queue full), MOA_ERR_ARG / MOA_ERR_DTYPE (bad descriptor).
+ * Every queued ticket completes exactly once. */
+int moa_serve_submit(moa_server* s, const moa_gemm_desc* d, uint64_t* ticket);
+
+/* Moves up to `max` completions into `out`; *n_out = how many. */
+int moa_serve_poll(moa_server* s, moa_completion* out, int max, int* n_out);
+
+/* Counters, arena use and latency percentiles of the completed requests. */
+int moa_serve_stats(moa_server* s, moa_serve_counters* out);
+
+/* Stops accepting, drains every queued and in-flight request, joins the
+ * scheduler, destroys the streams and frees the server (not the arena). */
+int moa_serve_destroy(moa_server* s);
+
+/* ---------------------------------------------------------------------- */
 /* Allocation-free variant                                                  */
 /* ---------------------------------------------------------------------- */
 

@@ -62,6 +62,33 @@ class moa_gemm_desc(ctypes.Structure):
                 ("C", ctypes.c_void_p)]
 
 
+class moa_serve_config(ctypes.Structure):
+    _fields_ = [("arena", ctypes.c_void_p), ("arena_bytes", ctypes.c_size_t),
+                ("max_inflight", ctypes.c_int), ("n_streams", ctypes.c_int),
+                ("queue_capacity", ctypes.c_int), ("queue_deadline_s", ctypes.c_double)]
+
+
+class moa_completion(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int), ("dt", ctypes.c_int),
+                ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("p", ctypes.c_int64),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+class moa_serve_counters(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64),
+                ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("queued", ctypes.c_uint64), ("inflight", ctypes.c_uint64),
+                ("inflight_peak", ctypes.c_int), ("arena_peak", ctypes.c_size_t),
+                ("arena_used", ctypes.c_size_t), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class MoaError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"moa status {status}: {msg}")
@@ -85,6 +112,14 @@ EXPORTS = {
     "moa_gemm_grouped": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(moa_gemm_desc), _vp, _sz,
                                         _vp]),
     "moa_gemm_f32split_noalloc": (ctypes.c_int, [_i64, _i64, _i64, _vp, _vp, _vp, _vp]),
+    "moa_serve_create": (ctypes.c_int, [ctypes.POINTER(moa_serve_config),
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "moa_serve_submit": (ctypes.c_int, [_vp, ctypes.POINTER(moa_gemm_desc),
+                                        ctypes.POINTER(ctypes.c_uint64)]),
+    "moa_serve_poll": (ctypes.c_int, [_vp, ctypes.POINTER(moa_completion), ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_int)]),
+    "moa_serve_stats": (ctypes.c_int, [_vp, ctypes.POINTER(moa_serve_counters)]),
+    "moa_serve_destroy": (ctypes.c_int, [_vp]),
     "moa_sync_status": (ctypes.c_int, [_vp]),
     "moa_last_error": (ctypes.c_char_p, []),
     "moa_set_wait_limit_ns": (ctypes.c_uint64, [ctypes.c_uint64]),
@@ -248,3 +283,45 @@ def gemm_grouped(problems, stream=None, workspace: Workspace | None = None, desc
     need = int(lib().moa_gemm_grouped_workspace_size(len(problems), descs))
     ws, wsb = workspace.get(need)
     check(lib().moa_gemm_grouped(len(problems), descs, ws, wsb, _stream_handle(stream)))
+
+
+class Server:
+    """The continuous-batching server (moa_serve_*) over a torch-owned arena."""
+
+    def __init__(self, arena_bytes: int, max_inflight: int = 32, n_streams: int = 4,
+                 queue_capacity: int = 0, queue_deadline_s: float = 0.0, device=None):
+        import torch
+        self.arena = torch.empty(arena_bytes + 256, dtype=torch.uint8,
+                                 device=device or torch.device("cuda")) if arena_bytes else None
+        base = 0 if self.arena is None else (self.arena.data_ptr() + 255) // 256 * 256
+        self.cfg = moa_serve_config(base, arena_bytes, max_inflight, n_streams, queue_capacity,
+                                    queue_deadline_s)
+        self.h = ctypes.c_void_p()
+        check(lib().moa_serve_create(ctypes.byref(self.cfg), ctypes.byref(self.h)))
+        self._buf = (moa_completion * 4096)()
+
+    def submit(self, A, B, C, dt):
+        """Returns (status, ticket); status != MOA_OK means not queued."""
+        d = make_descs([(A, B, C, dt)])
+        t = ctypes.c_uint64()
+        rc = lib().moa_serve_submit(self.h, d, ctypes.byref(t))
+        return rc, t.value
+
+    def poll(self):
+        n = ctypes.c_int()
+        out = []
+        while True:
+            check(lib().moa_serve_poll(self.h, self._buf, len(self._buf), ctypes.byref(n)))
+            out += [self._buf[i] for i in range(n.value)]
+            if n.value < len(self._buf):
+                return [(c.ticket, c.status, c.t_submit, c.t_start, c.t_done) for c in out]
+
+    def stats(self):
+        st = moa_serve_counters()
+        check(lib().moa_serve_stats(self.h, ctypes.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if self.h:
+            check(lib().moa_serve_destroy(self.h))
+            self.h = ctypes.c_void_p()
