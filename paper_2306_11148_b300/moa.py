@@ -308,13 +308,17 @@ class Server:
         return rc, t.value
 
     def poll(self):
+        """Completions as (ticket, status, t_submit, t_start, t_done) tuples."""
         n = ctypes.c_int()
         out = []
         while True:
             check(lib().moa_serve_poll(self.h, self._buf, len(self._buf), ctypes.byref(n)))
-            out += [self._buf[i] for i in range(n.value)]
+            # copy out now: the buffer is overwritten by the next poll
+            for i in range(n.value):
+                c = self._buf[i]
+                out.append((c.ticket, c.status, c.t_submit, c.t_start, c.t_done))
             if n.value < len(self._buf):
-                return [(c.ticket, c.status, c.t_submit, c.t_start, c.t_done) for c in out]
+                return out
 
     def stats(self):
         st = moa_serve_counters()

@@ -115,14 +115,16 @@ def test_budget_busy_and_deadline_paths():
     finally:
         srv.close()
     # one slot, short deadline, tiny queue: later requests are refused or rejected
-    big = _req(4096, 4096, 4096, moa.MOA_F64_SPLIT_F32IN, seed=2)
+    # the big request keeps the only slot busy for ~30 ms (21 BF16 slice
+    # products of 8192^3), so the small ones queue well past their 2 ms deadline
+    big = _req(8192, 8192, 8192, moa.MOA_F64_SPLIT_F32IN, seed=2)
     small = _req(64, 64, 64, moa.MOA_F32_SPLIT, seed=3)
     srv = moa.Server(arena_bytes=8 << 30, max_inflight=1, n_streams=1, queue_capacity=4,
                      queue_deadline_s=0.002)
     try:
         rc, tb = srv.submit(*big)
         assert rc == moa.MOA_OK
-        time.sleep(0.005)
+        time.sleep(0.001)
         codes = [srv.submit(*small) for _ in range(12)]
         queued = [t for rc, t in codes if rc == moa.MOA_OK]
         assert any(rc == moa.MOA_ERR_BUSY for rc, _ in codes)
