@@ -218,6 +218,25 @@ class Energy:
         except Exception:
             return None
 
+    def temp_c(self):
+        """GPU temperature (C) through NVML, or None."""
+        if self.h is None:
+            return None
+        try:
+            import pynvml
+            return float(pynvml.nvmlDeviceGetTemperature(self.h, pynvml.NVML_TEMPERATURE_GPU))
+        except Exception:
+            pass
+        try:
+            import ctypes
+            L = ctypes.CDLL("libnvidia-ml.so.1")
+            t = ctypes.c_uint()
+            if L.nvmlDeviceGetTemperature(self.h, 0, ctypes.byref(t)) == 0:
+                return float(t.value)
+        except Exception:
+            pass
+        return None
+
 
 # ------------------------------------------------------------------ distributed
 def dist_setup():
@@ -251,7 +270,8 @@ def max_over_ranks(x, ws):
 # ------------------------------------------------------------------ workloads
 MODE_OF = {"square": "tf32", "bf16": "bf16", "split_f32": "f32_split",
            "split_f64": "f64_split_f32in", "f64": "f64", "simt": "f32_simt",
-           "grouped": "grouped", "serve": "serve"}
+           "grouped": "grouped", "serve": "serve", "energy_n": "energy_n",
+           "tiles": "tiles"}
 
 
 def make_inputs(mode, N):
@@ -574,6 +594,125 @@ def bench_serve(pool, cring, rate, seconds, seed=0):
             "alone_vs_mix_checked": checked, "alone_vs_mix_mismatch": mism}
 
 
+def measure_window(step, energy, stream, t_est, min_window=1.5):
+    """Back-to-back GEMMs for >= min_window seconds: (seconds per GEMM by CUDA
+    events, joules per GEMM and average watts by the NVML energy counter,
+    temperature at the end)."""
+    import torch
+    reps = max(2, int(math.ceil(min_window / max(t_est, 1e-6))))
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    j0 = energy.read_j() if energy else None
+    w0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(reps):
+            step()
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    w1 = time.perf_counter()
+    j1 = energy.read_j() if energy else None
+    t = ev0.elapsed_time(ev1) / 1000.0 / reps
+    out = {"s_per_gemm": t, "reps": reps, "window_s": w1 - w0}
+    if j0 is not None and j1 is not None:
+        out["j_per_gemm"] = (j1 - j0) / reps
+        out["avg_w"] = (j1 - j0) / (w1 - w0)
+    out["temp_c"] = energy.temp_c() if energy else None
+    return out
+
+
+def _prep(mode, N, seed=0):
+    import torch
+    from paper_2306_11148_b300 import inputs, moa
+    dt = moa.MODES[mode]
+    A, B = inputs.square_uniform(N, moa.in_dtype(dt), seed=seed)
+    Ad, Bd = A.cuda(), B.cuda()
+    C = torch.empty((N, N), dtype=moa.out_dtype(dt), device="cuda")
+    ws = moa.Workspace(torch.device("cuda"))
+    w, wb = ws.get(moa.moa_gemm_workspace_size(N, N, N, dt, 0))
+    return dt, A, B, Ad, Bd, C, ws, w, wb
+
+
+def bench_energy_n(stream, energy, sizes=(1024, 2048, 4096, 8192, 16384),
+                   modes=("tf32", "f64_split_f64in", "f64")):
+    """Square sweep: per precision mode and N, time, TFLOP/s and NVML joules per
+    GEMM, plus the least-squares slope of log J against log N (the paper
+    claims energy quadratic in N)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2306_11148_b300 import moa
+    res = {}
+    for mode in modes:
+        rows = []
+        for N in sizes:
+            dt, A, B, Ad, Bd, C, ws, w, wb = _prep(mode, N)
+            sh = int(stream.cuda_stream)
+
+            def step():
+                moa.check(moa.moa_gemm_ex(N, N, N, dt, Ad.data_ptr(), Bd.data_ptr(), C.data_ptr(),
+                                          0, w, wb, sh, None))
+            with torch.cuda.stream(stream):
+                t0 = time.perf_counter()
+                step()
+                torch.cuda.synchronize()
+                t_est = time.perf_counter() - t0
+            m = measure_window(step, energy, stream, t_est)
+            moa.check(moa.moa_sync_status(sh))
+            idx = np.array([0, N // 2, N - 1], dtype=np.int64)
+            ref = oracle.gemm_rows(A.double().numpy(), B.double().numpy(), idx)
+            got = C[torch.from_numpy(idx).cuda()].cpu().double().numpy()
+            m.update({"N": N, "tflops": 2.0 * N ** 3 / m["s_per_gemm"] / 1e12,
+                      "rel_err_3_rows": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))})
+            rows.append(m)
+            del Ad, Bd, C, ws
+            torch.cuda.empty_cache()
+        fit = None
+        pts = [(math.log(r["N"]), math.log(r["j_per_gemm"])) for r in rows if r.get("j_per_gemm")]
+        if len(pts) >= 2:
+            x = np.array([p[0] for p in pts])
+            y = np.array([p[1] for p in pts])
+            fit = float(np.polyfit(x, y, 1)[0])
+        res[mode] = {"points": rows, "slope_logJ_logN": fit}
+    return res
+
+
+def bench_tiles(stream, energy, sizes=(2048, 4096, 8192), modes=("bf16", "tf32")):
+    """Tile-width sweep (the paper's time/energy/power/temperature versus
+    matrix size and block size): every block_n at every N."""
+    import torch
+    from paper_2306_11148_b300 import moa
+    L = moa.lib()
+    out = []
+    for mode in modes:
+        for N in sizes:
+            dt, A, B, Ad, Bd, C, ws, w, wb = _prep(mode, N)
+            sh = int(stream.cuda_stream)
+            for bn in (64, 128, 256):
+                moa.check(L.moa_set_block_n(bn))
+
+                def step():
+                    moa.check(moa.moa_gemm_ex(N, N, N, dt, Ad.data_ptr(), Bd.data_ptr(),
+                                              C.data_ptr(), 0, w, wb, sh, None))
+                with torch.cuda.stream(stream):
+                    step()
+                    t0 = time.perf_counter()
+                    step()
+                    torch.cuda.synchronize()
+                    t_est = time.perf_counter() - t0
+                m = measure_window(step, energy, stream, t_est, min_window=1.0)
+                m.update({"mode": mode, "N": N, "block_n": bn,
+                          "tflops": 2.0 * N ** 3 / m["s_per_gemm"] / 1e12})
+                out.append(m)
+            moa.check(L.moa_set_block_n(0))
+            moa.check(moa.moa_sync_status(sh))
+            del Ad, Bd, C, ws
+            torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args, ws, rank):
     if rank != 0:
@@ -642,6 +781,32 @@ def main():
     stream = torch.cuda.Stream()
     mode = MODE_OF[args.workload]
     N = args.n
+
+    if mode in ("energy_n", "tiles"):
+        clocks = ClockSampler(pci)
+        clocks.start()
+        if mode == "energy_n":
+            res = bench_energy_n(stream, energy)
+            metric = "joules per square ONF GEMM vs N (slope of log J vs log N)"
+            value = res["tf32"]["slope_logJ_logN"]
+            unit = "dlogJ/dlogN"
+        else:
+            res = bench_tiles(stream, energy)
+            metric = "time/energy/power/temperature vs N and tile width"
+            best = max(res, key=lambda r: r["tflops"])
+            value = best["tflops"]
+            unit = "TFLOP/s (best cell)"
+        clk = clocks.stop()
+        if rank == 0:
+            print(json.dumps({"metric": metric, "value": value, "unit": unit, "n_gpus": ws,
+                              "higher_is_better": mode == "tiles", "scaling": "weak",
+                              "vs_baseline": None, "data": "synthetic",
+                              "config": {"workload": mode, "parallelism": f"replicas x{ws}"},
+                              "results": res, "clocks": clk}), flush=True)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
 
     if mode == "serve":
         pool, cring = serve_pool()

@@ -134,6 +134,34 @@ int moa_gemm_grouped(int count, const moa_gemm_desc* descs,
                      void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------- */
+/* Tile widths of the dense tensor-core GEMMs (MOA_BF16, MOA_F32_TF32)       */
+/* ---------------------------------------------------------------------- */
+
+/* The tile is 128 rows x block_n columns; the planner picks block_n from the
+ * shape (Sec. 3.4 of the paper: block sizes from the static shapes and types).
+ * moa_set_block_n forces block_n (64, 128 or 256) for the calling thread's
+ * later dense calls; 0 restores the planner.  MOA_ERR_ARG otherwise. */
+int moa_set_block_n(int block_n);
+
+/* Measured refinement of the planner: times C := A . B with every block_n on
+ * the caller's buffers (1 warm-up + 3 timed calls each, CUDA events on
+ * `stream`, synchronous), records the fastest for the shape bucket of
+ * (m, n, p, dt) -- half-octaves of each dimension -- and returns it in
+ * *best_block_n (and its time in *best_ms; either may be NULL).  Later calls
+ * in the bucket use it.  Leaves C holding the product.  Workspace as for
+ * moa_gemm_ex.  MOA_ERR_DTYPE for modes without tile widths. */
+int moa_tune_dense(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const void* B,
+                   void* C, void* ws, size_t ws_bytes, void* stream, int* best_block_n,
+                   float* best_ms);
+
+/* Writes / reads / clears the measured table (text: "dt m n p block_n" per
+ * line, dimensions as half-octave buckets).  The file named by the
+ * MOA_TUNE_CACHE environment variable is loaded on first use. */
+int moa_tune_save(const char* path);
+int moa_tune_load(const char* path);
+int moa_tune_clear(void);
+
+/* ---------------------------------------------------------------------- */
 /* Serving: a continuous-batching GEMM server (the serving pattern).        */
 /* ---------------------------------------------------------------------- */
 
@@ -241,6 +269,14 @@ uint64_t moa_set_wait_limit_ns(uint64_t ns);
  * the pre-passes) and `stop_event` immediately after it, on the call's stream.
  * Pass NULL, NULL to stop.  The events stay owned by the caller.  Returns MOA_OK. */
 int moa_profile_events(void* start_event, void* stop_event);
+
+/* Failure-detection self-test: launches one CTA whose pipeline wait (the
+ * bounded mbarrier wait every tensor-core kernel uses) waits for an arrival
+ * that never comes; after `limit_ns` (0 < limit_ns <= 10 s) the kernel records
+ * the timeout in the device status word and returns, leaving the context
+ * usable.  A following moa_sync_status(stream) returns MOA_ERR_TIMEOUT.
+ * Diagnostic only; the paper has no counterpart. */
+int moa_selftest_wait_timeout(uint64_t limit_ns, void* stream);
 
 /* Library version string. */
 const char* moa_version(void);

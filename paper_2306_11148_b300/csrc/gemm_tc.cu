@@ -333,12 +333,17 @@ int dense_tc_launch(bool in_bf16, int64_t m, int64_t n, int64_t p, const void* A
                     const void* B, int64_t ldb, float* C, cudaStream_t s, moa_stats* st) {
     // Tile planner: the widest N tile (fewest A re-reads) unless that leaves
     // most SMs idle, in which case narrower tiles spread the work.
+    // A per-thread override (moa_set_block_n) or a measured choice for this
+    // shape bucket (moa_tune_dense) takes precedence.
     const long tiles256 = ceil_div(m, 128) * ceil_div(p, 256);
     const long tiles128 = ceil_div(m, 128) * ceil_div(p, 128);
     const int sms = num_sms();
     int bn = 256;
     if (tiles256 < sms && tiles128 > tiles256) bn = 128;
     if (bn == 128 && tiles128 < sms && p <= 64) bn = 64;
+    const int tuned = tuned_block_n(in_bf16 ? MOA_BF16 : MOA_F32_TF32, m, n, p);
+    if (tuned) bn = tuned;
+    if (tile_override()) bn = tile_override();
     if (in_bf16) {
         if (bn == 256) return launch_cfg<2, 256, 4, 0>(m, n, p, A, lda, B, ldb, C, s, st);
         if (bn == 128) return launch_cfg<2, 128, 6, 0>(m, n, p, A, lda, B, ldb, C, s, st);

@@ -48,6 +48,11 @@ struct TileChoice {
 int dense_tc_launch(bool in_bf16, int64_t m, int64_t n, int64_t p, const void* A, int64_t lda,
                     const void* B, int64_t ldb, float* C, cudaStream_t s, moa_stats* st);
 
+// Tile-width choice of the dense kernels (tuner.cu): per-thread override
+// (0 = none) and the measured width for a shape bucket (0 = none).
+int tile_override();
+int tuned_block_n(moa_dtype dt, int64_t m, int64_t n, int64_t p);
+
 // SIMT kernels (no tensor cores).
 int simt_f64_launch(int64_t m, int64_t n, int64_t p, const double* A, const double* B, double* C,
                     cudaStream_t s);

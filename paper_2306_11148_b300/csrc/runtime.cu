@@ -272,6 +272,26 @@ int transpose_pad_launch(const float* X, int64_t rows, int64_t cols, float* Xt, 
     return MOA_OK;
 }
 
+// ------------------------------------------------------------------ self-test
+namespace {
+// One CTA waits, through the same bounded mbar_wait every pipeline uses, on
+// an mbarrier that nothing ever arrives at; after `limit_ns` the wait gives
+// up, records kDevTimeout in the status word and the kernel returns.  Holds
+// no TMEM and issues no asynchronous copies.
+__global__ void wait_timeout_selftest_kernel(uint64_t limit_ns, int* status) {
+    __shared__ uint64_t bar;
+    __shared__ CtaCtl ctl;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        ctl.abort = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_wait(&bar, 0, &ctl, limit_ns, status);
+    __syncthreads();
+}
+}  // namespace
+
 }  // namespace moa
 
 // ------------------------------------------------------------------ public housekeeping
@@ -287,6 +307,18 @@ uint64_t moa_set_wait_limit_ns(uint64_t ns) {
 }
 
 const char* moa_version(void) { return "moa-b300 0.1.0 (sm_103a)"; }
+
+int moa_selftest_wait_timeout(uint64_t limit_ns, void* stream) {
+    if (limit_ns == 0 || limit_ns > 10000000000ull)
+        return moa::fail(MOA_ERR_ARG, "limit must be in (0, 10 s]");
+    int* status = moa::device_status_ptr();
+    if (!status) return MOA_ERR_CUDA;
+    moa::wait_timeout_selftest_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(limit_ns,
+                                                                                      status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return moa::cuda_fail(e, "wait_timeout_selftest_kernel launch");
+    return MOA_OK;
+}
 
 int moa_profile_events(void* start_event, void* stop_event) {
     moa::g_prof_start = static_cast<cudaEvent_t>(start_event);

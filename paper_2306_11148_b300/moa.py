@@ -125,6 +125,14 @@ EXPORTS = {
     "moa_set_wait_limit_ns": (ctypes.c_uint64, [ctypes.c_uint64]),
     "moa_version": (ctypes.c_char_p, []),
     "moa_profile_events": (ctypes.c_int, [_vp, _vp]),
+    "moa_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_uint64, _vp]),
+    "moa_set_block_n": (ctypes.c_int, [ctypes.c_int]),
+    "moa_tune_dense": (ctypes.c_int, [_i64, _i64, _i64, ctypes.c_int, _vp, _vp, _vp, _vp, _sz, _vp,
+                                      ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_float)]),
+    "moa_tune_save": (ctypes.c_int, [ctypes.c_char_p]),
+    "moa_tune_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "moa_tune_clear": (ctypes.c_int, []),
     "moa_shutdown": (None, []),
 }
 

@@ -1,0 +1,86 @@
+"""Tile widths of the dense tensor-core GEMMs: forced widths, the measured
+autotuner and its table file.
+
+Every tile width sums each output element over the same K blocks in the same
+order, so the result must not depend on the width (bit-identical), and the
+tuner's choice must be one of the widths and be reused for the shape bucket."""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2306_11148_b300 import build as moa_build
+from paper_2306_11148_b300 import inputs, moa
+
+
+@pytest.fixture(scope="module")
+def L():
+    moa_build.build()
+    return moa.lib()
+
+
+def test_block_n_argument_checked(L):
+    assert L.moa_set_block_n(96) == moa.MOA_ERR_ARG
+    assert L.moa_set_block_n(0) == moa.MOA_OK
+
+
+def test_tune_table_file_round_trip(L, tmp_path):
+    src = tmp_path / "in.txt"
+    src.write_text("3 20 20 20 128\n1 16 18 16 64\n1 2 2 2 99\n")   # last line invalid
+    assert L.moa_tune_clear() == moa.MOA_OK
+    assert L.moa_tune_load(str(src).encode()) == moa.MOA_OK
+    out = tmp_path / "out.txt"
+    assert L.moa_tune_save(str(out).encode()) == moa.MOA_OK
+    assert sorted(out.read_text().split("\n")[:-1]) == ["1 16 18 16 64", "3 20 20 20 128"]
+    assert L.moa_tune_load(str(tmp_path / "missing.txt").encode()) == moa.MOA_ERR_ARG
+    L.moa_tune_clear()
+
+
+def test_tune_rejects_modes_without_tiles(L):
+    assert L.moa_tune_dense(8, 8, 8, moa.MOA_F64, 256, 256, 256, None, 0, None, None, None) == \
+        moa.MOA_ERR_DTYPE
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dt", [moa.MOA_BF16, moa.MOA_F32_TF32])
+def test_every_tile_width_gives_the_same_bits(L, dt):
+    A, B = inputs.uniform_pair(300, 700, 520, dtype=moa.in_dtype(dt), seed=3)
+    A, B = A.cuda(), B.cuda()
+    outs = []
+    try:
+        for w in (64, 128, 256):
+            assert L.moa_set_block_n(w) == moa.MOA_OK
+            C, st = moa.gemm(A, B, dt, stats=True)
+            torch.cuda.synchronize()
+            assert st.block_n == w
+            outs.append(C)
+    finally:
+        L.moa_set_block_n(0)
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[1], outs[2])
+    ref = oracle.gemm(A.double().cpu().numpy(), B.double().cpu().numpy())
+    got = outs[0].double().cpu().numpy()
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= (5e-3 if dt == moa.MOA_F32_TF32 else 1e-5)
+
+
+@pytest.mark.gpu
+def test_tuner_records_and_reuses_choice(L, tmp_path):
+    L.moa_tune_clear()
+    m, n, p = 1024, 2048, 1536
+    A, B = inputs.uniform_pair(m, n, p, dtype=torch.bfloat16, seed=4)
+    A, B = A.cuda(), B.cuda()
+    C = torch.empty((m, p), dtype=torch.float32, device="cuda")
+    best = ctypes.c_int()
+    ms = ctypes.c_float()
+    moa.check(L.moa_tune_dense(m, n, p, moa.MOA_BF16, A.data_ptr(), B.data_ptr(), C.data_ptr(),
+                               None, 0, moa._stream_handle(None), ctypes.byref(best),
+                               ctypes.byref(ms)))
+    assert best.value in (64, 128, 256) and ms.value > 0
+    _, st = moa.gemm(A, B, moa.MOA_BF16, stats=True)
+    assert st.block_n == best.value
+    out = tmp_path / "tune.txt"
+    moa.check(L.moa_tune_save(str(out).encode()))
+    assert out.read_text().strip().endswith(str(best.value))
+    L.moa_tune_clear()
