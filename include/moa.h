@@ -139,8 +139,10 @@ int moa_gemm_grouped(int count, const moa_gemm_desc* descs,
 
 /* The tile is 128 rows x block_n columns; the planner picks block_n from the
  * shape (Sec. 3.4 of the paper: block sizes from the static shapes and types).
- * moa_set_block_n forces block_n (64, 128 or 256) for the calling thread's
- * later dense calls; 0 restores the planner.  MOA_ERR_ARG otherwise. */
+ * moa_set_block_n forces block_n for the calling thread's later calls: the
+ * dense modes take 64, 128 or 256, the split modes 128, 192 (FP64 accuracy)
+ * or 256 (FP32 accuracy); other values leave that mode to its planner.  0
+ * restores the planners.  MOA_ERR_ARG for values outside {0,64,128,192,256}. */
 int moa_set_block_n(int block_n);
 
 /* Measured refinement of the planner: times C := A . B with every block_n on

@@ -343,7 +343,8 @@ int dense_tc_launch(bool in_bf16, int64_t m, int64_t n, int64_t p, const void* A
     if (bn == 128 && tiles128 < sms && p <= 64) bn = 64;
     const int tuned = tuned_block_n(in_bf16 ? MOA_BF16 : MOA_F32_TF32, m, n, p);
     if (tuned) bn = tuned;
-    if (tile_override()) bn = tile_override();
+    if (tile_override() == 64 || tile_override() == 128 || tile_override() == 256)
+        bn = tile_override();
     if (in_bf16) {
         if (bn == 256) return launch_cfg<2, 256, 4, 0>(m, n, p, A, lda, B, ldb, C, s, st);
         if (bn == 128) return launch_cfg<2, 128, 6, 0>(m, n, p, A, lda, B, ldb, C, s, st);

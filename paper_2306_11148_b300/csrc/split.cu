@@ -250,15 +250,25 @@ int grid_for(int64_t total, int threads) {
 // ====================================================================== slice GEMM
 namespace {
 
-constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 6;
+constexpr int kBM = 128, kBK = 64;
 constexpr int kABytes = kBM * 128;                 // 128 rows x 64 BF16
-constexpr int kBChunkBytes = kBK * 128;            // 64 rows x 64 BF16
-constexpr int kBBytes = 2 * kBChunkBytes;          // 128 columns
-constexpr int kStageBytes = kABytes + kBBytes;
-constexpr int kSplitSmem = 1024 + kStages * kStageBytes + 256;
-constexpr int kSplitThreads = 320;
-constexpr uint32_t kSplitIdesc = make_idesc(1u, kBM, kBN, 0u, 1u);
+constexpr int kBChunkBytes = kBK * 128;            // 64 rows x 64 BF16 columns
 constexpr int kMaxLevels = 8;
+
+// Tile width BN (128, 192 or 256): stage ring, threads (two issuer warps
+// plus BN / 16 epilogue warps, each owning 64 columns of a 32-row TMEM
+// quadrant) and TMEM (two chunk accumulators of BN columns).
+template <int BN>
+struct SplitCfg {
+    static constexpr int kStages = BN == 256 ? 4 : (BN == 192 ? 5 : 6);
+    static constexpr int kBBytes = (BN / 64) * kBChunkBytes;
+    static constexpr int kStageBytes = kABytes + kBBytes;
+    static constexpr int kSmem = 1024 + kStages * kStageBytes + 256;
+    static constexpr int kEpiWarps = BN / 16;
+    static constexpr int kThreads = 64 + 32 * kEpiWarps;
+    static constexpr int kTmemCols = BN == 128 ? 256 : 512;
+    static constexpr uint32_t kIdesc = make_idesc(1u, kBM, BN, 0u, 1u);
+};
 
 struct SplitArgs {
     void* C;
@@ -304,15 +314,18 @@ __device__ __forceinline__ void pair_at(const SplitArgs& a, int L, int q, int& s
     }
 }
 
-__global__ void __launch_bounds__(kSplitThreads, 1)
+template <int BN, bool F64>
+__global__ void __launch_bounds__(SplitCfg<BN>::kThreads, 1)
     split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       const SplitArgs args) {
+    using Cfg = SplitCfg<BN>;
+    constexpr int kStages = Cfg::kStages;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                ~static_cast<uintptr_t>(1023));
     uint8_t* sA = smem;
     uint8_t* sB = smem + kStages * kABytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kStages * kBBytes);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kStages * Cfg::kBBytes);
     uint64_t* full = bars;
     uint64_t* empty = bars + kStages;
     uint64_t* tfull = bars + 2 * kStages;
@@ -333,7 +346,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 8);
+            mbar_init(&tempty[b], Cfg::kEpiWarps);
         }
         mbar_init(drain, 1);
         ctl->abort = 0;
@@ -344,7 +357,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
         prefetch_tmap(&tmB);
     }
     if (warp == 1) {
-        tmem_alloc(tmem_slot, 512);
+        tmem_alloc(tmem_slot, Cfg::kTmemCols);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -357,7 +370,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---------------- TMA producer: (tile, level, chunk, kb, pair)
+            // ---------------- TMA producer: (tile, level, kb, pair)
             int stage = 0;
             uint32_t phase = 0;
             long issued = 0;
@@ -375,13 +388,13 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
                                 ok = false;
                                 break;
                             }
-                            mbar_arrive_expect_tx(&full[stage], kStageBytes);
+                            mbar_arrive_expect_tx(&full[stage], Cfg::kStageBytes);
                             tma_load_3d(sA + stage * kABytes, &tmA, &full[stage], kb * kBK,
                                         tm * kBM, s);
-                            tma_load_3d(sB + stage * kBBytes, &tmB, &full[stage], tn * kBN,
-                                        kb * kBK, u);
-                            tma_load_3d(sB + stage * kBBytes + kBChunkBytes, &tmB, &full[stage],
-                                        tn * kBN + 64, kb * kBK, u);
+#pragma unroll
+                            for (int c = 0; c < BN / 64; ++c)
+                                tma_load_3d(sB + stage * Cfg::kBBytes + c * kBChunkBytes, &tmB,
+                                            &full[stage], tn * BN + c * 64, kb * kBK, u);
                             ++issued;
                             if (++stage == kStages) {
                                 stage = 0;
@@ -392,6 +405,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
                 }
             }
             if (!ok) {
+                // Let the loads already in flight land before the CTA exits.
                 CtaCtl local{0};
                 const long outstanding = issued < kStages ? issued : kStages;
                 for (long q = 1; q <= outstanding; ++q) {
@@ -421,7 +435,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t d = tmem_base + static_cast<uint32_t>(buf * kBN);
+                        const uint32_t d = tmem_base + static_cast<uint32_t>(buf * BN);
                         const int kb1 = min(num_kb, kb0 + kc);
                         bool first = true;
                         for (int kb = kb0; kb < kb1 && ok; ++kb) {
@@ -434,12 +448,12 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
                                 const uint64_t adesc =
                                     smem_desc_sw128(smem_u32(sA + stage * kABytes), 16, 1024);
                                 const uint64_t bdesc = smem_desc_sw128(
-                                    smem_u32(sB + stage * kBBytes), kBChunkBytes, 1024);
+                                    smem_u32(sB + stage * Cfg::kBBytes), kBChunkBytes, 1024);
 #pragma unroll
                                 for (int k = 0; k < kBK / 16; ++k) {
                                     mma_f16(d, adesc + static_cast<uint64_t>((k * 32) >> 4),
                                             bdesc + static_cast<uint64_t>((k * 16 * 128) >> 4),
-                                            kSplitIdesc, (first && k == 0) ? 0u : 1u);
+                                            Cfg::kIdesc, (first && k == 0) ? 0u : 1u);
                                 }
                                 first = false;
                                 mma_commit(&empty[stage]);
@@ -454,13 +468,14 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
                     }
                 }
             }
+            // Every MMA issued above must finish before TMEM is released.
             mma_commit(drain);
             CtaCtl local{0};
             mbar_wait(drain, 0, &local, limit, status);
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue: warps 2..9; quadrant q = warp % 4, column half h
+        // ---------------- epilogue: quadrant q = warp % 4, 64-column group h
         const int q = warp & 3;
         const int h = (warp - 2) >> 2;
         const uint32_t lane_base = static_cast<uint32_t>(q * 32) << 16;
@@ -470,17 +485,13 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
             int tm, tn;
             split_tile_coords(t, args.tiles_m, args.tiles_n, args.group_m, tm, tn);
             const int64_t row = static_cast<int64_t>(tm) * kBM + q * 32 + lane;
-            const int64_t col_base = static_cast<int64_t>(tn) * kBN + h * 64;
-            if (args.f64) {
-                // zero the int64 fixed-point total: TMEM columns 256 + 128h .. +128
-                uint32_t z[32];
-#pragma unroll
-                for (int i = 0; i < 32; ++i) z[i] = 0u;
-#pragma unroll
-                for (int g = 0; g < 4; ++g)
-                    tmem_st32(tmem_base + lane_base + 256u + 128u * h + 32u * g, z);
-                tmem_st_wait();
-            }
+            const int64_t col_base = static_cast<int64_t>(tn) * BN + h * 64;
+            const bool row_ok = row < args.m;
+            // FP64 mode keeps the tile's int64 fixed-point total T in C itself
+            // (same 8 bytes per element as the final FP64 value).
+            long long* trow = reinterpret_cast<long long*>(args.C) + row * args.p;
+            const int er = (F64 && row_ok) ? args.eA[row] : 0;
+            bool t_init = false;
             // Running sum per element: FP32 bits (FP32 mode) or the exact
             // int32 sum of the current level (FP64 mode); 0 is zero in both.
             uint32_t acc[64];
@@ -499,19 +510,22 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
                     }
                     tc_fence_after();
 #pragma unroll
-                    for (int g = 0; g < 2; ++g) {
-                        uint32_t r[32];
-                        tmem_ld32(tmem_base + lane_base + static_cast<uint32_t>(buf * kBN + h * 64 + g * 32), r);
+                    for (int g = 0; g < 4; ++g) {
+                        uint32_t r[16];
+                        tmem_ld16(tmem_base + lane_base +
+                                      static_cast<uint32_t>(buf * BN + h * 64 + g * 16),
+                                  r);
                         tmem_ld_wait();
-                        if (args.f64) {
+                        if constexpr (F64) {
 #pragma unroll
-                            for (int i = 0; i < 32; ++i)
-                                acc[g * 32 + i] = static_cast<uint32_t>(
-                                    static_cast<int>(acc[g * 32 + i]) + __float2int_rn(__uint_as_float(r[i])));
+                            for (int i = 0; i < 16; ++i)
+                                acc[g * 16 + i] = static_cast<uint32_t>(
+                                    static_cast<int>(acc[g * 16 + i]) +
+                                    __float2int_rn(__uint_as_float(r[i])));
                         } else {
 #pragma unroll
-                            for (int i = 0; i < 32; ++i)
-                                acc[g * 32 + i] = __float_as_uint(__uint_as_float(acc[g * 32 + i]) +
+                            for (int i = 0; i < 16; ++i)
+                                acc[g * 16 + i] = __float_as_uint(__uint_as_float(acc[g * 16 + i]) +
                                                                   __uint_as_float(r[i]));
                         }
                     }
@@ -520,32 +534,38 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
                     if (lane == 0) mbar_arrive(&tempty[buf]);
                     ++since_fold;
                     const bool level_end = kb0 + kc >= num_kb;
-                    if (args.f64 && (level_end || since_fold == 64)) {
+                    if (F64 && (level_end || since_fold == 64)) {
                         // fold the level's exact sum into the int64 total:
-                        // T += round(R * 2^(8(S-1-L) - drop))
+                        // T += round(R * 2^(8(S-1-L) - drop)); the last fold of
+                        // the tile converts once to FP64 and scales by
+                        // 2^(eA_i + eB_j - 8(S+1) + drop).
                         const int sh = kBeta * (args.S - 1 - L) - args.drop;
+                        const bool last = level_end && L == args.levels - 1;
+                        if (row_ok) {
 #pragma unroll
-                        for (int g = 0; g < 4; ++g) {
-                            uint32_t r[32];
-                            const uint32_t ta = tmem_base + lane_base + 256u + 128u * h + 32u * g;
-                            tmem_ld32(ta, r);
-                            tmem_ld_wait();
-#pragma unroll
-                            for (int i = 0; i < 16; ++i) {
-                                long long v = static_cast<int>(acc[g * 16 + i]);
+                            for (int i = 0; i < 64; ++i) {
+                                const int64_t col = col_base + i;
+                                if (col >= args.p) continue;
+                                long long v = static_cast<int>(acc[i]);
                                 if (sh >= 0)
                                     v = v * (1ll << sh);
                                 else
                                     v = (v + (1ll << (-sh - 1))) >> (-sh);
-                                long long tot = static_cast<long long>(
-                                    (static_cast<unsigned long long>(r[2 * i + 1]) << 32) | r[2 * i]);
-                                tot += v;
-                                r[2 * i] = static_cast<uint32_t>(tot);
-                                r[2 * i + 1] = static_cast<uint32_t>(static_cast<unsigned long long>(tot) >> 32);
+                                const long long tot = (t_init ? trow[col] : 0ll) + v;
+                                if (last) {
+                                    const int ex =
+                                        er + args.eB[col] - kBeta * (args.S + 1) + args.drop;
+                                    reinterpret_cast<double*>(trow)[col] =
+                                        ldexp(__ll2double_rn(tot), ex);
+                                } else {
+                                    trow[col] = tot;
+                                }
+                                // one element at a time: keeps the 64 loads of
+                                // T from being hoisted into registers at once
+                                asm volatile("" ::: "memory");
                             }
-                            tmem_st32(ta, r);
-                            tmem_st_wait();
                         }
+                        t_init = true;
 #pragma unroll
                         for (int i = 0; i < 64; ++i) acc[i] = 0u;
                         since_fold = 0;
@@ -553,30 +573,8 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
                 }
             }
             if (!ok) break;
-            // ---------------- store the tile
-            const bool row_ok = row < args.m;
-            if (args.f64) {
-                double* crow = static_cast<double*>(args.C) + row * args.p;
-                const int er = row_ok ? args.eA[row] : 0;
-#pragma unroll
-                for (int g = 0; g < 4; ++g) {
-                    uint32_t r[32];
-                    tmem_ld32(tmem_base + lane_base + 256u + 128u * h + 32u * g, r);
-                    tmem_ld_wait();
-                    if (row_ok) {
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            const int64_t col = col_base + g * 16 + i;
-                            if (col < args.p) {
-                                const long long tot = static_cast<long long>(
-                                    (static_cast<unsigned long long>(r[2 * i + 1]) << 32) | r[2 * i]);
-                                const int ex = er + args.eB[col] - kBeta * (args.S + 1) + args.drop;
-                                crow[col] = ldexp(__ll2double_rn(tot), ex);
-                            }
-                        }
-                    }
-                }
-            } else if (row_ok) {
+            // ---------------- FP32 mode: store the tile
+            if (!F64 && row_ok) {
                 float* crow = static_cast<float*>(args.C) + row * args.p;
                 if (args.vec_ok && col_base + 64 <= args.p) {
                     float4* dst = reinterpret_cast<float4*>(crow + col_base);
@@ -590,13 +588,12 @@ __global__ void __launch_bounds__(kSplitThreads, 1)
                         if (col_base + i < args.p) crow[col_base + i] = __uint_as_float(acc[i]);
                 }
             }
-            tc_fence_before();
         }
     }
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem_base, 512);
+        tmem_dealloc(tmem_base, Cfg::kTmemCols);
     }
 }
 
@@ -649,30 +646,45 @@ size_t split_workspace_bytes(int64_t m, int64_t n, int64_t p, moa_dtype dt, int 
     return split_layout(m, n, p, dt, S).total;
 }
 
-static int launch_split_gemm(const SplitArgs& a, const CUtensorMap& tmA, const CUtensorMap& tmB,
-                             cudaStream_t s, moa_stats* st) {
+template <int BN, bool F64>
+static int launch_split_cfg(const SplitArgs& a, const CUtensorMap& tmA, const CUtensorMap& tmB,
+                            cudaStream_t s, moa_stats* st) {
+    using Cfg = SplitCfg<BN>;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSplitSmem);
+        cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel<BN, F64>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(split_gemm)");
         attr_set = true;
     }
     const long tiles = static_cast<long>(a.tiles_m) * a.tiles_n;
     const int grid = static_cast<int>(std::min<long>(tiles, num_sms()));
     prof_begin(s);
-    split_gemm_kernel<<<grid, kSplitThreads, kSplitSmem, s>>>(tmA, tmB, a);
+    split_gemm_kernel<BN, F64><<<grid, Cfg::kThreads, Cfg::kSmem, s>>>(tmA, tmB, a);
     cudaError_t e = cudaGetLastError();
     prof_end(s);
     if (e != cudaSuccess) return cuda_fail(e, "split_gemm_kernel launch");
     if (st) {
         st->block_m = kBM;
-        st->block_n = kBN;
+        st->block_n = BN;
         st->block_k = kBK;
         st->grid = grid;
         st->tiles = tiles;
     }
     return MOA_OK;
+}
+
+// Tile width of the slice GEMM: the widest that still gives every SM a tile
+// (fewer B re-reads per flop); FP32 mode up to 256, FP64 mode up to 192 (its
+// epilogue keeps 64 exact running sums per thread, which 256-wide tiles'
+// 576 threads have no registers for).  moa_set_block_n(128 | 192 | 256)
+// forces it.
+static int split_block_n(int64_t m, int64_t p, bool f64) {
+    const int ov = tile_override();
+    if (ov == 128 || ov == 192 || (ov == 256 && !f64)) return ov;
+    const int wide = f64 ? 192 : 256;
+    const long tiles = ceil_div(m, kBM) * ceil_div(p, wide);
+    return tiles >= num_sms() ? wide : 128;
 }
 
 int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const void* B,
@@ -694,8 +706,9 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
     a.m = m;
     a.n = n;
     a.p = p;
+    const int bn = split_block_n(m, p, dt != MOA_F32_SPLIT);
     a.tiles_m = static_cast<int>(ceil_div(m, kBM));
-    a.tiles_n = static_cast<int>(ceil_div(p, kBN));
+    a.tiles_n = static_cast<int>(ceil_div(p, bn));
     a.num_kb = static_cast<int>(ceil_div(n, kBK));
     a.group_m = 16;
     a.S = S;
@@ -785,7 +798,12 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
                       static_cast<uint64_t>(n), static_cast<uint64_t>(S),
                       static_cast<uint64_t>(L.ldb) * 2, static_cast<uint64_t>(b_plane) * 2, 64, kBK);
     if (rc != MOA_OK) return rc;
-    rc = launch_split_gemm(a, tmA, tmB, s, st);
+    if (a.f64)
+        rc = bn == 192 ? launch_split_cfg<192, true>(a, tmA, tmB, s, st)
+                       : launch_split_cfg<128, true>(a, tmA, tmB, s, st);
+    else
+        rc = bn == 256 ? launch_split_cfg<256, false>(a, tmA, tmB, s, st)
+                       : launch_split_cfg<128, false>(a, tmA, tmB, s, st);
     if (st) {
         st->slices = S;
         st->products = dt == MOA_F32_SPLIT ? 6 : S * (S + 1) / 2;

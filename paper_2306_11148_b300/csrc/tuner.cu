@@ -68,8 +68,8 @@ int tuned_block_n(moa_dtype dt, int64_t m, int64_t n, int64_t p) {
 extern "C" {
 
 int moa_set_block_n(int block_n) {
-    if (block_n != 0 && block_n != 64 && block_n != 128 && block_n != 256)
-        return moa::fail(MOA_ERR_ARG, "block_n must be 0, 64, 128 or 256");
+    if (block_n != 0 && block_n != 64 && block_n != 128 && block_n != 192 && block_n != 256)
+        return moa::fail(MOA_ERR_ARG, "block_n must be 0, 64, 128, 192 or 256");
     moa::t_override = block_n;
     return MOA_OK;
 }

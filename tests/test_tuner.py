@@ -84,3 +84,29 @@ def test_tuner_records_and_reuses_choice(L, tmp_path):
     moa.check(L.moa_tune_save(str(out).encode()))
     assert out.read_text().strip().endswith(str(best.value))
     L.moa_tune_clear()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dt,widths", [(moa.MOA_F32_SPLIT, (128, 256)),
+                                       (moa.MOA_F64_SPLIT_F32IN, (128, 192))])
+def test_split_tile_widths_agree(L, dt, widths):
+    """Every slice-GEMM tile width sums the same chunks in the same order, so
+    the results are bit-identical; each is within the mode's tolerance."""
+    A, B = inputs.normal_pair(300, 900, 700, dtype=torch.float32, seed=9, scaled="rows")
+    A, B = A.cuda(), B.cuda()
+    outs = []
+    try:
+        for w in widths:
+            assert L.moa_set_block_n(w) == moa.MOA_OK
+            C, st = moa.gemm(A, B, dt, stats=True)
+            torch.cuda.synchronize()
+            moa.sync_status()
+            assert st.block_n == w
+            outs.append(C)
+    finally:
+        L.moa_set_block_n(0)
+    assert torch.equal(outs[0], outs[1])
+    ref = oracle.gemm(A.double().cpu().numpy(), B.double().cpu().numpy())
+    got = outs[1].double().cpu().numpy()
+    tol = 1e-5 if dt == moa.MOA_F32_SPLIT else 1e-12
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= tol
