@@ -542,26 +542,35 @@ __global__ void __launch_bounds__(SplitCfg<BN>::kThreads, 1)
                         const int sh = kBeta * (args.S - 1 - L) - args.drop;
                         const bool last = level_end && L == args.levels - 1;
                         if (row_ok) {
+                            // 4 blocks of 16 elements: the 16 loads of T in a
+                            // block are independent, so their latency overlaps
 #pragma unroll
-                            for (int i = 0; i < 64; ++i) {
-                                const int64_t col = col_base + i;
-                                if (col >= args.p) continue;
-                                long long v = static_cast<int>(acc[i]);
-                                if (sh >= 0)
-                                    v = v * (1ll << sh);
-                                else
-                                    v = (v + (1ll << (-sh - 1))) >> (-sh);
-                                const long long tot = (t_init ? trow[col] : 0ll) + v;
-                                if (last) {
-                                    const int ex =
-                                        er + args.eB[col] - kBeta * (args.S + 1) + args.drop;
-                                    reinterpret_cast<double*>(trow)[col] =
-                                        ldexp(__ll2double_rn(tot), ex);
-                                } else {
-                                    trow[col] = tot;
+                            for (int b = 0; b < 4; ++b) {
+                                long long told[16];
+#pragma unroll
+                                for (int i = 0; i < 16; ++i) {
+                                    const int64_t col = col_base + b * 16 + i;
+                                    told[i] = (t_init && col < args.p) ? trow[col] : 0ll;
                                 }
-                                // one element at a time: keeps the 64 loads of
-                                // T from being hoisted into registers at once
+#pragma unroll
+                                for (int i = 0; i < 16; ++i) {
+                                    const int64_t col = col_base + b * 16 + i;
+                                    if (col >= args.p) continue;
+                                    long long v = static_cast<int>(acc[b * 16 + i]);
+                                    if (sh >= 0)
+                                        v = v * (1ll << sh);
+                                    else
+                                        v = (v + (1ll << (-sh - 1))) >> (-sh);
+                                    const long long tot = told[i] + v;
+                                    if (last) {
+                                        const int ex =
+                                            er + args.eB[col] - kBeta * (args.S + 1) + args.drop;
+                                        reinterpret_cast<double*>(trow)[col] =
+                                            ldexp(__ll2double_rn(tot), ex);
+                                    } else {
+                                        trow[col] = tot;
+                                    }
+                                }
                                 asm volatile("" ::: "memory");
                             }
                         }

@@ -83,13 +83,17 @@ def test_results_same_alone_and_in_the_mix():
 
 @pytest.mark.gpu
 def test_continuous_batching_overlaps_requests():
-    big = _req(2048, 4096, 2048, moa.MOA_F64_SPLIT_F32IN, seed=50)
+    # the big request runs for several milliseconds (21 BF16 slice products
+    # of 4096 x 8192 x 4096); the small ones arrive once it has been admitted
+    big = _req(4096, 8192, 4096, moa.MOA_F64_SPLIT_F32IN, seed=50)
     small = [_req(256, 512, 256, moa.MOA_F32_SPLIT, seed=60 + i) for i in range(8)]
-    srv = moa.Server(arena_bytes=4 << 30, max_inflight=16, n_streams=4)
+    srv = moa.Server(arena_bytes=8 << 30, max_inflight=16, n_streams=4)
     try:
         rc, tb = srv.submit(*big)
         assert rc == moa.MOA_OK
-        time.sleep(0.001)    # arrive while the big request runs
+        t0 = time.time()
+        while srv.stats()["admitted"] < 1 and time.time() - t0 < 10:
+            time.sleep(0.0002)
         ts = [srv.submit(*r)[1] for r in small]
         got = _drain(srv, 1 + len(small))
         st = srv.stats()
