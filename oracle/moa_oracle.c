@@ -210,8 +210,9 @@ static double u128_scaled_to_double(unsigned __int128 mag, int exp2)
  * for digits dA (per-row exponents of A) and dB (per-column exponents of B)
  * as produced by moa_oracle_slice_fixed.  The inner sums are exact in int64;
  * the levels are combined in a 128-bit integer at the finest level's scale
- * and converted to FP64 with one rounding.  Requires
- * n * (2^beta)^2 * S < 2^62 and beta * (S + 1) <= 60. */
+ * and converted to FP64 with one rounding.  Requires n * 2^(2 beta) * S < 2^62
+ * (each level sum fits int64) and beta * (S - 1) + 62 < 127 (the shifted
+ * level sums fit the 128-bit total). */
 void moa_oracle_split_gemm_exact(int64_t m, int64_t n, int64_t p,
                                  const int32_t* dA, const int32_t* eA,
                                  const int32_t* dB, const int32_t* eB,

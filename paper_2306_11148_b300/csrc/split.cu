@@ -12,14 +12,14 @@
 // * FP64 accuracy (error-free digit slicing in the manner of Ozaki, Ogita,
 //   Oishi & Rump 2012): each row i of A gets the exponent eA_i with
 //   max_k |A[i,k]| in [2^(eA_i - 1), 2^eA_i), each column j of B likewise eB_j;
-//   x * 2^(8S - e) is rounded once to an integer D and written as S balanced
-//   base-256 digits (|d_0| <= 256, d_s in [-128, 128) for s >= 1), each exactly
+//   x * 2^(7S - e) is rounded once to an integer D and written as S balanced
+//   base-128 digits (|d_0| <= 128, d_s in [-64, 64) for s >= 1), each exactly
 //   a BF16 value.  Level L = s + t of the triangular product (s + t <= S - 1)
 //   is summed over chunks of K short enough that every FP32 partial sum is an
 //   integer below 2^24, hence exact; each chunk is flushed into an int32
 //   running sum, folded at the level's end into an int64 fixed-point total in
 //   TMEM, which the epilogue converts to FP64 once and scales by
-//   2^(eA_i + eB_j - 8(S+1) + drop).
+//   2^(eA_i + eB_j - 7(S+1) + drop).
 //
 // Kernel layout (one persistent CTA per SM, 320 threads): warp 0 issues TMA
 // loads of (A slice, B slice) K blocks; warp 1 issues tcgen05.mma into one of
@@ -781,14 +781,17 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
         a.eA = eA;
         a.eB = eB;
         // Chunk lengths: every FP32 partial sum of a level must stay an
-        // integer of magnitude <= 2^24.  Per k, level 0 adds at most 2^16
-        // (|d_0| <= 256) and level L >= 1 at most (L + 3) * 2^14.
+        // integer of magnitude <= 2^24.  With |d_0| <= 2^beta and
+        // |d_s| <= 2^(beta-1), per k level 0 adds at most 2^(2 beta) and
+        // level L >= 1 at most 2 * 2^(2 beta - 1) + (L - 1) * 2^(2 beta - 2)
+        // = (L + 3) * 2^(2 beta - 2).
         for (int lev = 0; lev < S; ++lev) {
-            const long long per_k = lev == 0 ? (1ll << 16) : static_cast<long long>(lev + 3) << 14;
+            const long long per_k = lev == 0 ? (1ll << (2 * kBeta))
+                                             : static_cast<long long>(lev + 3) << (2 * kBeta - 2);
             const long long kmax = (1ll << 24) / per_k;
             a.kc[lev] = static_cast<int>(std::max(1ll, kmax / kBK));
         }
-        // int64 total: |T| <= n * 2^(8(S+1)) * 1.01 in units of the finest
+        // int64 total: |T| <= n * 2^(beta(S+1)) * 1.02 in units of the finest
         // level before dropping `drop` bits; keep it below 2^62.
         int nbits = 0;
         while ((1ll << nbits) < n) ++nbits;

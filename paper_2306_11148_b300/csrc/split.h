@@ -10,10 +10,13 @@ inline bool is_split(moa_dtype dt) {
 }
 
 // Digit radix 2^kBeta of the FP64-accuracy mode and its slice-count limits.
-constexpr int kBeta = 8;
+// Base 128 (not 256): each digit product is 4x smaller, so the exact FP32
+// accumulation chunks are 4x longer and their flushes hide behind the MMAs;
+// 7 digits (28 slice products) keep 49 bits per operand.
+constexpr int kBeta = 7;
 constexpr int kMinSlices = 3;
-constexpr int kMaxSlices = 7;
-constexpr int kDefaultSlices = 6;
+constexpr int kMaxSlices = 8;
+constexpr int kDefaultSlices = 7;
 
 // Resolves the `slices` argument (0 = default); -1 if not allowed for dt.
 int split_slices(moa_dtype dt, int slices);

@@ -89,9 +89,9 @@ def test_workspace_sizes(L):
     assert moa.moa_gemm_workspace_size(256, 256, 256, moa.MOA_F64, 0) == 0
     s3 = moa.moa_gemm_workspace_size(256, 256, 256, moa.MOA_F32_SPLIT, 0)
     assert s3 >= 3 * 2 * (256 * 256 * 2)
-    s6 = moa.moa_gemm_workspace_size(256, 256, 256, moa.MOA_F64_SPLIT_F32IN, 0)
-    s7 = moa.moa_gemm_workspace_size(256, 256, 256, moa.MOA_F64_SPLIT_F32IN, 7)
-    assert s7 > s6 >= 6 * 2 * (256 * 256 * 2)
+    s7 = moa.moa_gemm_workspace_size(256, 256, 256, moa.MOA_F64_SPLIT_F32IN, 0)
+    s8 = moa.moa_gemm_workspace_size(256, 256, 256, moa.MOA_F64_SPLIT_F32IN, 8)
+    assert s8 > s7 >= 7 * 2 * (256 * 256 * 2)
     # unsupported slice counts report 0 and are rejected by the call
     assert moa.moa_gemm_workspace_size(256, 256, 256, moa.MOA_F64_SPLIT_F32IN, 9) == 0
     assert moa.moa_gemm_ex(64, 64, 64, moa.MOA_F64_SPLIT_F32IN, 256, 512, 1024, 9, 4096, 1 << 20,

@@ -85,16 +85,19 @@ def test_normal_scaled_inputs(dt, scaled):
     assert _rel(C, ref) <= TOL[dt]
 
 
-@pytest.mark.parametrize("S", [3, 4, 5, 6, 7])
+BETA = 7   # digit radix 2^7 of the FP64-accuracy mode
+
+
+@pytest.mark.parametrize("S", [3, 4, 5, 6, 7, 8])
 def test_f64_split_matches_exact_slice_product(S):
     """The FP64-accuracy mode reaches the exact triangular slice product of
     the oracle's digits, up to the final FP64 rounding and the int64 total's
     dropped low bits (relative 2^-48 of the scale)."""
     A, B = inputs.normal_pair(130, 700, 140, dtype=torch.float64, seed=5, scaled="rows")
     C = _run(A, B, moa.MOA_F64_SPLIT_F64IN, slices=S)
-    eA, dA = oracle.slice_fixed(A.numpy(), 0, 8, S)
-    eB, dB = oracle.slice_fixed(B.numpy(), 1, 8, S)
-    exact = oracle.split_gemm_exact(dA, eA, dB, eB, 8, S)
+    eA, dA = oracle.slice_fixed(A.numpy(), 0, BETA, S)
+    eB, dB = oracle.slice_fixed(B.numpy(), 1, BETA, S)
+    exact = oracle.split_gemm_exact(dA, eA, dB, eB, BETA, S)
     scale = np.outer(2.0 ** eA.astype(np.float64), 2.0 ** eB.astype(np.float64))
     assert np.all(np.abs(C - exact) <= scale * 2.0 ** -46 + np.abs(exact) * 2.0 ** -52)
 
