@@ -255,18 +255,28 @@ constexpr int kABytes = kBM * 128;                 // 128 rows x 64 BF16
 constexpr int kBChunkBytes = kBK * 128;            // 64 rows x 64 BF16 columns
 constexpr int kMaxLevels = 8;
 
-// Tile width BN (128, 192 or 256): stage ring, threads (two issuer warps
-// plus BN / 16 epilogue warps, each owning 64 columns of a 32-row TMEM
-// quadrant) and TMEM (two chunk accumulators of BN columns).
-template <int BN>
+// Kernel variants (tile width BN x epilogue mode):
+//   kModeF32     FP32 accuracy; two chunk accumulators; each epilogue warp keeps
+//                FP32 running sums of 64 columns in registers (BN / 16 warps).
+//   kModeF64Reg  FP64 accuracy; two chunk accumulators; exact int32 level sums
+//                of 64 columns per warp in registers (BN 128 or 192).
+//   kModeF64Tmem FP64 accuracy at BN = 256: one chunk accumulator (TMEM columns
+//                0..255) and the exact int32 level sums in TMEM (256..511);
+//                8 epilogue warps of 128 columns each.
+// The FP64 modes keep the tile's int64 fixed-point total in C itself.
+constexpr int kModeF32 = 0, kModeF64Reg = 1, kModeF64Tmem = 2;
+
+template <int BN, int MODE>
 struct SplitCfg {
     static constexpr int kStages = BN == 256 ? 4 : (BN == 192 ? 5 : 6);
     static constexpr int kBBytes = (BN / 64) * kBChunkBytes;
     static constexpr int kStageBytes = kABytes + kBBytes;
     static constexpr int kSmem = 1024 + kStages * kStageBytes + 256;
-    static constexpr int kEpiWarps = BN / 16;
+    static constexpr int kColsPerWarp = MODE == kModeF64Tmem ? 128 : 64;
+    static constexpr int kEpiWarps = 4 * (BN / kColsPerWarp);
     static constexpr int kThreads = 64 + 32 * kEpiWarps;
-    static constexpr int kTmemCols = BN == 128 ? 256 : 512;
+    static constexpr int kNBuf = MODE == kModeF64Tmem ? 1 : 2;
+    static constexpr int kTmemCols = (MODE == kModeF64Tmem || BN > 128) ? 512 : 256;
     static constexpr uint32_t kIdesc = make_idesc(1u, kBM, BN, 0u, 1u);
 };
 
@@ -314,11 +324,13 @@ __device__ __forceinline__ void pair_at(const SplitArgs& a, int L, int q, int& s
     }
 }
 
-template <int BN, bool F64>
-__global__ void __launch_bounds__(SplitCfg<BN>::kThreads, 1)
+template <int BN, int MODE>
+__global__ void __launch_bounds__(SplitCfg<BN, MODE>::kThreads, 1)
     split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       const SplitArgs args) {
-    using Cfg = SplitCfg<BN>;
+    using Cfg = SplitCfg<BN, MODE>;
+    constexpr bool F64 = MODE != kModeF32;
+    constexpr int kNBuf = Cfg::kNBuf;
     constexpr int kStages = Cfg::kStages;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -428,8 +440,8 @@ __global__ void __launch_bounds__(SplitCfg<BN>::kThreads, 1)
                     const int np = level_pairs(args, L);
                     const int kc = args.kc[L];
                     for (int kb0 = 0; kb0 < num_kb && ok; kb0 += kc, ++cnt) {
-                        const int buf = static_cast<int>(cnt & 1);
-                        const uint32_t bph = static_cast<uint32_t>((cnt >> 1) & 1);
+                        const int buf = static_cast<int>(cnt % kNBuf);
+                        const uint32_t bph = static_cast<uint32_t>((cnt / kNBuf) & 1);
                         if (!mbar_wait(&tempty[buf], bph ^ 1u, ctl, limit, status)) {
                             ok = false;
                             break;
@@ -475,7 +487,8 @@ __global__ void __launch_bounds__(SplitCfg<BN>::kThreads, 1)
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue: quadrant q = warp % 4, 64-column group h
+        // ---------------- epilogue: quadrant q = warp % 4, column group h
+        constexpr int kCols = Cfg::kColsPerWarp;
         const int q = warp & 3;
         const int h = (warp - 2) >> 2;
         const uint32_t lane_base = static_cast<uint32_t>(q * 32) << 16;
@@ -485,48 +498,69 @@ __global__ void __launch_bounds__(SplitCfg<BN>::kThreads, 1)
             int tm, tn;
             split_tile_coords(t, args.tiles_m, args.tiles_n, args.group_m, tm, tn);
             const int64_t row = static_cast<int64_t>(tm) * kBM + q * 32 + lane;
-            const int64_t col_base = static_cast<int64_t>(tn) * BN + h * 64;
+            const int64_t col_base = static_cast<int64_t>(tn) * BN + h * kCols;
             const bool row_ok = row < args.m;
-            // FP64 mode keeps the tile's int64 fixed-point total T in C itself
+            // FP64 modes keep the tile's int64 fixed-point total T in C itself
             // (same 8 bytes per element as the final FP64 value).
             long long* trow = reinterpret_cast<long long*>(args.C) + row * args.p;
             const int er = (F64 && row_ok) ? args.eA[row] : 0;
             bool t_init = false;
-            // Running sum per element: FP32 bits (FP32 mode) or the exact
-            // int32 sum of the current level (FP64 mode); 0 is zero in both.
-            uint32_t acc[64];
+            // Register running sums (kModeF32, kModeF64Reg): FP32 bits or the
+            // exact int32 sum of the current level; 0 is zero in both.
+            constexpr int kRegs = MODE == kModeF64Tmem ? 1 : 64;
+            uint32_t acc[kRegs];
 #pragma unroll
-            for (int i = 0; i < 64; ++i) acc[i] = 0u;
+            for (int i = 0; i < kRegs; ++i) acc[i] = 0u;
+            const uint32_t r_base = tmem_base + lane_base + 256u + static_cast<uint32_t>(h * kCols);
+            bool r_valid = false;   // kModeF64Tmem: TMEM level sums hold data
             for (int L = 0; L < args.levels && ok; ++L) {
                 const int kc = args.kc[L];
                 int since_fold = 0;
                 for (int kb0 = 0; kb0 < num_kb; kb0 += kc, ++cnt) {
-                    const int buf = static_cast<int>(cnt & 1);
-                    const uint32_t bph = static_cast<uint32_t>((cnt >> 1) & 1);
+                    const int buf = static_cast<int>(cnt % kNBuf);
+                    const uint32_t bph = static_cast<uint32_t>((cnt / kNBuf) & 1);
                     ok = mbar_wait(&tfull[buf], bph, ctl, limit, status);
                     if (!__all_sync(0xffffffffu, ok)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-#pragma unroll
-                    for (int g = 0; g < 4; ++g) {
-                        uint32_t r[16];
-                        tmem_ld16(tmem_base + lane_base +
-                                      static_cast<uint32_t>(buf * BN + h * 64 + g * 16),
-                                  r);
-                        tmem_ld_wait();
-                        if constexpr (F64) {
-#pragma unroll
-                            for (int i = 0; i < 16; ++i)
-                                acc[g * 16 + i] = static_cast<uint32_t>(
-                                    static_cast<int>(acc[g * 16 + i]) +
-                                    __float2int_rn(__uint_as_float(r[i])));
-                        } else {
+                    const uint32_t a_base = tmem_base + lane_base +
+                                            static_cast<uint32_t>(buf * BN + h * kCols);
+                    if constexpr (MODE == kModeF64Tmem) {
+#pragma unroll 2
+                        for (int g = 0; g < kCols / 16; ++g) {
+                            uint32_t a16[16], r16[16];
+                            tmem_ld16(a_base + 16u * g, a16);
+                            if (r_valid) tmem_ld16(r_base + 16u * g, r16);
+                            tmem_ld_wait();
 #pragma unroll
                             for (int i = 0; i < 16; ++i)
-                                acc[g * 16 + i] = __float_as_uint(__uint_as_float(acc[g * 16 + i]) +
-                                                                  __uint_as_float(r[i]));
+                                r16[i] = static_cast<uint32_t>(
+                                    (r_valid ? static_cast<int>(r16[i]) : 0) +
+                                    __float2int_rn(__uint_as_float(a16[i])));
+                            tmem_st16(r_base + 16u * g, r16);
+                        }
+                        tmem_st_wait();
+                        r_valid = true;
+                    } else {
+#pragma unroll
+                        for (int g = 0; g < 4; ++g) {
+                            uint32_t r[16];
+                            tmem_ld16(a_base + 16u * g, r);
+                            tmem_ld_wait();
+                            if constexpr (F64) {
+#pragma unroll
+                                for (int i = 0; i < 16; ++i)
+                                    acc[g * 16 + i] = static_cast<uint32_t>(
+                                        static_cast<int>(acc[g * 16 + i]) +
+                                        __float2int_rn(__uint_as_float(r[i])));
+                            } else {
+#pragma unroll
+                                for (int i = 0; i < 16; ++i)
+                                    acc[g * 16 + i] = __float_as_uint(
+                                        __uint_as_float(acc[g * 16 + i]) + __uint_as_float(r[i]));
+                            }
                         }
                     }
                     tc_fence_before();
@@ -536,16 +570,23 @@ __global__ void __launch_bounds__(SplitCfg<BN>::kThreads, 1)
                     const bool level_end = kb0 + kc >= num_kb;
                     if (F64 && (level_end || since_fold == 64)) {
                         // fold the level's exact sum into the int64 total:
-                        // T += round(R * 2^(8(S-1-L) - drop)); the last fold of
-                        // the tile converts once to FP64 and scales by
-                        // 2^(eA_i + eB_j - 8(S+1) + drop).
+                        // T += round(R * 2^(beta(S-1-L) - drop)); the last fold
+                        // of the tile converts once to FP64 and scales by
+                        // 2^(eA_i + eB_j - beta(S+1) + drop).
                         const int sh = kBeta * (args.S - 1 - L) - args.drop;
                         const bool last = level_end && L == args.levels - 1;
-                        if (row_ok) {
-                            // 4 blocks of 16 elements: the 16 loads of T in a
-                            // block are independent, so their latency overlaps
 #pragma unroll
-                            for (int b = 0; b < 4; ++b) {
+                        for (int b = 0; b < kCols / 16; ++b) {
+                            uint32_t rv[16];
+                            if constexpr (MODE == kModeF64Tmem) {
+                                tmem_ld16(r_base + 16u * b, rv);
+                                tmem_ld_wait();
+                            } else {
+#pragma unroll
+                                for (int i = 0; i < 16; ++i) rv[i] = 0u;
+                            }
+                            if (row_ok) {
+                                // 16 independent loads of T, so their latency overlaps
                                 long long told[16];
 #pragma unroll
                                 for (int i = 0; i < 16; ++i) {
@@ -556,7 +597,11 @@ __global__ void __launch_bounds__(SplitCfg<BN>::kThreads, 1)
                                 for (int i = 0; i < 16; ++i) {
                                     const int64_t col = col_base + b * 16 + i;
                                     if (col >= args.p) continue;
-                                    long long v = static_cast<int>(acc[b * 16 + i]);
+                                    long long v;
+                                    if constexpr (MODE == kModeF64Tmem)
+                                        v = static_cast<int>(rv[i]);
+                                    else
+                                        v = static_cast<int>(acc[(b * 16 + i) % kRegs]);
                                     if (sh >= 0)
                                         v = v * (1ll << sh);
                                     else
@@ -571,12 +616,12 @@ __global__ void __launch_bounds__(SplitCfg<BN>::kThreads, 1)
                                         trow[col] = tot;
                                     }
                                 }
-                                asm volatile("" ::: "memory");
                             }
                         }
                         t_init = true;
+                        r_valid = false;
 #pragma unroll
-                        for (int i = 0; i < 64; ++i) acc[i] = 0u;
+                        for (int i = 0; i < kRegs; ++i) acc[i] = 0u;
                         since_fold = 0;
                     }
                 }
@@ -589,12 +634,14 @@ __global__ void __launch_bounds__(SplitCfg<BN>::kThreads, 1)
                     float4* dst = reinterpret_cast<float4*>(crow + col_base);
 #pragma unroll
                     for (int v = 0; v < 16; ++v)
-                        dst[v] = make_float4(__uint_as_float(acc[4 * v]), __uint_as_float(acc[4 * v + 1]),
-                                             __uint_as_float(acc[4 * v + 2]), __uint_as_float(acc[4 * v + 3]));
+                        dst[v] = make_float4(__uint_as_float(acc[(4 * v) % kRegs]),
+                                             __uint_as_float(acc[(4 * v + 1) % kRegs]),
+                                             __uint_as_float(acc[(4 * v + 2) % kRegs]),
+                                             __uint_as_float(acc[(4 * v + 3) % kRegs]));
                 } else {
 #pragma unroll
                     for (int i = 0; i < 64; ++i)
-                        if (col_base + i < args.p) crow[col_base + i] = __uint_as_float(acc[i]);
+                        if (col_base + i < args.p) crow[col_base + i] = __uint_as_float(acc[i % kRegs]);
                 }
             }
         }
@@ -655,13 +702,13 @@ size_t split_workspace_bytes(int64_t m, int64_t n, int64_t p, moa_dtype dt, int 
     return split_layout(m, n, p, dt, S).total;
 }
 
-template <int BN, bool F64>
+template <int BN, int MODE>
 static int launch_split_cfg(const SplitArgs& a, const CUtensorMap& tmA, const CUtensorMap& tmB,
                             cudaStream_t s, moa_stats* st) {
-    using Cfg = SplitCfg<BN>;
+    using Cfg = SplitCfg<BN, MODE>;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel<BN, F64>,
+        cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel<BN, MODE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(split_gemm)");
         attr_set = true;
@@ -669,7 +716,7 @@ static int launch_split_cfg(const SplitArgs& a, const CUtensorMap& tmA, const CU
     const long tiles = static_cast<long>(a.tiles_m) * a.tiles_n;
     const int grid = static_cast<int>(std::min<long>(tiles, num_sms()));
     prof_begin(s);
-    split_gemm_kernel<BN, F64><<<grid, Cfg::kThreads, Cfg::kSmem, s>>>(tmA, tmB, a);
+    split_gemm_kernel<BN, MODE><<<grid, Cfg::kThreads, Cfg::kSmem, s>>>(tmA, tmB, a);
     cudaError_t e = cudaGetLastError();
     prof_end(s);
     if (e != cudaSuccess) return cuda_fail(e, "split_gemm_kernel launch");
@@ -683,17 +730,14 @@ static int launch_split_cfg(const SplitArgs& a, const CUtensorMap& tmA, const CU
     return MOA_OK;
 }
 
-// Tile width of the slice GEMM: the widest that still gives every SM a tile
-// (fewer B re-reads per flop); FP32 mode up to 256, FP64 mode up to 192 (its
-// epilogue keeps 64 exact running sums per thread, which 256-wide tiles'
-// 576 threads have no registers for).  moa_set_block_n(128 | 192 | 256)
-// forces it.
+// Tile width of the slice GEMM: 256 when that still gives every SM a tile
+// (fewest B re-reads per flop), else 128.  moa_set_block_n(128 | 192 | 256)
+// forces it (192: FP64 accuracy only).
 static int split_block_n(int64_t m, int64_t p, bool f64) {
     const int ov = tile_override();
-    if (ov == 128 || ov == 192 || (ov == 256 && !f64)) return ov;
-    const int wide = f64 ? 192 : 256;
-    const long tiles = ceil_div(m, kBM) * ceil_div(p, wide);
-    return tiles >= num_sms() ? wide : 128;
+    if (ov == 128 || ov == 256 || (ov == 192 && f64)) return ov;
+    const long tiles = ceil_div(m, kBM) * ceil_div(p, 256);
+    return tiles >= num_sms() ? 256 : 128;
 }
 
 int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const void* B,
@@ -811,11 +855,12 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
                       static_cast<uint64_t>(L.ldb) * 2, static_cast<uint64_t>(b_plane) * 2, 64, kBK);
     if (rc != MOA_OK) return rc;
     if (a.f64)
-        rc = bn == 192 ? launch_split_cfg<192, true>(a, tmA, tmB, s, st)
-                       : launch_split_cfg<128, true>(a, tmA, tmB, s, st);
+        rc = bn == 256   ? launch_split_cfg<256, kModeF64Tmem>(a, tmA, tmB, s, st)
+             : bn == 192 ? launch_split_cfg<192, kModeF64Reg>(a, tmA, tmB, s, st)
+                         : launch_split_cfg<128, kModeF64Reg>(a, tmA, tmB, s, st);
     else
-        rc = bn == 256 ? launch_split_cfg<256, false>(a, tmA, tmB, s, st)
-                       : launch_split_cfg<128, false>(a, tmA, tmB, s, st);
+        rc = bn == 256 ? launch_split_cfg<256, kModeF32>(a, tmA, tmB, s, st)
+                       : launch_split_cfg<128, kModeF32>(a, tmA, tmB, s, st);
     if (st) {
         st->slices = S;
         st->products = dt == MOA_F32_SPLIT ? 6 : S * (S + 1) / 2;

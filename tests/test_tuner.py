@@ -88,7 +88,7 @@ def test_tuner_records_and_reuses_choice(L, tmp_path):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("dt,widths", [(moa.MOA_F32_SPLIT, (128, 256)),
-                                       (moa.MOA_F64_SPLIT_F32IN, (128, 192))])
+                                       (moa.MOA_F64_SPLIT_F32IN, (128, 192, 256))])
 def test_split_tile_widths_agree(L, dt, widths):
     """Every slice-GEMM tile width sums the same chunks in the same order, so
     the results are bit-identical; each is within the mode's tolerance."""
@@ -105,7 +105,8 @@ def test_split_tile_widths_agree(L, dt, widths):
             outs.append(C)
     finally:
         L.moa_set_block_n(0)
-    assert torch.equal(outs[0], outs[1])
+    for o in outs[1:]:
+        assert torch.equal(outs[0], o)
     ref = oracle.gemm(A.double().cpu().numpy(), B.double().cpu().numpy())
     got = outs[1].double().cpu().numpy()
     tol = 1e-5 if dt == moa.MOA_F32_SPLIT else 1e-12
