@@ -217,6 +217,29 @@ def in_dtype(dt: int):
     return torch.float32
 
 
+def check_tensors(A, B, C, dt):
+    """Refuses operands whose dtype, device, layout or shape do not match the
+    mode: the C ABI receives raw pointers and reads exactly what the mode
+    implies (e.g. 8 bytes per element for FP64 inputs)."""
+    import torch
+    ind, outd = in_dtype(dt), out_dtype(dt)
+    if A.dtype != ind or B.dtype != ind:
+        raise TypeError(f"mode {dt} needs {ind} A and B, got {A.dtype} and {B.dtype}")
+    if C is not None and C.dtype != outd:
+        raise TypeError(f"mode {dt} writes {outd} C, got {C.dtype}")
+    for name, t in (("A", A), ("B", B), ("C", C)):
+        if t is None:
+            continue
+        if t.device.type != "cuda":
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dim() != 2 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous row-major matrix")
+    if A.shape[1] != B.shape[0]:
+        raise ValueError("A must be m x n and B n x p")
+    if C is not None and tuple(C.shape) != (A.shape[0], B.shape[1]):
+        raise ValueError("C must be m x p")
+
+
 class Workspace:
     """A growable device workspace owned by PyTorch (256-byte aligned)."""
 
@@ -243,10 +266,7 @@ def gemm(A, B, dt: int, C=None, slices: int = 0, stream=None, workspace: Workspa
          stats: bool = False):
     """C := A . B through moa_gemm_ex on torch CUDA tensors (row-major, contiguous)."""
     import torch
-    if A.dim() != 2 or B.dim() != 2 or A.shape[1] != B.shape[0]:
-        raise ValueError("A must be m x n and B n x p")
-    if not (A.is_contiguous() and B.is_contiguous()):
-        raise ValueError("A and B must be contiguous row-major tensors")
+    check_tensors(A, B, C, dt)
     m, n = A.shape
     p = B.shape[1]
     if C is None:
@@ -269,6 +289,7 @@ def make_descs(problems):
     """ctypes array of moa_gemm_desc from [(A, B, C, dt), ...] torch tensors."""
     arr = (moa_gemm_desc * len(problems))()
     for i, (A, B, C, dt) in enumerate(problems):
+        check_tensors(A, B, C, dt)
         arr[i].m, arr[i].n = A.shape
         arr[i].p = B.shape[1]
         arr[i].dt = dt

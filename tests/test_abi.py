@@ -108,3 +108,17 @@ def test_grouped_argument_errors(L):
     assert L.moa_gemm_grouped(-1, None, None, 0, None) == moa.MOA_ERR_ARG
     assert L.moa_gemm_grouped(0, None, None, 0, None) == moa.MOA_OK
     assert L.moa_gemm_grouped(2, None, None, 0, None) == moa.MOA_ERR_ARG
+
+
+def test_binding_refuses_mismatched_tensors(L):
+    import torch
+    A = torch.zeros((4, 8), dtype=torch.float32)
+    B = torch.zeros((8, 3), dtype=torch.float32)
+    with pytest.raises(TypeError):       # FP64-input mode reads 8 bytes per element
+        moa.check_tensors(A, B, None, moa.MOA_F64_SPLIT_F64IN)
+    with pytest.raises(TypeError):
+        moa.check_tensors(A, B, torch.zeros((4, 3), dtype=torch.float32), moa.MOA_F64_SPLIT_F32IN)
+    with pytest.raises(ValueError):      # CPU tensors are not device memory
+        moa.check_tensors(A, B, None, moa.MOA_F32_TF32)
+    with pytest.raises(ValueError):
+        moa.check_tensors(A, B[:5], None, moa.MOA_F32_TF32)
