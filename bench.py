@@ -436,7 +436,7 @@ def cpu_baseline(N, dtype_name, seconds_target=8.0):
                       f"rows), {dt:.2f} s", "host_cores": cores}
 
 
-def bench_grouped(steps, warmup, ws, stream, count=512):
+def bench_grouped(steps, warmup, ws, stream, count=512, compare=True):
     """Grouped batch: `count` BF16 GEMMs (m, n, p log-uniform in [32, 2048],
     multiples of 16, FP32 out) in one moa_gemm_grouped launch per step, and the
     same problems as `count` separate moa_gemm_ex launches."""
@@ -492,8 +492,10 @@ def bench_grouped(steps, warmup, ws, stream, count=512):
                                       w, wb, sh, None))
 
     nsep = max(2, steps // 2)
-    with torch.cuda.stream(stream):
-        t_sep = time_device(separate, nsep, 2, stream, ws)
+    t_sep = float("nan")
+    if compare:
+        with torch.cuda.stream(stream):
+            t_sep = time_device(separate, nsep, 2, stream, ws)
     return {"seconds": t, "kernel_seconds": kernel_s, "steps": steps, "flops_per_step": flops,
             "bytes_per_step": nbytes, "count": count,
             "separate_seconds_per_step": t_sep / nsep, "kernels_per_step": 1,
@@ -842,7 +844,7 @@ def main():
     clocks = ClockSampler(pci)
     clocks.start()
     if mode == "grouped":
-        main_res = bench_grouped(args.steps, args.warmup, ws, stream)
+        main_res = bench_grouped(args.steps, args.warmup, ws, stream, compare=not args.profile)
     else:
         main_res = bench_mode(mode, N, args.steps, args.warmup, ws, stream,
                               want_energy=not args.profile, energy=energy,
