@@ -716,22 +716,35 @@ def bench_tiles(stream, energy, sizes=(2048, 4096, 8192), modes=("bf16", "tf32")
 
 
 # ------------------------------------------------------------------ reference arm
+def square_metric_config(mode, N, ws):
+    """Metric name and config of the square workloads (shared by both arms)."""
+    metric = "GEMM TFLOP/s (FP32 ONF GEMM, TF32 tensor path)" if mode == "tf32" else \
+        f"GEMM TFLOP/s (ONF GEMM, {mode} path)"
+    config = {"workload": f"square ONF GEMM m=n=p={N}, row-major, seed 0, mode {mode}",
+              "N": N, "mode": mode, "parallelism": f"replicas x{ws}",
+              "l2": "inputs larger than L2 (3 x N^2 elements)"}
+    return metric, config
+
+
 def run_reference(args, ws, rank):
+    """Reference arm: the CPU oracle, as it stands, on the host cores; each
+    step is a bounded sample of rows of the same square problem."""
     if rank != 0:
         return
     N = args.n
+    mode = MODE_OF.get(args.workload, "tf32")
     per_step = []
     for _ in range(args.warmup):
         cpu_baseline(N, "f32", seconds_target=2.0)
     for _ in range(args.steps):
         per_step.append(cpu_baseline(N, "f32", seconds_target=4.0))
     v = sum(x["value"] for x in per_step) / len(per_step)
-    line = {"impl": "reference", "metric": "GEMM TFLOP/s", "value": v, "unit": "TFLOP/s",
+    metric, config = square_metric_config(mode, N, args.gpus)
+    config["arm"] = "CPU oracle (FP64 i-k-j loop, OpenMP over rows) on sampled rows"
+    line = {"impl": "reference", "metric": metric, "value": v, "unit": "TFLOP/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": f"square ONF GEMM N={N} (FP32 inputs), CPU oracle on "
-                                   "sampled rows", "N": N},
+            "data": "synthetic", "config": config,
             "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": per_step[0]["cores"],
                              "kind": "oracle", "sample": per_step[0]["sample"]},
             "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
@@ -927,11 +940,7 @@ def main():
                       "separate_tflops": main_res["flops_per_step"] /
                       main_res["separate_seconds_per_step"] / 1e12}
         else:
-            metric = "GEMM TFLOP/s (FP32 ONF GEMM, TF32 tensor path)" if mode == "tf32" else \
-                f"GEMM TFLOP/s (ONF GEMM, {mode} path)"
-            config = {"workload": f"square ONF GEMM m=n=p={N}, row-major, seed 0, mode {mode}",
-                      "N": N, "mode": mode, "parallelism": f"replicas x{ws}",
-                      "l2": "inputs larger than L2 (3 x N^2 elements)"}
+            metric, config = square_metric_config(mode, N, ws)
         line = {
             "metric": metric,
             "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
