@@ -258,13 +258,23 @@ def barrier(ws):
 
 
 def max_over_ranks(x, ws):
+    """Max of a per-rank time over all ranks (the only collective of the
+    benchmark; the GEMM itself is not sharded)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate(flops_per_step, steps, seconds, ws):
+    """Whole-job value for N replicas: total flops of all ranks over the
+    slowest rank's time (TFLOP/s)."""
+    t_max = max_over_ranks(seconds, ws)
+    return flops_per_step * steps * ws / t_max / 1e12, t_max
 
 
 # ------------------------------------------------------------------ workloads
@@ -864,9 +874,7 @@ def main():
                               want_e2e=not args.profile, check_rows=not args.profile)
     clk = clocks.stop()
 
-    t_max = max_over_ranks(main_res["seconds"], ws)
-    total_flops = main_res["flops_per_step"] * args.steps * ws
-    value = total_flops / t_max / 1e12
+    value, t_max = aggregate(main_res["flops_per_step"], args.steps, main_res["seconds"], ws)
     ms_per_step = t_max / args.steps * 1e3
 
     e2e = main_res.get("e2e", {})
