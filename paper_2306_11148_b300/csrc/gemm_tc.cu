@@ -295,7 +295,7 @@ int launch_cfg(int64_t m, int64_t n, int64_t p, const void* A, int64_t lda, cons
     args.tiles_m = static_cast<int>(ceil_div(m, Cfg::BLOCK_M));
     args.tiles_n = static_cast<int>(ceil_div(p, BLOCK_N));
     args.num_kb = static_cast<int>(ceil_div(n, Cfg::BK));
-    args.group_m = 16;
+    args.group_m = raster_group();
     args.vec_ok = (p % 4 == 0) && (reinterpret_cast<uintptr_t>(C) % 16 == 0);
     args.wait_limit_ns = wait_limit_ns();
     args.status = device_status_ptr();

@@ -53,6 +53,16 @@ int load_locked(const char* path) {
 
 int tile_override() { return t_override; }
 
+int raster_group() {
+    static int g = 0;
+    if (g == 0) {
+        const char* env = std::getenv("MOA_RASTER_GROUP");
+        const long v = env ? std::strtol(env, nullptr, 10) : 16;
+        g = static_cast<int>(v >= 1 && v <= 1024 ? v : 16);
+    }
+    return g;
+}
+
 int tuned_block_n(moa_dtype dt, int64_t m, int64_t n, int64_t p) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_loaded) {
