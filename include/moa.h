@@ -134,6 +134,25 @@ int moa_gemm_grouped(int count, const moa_gemm_desc* descs,
                      void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------- */
+/* Batched (3-D) contraction                                                */
+/* ---------------------------------------------------------------------- */
+
+/* C[b] := A[b] . B[b] for 0 <= b < batch: the contraction
+ *     C[b, i, j] = sum_k A[b, i, k] * B[b, k, j]
+ * the higher-dimensional extension of the inner product of Eq. (eq:dnf)
+ * (the paper's Appendix).  Entry b of each operand starts stride_x ELEMENTS
+ * after entry b - 1 (stride 0 broadcasts one A or B to every entry; C's
+ * stride must be >= m * p).  Each entry is row-major m x n, n x p, m x p in
+ * mode dt.  BF16 batches with 16-byte row pitches run as one persistent
+ * grouped launch; other modes one launch per entry.  Workspace as returned
+ * by moa_gemm_batched_workspace_size. */
+size_t moa_gemm_batched_workspace_size(int batch, int64_t m, int64_t n, int64_t p, moa_dtype dt,
+                                       int64_t stride_a, int64_t stride_b, int64_t stride_c);
+int moa_gemm_batched(int batch, int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A,
+                     int64_t stride_a, const void* B, int64_t stride_b, void* C, int64_t stride_c,
+                     void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------- */
 /* Tile widths of the dense tensor-core GEMMs (MOA_BF16, MOA_F32_TF32)       */
 /* ---------------------------------------------------------------------- */
 

@@ -552,3 +552,62 @@ int moa_gemm_grouped(int count, const moa_gemm_desc* d, void* ws, size_t ws_byte
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ batched
+// moa_gemm_batched: C[b] := A[b] . B[b] for b < batch, the 3-D contraction
+// C[b, i, j] = sum_k A[b, i, k] B[b, k, j] (the Appendix's higher-dimensional
+// extension of the inner product), with element strides between the batch
+// entries (stride 0 broadcasts one operand).  Built on the grouped path: BF16
+// batches are one persistent launch, other modes one launch per entry.
+namespace moa {
+namespace {
+int batched_descs(int batch, int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A,
+                  int64_t sa, const void* B, int64_t sb, void* C, int64_t sc,
+                  std::vector<moa_gemm_desc>& d) {
+    if (batch < 0) return fail(MOA_ERR_ARG, "negative batch");
+    if (sa < 0 || sb < 0 || sc < 0) return fail(MOA_ERR_ARG, "negative stride");
+    if (dt < MOA_F64 || dt > MOA_F64_SPLIT_F64IN) return fail(MOA_ERR_DTYPE, "unknown dtype");
+    if (batch > 1 && m > 0 && p > 0 && sc < m * p)
+        return fail(MOA_ERR_ARG, "C stride smaller than m * p would overlap outputs");
+    const int ies = (dt == MOA_F64 || dt == MOA_F64_SPLIT_F64IN) ? 8 : (dt == MOA_BF16 ? 2 : 4);
+    const int oes = (dt == MOA_F64 || dt == MOA_F64_SPLIT_F32IN || dt == MOA_F64_SPLIT_F64IN) ? 8 : 4;
+    d.resize(static_cast<size_t>(batch));
+    for (int b = 0; b < batch; ++b) {
+        d[b].m = m;
+        d[b].n = n;
+        d[b].p = p;
+        d[b].dt = dt;
+        d[b].A = static_cast<const uint8_t*>(A) + static_cast<int64_t>(b) * sa * ies;
+        d[b].B = static_cast<const uint8_t*>(B) + static_cast<int64_t>(b) * sb * ies;
+        d[b].C = static_cast<uint8_t*>(C) + static_cast<int64_t>(b) * sc * oes;
+    }
+    return MOA_OK;
+}
+}  // namespace
+}  // namespace moa
+
+extern "C" {
+
+size_t moa_gemm_batched_workspace_size(int batch, int64_t m, int64_t n, int64_t p, moa_dtype dt,
+                                       int64_t stride_a, int64_t stride_b, int64_t stride_c) {
+    std::vector<moa_gemm_desc> d;
+    // only the shapes and alignments matter for the size: use aligned stand-in pointers
+    if (moa::batched_descs(batch, m, n, p, dt, reinterpret_cast<void*>(256), stride_a,
+                           reinterpret_cast<void*>(256), stride_b, reinterpret_cast<void*>(256),
+                           stride_c, d) != MOA_OK || batch == 0)
+        return 0;
+    return moa::grouped_workspace(batch, d.data());
+}
+
+int moa_gemm_batched(int batch, int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A,
+                     int64_t stride_a, const void* B, int64_t stride_b, void* C, int64_t stride_c,
+                     void* ws, size_t ws_bytes, void* stream) {
+    std::vector<moa_gemm_desc> d;
+    const int rc = moa::batched_descs(batch, m, n, p, dt, A, stride_a, B, stride_b, C, stride_c, d);
+    if (rc != MOA_OK) return rc;
+    if (batch == 0) return MOA_OK;
+    return moa::grouped_launch(batch, d.data(), ws, ws_bytes, static_cast<cudaStream_t>(stream),
+                               true);
+}
+
+}  // extern "C"

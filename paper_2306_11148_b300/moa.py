@@ -127,6 +127,10 @@ EXPORTS = {
     "moa_profile_events": (ctypes.c_int, [_vp, _vp]),
     "moa_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_uint64, _vp]),
     "moa_set_block_n": (ctypes.c_int, [ctypes.c_int]),
+    "moa_gemm_batched_workspace_size": (_sz, [ctypes.c_int, _i64, _i64, _i64, ctypes.c_int, _i64,
+                                              _i64, _i64]),
+    "moa_gemm_batched": (ctypes.c_int, [ctypes.c_int, _i64, _i64, _i64, ctypes.c_int, _vp, _i64,
+                                        _vp, _i64, _vp, _i64, _vp, _sz, _vp]),
     "moa_tune_dense": (ctypes.c_int, [_i64, _i64, _i64, ctypes.c_int, _vp, _vp, _vp, _vp, _sz, _vp,
                                       ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_float)]),
@@ -358,3 +362,34 @@ class Server:
         if self.h:
             check(lib().moa_serve_destroy(self.h))
             self.h = ctypes.c_void_p()
+
+
+def gemm_batched(A, B, dt: int, C=None, stream=None, workspace: Workspace | None = None):
+    """C[b] := A[b] . B[b] for 3-D torch tensors (batch x m x n, batch x n x p);
+    a 2-D A or B is broadcast to every entry (stride 0)."""
+    import torch
+    a3 = A if A.dim() == 3 else A.unsqueeze(0)
+    b3 = B if B.dim() == 3 else B.unsqueeze(0)
+    batch = max(a3.shape[0], b3.shape[0])
+    m, n = a3.shape[1:]
+    p = b3.shape[2]
+    if b3.shape[1] != n:
+        raise ValueError("inner dimensions differ")
+    for t, name in ((a3, "A"), (b3, "B")):
+        if t.shape[0] not in (1, batch):
+            raise ValueError(f"{name} batch must be 1 or {batch}")
+        if t.dtype != in_dtype(dt) or not t.is_contiguous() or t.device.type != "cuda":
+            raise TypeError(f"{name} must be a contiguous CUDA {in_dtype(dt)} tensor")
+    sa = 0 if a3.shape[0] == 1 else m * n
+    sb = 0 if b3.shape[0] == 1 else n * p
+    if C is None:
+        C = torch.empty((batch, m, p), dtype=out_dtype(dt), device=A.device)
+    if C.shape != (batch, m, p) or C.dtype != out_dtype(dt) or not C.is_contiguous():
+        raise ValueError("C must be a contiguous batch x m x p tensor of the mode's output dtype")
+    if workspace is None:
+        workspace = _default_ws.setdefault(A.device, Workspace(A.device))
+    need = int(lib().moa_gemm_batched_workspace_size(batch, m, n, p, dt, sa, sb, m * p))
+    ws, wsb = workspace.get(need)
+    check(lib().moa_gemm_batched(batch, m, n, p, dt, _ptr(a3), sa, _ptr(b3), sb, _ptr(C), m * p,
+                                 ws, wsb, _stream_handle(stream)))
+    return C
