@@ -134,6 +134,23 @@ int moa_gemm_grouped(int count, const moa_gemm_desc* descs,
                      void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------- */
+/* The other products of the inner/outer-product family (paper's Appendix) */
+/* ---------------------------------------------------------------------- */
+
+/* Kronecker product C := A (x) B: A is m x n, B is p x q, C is (m*p) x (n*q),
+ * all row-major, C[(i*p)+k, (j*q)+l] = A[i,j] * B[k,l] (one rounding per
+ * element).  dt: MOA_F64 (FP64 in/out), MOA_F32_TF32 or MOA_F32_SIMT (FP32
+ * in/out, plain FP32 products), MOA_BF16 (BF16 in, FP32 out, exact).
+ * Asynchronous on `stream`.  MOA_ERR_DTYPE for other modes. */
+int moa_kronecker(int64_t m, int64_t n, int64_t p, int64_t q, moa_dtype dt, const void* A,
+                  const void* B, void* C, void* stream);
+
+/* Hadamard product C := A o B of two m x n arrays: C[i,j] = A[i,j] * B[i,j];
+ * dtypes as for moa_kronecker.  Asynchronous on `stream`. */
+int moa_hadamard(int64_t m, int64_t n, moa_dtype dt, const void* A, const void* B, void* C,
+                 void* stream);
+
+/* ---------------------------------------------------------------------- */
 /* Batched (3-D) contraction                                                */
 /* ---------------------------------------------------------------------- */
 

@@ -19,6 +19,8 @@ Functions and the passages they follow:
 * :func:`split3_bf16` -- FP32-accuracy slicing (not in the paper).
 * :func:`slice_fixed` -- FP64-accuracy integer-digit slicing (not in the paper).
 * :func:`split_gemm_exact` -- the exact value the digit-slice product reaches.
+* :func:`kronecker`, :func:`hadamard` -- the Appendix's other products of the
+  inner/outer-product family.
 """
 from __future__ import annotations
 
@@ -75,6 +77,10 @@ def _load():
                                                         _ptr, _ptr, ctypes.c_int,
                                                         ctypes.c_int, _ptr]
             lib.moa_oracle_split_gemm_exact.restype = None
+            lib.moa_oracle_kronecker_f64.argtypes = [_i64, _i64, _i64, _i64, _ptr, _ptr, _ptr]
+            lib.moa_oracle_kronecker_f64.restype = None
+            lib.moa_oracle_hadamard_f64.argtypes = [_i64, _i64, _ptr, _ptr, _ptr]
+            lib.moa_oracle_hadamard_f64.restype = None
             _lib = lib
     return _lib
 
@@ -166,4 +172,26 @@ def split_gemm_exact(dA, eA, dB, eB, beta: int, S: int) -> np.ndarray:
     C = np.empty((m, p), dtype=np.float64)
     _load().moa_oracle_split_gemm_exact(m, n, p, _p(dA), _p(eA), _p(dB), _p(eB),
                                         int(beta), int(S), _p(C))
+    return C
+
+
+def kronecker(A, B) -> np.ndarray:
+    """C[(i*p)+k, (j*q)+l] = A[i,j] * B[k,l] in FP64."""
+    A = _f64(A)
+    B = _f64(B)
+    m, n = A.shape
+    p, q = B.shape
+    C = np.empty((m * p, n * q), dtype=np.float64)
+    _load().moa_oracle_kronecker_f64(m, n, p, q, _p(A), _p(B), _p(C))
+    return C
+
+
+def hadamard(A, B) -> np.ndarray:
+    """C[i,j] = A[i,j] * B[i,j] in FP64."""
+    A = _f64(A)
+    B = _f64(B)
+    if A.shape != B.shape:
+        raise ValueError("shapes differ")
+    C = np.empty(A.shape, dtype=np.float64)
+    _load().moa_oracle_hadamard_f64(A.shape[0], A.shape[1], _p(A), _p(B), _p(C))
     return C

@@ -16,12 +16,16 @@
  *   moa_oracle_split3_bf16     precision slicing, FP32-accuracy mode (not in the paper)
  *   moa_oracle_slice_fixed     precision slicing, FP64-accuracy mode (not in the paper)
  *   moa_oracle_split_gemm_exact  the value the FP64-accuracy slice method reaches
+ *   moa_oracle_kronecker_f64   Kronecker product (Appendix: outer product, no reduction)
+ *   moa_oracle_hadamard_f64    Hadamard product (Appendix: diagonal of the outer product)
  *
  * Parity status: the GEMM functions are pinned by exact-integer, identity,
  * permutation, transpose, associativity and exact-rational (Higham bound)
  * tests.  The slicing functions are pinned by exact reconstruction, range and
  * library-rounding tests.  moa_oracle_split_gemm_exact is pinned against the
- * GEMM oracle within the slicing error bound.
+ * GEMM oracle within the slicing error bound.  The Kronecker and Hadamard
+ * products are pinned by the mixed-product property, identities and the
+ * trace identity on integer inputs.
  */
 #include <stdint.h>
 #include <math.h>
@@ -240,4 +244,31 @@ void moa_oracle_split_gemm_exact(int64_t m, int64_t n, int64_t p,
             C[i * p + j] = neg ? -v : v;
         }
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* The other products of the inner/outer-product family (paper's Appendix). */
+/* With the outer product T[i,j,k,l] = A[i,j] * B[k,l]:                      */
+/*   Kronecker  C[(i*p)+k, (j*q)+l] = T[i,j,k,l]                             */
+/*   Hadamard   C[i,j] = T[i,j,i,j]                                          */
+/* ------------------------------------------------------------------------ */
+
+/* A m x n, B p x q, C (m*p) x (n*q), all row-major FP64. */
+void moa_oracle_kronecker_f64(int64_t m, int64_t n, int64_t p, int64_t q,
+                              const double* A, const double* B, double* C)
+{
+    const int64_t ncols = n * q;
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t k = 0; k < p; ++k)
+                for (int64_t l = 0; l < q; ++l)
+                    C[(i * p + k) * ncols + (j * q + l)] = A[i * n + j] * B[k * q + l];
+}
+
+/* C[i,j] = A[i,j] * B[i,j] over m x n arrays, FP64. */
+void moa_oracle_hadamard_f64(int64_t m, int64_t n, const double* A, const double* B, double* C)
+{
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t j = 0; j < n; ++j)
+            C[i * n + j] = A[i * n + j] * B[i * n + j];
 }

@@ -127,6 +127,8 @@ EXPORTS = {
     "moa_profile_events": (ctypes.c_int, [_vp, _vp]),
     "moa_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_uint64, _vp]),
     "moa_set_block_n": (ctypes.c_int, [ctypes.c_int]),
+    "moa_kronecker": (ctypes.c_int, [_i64, _i64, _i64, _i64, ctypes.c_int, _vp, _vp, _vp, _vp]),
+    "moa_hadamard": (ctypes.c_int, [_i64, _i64, ctypes.c_int, _vp, _vp, _vp, _vp]),
     "moa_gemm_batched_workspace_size": (_sz, [ctypes.c_int, _i64, _i64, _i64, ctypes.c_int, _i64,
                                               _i64, _i64]),
     "moa_gemm_batched": (ctypes.c_int, [ctypes.c_int, _i64, _i64, _i64, ctypes.c_int, _vp, _i64,
@@ -392,4 +394,31 @@ def gemm_batched(A, B, dt: int, C=None, stream=None, workspace: Workspace | None
     ws, wsb = workspace.get(need)
     check(lib().moa_gemm_batched(batch, m, n, p, dt, _ptr(a3), sa, _ptr(b3), sb, _ptr(C), m * p,
                                  ws, wsb, _stream_handle(stream)))
+    return C
+
+
+def kronecker(A, B, dt: int, stream=None):
+    """C := A (x) B ((m*p) x (n*q)) through moa_kronecker."""
+    import torch
+    for t, name in ((A, "A"), (B, "B")):
+        if t.dtype != in_dtype(dt) or t.dim() != 2 or not t.is_contiguous() or t.device.type != "cuda":
+            raise TypeError(f"{name} must be a contiguous 2-D CUDA {in_dtype(dt)} tensor")
+    m, n = A.shape
+    p, q = B.shape
+    C = torch.empty((m * p, n * q), dtype=out_dtype(dt), device=A.device)
+    check(lib().moa_kronecker(m, n, p, q, dt, _ptr(A), _ptr(B), _ptr(C), _stream_handle(stream)))
+    return C
+
+
+def hadamard(A, B, dt: int, stream=None):
+    """C := A o B through moa_hadamard."""
+    import torch
+    if A.shape != B.shape:
+        raise ValueError("Hadamard operands must have the same shape")
+    for t, name in ((A, "A"), (B, "B")):
+        if t.dtype != in_dtype(dt) or t.dim() != 2 or not t.is_contiguous() or t.device.type != "cuda":
+            raise TypeError(f"{name} must be a contiguous 2-D CUDA {in_dtype(dt)} tensor")
+    C = torch.empty(A.shape, dtype=out_dtype(dt), device=A.device)
+    check(lib().moa_hadamard(A.shape[0], A.shape[1], dt, _ptr(A), _ptr(B), _ptr(C),
+                             _stream_handle(stream)))
     return C

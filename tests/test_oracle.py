@@ -416,3 +416,47 @@ def test_slice_fixed_matches_exact_rational_route():
             for c in range(X.shape[1]):
                 want = _digits_by_fractions(X[r, c], int(exps[r]), beta, S)
                 assert [int(digits[s, r, c]) for s in range(S)] == want
+
+
+# --------------------------------------------------------------------------
+# Kronecker and Hadamard products (the Appendix's product family).
+# --------------------------------------------------------------------------
+
+def test_kronecker_mixed_product_property():
+    # (A (x) B)(C (x) D) = (A C) (x) (B D), exact on small integers
+    rng = np.random.default_rng(31)
+    A = rng.integers(-3, 4, (3, 4)).astype(float)
+    Cm = rng.integers(-3, 4, (4, 2)).astype(float)
+    B = rng.integers(-3, 4, (2, 5)).astype(float)
+    D = rng.integers(-3, 4, (5, 3)).astype(float)
+    lhs = oracle.gemm(oracle.kronecker(A, B), oracle.kronecker(Cm, D))
+    rhs = oracle.kronecker(oracle.gemm(A, Cm), oracle.gemm(B, D))
+    assert np.array_equal(lhs, rhs)
+
+
+def test_kronecker_identities_and_layout():
+    assert np.array_equal(oracle.kronecker(np.eye(3), np.eye(4)), np.eye(12))
+    A = np.array([[1.0, 2.0], [3.0, 4.0]])
+    B = np.array([[0.0, 5.0], [6.0, 7.0]])
+    # block (i, j) of A (x) B is A[i, j] * B
+    K = oracle.kronecker(A, B)
+    for i in range(2):
+        for j in range(2):
+            assert np.array_equal(K[2 * i:2 * i + 2, 2 * j:2 * j + 2], A[i, j] * B)
+    # a 1 x 1 factor is a scalar multiple
+    assert np.array_equal(oracle.kronecker(np.array([[3.0]]), B), 3.0 * B)
+
+
+def test_hadamard_identities():
+    rng = np.random.default_rng(32)
+    A = rng.integers(-8, 9, (7, 9)).astype(float)
+    B = rng.integers(-8, 9, (7, 9)).astype(float)
+    assert np.array_equal(oracle.hadamard(A, B), oracle.hadamard(B, A))
+    assert np.array_equal(oracle.hadamard(A, np.ones_like(A)), A)
+    # sum of all entries of A o B = trace(A^T B), exact on integers
+    assert oracle.hadamard(A, B).sum() == np.trace(oracle.gemm(A.T.copy(), B))
+    # one rounding per element
+    x = rng.uniform(-1, 1, (3, 4))
+    y = rng.uniform(-1, 1, (3, 4))
+    h = oracle.hadamard(x, y)
+    assert all(h[i, j] == float(x[i, j]) * float(y[i, j]) for i in range(3) for j in range(4))
