@@ -372,7 +372,7 @@ def bench_mode(mode, N, steps, warmup, ws, stream, want_energy=False, energy=Non
             out["energy"] = {"j_per_gemm": (j1 - j0) / reps, "window_s": t1 - t0, "reps": reps,
                              "avg_w": (j1 - j0) / (t1 - t0)}
     if want_e2e:
-        out["e2e"] = bench_e2e(dt, A, B, C, N, max(2, min(steps, 5)), 1, stream, ws)
+        out["e2e"] = bench_e2e(dt, A, B, C, N, max(4, min(steps, 8)), 2, stream, ws)
     # oracle spot check of a few rows (cheap) to tie the timed output to parity
     try:
         if not check_rows:
@@ -391,31 +391,60 @@ def bench_mode(mode, N, steps, warmup, ws, stream, want_energy=False, energy=Non
 
 
 def bench_e2e(dt, A, B, C, N, steps, warmup, stream, ws):
-    """Same GEMM through the C ABI with host buffers: H2D of A and B from pinned
-    memory, the GEMM, and D2H of C, all inside the timed region."""
+    """Same GEMM through the C ABI with host buffers: every step copies its A
+    and B from pinned host memory to the device, runs the GEMM and copies C
+    back to pinned host memory, all inside the timed region.  Independent
+    steps alternate between two streams with their own device buffers, so one
+    step's host-to-device copy overlaps the previous step's GEMM and
+    device-to-host copy (separate copy engines)."""
     import torch
     from paper_2306_11148_b300 import moa
     Ah = A.pin_memory()
     Bh = B.pin_memory()
-    Ch = torch.empty(C.shape, dtype=C.dtype, pin_memory=True)
-    Ad = torch.empty_like(A, device="cuda")
-    Bd = torch.empty_like(B, device="cuda")
-    wspace = moa.Workspace(torch.device("cuda"))
-    wptr, wbytes = wspace.get(moa.moa_gemm_workspace_size(N, N, N, dt, 0))
-    sh = int(stream.cuda_stream)
+    lanes = []
+    for _ in range(2):
+        st = torch.cuda.Stream()
+        Ad = torch.empty_like(A, device="cuda")
+        Bd = torch.empty_like(B, device="cuda")
+        Cd = torch.empty_like(C)
+        Ch = torch.empty(C.shape, dtype=C.dtype, pin_memory=True)
+        wsp = moa.Workspace(torch.device("cuda"))
+        w, wb = wsp.get(moa.moa_gemm_workspace_size(N, N, N, dt, 0))
+        lanes.append((st, Ad, Bd, Cd, Ch, wsp, w, wb))
+    idx = [0]
 
     def step():
-        Ad.copy_(Ah, non_blocking=True)
-        Bd.copy_(Bh, non_blocking=True)
-        moa.check(moa.moa_gemm_ex(N, N, N, dt, Ad.data_ptr(), Bd.data_ptr(), C.data_ptr(), 0,
-                                  wptr, wbytes, sh, None))
-        Ch.copy_(C, non_blocking=True)
+        st, Ad, Bd, Cd, Ch, _, w, wb = lanes[idx[0] % 2]
+        idx[0] += 1
+        with torch.cuda.stream(st):
+            Ad.copy_(Ah, non_blocking=True)
+            Bd.copy_(Bh, non_blocking=True)
+            moa.check(moa.moa_gemm_ex(N, N, N, dt, Ad.data_ptr(), Bd.data_ptr(), Cd.data_ptr(), 0,
+                                      w, wb, int(st.cuda_stream), None))
+            Ch.copy_(Cd, non_blocking=True)
 
-    with torch.cuda.stream(stream):
-        t = time_device(step, steps, warmup, stream, ws)
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev0.record(lanes[0][0])
+    lanes[1][0].wait_event(ev0)
+    for _ in range(steps):
+        step()
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev2 = torch.cuda.Event(enable_timing=True)
+    ev1.record(lanes[0][0])
+    ev2.record(lanes[1][0])
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t0
+    t = max(ev0.elapsed_time(ev1), ev0.elapsed_time(ev2)) / 1000.0
+    barrier(ws)
     h2d = A.numel() * A.element_size() + B.numel() * B.element_size()
     d2h = C.numel() * C.element_size()
-    return {"seconds": t, "steps": steps, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    return {"seconds": t, "wall_seconds": t_wall, "steps": steps, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "streams": 2}
 
 
 def cpu_baseline(N, dtype_name, seconds_target=8.0):
@@ -557,7 +586,7 @@ def serve_pool(pool_size=64, ring=8, seed=0):
     return pool, cring
 
 
-def bench_serve(pool, cring, rate, seconds, seed=0):
+def bench_serve(pool, cring, rate, seconds, seed=0, energy=None):
     """Serving stream: Poisson arrivals at `rate` for `seconds` through one
     server (64 GB arena, 32 in flight, 8 streams, 2 s queue deadline).
     Arrival i uses pool entry i % len(pool) and the next of its output
@@ -569,11 +598,13 @@ def bench_serve(pool, cring, rate, seconds, seed=0):
     arrivals = [(a[0], i % len(pool)) for i, a in enumerate(arr)]
     srv = moa.Server(arena_bytes=64 << 30, max_inflight=32, n_streams=8,
                      queue_capacity=len(pool) * ring // 2 - 32, queue_deadline_s=2.0)
+    j0 = energy.read_j() if energy else None
     try:
         codes, got, wall = serve_run(srv, pool, arrivals, cring)
         st = srv.stats()
     finally:
         srv.close()
+    j1 = energy.read_j() if energy else None
     done_ok = [c for c in got.values() if c[1] == moa.MOA_OK]
     flops = sum(pool[i][3] for rc, tk, i in codes if rc == moa.MOA_OK and tk in got
                 and got[tk][1] == moa.MOA_OK)
@@ -603,6 +634,9 @@ def bench_serve(pool, cring, rate, seconds, seed=0):
             "mean_ms": st["mean_ms"], "batches": st["batches"],
             "inflight_peak": st["inflight_peak"], "arena_peak_gb": st["arena_peak"] / 1e9,
             "tflops_served": flops / span / 1e12 if done_ok else 0.0, "wall_s": wall,
+            "j_per_request": (j1 - j0) / len(done_ok) if (j0 is not None and j1 is not None
+                                                           and done_ok) else None,
+            "avg_w": (j1 - j0) / wall if (j0 is not None and j1 is not None) else None,
             "alone_vs_mix_checked": checked, "alone_vs_mix_mismatch": mism}
 
 
@@ -837,14 +871,14 @@ def main():
         pool, cring = serve_pool()
         clocks = ClockSampler(pci)
         clocks.start()
-        sat = bench_serve(pool, cring, args.serve_rate, args.serve_seconds)
+        sat = bench_serve(pool, cring, args.serve_rate, args.serve_seconds, energy=energy)
         sweep = []
         for r in args.serve_sweep:
-            sweep.append(bench_serve(pool, cring, r, args.serve_seconds))
+            sweep.append(bench_serve(pool, cring, r, args.serve_seconds, energy=energy))
         clk = clocks.stop()
         # capacity: the highest served rate seen; a run at ~70 % of it
         cap = max([sat["served_per_s"]] + [x["served_per_s"] for x in sweep])
-        light = bench_serve(pool, cring, 0.7 * cap, args.serve_seconds) \
+        light = bench_serve(pool, cring, 0.7 * cap, args.serve_seconds, energy=energy) \
             if args.serve_sweep else None
         if rank == 0:
             line = {"metric": "served GEMM requests/s (continuous batching), p50/p99 latency",
