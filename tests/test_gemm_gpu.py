@@ -185,3 +185,33 @@ def test_full_size_sampled_rows(dt, N):
     got = C[torch.from_numpy(rows).cuda()].cpu().double().numpy()
     ref = oracle.gemm_rows(A.double().numpy(), B.double().numpy(), rows)
     assert _rel(got, ref) <= TOL[dt]
+
+
+@pytest.mark.parametrize("dt", [moa.MOA_BF16, moa.MOA_F32_TF32, moa.MOA_F32_SPLIT,
+                                moa.MOA_F64_SPLIT_F32IN], ids=lambda d: NAMES[d])
+@pytest.mark.parametrize("m,n,p", [(1, 8192, 8192), (8192, 1, 8192), (8192, 8192, 1),
+                                   (2, 3, 16384), (16384, 7, 5)])
+def test_extreme_aspect_ratios(dt, m, n, p):
+    """Single-row, single-column and K = 1 problems: one ragged tile edge in
+    each direction; rows sampled against the oracle."""
+    A, B = inputs.normal_pair(m, n, p, dtype=moa.in_dtype(dt), seed=m + n + p)
+    C = moa.gemm(A.cuda(), B.cuda(), dt)
+    moa.sync_status()
+    rows = inputs.sample_rows(m, 16)
+    got = C[torch.from_numpy(rows).cuda()].cpu().double().numpy()
+    ref = oracle.gemm_rows(A.double().numpy(), B.double().numpy(), rows)
+    assert _rel(got, ref) <= TOL[dt]
+
+
+@pytest.mark.parametrize("dt", [moa.MOA_F32_TF32, moa.MOA_F64_SPLIT_F64IN], ids=lambda d: NAMES[d])
+def test_largest_square_size(dt):
+    """N = 16384, the largest size of the square sweep (FP64 operands: 3 x 2 GiB),
+    on 8 sampled rows."""
+    N = 16384
+    A, B = inputs.square_uniform(N, moa.in_dtype(dt), seed=0)
+    C = moa.gemm(A.cuda(), B.cuda(), dt)
+    moa.sync_status()
+    rows = inputs.sample_rows(N, 8)
+    got = C[torch.from_numpy(rows).cuda()].cpu().double().numpy()
+    ref = oracle.gemm_omp(A[torch.from_numpy(rows)].double().numpy(), B.double().numpy())[0]
+    assert _rel(got, ref) <= TOL[dt]
