@@ -42,29 +42,63 @@ namespace moa {
 // ====================================================================== pre-passes
 namespace {
 
-// FP32 -> three BF16 slices, zero-padded to row pitch ld; flags NaN/Inf (and
-// values whose leading slice overflows BF16) in the status word.
+__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    return static_cast<uint32_t>(__bfloat16_as_ushort(lo)) |
+           (static_cast<uint32_t>(__bfloat16_as_ushort(hi)) << 16);
+}
+
+// Loads X[r, c0 .. c0+7] (zero past `cols`); 16-byte loads when allowed.
+__device__ __forceinline__ void load8(const float* __restrict__ X, int64_t r, int64_t cols,
+                                      int64_t c0, bool vec, float (&x)[8]) {
+    const float* src = X + r * cols + c0;
+    if (vec && c0 + 8 <= cols) {
+        const float4 a = reinterpret_cast<const float4*>(src)[0];
+        const float4 b = reinterpret_cast<const float4*>(src)[1];
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+        x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = (c0 + i < cols) ? src[i] : 0.f;
+    }
+}
+
+// FP32 -> three BF16 slices, zero-padded to row pitch ld (a multiple of 8);
+// 8 consecutive elements per thread, one 16-byte store per slice plane.
+// Flags NaN/Inf (and values whose leading slice overflows BF16) in the
+// status word.
 __global__ void split3_kernel(const float* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
-                              __nv_bfloat16* __restrict__ out, int64_t plane, int* status) {
-    const int64_t total = rows * ld;
+                              __nv_bfloat16* __restrict__ out, int64_t plane, int vec, int* status) {
+    const int64_t gpr = ld / 8;                 // 8-element groups per row
+    const int64_t total = rows * gpr;
     bool bad = false;
-    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
-         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t r = e / ld, c = e - r * ld;
-        __nv_bfloat16 s0 = __float2bfloat16_rn(0.f), s1 = s0, s2 = s0;
-        if (c < cols) {
-            const float x = X[r * cols + c];
-            s0 = __float2bfloat16_rn(x);
-            const float a = __bfloat162float(s0);
-            const float r1 = __fsub_rn(x, a);
-            s1 = __float2bfloat16_rn(r1);
-            const float r2 = __fsub_rn(r1, __bfloat162float(s1));
-            s2 = __float2bfloat16_rn(r2);
-            bad |= !isfinite(x) || !isfinite(a);
+    for (int64_t g = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; g < total;
+         g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t r = g / gpr, c0 = (g - r * gpr) * 8;
+        float x[8];
+        load8(X, r, cols, c0, vec != 0, x);
+        uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) {
+            __nv_bfloat16 a[2], b[2], c[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float v = x[i + h];
+                a[h] = __float2bfloat16_rn(v);
+                const float av = __bfloat162float(a[h]);
+                const float r1 = __fsub_rn(v, av);
+                b[h] = __float2bfloat16_rn(r1);
+                const float r2 = __fsub_rn(r1, __bfloat162float(b[h]));
+                c[h] = __float2bfloat16_rn(r2);
+                bad |= !isfinite(v) || !isfinite(av);
+            }
+            w0[i / 2] = pack_bf16x2(a[0], a[1]);
+            w1[i / 2] = pack_bf16x2(b[0], b[1]);
+            w2[i / 2] = pack_bf16x2(c[0], c[1]);
         }
-        out[e] = s0;
-        out[plane + e] = s1;
-        out[2 * plane + e] = s2;
+        const int64_t o = r * ld + c0;
+        *reinterpret_cast<uint4*>(out + o) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+        *reinterpret_cast<uint4*>(out + plane + o) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+        *reinterpret_cast<uint4*>(out + 2 * plane + o) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
     }
     if (bad) atomicCAS(status, kDevOk, kDevNonFinite);
 }
@@ -212,30 +246,51 @@ __global__ void col_exp_kernel(const typename Bits<T>::U* __restrict__ cmax, int
     e_out[c] = B::frexp_exp(M);
 }
 
-// Integer digits of every element into S BF16 planes (row pitch ld, zero pad).
-// axis 0: exponent per row (e[r]); axis 1: per column (e[c]).
+// Integer digits of every element into S BF16 planes (row pitch ld, a
+// multiple of 8; zero pad); 8 consecutive elements per thread, one 16-byte
+// store per digit plane.  axis 0: exponent per row (e[r]); axis 1: per
+// column (e[c]).
 template <typename T>
 __global__ void digits_kernel(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
                               const int* __restrict__ e, int axis, int S,
                               __nv_bfloat16* __restrict__ out, int64_t plane) {
-    const int64_t total = rows * ld;
+    const int64_t gpr = ld / 8;
+    const int64_t total = rows * gpr;
     constexpr long long radix = 1ll << kBeta;
     constexpr long long half = radix / 2;
-    for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
-         idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int64_t r = idx / ld, c = idx - r * ld;
-        long long D = 0;
-        if (c < cols) {
-            const int ex = axis == 0 ? e[r] : e[c];
-            D = Bits<T>::round_scaled(X[r * cols + c], kBeta * S - ex);
+    for (int64_t g = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; g < total;
+         g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t r = g / gpr, c0 = (g - r * gpr) * 8;
+        long long D[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int64_t c = c0 + i;
+            D[i] = 0;
+            if (c < cols) {
+                const int ex = axis == 0 ? e[r] : e[c];
+                D[i] = Bits<T>::round_scaled(X[r * cols + c], kBeta * S - ex);
+            }
         }
-        for (int s = S - 1; s >= 1; --s) {
-            long long low = D & (radix - 1);
-            if (low >= half) low -= radix;
-            out[s * plane + idx] = __float2bfloat16_rn(static_cast<float>(low));
-            D = (D - low) >> kBeta;
+        const int64_t o = r * ld + c0;
+        for (int s = S - 1; s >= 0; --s) {
+            uint32_t w[4];
+#pragma unroll
+            for (int i = 0; i < 8; i += 2) {
+                __nv_bfloat16 d[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    long long low = D[i + h];
+                    if (s > 0) {
+                        low = D[i + h] & (radix - 1);
+                        if (low >= half) low -= radix;
+                        D[i + h] = (D[i + h] - low) >> kBeta;
+                    }
+                    d[h] = __float2bfloat16_rn(static_cast<float>(low));
+                }
+                w[i / 2] = pack_bf16x2(d[0], d[1]);
+            }
+            *reinterpret_cast<uint4*>(out + s * plane + o) = make_uint4(w[0], w[1], w[2], w[3]);
         }
-        out[idx] = __float2bfloat16_rn(static_cast<float>(D));
     }
 }
 
@@ -770,10 +825,12 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
     a.vec_ok = (p % 4 == 0) && (reinterpret_cast<uintptr_t>(C) % 16 == 0);
 
     if (dt == MOA_F32_SPLIT) {
-        split3_kernel<<<grid_for(a_plane, 256), 256, 0, s>>>(static_cast<const float*>(A), m, n,
-                                                             L.lda, a_sl, a_plane, status);
-        split3_kernel<<<grid_for(b_plane, 256), 256, 0, s>>>(static_cast<const float*>(B), n, p,
-                                                             L.ldb, b_sl, b_plane, status);
+        const int va = (n % 4 == 0) && (reinterpret_cast<uintptr_t>(A) % 16 == 0);
+        const int vb = (p % 4 == 0) && (reinterpret_cast<uintptr_t>(B) % 16 == 0);
+        split3_kernel<<<grid_for(a_plane / 8, 256), 256, 0, s>>>(
+            static_cast<const float*>(A), m, n, L.lda, a_sl, a_plane, va, status);
+        split3_kernel<<<grid_for(b_plane / 8, 256), 256, 0, s>>>(
+            static_cast<const float*>(B), n, p, L.ldb, b_sl, b_plane, vb, status);
         kernels += 2;
         a.f64 = 0;
         a.levels = 1;
@@ -802,9 +859,9 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
                                                          static_cast<unsigned long long*>(cmax));
             col_exp_kernel<double><<<static_cast<int>(ceil_div(p, 256)), 256, 0, s>>>(
                 static_cast<const unsigned long long*>(cmax), p, eB, status);
-            digits_kernel<double><<<grid_for(a_plane, 256), 256, 0, s>>>(Ad, m, n, L.lda, eA, 0, S,
+            digits_kernel<double><<<grid_for(a_plane / 8, 256), 256, 0, s>>>(Ad, m, n, L.lda, eA, 0, S,
                                                                           a_sl, a_plane);
-            digits_kernel<double><<<grid_for(b_plane, 256), 256, 0, s>>>(Bd, n, p, L.ldb, eB, 1, S,
+            digits_kernel<double><<<grid_for(b_plane / 8, 256), 256, 0, s>>>(Bd, n, p, L.ldb, eB, 1, S,
                                                                           b_sl, b_plane);
         } else {
             const float* Af = static_cast<const float*>(A);
@@ -814,9 +871,9 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
                                                         static_cast<unsigned int*>(cmax));
             col_exp_kernel<float><<<static_cast<int>(ceil_div(p, 256)), 256, 0, s>>>(
                 static_cast<const unsigned int*>(cmax), p, eB, status);
-            digits_kernel<float><<<grid_for(a_plane, 256), 256, 0, s>>>(Af, m, n, L.lda, eA, 0, S,
+            digits_kernel<float><<<grid_for(a_plane / 8, 256), 256, 0, s>>>(Af, m, n, L.lda, eA, 0, S,
                                                                         a_sl, a_plane);
-            digits_kernel<float><<<grid_for(b_plane, 256), 256, 0, s>>>(Bf, n, p, L.ldb, eB, 1, S,
+            digits_kernel<float><<<grid_for(b_plane / 8, 256), 256, 0, s>>>(Bf, n, p, L.ldb, eB, 1, S,
                                                                         b_sl, b_plane);
         }
         kernels += 6;
