@@ -298,7 +298,7 @@ int launch_cfg(int64_t m, int64_t n, int64_t p, const void* A, int64_t lda, cons
     args.group_m = raster_group();
     args.vec_ok = (p % 4 == 0) && (reinterpret_cast<uintptr_t>(C) % 16 == 0);
     args.wait_limit_ns = wait_limit_ns();
-    args.status = device_status_ptr();
+    args.status = launch_status_ptr();
     if (!args.status) return MOA_ERR_CUDA;
 
     auto kern = dense_tc_kernel<ESIZE, BLOCK_N, STAGES, BKM>;

@@ -365,7 +365,7 @@ int launch_kernel(uint8_t* dev, const Layout& L, int grid, cudaStream_t s) {
     a.tiles = reinterpret_cast<const int4*>(dev + L.tiles_off);
     a.cta_begin = reinterpret_cast<const int*>(dev + L.begin_off);
     a.wait_limit_ns = wait_limit_ns();
-    a.status = device_status_ptr();
+    a.status = launch_status_ptr();
     if (!a.status) return MOA_ERR_CUDA;
     static bool attr_set = false;
     if (!attr_set) {

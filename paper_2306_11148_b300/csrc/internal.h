@@ -24,6 +24,11 @@ void prof_end(cudaStream_t s);
 
 // Per-device status word (device address), created on first use.
 int* device_status_ptr();
+// Status word the kernels launched by this thread record into: the
+// per-device word, unless a caller (the serving loop) set a per-request
+// slot with set_status_override (nullptr restores the default).
+int* launch_status_ptr();
+void set_status_override(int* p);
 uint64_t wait_limit_ns();
 int num_sms();
 

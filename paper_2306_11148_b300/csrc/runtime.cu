@@ -26,6 +26,7 @@ int* g_status[kMaxDevices] = {nullptr};
 int g_sms[kMaxDevices] = {0};
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 thread_local cudaEvent_t g_prof_start = nullptr;
+thread_local int* t_status_override = nullptr;
 thread_local cudaEvent_t g_prof_stop = nullptr;
 
 int current_device() {
@@ -76,6 +77,12 @@ int* device_status_ptr() {
     }
     return g_status[d];
 }
+
+int* launch_status_ptr() {
+    return t_status_override ? t_status_override : device_status_ptr();
+}
+
+void set_status_override(int* p) { t_status_override = p; }
 
 int num_sms() {
     const int d = current_device();

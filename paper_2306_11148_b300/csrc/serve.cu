@@ -14,6 +14,11 @@
 // the device.  A host callback on the stream timestamps each completion and
 // hands it back to the scheduler, which frees its arena block and publishes
 // the completion to moa_serve_poll.  Latency = completion - submission.
+// Every request also gets its own device status slot (after its workspace in
+// the arena): its kernels record a pipeline timeout or a non-finite split
+// input there instead of in the per-device word, the slot is copied back
+// before the completion callback, and the request completes with
+// MOA_ERR_TIMEOUT / MOA_ERR_NONFINITE accordingly.
 //
 // Each GEMM is Eq. (eq:dnf) of Sec. 2, computed by the same kernels as a
 // moa_gemm_ex call with the same arguments, so a result does not depend on
@@ -31,6 +36,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "ptx.cuh"
 
 namespace moa {
 int gemm_ex(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const void* B, void* C,
@@ -106,7 +112,8 @@ class Arena {
 struct Request {
     uint64_t ticket = 0;
     moa_gemm_desc d{};
-    size_t ws_bytes = 0, ws_off = 0;
+    size_t ws_bytes = 0, ws_off = 0;   // block = workspace + one 256-byte status slot
+    int hidx = -1;                     // pinned host status index
     size_t extra_bytes = 0, extra_off = 0;   // grouped tables of a batch (lead request only)
     double t_submit = 0, t_start = 0, t_done = 0;
     int status = MOA_OK;
@@ -134,6 +141,8 @@ struct moa_server {
              n_batches = 0;
     int inflight_peak = 0;
     int next_stream = 0;
+    int* host_status = nullptr;        // pinned, one int per in-flight slot
+    std::vector<int> free_hidx;
     bool stop = false;
     std::thread sched;
 };
@@ -173,6 +182,19 @@ moa_completion completion_of(const Request& r, int status, double t_done) {
     return c;
 }
 
+constexpr size_t kSlot = 256;
+size_t block_bytes(size_t ws) { return Arena::granule(ws) + kSlot; }
+void* slot_ptr(moa_server* s, size_t off, size_t ws) {
+    return static_cast<uint8_t*>(s->arena.ptr(off)) + Arena::granule(ws);
+}
+
+int status_of(int launch_rc, int dev) {
+    if (launch_rc != MOA_OK) return launch_rc;
+    if (dev == kDevTimeout) return MOA_ERR_TIMEOUT;
+    if (dev == kDevNonFinite) return MOA_ERR_NONFINITE;
+    return dev == kDevOk ? MOA_OK : MOA_ERR_CUDA;
+}
+
 int take_stream(moa_server* s) {
     const int si = s->next_stream;
     s->next_stream = (s->next_stream + 1) % static_cast<int>(s->streams.size());
@@ -188,8 +210,10 @@ void scheduler(moa_server* s) {
             auto it = s->inflight.find(t);
             if (it == s->inflight.end()) continue;
             Request& r = it->second;
-            s->arena.release(r.ws_off, r.ws_bytes);
-            if (r.extra_bytes) s->arena.release(r.extra_off, r.extra_bytes);
+            s->arena.release(r.ws_off, block_bytes(r.ws_bytes));
+            if (r.extra_bytes) s->arena.release(r.extra_off, block_bytes(r.extra_bytes));
+            r.status = status_of(r.status, r.hidx >= 0 ? s->host_status[r.hidx] : kDevOk);
+            if (r.hidx >= 0) s->free_hidx.push_back(r.hidx);
             const double td = r.t_done > 0 ? r.t_done : now_s();
             s->done.push_back(completion_of(r, r.status, td));
             if (r.status == MOA_OK) {
@@ -215,9 +239,12 @@ void scheduler(moa_server* s) {
                 s->queue.pop_front();
                 continue;
             }
-            const size_t off = s->arena.alloc(r.ws_bytes);
+            const size_t off = s->arena.alloc(block_bytes(r.ws_bytes));
             if (off == SIZE_MAX) break;   // wait until memory frees up
             r.ws_off = off;
+            r.hidx = s->free_hidx.back();
+            s->free_hidx.pop_back();
+            s->host_status[r.hidx] = kDevOk;
             r.t_start = tnow;
             batch.push_back(r);
             s->queue.pop_front();
@@ -242,7 +269,7 @@ void scheduler(moa_server* s) {
         size_t toff = SIZE_MAX, tbytes = 0;
         if (bf.size() > 1) {
             tbytes = grouped_workspace(static_cast<int>(bf.size()), bf.data());
-            toff = s->arena.alloc(tbytes);
+            toff = s->arena.alloc(block_bytes(tbytes));
             if (toff != SIZE_MAX) {
                 batch[bf_idx[0]].extra_off = toff;
                 batch[bf_idx[0]].extra_bytes = tbytes;
@@ -257,17 +284,34 @@ void scheduler(moa_server* s) {
 
         std::vector<int> rcs(batch.size(), MOA_OK);
         if (grouped) {
+            cudaStream_t gs = s->streams[gstream];
+            int* slot = static_cast<int*>(slot_ptr(s, toff, tbytes));
+            cudaMemsetAsync(slot, 0, sizeof(int), gs);
+            set_status_override(slot);
             const int rc = grouped_launch(static_cast<int>(bf.size()), bf.data(), s->arena.ptr(toff),
-                                          tbytes, s->streams[gstream], false);
-            for (size_t i : bf_idx) rcs[i] = rc;
+                                          tbytes, gs, false);
+            set_status_override(nullptr);
+            for (size_t i : bf_idx) {
+                rcs[i] = rc;
+                cudaMemcpyAsync(s->host_status + batch[i].hidx, slot, sizeof(int),
+                                cudaMemcpyDeviceToHost, gs);
+            }
         }
         std::vector<uint64_t> failed_now;
         for (size_t i = 0; i < batch.size(); ++i) {
             Request& r = batch[i];
-            if (!(grouped && r.d.dt == MOA_BF16))
+            if (!(grouped && r.d.dt == MOA_BF16)) {
+                cudaStream_t rs = s->streams[r.stream];
+                int* slot = static_cast<int*>(slot_ptr(s, r.ws_off, r.ws_bytes));
+                cudaMemsetAsync(slot, 0, sizeof(int), rs);
+                set_status_override(slot);
                 rcs[i] = gemm_ex(r.d.m, r.d.n, r.d.p, r.d.dt, r.d.A, r.d.B, r.d.C, 0,
-                                 r.ws_bytes ? s->arena.ptr(r.ws_off) : nullptr, r.ws_bytes,
-                                 s->streams[r.stream], nullptr);
+                                 r.ws_bytes ? s->arena.ptr(r.ws_off) : nullptr, r.ws_bytes, rs,
+                                 nullptr);
+                set_status_override(nullptr);
+                cudaMemcpyAsync(s->host_status + r.hidx, slot, sizeof(int), cudaMemcpyDeviceToHost,
+                                rs);
+            }
             auto* ctx = new CallbackCtx{s, r.ticket};
             if (cudaLaunchHostFunc(s->streams[r.stream], on_done, ctx) != cudaSuccess) {
                 delete ctx;
@@ -315,6 +359,14 @@ int moa_serve_create(const moa_serve_config* cfg, moa_server** out) {
         s->streams.push_back(st);
     }
     s->arena.init(reinterpret_cast<uintptr_t>(cfg->arena), cfg->arena_bytes);
+    e = cudaHostAlloc(reinterpret_cast<void**>(&s->host_status),
+                      sizeof(int) * static_cast<size_t>(cfg->max_inflight), cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
+        delete s;
+        return moa::cuda_fail(e, "cudaHostAlloc(status ring)");
+    }
+    for (int i = cfg->max_inflight - 1; i >= 0; --i) s->free_hidx.push_back(i);
     s->sched = std::thread(moa::scheduler, s);
     *out = s;
     return MOA_OK;
@@ -333,7 +385,7 @@ int moa_serve_submit(moa_server* s, const moa_gemm_desc* d, uint64_t* ticket) {
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->stop) return moa::fail(MOA_ERR_REJECTED, "server is shutting down");
-        if (moa::Arena::granule(r.ws_bytes) > s->arena.bytes()) {
+        if (moa::block_bytes(r.ws_bytes) > s->arena.bytes()) {
             ++s->n_rejected;
             return moa::fail(MOA_ERR_BUDGET, "request workspace exceeds the arena");
         }
@@ -408,6 +460,7 @@ int moa_serve_destroy(moa_server* s) {
         if (cudaStreamSynchronize(st) != cudaSuccess) rc = MOA_ERR_CUDA;
         cudaStreamDestroy(st);
     }
+    if (s->host_status) cudaFreeHost(s->host_status);
     delete s;
     return rc;
 }

@@ -801,7 +801,7 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
     if (S < 0) return fail(MOA_ERR_DTYPE, "slice count not supported for this mode");
     const SplitLayout L = split_layout(m, n, p, dt, S);
     if (ws_bytes < L.total) return fail(MOA_ERR_WORKSPACE, "workspace too small for split mode");
-    int* status = device_status_ptr();
+    int* status = launch_status_ptr();
     if (!status) return MOA_ERR_CUDA;
     uint8_t* base = static_cast<uint8_t*>(ws);
     __nv_bfloat16* a_sl = reinterpret_cast<__nv_bfloat16*>(base + L.a_off);

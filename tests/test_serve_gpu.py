@@ -158,3 +158,27 @@ def test_bad_configs_rejected_on_the_host():
     cfg = moa.moa_serve_config(256, 1024, 4, 65, 0, 0.0)       # too many streams
     assert L.moa_serve_create(ctypes.byref(cfg), ctypes.byref(h)) == moa.MOA_ERR_ARG
     assert L.moa_serve_destroy(None) == moa.MOA_ERR_ARG
+
+
+@pytest.mark.gpu
+def test_per_request_device_status():
+    """A split-mode request with a NaN input completes as MOA_ERR_NONFINITE;
+    its neighbours complete normally and the per-device status word stays
+    clean (each request records into its own status slot)."""
+    good = [_req(128, 256, 128, moa.MOA_F32_SPLIT, seed=70 + i) for i in range(3)]
+    bad = _req(128, 256, 128, moa.MOA_F64_SPLIT_F32IN, seed=80)
+    bad[0][5, 7] = float("nan")
+    moa.check(moa.moa_sync_status(moa._stream_handle(None)))
+    srv = moa.Server(arena_bytes=1 << 28, max_inflight=4, n_streams=2)
+    try:
+        tg = [srv.submit(*r)[1] for r in good[:2]]
+        tb = srv.submit(*bad)[1]
+        tg.append(srv.submit(*good[2])[1])
+        got = _drain(srv, 4)
+        st = srv.stats()
+    finally:
+        srv.close()
+    assert got[tb][1] == moa.MOA_ERR_NONFINITE
+    assert all(got[t][1] == moa.MOA_OK for t in tg)
+    assert st["failed"] == 1 and st["completed"] == 3
+    assert moa.moa_sync_status(moa._stream_handle(None)) == moa.MOA_OK
