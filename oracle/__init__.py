@@ -71,7 +71,8 @@ def _load():
             lib.moa_oracle_split3_bf16.argtypes = [_i64, _ptr, _ptr, _ptr, _ptr]
             lib.moa_oracle_split3_bf16.restype = None
             lib.moa_oracle_slice_fixed.argtypes = [_i64, _i64, _ptr, ctypes.c_int,
-                                                   ctypes.c_int, ctypes.c_int, _ptr, _ptr]
+                                                   ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                   _ptr, _ptr]
             lib.moa_oracle_slice_fixed.restype = None
             lib.moa_oracle_split_gemm_exact.argtypes = [_i64, _i64, _i64, _ptr, _ptr,
                                                         _ptr, _ptr, ctypes.c_int,
@@ -144,18 +145,22 @@ def split3_bf16(x):
     return tuple(s)
 
 
-def slice_fixed(X, axis: int, beta: int, S: int):
+def slice_fixed(X, axis: int, beta: int, S: int, headroom: int = 0):
     """Per-group exponents and S integer digits of radix 2^beta.
 
     ``axis=0``: one exponent per row; ``axis=1``: one per column.
+    ``headroom``: bits left unused above the top digit (the exponent is the
+    group's frexp exponent plus ``headroom``, so |d_0| <= 2^(beta - headroom)).
     Returns ``(exps int32[groups], digits int32[S, rows, cols])``.
     """
     X = _f64(X)
     rows, cols = X.shape
     exps = np.empty(rows if axis == 0 else cols, dtype=np.int32)
     digits = np.empty((S, rows, cols), dtype=np.int32)
+    if not 0 <= headroom < beta:
+        raise ValueError("headroom must lie in [0, beta)")
     _load().moa_oracle_slice_fixed(rows, cols, _p(X), int(axis), int(beta), int(S),
-                                   _p(exps), _p(digits))
+                                   int(headroom), _p(exps), _p(digits))
     return exps, digits
 
 

@@ -139,22 +139,26 @@ void moa_oracle_split3_bf16(int64_t count, const float* x,
 /* ------------------------------------------------------------------------ */
 /* Precision slicing, FP64-accuracy mode.  Not in the paper: error-free      */
 /* slicing in the manner of Ozaki, Ogita, Oishi & Rump (2012).               */
-/* Each group (a row of A, or a column of B) gets the exponent e such that   */
-/* max|x| over the group lies in [2^(e-1), 2^e) (e = 0 for an all-zero       */
-/* group).  Each x of the group is scaled to X = x * 2^(beta*S - e), so      */
-/* |X| < 2^(beta*S), and rounded once to the nearest integer D (ties to      */
+/* Each group (a row of A, or a column of B) gets the exponent e = f + h,    */
+/* where max|x| over the group lies in [2^(f-1), 2^f) (f = 0 for an          */
+/* all-zero group) and h >= 0 is the headroom: bits left unused above the    */
+/* top digit.  Each x of the group is scaled to X = x * 2^(beta*S - e), so   */
+/* |X| < 2^(beta*S - h), and rounded once to the nearest integer D (ties to  */
 /* even).  D is then written in balanced radix 2^beta with S digits:         */
 /*   D = sum_{s=0}^{S-1} d_s 2^(beta(S-1-s)),                                */
 /*   d_s in [-2^(beta-1), 2^(beta-1)) for s >= 1 (taken from the bottom),   */
-/*   |d_0| <= 2^beta,                                                        */
+/*   |d_0| <= 2^(beta-h),                                                    */
 /* so that |x - 2^e sum_s d_s 2^(-beta(s+1))| <= 2^(e - beta S) / 2.         */
+/* h = 0 suits BF16 digit planes (beta <= 8: every |d| <= 2^beta is a BF16   */
+/* value); h = 1 with beta = 5 keeps every digit within [-16, 16], the       */
+/* integers that FP8 E4M3 holds exactly.                                     */
 /* ------------------------------------------------------------------------ */
 
 /* X is rows x cols row-major.  axis 0: one exponent per row (length rows);
  * axis 1: one exponent per column (length cols).  digits is S x rows x cols
- * (slice-major), int32.  Requires beta * S <= 60. */
+ * (slice-major), int32.  Requires beta * S <= 60 and 0 <= headroom < beta. */
 void moa_oracle_slice_fixed(int64_t rows, int64_t cols, const double* X,
-                            int axis, int beta, int S,
+                            int axis, int beta, int S, int headroom,
                             int32_t* exps, int32_t* digits)
 {
     const int64_t ngroups = axis == 0 ? rows : cols;
@@ -166,9 +170,9 @@ void moa_oracle_slice_fixed(int64_t rows, int64_t cols, const double* X,
             const double av = fabs(v);
             if (av > mu) mu = av;
         }
-        int e = 0;
-        if (mu != 0.0) (void)frexp(mu, &e);     /* mu = f * 2^e, f in [1/2, 1) */
-        exps[g] = e;
+        int f = 0;
+        if (mu != 0.0) (void)frexp(mu, &f);     /* mu = q * 2^f, q in [1/2, 1) */
+        exps[g] = f + headroom;
     }
     const int64_t radix = (int64_t)1 << beta;
     const int64_t half = radix / 2;

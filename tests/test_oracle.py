@@ -321,22 +321,23 @@ def test_split3_special_values():
 
 
 @pytest.mark.parametrize("axis", [0, 1])
-@pytest.mark.parametrize("beta,S", [(8, 6), (7, 7), (8, 3), (8, 7)])
-def test_slice_fixed_reconstruction_bound(axis, beta, S):
+@pytest.mark.parametrize("beta,S,h", [(8, 6, 0), (7, 7, 0), (8, 3, 0), (8, 7, 0), (5, 10, 1),
+                                      (5, 6, 1), (4, 12, 1)])
+def test_slice_fixed_reconstruction_bound(axis, beta, S, h):
     rng = np.random.default_rng(10 + axis + beta + S)
     X = rng.standard_normal((13, 17)) * 10.0 ** rng.uniform(-4, 4, (13, 1))
     X[3, :] = 0.0
     X[:, 5] = 0.0
-    exps, digits = oracle.slice_fixed(X, axis, beta, S)
-    # exponent: 2^(e-1) <= max|x| < 2^e per group (e = 0 for all-zero groups)
+    exps, digits = oracle.slice_fixed(X, axis, beta, S, headroom=h)
+    # exponent: 2^(e-h-1) <= max|x| < 2^(e-h) per group (e = h for all-zero groups)
     mx = np.abs(X).max(axis=1 - axis)
     for g, e in enumerate(exps):
         if mx[g] == 0:
-            assert e == 0
+            assert e == h
         else:
-            assert math.ldexp(1.0, int(e) - 1) <= mx[g] < math.ldexp(1.0, int(e))
-    # digit ranges: |d_0| <= 2^beta, d_s in [-2^(beta-1), 2^(beta-1)) for s >= 1
-    assert np.all(np.abs(digits[0]) <= 2 ** beta)
+            assert math.ldexp(1.0, int(e) - h - 1) <= mx[g] < math.ldexp(1.0, int(e) - h)
+    # digit ranges: |d_0| <= 2^(beta-h), d_s in [-2^(beta-1), 2^(beta-1)) for s >= 1
+    assert np.all(np.abs(digits[0]) <= 2 ** (beta - h))
     assert np.all(digits[1:] >= -2 ** (beta - 1)) and np.all(digits[1:] < 2 ** (beta - 1))
     # exact reconstruction bound |x - 2^e sum_s d_s 2^-beta(s+1)| <= 2^(e - beta S) / 2
     for r in range(X.shape[0]):
@@ -346,6 +347,36 @@ def test_slice_fixed_reconstruction_bound(axis, beta, S):
                          for s in range(S))
             err = abs(Fraction(X[r, c]) - approx)
             assert err <= Fraction(2) ** (e - beta * S) / 2
+
+
+def test_slice_fixed_headroom_top_digit_reaches_its_bound():
+    # x just below the group's power of two rounds up to D = 2^(beta S - h):
+    # the top digit is then exactly 2^(beta - h) and every other digit is 0.
+    X = np.array([[1.0 - 2.0 ** -53, 0.25]])
+    for beta, S, h in [(5, 10, 1), (7, 7, 0)]:
+        exps, digits = oracle.slice_fixed(X, 0, beta, S, headroom=h)
+        assert int(exps[0]) == h
+        assert int(digits[0, 0, 0]) == 2 ** (beta - h)
+        assert np.all(digits[1:, 0, 0] == 0)
+
+
+def test_headroom_one_radix_32_digits_are_e4m3_values():
+    # The FP8 E4M3 slice planes need every digit exactly representable in
+    # E4M3 (3 stored mantissa bits: all integers of magnitude <= 16).  The
+    # check uses torch's own float8_e4m3fn rounding, which the oracle does
+    # not use.
+    rng = np.random.default_rng(33)
+    X = rng.standard_normal((40, 50)) * 10.0 ** rng.uniform(-4, 4, (40, 1))
+    X[0, :3] = [1.0 - 2.0 ** -53, -(1.0 - 2.0 ** -53), 2.0 ** -1074]
+    for axis in (0, 1):
+        _, digits = oracle.slice_fixed(X, axis, 5, 10, headroom=1)
+        d = torch.from_numpy(digits.astype(np.float32))
+        back = d.to(torch.float8_e4m3fn).to(torch.float32)
+        assert torch.equal(back, d)
+        assert int(np.abs(digits).max()) <= 16
+    # without the headroom bit the top digit can reach 32, which E4M3 cannot
+    # hold for every integer up to it (17 is not an E4M3 value)
+    assert torch.tensor([17.0]).to(torch.float8_e4m3fn).float().item() != 17.0
 
 
 def test_slice_fixed_integers_exact_digits():
@@ -368,12 +399,12 @@ def test_split_gemm_exact_integer_inputs_bit_exact():
     assert np.array_equal(C, (A.astype(np.int64) @ B.astype(np.int64)).astype(np.float64))
 
 
-@pytest.mark.parametrize("beta,S", [(8, 6), (7, 7)])
-def test_split_gemm_exact_close_to_fp64_product(beta, S):
+@pytest.mark.parametrize("beta,S,h", [(8, 6, 0), (7, 7, 0), (5, 10, 1)])
+def test_split_gemm_exact_close_to_fp64_product(beta, S, h):
     A, B = inputs.normal_pair(24, 64, 20, dtype=torch.float64, seed=1, scaled="rows")
     A, B = A.numpy(), B.numpy()
-    eA, dA = oracle.slice_fixed(A, 0, beta, S)
-    eB, dB = oracle.slice_fixed(B, 1, beta, S)
+    eA, dA = oracle.slice_fixed(A, 0, beta, S, headroom=h)
+    eB, dB = oracle.slice_fixed(B, 1, beta, S, headroom=h)
     C = oracle.split_gemm_exact(dA, eA, dB, eB, beta, S)
     ref = oracle.gemm(A, B)
     # Truncation bound per element: each operand digit expansion is within
@@ -410,8 +441,8 @@ def test_slice_fixed_matches_exact_rational_route():
     X[0, 0] = 1.0 + 2.0 ** -48          # with e = 1, beta S = 48: X = 2^47 + 0.5
     X[0, 1] = -(1.0 + 3 * 2.0 ** -48)
     X[1, :] = 2.0 ** -1074              # subnormal row
-    for beta, S in [(8, 6), (7, 7), (8, 3)]:
-        exps, digits = oracle.slice_fixed(X, 0, beta, S)
+    for beta, S, h in [(8, 6, 0), (7, 7, 0), (8, 3, 0), (5, 10, 1)]:
+        exps, digits = oracle.slice_fixed(X, 0, beta, S, headroom=h)
         for r in range(X.shape[0]):
             for c in range(X.shape[1]):
                 want = _digits_by_fractions(X[r, c], int(exps[r]), beta, S)
