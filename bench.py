@@ -279,7 +279,8 @@ def aggregate(flops_per_step, steps, seconds, ws):
 
 # ------------------------------------------------------------------ workloads
 MODE_OF = {"square": "tf32", "bf16": "bf16", "split_f32": "f32_split",
-           "split_f64": "f64_split_f32in", "f64": "f64", "simt": "f32_simt",
+           "split_f64": "f64_split_f32in", "split_f64_e4m3": "f64_split_f32in_e4m3",
+           "f64": "f64", "simt": "f32_simt",
            "grouped": "grouped", "serve": "serve", "energy_n": "energy_n",
            "tiles": "tiles"}
 
@@ -288,7 +289,7 @@ def make_inputs(mode, N):
     import torch
     from paper_2306_11148_b300 import inputs, moa
     dt = moa.MODES[mode]
-    if mode in ("f32_split", "f64_split_f32in"):
+    if mode in ("f32_split", "f64_split_f32in", "f64_split_f32in_e4m3"):
         A, B = inputs.normal_pair(N, N, N, dtype=torch.float32, seed=0)
     else:
         A, B = inputs.square_uniform(N, moa.in_dtype(dt), seed=0)
@@ -919,7 +920,8 @@ def main():
     # / that kernel's own CUDA-event duration, recorded by the library on the
     # launching stream.
     kdtype = {"tf32": "tf32", "bf16": "bf16", "f32_split": "bf16",
-              "f64_split_f32in": "bf16", "grouped": "bf16"}.get(mode)
+              "f64_split_f32in": "bf16", "f64_split_f32in_e4m3": "fp8",
+              "grouped": "bf16"}.get(mode)
     kernel_ms = main_res["kernel_seconds"] / args.steps * 1e3
     if mode == "grouped":
         # mixed: small problems are HBM-bound, large ones tensor-bound; the
@@ -955,7 +957,8 @@ def main():
 
     modes = {}
     if not args.no_extras and rank == 0 and ws == 1 and mode != "grouped":
-        for m2, n2 in [("bf16", N), ("f32_split", N), ("f64_split_f32in", N), ("f32_simt", N // 2),
+        for m2, n2 in [("bf16", N), ("f32_split", N), ("f64_split_f32in", N),
+                       ("f64_split_f32in_e4m3", N), ("f32_simt", N // 2),
                        ("f64", N // 4)]:
             if m2 == mode:
                 continue
@@ -989,7 +992,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"tf32": "tf32", "bf16": "bf16", "f32_split": "bf16x6",
-                      "f64_split_f32in": "bf16-digits", "f64": "f64",
+                      "f64_split_f32in": "bf16-digits",
+                      "f64_split_f32in_e4m3": "e4m3-digits", "f64": "f64",
                       "f32_simt": "f32", "grouped": "bf16"}[mode],
             "data": "synthetic",
             "config": config,

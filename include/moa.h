@@ -14,8 +14,9 @@
  *
  * Memory: A, B, C, workspaces and the serving arena are DEVICE pointers owned
  * by the caller (allocate them with cudaMalloc or PyTorch).  The library
- * allocates device memory in exactly two places, both documented below:
- * moa_gemm()'s internal workspace and nothing else.  Streams are passed as
+ * allocates device memory in one place only, moa_gemm()'s internal workspace
+ * (documented below); it also holds pinned host staging buffers for grouped
+ * calls and serving status slots.  Streams are passed as
  * `void*` holding a cudaStream_t (NULL = the legacy default stream).
  *
  * Errors: every entry point returns a moa_status.  Argument errors are
@@ -27,7 +28,7 @@
  *
  * Precision modes (moa_dtype): see the enum.  Tolerances the test suite
  * holds each mode to, as relative Frobenius error against the FP64 oracle:
- * MOA_F64 1e-12, MOA_F64_SPLIT_* 1e-12, MOA_F32_SPLIT 1e-5, MOA_F32_TF32
+ * MOA_F64 1e-12, MOA_F64_SPLIT_* (both digit formats) 1e-12, MOA_F32_SPLIT 1e-5, MOA_F32_TF32
  * 5e-3, MOA_BF16 1e-2 (and bit-exact on integer-valued inputs in {-8..8}
  * for every mode).
  */
@@ -64,7 +65,13 @@ typedef enum {
     MOA_F32_SPLIT = 4,        /* A,B,C FP32.  3 BF16 slices each, 6 slice products, FP32 acc.*/
     MOA_F64_SPLIT_F32IN = 5,  /* A,B FP32, C FP64.  Integer-digit BF16 slices, exact         */
                               /*   chunked accumulation, FP64 recombination.                 */
-    MOA_F64_SPLIT_F64IN = 6   /* A,B,C FP64.  As above with FP64 inputs.                     */
+    MOA_F64_SPLIT_F64IN = 6,  /* A,B,C FP64.  As above with FP64 inputs.                     */
+    MOA_F64_SPLIT_F32IN_E4M3 = 7, /* A,B FP32, C FP64.  As MOA_F64_SPLIT_F32IN with FP8 E4M3 */
+                              /*   digit slices (radix 2^5, one headroom bit: every digit in */
+                              /*   [-16, 16], exact in E4M3) on tcgen05 kind::f8f6f4.        */
+                              /*   slices: 4..12, default 10 (49 bits per operand, as 7     */
+                              /*   BF16 digits); 55 slice products at twice the BF16 rate.   */
+    MOA_F64_SPLIT_F64IN_E4M3 = 8  /* A,B,C FP64.  As above with FP64 inputs.                 */
 } moa_dtype;
 
 /* Optional per-call report (may be NULL). */
@@ -92,7 +99,9 @@ int moa_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt,
              const void* A, const void* B, void* C);
 
 /* Bytes of workspace moa_gemm_ex needs for this problem (0 if none).
- * slices: split modes only (0 = default); ignored otherwise. */
+ * slices: split modes only (0 = default); ignored otherwise.  Allowed slice
+ * counts: MOA_F32_SPLIT 3; MOA_F64_SPLIT_F32IN / _F64IN 3..8 (default 7);
+ * the _E4M3 forms 4..12 (default 10).  Returns 0 for a count not allowed. */
 size_t moa_gemm_workspace_size(int64_t m, int64_t n, int64_t p, moa_dtype dt, int slices);
 
 /* C := A . B on `stream` with a caller-provided device workspace of at least

@@ -20,30 +20,8 @@ constexpr size_t kAlign = 256;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-bool valid_dtype(int dt) { return dt >= MOA_F64 && dt <= MOA_F64_SPLIT_F64IN; }
-
-int in_size(moa_dtype dt) {
-    switch (dt) {
-        case MOA_F64:
-        case MOA_F64_SPLIT_F64IN:
-            return 8;
-        case MOA_BF16:
-            return 2;
-        default:
-            return 4;
-    }
-}
-
-int out_size(moa_dtype dt) {
-    switch (dt) {
-        case MOA_F64:
-        case MOA_F64_SPLIT_F32IN:
-        case MOA_F64_SPLIT_F64IN:
-            return 8;
-        default:
-            return 4;
-    }
-}
+int in_size(moa_dtype dt) { return dtype_in_bytes(dt); }
+int out_size(moa_dtype dt) { return dtype_out_bytes(dt); }
 
 bool is_tc_dense(moa_dtype dt) { return dt == MOA_BF16 || dt == MOA_F32_TF32; }
 

@@ -418,8 +418,7 @@ int grouped_launch(int count, const moa_gemm_desc* d, void* ws, size_t ws_bytes,
     long T = 0;
     for (int g = 0; g < count; ++g) {
         const moa_gemm_desc& x = d[g];
-        if (x.dt < MOA_F64 || x.dt > MOA_F64_SPLIT_F64IN)
-            return fail(MOA_ERR_DTYPE, "unknown dtype in descriptor");
+        if (!valid_dtype(x.dt)) return fail(MOA_ERR_DTYPE, "unknown dtype in descriptor");
         if (x.m < 0 || x.n < 0 || x.p < 0) return fail(MOA_ERR_ARG, "negative dimension in descriptor");
         if (x.m > 0 && x.p > 0 && x.C == nullptr) return fail(MOA_ERR_ARG, "descriptor C is NULL");
         if (x.m > 0 && x.p > 0 && x.n > 0 && (x.A == nullptr || x.B == nullptr))
@@ -566,11 +565,11 @@ int batched_descs(int batch, int64_t m, int64_t n, int64_t p, moa_dtype dt, cons
                   std::vector<moa_gemm_desc>& d) {
     if (batch < 0) return fail(MOA_ERR_ARG, "negative batch");
     if (sa < 0 || sb < 0 || sc < 0) return fail(MOA_ERR_ARG, "negative stride");
-    if (dt < MOA_F64 || dt > MOA_F64_SPLIT_F64IN) return fail(MOA_ERR_DTYPE, "unknown dtype");
+    if (!valid_dtype(dt)) return fail(MOA_ERR_DTYPE, "unknown dtype");
     if (batch > 1 && m > 0 && p > 0 && sc < m * p)
         return fail(MOA_ERR_ARG, "C stride smaller than m * p would overlap outputs");
-    const int ies = (dt == MOA_F64 || dt == MOA_F64_SPLIT_F64IN) ? 8 : (dt == MOA_BF16 ? 2 : 4);
-    const int oes = (dt == MOA_F64 || dt == MOA_F64_SPLIT_F32IN || dt == MOA_F64_SPLIT_F64IN) ? 8 : 4;
+    const int ies = dtype_in_bytes(dt);
+    const int oes = dtype_out_bytes(dt);
     d.resize(static_cast<size_t>(batch));
     for (int b = 0; b < batch; ++b) {
         d[b].m = m;

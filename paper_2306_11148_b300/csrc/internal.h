@@ -12,6 +12,21 @@
 
 namespace moa {
 
+// ------------------------------------------------------------------ modes
+inline bool valid_dtype(int dt) { return dt >= MOA_F64 && dt <= MOA_F64_SPLIT_F64IN_E4M3; }
+// Bytes per element of A and B, and of C, for each mode.
+inline int dtype_in_bytes(moa_dtype dt) {
+    return (dt == MOA_F64 || dt == MOA_F64_SPLIT_F64IN || dt == MOA_F64_SPLIT_F64IN_E4M3)
+               ? 8
+               : (dt == MOA_BF16 ? 2 : 4);
+}
+inline int dtype_out_bytes(moa_dtype dt) {
+    return (dt == MOA_F64 || dt == MOA_F64_SPLIT_F32IN || dt == MOA_F64_SPLIT_F64IN ||
+            dt == MOA_F64_SPLIT_F32IN_E4M3 || dt == MOA_F64_SPLIT_F64IN_E4M3)
+               ? 8
+               : 4;
+}
+
 // ------------------------------------------------------------------ errors
 void set_error(const std::string& msg);
 int fail(int status, const std::string& msg);

@@ -153,6 +153,17 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint6
         : "memory");
 }
 
+// FP8/FP6/FP4 operands (the formats are in the instruction descriptor).
+__device__ __forceinline__ void mma_f8f6f4(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                           uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 // Arrive (once) on `bar` when all tcgen05 operations issued so far by this
 // thread have completed.
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -237,8 +248,9 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr, uint32_t lbo
     return d;
 }
 
-// Instruction descriptor for kind::f16 / kind::tf32 with FP32 accumulation.
-// ab_format: 1 = BF16 (kind::f16), 2 = TF32 (kind::tf32).  a_mn / b_mn: operand
+// Instruction descriptor for kind::f16 / kind::tf32 / kind::f8f6f4 with FP32
+// accumulation.  ab_format: 1 = BF16 (kind::f16), 2 = TF32 (kind::tf32),
+// 0 = E4M3 (kind::f8f6f4).  a_mn / b_mn: operand
 // is MN-major in shared memory.
 __host__ __device__ constexpr uint32_t make_idesc(uint32_t ab_format, uint32_t M, uint32_t N,
                                                   uint32_t a_mn, uint32_t b_mn) {

@@ -375,7 +375,7 @@ int moa_serve_create(const moa_serve_config* cfg, moa_server** out) {
 int moa_serve_submit(moa_server* s, const moa_gemm_desc* d, uint64_t* ticket) {
     if (!s || !d || !ticket) return moa::fail(MOA_ERR_ARG, "NULL argument");
     const moa_gemm_desc& x = *d;
-    if (x.dt < MOA_F64 || x.dt > MOA_F64_SPLIT_F64IN) return moa::fail(MOA_ERR_DTYPE, "unknown dtype");
+    if (!moa::valid_dtype(x.dt)) return moa::fail(MOA_ERR_DTYPE, "unknown dtype");
     if (x.m < 0 || x.n < 0 || x.p < 0) return moa::fail(MOA_ERR_ARG, "negative dimension");
     if (x.m > 0 && x.p > 0 && (!x.C || (x.n > 0 && (!x.A || !x.B))))
         return moa::fail(MOA_ERR_ARG, "NULL operand");

@@ -17,14 +17,14 @@
 //   a BF16 value.  Level L = s + t of the triangular product (s + t <= S - 1)
 //   is summed over chunks of K short enough that every FP32 partial sum is an
 //   integer below 2^24, hence exact; each chunk is flushed into an int32
-//   running sum, folded at the level's end into an int64 fixed-point total in
-//   TMEM, which the epilogue converts to FP64 once and scales by
+//   running sum, folded at the level's end into an int64 fixed-point total
+//   kept in C, which the epilogue converts to FP64 once and scales by
 //   2^(eA_i + eB_j - 7(S+1) + drop).
 //
-// Kernel layout (one persistent CTA per SM, 320 threads): warp 0 issues TMA
-// loads of (A slice, B slice) K blocks; warp 1 issues tcgen05.mma into one of
-// two TMEM chunk accumulators; warps 2..9 (two per TMEM lane quadrant, 64
-// columns each) flush chunks and write C.
+// Kernel layout (one persistent CTA per SM): warp 0 issues TMA loads of
+// (A slice, B slice) K blocks; warp 1 issues tcgen05.mma into one of one or
+// two TMEM chunk accumulators; the epilogue warps (one per TMEM lane
+// quadrant and column group) flush chunks and write C.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -42,9 +42,23 @@ namespace moa {
 // ====================================================================== pre-passes
 namespace {
 
-__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-    return static_cast<uint32_t>(__bfloat16_as_ushort(lo)) |
-           (static_cast<uint32_t>(__bfloat16_as_ushort(hi)) << 16);
+__device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 v) {
+    return static_cast<uint32_t>(__bfloat16_as_ushort(v.x)) |
+           (static_cast<uint32_t>(__bfloat16_as_ushort(v.y)) << 16);
+}
+
+// BF16 bit patterns of two small integers (|lo|, |hi| < 2^8, exact in BF16),
+// packed low half first.  The integer is placed in the significand of
+// 1.5 * 2^23 (magic-number conversion: for |k| < 2^22 the float with bits
+// 0x4B400000 + k equals 1.5 * 2^23 + k) and the offset subtracted, both
+// exact; the result has at most 8 significant bits, so its upper 16 bits are
+// its BF16 pattern.  Plain ALU work instead of integer-to-float conversions.
+__device__ __forceinline__ uint32_t small_ints_bf16x2(int lo, int hi) {
+    const uint32_t flo =
+        __float_as_uint(__fsub_rn(__uint_as_float(0x4B400000u + static_cast<uint32_t>(lo)), 12582912.0f));
+    const uint32_t fhi =
+        __float_as_uint(__fsub_rn(__uint_as_float(0x4B400000u + static_cast<uint32_t>(hi)), 12582912.0f));
+    return (flo >> 16) | (fhi & 0xFFFF0000u);
 }
 
 // Loads X[r, c0 .. c0+7] (zero past `cols`); 16-byte loads when allowed.
@@ -79,21 +93,18 @@ __global__ void split3_kernel(const float* __restrict__ X, int64_t rows, int64_t
         uint32_t w0[4], w1[4], w2[4];
 #pragma unroll
         for (int i = 0; i < 8; i += 2) {
-            __nv_bfloat16 a[2], b[2], c[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const float v = x[i + h];
-                a[h] = __float2bfloat16_rn(v);
-                const float av = __bfloat162float(a[h]);
-                const float r1 = __fsub_rn(v, av);
-                b[h] = __float2bfloat16_rn(r1);
-                const float r2 = __fsub_rn(r1, __bfloat162float(b[h]));
-                c[h] = __float2bfloat16_rn(r2);
-                bad |= !isfinite(v) || !isfinite(av);
-            }
-            w0[i / 2] = pack_bf16x2(a[0], a[1]);
-            w1[i / 2] = pack_bf16x2(b[0], b[1]);
-            w2[i / 2] = pack_bf16x2(c[0], c[1]);
+            // two elements per conversion instruction; BF16 -> FP32 is exact
+            const __nv_bfloat162 a = __floats2bfloat162_rn(x[i], x[i + 1]);
+            const float2 af = __bfloat1622float2(a);
+            const float r0 = __fsub_rn(x[i], af.x), r1 = __fsub_rn(x[i + 1], af.y);
+            const __nv_bfloat162 b = __floats2bfloat162_rn(r0, r1);
+            const float2 bf = __bfloat1622float2(b);
+            const __nv_bfloat162 c =
+                __floats2bfloat162_rn(__fsub_rn(r0, bf.x), __fsub_rn(r1, bf.y));
+            bad |= !isfinite(x[i]) || !isfinite(x[i + 1]) || !isfinite(af.x) || !isfinite(af.y);
+            w0[i / 2] = bf16x2_bits(a);
+            w1[i / 2] = bf16x2_bits(b);
+            w2[i / 2] = bf16x2_bits(c);
         }
         const int64_t o = r * ld + c0;
         *reinterpret_cast<uint4*>(out + o) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
@@ -196,9 +207,9 @@ struct Bits<float> {
     }
 };
 
-// One warp per row: exponent of max |A[i,:]|.
+// One warp per row: exponent of max |A[i,:]| plus `bias` (headroom bits).
 template <typename T>
-__global__ void row_exp_kernel(const T* __restrict__ X, int64_t rows, int64_t cols,
+__global__ void row_exp_kernel(const T* __restrict__ X, int64_t rows, int64_t cols, int bias,
                                int* __restrict__ e_out, int* status) {
     using B = Bits<T>;
     const int lane = threadIdx.x & 31;
@@ -215,7 +226,7 @@ __global__ void row_exp_kernel(const T* __restrict__ X, int64_t rows, int64_t co
         }
         if (lane == 0) {
             bad |= mx >= B::kInf;
-            e_out[r] = B::frexp_exp(mx);
+            e_out[r] = B::frexp_exp(mx) + bias;
         }
     }
     if (bad) atomicCAS(status, kDevOk, kDevNonFinite);
@@ -237,61 +248,191 @@ __global__ void col_max_kernel(const T* __restrict__ X, int64_t rows, int64_t co
 
 template <typename T>
 __global__ void col_exp_kernel(const typename Bits<T>::U* __restrict__ cmax, int64_t cols,
-                               int* __restrict__ e_out, int* status) {
+                               int bias, int* __restrict__ e_out, int* status) {
     using B = Bits<T>;
     const int64_t c = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
     if (c >= cols) return;
     const typename B::U M = cmax[c];
     if (M >= B::kInf) atomicCAS(status, kDevOk, kDevNonFinite);
-    e_out[c] = B::frexp_exp(M);
+    e_out[c] = B::frexp_exp(M) + bias;
+}
+
+// Loads X[r, c0 .. c0+7] of an FP64 matrix (zero past `cols`).
+__device__ __forceinline__ void load8(const double* __restrict__ X, int64_t r, int64_t cols,
+                                      int64_t c0, bool vec, double (&x)[8]) {
+    const double* src = X + r * cols + c0;
+    if (vec && c0 + 8 <= cols) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const double2 d = reinterpret_cast<const double2*>(src)[v];
+            x[2 * v] = d.x;
+            x[2 * v + 1] = d.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = (c0 + i < cols) ? src[i] : 0.0;
+    }
 }
 
 // Integer digits of every element into S BF16 planes (row pitch ld, a
 // multiple of 8; zero pad); 8 consecutive elements per thread, one 16-byte
 // store per digit plane.  axis 0: exponent per row (e[r]); axis 1: per
-// column (e[c]).
+// column (e[c]).  vec: X rows start 16-byte aligned (16-byte loads).
 template <typename T>
 __global__ void digits_kernel(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
-                              const int* __restrict__ e, int axis, int S,
+                              const int* __restrict__ e, int axis, int S, int vec,
                               __nv_bfloat16* __restrict__ out, int64_t plane) {
     const int64_t gpr = ld / 8;
     const int64_t total = rows * gpr;
-    constexpr long long radix = 1ll << kBeta;
-    constexpr long long half = radix / 2;
+    constexpr int radix = 1 << kBeta;
     for (int64_t g = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; g < total;
          g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int64_t r = g / gpr, c0 = (g - r * gpr) * 8;
+        T x[8];
+        load8(X, r, cols, c0, vec != 0, x);
         long long D[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int64_t c = c0 + i;
-            D[i] = 0;
-            if (c < cols) {
-                const int ex = axis == 0 ? e[r] : e[c];
-                D[i] = Bits<T>::round_scaled(X[r * cols + c], kBeta * S - ex);
-            }
+            const int ex = c < cols ? (axis == 0 ? e[r] : e[c]) : 0;
+            D[i] = Bits<T>::round_scaled(x[i], kBeta * S - ex);
         }
         const int64_t o = r * ld + c0;
         for (int s = S - 1; s >= 0; --s) {
             uint32_t w[4];
 #pragma unroll
             for (int i = 0; i < 8; i += 2) {
-                __nv_bfloat16 d[2];
+                int d[2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    long long low = D[i + h];
                     if (s > 0) {
-                        low = D[i + h] & (radix - 1);
-                        if (low >= half) low -= radix;
+                        // balanced digit in [-radix/2, radix/2): the low kBeta
+                        // bits, less radix when the top one is set
+                        int low = static_cast<int>(D[i + h]) & (radix - 1);
+                        low -= (low & (radix >> 1)) << 1;
                         D[i + h] = (D[i + h] - low) >> kBeta;
+                        d[h] = low;
+                    } else {
+                        d[h] = static_cast<int>(D[i + h]);   // |d_0| <= radix
                     }
-                    d[h] = __float2bfloat16_rn(static_cast<float>(low));
                 }
-                w[i / 2] = pack_bf16x2(d[0], d[1]);
+                w[i / 2] = small_ints_bf16x2(d[0], d[1]);
             }
             *reinterpret_cast<uint4*>(out + s * plane + o) = make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
+}
+
+// E4M3 bit pattern of an integer v with |v| <= 16 (exact in E4M3: sign,
+// 4 exponent bits with bias 7, 3 stored mantissa bits).  |v| in [2^q, 2^(q+1))
+// has exponent field q + 7 and mantissa bits (|v| * 2^(3 - q)) mod 8.
+__device__ __forceinline__ uint32_t e4m3_of_small_int(int v) {
+    const uint32_t a = static_cast<uint32_t>(v < 0 ? -v : v);
+    const int q = 31 - __clz(static_cast<int>(a | 1u));       // a = 0 gives q = 0
+    const uint32_t bits = (static_cast<uint32_t>(q + 7) << 3) | (((a << 3) >> q) & 7u);
+    return a == 0 ? 0u : (bits | (v < 0 ? 0x80u : 0u));
+}
+
+// Balanced radix-2^beta digit at position s (s >= 1 from the bottom; the
+// remainder D is shifted down in place); s == 0 returns what is left.
+__device__ __forceinline__ int next_digit(long long& D, int s, int beta) {
+    if (s == 0) return static_cast<int>(D);
+    const int radix = 1 << beta;
+    int low = static_cast<int>(D) & (radix - 1);
+    low -= (low & (radix >> 1)) << 1;
+    D = (D - low) >> beta;
+    return low;
+}
+
+// Integer digits (radix 2^beta) of a row-major matrix whose exponent is per
+// row, as E4M3 bytes in S planes of row pitch ld (a multiple of 16; zero
+// pad): 16 consecutive elements per thread, one 16-byte store per plane.
+template <typename T>
+__global__ void digits_e4m3_rows_kernel(const T* __restrict__ X, int64_t rows, int64_t cols,
+                                        int64_t ld, const int* __restrict__ e, int S, int beta,
+                                        int vec, uint8_t* __restrict__ out, int64_t plane) {
+    const int64_t gpr = ld / 16;
+    const int64_t total = rows * gpr;
+    for (int64_t g = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; g < total;
+         g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t r = g / gpr, c0 = (g - r * gpr) * 16;
+        const int ex = e[r];
+        long long D[16];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            T x[8];
+            load8(X, r, cols, c0 + 8 * h, vec != 0, x);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) D[8 * h + i] = Bits<T>::round_scaled(x[i], beta * S - ex);
+        }
+        const int64_t o = r * ld + c0;
+        for (int s = S - 1; s >= 0; --s) {
+            uint32_t w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t word = 0;
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    word |= e4m3_of_small_int(next_digit(D[4 * q + b], s, beta)) << (8 * b);
+                w[q] = word;
+            }
+            *reinterpret_cast<uint4*>(out + s * plane + o) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
+// Integer digits of B (n x p row-major, exponent per column j) written
+// transposed as E4M3 bytes: plane s holds B_s^T, p rows of pitch ld (a
+// multiple of 16; zero pad past n), so that the slice GEMM reads B K-major.
+// One 64 (k) x 64 (j) tile per block pass, 256 threads: reads are coalesced
+// along j, each plane goes through a padded shared-memory tile and is
+// written as 16-byte row segments along k.
+constexpr int kTT = 64;
+template <typename T>
+__global__ void __launch_bounds__(256)
+    digits_e4m3_cols_t_kernel(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
+                              const int* __restrict__ e, int S, int beta,
+                              uint8_t* __restrict__ out, int64_t plane) {
+    __shared__ uint32_t tile[kTT * (kTT / 4 + 1)];   // [j][k/4], 17 words per row
+    const int t = threadIdx.x;
+    const int64_t tk = (rows + kTT - 1) / kTT, tj = (cols + kTT - 1) / kTT;
+    for (int64_t b = blockIdx.x; b < tk * tj; b += gridDim.x) {
+        const int64_t k0 = (b / tj) * kTT, j0 = (b % tj) * kTT;
+        const int jl = t % kTT, kq = t / kTT;          // column in tile, k phase 0..3
+        const int64_t j = j0 + jl;
+        const int ex = j < cols ? e[j] : 0;
+        long long D[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int64_t k = k0 + kq + 4 * i;
+            const T x = (j < cols && k < rows) ? X[k * cols + j] : T(0);
+            D[i] = Bits<T>::round_scaled(x, beta * S - ex);
+        }
+        uint8_t* tb = reinterpret_cast<uint8_t*>(tile);
+        for (int s = S - 1; s >= 0; --s) {
+            __syncthreads();   // the previous plane's tile has been written out
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+                tb[jl * (4 * (kTT / 4 + 1)) + kq + 4 * i] =
+                    static_cast<uint8_t>(e4m3_of_small_int(next_digit(D[i], s, beta)));
+            __syncthreads();
+            // thread t writes row jr = t / 4, bytes [16 c, 16 c + 16) of the tile
+            const int jr = t / 4, c = t % 4;
+            const int64_t kk = k0 + 16 * c;
+            if (j0 + jr < cols && kk < ld) {
+                const uint32_t* row = tile + jr * (kTT / 4 + 1) + 4 * c;
+                *reinterpret_cast<uint4*>(out + s * plane + (j0 + jr) * ld + kk) =
+                    make_uint4(row[0], row[1], row[2], row[3]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// 1 when every row of a row-major matrix with `cols` columns starts on a
+// 16-byte boundary (base aligned, row length a multiple of `per16` elements).
+int vec_rows(const void* X, int64_t cols, int per16) {
+    return (cols % per16 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
 }
 
 int grid_for(int64_t total, int threads) {
@@ -305,10 +446,17 @@ int grid_for(int64_t total, int threads) {
 // ====================================================================== slice GEMM
 namespace {
 
-constexpr int kBM = 128, kBK = 64;
-constexpr int kABytes = kBM * 128;                 // 128 rows x 64 BF16
+constexpr int kBM = 128, kBK = 64;                // kBK: BF16 elements per K block
+constexpr int kABytes = kBM * 128;                 // 128 rows x 128 bytes of K
 constexpr int kBChunkBytes = kBK * 128;            // 64 rows x 64 BF16 columns
-constexpr int kMaxLevels = 8;
+constexpr int kMaxLevels = 12;
+// Digit-plane formats of the slice GEMM.  kFmtBF16: kind::f16, B planes
+// MN-major (n x p, read as 64-column chunks).  kFmtE4M3: kind::f8f6f4, B
+// planes hold B^T (p x n, K-major, one box per stage).  A K block is 128
+// bytes of K either way: 64 BF16 or 128 E4M3 elements.
+constexpr int kFmtBF16 = 0, kFmtE4M3 = 1;
+template <int FMT>
+constexpr int block_k() { return FMT == kFmtE4M3 ? 128 : 64; }
 
 // Kernel variants (tile width BN x epilogue mode):
 //   kModeF32     FP32 accuracy; two chunk accumulators; each epilogue warp keeps
@@ -321,8 +469,9 @@ constexpr int kMaxLevels = 8;
 // The FP64 modes keep the tile's int64 fixed-point total in C itself.
 constexpr int kModeF32 = 0, kModeF64Reg = 1, kModeF64Tmem = 2;
 
-template <int BN, int MODE>
+template <int BN, int MODE, int FMT>
 struct SplitCfg {
+    static constexpr int kBKe = block_k<FMT>();   // K elements per stage
     static constexpr int kStages = BN == 256 ? 4 : (BN == 192 ? 5 : 6);
     static constexpr int kBBytes = (BN / 64) * kBChunkBytes;
     static constexpr int kStageBytes = kABytes + kBBytes;
@@ -332,7 +481,10 @@ struct SplitCfg {
     static constexpr int kThreads = 64 + 32 * kEpiWarps;
     static constexpr int kNBuf = MODE == kModeF64Tmem ? 1 : 2;
     static constexpr int kTmemCols = (MODE == kModeF64Tmem || BN > 128) ? 512 : 256;
-    static constexpr uint32_t kIdesc = make_idesc(1u, kBM, BN, 0u, 1u);
+    // A/B format fields: BF16 = 1 (kind::f16), E4M3 = 0 (kind::f8f6f4); B is
+    // MN-major for BF16, K-major for E4M3.
+    static constexpr uint32_t kIdesc =
+        FMT == kFmtE4M3 ? make_idesc(0u, kBM, BN, 0u, 0u) : make_idesc(1u, kBM, BN, 0u, 1u);
 };
 
 struct SplitArgs {
@@ -344,6 +496,7 @@ struct SplitArgs {
     int levels;         // number of levels
     int kc[kMaxLevels]; // chunk length per level, in K blocks
     int S;
+    int beta;           // digit radix 2^beta (FP64 mode)
     int drop;           // fixed-point bits dropped from the int64 total (FP64 mode)
     const int* eA;
     const int* eB;
@@ -379,11 +532,12 @@ __device__ __forceinline__ void pair_at(const SplitArgs& a, int L, int q, int& s
     }
 }
 
-template <int BN, int MODE>
-__global__ void __launch_bounds__(SplitCfg<BN, MODE>::kThreads, 1)
+template <int BN, int MODE, int FMT>
+__global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
     split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       const SplitArgs args) {
-    using Cfg = SplitCfg<BN, MODE>;
+    using Cfg = SplitCfg<BN, MODE, FMT>;
+    constexpr int kBKe = Cfg::kBKe;
     constexpr bool F64 = MODE != kModeF32;
     constexpr int kNBuf = Cfg::kNBuf;
     constexpr int kStages = Cfg::kStages;
@@ -456,12 +610,18 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE>::kThreads, 1)
                                 break;
                             }
                             mbar_arrive_expect_tx(&full[stage], Cfg::kStageBytes);
-                            tma_load_3d(sA + stage * kABytes, &tmA, &full[stage], kb * kBK,
+                            tma_load_3d(sA + stage * kABytes, &tmA, &full[stage], kb * kBKe,
                                         tm * kBM, s);
+                            if constexpr (FMT == kFmtE4M3) {
+                                // B^T plane u: BN rows (j) x 128 bytes (k)
+                                tma_load_3d(sB + stage * Cfg::kBBytes, &tmB, &full[stage],
+                                            kb * kBKe, tn * BN, u);
+                            } else {
 #pragma unroll
-                            for (int c = 0; c < BN / 64; ++c)
-                                tma_load_3d(sB + stage * Cfg::kBBytes + c * kBChunkBytes, &tmB,
-                                            &full[stage], tn * BN + c * 64, kb * kBK, u);
+                                for (int c = 0; c < BN / 64; ++c)
+                                    tma_load_3d(sB + stage * Cfg::kBBytes + c * kBChunkBytes, &tmB,
+                                                &full[stage], tn * BN + c * 64, kb * kBK, u);
+                            }
                             ++issued;
                             if (++stage == kStages) {
                                 stage = 0;
@@ -515,12 +675,19 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE>::kThreads, 1)
                                 const uint64_t adesc =
                                     smem_desc_sw128(smem_u32(sA + stage * kABytes), 16, 1024);
                                 const uint64_t bdesc = smem_desc_sw128(
-                                    smem_u32(sB + stage * Cfg::kBBytes), kBChunkBytes, 1024);
+                                    smem_u32(sB + stage * Cfg::kBBytes),
+                                    FMT == kFmtE4M3 ? 16 : kBChunkBytes, 1024);
+                                // four MMAs of 32 bytes of K each
 #pragma unroll
-                                for (int k = 0; k < kBK / 16; ++k) {
-                                    mma_f16(d, adesc + static_cast<uint64_t>((k * 32) >> 4),
-                                            bdesc + static_cast<uint64_t>((k * 16 * 128) >> 4),
-                                            Cfg::kIdesc, (first && k == 0) ? 0u : 1u);
+                                for (int k = 0; k < 4; ++k) {
+                                    const uint64_t a_off = static_cast<uint64_t>((k * 32) >> 4);
+                                    if constexpr (FMT == kFmtE4M3)
+                                        mma_f8f6f4(d, adesc + a_off, bdesc + a_off, Cfg::kIdesc,
+                                                   (first && k == 0) ? 0u : 1u);
+                                    else
+                                        mma_f16(d, adesc + a_off,
+                                                bdesc + static_cast<uint64_t>((k * 16 * 128) >> 4),
+                                                Cfg::kIdesc, (first && k == 0) ? 0u : 1u);
                                 }
                                 first = false;
                                 mma_commit(&empty[stage]);
@@ -628,7 +795,7 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE>::kThreads, 1)
                         // T += round(R * 2^(beta(S-1-L) - drop)); the last fold
                         // of the tile converts once to FP64 and scales by
                         // 2^(eA_i + eB_j - beta(S+1) + drop).
-                        const int sh = kBeta * (args.S - 1 - L) - args.drop;
+                        const int sh = args.beta * (args.S - 1 - L) - args.drop;
                         const bool last = level_end && L == args.levels - 1;
 #pragma unroll
                         for (int b = 0; b < kCols / 16; ++b) {
@@ -664,7 +831,7 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE>::kThreads, 1)
                                     const long long tot = told[i] + v;
                                     if (last) {
                                         const int ex =
-                                            er + args.eB[col] - kBeta * (args.S + 1) + args.drop;
+                                            er + args.eB[col] - args.beta * (args.S + 1) + args.drop;
                                         reinterpret_cast<double*>(trow)[col] =
                                             ldexp(__ll2double_rn(tot), ex);
                                     } else {
@@ -723,6 +890,10 @@ static int f32_split_chunk_kb() {
 
 int split_slices(moa_dtype dt, int slices) {
     if (dt == MOA_F32_SPLIT) return (slices == 0 || slices == 3) ? 3 : -1;
+    if (is_e4m3_split(dt)) {
+        if (slices == 0) return kDefaultSlicesE4M3;
+        return (slices < kMinSlicesE4M3 || slices > kMaxSlicesE4M3) ? -1 : slices;
+    }
     if (slices == 0) return kDefaultSlices;
     if (slices < kMinSlices || slices > kMaxSlices) return -1;
     return slices;
@@ -732,13 +903,17 @@ SplitLayout split_layout(int64_t m, int64_t n, int64_t p, moa_dtype dt, int S) {
     auto al = [](size_t x) { return (x + 255) / 256 * 256; };
     SplitLayout L{};
     L.S = S;
-    L.lda = round_up(n, 8);
-    L.ldb = round_up(p, 8);
+    L.esize = is_e4m3_split(dt) ? 1 : 2;
+    L.b_trans = is_e4m3_split(dt);
+    // row pitches: multiples of 16 bytes (TMA strides)
+    L.lda = round_up(n, 16 / L.esize);
+    L.ldb = L.b_trans ? round_up(n, 16) : round_up(p, 8);
+    const int64_t b_rows = L.b_trans ? p : n;
     size_t off = 0;
     L.a_off = off;
-    off += al(static_cast<size_t>(S) * m * L.lda * 2);
+    off += al(static_cast<size_t>(S) * m * L.lda * L.esize);
     L.b_off = off;
-    off += al(static_cast<size_t>(S) * n * L.ldb * 2);
+    off += al(static_cast<size_t>(S) * b_rows * L.ldb * L.esize);
     if (dt != MOA_F32_SPLIT) {
         L.ea_off = off;
         off += al(static_cast<size_t>(m) * 4);
@@ -757,13 +932,13 @@ size_t split_workspace_bytes(int64_t m, int64_t n, int64_t p, moa_dtype dt, int 
     return split_layout(m, n, p, dt, S).total;
 }
 
-template <int BN, int MODE>
+template <int BN, int MODE, int FMT>
 static int launch_split_cfg(const SplitArgs& a, const CUtensorMap& tmA, const CUtensorMap& tmB,
                             cudaStream_t s, moa_stats* st) {
-    using Cfg = SplitCfg<BN, MODE>;
+    using Cfg = SplitCfg<BN, MODE, FMT>;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel<BN, MODE>,
+        cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel<BN, MODE, FMT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(split_gemm)");
         attr_set = true;
@@ -771,14 +946,14 @@ static int launch_split_cfg(const SplitArgs& a, const CUtensorMap& tmA, const CU
     const long tiles = static_cast<long>(a.tiles_m) * a.tiles_n;
     const int grid = static_cast<int>(std::min<long>(tiles, num_sms()));
     prof_begin(s);
-    split_gemm_kernel<BN, MODE><<<grid, Cfg::kThreads, Cfg::kSmem, s>>>(tmA, tmB, a);
+    split_gemm_kernel<BN, MODE, FMT><<<grid, Cfg::kThreads, Cfg::kSmem, s>>>(tmA, tmB, a);
     cudaError_t e = cudaGetLastError();
     prof_end(s);
     if (e != cudaSuccess) return cuda_fail(e, "split_gemm_kernel launch");
     if (st) {
         st->block_m = kBM;
         st->block_n = BN;
-        st->block_k = kBK;
+        st->block_k = Cfg::kBKe;
         st->grid = grid;
         st->tiles = tiles;
     }
@@ -795,6 +970,42 @@ static int split_block_n(int64_t m, int64_t p, bool f64) {
     return tiles >= num_sms() ? 256 : 128;
 }
 
+// Exponent and digit pre-passes of the FP64-accuracy modes for input type T.
+template <typename T>
+static void digit_prepasses(const SplitLayout& L, int64_t m, int64_t n, int64_t p, const T* A,
+                            const T* B, int beta, int headroom, int* eA, int* eB, void* cmax,
+                            uint8_t* a_sl, uint8_t* b_sl, int* status, cudaStream_t s) {
+    using U = typename Bits<T>::U;
+    constexpr int per16 = 16 / sizeof(T);
+    const int S = L.S;
+    const int rows_per_block = 8;   // 8 warps of 32 threads
+    const int64_t rblocks = std::min<int64_t>(ceil_div(m, rows_per_block), 16L * num_sms());
+    const int64_t chunk = 256;
+    const dim3 cgrid(static_cast<unsigned>(ceil_div(p, 256)), static_cast<unsigned>(ceil_div(n, chunk)));
+    row_exp_kernel<T><<<static_cast<int>(rblocks), 256, 0, s>>>(A, m, n, headroom, eA, status);
+    col_max_kernel<T><<<cgrid, 256, 0, s>>>(B, n, p, chunk, static_cast<U*>(cmax));
+    col_exp_kernel<T><<<static_cast<int>(ceil_div(p, 256)), 256, 0, s>>>(
+        static_cast<const U*>(cmax), p, headroom, eB, status);
+    const int64_t a_plane = m * L.lda;
+    if (L.esize == 1) {
+        const int64_t b_plane = p * L.ldb;
+        digits_e4m3_rows_kernel<T><<<grid_for(a_plane / 16, 256), 256, 0, s>>>(
+            A, m, n, L.lda, eA, S, beta, vec_rows(A, n, per16), a_sl, a_plane);
+        const int64_t tiles = ceil_div(n, kTT) * ceil_div(p, kTT);
+        const int tgrid = static_cast<int>(std::min<int64_t>(tiles, 8L * num_sms()));
+        digits_e4m3_cols_t_kernel<T><<<tgrid, 256, 0, s>>>(B, n, p, L.ldb, eB, S, beta, b_sl,
+                                                           b_plane);
+    } else {
+        const int64_t b_plane = n * L.ldb;
+        auto* a16 = reinterpret_cast<__nv_bfloat16*>(a_sl);
+        auto* b16 = reinterpret_cast<__nv_bfloat16*>(b_sl);
+        digits_kernel<T><<<grid_for(a_plane / 8, 256), 256, 0, s>>>(
+            A, m, n, L.lda, eA, 0, S, vec_rows(A, n, per16), a16, a_plane);
+        digits_kernel<T><<<grid_for(b_plane / 8, 256), 256, 0, s>>>(
+            B, n, p, L.ldb, eB, 1, S, vec_rows(B, p, per16), b16, b_plane);
+    }
+}
+
 int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const void* B,
                void* C, int slices, void* ws, size_t ws_bytes, cudaStream_t s, moa_stats* st) {
     const int S = split_slices(dt, slices);
@@ -803,10 +1014,13 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
     if (ws_bytes < L.total) return fail(MOA_ERR_WORKSPACE, "workspace too small for split mode");
     int* status = launch_status_ptr();
     if (!status) return MOA_ERR_CUDA;
+    const bool e4m3 = is_e4m3_split(dt);
+    const int bke = e4m3 ? block_k<kFmtE4M3>() : block_k<kFmtBF16>();
     uint8_t* base = static_cast<uint8_t*>(ws);
-    __nv_bfloat16* a_sl = reinterpret_cast<__nv_bfloat16*>(base + L.a_off);
-    __nv_bfloat16* b_sl = reinterpret_cast<__nv_bfloat16*>(base + L.b_off);
-    const int64_t a_plane = m * L.lda, b_plane = n * L.ldb;
+    uint8_t* a_sl = base + L.a_off;
+    uint8_t* b_sl = base + L.b_off;
+    const int64_t a_plane = m * L.lda;
+    const int64_t b_plane = (L.b_trans ? p : n) * L.ldb;
     int kernels = 0;
 
     SplitArgs a{};
@@ -817,7 +1031,7 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
     const int bn = split_block_n(m, p, dt != MOA_F32_SPLIT);
     a.tiles_m = static_cast<int>(ceil_div(m, kBM));
     a.tiles_n = static_cast<int>(ceil_div(p, bn));
-    a.num_kb = static_cast<int>(ceil_div(n, kBK));
+    a.num_kb = static_cast<int>(ceil_div(n, bke));
     a.group_m = raster_group();
     a.S = S;
     a.wait_limit_ns = wait_limit_ns();
@@ -825,15 +1039,16 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
     a.vec_ok = (p % 4 == 0) && (reinterpret_cast<uintptr_t>(C) % 16 == 0);
 
     if (dt == MOA_F32_SPLIT) {
-        const int va = (n % 4 == 0) && (reinterpret_cast<uintptr_t>(A) % 16 == 0);
-        const int vb = (p % 4 == 0) && (reinterpret_cast<uintptr_t>(B) % 16 == 0);
+        auto* a16 = reinterpret_cast<__nv_bfloat16*>(a_sl);
+        auto* b16 = reinterpret_cast<__nv_bfloat16*>(b_sl);
         split3_kernel<<<grid_for(a_plane / 8, 256), 256, 0, s>>>(
-            static_cast<const float*>(A), m, n, L.lda, a_sl, a_plane, va, status);
+            static_cast<const float*>(A), m, n, L.lda, a16, a_plane, vec_rows(A, n, 4), status);
         split3_kernel<<<grid_for(b_plane / 8, 256), 256, 0, s>>>(
-            static_cast<const float*>(B), n, p, L.ldb, b_sl, b_plane, vb, status);
+            static_cast<const float*>(B), n, p, L.ldb, b16, b_plane, vec_rows(B, p, 4), status);
         kernels += 2;
         a.f64 = 0;
         a.levels = 1;
+        a.beta = 0;
         // Flush the FP32 TMEM accumulator into the epilogue's FP32 running sum
         // every kc K blocks: shorter chunks bound the accumulation error of
         // the tensor core's FP32 adds (MOA_F32_SPLIT_CHUNK_K, default 256).
@@ -843,81 +1058,82 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
         int* eA = reinterpret_cast<int*>(base + L.ea_off);
         int* eB = reinterpret_cast<int*>(base + L.eb_off);
         void* cmax = base + L.cmax_off;
-        const bool in64 = dt == MOA_F64_SPLIT_F64IN;
+        const int beta = e4m3 ? kBetaE4M3 : kBeta;
+        const int h = e4m3 ? kHeadroomE4M3 : 0;
+        if (ceil_div(n, 256) > 65535) return fail(MOA_ERR_ARG, "n too large for the column-max grid");
         cudaError_t e = cudaMemsetAsync(cmax, 0, static_cast<size_t>(p) * 8, s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(colmax)");
-        const int rows_per_block = 8;   // 8 warps of 32 threads
-        const int64_t rblocks = std::min<int64_t>(ceil_div(m, rows_per_block), 16L * num_sms());
-        const int64_t chunk = 256;
-        dim3 cgrid(static_cast<unsigned>(ceil_div(p, 256)), static_cast<unsigned>(ceil_div(n, chunk)));
-        if (cgrid.y > 65535) return fail(MOA_ERR_ARG, "n too large for the column-max grid");
-        if (in64) {
-            const double* Ad = static_cast<const double*>(A);
-            const double* Bd = static_cast<const double*>(B);
-            row_exp_kernel<double><<<static_cast<int>(rblocks), 256, 0, s>>>(Ad, m, n, eA, status);
-            col_max_kernel<double><<<cgrid, 256, 0, s>>>(Bd, n, p, chunk,
-                                                         static_cast<unsigned long long*>(cmax));
-            col_exp_kernel<double><<<static_cast<int>(ceil_div(p, 256)), 256, 0, s>>>(
-                static_cast<const unsigned long long*>(cmax), p, eB, status);
-            digits_kernel<double><<<grid_for(a_plane / 8, 256), 256, 0, s>>>(Ad, m, n, L.lda, eA, 0, S,
-                                                                          a_sl, a_plane);
-            digits_kernel<double><<<grid_for(b_plane / 8, 256), 256, 0, s>>>(Bd, n, p, L.ldb, eB, 1, S,
-                                                                          b_sl, b_plane);
-        } else {
-            const float* Af = static_cast<const float*>(A);
-            const float* Bf = static_cast<const float*>(B);
-            row_exp_kernel<float><<<static_cast<int>(rblocks), 256, 0, s>>>(Af, m, n, eA, status);
-            col_max_kernel<float><<<cgrid, 256, 0, s>>>(Bf, n, p, chunk,
-                                                        static_cast<unsigned int*>(cmax));
-            col_exp_kernel<float><<<static_cast<int>(ceil_div(p, 256)), 256, 0, s>>>(
-                static_cast<const unsigned int*>(cmax), p, eB, status);
-            digits_kernel<float><<<grid_for(a_plane / 8, 256), 256, 0, s>>>(Af, m, n, L.lda, eA, 0, S,
-                                                                        a_sl, a_plane);
-            digits_kernel<float><<<grid_for(b_plane / 8, 256), 256, 0, s>>>(Bf, n, p, L.ldb, eB, 1, S,
-                                                                        b_sl, b_plane);
-        }
+        if (dt == MOA_F64_SPLIT_F64IN || dt == MOA_F64_SPLIT_F64IN_E4M3)
+            digit_prepasses<double>(L, m, n, p, static_cast<const double*>(A),
+                                    static_cast<const double*>(B), beta, h, eA, eB, cmax, a_sl,
+                                    b_sl, status, s);
+        else
+            digit_prepasses<float>(L, m, n, p, static_cast<const float*>(A),
+                                   static_cast<const float*>(B), beta, h, eA, eB, cmax, a_sl, b_sl,
+                                   status, s);
         kernels += 6;
         a.f64 = 1;
         a.levels = S;
+        a.beta = beta;
         a.eA = eA;
         a.eB = eB;
         // Chunk lengths: every FP32 partial sum of a level must stay an
-        // integer of magnitude <= 2^24.  With |d_0| <= 2^beta and
-        // |d_s| <= 2^(beta-1), per k level 0 adds at most 2^(2 beta) and
-        // level L >= 1 at most 2 * 2^(2 beta - 1) + (L - 1) * 2^(2 beta - 2)
-        // = (L + 3) * 2^(2 beta - 2).
+        // integer of magnitude <= 2^24.  With |d_0| <= 2^(beta-h) and
+        // |d_s| <= 2^(beta-1), per k level 0 adds at most 2^(2(beta-h)) and
+        // level L >= 1 at most 2 * 2^(2 beta - 1 - h) + (L - 1) * 2^(2 beta - 2)
+        // = (L + 3 - 2h) * 2^(2 beta - 2).
         for (int lev = 0; lev < S; ++lev) {
-            const long long per_k = lev == 0 ? (1ll << (2 * kBeta))
-                                             : static_cast<long long>(lev + 3) << (2 * kBeta - 2);
+            const long long per_k = lev == 0
+                                        ? (1ll << (2 * (beta - h)))
+                                        : static_cast<long long>(lev + 3 - 2 * h) << (2 * beta - 2);
             const long long kmax = (1ll << 24) / per_k;
-            a.kc[lev] = static_cast<int>(std::max(1ll, kmax / kBK));
+            a.kc[lev] = static_cast<int>(std::max(1ll, kmax / bke));
         }
-        // int64 total: |T| <= n * 2^(beta(S+1)) * 1.02 in units of the finest
-        // level before dropping `drop` bits; keep it below 2^62.
+        // int64 total: |T| <= n * 2^(beta(S+1) - 2h) * 1.07 in units of the
+        // finest level before dropping `drop` bits; keep it below 2^62.
         int nbits = 0;
         while ((1ll << nbits) < n) ++nbits;
-        a.drop = std::max(0, nbits + kBeta * (S + 1) + 1 - 62);
+        a.drop = std::max(0, nbits + beta * (S + 1) - 2 * h + 1 - 62);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "split pre-pass launch");
 
     CUtensorMap tmA, tmB;
-    int rc = make_tmap_3d(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, a_sl, static_cast<uint64_t>(n),
+    int rc;
+    if (e4m3) {
+        // A planes: m rows x n bytes; B^T planes: p rows x n bytes; box
+        // 128 bytes of K x (128 | BN) rows.
+        rc = make_tmap_3d(&tmA, CU_TENSOR_MAP_DATA_TYPE_UINT8, a_sl, static_cast<uint64_t>(n),
+                          static_cast<uint64_t>(m), static_cast<uint64_t>(S),
+                          static_cast<uint64_t>(L.lda), static_cast<uint64_t>(a_plane), 128, kBM);
+        if (rc != MOA_OK) return rc;
+        rc = make_tmap_3d(&tmB, CU_TENSOR_MAP_DATA_TYPE_UINT8, b_sl, static_cast<uint64_t>(n),
+                          static_cast<uint64_t>(p), static_cast<uint64_t>(S),
+                          static_cast<uint64_t>(L.ldb), static_cast<uint64_t>(b_plane), 128,
+                          static_cast<uint32_t>(bn));
+        if (rc != MOA_OK) return rc;
+        rc = bn == 256   ? launch_split_cfg<256, kModeF64Tmem, kFmtE4M3>(a, tmA, tmB, s, st)
+             : bn == 192 ? launch_split_cfg<192, kModeF64Reg, kFmtE4M3>(a, tmA, tmB, s, st)
+                         : launch_split_cfg<128, kModeF64Reg, kFmtE4M3>(a, tmA, tmB, s, st);
+    } else {
+        rc = make_tmap_3d(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, a_sl, static_cast<uint64_t>(n),
                           static_cast<uint64_t>(m), static_cast<uint64_t>(S),
                           static_cast<uint64_t>(L.lda) * 2, static_cast<uint64_t>(a_plane) * 2, 64,
                           kBM);
-    if (rc != MOA_OK) return rc;
-    rc = make_tmap_3d(&tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, b_sl, static_cast<uint64_t>(p),
-                      static_cast<uint64_t>(n), static_cast<uint64_t>(S),
-                      static_cast<uint64_t>(L.ldb) * 2, static_cast<uint64_t>(b_plane) * 2, 64, kBK);
-    if (rc != MOA_OK) return rc;
-    if (a.f64)
-        rc = bn == 256   ? launch_split_cfg<256, kModeF64Tmem>(a, tmA, tmB, s, st)
-             : bn == 192 ? launch_split_cfg<192, kModeF64Reg>(a, tmA, tmB, s, st)
-                         : launch_split_cfg<128, kModeF64Reg>(a, tmA, tmB, s, st);
-    else
-        rc = bn == 256 ? launch_split_cfg<256, kModeF32>(a, tmA, tmB, s, st)
-                       : launch_split_cfg<128, kModeF32>(a, tmA, tmB, s, st);
+        if (rc != MOA_OK) return rc;
+        rc = make_tmap_3d(&tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, b_sl, static_cast<uint64_t>(p),
+                          static_cast<uint64_t>(n), static_cast<uint64_t>(S),
+                          static_cast<uint64_t>(L.ldb) * 2, static_cast<uint64_t>(b_plane) * 2, 64,
+                          kBK);
+        if (rc != MOA_OK) return rc;
+        if (a.f64)
+            rc = bn == 256   ? launch_split_cfg<256, kModeF64Tmem, kFmtBF16>(a, tmA, tmB, s, st)
+                 : bn == 192 ? launch_split_cfg<192, kModeF64Reg, kFmtBF16>(a, tmA, tmB, s, st)
+                             : launch_split_cfg<128, kModeF64Reg, kFmtBF16>(a, tmA, tmB, s, st);
+        else
+            rc = bn == 256 ? launch_split_cfg<256, kModeF32, kFmtBF16>(a, tmA, tmB, s, st)
+                           : launch_split_cfg<128, kModeF32, kFmtBF16>(a, tmA, tmB, s, st);
+    }
     if (st) {
         st->slices = S;
         st->products = dt == MOA_F32_SPLIT ? 6 : S * (S + 1) / 2;

@@ -5,8 +5,12 @@
 
 namespace moa {
 
+inline bool is_e4m3_split(moa_dtype dt) {
+    return dt == MOA_F64_SPLIT_F32IN_E4M3 || dt == MOA_F64_SPLIT_F64IN_E4M3;
+}
 inline bool is_split(moa_dtype dt) {
-    return dt == MOA_F32_SPLIT || dt == MOA_F64_SPLIT_F32IN || dt == MOA_F64_SPLIT_F64IN;
+    return dt == MOA_F32_SPLIT || dt == MOA_F64_SPLIT_F32IN || dt == MOA_F64_SPLIT_F64IN ||
+           is_e4m3_split(dt);
 }
 
 // Digit radix 2^kBeta of the FP64-accuracy mode and its slice-count limits.
@@ -17,6 +21,19 @@ constexpr int kBeta = 7;
 constexpr int kMinSlices = 3;
 constexpr int kMaxSlices = 8;
 constexpr int kDefaultSlices = 7;
+
+// The same method with FP8 E4M3 digit planes (kind::f8f6f4, twice the BF16
+// MMA rate): radix 2^5 and one headroom bit, so every digit, the top one
+// included, lies in [-16, 16] -- integers E4M3 holds exactly (3 stored
+// mantissa bits).  10 digits keep 5 * 10 - 1 = 49 bits per operand, as 7
+// BF16 digits do; the triangle has 55 products instead of 28, each at twice
+// the rate, and every per-k digit product is at most 2^8, so the exact FP32
+// chunks are 16x longer than with radix 2^7.
+constexpr int kBetaE4M3 = 5;
+constexpr int kHeadroomE4M3 = 1;
+constexpr int kMinSlicesE4M3 = 4;
+constexpr int kMaxSlicesE4M3 = 12;
+constexpr int kDefaultSlicesE4M3 = 10;
 
 // Resolves the `slices` argument (0 = default); -1 if not allowed for dt.
 int split_slices(moa_dtype dt, int slices);
@@ -29,8 +46,11 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
 // Workspace layout of a split call (byte offsets from the workspace base).
 struct SplitLayout {
     int S;                 // slices per operand
+    int esize;             // bytes per slice element: 2 (BF16) or 1 (E4M3)
+    bool b_trans;          // E4M3: B's planes hold B^T (p x ldb, K-major)
     int64_t lda, ldb;      // padded row pitches of the slice planes (elements)
-    size_t a_off, b_off;   // slice planes: S x m x lda and S x n x ldb BF16
+    size_t a_off, b_off;   // slice planes: S x m x lda and S x n x ldb (S x p x ldb
+                           // when b_trans)
     size_t ea_off, eb_off; // FP64-accuracy: per-row / per-column exponents (int32)
     size_t cmax_off;       // FP64-accuracy: per-column max |B| bit patterns (uint64)
     size_t total;

@@ -40,12 +40,23 @@ MOA_BF16 = 3
 MOA_F32_SPLIT = 4
 MOA_F64_SPLIT_F32IN = 5
 MOA_F64_SPLIT_F64IN = 6
+MOA_F64_SPLIT_F32IN_E4M3 = 7
+MOA_F64_SPLIT_F64IN_E4M3 = 8
 
 MODES = {
     "f64": MOA_F64, "tf32": MOA_F32_TF32, "f32_simt": MOA_F32_SIMT, "bf16": MOA_BF16,
     "f32_split": MOA_F32_SPLIT, "f64_split_f32in": MOA_F64_SPLIT_F32IN,
     "f64_split_f64in": MOA_F64_SPLIT_F64IN,
+    "f64_split_f32in_e4m3": MOA_F64_SPLIT_F32IN_E4M3,
+    "f64_split_f64in_e4m3": MOA_F64_SPLIT_F64IN_E4M3,
 }
+# FP64-accuracy modes (FP64 output) and their digit format: (radix bits, headroom bits)
+F64_ACCURATE = (MOA_F64, MOA_F64_SPLIT_F32IN, MOA_F64_SPLIT_F64IN, MOA_F64_SPLIT_F32IN_E4M3,
+                MOA_F64_SPLIT_F64IN_E4M3)
+DIGITS = {MOA_F64_SPLIT_F32IN: (7, 0), MOA_F64_SPLIT_F64IN: (7, 0),
+          MOA_F64_SPLIT_F32IN_E4M3: (5, 1), MOA_F64_SPLIT_F64IN_E4M3: (5, 1)}
+DEFAULT_SLICES = {MOA_F32_SPLIT: 3, MOA_F64_SPLIT_F32IN: 7, MOA_F64_SPLIT_F64IN: 7,
+                  MOA_F64_SPLIT_F32IN_E4M3: 10, MOA_F64_SPLIT_F64IN_E4M3: 10}
 
 
 class moa_stats(ctypes.Structure):
@@ -210,13 +221,12 @@ def moa_version() -> str:
 # ---------------------------------------------------------------- torch helpers
 def out_dtype(dt: int):
     import torch
-    return torch.float64 if dt in (MOA_F64, MOA_F64_SPLIT_F32IN, MOA_F64_SPLIT_F64IN) \
-        else torch.float32
+    return torch.float64 if dt in F64_ACCURATE else torch.float32
 
 
 def in_dtype(dt: int):
     import torch
-    if dt in (MOA_F64, MOA_F64_SPLIT_F64IN):
+    if dt in (MOA_F64, MOA_F64_SPLIT_F64IN, MOA_F64_SPLIT_F64IN_E4M3):
         return torch.float64
     if dt == MOA_BF16:
         return torch.bfloat16

@@ -75,7 +75,8 @@ def test_missing_workspace_rejected(L):
     assert need > 0
     rc = moa.moa_gemm_ex(8, 5, 8, moa.MOA_F32_TF32, 256, 512, 1024, 0, None, 0, None)
     assert rc == moa.MOA_ERR_WORKSPACE
-    for dt in (moa.MOA_F32_SPLIT, moa.MOA_F64_SPLIT_F32IN, moa.MOA_F64_SPLIT_F64IN):
+    for dt in (moa.MOA_F32_SPLIT, moa.MOA_F64_SPLIT_F32IN, moa.MOA_F64_SPLIT_F64IN,
+               moa.MOA_F64_SPLIT_F32IN_E4M3, moa.MOA_F64_SPLIT_F64IN_E4M3):
         assert moa.moa_gemm_workspace_size(64, 64, 64, dt, 0) > 0
         rc = moa.moa_gemm_ex(64, 64, 64, dt, 256, 512, 1024, 0, None, 0, None)
         assert rc == moa.MOA_ERR_WORKSPACE
@@ -96,6 +97,17 @@ def test_workspace_sizes(L):
     assert moa.moa_gemm_workspace_size(256, 256, 256, moa.MOA_F64_SPLIT_F32IN, 9) == 0
     assert moa.moa_gemm_ex(64, 64, 64, moa.MOA_F64_SPLIT_F32IN, 256, 512, 1024, 9, 4096, 1 << 20,
                            None) == moa.MOA_ERR_DTYPE
+    # E4M3 digit planes: one byte per element, B stored transposed; 4..12 slices
+    e10 = moa.moa_gemm_workspace_size(256, 256, 256, moa.MOA_F64_SPLIT_F32IN_E4M3, 0)
+    assert e10 == moa.moa_gemm_workspace_size(256, 256, 256, moa.MOA_F64_SPLIT_F32IN_E4M3, 10)
+    assert e10 >= 10 * 2 * (256 * 256)
+    assert moa.moa_gemm_workspace_size(256, 256, 256, moa.MOA_F64_SPLIT_F64IN_E4M3, 12) > e10
+    for bad in (3, 13):
+        assert moa.moa_gemm_workspace_size(256, 256, 256, moa.MOA_F64_SPLIT_F32IN_E4M3, bad) == 0
+    # a 5-column B is padded to 16-byte rows of its transpose: p rows of round_up(n, 16)
+    w = moa.moa_gemm_workspace_size(16, 5, 3, moa.MOA_F64_SPLIT_F32IN_E4M3, 4)
+    assert w >= 4 * (16 * 16 + 3 * 16)
+    assert moa.moa_gemm_ex(4, 4, 4, 9, 16, 16, 16, 0, None, 0, None) == moa.MOA_ERR_DTYPE
 
 
 def test_empty_problems_are_noops(L):
@@ -116,6 +128,8 @@ def test_binding_refuses_mismatched_tensors(L):
     B = torch.zeros((8, 3), dtype=torch.float32)
     with pytest.raises(TypeError):       # FP64-input mode reads 8 bytes per element
         moa.check_tensors(A, B, None, moa.MOA_F64_SPLIT_F64IN)
+    with pytest.raises(TypeError):
+        moa.check_tensors(A, B, None, moa.MOA_F64_SPLIT_F64IN_E4M3)
     with pytest.raises(TypeError):
         moa.check_tensors(A, B, torch.zeros((4, 3), dtype=torch.float32), moa.MOA_F64_SPLIT_F32IN)
     with pytest.raises(ValueError):      # CPU tensors are not device memory

@@ -29,6 +29,8 @@ TOL = {
     moa.MOA_F32_SPLIT: 1e-5,
     moa.MOA_F64_SPLIT_F32IN: 1e-12,
     moa.MOA_F64_SPLIT_F64IN: 1e-12,
+    moa.MOA_F64_SPLIT_F32IN_E4M3: 1e-12,
+    moa.MOA_F64_SPLIT_F64IN_E4M3: 1e-12,
 }
 ALL_MODES = list(TOL)
 NAMES = {v: k for k, v in moa.MODES.items()}
@@ -75,8 +77,8 @@ def test_uniform_inputs_within_tolerance(dt, m, n, p):
     assert _rel(C, ref) <= TOL[dt]
 
 
-@pytest.mark.parametrize("dt", [moa.MOA_F32_SPLIT, moa.MOA_F64_SPLIT_F32IN, moa.MOA_F32_TF32],
-                         ids=lambda d: NAMES[d])
+@pytest.mark.parametrize("dt", [moa.MOA_F32_SPLIT, moa.MOA_F64_SPLIT_F32IN, moa.MOA_F32_TF32,
+                                moa.MOA_F64_SPLIT_F32IN_E4M3], ids=lambda d: NAMES[d])
 @pytest.mark.parametrize("scaled", [None, "rows", "rowcol"])
 def test_normal_scaled_inputs(dt, scaled):
     A, B = inputs.normal_pair(200, 1536, 160, dtype=torch.float32, seed=3, scaled=scaled)
@@ -85,19 +87,21 @@ def test_normal_scaled_inputs(dt, scaled):
     assert _rel(C, ref) <= TOL[dt]
 
 
-BETA = 7   # digit radix 2^7 of the FP64-accuracy mode
-
-
-@pytest.mark.parametrize("S", [3, 4, 5, 6, 7, 8])
-def test_f64_split_matches_exact_slice_product(S):
+@pytest.mark.parametrize("dt,S", [pytest.param(dt, S, id=f"{NAMES[dt]}-S{S}")
+                                  for dt, Ss in ((moa.MOA_F64_SPLIT_F64IN, (3, 4, 5, 6, 7, 8)),
+                                                 (moa.MOA_F64_SPLIT_F64IN_E4M3, (4, 6, 8, 10, 12)))
+                                  for S in Ss])
+def test_f64_split_matches_exact_slice_product(dt, S):
     """The FP64-accuracy mode reaches the exact triangular slice product of
-    the oracle's digits, up to the final FP64 rounding and the int64 total's
-    dropped low bits (relative 2^-48 of the scale)."""
+    the oracle's digits (radix 2^7 for BF16 planes; radix 2^5 with one
+    headroom bit for E4M3 planes), up to the final FP64 rounding and the
+    int64 total's dropped low bits (relative 2^-46 of the scale)."""
+    beta, h = moa.DIGITS[dt]
     A, B = inputs.normal_pair(130, 700, 140, dtype=torch.float64, seed=5, scaled="rows")
-    C = _run(A, B, moa.MOA_F64_SPLIT_F64IN, slices=S)
-    eA, dA = oracle.slice_fixed(A.numpy(), 0, BETA, S)
-    eB, dB = oracle.slice_fixed(B.numpy(), 1, BETA, S)
-    exact = oracle.split_gemm_exact(dA, eA, dB, eB, BETA, S)
+    C = _run(A, B, dt, slices=S)
+    eA, dA = oracle.slice_fixed(A.numpy(), 0, beta, S, headroom=h)
+    eB, dB = oracle.slice_fixed(B.numpy(), 1, beta, S, headroom=h)
+    exact = oracle.split_gemm_exact(dA, eA, dB, eB, beta, S)
     scale = np.outer(2.0 ** eA.astype(np.float64), 2.0 ** eB.astype(np.float64))
     assert np.all(np.abs(C - exact) <= scale * 2.0 ** -46 + np.abs(exact) * 2.0 ** -52)
 
@@ -137,7 +141,7 @@ def test_empty_outer_dimensions_touch_nothing():
 
 
 def test_nonfinite_input_reported_by_split_modes():
-    for dt in (moa.MOA_F32_SPLIT, moa.MOA_F64_SPLIT_F32IN):
+    for dt in (moa.MOA_F32_SPLIT, moa.MOA_F64_SPLIT_F32IN, moa.MOA_F64_SPLIT_F32IN_E4M3):
         A, B = inputs.uniform_pair(64, 64, 64, dtype=torch.float32, seed=2)
         A[3, 5] = float("nan")
         moa.gemm(A.cuda(), B.cuda(), dt)
@@ -162,7 +166,8 @@ def test_deterministic_repeat():
     """Two runs give bit-identical results (catches pipeline races)."""
     A, B = inputs.uniform_pair(384, 2048, 512, dtype=torch.float32, seed=6)
     Ad, Bd = A.cuda(), B.cuda()
-    for dt in (moa.MOA_F32_TF32, moa.MOA_F32_SPLIT, moa.MOA_F64_SPLIT_F32IN):
+    for dt in (moa.MOA_F32_TF32, moa.MOA_F32_SPLIT, moa.MOA_F64_SPLIT_F32IN,
+               moa.MOA_F64_SPLIT_F32IN_E4M3):
         c1 = moa.gemm(Ad, Bd, dt).clone()
         c2 = moa.gemm(Ad, Bd, dt)
         torch.cuda.synchronize()
@@ -171,6 +176,7 @@ def test_deterministic_repeat():
 
 @pytest.mark.parametrize("dt,N", [(moa.MOA_F32_TF32, 8192), (moa.MOA_BF16, 8192),
                                   (moa.MOA_F32_SPLIT, 8192), (moa.MOA_F64_SPLIT_F32IN, 8192),
+                                  (moa.MOA_F64_SPLIT_F32IN_E4M3, 8192),
                                   (moa.MOA_F64, 2048), (moa.MOA_F32_SIMT, 4096)],
                          ids=lambda x: NAMES.get(x, str(x)) if isinstance(x, int) and x < 10 else str(x))
 def test_full_size_sampled_rows(dt, N):
@@ -188,7 +194,8 @@ def test_full_size_sampled_rows(dt, N):
 
 
 @pytest.mark.parametrize("dt", [moa.MOA_BF16, moa.MOA_F32_TF32, moa.MOA_F32_SPLIT,
-                                moa.MOA_F64_SPLIT_F32IN], ids=lambda d: NAMES[d])
+                                moa.MOA_F64_SPLIT_F32IN, moa.MOA_F64_SPLIT_F32IN_E4M3],
+                         ids=lambda d: NAMES[d])
 @pytest.mark.parametrize("m,n,p", [(1, 8192, 8192), (8192, 1, 8192), (8192, 8192, 1),
                                    (2, 3, 16384), (16384, 7, 5)])
 def test_extreme_aspect_ratios(dt, m, n, p):
@@ -203,7 +210,8 @@ def test_extreme_aspect_ratios(dt, m, n, p):
     assert _rel(got, ref) <= TOL[dt]
 
 
-@pytest.mark.parametrize("dt", [moa.MOA_F32_TF32, moa.MOA_F64_SPLIT_F64IN], ids=lambda d: NAMES[d])
+@pytest.mark.parametrize("dt", [moa.MOA_F32_TF32, moa.MOA_F64_SPLIT_F64IN,
+                                moa.MOA_F64_SPLIT_F64IN_E4M3], ids=lambda d: NAMES[d])
 def test_largest_square_size(dt):
     """N = 16384, the largest size of the square sweep (FP64 operands: 3 x 2 GiB),
     on 8 sampled rows."""

@@ -88,7 +88,8 @@ def test_tuner_records_and_reuses_choice(L, tmp_path):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("dt,widths", [(moa.MOA_F32_SPLIT, (128, 256)),
-                                       (moa.MOA_F64_SPLIT_F32IN, (128, 192, 256))])
+                                       (moa.MOA_F64_SPLIT_F32IN, (128, 192, 256)),
+                                       (moa.MOA_F64_SPLIT_F32IN_E4M3, (128, 192, 256))])
 def test_split_tile_widths_agree(L, dt, widths):
     """Every slice-GEMM tile width sums the same chunks in the same order, so
     the results are bit-identical; each is within the mode's tolerance."""
