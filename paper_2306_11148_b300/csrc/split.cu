@@ -175,35 +175,94 @@ struct Bits<float> {
         if (ex > 0) return ex - 126;
         return (32 - __clz(static_cast<int>(M))) - 149;
     }
-    __device__ static long long round_scaled(float x, int k) {
-        const U b = __float_as_uint(x);
-        const bool neg = (b >> 31) != 0;
+};
+
+// Digit generator of one element: D = round_half_even(x * 2^k) written as
+// balanced radix-2^beta digits from the bottom, d_s for s = S-1 .. 1 in
+// [-2^(beta-1), 2^(beta-1)), then d_0 = what is left.  next(s) must be called
+// for s = S-1, S-2, ..., 0 in that order.
+template <typename T>
+struct DigitGen;
+
+// FP64 input: D needs up to 62 bits; 64-bit integer steps.
+template <>
+struct DigitGen<double> {
+    long long D;
+    __device__ void start(double x, int k, int) { D = Bits<double>::round_scaled(x, k); }
+    __device__ int next(int s, int beta, int) {
+        if (s == 0) return static_cast<int>(D);
+        const int radix = 1 << beta;
+        int low = static_cast<int>(D) & (radix - 1);
+        low -= (low & (radix >> 1)) << 1;
+        D = (D - low) >> beta;
+        return low;
+    }
+    // next(s) + 2^(beta-1): with t = D + 2^(beta-1), the balanced digit plus
+    // its bias is t mod 2^beta and the remainder is floor(t / 2^beta).
+    __device__ int next_biased(int s, int beta, int) {
+        const long long t = D + (1ll << (beta - 1));
+        if (s == 0) return static_cast<int>(t);
+        D = t >> beta;
+        return static_cast<int>(t) & ((1 << beta) - 1);
+    }
+};
+
+// FP32 input: D = M * 2^sh with a 24-bit M.  For sh >= 0 the bottom
+// zd = floor(sh / beta) digits are zero and the rest come from the 32-bit
+// m = M * 2^(sh mod beta) (below 2^(24 + beta - 1) <= 2^30); for sh < 0, D
+// itself is below 2^25.  All steps are 32-bit.
+template <>
+struct DigitGen<float> {
+    int m;
+    int zd;
+    __device__ void start(float x, int k, int beta) {
+        const uint32_t b = __float_as_uint(x);
         const int ex = static_cast<int>((b >> 23) & 0xFF);
-        unsigned long long mant = b & 0x7FFFFFu;
-        int E;
-        if (ex == 0) {
-            E = -149;
-        } else {
-            mant |= 1ull << 23;
+        uint32_t mant = b & 0x7FFFFFu;
+        int E = -149;
+        if (ex != 0) {
+            mant |= 1u << 23;
             E = ex - 150;
         }
-        if (mant == 0) return 0;
         const int sh = E + k;
-        unsigned long long D;
-        if (sh >= 0) {
-            D = mant << sh;
+        uint32_t mag;
+        if (mant == 0) {
+            mag = 0;
+            zd = 0;
+        } else if (sh >= 0) {
+            zd = sh / beta;
+            mag = mant << (sh - zd * beta);
         } else {
+            zd = 0;
             const int kk = -sh;
             if (kk > 25) {
-                D = 0;
+                mag = 0;
             } else {
-                const unsigned long long q = mant >> kk;
-                const unsigned long long rem = mant & ((1ull << kk) - 1);
-                const unsigned long long half = 1ull << (kk - 1);
-                D = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+                const uint32_t q = mant >> kk;
+                const uint32_t rem = mant & ((1u << kk) - 1u);
+                const uint32_t half = 1u << (kk - 1);
+                mag = q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u);
             }
         }
-        return neg ? -static_cast<long long>(D) : static_cast<long long>(D);
+        m = (b >> 31) ? -static_cast<int>(mag) : static_cast<int>(mag);
+    }
+    __device__ int next(int s, int beta, int S) {
+        const int pos = S - 1 - s;   // digit position from the bottom
+        if (pos < zd) return 0;
+        if (s == 0) return m;
+        const int radix = 1 << beta;
+        int low = m & (radix - 1);
+        low -= (low & (radix >> 1)) << 1;
+        m = (m - low) >> beta;
+        return low;
+    }
+    __device__ int next_biased(int s, int beta, int S) {
+        const int half = 1 << (beta - 1);
+        const int t = m + half;
+        const bool zero = S - 1 - s < zd;
+        if (s == 0) return zero ? half : t;
+        m = zero ? m : (t >> beta);
+        return zero ? half : (t & ((1 << beta) - 1));
     }
 };
 
@@ -284,40 +343,24 @@ __global__ void digits_kernel(const T* __restrict__ X, int64_t rows, int64_t col
                               __nv_bfloat16* __restrict__ out, int64_t plane) {
     const int64_t gpr = ld / 8;
     const int64_t total = rows * gpr;
-    constexpr int radix = 1 << kBeta;
     for (int64_t g = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; g < total;
          g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int64_t r = g / gpr, c0 = (g - r * gpr) * 8;
         T x[8];
         load8(X, r, cols, c0, vec != 0, x);
-        long long D[8];
+        DigitGen<T> D[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int64_t c = c0 + i;
             const int ex = c < cols ? (axis == 0 ? e[r] : e[c]) : 0;
-            D[i] = Bits<T>::round_scaled(x[i], kBeta * S - ex);
+            D[i].start(x[i], kBeta * S - ex, kBeta);
         }
         const int64_t o = r * ld + c0;
         for (int s = S - 1; s >= 0; --s) {
             uint32_t w[4];
 #pragma unroll
-            for (int i = 0; i < 8; i += 2) {
-                int d[2];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if (s > 0) {
-                        // balanced digit in [-radix/2, radix/2): the low kBeta
-                        // bits, less radix when the top one is set
-                        int low = static_cast<int>(D[i + h]) & (radix - 1);
-                        low -= (low & (radix >> 1)) << 1;
-                        D[i + h] = (D[i + h] - low) >> kBeta;
-                        d[h] = low;
-                    } else {
-                        d[h] = static_cast<int>(D[i + h]);   // |d_0| <= radix
-                    }
-                }
-                w[i / 2] = small_ints_bf16x2(d[0], d[1]);
-            }
+            for (int i = 0; i < 8; i += 2)   // |d| <= 2^kBeta: exact BF16 values
+                w[i / 2] = small_ints_bf16x2(D[i].next(s, kBeta, S), D[i + 1].next(s, kBeta, S));
             *reinterpret_cast<uint4*>(out + s * plane + o) = make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
@@ -333,15 +376,13 @@ __device__ __forceinline__ uint32_t e4m3_of_small_int(int v) {
     return a == 0 ? 0u : (bits | (v < 0 ? 0x80u : 0u));
 }
 
-// Balanced radix-2^beta digit at position s (s >= 1 from the bottom; the
-// remainder D is shifted down in place); s == 0 returns what is left.
-__device__ __forceinline__ int next_digit(long long& D, int s, int beta) {
-    if (s == 0) return static_cast<int>(D);
-    const int radix = 1 << beta;
-    int low = static_cast<int>(D) & (radix - 1);
-    low -= (low & (radix >> 1)) << 1;
-    D = (D - low) >> beta;
-    return low;
+// Shared-memory table of the E4M3 codes of the biased digits: lut[i] is the
+// code of i - 2^(beta-1), i in [0, 2^beta].  Filled by the first threads of
+// the block; the caller synchronises before use.
+__device__ __forceinline__ void fill_e4m3_lut(uint8_t* lut, int beta) {
+    const int half = 1 << (beta - 1);
+    if (threadIdx.x <= 2 * half) lut[threadIdx.x] = static_cast<uint8_t>(e4m3_of_small_int(
+                                     static_cast<int>(threadIdx.x) - half));
 }
 
 // Integer digits (radix 2^beta) of a row-major matrix whose exponent is per
@@ -351,19 +392,22 @@ template <typename T>
 __global__ void digits_e4m3_rows_kernel(const T* __restrict__ X, int64_t rows, int64_t cols,
                                         int64_t ld, const int* __restrict__ e, int S, int beta,
                                         int vec, uint8_t* __restrict__ out, int64_t plane) {
+    __shared__ uint8_t lut[64];
+    fill_e4m3_lut(lut, beta);
+    __syncthreads();
     const int64_t gpr = ld / 16;
     const int64_t total = rows * gpr;
     for (int64_t g = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; g < total;
          g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int64_t r = g / gpr, c0 = (g - r * gpr) * 16;
         const int ex = e[r];
-        long long D[16];
+        DigitGen<T> D[16];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             T x[8];
             load8(X, r, cols, c0 + 8 * h, vec != 0, x);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) D[8 * h + i] = Bits<T>::round_scaled(x[i], beta * S - ex);
+            for (int i = 0; i < 8; ++i) D[8 * h + i].start(x[i], beta * S - ex, beta);
         }
         const int64_t o = r * ld + c0;
         for (int s = S - 1; s >= 0; --s) {
@@ -373,7 +417,8 @@ __global__ void digits_e4m3_rows_kernel(const T* __restrict__ X, int64_t rows, i
                 uint32_t word = 0;
 #pragma unroll
                 for (int b = 0; b < 4; ++b)
-                    word |= e4m3_of_small_int(next_digit(D[4 * q + b], s, beta)) << (8 * b);
+                    word |= static_cast<uint32_t>(lut[D[4 * q + b].next_biased(s, beta, S)])
+                            << (8 * b);
                 w[q] = word;
             }
             *reinterpret_cast<uint4*>(out + s * plane + o) = make_uint4(w[0], w[1], w[2], w[3]);
@@ -384,9 +429,10 @@ __global__ void digits_e4m3_rows_kernel(const T* __restrict__ X, int64_t rows, i
 // Integer digits of B (n x p row-major, exponent per column j) written
 // transposed as E4M3 bytes: plane s holds B_s^T, p rows of pitch ld (a
 // multiple of 16; zero pad past n), so that the slice GEMM reads B K-major.
-// One 64 (k) x 64 (j) tile per block pass, 256 threads: reads are coalesced
-// along j, each plane goes through a padded shared-memory tile and is
-// written as 16-byte row segments along k.
+// One 64 (k) x 64 (j) tile per block pass, 256 threads; thread (j, q) holds
+// the 16 consecutive k of quarter q in column j.  Reads are coalesced along j;
+// each plane goes through a padded shared-memory tile (one 32-bit store per
+// 4 bytes) and is written as 16-byte row segments along k.
 constexpr int kTT = 64;
 template <typename T>
 __global__ void __launch_bounds__(256)
@@ -394,27 +440,34 @@ __global__ void __launch_bounds__(256)
                               const int* __restrict__ e, int S, int beta,
                               uint8_t* __restrict__ out, int64_t plane) {
     __shared__ uint32_t tile[kTT * (kTT / 4 + 1)];   // [j][k/4], 17 words per row
+    __shared__ uint8_t lut[64];
+    fill_e4m3_lut(lut, beta);
+    __syncthreads();
     const int t = threadIdx.x;
     const int64_t tk = (rows + kTT - 1) / kTT, tj = (cols + kTT - 1) / kTT;
     for (int64_t b = blockIdx.x; b < tk * tj; b += gridDim.x) {
         const int64_t k0 = (b / tj) * kTT, j0 = (b % tj) * kTT;
-        const int jl = t % kTT, kq = t / kTT;          // column in tile, k phase 0..3
+        const int jl = t % kTT, kq = t / kTT;          // column in tile, k quarter 0..3
         const int64_t j = j0 + jl;
         const int ex = j < cols ? e[j] : 0;
-        long long D[16];
+        DigitGen<T> D[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-            const int64_t k = k0 + kq + 4 * i;
+            const int64_t k = k0 + 16 * kq + i;
             const T x = (j < cols && k < rows) ? X[k * cols + j] : T(0);
-            D[i] = Bits<T>::round_scaled(x, beta * S - ex);
+            D[i].start(x, beta * S - ex, beta);
         }
-        uint8_t* tb = reinterpret_cast<uint8_t*>(tile);
         for (int s = S - 1; s >= 0; --s) {
             __syncthreads();   // the previous plane's tile has been written out
 #pragma unroll
-            for (int i = 0; i < 16; ++i)
-                tb[jl * (4 * (kTT / 4 + 1)) + kq + 4 * i] =
-                    static_cast<uint8_t>(e4m3_of_small_int(next_digit(D[i], s, beta)));
+            for (int q = 0; q < 4; ++q) {
+                uint32_t word = 0;
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    word |= static_cast<uint32_t>(lut[D[4 * q + b].next_biased(s, beta, S)])
+                            << (8 * b);
+                tile[jl * (kTT / 4 + 1) + 4 * kq + q] = word;
+            }
             __syncthreads();
             // thread t writes row jr = t / 4, bytes [16 c, 16 c + 16) of the tile
             const int jr = t / 4, c = t % 4;
