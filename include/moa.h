@@ -69,8 +69,8 @@ typedef enum {
     MOA_F64_SPLIT_F32IN_E4M3 = 7, /* A,B FP32, C FP64.  As MOA_F64_SPLIT_F32IN with FP8 E4M3 */
                               /*   digit slices (radix 2^5, one headroom bit: every digit in */
                               /*   [-16, 16], exact in E4M3) on tcgen05 kind::f8f6f4.        */
-                              /*   slices: 4..12, default 10 (49 bits per operand, as 7     */
-                              /*   BF16 digits); 55 slice products at twice the BF16 rate.   */
+                              /*   slices: 4..12, default 10 (a 49-bit span per operand);   */
+                              /*   55 slice products at twice the BF16 rate.                 */
     MOA_F64_SPLIT_F64IN_E4M3 = 8  /* A,B,C FP64.  As above with FP64 inputs.                 */
 } moa_dtype;
 

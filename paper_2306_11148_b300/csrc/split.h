@@ -25,10 +25,12 @@ constexpr int kDefaultSlices = 7;
 // The same method with FP8 E4M3 digit planes (kind::f8f6f4, twice the BF16
 // MMA rate): radix 2^5 and one headroom bit, so every digit, the top one
 // included, lies in [-16, 16] -- integers E4M3 holds exactly (3 stored
-// mantissa bits).  10 digits keep 5 * 10 - 1 = 49 bits per operand, as 7
-// BF16 digits do; the triangle has 55 products instead of 28, each at twice
-// the rate, and every per-k digit product is at most 2^8, so the exact FP32
-// chunks are 16x longer than with radix 2^7.
+// mantissa bits).  10 digits span 5 * 10 - 1 = 49 bits per operand, as 7
+// BF16 digits do, and keep the relative error of the slice product near
+// 1e-13 (the dropped part of the triangle is larger than with radix 2^7);
+// the triangle has 55 products instead of 28, each at twice the rate, and
+// every per-k digit product is at most 2^8, so the exact FP32 chunks are 16x
+// longer than with radix 2^7.
 constexpr int kBetaE4M3 = 5;
 constexpr int kHeadroomE4M3 = 1;
 constexpr int kMinSlicesE4M3 = 4;

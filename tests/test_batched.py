@@ -31,7 +31,8 @@ def test_batched_argument_errors(L):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("dt", [moa.MOA_BF16, moa.MOA_F32_TF32, moa.MOA_F64_SPLIT_F32IN])
+@pytest.mark.parametrize("dt", [moa.MOA_BF16, moa.MOA_F32_TF32, moa.MOA_F64_SPLIT_F32IN,
+                                moa.MOA_F64_SPLIT_F32IN_E4M3])
 @pytest.mark.parametrize("broadcast_b", [False, True])
 def test_batched_matches_single_and_oracle(dt, broadcast_b):
     batch, m, n, p = 6, 192, 320, 256

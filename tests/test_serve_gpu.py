@@ -22,7 +22,8 @@ import torch
 import oracle
 from paper_2306_11148_b300 import inputs, moa
 
-TOL = {moa.MOA_F32_SPLIT: 1e-5, moa.MOA_F64_SPLIT_F32IN: 1e-12, moa.MOA_BF16: 1e-5}
+TOL = {moa.MOA_F32_SPLIT: 1e-5, moa.MOA_F64_SPLIT_F32IN: 1e-12, moa.MOA_BF16: 1e-5,
+       moa.MOA_F64_SPLIT_F32IN_E4M3: 1e-12}
 
 
 def _req(m, n, p, dt, seed):
@@ -50,7 +51,8 @@ def test_results_same_alone_and_in_the_mix():
     for i in range(36):
         m, p = (int(x) for x in rng.integers(1, 40, 2) * 16)
         n = int(rng.integers(1, 80)) * 16
-        dt = [moa.MOA_F32_SPLIT, moa.MOA_F64_SPLIT_F32IN, moa.MOA_BF16][i % 3]
+        dt = [moa.MOA_F32_SPLIT, moa.MOA_F64_SPLIT_F32IN, moa.MOA_BF16,
+              moa.MOA_F64_SPLIT_F32IN_E4M3][i % 4]
         reqs.append(_req(m, n, p, dt, seed=i))
     alone = [moa.gemm(A, B, dt) for A, B, C, dt in reqs]
     torch.cuda.synchronize()
