@@ -16,13 +16,15 @@
 // K-major (contiguous in k), B row strips are MN-major (contiguous in j, the
 // "row of B" of Fig. fig:mm).  TMA stages them into 128-byte-swizzled shared
 // memory; one thread issues tcgen05.mma; four epilogue warps drain the TMEM
-// accumulator (double-buffered, so the next tile's MMAs overlap the stores).
+// accumulator (double-buffered, so the next tile's MMAs overlap the stores)
+// and write C through a shared-memory staging tile in coalesced row segments.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 
+#include "epilogue.cuh"
 #include "internal.h"
 #include "ptx.cuh"
 
@@ -61,7 +63,8 @@ struct DenseCfg {
     static constexpr int B_BYTES = BLOCK_N * BK * ESIZE;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int TMEM_COLS = 2 * BLOCK_N <= 32 ? 32 : (2 * BLOCK_N <= 64 ? 64 : (2 * BLOCK_N <= 128 ? 128 : (2 * BLOCK_N <= 256 ? 256 : 512)));
-    static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + 256;
+    static constexpr int OUT_STAGE = 4 * 4096;     // 4 KB store staging per epilogue warp
+    static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + OUT_STAGE + 256;
     static constexpr uint32_t IDESC =
         make_idesc(ESIZE == 2 ? 1u : 2u, BLOCK_M, BLOCK_N, 0u, BKM ? 0u : 1u);
 };
@@ -79,7 +82,8 @@ __global__ void __launch_bounds__(192, 1)
                                                ~static_cast<uintptr_t>(1023));
     uint8_t* sA = smem;
     uint8_t* sB = smem + STAGES * Cfg::A_BYTES;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + STAGES * Cfg::B_BYTES);
+    uint8_t* out_stage = sB + STAGES * Cfg::B_BYTES;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(out_stage + Cfg::OUT_STAGE);
     uint64_t* full = bars;
     uint64_t* empty = bars + STAGES;
     uint64_t* tfull = bars + 2 * STAGES;
@@ -231,9 +235,10 @@ __global__ void __launch_bounds__(192, 1)
             tc_fence_after();
             int tm, tn;
             tile_coords(t, args.tiles_m, args.tiles_n, args.group_m, tm, tn);
-            const int64_t row = static_cast<int64_t>(tm) * Cfg::BLOCK_M + q * 32 + lane;
-            const bool row_ok = row < args.m;
-            float* crow = args.C + row * args.p;
+            const int64_t row0 = static_cast<int64_t>(tm) * Cfg::BLOCK_M + q * 32;
+            const int64_t rl = args.m - row0;
+            const int rows_left = rl <= 0 ? 0 : (rl >= 32 ? 32 : static_cast<int>(rl));
+            uint8_t* stage_w = out_stage + (warp - 2) * 4096;
 #pragma unroll 1
             for (int c = 0; c < BLOCK_N / 32; ++c) {
                 uint32_t r[32];
@@ -242,20 +247,9 @@ __global__ void __launch_bounds__(192, 1)
                           r);
                 tmem_ld_wait();
                 const int64_t col0 = static_cast<int64_t>(tn) * BLOCK_N + c * 32;
-                if (row_ok) {
-                    if (args.vec_ok && col0 + 32 <= args.p) {
-                        float4* dst = reinterpret_cast<float4*>(crow + col0);
-#pragma unroll
-                        for (int v = 0; v < 8; ++v)
-                            dst[v] = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
-                                                 __uint_as_float(r[4 * v + 2]),
-                                                 __uint_as_float(r[4 * v + 3]));
-                    } else {
-#pragma unroll
-                        for (int v = 0; v < 32; ++v)
-                            if (col0 + v < args.p) crow[col0 + v] = __uint_as_float(r[v]);
-                    }
-                }
+                if (rows_left > 0 && col0 < args.p)
+                    store_block32(stage_w, r, args.C, args.p, row0, rows_left, col0,
+                                  args.p - col0, args.vec_ok != 0);
             }
             tc_fence_before();
             __syncwarp();

@@ -25,6 +25,7 @@
 #include <queue>
 #include <vector>
 
+#include "epilogue.cuh"
 #include "internal.h"
 #include "ptx.cuh"
 
@@ -39,7 +40,12 @@ constexpr int kGBM = 128, kGBK = 64, kGStages = 4;
 constexpr int kGABytes = kGBM * 128;                    // 128 rows x 64 BF16
 constexpr int kGBChunk = kGBK * 128;                    // 64 rows x 64 BF16 columns
 constexpr int kGStageBytes = kGABytes + 4 * kGBChunk;   // room for BN = 256
-constexpr int kGSmem = 1024 + kGStages * kGStageBytes + 256;
+// Epilogue: two warps per TMEM lane quadrant (alternate 32-column blocks),
+// each with a 4 KB staging tile for coalesced stores.
+constexpr int kGEpiWarps = 8;
+constexpr int kGThreads = 64 + 32 * kGEpiWarps;
+constexpr int kGStageOut = kGEpiWarps * 4096;
+constexpr int kGSmem = 1024 + kGStages * kGStageBytes + kGStageOut + 256;
 
 struct GroupDev {
     float* C;
@@ -60,11 +66,12 @@ struct GroupedArgs {
     int* status;
 };
 
-__global__ void __launch_bounds__(192, 1) grouped_tc_kernel(const GroupedArgs args) {
+__global__ void __launch_bounds__(kGThreads, 1) grouped_tc_kernel(const GroupedArgs args) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                ~static_cast<uintptr_t>(1023));
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kGStages * kGStageBytes);
+    uint8_t* out_stage = smem + kGStages * kGStageBytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(out_stage + kGStageOut);
     uint64_t* full = bars;
     uint64_t* empty = bars + kGStages;
     uint64_t* tfull = bars + 2 * kGStages;
@@ -85,7 +92,7 @@ __global__ void __launch_bounds__(192, 1) grouped_tc_kernel(const GroupedArgs ar
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&tfull[a], 1);
-            mbar_init(&tempty[a], 4);
+            mbar_init(&tempty[a], kGEpiWarps);
         }
         mbar_init(drain, 1);
         ctl->abort = 0;
@@ -195,8 +202,11 @@ __global__ void __launch_bounds__(192, 1) grouped_tc_kernel(const GroupedArgs ar
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue: warps 2..5, TMEM lane quadrant = warp % 4
+        // ---------------- epilogue: warps 2..9; TMEM lane quadrant q = warp % 4,
+        // column blocks h, h + 2, ... of 32 (h = 0 for warps 2..5, 1 for 6..9)
         const int q = warp & 3;
+        const int h = (warp - 2) >> 2;
+        uint8_t* stage_w = out_stage + (warp - 2) * 4096;
         int local_t = 0;
         for (int t = t0; t < t1; ++t, ++local_t) {
             const int acc = local_t & 1;
@@ -206,30 +216,19 @@ __global__ void __launch_bounds__(192, 1) grouped_tc_kernel(const GroupedArgs ar
             tc_fence_after();
             const int4 tl = args.tiles[t];
             const GroupDev g = args.groups[tl.x];
-            const int64_t row = static_cast<int64_t>(tl.y) * kGBM + q * 32 + lane;
-            const bool row_ok = row < g.m;
-            float* crow = g.C + row * g.p;
-            for (int c = 0; c < g.bn / 32; ++c) {
+            const int64_t row0 = static_cast<int64_t>(tl.y) * kGBM + q * 32;
+            const int64_t rl = g.m - row0;
+            const int rows_left = rl <= 0 ? 0 : (rl >= 32 ? 32 : static_cast<int>(rl));
+            for (int c = h; c < g.bn / 32; c += 2) {
                 uint32_t r[32];
                 tmem_ld32(tmem_base + (static_cast<uint32_t>(q * 32) << 16) +
                               static_cast<uint32_t>(acc * 256 + c * 32),
                           r);
                 tmem_ld_wait();
                 const int64_t col0 = static_cast<int64_t>(tl.z) * g.bn + c * 32;
-                if (row_ok) {
-                    if (g.vec_ok && col0 + 32 <= g.p) {
-                        float4* dst = reinterpret_cast<float4*>(crow + col0);
-#pragma unroll
-                        for (int v = 0; v < 8; ++v)
-                            dst[v] = make_float4(__uint_as_float(r[4 * v]), __uint_as_float(r[4 * v + 1]),
-                                                 __uint_as_float(r[4 * v + 2]),
-                                                 __uint_as_float(r[4 * v + 3]));
-                    } else {
-#pragma unroll
-                        for (int v = 0; v < 32; ++v)
-                            if (col0 + v < g.p) crow[col0 + v] = __uint_as_float(r[v]);
-                    }
-                }
+                if (rows_left > 0 && col0 < g.p)
+                    store_block32(stage_w, r, g.C, g.p, row0, rows_left, col0, g.p - col0,
+                                  g.vec_ok != 0);
             }
             tc_fence_before();
             __syncwarp();
@@ -375,7 +374,7 @@ int launch_kernel(uint8_t* dev, const Layout& L, int grid, cudaStream_t s) {
         attr_set = true;
     }
     prof_begin(s);
-    grouped_tc_kernel<<<grid, 192, kGSmem, s>>>(a);
+    grouped_tc_kernel<<<grid, kGThreads, kGSmem, s>>>(a);
     cudaError_t e = cudaGetLastError();
     prof_end(s);
     if (e != cudaSuccess) return cuda_fail(e, "grouped_tc_kernel launch");
