@@ -15,7 +15,8 @@
 // Both operands are read exactly as the ONF lays them out: A row strips are
 // K-major (contiguous in k), B row strips are MN-major (contiguous in j, the
 // "row of B" of Fig. fig:mm).  TMA stages them into 128-byte-swizzled shared
-// memory; one thread issues tcgen05.mma; four epilogue warps drain the TMEM
+// memory; one thread issues tcgen05.mma; four epilogue warps (one per TMEM
+// lane quadrant) drain the TMEM
 // accumulator (double-buffered, so the next tile's MMAs overlap the stores)
 // and write C through a shared-memory staging tile in coalesced row segments.
 #include <cuda.h>
