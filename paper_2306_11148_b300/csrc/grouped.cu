@@ -66,6 +66,23 @@ struct GroupedArgs {
     int* status;
 };
 
+// A role's walk over its CTA's work list.  The tile record of tile t + 2 and
+// the problem record of tile t + 1 are requested while tile t is processed,
+// so the dependent global-memory lookups (tile -> problem) never stall the
+// role between tiles.
+struct TileWalk {
+    int4 tl;        // current tile (problem, tm, tn, 0)
+    GroupDev g;     // its problem
+    int4 tl_next;   // the next tile
+    __device__ void start(const GroupedArgs& a, int t0, int t1) {
+        if (t0 < t1) {
+            tl = a.tiles[t0];
+            g = a.groups[tl.x];
+        }
+        tl_next = (t0 + 1 < t1) ? a.tiles[t0 + 1] : tl;
+    }
+};
+
 __global__ void __launch_bounds__(kGThreads, 1) grouped_tc_kernel(const GroupedArgs args) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -116,9 +133,17 @@ __global__ void __launch_bounds__(kGThreads, 1) grouped_tc_kernel(const GroupedA
             uint32_t phase = 0;
             long issued = 0;
             bool ok = true;
+            TileWalk w;
+            w.start(args, t0, t1);
             for (int t = t0; t < t1 && ok; ++t) {
-                const int4 tl = args.tiles[t];
-                const GroupDev g = args.groups[tl.x];
+                const int4 tl_nn = (t + 2 < t1) ? args.tiles[t + 2] : w.tl_next;
+                const GroupDev g_n = (t + 1 < t1) ? args.groups[w.tl_next.x] : w.g;
+                if (t + 1 < t1) {   // the next problem's TMA descriptors
+                    prefetch_tmap(args.maps + 2 * w.tl_next.x);
+                    prefetch_tmap(args.maps + 2 * w.tl_next.x + 1);
+                }
+                const int4 tl = w.tl;
+                const GroupDev g = w.g;
                 const CUtensorMap* mA = args.maps + 2 * tl.x;
                 const CUtensorMap* mB = mA + 1;
                 const uint32_t bytes = kGABytes + static_cast<uint32_t>(g.bn) * kGBK * 2;
@@ -139,6 +164,9 @@ __global__ void __launch_bounds__(kGThreads, 1) grouped_tc_kernel(const GroupedA
                         phase ^= 1u;
                     }
                 }
+                w.tl = w.tl_next;
+                w.g = g_n;
+                w.tl_next = tl_nn;
             }
             if (!ok) {
                 // Let the loads already in flight land before the CTA exits.
@@ -159,10 +187,16 @@ __global__ void __launch_bounds__(kGThreads, 1) grouped_tc_kernel(const GroupedA
             uint32_t phase = 0;
             int local_t = 0;
             bool ok = true;
+            TileWalk w;
+            w.start(args, t0, t1);
             for (int t = t0; t < t1 && ok; ++t, ++local_t) {
-                const int4 tl = args.tiles[t];
-                const int bn = args.groups[tl.x].bn;
-                const int num_kb = args.groups[tl.x].num_kb;
+                const int4 tl_nn = (t + 2 < t1) ? args.tiles[t + 2] : w.tl_next;
+                const GroupDev g_n = (t + 1 < t1) ? args.groups[w.tl_next.x] : w.g;
+                const int bn = w.g.bn;
+                const int num_kb = w.g.num_kb;
+                w.tl = w.tl_next;
+                w.g = g_n;
+                w.tl_next = tl_nn;
                 const uint32_t idesc = make_idesc(1u, kGBM, static_cast<uint32_t>(bn), 0u, 1u);
                 const int acc = local_t & 1;
                 const uint32_t acc_phase = static_cast<uint32_t>(local_t >> 1) & 1u;
@@ -208,14 +242,21 @@ __global__ void __launch_bounds__(kGThreads, 1) grouped_tc_kernel(const GroupedA
         const int h = (warp - 2) >> 2;
         uint8_t* stage_w = out_stage + (warp - 2) * 4096;
         int local_t = 0;
+        TileWalk w;
+        w.start(args, t0, t1);
         for (int t = t0; t < t1; ++t, ++local_t) {
+            const int4 tl_nn = (t + 2 < t1) ? args.tiles[t + 2] : w.tl_next;
+            const GroupDev g_n = (t + 1 < t1) ? args.groups[w.tl_next.x] : w.g;
+            const int4 tl = w.tl;
+            const GroupDev g = w.g;
+            w.tl = w.tl_next;
+            w.g = g_n;
+            w.tl_next = tl_nn;
             const int acc = local_t & 1;
             const uint32_t acc_phase = static_cast<uint32_t>(local_t >> 1) & 1u;
             bool ok = mbar_wait(&tfull[acc], acc_phase, ctl, limit, status);
             if (!__all_sync(0xffffffffu, ok)) break;
             tc_fence_after();
-            const int4 tl = args.tiles[t];
-            const GroupDev g = args.groups[tl.x];
             const int64_t row0 = static_cast<int64_t>(tl.y) * kGBM + q * 32;
             const int64_t rl = g.m - row0;
             const int rows_left = rl <= 0 ? 0 : (rl >= 32 ? 32 : static_cast<int>(rl));
@@ -244,16 +285,22 @@ __global__ void __launch_bounds__(kGThreads, 1) grouped_tc_kernel(const GroupedA
 
 // ------------------------------------------------------------------ planning
 // Cost of one output tile in units of "one K block of a 128 x 256 tile at full
-// tensor rate": MMA work bn/256 per K block, divided by the width's MMA
-// efficiency (narrow tiles re-read A from shared memory for fewer columns and
-// are shared-memory bound), plus a fixed share per tile for the TMEM drain,
-// the stores and the pipeline fill.
+// tensor rate" (512 SM cycles): the larger of its MMA work (bn/256 per K block,
+// divided by the width's MMA efficiency: narrow tiles re-read A from shared
+// memory for fewer columns and are shared-memory bound) and its memory time
+// (A strip + B strip + C tile bytes at one SM's share of HBM bandwidth,
+// about 12 KB per unit), plus a fixed share per tile for the TMEM drain, the
+// stores and the pipeline fill.  Small-K tiles of a mixed batch are memory
+// bound; costing them by MMA work alone let the dealing overload some SMs.
 constexpr double kTileOverheadKb = 3.0;
 
 double mma_eff(int bn) { return bn >= 256 ? 1.0 : (bn >= 128 ? 0.9 : 0.67); }
 
 double tile_cost(int64_t n, int bn) {
-    return static_cast<double>(ceil_div(n, kGBK)) * (bn / 256.0) / mma_eff(bn) + kTileOverheadKb;
+    const double compute = static_cast<double>(ceil_div(n, kGBK)) * (bn / 256.0) / mma_eff(bn);
+    const double bytes = 2.0 * kGBM * n + 2.0 * n * bn + 4.0 * kGBM * bn;
+    const double memory = bytes / (12.0 * 1024.0);
+    return (compute > memory ? compute : memory) + kTileOverheadKb;
 }
 
 bool persistent_ok(const moa_gemm_desc& d) {
