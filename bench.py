@@ -282,7 +282,7 @@ MODE_OF = {"square": "tf32", "bf16": "bf16", "split_f32": "f32_split",
            "split_f64": "f64_split_f32in", "split_f64_e4m3": "f64_split_f32in_e4m3",
            "f64": "f64", "simt": "f32_simt",
            "grouped": "grouped", "serve": "serve", "energy_n": "energy_n",
-           "tiles": "tiles"}
+           "tiles": "tiles", "peaks": "peaks"}
 
 
 def make_inputs(mode, N):
@@ -763,6 +763,66 @@ def bench_tiles(stream, energy, sizes=(2048, 4096, 8192), modes=("bf16", "tf32")
     return out
 
 
+def bench_library_rates(N=8192, reps=10):
+    """Dense GEMM rates of the vendor library (cuBLAS through torch) per data
+    type on this GPU, next to this library's dense kernels: context for the
+    roofline denominators (which stay MEASURED_PEAKS.json's BF16 figure times
+    the nominal dtype ratio).  Not used on any product path."""
+    import torch
+    from paper_2306_11148_b300 import moa
+    out = {}
+
+    def best_ms(fn, r):
+        fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(r):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        return best
+
+    def rate(n, ms):
+        return 2.0 * n ** 3 / (ms / 1e3) / 1e12
+
+    g = torch.Generator(device="cuda").manual_seed(0)
+    a32 = torch.rand((N, N), generator=g, device="cuda") * 2 - 1
+    b32 = torch.rand((N, N), generator=g, device="cuda") * 2 - 1
+    prev = torch.backends.cuda.matmul.allow_tf32
+    try:
+        torch.backends.cuda.matmul.allow_tf32 = True
+        out["cublas_tf32"] = rate(N, best_ms(lambda: a32 @ b32, reps))
+        torch.backends.cuda.matmul.allow_tf32 = False
+        n32 = N // 2
+        out["cublas_fp32_n4096"] = rate(n32, best_ms(lambda: a32[:n32, :n32] @ b32[:n32, :n32], reps))
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    a16, b16 = a32.bfloat16(), b32.bfloat16()
+    out["cublas_bf16"] = rate(N, best_ms(lambda: a16 @ b16, reps))
+    try:
+        a8 = a32.to(torch.float8_e4m3fn)
+        b8t = b32.t().contiguous().to(torch.float8_e4m3fn)
+        one = torch.ones((), device="cuda")
+        out["cublas_fp8_e4m3"] = rate(N, best_ms(
+            lambda: torch._scaled_mm(a8, b8t.t(), scale_a=one, scale_b=one,
+                                     out_dtype=torch.bfloat16), reps))
+    except Exception as e:  # report, do not hide
+        out["cublas_fp8_e4m3"] = f"unavailable: {e}"
+    n64 = N // 4
+    a64, b64 = a32[:n64, :n64].double(), b32[:n64, :n64].double()
+    out["cublas_fp64_n2048"] = rate(n64, best_ms(lambda: a64 @ b64, 3))
+    # this library's dense kernels on the same operands
+    c32 = torch.empty((N, N), device="cuda")
+    out["moa_tf32"] = rate(N, best_ms(lambda: moa.gemm(a32, b32, moa.MOA_F32_TF32, C=c32), reps))
+    out["moa_bf16"] = rate(N, best_ms(lambda: moa.gemm(a16, b16, moa.MOA_BF16, C=c32), reps))
+    c64 = torch.empty((n64, n64), dtype=torch.float64, device="cuda")
+    out["moa_fp64_n2048"] = rate(n64, best_ms(lambda: moa.gemm(a64, b64, moa.MOA_F64, C=c64), 3))
+    return out
+
+
 # ------------------------------------------------------------------ reference arm
 def square_metric_config(mode, N, ws):
     """Metric name and config of the square workloads (shared by both arms)."""
@@ -845,10 +905,15 @@ def main():
     mode = MODE_OF[args.workload]
     N = args.n
 
-    if mode in ("energy_n", "tiles"):
+    if mode in ("energy_n", "tiles", "peaks"):
         clocks = ClockSampler(pci)
         clocks.start()
-        if mode == "energy_n":
+        if mode == "peaks":
+            res = bench_library_rates(args.n)
+            metric = "dense GEMM TFLOP/s per dtype: vendor library vs this library"
+            value = res["moa_tf32"]
+            unit = "TFLOP/s (this library, TF32)"
+        elif mode == "energy_n":
             res = bench_energy_n(stream, energy)
             metric = "joules per square ONF GEMM vs N (slope of log J vs log N)"
             value = res["tf32"]["slope_logJ_logN"]
@@ -862,7 +927,7 @@ def main():
         clk = clocks.stop()
         if rank == 0:
             print(json.dumps({"metric": metric, "value": value, "unit": unit, "n_gpus": ws,
-                              "higher_is_better": mode == "tiles", "scaling": "weak",
+                              "higher_is_better": mode != "energy_n", "scaling": "weak",
                               "vs_baseline": None, "data": "synthetic",
                               "config": {"workload": mode, "parallelism": f"replicas x{ws}"},
                               "results": res, "clocks": clk}), flush=True)
