@@ -66,6 +66,27 @@ def test_every_tile_width_gives_the_same_bits(L, dt):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("dt", [moa.MOA_BF16, moa.MOA_F32_TF32])
+@pytest.mark.parametrize("m", [129, 515, 1024])
+def test_cluster_pairs_exact_with_odd_and_even_row_tiles(L, dt, m):
+    """256-wide tiles run as clusters of two CTAs on vertically adjacent row
+    tiles sharing one multicast B tile; with an odd number of row tiles the
+    second CTA of the last pair computes on zero rows and stores nothing.
+    Integer inputs: exact against the oracle."""
+    n, p = 1000, 1100
+    A, B = inputs.integer_pair(m, n, p, dtype=moa.in_dtype(dt), seed=m)
+    try:
+        assert L.moa_set_block_n(256) == moa.MOA_OK
+        C, st = moa.gemm(A.cuda(), B.cuda(), dt, stats=True)
+        moa.sync_status()
+        assert st.block_n == 256
+    finally:
+        L.moa_set_block_n(0)
+    ref = oracle.gemm(A.double().numpy(), B.double().numpy())
+    assert np.array_equal(C.double().cpu().numpy(), ref)
+
+
+@pytest.mark.gpu
 def test_tuner_records_and_reuses_choice(L, tmp_path):
     L.moa_tune_clear()
     m, n, p = 1024, 2048, 1536
