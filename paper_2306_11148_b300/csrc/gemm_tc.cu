@@ -24,7 +24,6 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <cstdlib>
 
 #include "epilogue.cuh"
 #include "internal.h"
@@ -74,21 +73,11 @@ struct DenseCfg {
 // BKM = 0: B staged MN-major (row-major n x p, contiguous in j).
 // BKM = 1: B staged K-major from its transpose (p x n), for the TF32 kind,
 //          whose MMA does not read MN-major operands.
-// CL = 1: one CTA per output tile.
-// CL = 2: clusters of two CTAs on vertically adjacent tiles (2u, tn) and
-//         (2u + 1, tn), which need the same B tile: each CTA loads half of it
-//         and multicasts that half into both CTAs' shared memory, so every
-//         B byte leaves L2 once per pair.  A stage of a CTA is free only when
-//         both CTAs' MMAs have read it (each MMA commit arrives on the empty
-//         barriers of both), since the peer's half lands in it too.
-template <int ESIZE, int BLOCK_N, int STAGES, int BKM, int CL>
+template <int ESIZE, int BLOCK_N, int STAGES, int BKM>
 __global__ void __launch_bounds__(192, 1)
     dense_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const DenseArgs args) {
     using Cfg = DenseCfg<ESIZE, BLOCK_N, STAGES, BKM>;
-    static_assert(CL == 1 || CL == 2, "cluster of one or two CTAs");
-    static_assert(CL == 1 || BKM == 1 || (BLOCK_N / Cfg::CHUNK_N) % 2 == 0,
-                  "B chunks split evenly between the two CTAs");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                ~static_cast<uintptr_t>(1023));
@@ -109,13 +98,10 @@ __global__ void __launch_bounds__(192, 1)
     const uint64_t limit = args.wait_limit_ns;
     int* status = args.status;
 
-    const int rank = CL == 2 ? static_cast<int>(cluster_ctarank()) : 0;
-    constexpr uint16_t kPair = 0x3;   // multicast to both CTAs of the cluster
-
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], CL);
+            mbar_init(&empty[s], 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&tfull[a], 1);
@@ -136,18 +122,9 @@ __global__ void __launch_bounds__(192, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    // the peer's barriers must be initialised before anything is multicast
-    if constexpr (CL == 2) cluster_sync();
     const uint32_t tmem_base = *tmem_slot;
 
-    // Work units: tiles (CL = 1) or vertical pairs of tiles (CL = 2; this CTA
-    // takes row tile CL * um + rank, which for an odd tile count can lie one
-    // past the last row tile: its A loads then read zeros and it stores nothing).
-    const int units_m = (args.tiles_m + CL - 1) / CL;
-    const int num_units = units_m * args.tiles_n;
-    const int unit0 = static_cast<int>(blockIdx.x) / CL;
-    const int unit_step = static_cast<int>(gridDim.x) / CL;
-    const int group = CL == 2 ? max(1, args.group_m / 2) : args.group_m;
+    const int num_tiles = args.tiles_m * args.tiles_n;
     const int num_kb = args.num_kb;
 
     if (warp == 0) {
@@ -157,41 +134,25 @@ __global__ void __launch_bounds__(192, 1)
             uint32_t phase = 0;
             long issued = 0;
             bool ok = true;
-            for (int u = unit0; u < num_units && ok; u += unit_step) {
-                int um, tn;
-                tile_coords(u, units_m, args.tiles_n, group, um, tn);
-                const int tm = CL * um + rank;
+            for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+                int tm, tn;
+                tile_coords(t, args.tiles_m, args.tiles_n, args.group_m, tm, tn);
                 for (int kb = 0; kb < num_kb; ++kb) {
                     if (!mbar_wait(&empty[stage], phase ^ 1u, ctl, limit, status)) {
                         ok = false;
                         break;
                     }
-                    // this CTA's A tile plus the whole B tile (with CL = 2 half
-                    // of it arrives from the peer's multicast)
                     mbar_arrive_expect_tx(&full[stage], Cfg::STAGE_BYTES);
                     tma_load_2d(sA + stage * Cfg::A_BYTES, &tmA, &full[stage], kb * Cfg::BK,
                                 tm * Cfg::BLOCK_M);
-                    if constexpr (BKM && CL == 1) {
+                    if constexpr (BKM) {
                         tma_load_2d(sB + stage * Cfg::B_BYTES, &tmB, &full[stage], kb * Cfg::BK,
                                     tn * BLOCK_N);
-                    } else if constexpr (BKM) {
-                        // K-major B^T: rows [rank * BN/2, (rank + 1) * BN/2) of the tile
-                        tma_load_2d_mc(sB + stage * Cfg::B_BYTES + rank * (BLOCK_N / 2) * 128, &tmB,
-                                       &full[stage], kb * Cfg::BK,
-                                       tn * BLOCK_N + rank * (BLOCK_N / 2), kPair);
                     } else {
 #pragma unroll
-                        for (int c = 0; c < BLOCK_N / Cfg::CHUNK_N; ++c) {
-                            if constexpr (CL == 1) {
-                                tma_load_2d(sB + stage * Cfg::B_BYTES + c * Cfg::CHUNK_BYTES, &tmB,
-                                            &full[stage], tn * BLOCK_N + c * Cfg::CHUNK_N,
-                                            kb * Cfg::BK);
-                            } else if ((c & 1) == rank) {
-                                tma_load_2d_mc(sB + stage * Cfg::B_BYTES + c * Cfg::CHUNK_BYTES,
-                                               &tmB, &full[stage], tn * BLOCK_N + c * Cfg::CHUNK_N,
-                                               kb * Cfg::BK, kPair);
-                            }
-                        }
+                        for (int c = 0; c < BLOCK_N / Cfg::CHUNK_N; ++c)
+                            tma_load_2d(sB + stage * Cfg::B_BYTES + c * Cfg::CHUNK_BYTES, &tmB,
+                                        &full[stage], tn * BLOCK_N + c * Cfg::CHUNK_N, kb * Cfg::BK);
                     }
                     ++issued;
                     if (++stage == STAGES) {
@@ -210,18 +171,6 @@ __global__ void __launch_bounds__(192, 1)
                               limit, status);
                 }
             }
-            if constexpr (CL == 2) {
-                // Wait until both MMAs have released every stage this CTA
-                // filled, so that no commit of the peer is still on its way to
-                // this CTA's barriers when the cluster leaves.
-                CtaCtl local{0};
-                const long outstanding = issued < STAGES ? issued : STAGES;
-                for (long q = 1; q <= outstanding; ++q) {
-                    const long idx = issued - q;
-                    mbar_wait(&empty[idx % STAGES], static_cast<uint32_t>((idx / STAGES) & 1),
-                              &local, limit, status);
-                }
-            }
         }
         __syncwarp();
     } else if (warp == 1) {
@@ -231,7 +180,7 @@ __global__ void __launch_bounds__(192, 1)
             uint32_t phase = 0;
             int local_t = 0;
             bool ok = true;
-            for (int u = unit0; u < num_units && ok; u += unit_step, ++local_t) {
+            for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x, ++local_t) {
                 const int acc = local_t & 1;
                 const uint32_t acc_phase = static_cast<uint32_t>(local_t >> 1) & 1u;
                 if (!mbar_wait(&tempty[acc], acc_phase ^ 1u, ctl, limit, status)) {
@@ -260,10 +209,7 @@ __global__ void __launch_bounds__(192, 1)
                         else
                             mma_tf32(d, adesc + a_off, bdesc + b_off, Cfg::IDESC, (kb | k) != 0);
                     }
-                    if constexpr (CL == 2)
-                        mma_commit_mc(&empty[stage], kPair);   // frees the stage in both CTAs
-                    else
-                        mma_commit(&empty[stage]);
+                    mma_commit(&empty[stage]);
                     if (++stage == STAGES) {
                         stage = 0;
                         phase ^= 1u;
@@ -282,15 +228,14 @@ __global__ void __launch_bounds__(192, 1)
         // ---------------- epilogue: warps 2..5, TMEM lane quadrant = warp % 4
         const int q = warp & 3;
         int local_t = 0;
-        for (int u = unit0; u < num_units; u += unit_step, ++local_t) {
+        for (int t = blockIdx.x; t < num_tiles; t += gridDim.x, ++local_t) {
             const int acc = local_t & 1;
             const uint32_t acc_phase = static_cast<uint32_t>(local_t >> 1) & 1u;
             bool ok = mbar_wait(&tfull[acc], acc_phase, ctl, limit, status);
             if (!__all_sync(0xffffffffu, ok)) break;
             tc_fence_after();
-            int um, tn;
-            tile_coords(u, units_m, args.tiles_n, group, um, tn);
-            const int tm = CL * um + rank;
+            int tm, tn;
+            tile_coords(t, args.tiles_m, args.tiles_n, args.group_m, tm, tn);
             const int64_t row0 = static_cast<int64_t>(tm) * Cfg::BLOCK_M + q * 32;
             const int64_t rl = args.m - row0;
             const int rows_left = rl <= 0 ? 0 : (rl >= 32 ? 32 : static_cast<int>(rl));
@@ -313,38 +258,13 @@ __global__ void __launch_bounds__(192, 1)
         }
     }
     __syncthreads();
-    // neither CTA of a pair leaves while the other may still signal it
-    if constexpr (CL == 2) cluster_sync();
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem_base, Cfg::TMEM_COLS);
     }
 }
 
-// Clusters of two CTAs that the device can keep resident at once for this
-// kernel (0 if it cannot run clusters of two).
-template <typename Kern>
-int max_pair_clusters(Kern kern, int smem) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(2 * static_cast<unsigned>(num_sms()));
-    cfg.blockDim = dim3(192);
-    cfg.dynamicSmemBytes = static_cast<size_t>(smem);
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
-        cudaGetLastError();
-        n = 0;
-    }
-    return n;
-}
-
-template <int ESIZE, int BLOCK_N, int STAGES, int BKM, int CL>
+template <int ESIZE, int BLOCK_N, int STAGES, int BKM>
 int launch_cfg(int64_t m, int64_t n, int64_t p, const void* A, int64_t lda, const void* B,
                int64_t ldb, float* C, cudaStream_t s, moa_stats* st) {
     using Cfg = DenseCfg<ESIZE, BLOCK_N, STAGES, BKM>;
@@ -354,9 +274,9 @@ int launch_cfg(int64_t m, int64_t n, int64_t p, const void* A, int64_t lda, cons
     int rc = make_tmap_2d(&tmA, dt, A, static_cast<uint64_t>(n), static_cast<uint64_t>(m),
                           static_cast<uint64_t>(lda) * ESIZE, Cfg::BK, Cfg::BLOCK_M);
     if (rc != MOA_OK) return rc;
-    if (BKM)   // B^T: p rows of n (pitch ldb), box = BLOCK_N / CL rows x 128 bytes
+    if (BKM)   // B^T: p rows of n (pitch ldb), box = BLOCK_N rows x 128 bytes
         rc = make_tmap_2d(&tmB, dt, B, static_cast<uint64_t>(n), static_cast<uint64_t>(p),
-                          static_cast<uint64_t>(ldb) * ESIZE, Cfg::BK, BLOCK_N / CL);
+                          static_cast<uint64_t>(ldb) * ESIZE, Cfg::BK, BLOCK_N);
     else
         rc = make_tmap_2d(&tmB, dt, B, static_cast<uint64_t>(p), static_cast<uint64_t>(n),
                           static_cast<uint64_t>(ldb) * ESIZE, Cfg::CHUNK_N, Cfg::BK);
@@ -376,7 +296,7 @@ int launch_cfg(int64_t m, int64_t n, int64_t p, const void* A, int64_t lda, cons
     args.status = launch_status_ptr();
     if (!args.status) return MOA_ERR_CUDA;
 
-    auto kern = dense_tc_kernel<ESIZE, BLOCK_N, STAGES, BKM, CL>;
+    auto kern = dense_tc_kernel<ESIZE, BLOCK_N, STAGES, BKM>;
     static bool attr_set = false;   // per instantiation; the attribute is per device function
     if (!attr_set) {
         cudaError_t e =
@@ -385,35 +305,10 @@ int launch_cfg(int64_t m, int64_t n, int64_t p, const void* A, int64_t lda, cons
         attr_set = true;
     }
     const long tiles = static_cast<long>(args.tiles_m) * args.tiles_n;
-    int grid;
-    cudaError_t e;
-    if constexpr (CL == 1) {
-        grid = static_cast<int>(std::min<long>(tiles, num_sms()));
-        prof_begin(s);
-        kern<<<grid, 192, Cfg::SMEM, s>>>(tmA, tmB, args);
-        e = cudaGetLastError();
-    } else {
-        const long units = static_cast<long>((args.tiles_m + 1) / 2) * args.tiles_n;
-        static int clusters = -1;   // per instantiation (device function)
-        if (clusters < 0) clusters = max_pair_clusters(kern, Cfg::SMEM);
-        if (clusters <= 0) return fail(MOA_ERR_CUDA, "clusters of two CTAs cannot be resident");
-        grid = 2 * static_cast<int>(std::min<long>(units, clusters));
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(static_cast<unsigned>(grid));
-        cfg.blockDim = dim3(192);
-        cfg.dynamicSmemBytes = static_cast<size_t>(Cfg::SMEM);
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = 2;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        prof_begin(s);
-        e = cudaLaunchKernelEx(&cfg, kern, tmA, tmB, args);
-        if (e == cudaSuccess) e = cudaGetLastError();
-    }
+    const int grid = static_cast<int>(std::min<long>(tiles, num_sms()));
+    prof_begin(s);
+    dense_tc_kernel<ESIZE, BLOCK_N, STAGES, BKM><<<grid, 192, Cfg::SMEM, s>>>(tmA, tmB, args);
+    cudaError_t e = cudaGetLastError();
     prof_end(s);
     if (e != cudaSuccess) return cuda_fail(e, "dense_tc_kernel launch");
     if (st) {
@@ -425,16 +320,6 @@ int launch_cfg(int64_t m, int64_t n, int64_t p, const void* A, int64_t lda, cons
         st->kernels += 1;
     }
     return MOA_OK;
-}
-
-// Multicast pairs for the 256-wide dense tiles: on unless MOA_DENSE_PAIRS=0.
-bool dense_pairs_enabled() {
-    static int on = -1;
-    if (on < 0) {
-        const char* env = std::getenv("MOA_DENSE_PAIRS");
-        on = (env && env[0] == '0') ? 0 : 1;
-    }
-    return on == 1;
 }
 
 }  // namespace
@@ -455,21 +340,15 @@ int dense_tc_launch(bool in_bf16, int64_t m, int64_t n, int64_t p, const void* A
     if (tuned) bn = tuned;
     if (tile_override() == 64 || tile_override() == 128 || tile_override() == 256)
         bn = tile_override();
-    // 256-wide tiles on at least two row tiles run as multicast pairs.
-    const bool pair = bn == 256 && ceil_div(m, 128) >= 2 && dense_pairs_enabled();
     if (in_bf16) {
-        if (bn == 256)
-            return pair ? launch_cfg<2, 256, 4, 0, 2>(m, n, p, A, lda, B, ldb, C, s, st)
-                        : launch_cfg<2, 256, 4, 0, 1>(m, n, p, A, lda, B, ldb, C, s, st);
-        if (bn == 128) return launch_cfg<2, 128, 6, 0, 1>(m, n, p, A, lda, B, ldb, C, s, st);
-        return launch_cfg<2, 64, 8, 0, 1>(m, n, p, A, lda, B, ldb, C, s, st);
+        if (bn == 256) return launch_cfg<2, 256, 4, 0>(m, n, p, A, lda, B, ldb, C, s, st);
+        if (bn == 128) return launch_cfg<2, 128, 6, 0>(m, n, p, A, lda, B, ldb, C, s, st);
+        return launch_cfg<2, 64, 8, 0>(m, n, p, A, lda, B, ldb, C, s, st);
     }
     // TF32: B is passed transposed (p x n, row pitch ldb), K-major.
-    if (bn == 256)
-        return pair ? launch_cfg<4, 256, 4, 1, 2>(m, n, p, A, lda, B, ldb, C, s, st)
-                    : launch_cfg<4, 256, 4, 1, 1>(m, n, p, A, lda, B, ldb, C, s, st);
-    if (bn == 128) return launch_cfg<4, 128, 6, 1, 1>(m, n, p, A, lda, B, ldb, C, s, st);
-    return launch_cfg<4, 64, 8, 1, 1>(m, n, p, A, lda, B, ldb, C, s, st);
+    if (bn == 256) return launch_cfg<4, 256, 4, 1>(m, n, p, A, lda, B, ldb, C, s, st);
+    if (bn == 128) return launch_cfg<4, 128, 6, 1>(m, n, p, A, lda, B, ldb, C, s, st);
+    return launch_cfg<4, 64, 8, 1>(m, n, p, A, lda, B, ldb, C, s, st);
 }
 
 }  // namespace moa

@@ -68,11 +68,10 @@ def test_every_tile_width_gives_the_same_bits(L, dt):
 @pytest.mark.gpu
 @pytest.mark.parametrize("dt", [moa.MOA_BF16, moa.MOA_F32_TF32])
 @pytest.mark.parametrize("m", [129, 515, 1024])
-def test_cluster_pairs_exact_with_odd_and_even_row_tiles(L, dt, m):
-    """256-wide tiles run as clusters of two CTAs on vertically adjacent row
-    tiles sharing one multicast B tile; with an odd number of row tiles the
-    second CTA of the last pair computes on zero rows and stores nothing.
-    Integer inputs: exact against the oracle."""
+def test_widest_tiles_exact_with_ragged_rows_and_columns(L, dt, m):
+    """256-wide tiles forced on 2, 5 and 8 row tiles (the last one ragged for
+    m = 129 and 515) and a ragged last column tile (p = 1100): integer inputs,
+    exact against the oracle."""
     n, p = 1000, 1100
     A, B = inputs.integer_pair(m, n, p, dtype=moa.in_dtype(dt), seed=m)
     try:
