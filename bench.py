@@ -533,12 +533,22 @@ def bench_grouped(steps, warmup, ws, stream, count=512, compare=True):
 
     nsep = max(2, steps // 2)
     t_sep = float("nan")
+    t_graph = float("nan")
     if compare:
         with torch.cuda.stream(stream):
             t_sep = time_device(separate, nsep, 2, stream, ws)
+        # the same 512 launches captured once in a CUDA graph and replayed:
+        # separate kernels without the host launch cost
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            separate()
+        with torch.cuda.stream(stream):
+            t_graph = time_device(graph.replay, nsep, 2, stream, ws)
+        del graph
     return {"seconds": t, "kernel_seconds": kernel_s, "steps": steps, "flops_per_step": flops,
             "bytes_per_step": nbytes, "count": count,
-            "separate_seconds_per_step": t_sep / nsep, "kernels_per_step": 1,
+            "separate_seconds_per_step": t_sep / nsep,
+            "graph_seconds_per_step": t_graph / nsep, "kernels_per_step": 1,
             "products": 1, "tile": [128, 0, 64]}
 
 
@@ -1051,7 +1061,10 @@ def main():
                       "l2": "operands ~0.96 GB per step, larger than L2",
                       "separate_launches_ms": main_res["separate_seconds_per_step"] * 1e3,
                       "separate_tflops": main_res["flops_per_step"] /
-                      main_res["separate_seconds_per_step"] / 1e12}
+                      main_res["separate_seconds_per_step"] / 1e12,
+                      "separate_in_cuda_graph_ms": main_res["graph_seconds_per_step"] * 1e3,
+                      "separate_in_cuda_graph_tflops": main_res["flops_per_step"] /
+                      main_res["graph_seconds_per_step"] / 1e12}
         else:
             metric, config = square_metric_config(mode, N, ws)
         line = {

@@ -106,7 +106,11 @@ size_t moa_gemm_workspace_size(int64_t m, int64_t n, int64_t p, moa_dtype dt, in
 
 /* C := A . B on `stream` with a caller-provided device workspace of at least
  * moa_gemm_workspace_size(...) bytes (ws may be NULL when that size is 0).
- * Allocates nothing.  stats may be NULL. */
+ * Allocates nothing.  stats may be NULL.
+ * CUDA graphs: once a call of the same mode has run on the device (it sets up
+ * kernel attributes and the device status word), a call records only kernel
+ * launches and memsets on `stream`, so it can be captured into a CUDA graph
+ * and replayed; each replay reads the current contents of A, B and ws. */
 int moa_gemm_ex(int64_t m, int64_t n, int64_t p, moa_dtype dt,
                 const void* A, const void* B, void* C, int slices,
                 void* ws, size_t ws_bytes, void* stream, moa_stats* stats);
