@@ -597,7 +597,7 @@ def serve_pool(pool_size=64, ring=8, seed=0):
     return pool, cring
 
 
-def bench_serve(pool, cring, rate, seconds, seed=0, energy=None):
+def bench_serve(pool, cring, rate, seconds, seed=0, energy=None, n_streams=8):
     """Serving stream: Poisson arrivals at `rate` for `seconds` through one
     server (64 GB arena, 32 in flight, 8 streams, 2 s queue deadline).
     Arrival i uses pool entry i % len(pool) and the next of its output
@@ -607,7 +607,7 @@ def bench_serve(pool, cring, rate, seconds, seed=0, energy=None):
     ring = len(cring[0])
     arr = inputs.serve_arrivals(rate=rate, seconds=seconds, seed=seed)
     arrivals = [(a[0], i % len(pool)) for i, a in enumerate(arr)]
-    srv = moa.Server(arena_bytes=64 << 30, max_inflight=32, n_streams=8,
+    srv = moa.Server(arena_bytes=64 << 30, max_inflight=32, n_streams=n_streams,
                      queue_capacity=len(pool) * ring // 2 - 32, queue_deadline_s=2.0)
     j0 = energy.read_j() if energy else None
     try:
@@ -620,6 +620,13 @@ def bench_serve(pool, cring, rate, seconds, seed=0, energy=None):
     flops = sum(pool[i][3] for rc, tk, i in codes if rc == moa.MOA_OK and tk in got
                 and got[tk][1] == moa.MOA_OK)
     span = (max(c[4] for c in done_ok) - min(c[2] for c in done_ok)) if done_ok else float("nan")
+    # latency split: queue wait (submit -> admission by the scheduler) and
+    # service (admission -> completion callback on the stream)
+    def pct(xs, q):
+        xs = sorted(xs)
+        return xs[min(len(xs) - 1, int(q * len(xs)))] * 1e3 if xs else float("nan")
+    waits = [c[3] - c[2] for c in done_ok]
+    service = [c[4] - c[3] for c in done_ok]
     # alone vs mix: the last output of some pool entries against the same GEMM alone
     torch.cuda.synchronize()
     mism = checked = 0
@@ -643,6 +650,8 @@ def bench_serve(pool, cring, rate, seconds, seed=0, energy=None):
             "failed": st["failed"], "served_per_s": len(done_ok) / span if done_ok else 0.0,
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
             "mean_ms": st["mean_ms"], "batches": st["batches"],
+            "queue_wait_p50_ms": pct(waits, 0.5), "queue_wait_p99_ms": pct(waits, 0.99),
+            "service_p50_ms": pct(service, 0.5), "service_p99_ms": pct(service, 0.99),
             "inflight_peak": st["inflight_peak"], "arena_peak_gb": st["arena_peak"] / 1e9,
             "tflops_served": flops / span / 1e12 if done_ok else 0.0, "wall_s": wall,
             "j_per_request": (j1 - j0) / len(done_ok) if (j0 is not None and j1 is not None
