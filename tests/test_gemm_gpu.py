@@ -223,3 +223,20 @@ def test_largest_square_size(dt):
     got = C[torch.from_numpy(rows).cuda()].cpu().double().numpy()
     ref = oracle.gemm_omp(A[torch.from_numpy(rows)].double().numpy(), B.double().numpy())[0]
     assert _rel(got, ref) <= TOL[dt]
+
+
+@pytest.mark.parametrize("dt", ALL_MODES, ids=lambda d: NAMES[d])
+def test_gpu_matches_golden_records(dt):
+    """The CUDA path against the frozen oracle records of tests/golden:
+    bit-exact on the integer record in every mode; the FP64 modes also on
+    the uniform record within their tolerance."""
+    from golden_io import read_record
+    r = read_record("gemm_int_7x9x5.txt")
+    tdt = moa.in_dtype(dt)
+    C = _run(torch.from_numpy(r["A"]).to(tdt), torch.from_numpy(r["B"]).to(tdt), dt)
+    assert np.array_equal(C, r["C"])
+    if moa.in_dtype(dt) == torch.float64:
+        r = read_record("gemm_uniform_6x10x4.txt")
+        C = _run(torch.from_numpy(r["A"]), torch.from_numpy(r["B"]), dt)
+        assert _rel(C, r["C"]) <= TOL[dt]
+

@@ -491,3 +491,22 @@ def test_hadamard_identities():
     y = rng.uniform(-1, 1, (3, 4))
     h = oracle.hadamard(x, y)
     assert all(h[i, j] == float(x[i, j]) * float(y[i, j]) for i in range(3) for j in range(4))
+
+
+# --------------------------------------------------------------------------
+# Regression records (tests/golden): the oracle must reproduce them bit for bit.
+# --------------------------------------------------------------------------
+
+def test_oracle_reproduces_golden_records():
+    from golden_io import read_record
+    r = read_record("gemm_int_7x9x5.txt")
+    assert np.array_equal(oracle.gemm(r["A"], r["B"]), r["C"])
+    # integer inputs: the record is also the exact integer product
+    assert np.array_equal(r["C"], (r["A"].astype(np.int64) @ r["B"].astype(np.int64)))
+    r = read_record("gemm_uniform_6x10x4.txt")
+    assert np.array_equal(oracle.gemm(r["A"], r["B"]), r["C"])
+    r = read_record("split_exact_b7_s4_5x12x3.txt")
+    eA, dA = oracle.slice_fixed(r["A"], 0, 7, 4)
+    eB, dB = oracle.slice_fixed(r["B"], 1, 7, 4)
+    assert np.array_equal(oracle.split_gemm_exact(dA, eA, dB, eB, 7, 4), r["C"])
+
