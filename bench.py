@@ -35,7 +35,7 @@ NOMINAL_RATIO = {"bf16": 1.0, "tf32": 1.1 / 2.25, "fp8": 2.0}
 # DRAM traffic (read + write bytes) per launch of the dominant kernel from one
 # ncu capture, keyed by (mode, N); see profiles/.  Remove an entry when its
 # kernel changes.
-TRAFFIC = {("tf32", 8192): 2.277662e9 + 0.256374e9}
+TRAFFIC = {("tf32", 8192): 1.652613e9 + 0.236939e9}
 
 
 def load_peaks():

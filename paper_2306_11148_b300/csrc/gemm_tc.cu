@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "epilogue.cuh"
 #include "internal.h"
@@ -53,9 +54,15 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
     tn = r / gsize;
 }
 
-template <int ESIZE, int BLOCK_N, int STAGES, int BKM>
+// MT: 128-row halves per CTA tile.  MT = 1: 128 x BLOCK_N tiles with a
+// double-buffered TMEM accumulator (the next tile's MMAs overlap the
+// stores).  MT = 2: 256 x BLOCK_N tiles, two M = 128 MMAs per K step sharing
+// each staged B tile (a third fewer operand bytes per flop, so the same
+// shared memory buffers more MMA time), single-buffered accumulators (all
+// 512 TMEM columns) drained by eight epilogue warps.
+template <int ESIZE, int BLOCK_N, int STAGES, int BKM, int MT = 1>
 struct DenseCfg {
-    static constexpr int BLOCK_M = 128;
+    static constexpr int BLOCK_M = 128 * MT;
     static constexpr int BK = 128 / ESIZE;          // K elements per stage (128 bytes)
     static constexpr int MMA_K = 32 / ESIZE;        // K per tcgen05.mma (32 bytes)
     static constexpr int CHUNK_N = 128 / ESIZE;     // B columns per 128-byte swizzle row
@@ -63,21 +70,24 @@ struct DenseCfg {
     static constexpr int A_BYTES = BLOCK_M * 128;
     static constexpr int B_BYTES = BLOCK_N * BK * ESIZE;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int NBUF = MT == 1 ? 2 : 1;   // accumulator buffers
     static constexpr int TMEM_COLS = 2 * BLOCK_N <= 32 ? 32 : (2 * BLOCK_N <= 64 ? 64 : (2 * BLOCK_N <= 128 ? 128 : (2 * BLOCK_N <= 256 ? 256 : 512)));
-    static constexpr int OUT_STAGE = 4 * 4096;     // 4 KB store staging per epilogue warp
+    static constexpr int EPI_WARPS = 4 * MT;
+    static constexpr int THREADS = 64 + 32 * EPI_WARPS;
+    static constexpr int OUT_STAGE = EPI_WARPS * 4096;   // 4 KB store staging per epilogue warp
     static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + OUT_STAGE + 256;
     static constexpr uint32_t IDESC =
-        make_idesc(ESIZE == 2 ? 1u : 2u, BLOCK_M, BLOCK_N, 0u, BKM ? 0u : 1u);
+        make_idesc(ESIZE == 2 ? 1u : 2u, 128, BLOCK_N, 0u, BKM ? 0u : 1u);
 };
 
 // BKM = 0: B staged MN-major (row-major n x p, contiguous in j).
 // BKM = 1: B staged K-major from its transpose (p x n), for the TF32 kind,
 //          whose MMA does not read MN-major operands.
-template <int ESIZE, int BLOCK_N, int STAGES, int BKM>
-__global__ void __launch_bounds__(192, 1)
+template <int ESIZE, int BLOCK_N, int STAGES, int BKM, int MT>
+__global__ void __launch_bounds__(DenseCfg<ESIZE, BLOCK_N, STAGES, BKM, MT>::THREADS, 1)
     dense_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const DenseArgs args) {
-    using Cfg = DenseCfg<ESIZE, BLOCK_N, STAGES, BKM>;
+    using Cfg = DenseCfg<ESIZE, BLOCK_N, STAGES, BKM, MT>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                ~static_cast<uintptr_t>(1023));
@@ -105,7 +115,7 @@ __global__ void __launch_bounds__(192, 1)
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&tfull[a], 1);
-            mbar_init(&tempty[a], 4);
+            mbar_init(&tempty[a], Cfg::EPI_WARPS);
         }
         mbar_init(drain, 1);
         ctl->abort = 0;
@@ -181,8 +191,9 @@ __global__ void __launch_bounds__(192, 1)
             int local_t = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x, ++local_t) {
-                const int acc = local_t & 1;
-                const uint32_t acc_phase = static_cast<uint32_t>(local_t >> 1) & 1u;
+                const int acc = Cfg::NBUF == 2 ? (local_t & 1) : 0;
+                const uint32_t acc_phase =
+                    static_cast<uint32_t>(Cfg::NBUF == 2 ? (local_t >> 1) : local_t) & 1u;
                 if (!mbar_wait(&tempty[acc], acc_phase ^ 1u, ctl, limit, status)) {
                     ok = false;
                     break;
@@ -204,10 +215,17 @@ __global__ void __launch_bounds__(192, 1)
                         const uint64_t a_off = static_cast<uint64_t>((k * 32) >> 4);
                         const uint64_t b_off = BKM ? a_off
                                                    : static_cast<uint64_t>((k * Cfg::MMA_K * 128) >> 4);
-                        if constexpr (ESIZE == 2)
-                            mma_f16(d, adesc + a_off, bdesc + b_off, Cfg::IDESC, (kb | k) != 0);
-                        else
-                            mma_tf32(d, adesc + a_off, bdesc + b_off, Cfg::IDESC, (kb | k) != 0);
+#pragma unroll
+                        for (int h = 0; h < MT; ++h) {
+                            // half h: A rows 128h.. (16 KB further in the stage),
+                            // accumulator columns h * BLOCK_N
+                            const uint32_t dh = d + static_cast<uint32_t>(h * BLOCK_N);
+                            const uint64_t ah = adesc + a_off + static_cast<uint64_t>((h * 128 * 128) >> 4);
+                            if constexpr (ESIZE == 2)
+                                mma_f16(dh, ah, bdesc + b_off, Cfg::IDESC, (kb | k) != 0);
+                            else
+                                mma_tf32(dh, ah, bdesc + b_off, Cfg::IDESC, (kb | k) != 0);
+                        }
                     }
                     mma_commit(&empty[stage]);
                     if (++stage == STAGES) {
@@ -225,18 +243,21 @@ __global__ void __launch_bounds__(192, 1)
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue: warps 2..5, TMEM lane quadrant = warp % 4
+        // ---------------- epilogue: TMEM lane quadrant q = warp % 4; with MT = 2
+        // warps 2..5 drain the upper half (rows 0..127), warps 6..9 the lower
         const int q = warp & 3;
+        const int h = (warp - 2) >> 2;
         int local_t = 0;
         for (int t = blockIdx.x; t < num_tiles; t += gridDim.x, ++local_t) {
-            const int acc = local_t & 1;
-            const uint32_t acc_phase = static_cast<uint32_t>(local_t >> 1) & 1u;
+            const int acc = Cfg::NBUF == 2 ? (local_t & 1) : 0;
+            const uint32_t acc_phase =
+                static_cast<uint32_t>(Cfg::NBUF == 2 ? (local_t >> 1) : local_t) & 1u;
             bool ok = mbar_wait(&tfull[acc], acc_phase, ctl, limit, status);
             if (!__all_sync(0xffffffffu, ok)) break;
             tc_fence_after();
             int tm, tn;
             tile_coords(t, args.tiles_m, args.tiles_n, args.group_m, tm, tn);
-            const int64_t row0 = static_cast<int64_t>(tm) * Cfg::BLOCK_M + q * 32;
+            const int64_t row0 = static_cast<int64_t>(tm) * Cfg::BLOCK_M + h * 128 + q * 32;
             const int64_t rl = args.m - row0;
             const int rows_left = rl <= 0 ? 0 : (rl >= 32 ? 32 : static_cast<int>(rl));
             uint8_t* stage_w = out_stage + (warp - 2) * 4096;
@@ -244,7 +265,7 @@ __global__ void __launch_bounds__(192, 1)
             for (int c = 0; c < BLOCK_N / 32; ++c) {
                 uint32_t r[32];
                 tmem_ld32(tmem_base + (static_cast<uint32_t>(q * 32) << 16) +
-                              static_cast<uint32_t>(acc * BLOCK_N + c * 32),
+                              static_cast<uint32_t>((acc + h) * BLOCK_N + c * 32),
                           r);
                 tmem_ld_wait();
                 const int64_t col0 = static_cast<int64_t>(tn) * BLOCK_N + c * 32;
@@ -264,10 +285,10 @@ __global__ void __launch_bounds__(192, 1)
     }
 }
 
-template <int ESIZE, int BLOCK_N, int STAGES, int BKM>
+template <int ESIZE, int BLOCK_N, int STAGES, int BKM, int MT>
 int launch_cfg(int64_t m, int64_t n, int64_t p, const void* A, int64_t lda, const void* B,
                int64_t ldb, float* C, cudaStream_t s, moa_stats* st) {
-    using Cfg = DenseCfg<ESIZE, BLOCK_N, STAGES, BKM>;
+    using Cfg = DenseCfg<ESIZE, BLOCK_N, STAGES, BKM, MT>;
     const CUtensorMapDataType dt =
         ESIZE == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     CUtensorMap tmA, tmB;
@@ -296,7 +317,7 @@ int launch_cfg(int64_t m, int64_t n, int64_t p, const void* A, int64_t lda, cons
     args.status = launch_status_ptr();
     if (!args.status) return MOA_ERR_CUDA;
 
-    auto kern = dense_tc_kernel<ESIZE, BLOCK_N, STAGES, BKM>;
+    auto kern = dense_tc_kernel<ESIZE, BLOCK_N, STAGES, BKM, MT>;
     static bool attr_set = false;   // per instantiation; the attribute is per device function
     if (!attr_set) {
         cudaError_t e =
@@ -307,7 +328,7 @@ int launch_cfg(int64_t m, int64_t n, int64_t p, const void* A, int64_t lda, cons
     const long tiles = static_cast<long>(args.tiles_m) * args.tiles_n;
     const int grid = static_cast<int>(std::min<long>(tiles, num_sms()));
     prof_begin(s);
-    dense_tc_kernel<ESIZE, BLOCK_N, STAGES, BKM><<<grid, 192, Cfg::SMEM, s>>>(tmA, tmB, args);
+    kern<<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(tmA, tmB, args);
     cudaError_t e = cudaGetLastError();
     prof_end(s);
     if (e != cudaSuccess) return cuda_fail(e, "dense_tc_kernel launch");
@@ -320,6 +341,16 @@ int launch_cfg(int64_t m, int64_t n, int64_t p, const void* A, int64_t lda, cons
         st->kernels += 1;
     }
     return MOA_OK;
+}
+
+// 256 x 256 tiles for the 256-wide case: on unless MOA_DENSE_TALL=0.
+bool dense_tall_tiles() {
+    static int on = -1;
+    if (on < 0) {
+        const char* env = std::getenv("MOA_DENSE_TALL");
+        on = (env && env[0] == '0') ? 0 : 1;
+    }
+    return on == 1;
 }
 
 }  // namespace
@@ -340,15 +371,22 @@ int dense_tc_launch(bool in_bf16, int64_t m, int64_t n, int64_t p, const void* A
     if (tuned) bn = tuned;
     if (tile_override() == 64 || tile_override() == 128 || tile_override() == 256)
         bn = tile_override();
+    // 256 x 256 tiles once they still give every SM a tile (they halve the
+    // tile count of 128 x 256)
+    const bool tall = dense_tall_tiles() && ceil_div(m, 256) * ceil_div(p, 256) >= sms;
     if (in_bf16) {
-        if (bn == 256) return launch_cfg<2, 256, 4, 0>(m, n, p, A, lda, B, ldb, C, s, st);
-        if (bn == 128) return launch_cfg<2, 128, 6, 0>(m, n, p, A, lda, B, ldb, C, s, st);
-        return launch_cfg<2, 64, 8, 0>(m, n, p, A, lda, B, ldb, C, s, st);
+        if (bn == 256)
+            return tall ? launch_cfg<2, 256, 3, 0, 2>(m, n, p, A, lda, B, ldb, C, s, st)
+                        : launch_cfg<2, 256, 4, 0, 1>(m, n, p, A, lda, B, ldb, C, s, st);
+        if (bn == 128) return launch_cfg<2, 128, 6, 0, 1>(m, n, p, A, lda, B, ldb, C, s, st);
+        return launch_cfg<2, 64, 8, 0, 1>(m, n, p, A, lda, B, ldb, C, s, st);
     }
     // TF32: B is passed transposed (p x n, row pitch ldb), K-major.
-    if (bn == 256) return launch_cfg<4, 256, 4, 1>(m, n, p, A, lda, B, ldb, C, s, st);
-    if (bn == 128) return launch_cfg<4, 128, 6, 1>(m, n, p, A, lda, B, ldb, C, s, st);
-    return launch_cfg<4, 64, 8, 1>(m, n, p, A, lda, B, ldb, C, s, st);
+    if (bn == 256)
+        return tall ? launch_cfg<4, 256, 3, 1, 2>(m, n, p, A, lda, B, ldb, C, s, st)
+                    : launch_cfg<4, 256, 4, 1, 1>(m, n, p, A, lda, B, ldb, C, s, st);
+    if (bn == 128) return launch_cfg<4, 128, 6, 1, 1>(m, n, p, A, lda, B, ldb, C, s, st);
+    return launch_cfg<4, 64, 8, 1, 1>(m, n, p, A, lda, B, ldb, C, s, st);
 }
 
 }  // namespace moa
