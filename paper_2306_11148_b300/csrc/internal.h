@@ -56,7 +56,7 @@ int make_tmap_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uin
 // 3-D variant: `depth` matrices of outer x inner, matrix pitch `plane_bytes`.
 int make_tmap_3d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uint64_t inner,
                  uint64_t outer, uint64_t depth, uint64_t pitch_bytes, uint64_t plane_bytes,
-                 uint32_t box_inner, uint32_t box_outer);
+                 uint32_t box_inner, uint32_t box_outer, int swizzle_bytes = 128);
 
 // ------------------------------------------------------------------ kernels
 // Dense tcgen05 GEMM, A (m x n, row pitch lda elements), C (m x p, FP32,

@@ -248,6 +248,19 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr, uint32_t lbo
     return d;
 }
 
+// The same for the 64-byte swizzle (layout type 4): K-major rows of 64 bytes,
+// 8-row atoms of 512 bytes.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr, uint32_t lbo_bytes,
+                                                   uint32_t sbo_bytes) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);
+    d |= static_cast<uint64_t>((lbo_bytes >> 4) & 0x3FFFu) << 16;
+    d |= static_cast<uint64_t>((sbo_bytes >> 4) & 0x3FFFu) << 32;
+    d |= static_cast<uint64_t>(1) << 46;
+    d |= static_cast<uint64_t>(4) << 61;
+    return d;
+}
+
 // Instruction descriptor for kind::f16 / kind::tf32 / kind::f8f6f4 with FP32
 // accumulation.  ab_format: 1 = BF16 (kind::f16), 2 = TF32 (kind::tf32),
 // 0 = E4M3 (kind::f8f6f4).  a_mn / b_mn: operand

@@ -143,7 +143,7 @@ int make_tmap_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uin
 
 int make_tmap_3d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uint64_t inner,
                  uint64_t outer, uint64_t depth, uint64_t pitch_bytes, uint64_t plane_bytes,
-                 uint32_t box_inner, uint32_t box_outer) {
+                 uint32_t box_inner, uint32_t box_outer, int swizzle_bytes) {
     int rc = get_encode();
     if (rc != MOA_OK) return rc;
     cuuint64_t dims[3] = {inner, outer, depth};
@@ -151,7 +151,8 @@ int make_tmap_3d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uin
     cuuint32_t box[3] = {box_inner, box_outer, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = g_encode(map, dt, 3, const_cast<void*>(base), dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         char buf[256];

@@ -501,15 +501,19 @@ namespace {
 
 constexpr int kBM = 128, kBK = 64;                // kBK: BF16 elements per K block
 constexpr int kABytes = kBM * 128;                 // 128 rows x 128 bytes of K
-constexpr int kBChunkBytes = kBK * 128;            // 64 rows x 64 BF16 columns
 constexpr int kMaxLevels = 12;
 // Digit-plane formats of the slice GEMM.  kFmtBF16: kind::f16, B planes
 // MN-major (n x p, read as 64-column chunks).  kFmtE4M3: kind::f8f6f4, B
 // planes hold B^T (p x n, K-major, one box per stage).  A K block is 128
 // bytes of K either way: 64 BF16 or 128 E4M3 elements.
-constexpr int kFmtBF16 = 0, kFmtE4M3 = 1;
+// kFmtBF16KB (FP32 accuracy only): all three BF16 slices of A and of B of
+// one 32-deep K block share a stage (A K-major with 64-byte rows, 64-byte
+// swizzle), and the six slice products of that K block run from it: every
+// staged byte feeds two or three products, half the operand bytes per MMA
+// cycle of one (A slice, B slice) pair per stage.
+constexpr int kFmtBF16 = 0, kFmtE4M3 = 1, kFmtBF16KB = 2;
 template <int FMT>
-constexpr int block_k() { return FMT == kFmtE4M3 ? 128 : 64; }
+constexpr int block_k() { return FMT == kFmtE4M3 ? 128 : (FMT == kFmtBF16KB ? 32 : 64); }
 
 // Kernel variants (tile width BN x epilogue mode):
 //   kModeF32     FP32 accuracy; two chunk accumulators; each epilogue warp keeps
@@ -525,9 +529,17 @@ constexpr int kModeF32 = 0, kModeF64Reg = 1, kModeF64Tmem = 2;
 template <int BN, int MODE, int FMT>
 struct SplitCfg {
     static constexpr int kBKe = block_k<FMT>();   // K elements per stage
-    static constexpr int kStages = BN == 256 ? 4 : (BN == 192 ? 5 : 6);
-    static constexpr int kBBytes = (BN / 64) * kBChunkBytes;
-    static constexpr int kStageBytes = kABytes + kBBytes;
+    static constexpr bool kKB = FMT == kFmtBF16KB;
+    // A part of a stage: one slice (128 rows x 128 B) or, kb-major, three
+    // slices of 128 rows x 64 B; B part: BN / 64 chunks of 64 columns x kBKe
+    // K rows per slice staged.
+    static constexpr int kASlice = kKB ? kBM * 64 : kABytes;
+    static constexpr int kAStage = kKB ? 3 * kASlice : kABytes;
+    static constexpr int kBChunk = kBKe * 128;   // MN-major chunk (BF16 formats)
+    static constexpr int kBSlice = FMT == kFmtE4M3 ? BN * 128 : (BN / 64) * kBChunk;
+    static constexpr int kBBytes = kKB ? 3 * kBSlice : kBSlice;
+    static constexpr int kStageBytes = kAStage + kBBytes;
+    static constexpr int kStages = kKB ? (BN == 256 ? 3 : 4) : (BN == 256 ? 4 : (BN == 192 ? 5 : 6));
     static constexpr int kSmem = 1024 + kStages * kStageBytes + 256;
     static constexpr int kColsPerWarp = MODE == kModeF64Tmem ? 128 : 64;
     static constexpr int kEpiWarps = 4 * (BN / kColsPerWarp);
@@ -598,7 +610,7 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                ~static_cast<uintptr_t>(1023));
     uint8_t* sA = smem;
-    uint8_t* sB = smem + kStages * kABytes;
+    uint8_t* sB = smem + kStages * Cfg::kAStage;
     uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kStages * Cfg::kBBytes);
     uint64_t* full = bars;
     uint64_t* empty = bars + kStages;
@@ -654,6 +666,33 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
                 split_tile_coords(t, args.tiles_m, args.tiles_n, args.group_m, tm, tn);
                 for (int L = 0; L < args.levels && ok; ++L) {
                     const int np = level_pairs(args, L);
+                    if constexpr (Cfg::kKB) {
+                        // kb-major: the three slices of A and of B of K block kb
+                        for (int kb = 0; kb < num_kb && ok; ++kb) {
+                            if (!mbar_wait(&empty[stage], phase ^ 1u, ctl, limit, status)) {
+                                ok = false;
+                                break;
+                            }
+                            mbar_arrive_expect_tx(&full[stage], Cfg::kStageBytes);
+                            uint8_t* a_st = sA + stage * Cfg::kAStage;
+                            uint8_t* b_st = sB + stage * Cfg::kBBytes;
+#pragma unroll
+                            for (int sl = 0; sl < 3; ++sl) {
+                                tma_load_3d(a_st + sl * Cfg::kASlice, &tmA, &full[stage],
+                                            kb * kBKe, tm * kBM, sl);
+#pragma unroll
+                                for (int c = 0; c < BN / 64; ++c)
+                                    tma_load_3d(b_st + sl * Cfg::kBSlice + c * Cfg::kBChunk, &tmB,
+                                                &full[stage], tn * BN + c * 64, kb * kBKe, sl);
+                            }
+                            ++issued;
+                            if (++stage == kStages) {
+                                stage = 0;
+                                phase ^= 1u;
+                            }
+                        }
+                        continue;
+                    }
                     for (int kb = 0; kb < num_kb && ok; ++kb) {
                         for (int q = 0; q < np; ++q) {
                             int s, u;
@@ -663,7 +702,7 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
                                 break;
                             }
                             mbar_arrive_expect_tx(&full[stage], Cfg::kStageBytes);
-                            tma_load_3d(sA + stage * kABytes, &tmA, &full[stage], kb * kBKe,
+                            tma_load_3d(sA + stage * Cfg::kAStage, &tmA, &full[stage], kb * kBKe,
                                         tm * kBM, s);
                             if constexpr (FMT == kFmtE4M3) {
                                 // B^T plane u: BN rows (j) x 128 bytes (k)
@@ -672,8 +711,8 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
                             } else {
 #pragma unroll
                                 for (int c = 0; c < BN / 64; ++c)
-                                    tma_load_3d(sB + stage * Cfg::kBBytes + c * kBChunkBytes, &tmB,
-                                                &full[stage], tn * BN + c * 64, kb * kBK, u);
+                                    tma_load_3d(sB + stage * Cfg::kBBytes + c * Cfg::kBChunk, &tmB,
+                                                &full[stage], tn * BN + c * 64, kb * kBKe, u);
                             }
                             ++issued;
                             if (++stage == kStages) {
@@ -719,6 +758,37 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
                         const int kb1 = min(num_kb, kb0 + kc);
                         bool first = true;
                         for (int kb = kb0; kb < kb1 && ok; ++kb) {
+                            if constexpr (Cfg::kKB) {
+                                // the six slice products of K block kb from one stage
+                                if (!mbar_wait(&full[stage], phase, ctl, limit, status)) {
+                                    ok = false;
+                                    break;
+                                }
+                                tc_fence_after();
+                                const uint8_t* a_st = sA + stage * Cfg::kAStage;
+                                const uint8_t* b_st = sB + stage * Cfg::kBBytes;
+#pragma unroll
+                                for (int q = 0; q < 6; ++q) {
+                                    int sl, u;
+                                    pair_at(args, 0, q, sl, u);
+                                    const uint64_t adesc = smem_desc_sw64(
+                                        smem_u32(a_st + sl * Cfg::kASlice), 16, 512);
+                                    const uint64_t bdesc = smem_desc_sw128(
+                                        smem_u32(b_st + u * Cfg::kBSlice), Cfg::kBChunk, 1024);
+#pragma unroll
+                                    for (int k = 0; k < kBKe / 16; ++k)
+                                        mma_f16(d, adesc + static_cast<uint64_t>((k * 32) >> 4),
+                                                bdesc + static_cast<uint64_t>((k * 16 * 128) >> 4),
+                                                Cfg::kIdesc, (first && q == 0 && k == 0) ? 0u : 1u);
+                                }
+                                first = false;
+                                mma_commit(&empty[stage]);
+                                if (++stage == kStages) {
+                                    stage = 0;
+                                    phase ^= 1u;
+                                }
+                                continue;
+                            }
                             for (int q = 0; q < np; ++q) {
                                 if (!mbar_wait(&full[stage], phase, ctl, limit, status)) {
                                     ok = false;
@@ -726,10 +796,10 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
                                 }
                                 tc_fence_after();
                                 const uint64_t adesc =
-                                    smem_desc_sw128(smem_u32(sA + stage * kABytes), 16, 1024);
+                                    smem_desc_sw128(smem_u32(sA + stage * Cfg::kAStage), 16, 1024);
                                 const uint64_t bdesc = smem_desc_sw128(
                                     smem_u32(sB + stage * Cfg::kBBytes),
-                                    FMT == kFmtE4M3 ? 16 : kBChunkBytes, 1024);
+                                    FMT == kFmtE4M3 ? 16 : Cfg::kBChunk, 1024);
                                 // four MMAs of 32 bytes of K each
 #pragma unroll
                                 for (int k = 0; k < 4; ++k) {
@@ -931,14 +1001,16 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
 }  // namespace
 
 // ====================================================================== host side
-static int f32_split_chunk_kb() {
-    static int kb = 0;
-    if (kb == 0) {
+// FP32-accuracy chunk length in K blocks of `bk` elements
+// (MOA_F32_SPLIT_CHUNK_K elements, default 256).
+static int f32_split_chunk_kb(int bk) {
+    static long k = 0;
+    if (k == 0) {
         const char* env = std::getenv("MOA_F32_SPLIT_CHUNK_K");
-        const long k = env ? std::strtol(env, nullptr, 10) : 256;
-        kb = static_cast<int>(std::max<long>(1, (k + kBK - 1) / kBK));
+        k = env ? std::strtol(env, nullptr, 10) : 256;
+        if (k < 1) k = 256;
     }
-    return kb;
+    return static_cast<int>(std::max<long>(1, (k + bk - 1) / bk));
 }
 
 int split_slices(moa_dtype dt, int slices) {
@@ -1068,7 +1140,8 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
     int* status = launch_status_ptr();
     if (!status) return MOA_ERR_CUDA;
     const bool e4m3 = is_e4m3_split(dt);
-    const int bke = e4m3 ? block_k<kFmtE4M3>() : block_k<kFmtBF16>();
+    const int bke = e4m3 ? block_k<kFmtE4M3>()
+                         : (dt == MOA_F32_SPLIT ? block_k<kFmtBF16KB>() : block_k<kFmtBF16>());
     uint8_t* base = static_cast<uint8_t*>(ws);
     uint8_t* a_sl = base + L.a_off;
     uint8_t* b_sl = base + L.b_off;
@@ -1105,7 +1178,7 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
         // Flush the FP32 TMEM accumulator into the epilogue's FP32 running sum
         // every kc K blocks: shorter chunks bound the accumulation error of
         // the tensor core's FP32 adds (MOA_F32_SPLIT_CHUNK_K, default 256).
-        a.kc[0] = f32_split_chunk_kb();
+        a.kc[0] = f32_split_chunk_kb(bke);
         a.drop = 0;
     } else {
         int* eA = reinterpret_cast<int*>(base + L.ea_off);
@@ -1168,6 +1241,21 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
         rc = bn == 256   ? launch_split_cfg<256, kModeF64Tmem, kFmtE4M3>(a, tmA, tmB, s, st)
              : bn == 192 ? launch_split_cfg<192, kModeF64Reg, kFmtE4M3>(a, tmA, tmB, s, st)
                          : launch_split_cfg<128, kModeF64Reg, kFmtE4M3>(a, tmA, tmB, s, st);
+    } else if (dt == MOA_F32_SPLIT) {
+        // kb-major stages: A slices 32 K x 128 rows (64-byte swizzle), B
+        // slices 64 columns x 32 K rows per chunk
+        rc = make_tmap_3d(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, a_sl, static_cast<uint64_t>(n),
+                          static_cast<uint64_t>(m), static_cast<uint64_t>(S),
+                          static_cast<uint64_t>(L.lda) * 2, static_cast<uint64_t>(a_plane) * 2, bke,
+                          kBM, 64);
+        if (rc != MOA_OK) return rc;
+        rc = make_tmap_3d(&tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, b_sl, static_cast<uint64_t>(p),
+                          static_cast<uint64_t>(n), static_cast<uint64_t>(S),
+                          static_cast<uint64_t>(L.ldb) * 2, static_cast<uint64_t>(b_plane) * 2, 64,
+                          bke);
+        if (rc != MOA_OK) return rc;
+        rc = bn == 256 ? launch_split_cfg<256, kModeF32, kFmtBF16KB>(a, tmA, tmB, s, st)
+                       : launch_split_cfg<128, kModeF32, kFmtBF16KB>(a, tmA, tmB, s, st);
     } else {
         rc = make_tmap_3d(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, a_sl, static_cast<uint64_t>(n),
                           static_cast<uint64_t>(m), static_cast<uint64_t>(S),
@@ -1179,13 +1267,9 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
                           static_cast<uint64_t>(L.ldb) * 2, static_cast<uint64_t>(b_plane) * 2, 64,
                           kBK);
         if (rc != MOA_OK) return rc;
-        if (a.f64)
-            rc = bn == 256   ? launch_split_cfg<256, kModeF64Tmem, kFmtBF16>(a, tmA, tmB, s, st)
-                 : bn == 192 ? launch_split_cfg<192, kModeF64Reg, kFmtBF16>(a, tmA, tmB, s, st)
-                             : launch_split_cfg<128, kModeF64Reg, kFmtBF16>(a, tmA, tmB, s, st);
-        else
-            rc = bn == 256 ? launch_split_cfg<256, kModeF32, kFmtBF16>(a, tmA, tmB, s, st)
-                           : launch_split_cfg<128, kModeF32, kFmtBF16>(a, tmA, tmB, s, st);
+        rc = bn == 256   ? launch_split_cfg<256, kModeF64Tmem, kFmtBF16>(a, tmA, tmB, s, st)
+             : bn == 192 ? launch_split_cfg<192, kModeF64Reg, kFmtBF16>(a, tmA, tmB, s, st)
+                         : launch_split_cfg<128, kModeF64Reg, kFmtBF16>(a, tmA, tmB, s, st);
     }
     if (st) {
         st->slices = S;
