@@ -357,23 +357,34 @@ bool dense_tall_tiles() {
 
 int dense_tc_launch(bool in_bf16, int64_t m, int64_t n, int64_t p, const void* A, int64_t lda,
                     const void* B, int64_t ldb, float* C, cudaStream_t s, moa_stats* st) {
-    // Tile planner: the widest N tile (fewest A re-reads) unless that leaves
-    // most SMs idle, in which case narrower tiles spread the work.
-    // A per-thread override (moa_set_block_n) or a measured choice for this
-    // shape bucket (moa_tune_dense) takes precedence.
-    const long tiles256 = ceil_div(m, 128) * ceil_div(p, 256);
-    const long tiles128 = ceil_div(m, 128) * ceil_div(p, 128);
+    // Tile planner (the block-size model of Sec. 3.4 on this machine): the
+    // candidate tiles are 256 x 256, 128 x 256, 128 x 128 and 128 x 64; each
+    // costs ceil(tiles / SMs) waves of (tile area / its relative MMA
+    // efficiency), the efficiencies measured on the B300 (1.0, 0.9, 0.7, 0.39:
+    // narrower tiles re-read their operands more often per flop).  The
+    // cheapest wins, the larger tile on a tie.  A per-thread override
+    // (moa_set_block_n) or a measured choice for this shape bucket
+    // (moa_tune_dense) fixes the width; the 256 x 256 / 128 x 256 choice for
+    // width 256 stays with the model (MOA_DENSE_TALL=0 rules out 256 x 256).
     const int sms = num_sms();
+    auto cost = [&](int bm, int bn_, double eff) {
+        const long tiles = ceil_div(m, bm) * ceil_div(p, bn_);
+        return static_cast<double>((tiles + sms - 1) / sms) * (bm * bn_) / eff;
+    };
+    const double c_tall = dense_tall_tiles() ? cost(256, 256, 1.0) : 1e300;
+    const double c256 = cost(128, 256, 0.9), c128 = cost(128, 128, 0.7), c64 = cost(128, 64, 0.39);
     int bn = 256;
-    if (tiles256 < sms && tiles128 > tiles256) bn = 128;
-    if (bn == 128 && tiles128 < sms && p <= 64) bn = 64;
+    double best = std::min(c_tall, c256);
+    if (c128 < best) {
+        bn = 128;
+        best = c128;
+    }
+    if (c64 < best) bn = 64;
     const int tuned = tuned_block_n(in_bf16 ? MOA_BF16 : MOA_F32_TF32, m, n, p);
     if (tuned) bn = tuned;
     if (tile_override() == 64 || tile_override() == 128 || tile_override() == 256)
         bn = tile_override();
-    // 256 x 256 tiles once they still give every SM a tile (they halve the
-    // tile count of 128 x 256)
-    const bool tall = dense_tall_tiles() && ceil_div(m, 256) * ceil_div(p, 256) >= sms;
+    const bool tall = bn == 256 && c_tall <= c256;
     if (in_bf16) {
         if (bn == 256)
             return tall ? launch_cfg<2, 256, 3, 0, 2>(m, n, p, A, lda, B, ldb, C, s, st)
