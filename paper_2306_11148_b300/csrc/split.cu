@@ -1085,14 +1085,30 @@ static int launch_split_cfg(const SplitArgs& a, const CUtensorMap& tmA, const CU
     return MOA_OK;
 }
 
-// Tile width of the slice GEMM: 256 when that still gives every SM a tile
-// (fewest B re-reads per flop), else 128.  moa_set_block_n(128 | 192 | 256)
-// forces it (192: FP64 accuracy only).
+// Tile width of the slice GEMM by a wave-count cost model: each width costs
+// ceil(tiles / SMs) waves of (width / its relative efficiency), measured on
+// the B300 for the split kernels (FP32 accuracy: 128 at 0.8 of 256; FP64
+// accuracy: 192 at 0.97, 128 at 0.9); the cheapest wins, the wider on a
+// tie.  moa_set_block_n(128 | 192 | 256) forces it (192: FP64 accuracy only).
 static int split_block_n(int64_t m, int64_t p, bool f64) {
     const int ov = tile_override();
     if (ov == 128 || ov == 256 || (ov == 192 && f64)) return ov;
-    const long tiles = ceil_div(m, kBM) * ceil_div(p, 256);
-    return tiles >= num_sms() ? 256 : 128;
+    const long sms = num_sms();
+    auto cost = [&](int bn, double eff) {
+        const long tiles = ceil_div(m, kBM) * ceil_div(p, bn);
+        return static_cast<double>((tiles + sms - 1) / sms) * bn / eff;
+    };
+    int best = 256;
+    double c = cost(256, 1.0);
+    if (f64) {
+        const double c192 = cost(192, 0.97);
+        if (c192 < c) {
+            best = 192;
+            c = c192;
+        }
+    }
+    if (cost(128, f64 ? 0.9 : 0.8) < c) best = 128;
+    return best;
 }
 
 // Exponent and digit pre-passes of the FP64-accuracy modes for input type T.
