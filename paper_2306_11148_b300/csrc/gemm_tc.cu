@@ -3,22 +3,25 @@
 // C[(i*p)+j] := sum_k A[(i*n)+k] * B[(k*p)+j]   (Eq. (eq:dnf), Sec. 2)
 //
 // Dimension lifting (Sec. 3.1) mapped onto the B300:
-//   * the i loop is split into 128-row tiles (one tile row per TMEM lane), the
-//     j loop into BLOCK_N-column tiles (the MMA N extent), so that each output
-//     tile is an independent block product (Fig. fig:omega);
+//   * the i loop is split into 128- or 256-row tiles (128 rows per TMEM lane
+//     set; a 256-row tile runs two M = 128 MMAs per K step on one staged B
+//     tile), the j loop into BLOCK_N-column tiles (the MMA N extent), so that
+//     each output tile is an independent block product (Fig. fig:omega);
 //   * the sigma (k) loop is split into K blocks of 128 bytes of operand each,
 //     summed into the same TMEM accumulator (the "extra summation loop" that
 //     closes Sec. 3.1);
 //   * output tiles are dealt round-robin to persistent CTAs, one per SM, in a
 //     grouped raster order so that neighbouring CTAs share A rows and B
-//     columns in L2 (the L2-level lift of Sec. 3.4).
+//     columns in L2 (the L2-level lift of Sec. 3.4);
+//   * the tile shape is chosen per problem by a wave-count cost model (the
+//     block-size model of Sec. 3.4).
 // Both operands are read exactly as the ONF lays them out: A row strips are
 // K-major (contiguous in k), B row strips are MN-major (contiguous in j, the
 // "row of B" of Fig. fig:mm).  TMA stages them into 128-byte-swizzled shared
-// memory; one thread issues tcgen05.mma; four epilogue warps (one per TMEM
-// lane quadrant) drain the TMEM
-// accumulator (double-buffered, so the next tile's MMAs overlap the stores)
-// and write C through a shared-memory staging tile in coalesced row segments.
+// memory; one thread issues tcgen05.mma; the epilogue warps (one or two per
+// TMEM lane quadrant) drain the accumulator (double-buffered for 128-row
+// tiles, so the next tile's MMAs overlap the stores) and write C through a
+// shared-memory staging tile in coalesced row segments.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
