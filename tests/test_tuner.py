@@ -88,18 +88,18 @@ def test_widest_tiles_exact_with_ragged_rows_and_columns(L, dt, m):
 @pytest.mark.gpu
 @pytest.mark.parametrize("dt", [moa.MOA_BF16, moa.MOA_F32_TF32])
 def test_tall_tiles_ragged_edges_exact(L, dt):
-    """256 x 256 tiles (two M = 128 MMAs per K step) are used once they still
-    give every SM a tile: 13 x 12 of them here, the last row and column tiles
-    ragged (m = 13 * 256 - 50, p = 12 * 256 - 7).  Integer inputs: the rows
-    around every tile boundary and the ragged edge are exact against the
-    oracle."""
-    m, n, p = 13 * 256 - 50, 1000, 12 * 256 - 7
+    """256 x 256 tiles (two M = 128 MMAs per K step) are the planner's choice
+    here: 16 x 9 of them make one wave on 148 SMs, against two waves of
+    128 x 256 tiles.  The last row and column tiles are ragged
+    (m = 16 * 256 - 50, p = 9 * 256 - 7).  Integer inputs: the rows around
+    every tile boundary and the ragged edge are exact against the oracle."""
+    m, n, p = 16 * 256 - 50, 1000, 9 * 256 - 7
     A, B = inputs.integer_pair(m, n, p, dtype=moa.in_dtype(dt), seed=77)
     C, st = moa.gemm(A.cuda(), B.cuda(), dt, stats=True)
     moa.sync_status()
     assert st.block_m == 256 and st.block_n == 256
-    rows = np.array(sorted({0, 1, 127, 128, 255, 256, 1000, 2047, 2048, 3071, 3072, m - 50, m - 2, m - 1}),
-                    dtype=np.int64)
+    rows = np.array(sorted({0, 1, 127, 128, 255, 256, 1000, 2047, 2048, 3071, 3072, 3839, 3840,
+                            m - 50, m - 2, m - 1}), dtype=np.int64)
     got = C[torch.from_numpy(rows).cuda()].double().cpu().numpy()
     ref = oracle.gemm_rows(A.double().numpy(), B.double().numpy(), rows)
     assert np.array_equal(got, ref)
