@@ -80,13 +80,16 @@ __device__ __forceinline__ void load8(const float* __restrict__ X, int64_t r, in
 // 8 consecutive elements per thread, one 16-byte store per slice plane.
 // Flags NaN/Inf (and values whose leading slice overflows BF16) in the
 // status word.
-__global__ void split3_kernel(const float* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
-                              __nv_bfloat16* __restrict__ out, int64_t plane, int vec, int* status) {
+// The pre-pass kernels below are written as "parts" over a range of blocks
+// (bid of nblk), so that one launch can run the part for A and the part for
+// B side by side: fewer launches per GEMM, which matters for small problems.
+__device__ void split3_part(const float* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
+                            __nv_bfloat16* __restrict__ out, int64_t plane, int vec, int* status,
+                            int64_t bid, int64_t nblk) {
     const int64_t gpr = ld / 8;                 // 8-element groups per row
     const int64_t total = rows * gpr;
     bool bad = false;
-    for (int64_t g = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; g < total;
-         g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    for (int64_t g = bid * blockDim.x + threadIdx.x; g < total; g += nblk * blockDim.x) {
         const int64_t r = g / gpr, c0 = (g - r * gpr) * 8;
         float x[8];
         load8(X, r, cols, c0, vec != 0, x);
@@ -112,6 +115,18 @@ __global__ void split3_kernel(const float* __restrict__ X, int64_t rows, int64_t
         *reinterpret_cast<uint4*>(out + 2 * plane + o) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
     }
     if (bad) atomicCAS(status, kDevOk, kDevNonFinite);
+}
+
+// Blocks [0, ga) split A, the rest split B.
+__global__ void split3_pair_kernel(const float* __restrict__ A, int64_t m, int64_t n, int64_t lda,
+                                   __nv_bfloat16* __restrict__ a_out, int64_t a_plane, int va,
+                                   const float* __restrict__ B, int64_t p, int64_t ldb,
+                                   __nv_bfloat16* __restrict__ b_out, int64_t b_plane, int vb,
+                                   int* status, int ga) {
+    if (static_cast<int>(blockIdx.x) < ga)
+        split3_part(A, m, n, lda, a_out, a_plane, va, status, blockIdx.x, ga);
+    else
+        split3_part(B, n, p, ldb, b_out, b_plane, vb, status, blockIdx.x - ga, gridDim.x - ga);
 }
 
 template <typename T>
@@ -268,14 +283,13 @@ struct DigitGen<float> {
 
 // One warp per row: exponent of max |A[i,:]| plus `bias` (headroom bits).
 template <typename T>
-__global__ void row_exp_kernel(const T* __restrict__ X, int64_t rows, int64_t cols, int bias,
-                               int* __restrict__ e_out, int* status) {
+__device__ void row_exp_part(const T* __restrict__ X, int64_t rows, int64_t cols, int bias,
+                             int* __restrict__ e_out, int* status, int64_t bid, int64_t nblk) {
     using B = Bits<T>;
     const int lane = threadIdx.x & 31;
-    const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    const int64_t warps = nblk * (blockDim.x >> 5);
     bool bad = false;
-    for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5);
-         r < rows; r += warps) {
+    for (int64_t r = bid * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
         typename B::U mx = 0;
         for (int64_t c = lane; c < cols; c += 32) mx = max(mx, B::abs_bits(X[r * cols + c]));
 #pragma unroll
@@ -291,29 +305,39 @@ __global__ void row_exp_kernel(const T* __restrict__ X, int64_t rows, int64_t co
     if (bad) atomicCAS(status, kDevOk, kDevNonFinite);
 }
 
-// Column maxima of |B| (bit patterns), by atomicMax over row chunks.
+// Column maxima of |B| (bit patterns), by atomicMax over row chunks: block
+// bid covers columns 256 (bid % gx) .. + 255 and rows chunk (bid / gx) ..
 template <typename T>
-__global__ void col_max_kernel(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t chunk,
-                               typename Bits<T>::U* __restrict__ cmax) {
+__device__ void col_max_part(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t chunk,
+                             typename Bits<T>::U* __restrict__ cmax, int64_t bid, int64_t gx) {
     using B = Bits<T>;
-    const int64_t c = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    const int64_t c = (bid % gx) * blockDim.x + threadIdx.x;
     if (c >= cols) return;
-    const int64_t r0 = blockIdx.y * chunk;
+    const int64_t r0 = (bid / gx) * chunk;
     const int64_t r1 = min(rows, r0 + chunk);
     typename B::U mx = 0;
     for (int64_t r = r0; r < r1; ++r) mx = max(mx, B::abs_bits(X[r * cols + c]));
     atomicMax(&cmax[c], mx);
 }
 
+// Exponent of a column of B from its max bit pattern (plus `bias`); flags
+// NaN/Inf in *status unless status is null.
 template <typename T>
-__global__ void col_exp_kernel(const typename Bits<T>::U* __restrict__ cmax, int64_t cols,
-                               int bias, int* __restrict__ e_out, int* status) {
-    using B = Bits<T>;
-    const int64_t c = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-    if (c >= cols) return;
-    const typename B::U M = cmax[c];
-    if (M >= B::kInf) atomicCAS(status, kDevOk, kDevNonFinite);
-    e_out[c] = B::frexp_exp(M) + bias;
+__device__ __forceinline__ int col_exp(typename Bits<T>::U M, int bias, int* status) {
+    if (status && M >= Bits<T>::kInf) atomicCAS(status, kDevOk, kDevNonFinite);
+    return Bits<T>::frexp_exp(M) + bias;
+}
+
+// Blocks [0, rblocks): row exponents of A; the rest: column maxima of B.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    exps_kernel(const T* __restrict__ A, int64_t m, int64_t n, const T* __restrict__ B, int64_t p,
+                int64_t chunk, int bias, int* __restrict__ eA, typename Bits<T>::U* __restrict__ cmax,
+                int* status, int rblocks, int64_t gx) {
+    if (static_cast<int>(blockIdx.x) < rblocks)
+        row_exp_part(A, m, n, bias, eA, status, blockIdx.x, rblocks);
+    else
+        col_max_part(B, n, p, chunk, cmax, blockIdx.x - rblocks, gx);
 }
 
 // Loads X[r, c0 .. c0+7] of an FP64 matrix (zero past `cols`).
@@ -335,16 +359,19 @@ __device__ __forceinline__ void load8(const double* __restrict__ X, int64_t r, i
 
 // Integer digits of every element into S BF16 planes (row pitch ld, a
 // multiple of 8; zero pad); 8 consecutive elements per thread, one 16-byte
-// store per digit plane.  axis 0: exponent per row (e[r]); axis 1: per
-// column (e[c]).  vec: X rows start 16-byte aligned (16-byte loads).
-template <typename T>
-__global__ void digits_kernel(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
-                              const int* __restrict__ e, int axis, int S, int vec,
-                              __nv_bfloat16* __restrict__ out, int64_t plane) {
+// store per digit plane.  AXIS 0: exponent per row, read from e[r].  AXIS 1:
+// exponent per column, formed here from the column maximum cmax[c] plus
+// `bias`; the threads of row 0 store it to e[c] and flag NaN/Inf.  vec: X
+// rows start 16-byte aligned (16-byte loads).
+template <typename T, int AXIS>
+__device__ void digits_part(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
+                            int* __restrict__ e, const typename Bits<T>::U* __restrict__ cmax,
+                            int bias, int* status, int S, int vec,
+                            __nv_bfloat16* __restrict__ out, int64_t plane, int64_t bid,
+                            int64_t nblk) {
     const int64_t gpr = ld / 8;
     const int64_t total = rows * gpr;
-    for (int64_t g = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; g < total;
-         g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    for (int64_t g = bid * blockDim.x + threadIdx.x; g < total; g += nblk * blockDim.x) {
         const int64_t r = g / gpr, c0 = (g - r * gpr) * 8;
         T x[8];
         load8(X, r, cols, c0, vec != 0, x);
@@ -352,7 +379,15 @@ __global__ void digits_kernel(const T* __restrict__ X, int64_t rows, int64_t col
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int64_t c = c0 + i;
-            const int ex = c < cols ? (axis == 0 ? e[r] : e[c]) : 0;
+            int ex = 0;
+            if (c < cols) {
+                if (AXIS == 0) {
+                    ex = e[r];
+                } else {
+                    ex = col_exp<T>(cmax[c], bias, r == 0 ? status : nullptr);
+                    if (r == 0) e[c] = ex;
+                }
+            }
             D[i].start(x[i], kBeta * S - ex, kBeta);
         }
         const int64_t o = r * ld + c0;
@@ -364,6 +399,23 @@ __global__ void digits_kernel(const T* __restrict__ X, int64_t rows, int64_t col
             *reinterpret_cast<uint4*>(out + s * plane + o) = make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
+}
+
+// Blocks [0, ga): digits of A (row exponents eA); the rest: digits of B
+// (column exponents from cmax, stored to eB).
+template <typename T>
+__global__ void __launch_bounds__(256)
+    digits_pair_kernel(const T* __restrict__ A, int64_t m, int64_t n, int64_t lda, int va,
+                       const int* __restrict__ eA, const T* __restrict__ B, int64_t p, int64_t ldb,
+                       int vb, int* __restrict__ eB, const typename Bits<T>::U* __restrict__ cmax,
+                       int bias, int* status, int S, __nv_bfloat16* __restrict__ a_out,
+                       int64_t a_plane, __nv_bfloat16* __restrict__ b_out, int64_t b_plane, int ga) {
+    if (static_cast<int>(blockIdx.x) < ga)
+        digits_part<T, 0>(A, m, n, lda, const_cast<int*>(eA), nullptr, 0, status, S, va, a_out,
+                          a_plane, blockIdx.x, ga);
+    else
+        digits_part<T, 1>(B, n, p, ldb, eB, cmax, bias, status, S, vb, b_out, b_plane,
+                          blockIdx.x - ga, gridDim.x - ga);
 }
 
 // E4M3 bit pattern of an integer v with |v| <= 16 (exact in E4M3: sign,
@@ -388,17 +440,15 @@ __device__ __forceinline__ void fill_e4m3_lut(uint8_t* lut, int beta) {
 // Integer digits (radix 2^beta) of a row-major matrix whose exponent is per
 // row, as E4M3 bytes in S planes of row pitch ld (a multiple of 16; zero
 // pad): 16 consecutive elements per thread, one 16-byte store per plane.
+// lut: the block's E4M3 code table (fill_e4m3_lut, synchronised).
 template <typename T>
-__global__ void digits_e4m3_rows_kernel(const T* __restrict__ X, int64_t rows, int64_t cols,
-                                        int64_t ld, const int* __restrict__ e, int S, int beta,
-                                        int vec, uint8_t* __restrict__ out, int64_t plane) {
-    __shared__ uint8_t lut[64];
-    fill_e4m3_lut(lut, beta);
-    __syncthreads();
+__device__ void digits_e4m3_rows_part(const T* __restrict__ X, int64_t rows, int64_t cols,
+                                      int64_t ld, const int* __restrict__ e, int S, int beta,
+                                      int vec, uint8_t* __restrict__ out, int64_t plane,
+                                      const uint8_t* lut, int64_t bid, int64_t nblk) {
     const int64_t gpr = ld / 16;
     const int64_t total = rows * gpr;
-    for (int64_t g = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; g < total;
-         g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    for (int64_t g = bid * blockDim.x + threadIdx.x; g < total; g += nblk * blockDim.x) {
         const int64_t r = g / gpr, c0 = (g - r * gpr) * 16;
         const int ex = e[r];
         DigitGen<T> D[16];
@@ -426,30 +476,35 @@ __global__ void digits_e4m3_rows_kernel(const T* __restrict__ X, int64_t rows, i
     }
 }
 
-// Integer digits of B (n x p row-major, exponent per column j) written
-// transposed as E4M3 bytes: plane s holds B_s^T, p rows of pitch ld (a
-// multiple of 16; zero pad past n), so that the slice GEMM reads B K-major.
+// Integer digits of B (n x p row-major, exponent per column j, formed from
+// the column maximum cmax[j] plus `bias`; the tiles at k = 0 store it to e[j]
+// and flag NaN/Inf) written transposed as E4M3 bytes: plane s holds B_s^T, p
+// rows of pitch ld (a multiple of 16; zero pad past n), so that the slice
+// GEMM reads B K-major.
 // One 64 (k) x 64 (j) tile per block pass, 256 threads; thread (j, q) holds
 // the 16 consecutive k of quarter q in column j.  Reads are coalesced along j;
 // each plane goes through a padded shared-memory tile (one 32-bit store per
 // 4 bytes) and is written as 16-byte row segments along k.
 constexpr int kTT = 64;
+// tile: kTT * (kTT / 4 + 1) words of shared memory; lut as above.  Every
+// thread of the block runs this part (it synchronises the block).
+constexpr int kTileWords = kTT * (kTT / 4 + 1);
 template <typename T>
-__global__ void __launch_bounds__(256)
-    digits_e4m3_cols_t_kernel(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
-                              const int* __restrict__ e, int S, int beta,
-                              uint8_t* __restrict__ out, int64_t plane) {
-    __shared__ uint32_t tile[kTT * (kTT / 4 + 1)];   // [j][k/4], 17 words per row
-    __shared__ uint8_t lut[64];
-    fill_e4m3_lut(lut, beta);
-    __syncthreads();
+__device__ void digits_e4m3_cols_t_part(const T* __restrict__ X, int64_t rows, int64_t cols,
+                                        int64_t ld, int* __restrict__ e,
+                                        const typename Bits<T>::U* __restrict__ cmax, int bias,
+                                        int* status, int S, int beta, uint8_t* __restrict__ out,
+                                        int64_t plane, uint32_t* tile, const uint8_t* lut,
+                                        int64_t bid, int64_t nblk) {
     const int t = threadIdx.x;
     const int64_t tk = (rows + kTT - 1) / kTT, tj = (cols + kTT - 1) / kTT;
-    for (int64_t b = blockIdx.x; b < tk * tj; b += gridDim.x) {
+    for (int64_t b = bid; b < tk * tj; b += nblk) {
         const int64_t k0 = (b / tj) * kTT, j0 = (b % tj) * kTT;
         const int jl = t % kTT, kq = t / kTT;          // column in tile, k quarter 0..3
         const int64_t j = j0 + jl;
-        const int ex = j < cols ? e[j] : 0;
+        const bool first = k0 == 0 && kq == 0;
+        const int ex = j < cols ? col_exp<T>(cmax[j], bias, first ? status : nullptr) : 0;
+        if (first && j < cols) e[j] = ex;
         DigitGen<T> D[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
@@ -480,6 +535,29 @@ __global__ void __launch_bounds__(256)
         }
         __syncthreads();
     }
+}
+
+// Blocks [0, ga): E4M3 digits of A by rows; the rest: transposed E4M3 digits
+// of B (column exponents from cmax, stored to eB).  The branch is uniform per
+// block, so the block-wide barriers of the B part are safe.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    digits_e4m3_pair_kernel(const T* __restrict__ A, int64_t m, int64_t n, int64_t lda, int va,
+                            const int* __restrict__ eA, const T* __restrict__ B, int64_t p,
+                            int64_t ldb, int* __restrict__ eB,
+                            const typename Bits<T>::U* __restrict__ cmax, int bias, int* status,
+                            int S, int beta, uint8_t* __restrict__ a_out, int64_t a_plane,
+                            uint8_t* __restrict__ b_out, int64_t b_plane, int ga) {
+    __shared__ uint32_t tile[kTileWords];   // [j][k/4], 17 words per row
+    __shared__ uint8_t lut[64];
+    fill_e4m3_lut(lut, beta);
+    __syncthreads();
+    if (static_cast<int>(blockIdx.x) < ga)
+        digits_e4m3_rows_part<T>(A, m, n, lda, eA, S, beta, va, a_out, a_plane, lut, blockIdx.x,
+                                 ga);
+    else
+        digits_e4m3_cols_t_part<T>(B, n, p, ldb, eB, cmax, bias, status, S, beta, b_out, b_plane,
+                                   tile, lut, blockIdx.x - ga, gridDim.x - ga);
 }
 
 // 1 when every row of a row-major matrix with `cols` columns starts on a
@@ -1119,31 +1197,35 @@ static void digit_prepasses(const SplitLayout& L, int64_t m, int64_t n, int64_t 
     using U = typename Bits<T>::U;
     constexpr int per16 = 16 / sizeof(T);
     const int S = L.S;
+    // launch 1: row exponents of A (one warp per row) beside the column
+    // maxima of B (256 columns x 256 rows per block)
     const int rows_per_block = 8;   // 8 warps of 32 threads
     const int64_t rblocks = std::min<int64_t>(ceil_div(m, rows_per_block), 16L * num_sms());
     const int64_t chunk = 256;
-    const dim3 cgrid(static_cast<unsigned>(ceil_div(p, 256)), static_cast<unsigned>(ceil_div(n, chunk)));
-    row_exp_kernel<T><<<static_cast<int>(rblocks), 256, 0, s>>>(A, m, n, headroom, eA, status);
-    col_max_kernel<T><<<cgrid, 256, 0, s>>>(B, n, p, chunk, static_cast<U*>(cmax));
-    col_exp_kernel<T><<<static_cast<int>(ceil_div(p, 256)), 256, 0, s>>>(
-        static_cast<const U*>(cmax), p, headroom, eB, status);
+    const int64_t gx = ceil_div(p, 256);
+    const int64_t eblocks = rblocks + gx * ceil_div(n, chunk);
+    exps_kernel<T><<<static_cast<unsigned>(eblocks), 256, 0, s>>>(
+        A, m, n, B, p, chunk, headroom, eA, static_cast<U*>(cmax), status,
+        static_cast<int>(rblocks), gx);
+    // launch 2: digit planes of A and of B (B's column exponents formed there)
     const int64_t a_plane = m * L.lda;
+    const U* cm = static_cast<const U*>(cmax);
     if (L.esize == 1) {
         const int64_t b_plane = p * L.ldb;
-        digits_e4m3_rows_kernel<T><<<grid_for(a_plane / 16, 256), 256, 0, s>>>(
-            A, m, n, L.lda, eA, S, beta, vec_rows(A, n, per16), a_sl, a_plane);
+        const int ga = grid_for(a_plane / 16, 256);
         const int64_t tiles = ceil_div(n, kTT) * ceil_div(p, kTT);
-        const int tgrid = static_cast<int>(std::min<int64_t>(tiles, 8L * num_sms()));
-        digits_e4m3_cols_t_kernel<T><<<tgrid, 256, 0, s>>>(B, n, p, L.ldb, eB, S, beta, b_sl,
-                                                           b_plane);
+        const int gb = static_cast<int>(std::min<int64_t>(tiles, 8L * num_sms()));
+        digits_e4m3_pair_kernel<T><<<ga + gb, 256, 0, s>>>(
+            A, m, n, L.lda, vec_rows(A, n, per16), eA, B, p, L.ldb, eB, cm, headroom, status, S,
+            beta, a_sl, a_plane, b_sl, b_plane, ga);
     } else {
         const int64_t b_plane = n * L.ldb;
-        auto* a16 = reinterpret_cast<__nv_bfloat16*>(a_sl);
-        auto* b16 = reinterpret_cast<__nv_bfloat16*>(b_sl);
-        digits_kernel<T><<<grid_for(a_plane / 8, 256), 256, 0, s>>>(
-            A, m, n, L.lda, eA, 0, S, vec_rows(A, n, per16), a16, a_plane);
-        digits_kernel<T><<<grid_for(b_plane / 8, 256), 256, 0, s>>>(
-            B, n, p, L.ldb, eB, 1, S, vec_rows(B, p, per16), b16, b_plane);
+        const int ga = grid_for(a_plane / 8, 256);
+        const int gb = grid_for(b_plane / 8, 256);
+        digits_pair_kernel<T><<<ga + gb, 256, 0, s>>>(
+            A, m, n, L.lda, vec_rows(A, n, per16), eA, B, p, L.ldb, vec_rows(B, p, per16), eB, cm,
+            headroom, status, S, reinterpret_cast<__nv_bfloat16*>(a_sl), a_plane,
+            reinterpret_cast<__nv_bfloat16*>(b_sl), b_plane, ga);
     }
 }
 
@@ -1183,11 +1265,11 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
     if (dt == MOA_F32_SPLIT) {
         auto* a16 = reinterpret_cast<__nv_bfloat16*>(a_sl);
         auto* b16 = reinterpret_cast<__nv_bfloat16*>(b_sl);
-        split3_kernel<<<grid_for(a_plane / 8, 256), 256, 0, s>>>(
-            static_cast<const float*>(A), m, n, L.lda, a16, a_plane, vec_rows(A, n, 4), status);
-        split3_kernel<<<grid_for(b_plane / 8, 256), 256, 0, s>>>(
-            static_cast<const float*>(B), n, p, L.ldb, b16, b_plane, vec_rows(B, p, 4), status);
-        kernels += 2;
+        const int ga = grid_for(a_plane / 8, 256);
+        split3_pair_kernel<<<ga + grid_for(b_plane / 8, 256), 256, 0, s>>>(
+            static_cast<const float*>(A), m, n, L.lda, a16, a_plane, vec_rows(A, n, 4),
+            static_cast<const float*>(B), p, L.ldb, b16, b_plane, vec_rows(B, p, 4), status, ga);
+        kernels += 1;
         a.f64 = 0;
         a.levels = 1;
         a.beta = 0;
@@ -1202,7 +1284,8 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
         void* cmax = base + L.cmax_off;
         const int beta = e4m3 ? kBetaE4M3 : kBeta;
         const int h = e4m3 ? kHeadroomE4M3 : 0;
-        if (ceil_div(n, 256) > 65535) return fail(MOA_ERR_ARG, "n too large for the column-max grid");
+        if (ceil_div(n, 256) * ceil_div(p, 256) > (1L << 30))
+            return fail(MOA_ERR_ARG, "n x p too large for the column-max grid");
         cudaError_t e = cudaMemsetAsync(cmax, 0, static_cast<size_t>(p) * 8, s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(colmax)");
         if (dt == MOA_F64_SPLIT_F64IN || dt == MOA_F64_SPLIT_F64IN_E4M3)
@@ -1213,7 +1296,7 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
             digit_prepasses<float>(L, m, n, p, static_cast<const float*>(A),
                                    static_cast<const float*>(B), beta, h, eA, eB, cmax, a_sl, b_sl,
                                    status, s);
-        kernels += 6;
+        kernels += 3;   // the column-max clear, the exponent pass and the digit pass
         a.f64 = 1;
         a.levels = S;
         a.beta = beta;
