@@ -617,10 +617,16 @@ struct SplitCfg {
     static constexpr int kBSlice = FMT == kFmtE4M3 ? BN * 128 : (BN / 64) * kBChunk;
     static constexpr int kBBytes = kKB ? 3 * kBSlice : kBSlice;
     static constexpr int kStageBytes = kAStage + kBBytes;
-    static constexpr int kStages = kKB ? (BN == 256 ? 3 : 4) : (BN == 256 ? 4 : (BN == 192 ? 5 : 6));
-    static constexpr int kSmem = 1024 + kStages * kStageBytes + 256;
     static constexpr int kColsPerWarp = MODE == kModeF64Tmem ? 128 : 64;
     static constexpr int kEpiWarps = 4 * (BN / kColsPerWarp);
+    // FP64 modes: a 4 KB staging tile per epilogue warp for the folds
+    static constexpr int kEpiStage = MODE == kModeF32 ? 0 : kEpiWarps * 4096;
+    static constexpr int kStagesWant =
+        kKB ? (BN == 256 ? 3 : 4) : (BN == 256 ? 4 : (BN == 192 ? 5 : 6));
+    static constexpr int kStagesFit = (227 * 1024 - 1024 - 256 - kEpiStage) / kStageBytes;
+    static constexpr int kStages = kStagesWant < kStagesFit ? kStagesWant : kStagesFit;
+    static constexpr int kSmem = 1024 + kStages * kStageBytes + kEpiStage + 256;
+    static_assert(kStages >= 2 && kSmem <= 227 * 1024, "split kernel shared memory");
     static constexpr int kThreads = 64 + 32 * kEpiWarps;
     static constexpr int kNBuf = MODE == kModeF64Tmem ? 1 : 2;
     static constexpr int kTmemCols = (MODE == kModeF64Tmem || BN > 128) ? 512 : 256;
@@ -675,6 +681,100 @@ __device__ __forceinline__ void pair_at(const SplitArgs& a, int L, int q, int& s
     }
 }
 
+// v * 2^sh for sh >= 0; else v / 2^-sh rounded to nearest (ties up): the
+// fixed-point alignment of a level sum to the int64 total.
+__device__ __forceinline__ long long align_level(int v, int sh) {
+    const long long x = v;
+    return sh >= 0 ? x * (1ll << sh) : (x + (1ll << (-sh - 1))) >> (-sh);
+}
+
+// Folds a 32 x 32 block of exact level sums into the int64 fixed-point
+// totals T kept in C (FP64 modes): T += align_level(R, sh) (T = 0 before the
+// tile's first fold, !t_init); with `last` the sum is converted once to FP64,
+// scaled by 2^(eA_i + eB_j + ebias) and stored over T.  Lane l holds row l of
+// the block in v (32 int32 values).  The block goes through this warp's 4 KB
+// staging tile (16-byte chunks XOR-swizzled by row) so that each warp access
+// to C covers 2 rows x 256 contiguous bytes (16-byte pairs) instead of one
+// 8-byte element in each of 32 rows.
+// row0, col0: the block's origin in C (pitch ld elements); rows_left /
+// cols_left: its rows and columns inside C; er: the lane's row exponent eA
+// (lane = row); vec: C is 16-byte aligned and ld even.
+__device__ __forceinline__ void fold_block32(uint8_t* stage, const uint32_t (&v)[32],
+                                             long long* C64, int64_t ld, int64_t row0,
+                                             int rows_left, int64_t col0, int64_t cols_left,
+                                             int sh, bool t_init, bool last, int er,
+                                             const int* __restrict__ eB, int ebias, bool vec) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        *reinterpret_cast<uint4*>(stage + lane * 128 + ((c ^ (lane & 7)) << 4)) =
+            make_uint4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+    __syncwarp();
+    // lane -> (row parity, column pair): columns 2 c2, 2 c2 + 1 of rows
+    // 2 i + half, i = 0..15
+    const int half = lane >> 4, c2 = lane & 15;
+    const int64_t col = col0 + 2 * c2;
+    const int64_t cl = cols_left - 2 * c2;
+    int eb0 = 0, eb1 = 0;
+    if (last) {
+        if (cl > 0) eb0 = eB[col];
+        if (cl > 1) eb1 = eB[col + 1];
+    }
+    const bool pair = vec && cl >= 2;
+    constexpr int kBatch = 4;   // row pairs whose totals are loaded together
+#pragma unroll
+    for (int i0 = 0; i0 < 16; i0 += kBatch) {
+        long long t0[kBatch], t1[kBatch];
+#pragma unroll
+        for (int i = 0; i < kBatch; ++i) {
+            const int rr = 2 * (i0 + i) + half;
+            t0[i] = 0;
+            t1[i] = 0;
+            if (t_init && rr < rows_left && cl > 0) {
+                const long long* src = C64 + (row0 + rr) * ld + col;
+                if (pair) {
+                    const longlong2 x = *reinterpret_cast<const longlong2*>(src);
+                    t0[i] = x.x;
+                    t1[i] = x.y;
+                } else {
+                    t0[i] = src[0];
+                    if (cl > 1) t1[i] = src[1];
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kBatch; ++i) {
+            const int rr = 2 * (i0 + i) + half;
+            const int er_r = __shfl_sync(0xffffffffu, er, rr);
+            if (rr >= rows_left || cl <= 0) continue;
+            const uint2 sv = *reinterpret_cast<const uint2*>(
+                stage + rr * 128 + (((c2 >> 1) ^ (rr & 7)) << 4) + (c2 & 1) * 8);
+            const long long tot0 = t0[i] + align_level(static_cast<int>(sv.x), sh);
+            const long long tot1 = t1[i] + align_level(static_cast<int>(sv.y), sh);
+            long long* dst = C64 + (row0 + rr) * ld + col;
+            if (last) {
+                const double d0 = ldexp(__ll2double_rn(tot0), er_r + eb0 + ebias);
+                const double d1 = ldexp(__ll2double_rn(tot1), er_r + eb1 + ebias);
+                double* dd = reinterpret_cast<double*>(dst);
+                if (pair) {
+                    *reinterpret_cast<double2*>(dd) = make_double2(d0, d1);
+                } else {
+                    dd[0] = d0;
+                    if (cl > 1) dd[1] = d1;
+                }
+            } else {
+                if (pair) {
+                    *reinterpret_cast<longlong2*>(dst) = make_longlong2(tot0, tot1);
+                } else {
+                    dst[0] = tot0;
+                    if (cl > 1) dst[1] = tot1;
+                }
+            }
+        }
+    }
+    __syncwarp();   // the staging tile is free for the next block
+}
+
 template <int BN, int MODE, int FMT>
 __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
     split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -689,7 +789,8 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
                                                ~static_cast<uintptr_t>(1023));
     uint8_t* sA = smem;
     uint8_t* sB = smem + kStages * Cfg::kAStage;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kStages * Cfg::kBBytes);
+    uint8_t* epi = sB + kStages * Cfg::kBBytes;   // FP64 fold staging, 4 KB per epilogue warp
+    uint64_t* bars = reinterpret_cast<uint64_t*>(epi + Cfg::kEpiStage);
     uint64_t* full = bars;
     uint64_t* empty = bars + kStages;
     uint64_t* tfull = bars + 2 * kStages;
@@ -915,6 +1016,7 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
         const int q = warp & 3;
         const int h = (warp - 2) >> 2;
         const uint32_t lane_base = static_cast<uint32_t>(q * 32) << 16;
+        uint8_t* epi_stage = epi + (F64 ? (warp - 2) * 4096 : 0);
         long cnt = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
@@ -925,7 +1027,6 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
             const bool row_ok = row < args.m;
             // FP64 modes keep the tile's int64 fixed-point total T in C itself
             // (same 8 bytes per element as the final FP64 value).
-            long long* trow = reinterpret_cast<long long*>(args.C) + row * args.p;
             const int er = (F64 && row_ok) ? args.eA[row] : 0;
             bool t_init = false;
             // Register running sums (kModeF32, kModeF64Reg): FP32 bits or the
@@ -998,48 +1099,24 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
                         // 2^(eA_i + eB_j - beta(S+1) + drop).
                         const int sh = args.beta * (args.S - 1 - L) - args.drop;
                         const bool last = level_end && L == args.levels - 1;
+                        const int64_t row0 = static_cast<int64_t>(tm) * kBM + q * 32;
+                        const int64_t rl = args.m - row0;
+                        const int rows_left = rl < 0 ? 0 : (rl > 32 ? 32 : static_cast<int>(rl));
 #pragma unroll
-                        for (int b = 0; b < kCols / 16; ++b) {
-                            uint32_t rv[16];
+                        for (int b = 0; b < kCols / 32; ++b) {
+                            uint32_t rv[32];
                             if constexpr (MODE == kModeF64Tmem) {
-                                tmem_ld16(r_base + 16u * b, rv);
+                                tmem_ld32(r_base + 32u * b, rv);
                                 tmem_ld_wait();
                             } else {
 #pragma unroll
-                                for (int i = 0; i < 16; ++i) rv[i] = 0u;
+                                for (int i = 0; i < 32; ++i) rv[i] = acc[(b * 32 + i) % kRegs];
                             }
-                            if (row_ok) {
-                                // 16 independent loads of T, so their latency overlaps
-                                long long told[16];
-#pragma unroll
-                                for (int i = 0; i < 16; ++i) {
-                                    const int64_t col = col_base + b * 16 + i;
-                                    told[i] = (t_init && col < args.p) ? trow[col] : 0ll;
-                                }
-#pragma unroll
-                                for (int i = 0; i < 16; ++i) {
-                                    const int64_t col = col_base + b * 16 + i;
-                                    if (col >= args.p) continue;
-                                    long long v;
-                                    if constexpr (MODE == kModeF64Tmem)
-                                        v = static_cast<int>(rv[i]);
-                                    else
-                                        v = static_cast<int>(acc[(b * 16 + i) % kRegs]);
-                                    if (sh >= 0)
-                                        v = v * (1ll << sh);
-                                    else
-                                        v = (v + (1ll << (-sh - 1))) >> (-sh);
-                                    const long long tot = told[i] + v;
-                                    if (last) {
-                                        const int ex =
-                                            er + args.eB[col] - args.beta * (args.S + 1) + args.drop;
-                                        reinterpret_cast<double*>(trow)[col] =
-                                            ldexp(__ll2double_rn(tot), ex);
-                                    } else {
-                                        trow[col] = tot;
-                                    }
-                                }
-                            }
+                            const int64_t c0 = col_base + b * 32;
+                            fold_block32(epi_stage, rv, reinterpret_cast<long long*>(args.C),
+                                         args.p, row0, rows_left, c0, args.p - c0, sh, t_init,
+                                         last, er, args.eB,
+                                         args.drop - args.beta * (args.S + 1), args.vec_ok != 0);
                         }
                         t_init = true;
                         r_valid = false;
