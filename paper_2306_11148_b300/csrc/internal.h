@@ -74,6 +74,10 @@ int tile_override();
 // Tile rows per raster group of the persistent kernels (the L2-level lift):
 // MOA_RASTER_GROUP, default 16.
 int raster_group();
+// The same for the slice GEMM, whose tiles each sweep the K range once per
+// slice product: MOA_RASTER_GROUP, default 16, or 8 once n > 12288 (measured
+// on the B300 at n = 16384: 4-7 % faster than 16; 16 best at n = 8192).
+int split_raster_group(int64_t n);
 int tuned_block_n(moa_dtype dt, int64_t m, int64_t n, int64_t p);
 
 // SIMT kernels (no tensor cores).

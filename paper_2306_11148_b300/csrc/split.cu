@@ -1333,7 +1333,7 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
     a.tiles_m = static_cast<int>(ceil_div(m, kBM));
     a.tiles_n = static_cast<int>(ceil_div(p, bn));
     a.num_kb = static_cast<int>(ceil_div(n, bke));
-    a.group_m = raster_group();
+    a.group_m = split_raster_group(n);
     a.S = S;
     a.wait_limit_ns = wait_limit_ns();
     a.status = status;

@@ -53,14 +53,25 @@ int load_locked(const char* path) {
 
 int tile_override() { return t_override; }
 
-int raster_group() {
-    static int g = 0;
-    if (g == 0) {
+// MOA_RASTER_GROUP if set (1..1024), else 0.
+static int raster_env() {
+    static int g = -1;
+    if (g < 0) {
         const char* env = std::getenv("MOA_RASTER_GROUP");
-        const long v = env ? std::strtol(env, nullptr, 10) : 16;
-        g = static_cast<int>(v >= 1 && v <= 1024 ? v : 16);
+        const long v = env ? std::strtol(env, nullptr, 10) : 0;
+        g = static_cast<int>(v >= 1 && v <= 1024 ? v : 0);
     }
     return g;
+}
+
+int raster_group() {
+    const int g = raster_env();
+    return g ? g : 16;
+}
+
+int split_raster_group(int64_t n) {
+    const int g = raster_env();
+    return g ? g : (n > 12288 ? 8 : 16);
 }
 
 int tuned_block_n(moa_dtype dt, int64_t m, int64_t n, int64_t p) {
