@@ -619,8 +619,9 @@ struct SplitCfg {
     static constexpr int kStageBytes = kAStage + kBBytes;
     static constexpr int kColsPerWarp = MODE == kModeF64Tmem ? 128 : 64;
     static constexpr int kEpiWarps = 4 * (BN / kColsPerWarp);
-    // FP64 modes: a 4 KB staging tile per epilogue warp for the folds
-    static constexpr int kEpiStage = MODE == kModeF32 ? 0 : kEpiWarps * 4096;
+    // FP64 modes: a 2 KB staging tile per epilogue warp for the folds
+    static constexpr int kEpiStageWarp = 2048;
+    static constexpr int kEpiStage = MODE == kModeF32 ? 0 : kEpiWarps * kEpiStageWarp;
     static constexpr int kStagesWant =
         kKB ? (BN == 256 ? 3 : 4) : (BN == 256 ? 4 : (BN == 192 ? 5 : 6));
     static constexpr int kStagesFit = (227 * 1024 - 1024 - 256 - kEpiStage) / kStageBytes;
@@ -688,31 +689,31 @@ __device__ __forceinline__ long long align_level(int v, int sh) {
     return sh >= 0 ? x * (1ll << sh) : (x + (1ll << (-sh - 1))) >> (-sh);
 }
 
-// Folds a 32 x 32 block of exact level sums into the int64 fixed-point
+// Folds a 32 x 16 block of exact level sums into the int64 fixed-point
 // totals T kept in C (FP64 modes): T += align_level(R, sh) (T = 0 before the
 // tile's first fold, !t_init); with `last` the sum is converted once to FP64,
 // scaled by 2^(eA_i + eB_j + ebias) and stored over T.  Lane l holds row l of
-// the block in v (32 int32 values).  The block goes through this warp's 4 KB
+// the block in v (16 int32 values).  The block goes through this warp's 2 KB
 // staging tile (16-byte chunks XOR-swizzled by row) so that each warp access
-// to C covers 2 rows x 256 contiguous bytes (16-byte pairs) instead of one
-// 8-byte element in each of 32 rows.
-// row0, col0: the block's origin in C (pitch ld elements); rows_left /
-// cols_left: its rows and columns inside C; er: the lane's row exponent eA
-// (lane = row); vec: C is 16-byte aligned and ld even.
-__device__ __forceinline__ void fold_block32(uint8_t* stage, const uint32_t (&v)[32],
+// to C moves 16-byte pairs covering 4 rows x 128 contiguous bytes, instead
+// of one 8-byte element in each of 32 rows.  row0, col0: the block's origin
+// in C (pitch ld elements); rows_left / cols_left: its rows and columns
+// inside C; er: the lane's row exponent eA (lane = row); vec: C is 16-byte
+// aligned and ld even.
+__device__ __forceinline__ void fold_block16(uint8_t* stage, const uint32_t (&v)[16],
                                              long long* C64, int64_t ld, int64_t row0,
                                              int rows_left, int64_t col0, int64_t cols_left,
                                              int sh, bool t_init, bool last, int er,
                                              const int* __restrict__ eB, int ebias, bool vec) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int c = 0; c < 8; ++c)
-        *reinterpret_cast<uint4*>(stage + lane * 128 + ((c ^ (lane & 7)) << 4)) =
+    for (int c = 0; c < 4; ++c)
+        *reinterpret_cast<uint4*>(stage + lane * 64 + ((c ^ (lane & 3)) << 4)) =
             make_uint4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
     __syncwarp();
-    // lane -> (row parity, column pair): columns 2 c2, 2 c2 + 1 of rows
-    // 2 i + half, i = 0..15
-    const int half = lane >> 4, c2 = lane & 15;
+    // lane -> (row in a group of 4, column pair): columns 2 c2, 2 c2 + 1 of
+    // rows 4 i + r4, i = 0..7
+    const int r4 = lane >> 3, c2 = lane & 7;
     const int64_t col = col0 + 2 * c2;
     const int64_t cl = cols_left - 2 * c2;
     int eb0 = 0, eb1 = 0;
@@ -721,13 +722,13 @@ __device__ __forceinline__ void fold_block32(uint8_t* stage, const uint32_t (&v)
         if (cl > 1) eb1 = eB[col + 1];
     }
     const bool pair = vec && cl >= 2;
-    constexpr int kBatch = 4;   // row pairs whose totals are loaded together
+    constexpr int kBatch = 4;   // row groups whose totals are loaded together
 #pragma unroll
-    for (int i0 = 0; i0 < 16; i0 += kBatch) {
+    for (int i0 = 0; i0 < 8; i0 += kBatch) {
         long long t0[kBatch], t1[kBatch];
 #pragma unroll
         for (int i = 0; i < kBatch; ++i) {
-            const int rr = 2 * (i0 + i) + half;
+            const int rr = 4 * (i0 + i) + r4;
             t0[i] = 0;
             t1[i] = 0;
             if (t_init && rr < rows_left && cl > 0) {
@@ -744,11 +745,11 @@ __device__ __forceinline__ void fold_block32(uint8_t* stage, const uint32_t (&v)
         }
 #pragma unroll
         for (int i = 0; i < kBatch; ++i) {
-            const int rr = 2 * (i0 + i) + half;
+            const int rr = 4 * (i0 + i) + r4;
             const int er_r = __shfl_sync(0xffffffffu, er, rr);
             if (rr >= rows_left || cl <= 0) continue;
             const uint2 sv = *reinterpret_cast<const uint2*>(
-                stage + rr * 128 + (((c2 >> 1) ^ (rr & 7)) << 4) + (c2 & 1) * 8);
+                stage + rr * 64 + (((c2 >> 1) ^ (rr & 3)) << 4) + (c2 & 1) * 8);
             const long long tot0 = t0[i] + align_level(static_cast<int>(sv.x), sh);
             const long long tot1 = t1[i] + align_level(static_cast<int>(sv.y), sh);
             long long* dst = C64 + (row0 + rr) * ld + col;
@@ -1016,7 +1017,7 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
         const int q = warp & 3;
         const int h = (warp - 2) >> 2;
         const uint32_t lane_base = static_cast<uint32_t>(q * 32) << 16;
-        uint8_t* epi_stage = epi + (F64 ? (warp - 2) * 4096 : 0);
+        uint8_t* epi_stage = epi + (F64 ? (warp - 2) * Cfg::kEpiStageWarp : 0);
         long cnt = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
@@ -1103,17 +1104,17 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
                         const int64_t rl = args.m - row0;
                         const int rows_left = rl < 0 ? 0 : (rl > 32 ? 32 : static_cast<int>(rl));
 #pragma unroll
-                        for (int b = 0; b < kCols / 32; ++b) {
-                            uint32_t rv[32];
+                        for (int b = 0; b < kCols / 16; ++b) {
+                            uint32_t rv[16];
                             if constexpr (MODE == kModeF64Tmem) {
-                                tmem_ld32(r_base + 32u * b, rv);
+                                tmem_ld16(r_base + 16u * b, rv);
                                 tmem_ld_wait();
                             } else {
 #pragma unroll
-                                for (int i = 0; i < 32; ++i) rv[i] = acc[(b * 32 + i) % kRegs];
+                                for (int i = 0; i < 16; ++i) rv[i] = acc[(b * 16 + i) % kRegs];
                             }
-                            const int64_t c0 = col_base + b * 32;
-                            fold_block32(epi_stage, rv, reinterpret_cast<long long*>(args.C),
+                            const int64_t c0 = col_base + b * 16;
+                            fold_block16(epi_stage, rv, reinterpret_cast<long long*>(args.C),
                                          args.p, row0, rows_left, c0, args.p - c0, sh, t_init,
                                          last, er, args.eB,
                                          args.drop - args.beta * (args.S + 1), args.vec_ok != 0);
