@@ -11,13 +11,19 @@
 // forms a batch of all requests it can admit; the BF16 requests of a batch go
 // into one grouped persistent launch, the others are launched one by one;
 // launches rotate over `n_streams` CUDA streams so that their work overlaps on
-// the device.  A host callback on the stream timestamps each completion and
-// hands it back to the scheduler, which frees its arena block and publishes
-// the completion to moa_serve_poll.  Latency = completion - submission.
+// the device.  Each request's last stream operation records a CUDA event; the
+// scheduler polls the oldest unfinished event of every stream (streams run in
+// order), timestamps each completion when it sees it, frees the request's
+// arena block and publishes the completion to moa_serve_poll.  Latency =
+// completion - submission.  While requests are queued or in flight, and for
+// a short grace period after the last activity, the scheduler thread polls
+// without sleeping (one host core busy) so that neither admission nor
+// completion waits for a thread wake-up; an idle server sleeps on a
+// condition variable that moa_serve_submit signals.
 // Every request also gets its own device status slot (after its workspace in
 // the arena): its kernels record a pipeline timeout or a non-finite split
 // input there instead of in the per-device word, the slot is copied back
-// before the completion callback, and the request completes with
+// before the completion event, and the request completes with
 // MOA_ERR_TIMEOUT / MOA_ERR_NONFINITE accordingly.
 //
 // Each GEMM is Eq. (eq:dnf) of Sec. 2, computed by the same kernels as a
@@ -134,7 +140,9 @@ struct moa_server {
     std::deque<moa::Request> queue;               // submitted, not admitted
     std::map<uint64_t, moa::Request> inflight;    // admitted, on the GPU
     std::deque<moa_completion> done;              // completed, not yet polled
-    std::vector<uint64_t> finished;               // tickets finished on the device
+    std::vector<uint64_t> finished;               // tickets that failed to launch
+    std::vector<std::deque<uint64_t>> launched;   // per stream: tickets in launch order
+    std::vector<cudaEvent_t> done_ev;             // per status index: completion event
     std::vector<double> latencies_ms;
     uint64_t next_ticket = 1;
     uint64_t n_submitted = 0, n_admitted = 0, n_completed = 0, n_rejected = 0, n_failed = 0,
@@ -149,24 +157,6 @@ struct moa_server {
 
 namespace moa {
 namespace {
-
-struct CallbackCtx {
-    moa_server* srv;
-    uint64_t ticket;
-};
-
-// Host callback: runs on a CUDA driver thread once the stream reaches it.
-void CUDART_CB on_done(void* p) {
-    CallbackCtx* c = static_cast<CallbackCtx*>(p);
-    {
-        std::lock_guard<std::mutex> lk(c->srv->mu);
-        auto it = c->srv->inflight.find(c->ticket);
-        if (it != c->srv->inflight.end()) it->second.t_done = now_s();
-        c->srv->finished.push_back(c->ticket);
-    }
-    c->srv->cv.notify_all();
-    delete c;
-}
 
 moa_completion completion_of(const Request& r, int status, double t_done) {
     moa_completion c{};
@@ -201,11 +191,35 @@ int take_stream(moa_server* s) {
     return si;
 }
 
+// Moves the tickets whose completion events have fired (the oldest first on
+// every stream) to s->finished, with their completion times.
+void collect_completions(moa_server* s) {
+    for (auto& fifo : s->launched) {
+        while (!fifo.empty()) {
+            auto it = s->inflight.find(fifo.front());
+            if (it == s->inflight.end()) {
+                fifo.pop_front();
+                continue;
+            }
+            const cudaError_t e = cudaEventQuery(s->done_ev[it->second.hidx]);
+            if (e == cudaErrorNotReady) break;
+            if (e != cudaSuccess && it->second.status == MOA_OK) it->second.status = MOA_ERR_CUDA;
+            it->second.t_done = now_s();
+            s->finished.push_back(fifo.front());
+            fifo.pop_front();
+        }
+    }
+}
+
 void scheduler(moa_server* s) {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lk(s->mu);
+    double last_activity = now_s();
+    constexpr double kSpinGrace = 2e-3;   // seconds of polling after the last activity
     while (true) {
         // 1. retire requests the device has finished
+        collect_completions(s);
+        if (!s->finished.empty()) last_activity = now_s();
         for (uint64_t t : s->finished) {
             auto it = s->inflight.find(t);
             if (it == s->inflight.end()) continue;
@@ -250,9 +264,19 @@ void scheduler(moa_server* s) {
             s->queue.pop_front();
         }
         if (batch.empty()) {
-            s->cv.wait_for(lk, std::chrono::microseconds(200));
+            if (!s->queue.empty() || !s->inflight.empty() ||
+                now_s() - last_activity < kSpinGrace) {
+                // poll: let submitters take the lock, then look again
+                lk.unlock();
+                std::this_thread::yield();
+                lk.lock();
+            } else {
+                s->cv.wait_for(lk, std::chrono::microseconds(200));
+                last_activity = now_s();   // a wake-up (submit or timeout) starts a new grace
+            }
             continue;
         }
+        last_activity = now_s();
         ++s->n_batches;
         s->n_admitted += batch.size();
 
@@ -312,14 +336,22 @@ void scheduler(moa_server* s) {
                 cudaMemcpyAsync(s->host_status + r.hidx, slot, sizeof(int), cudaMemcpyDeviceToHost,
                                 rs);
             }
-            auto* ctx = new CallbackCtx{s, r.ticket};
-            if (cudaLaunchHostFunc(s->streams[r.stream], on_done, ctx) != cudaSuccess) {
-                delete ctx;
+            if (cudaEventRecord(s->done_ev[r.hidx], s->streams[r.stream]) != cudaSuccess) {
                 rcs[i] = MOA_ERR_CUDA;
                 failed_now.push_back(r.ticket);
             }
         }
         lk.lock();
+        {
+            size_t f = 0;
+            for (const Request& r : batch) {
+                if (f < failed_now.size() && failed_now[f] == r.ticket) {
+                    ++f;
+                    continue;
+                }
+                s->launched[r.stream].push_back(r.ticket);
+            }
+        }
         for (size_t i = 0; i < batch.size(); ++i) {
             auto it = s->inflight.find(batch[i].ticket);
             if (it != s->inflight.end() && rcs[i] != MOA_OK) it->second.status = rcs[i];
@@ -367,6 +399,19 @@ int moa_serve_create(const moa_serve_config* cfg, moa_server** out) {
         return moa::cuda_fail(e, "cudaHostAlloc(status ring)");
     }
     for (int i = cfg->max_inflight - 1; i >= 0; --i) s->free_hidx.push_back(i);
+    s->done_ev.assign(static_cast<size_t>(cfg->max_inflight), nullptr);
+    for (cudaEvent_t& ev : s->done_ev) {
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            for (cudaEvent_t x : s->done_ev)
+                if (x) cudaEventDestroy(x);
+            for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
+            cudaFreeHost(s->host_status);
+            delete s;
+            return moa::cuda_fail(e, "cudaEventCreateWithFlags");
+        }
+    }
+    s->launched.resize(s->streams.size());
     s->sched = std::thread(moa::scheduler, s);
     *out = s;
     return MOA_OK;
@@ -460,6 +505,8 @@ int moa_serve_destroy(moa_server* s) {
         if (cudaStreamSynchronize(st) != cudaSuccess) rc = MOA_ERR_CUDA;
         cudaStreamDestroy(st);
     }
+    for (cudaEvent_t ev : s->done_ev)
+        if (ev) cudaEventDestroy(ev);
     if (s->host_status) cudaFreeHost(s->host_status);
     delete s;
     return rc;
