@@ -243,9 +243,13 @@ typedef struct {
     double p50_ms, p99_ms, max_ms, mean_ms;   /* submit -> done, completed requests */
 } moa_serve_counters;
 
-/* Starts a server on the current device: creates its streams and a scheduler
- * thread.  The arena (256-byte aligned) stays owned by the caller and must
- * outlive the server.  MOA_ERR_ARG / MOA_ERR_ALIGN on a bad config. */
+/* Starts a server on the current device: creates its streams, one completion
+ * event per in-flight slot and a scheduler thread.  The scheduler polls the
+ * completion events without sleeping while requests are queued or in flight
+ * (and for 2 ms after the last activity), so a busy server keeps one host
+ * core busy; an idle one sleeps until moa_serve_submit wakes it.  The arena
+ * (256-byte aligned) stays owned by the caller and must outlive the server.
+ * MOA_ERR_ARG / MOA_ERR_ALIGN on a bad config. */
 int moa_serve_create(const moa_serve_config* cfg, moa_server** out);
 
 /* Queues C := A . B (any moa_dtype; operands and C are device memory that
