@@ -248,8 +248,11 @@ typedef struct {
  * completion events without sleeping while requests are queued or in flight
  * (and for 2 ms after the last activity), so a busy server keeps one host
  * core busy; an idle one sleeps until moa_serve_submit wakes it.  The arena
- * (256-byte aligned) stays owned by the caller and must outlive the server.
- * MOA_ERR_ARG / MOA_ERR_ALIGN on a bad config. */
+ * (256-byte aligned) stays owned by the caller and must outlive the server;
+ * its first 256-byte granules (4 bytes per in-flight slot) hold the slots'
+ * device status words, the rest is the request workspace pool.
+ * MOA_ERR_ARG / MOA_ERR_ALIGN on a bad config, MOA_ERR_BUDGET if the arena
+ * cannot hold the status words. */
 int moa_serve_create(const moa_serve_config* cfg, moa_server** out);
 
 /* Queues C := A . B (any moa_dtype; operands and C are device memory that

@@ -20,11 +20,12 @@
 // without sleeping (one host core busy) so that neither admission nor
 // completion waits for a thread wake-up; an idle server sleeps on a
 // condition variable that moa_serve_submit signals.
-// Every request also gets its own device status slot (after its workspace in
-// the arena): its kernels record a pipeline timeout or a non-finite split
-// input there instead of in the per-device word, the slot is copied back
-// before the completion event, and the request completes with
-// MOA_ERR_TIMEOUT / MOA_ERR_NONFINITE accordingly.
+// Every in-flight slot also has its own device status word (at the start of
+// the arena): a request's kernels record a pipeline timeout or a non-finite
+// split input there instead of in the per-device word; a one-thread kernel
+// after them stores the word into mapped pinned host memory and clears it for
+// the slot's next request, so the request completes with MOA_ERR_TIMEOUT /
+// MOA_ERR_NONFINITE accordingly without a copy-engine transfer.
 //
 // Each GEMM is Eq. (eq:dnf) of Sec. 2, computed by the same kernels as a
 // moa_gemm_ex call with the same arguments, so a result does not depend on
@@ -149,7 +150,9 @@ struct moa_server {
              n_batches = 0;
     int inflight_peak = 0;
     int next_stream = 0;
-    int* host_status = nullptr;        // pinned, one int per in-flight slot
+    int* host_status = nullptr;        // mapped pinned host memory, one int per in-flight slot
+    int* host_status_dev = nullptr;    // the same memory as the device sees it
+    int* dev_status = nullptr;         // device status words (arena start), one per slot
     std::vector<int> free_hidx;
     bool stop = false;
     std::thread sched;
@@ -172,10 +175,20 @@ moa_completion completion_of(const Request& r, int status, double t_done) {
     return c;
 }
 
-constexpr size_t kSlot = 256;
-size_t block_bytes(size_t ws) { return Arena::granule(ws) + kSlot; }
-void* slot_ptr(moa_server* s, size_t off, size_t ws) {
-    return static_cast<uint8_t*>(s->arena.ptr(off)) + Arena::granule(ws);
+size_t block_bytes(size_t ws) { return Arena::granule(ws); }
+
+// Publishes a request's device status word to the host (mapped pinned
+// memory); `reset` clears the word for the slot's next request.
+__global__ void publish_status_kernel(int* dev_word, int* host_word, int reset) {
+    const int v = *reinterpret_cast<volatile int*>(dev_word);
+    *reinterpret_cast<volatile int*>(host_word) = v;
+    if (reset) *dev_word = kDevOk;
+}
+
+int publish_status(moa_server* s, int dev_slot, int host_slot, bool reset, cudaStream_t st) {
+    publish_status_kernel<<<1, 1, 0, st>>>(s->dev_status + dev_slot,
+                                           s->host_status_dev + host_slot, reset ? 1 : 0);
+    return cudaGetLastError() == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
 }
 
 int status_of(int launch_rc, int dev) {
@@ -226,7 +239,9 @@ void scheduler(moa_server* s) {
             Request& r = it->second;
             s->arena.release(r.ws_off, block_bytes(r.ws_bytes));
             if (r.extra_bytes) s->arena.release(r.extra_off, block_bytes(r.extra_bytes));
-            r.status = status_of(r.status, r.hidx >= 0 ? s->host_status[r.hidx] : kDevOk);
+            r.status = status_of(
+                r.status,
+                r.hidx >= 0 ? *reinterpret_cast<volatile int*>(s->host_status + r.hidx) : kDevOk);
             if (r.hidx >= 0) s->free_hidx.push_back(r.hidx);
             const double td = r.t_done > 0 ? r.t_done : now_s();
             s->done.push_back(completion_of(r, r.status, td));
@@ -309,16 +324,15 @@ void scheduler(moa_server* s) {
         std::vector<int> rcs(batch.size(), MOA_OK);
         if (grouped) {
             cudaStream_t gs = s->streams[gstream];
-            int* slot = static_cast<int*>(slot_ptr(s, toff, tbytes));
-            cudaMemsetAsync(slot, 0, sizeof(int), gs);
-            set_status_override(slot);
+            const int lead = batch[bf_idx[0]].hidx;   // the batch shares the lead's status word
+            set_status_override(s->dev_status + lead);
             const int rc = grouped_launch(static_cast<int>(bf.size()), bf.data(), s->arena.ptr(toff),
                                           tbytes, gs, false);
             set_status_override(nullptr);
-            for (size_t i : bf_idx) {
-                rcs[i] = rc;
-                cudaMemcpyAsync(s->host_status + batch[i].hidx, slot, sizeof(int),
-                                cudaMemcpyDeviceToHost, gs);
+            for (size_t k = 0; k < bf_idx.size(); ++k) {
+                const size_t i = bf_idx[k];
+                const int prc = publish_status(s, lead, batch[i].hidx, k + 1 == bf_idx.size(), gs);
+                rcs[i] = rc != MOA_OK ? rc : prc;
             }
         }
         std::vector<uint64_t> failed_now;
@@ -326,15 +340,13 @@ void scheduler(moa_server* s) {
             Request& r = batch[i];
             if (!(grouped && r.d.dt == MOA_BF16)) {
                 cudaStream_t rs = s->streams[r.stream];
-                int* slot = static_cast<int*>(slot_ptr(s, r.ws_off, r.ws_bytes));
-                cudaMemsetAsync(slot, 0, sizeof(int), rs);
-                set_status_override(slot);
+                set_status_override(s->dev_status + r.hidx);
                 rcs[i] = gemm_ex(r.d.m, r.d.n, r.d.p, r.d.dt, r.d.A, r.d.B, r.d.C, 0,
                                  r.ws_bytes ? s->arena.ptr(r.ws_off) : nullptr, r.ws_bytes, rs,
                                  nullptr);
                 set_status_override(nullptr);
-                cudaMemcpyAsync(s->host_status + r.hidx, slot, sizeof(int), cudaMemcpyDeviceToHost,
-                                rs);
+                const int prc = publish_status(s, r.hidx, r.hidx, true, rs);
+                if (rcs[i] == MOA_OK) rcs[i] = prc;
             }
             if (cudaEventRecord(s->done_ev[r.hidx], s->streams[r.stream]) != cudaSuccess) {
                 rcs[i] = MOA_ERR_CUDA;
@@ -390,13 +402,27 @@ int moa_serve_create(const moa_serve_config* cfg, moa_server** out) {
         }
         s->streams.push_back(st);
     }
-    s->arena.init(reinterpret_cast<uintptr_t>(cfg->arena), cfg->arena_bytes);
-    e = cudaHostAlloc(reinterpret_cast<void**>(&s->host_status),
-                      sizeof(int) * static_cast<size_t>(cfg->max_inflight), cudaHostAllocDefault);
-    if (e != cudaSuccess) {
+    // the first bytes of the arena hold the per-slot device status words
+    const size_t words = moa::Arena::granule(sizeof(int) * static_cast<size_t>(cfg->max_inflight));
+    if (cfg->arena_bytes < words) {
         for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
         delete s;
-        return moa::cuda_fail(e, "cudaHostAlloc(status ring)");
+        return moa::fail(MOA_ERR_BUDGET, "arena smaller than the status words of the slots");
+    }
+    s->dev_status = static_cast<int*>(cfg->arena);
+    s->arena.init(reinterpret_cast<uintptr_t>(cfg->arena) + words, cfg->arena_bytes - words);
+    e = cudaMemset(s->dev_status, 0, words);
+    if (e == cudaSuccess)
+        e = cudaHostAlloc(reinterpret_cast<void**>(&s->host_status),
+                          sizeof(int) * static_cast<size_t>(cfg->max_inflight),
+                          cudaHostAllocMapped);
+    if (e == cudaSuccess)
+        e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->host_status_dev), s->host_status, 0);
+    if (e != cudaSuccess) {
+        if (s->host_status) cudaFreeHost(s->host_status);
+        for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
+        delete s;
+        return moa::cuda_fail(e, "status words");
     }
     for (int i = cfg->max_inflight - 1; i >= 0; --i) s->free_hidx.push_back(i);
     s->done_ev.assign(static_cast<size_t>(cfg->max_inflight), nullptr);
