@@ -328,16 +328,29 @@ __device__ __forceinline__ int col_exp(typename Bits<T>::U M, int bias, int* sta
     return Bits<T>::frexp_exp(M) + bias;
 }
 
-// Blocks [0, rblocks): row exponents of A; the rest: column maxima of B.
+// Blocks [0, rblocks): row exponents of A; the next cblocks: column maxima
+// of B; the last zblocks (split K only): clear z0[0 .. n0) and z1[0 .. n1)
+// (the int64 totals in C and the finished-unit counters).
 template <typename T>
 __global__ void __launch_bounds__(256)
     exps_kernel(const T* __restrict__ A, int64_t m, int64_t n, const T* __restrict__ B, int64_t p,
                 int64_t chunk, int bias, int* __restrict__ eA, typename Bits<T>::U* __restrict__ cmax,
-                int* status, int rblocks, int64_t gx) {
-    if (static_cast<int>(blockIdx.x) < rblocks)
-        row_exp_part(A, m, n, bias, eA, status, blockIdx.x, rblocks);
-    else
-        col_max_part(B, n, p, chunk, cmax, blockIdx.x - rblocks, gx);
+                int* status, int rblocks, int64_t gx, int cblocks, unsigned long long* z0,
+                int64_t n0, unsigned long long* z1, int64_t n1) {
+    const int b = static_cast<int>(blockIdx.x);
+    if (b < rblocks) {
+        row_exp_part(A, m, n, bias, eA, status, b, rblocks);
+    } else if (b < rblocks + cblocks) {
+        col_max_part(B, n, p, chunk, cmax, b - rblocks, gx);
+    } else {
+        const int64_t zb = b - rblocks - cblocks, nz = gridDim.x - rblocks - cblocks;
+        for (int64_t i = zb * blockDim.x + threadIdx.x; i < n0 + n1; i += nz * blockDim.x) {
+            if (i < n0)
+                z0[i] = 0ull;
+            else
+                z1[i - n0] = 0ull;
+        }
+    }
 }
 
 // Loads X[r, c0 .. c0+7] of an FP64 matrix (zero past `cols`).
@@ -653,7 +666,31 @@ struct SplitArgs {
     int vec_ok;
     uint64_t wait_limit_ns;
     int* status;
+    // FP64 modes, split K: every tile's K range is cut into `ksplit` slices
+    // run as separate work units; their folds add into C atomically (exact
+    // int64 adds, order-free), and cnt[tile * epilogue warps + warp] counts
+    // the units that have finished a warp's region (zeroed before launch).
+    int ksplit;
+    int* cnt;
 };
+
+// Work unit u: tile t and the K blocks [kb_lo, kb_hi) of its K slice (SK:
+// the split-K kernel variant; without it every unit is a whole tile).
+template <bool SK>
+__device__ __forceinline__ void split_unit(const SplitArgs& a, int u, int& t, int& kb_lo,
+                                           int& kb_hi) {
+    if constexpr (!SK) {
+        t = u;
+        kb_lo = 0;
+        kb_hi = a.num_kb;
+        return;
+    }
+    const int ks = a.ksplit;
+    t = u / ks;
+    const int sl = u - t * ks;
+    kb_lo = static_cast<int>(static_cast<long long>(sl) * a.num_kb / ks);
+    kb_hi = static_cast<int>(static_cast<long long>(sl + 1) * a.num_kb / ks);
+}
 
 __device__ __forceinline__ void split_tile_coords(int t, int tiles_m, int tiles_n, int group_m,
                                                   int& tm, int& tn) {
@@ -700,11 +737,14 @@ __device__ __forceinline__ long long align_level(int v, int sh) {
 // in C (pitch ld elements); rows_left / cols_left: its rows and columns
 // inside C; er: the lane's row exponent eA (lane = row); vec: C is 16-byte
 // aligned and ld even.
+// `atomic` (split K): T += align_level(R, sh) by atomic adds into a C that
+// was zeroed before the launch (t_init and last are ignored).
 __device__ __forceinline__ void fold_block16(uint8_t* stage, const uint32_t (&v)[16],
                                              long long* C64, int64_t ld, int64_t row0,
                                              int rows_left, int64_t col0, int64_t cols_left,
                                              int sh, bool t_init, bool last, int er,
-                                             const int* __restrict__ eB, int ebias, bool vec) {
+                                             const int* __restrict__ eB, int ebias, bool vec,
+                                             bool atomic) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int c = 0; c < 4; ++c)
@@ -716,6 +756,22 @@ __device__ __forceinline__ void fold_block16(uint8_t* stage, const uint32_t (&v)
     const int r4 = lane >> 3, c2 = lane & 7;
     const int64_t col = col0 + 2 * c2;
     const int64_t cl = cols_left - 2 * c2;
+    if (atomic) {
+#pragma unroll 4
+        for (int i = 0; i < 8; ++i) {
+            const int rr = 4 * i + r4;
+            if (rr >= rows_left || cl <= 0) continue;
+            const uint2 sv = *reinterpret_cast<const uint2*>(
+                stage + rr * 64 + (((c2 >> 1) ^ (rr & 3)) << 4) + (c2 & 1) * 8);
+            auto* dst = reinterpret_cast<unsigned long long*>(C64 + (row0 + rr) * ld + col);
+            atomicAdd(dst, static_cast<unsigned long long>(align_level(static_cast<int>(sv.x), sh)));
+            if (cl > 1)
+                atomicAdd(dst + 1,
+                          static_cast<unsigned long long>(align_level(static_cast<int>(sv.y), sh)));
+        }
+        __syncwarp();
+        return;
+    }
     int eb0 = 0, eb1 = 0;
     if (last) {
         if (cl > 0) eb0 = eB[col];
@@ -776,7 +832,51 @@ __device__ __forceinline__ void fold_block16(uint8_t* stage, const uint32_t (&v)
     __syncwarp();   // the staging tile is free for the next block
 }
 
-template <int BN, int MODE, int FMT>
+// Split K, last unit of a warp's region: converts the region's int64 totals
+// (32 rows x `cols` columns from (row0, col0), every unit's adds complete)
+// once to FP64, scaled by 2^(eA_i + eB_j + ebias), in place.  Loads bypass
+// L1 (the other units' adds happened in L2).
+__device__ __forceinline__ void convert_region(long long* C64, int64_t ld, int64_t row0,
+                                               int rows_left, int64_t col0, int64_t cols_left,
+                                               int cols, int er, const int* __restrict__ eB,
+                                               int ebias, bool vec) {
+    const int lane = threadIdx.x & 31;
+    const int r4 = lane >> 3, c2 = lane & 7;
+    for (int b = 0; b < cols; b += 16) {
+        const int64_t col = col0 + b + 2 * c2;
+        const int64_t cl = cols_left - b - 2 * c2;
+        const bool pair = vec && cl >= 2;
+        const int eb0 = cl > 0 ? eB[col] : 0;
+        const int eb1 = cl > 1 ? eB[col + 1] : 0;
+#pragma unroll 4
+        for (int i = 0; i < 8; ++i) {
+            const int rr = 4 * i + r4;
+            const int er_r = __shfl_sync(0xffffffffu, er, rr);
+            if (rr >= rows_left || cl <= 0) continue;
+            long long* src = C64 + (row0 + rr) * ld + col;
+            long long t0, t1 = 0;
+            if (pair) {
+                const longlong2 x = __ldcg(reinterpret_cast<const longlong2*>(src));
+                t0 = x.x;
+                t1 = x.y;
+            } else {
+                t0 = __ldcg(src);
+                if (cl > 1) t1 = __ldcg(src + 1);
+            }
+            const double d0 = ldexp(__ll2double_rn(t0), er_r + eb0 + ebias);
+            const double d1 = ldexp(__ll2double_rn(t1), er_r + eb1 + ebias);
+            double* dd = reinterpret_cast<double*>(src);
+            if (pair) {
+                *reinterpret_cast<double2*>(dd) = make_double2(d0, d1);
+            } else {
+                dd[0] = d0;
+                if (cl > 1) dd[1] = d1;
+            }
+        }
+    }
+}
+
+template <int BN, int MODE, int FMT, bool SK>
 __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
     split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       const SplitArgs args) {
@@ -831,8 +931,7 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
-    const int num_tiles = args.tiles_m * args.tiles_n;
-    const int num_kb = args.num_kb;
+    const int num_units = args.tiles_m * args.tiles_n * (SK ? args.ksplit : 1);
 
     if (warp == 0) {
         if (lane == 0) {
@@ -841,14 +940,15 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
             uint32_t phase = 0;
             long issued = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
-                int tm, tn;
+            for (int u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
+                int t, kb_lo, kb_hi, tm, tn;
+                split_unit<SK>(args, u, t, kb_lo, kb_hi);
                 split_tile_coords(t, args.tiles_m, args.tiles_n, args.group_m, tm, tn);
                 for (int L = 0; L < args.levels && ok; ++L) {
                     const int np = level_pairs(args, L);
                     if constexpr (Cfg::kKB) {
                         // kb-major: the three slices of A and of B of K block kb
-                        for (int kb = 0; kb < num_kb && ok; ++kb) {
+                        for (int kb = kb_lo; kb < kb_hi && ok; ++kb) {
                             if (!mbar_wait(&empty[stage], phase ^ 1u, ctl, limit, status)) {
                                 ok = false;
                                 break;
@@ -873,7 +973,7 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
                         }
                         continue;
                     }
-                    for (int kb = 0; kb < num_kb && ok; ++kb) {
+                    for (int kb = kb_lo; kb < kb_hi && ok; ++kb) {
                         for (int q = 0; q < np; ++q) {
                             int s, u;
                             pair_at(args, L, q, s, u);
@@ -922,11 +1022,13 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
             uint32_t phase = 0;
             long cnt = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
+            for (int u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
+                int t, kb_lo, kb_hi;
+                split_unit<SK>(args, u, t, kb_lo, kb_hi);
                 for (int L = 0; L < args.levels && ok; ++L) {
                     const int np = level_pairs(args, L);
                     const int kc = args.kc[L];
-                    for (int kb0 = 0; kb0 < num_kb && ok; kb0 += kc, ++cnt) {
+                    for (int kb0 = kb_lo; kb0 < kb_hi && ok; kb0 += kc, ++cnt) {
                         const int buf = static_cast<int>(cnt % kNBuf);
                         const uint32_t bph = static_cast<uint32_t>((cnt / kNBuf) & 1);
                         if (!mbar_wait(&tempty[buf], bph ^ 1u, ctl, limit, status)) {
@@ -935,7 +1037,7 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
                         }
                         tc_fence_after();
                         const uint32_t d = tmem_base + static_cast<uint32_t>(buf * BN);
-                        const int kb1 = min(num_kb, kb0 + kc);
+                        const int kb1 = min(kb_hi, kb0 + kc);
                         bool first = true;
                         for (int kb = kb0; kb < kb1 && ok; ++kb) {
                             if constexpr (Cfg::kKB) {
@@ -1020,8 +1122,10 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
         uint8_t* epi_stage = epi + (F64 ? (warp - 2) * Cfg::kEpiStageWarp : 0);
         long cnt = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x) {
-            int tm, tn;
+        constexpr bool atomic = SK;
+        for (int u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
+            int t, kb_lo, kb_hi, tm, tn;
+            split_unit<SK>(args, u, t, kb_lo, kb_hi);
             split_tile_coords(t, args.tiles_m, args.tiles_n, args.group_m, tm, tn);
             const int64_t row = static_cast<int64_t>(tm) * kBM + q * 32 + lane;
             const int64_t col_base = static_cast<int64_t>(tn) * BN + h * kCols;
@@ -1041,7 +1145,7 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
             for (int L = 0; L < args.levels && ok; ++L) {
                 const int kc = args.kc[L];
                 int since_fold = 0;
-                for (int kb0 = 0; kb0 < num_kb; kb0 += kc, ++cnt) {
+                for (int kb0 = kb_lo; kb0 < kb_hi; kb0 += kc, ++cnt) {
                     const int buf = static_cast<int>(cnt % kNBuf);
                     const uint32_t bph = static_cast<uint32_t>((cnt / kNBuf) & 1);
                     ok = mbar_wait(&tfull[buf], bph, ctl, limit, status);
@@ -1092,7 +1196,7 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&tempty[buf]);
                     ++since_fold;
-                    const bool level_end = kb0 + kc >= num_kb;
+                    const bool level_end = kb0 + kc >= kb_hi;
                     if (F64 && (level_end || since_fold == 64)) {
                         // fold the level's exact sum into the int64 total:
                         // T += round(R * 2^(beta(S-1-L) - drop)); the last fold
@@ -1117,7 +1221,28 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
                             fold_block16(epi_stage, rv, reinterpret_cast<long long*>(args.C),
                                          args.p, row0, rows_left, c0, args.p - c0, sh, t_init,
                                          last, er, args.eB,
-                                         args.drop - args.beta * (args.S + 1), args.vec_ok != 0);
+                                         args.drop - args.beta * (args.S + 1), args.vec_ok != 0,
+                                         atomic);
+                        }
+                        if (atomic && last) {
+                            // this unit's adds to the warp's region are done;
+                            // the region's last unit converts it to FP64
+                            __threadfence();
+                            __syncwarp();
+                            int old = 0;
+                            if (lane == 0)
+                                old = atomicAdd(&args.cnt[static_cast<int64_t>(t) * Cfg::kEpiWarps +
+                                                          (warp - 2)],
+                                                1);
+                            old = __shfl_sync(0xffffffffu, old, 0);
+                            if (old == args.ksplit - 1) {
+                                __threadfence();
+                                const int64_t left = args.p - col_base;
+                                convert_region(reinterpret_cast<long long*>(args.C), args.p, row0,
+                                               rows_left, col_base, left, kCols, er, args.eB,
+                                               args.drop - args.beta * (args.S + 1),
+                                               args.vec_ok != 0);
+                            }
                         }
                         t_init = true;
                         r_valid = false;
@@ -1202,6 +1327,10 @@ SplitLayout split_layout(int64_t m, int64_t n, int64_t p, moa_dtype dt, int S) {
         off += al(static_cast<size_t>(p) * 4);
         L.cmax_off = off;
         off += al(static_cast<size_t>(p) * 8);
+        // split-K counters: at most ceil(m/128) x ceil(p/128) tiles, 16 warps
+        L.cnt_bytes = static_cast<size_t>(ceil_div(m, kBM)) * ceil_div(p, 128) * 16 * 4;
+        L.cnt_off = off;
+        off += al(L.cnt_bytes);
     }
     L.total = off;
     return L;
@@ -1213,21 +1342,21 @@ size_t split_workspace_bytes(int64_t m, int64_t n, int64_t p, moa_dtype dt, int 
     return split_layout(m, n, p, dt, S).total;
 }
 
-template <int BN, int MODE, int FMT>
+template <int BN, int MODE, int FMT, bool SK = false>
 static int launch_split_cfg(const SplitArgs& a, const CUtensorMap& tmA, const CUtensorMap& tmB,
                             cudaStream_t s, moa_stats* st) {
     using Cfg = SplitCfg<BN, MODE, FMT>;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel<BN, MODE, FMT>,
+        cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel<BN, MODE, FMT, SK>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(split_gemm)");
         attr_set = true;
     }
     const long tiles = static_cast<long>(a.tiles_m) * a.tiles_n;
-    const int grid = static_cast<int>(std::min<long>(tiles, num_sms()));
+    const int grid = static_cast<int>(std::min<long>(tiles * (SK ? a.ksplit : 1), num_sms()));
     prof_begin(s);
-    split_gemm_kernel<BN, MODE, FMT><<<grid, Cfg::kThreads, Cfg::kSmem, s>>>(tmA, tmB, a);
+    split_gemm_kernel<BN, MODE, FMT, SK><<<grid, Cfg::kThreads, Cfg::kSmem, s>>>(tmA, tmB, a);
     cudaError_t e = cudaGetLastError();
     prof_end(s);
     if (e != cudaSuccess) return cuda_fail(e, "split_gemm_kernel launch");
@@ -1267,11 +1396,32 @@ static int split_block_n(int64_t m, int64_t p, bool f64) {
     return best;
 }
 
+// K slices per tile of the FP64-accuracy slice GEMM: when the tiles fill at
+// most half of the SMs, each tile's K range is cut so that the work units
+// (tiles x slices) fill them, keeping at least 1024 K elements per unit
+// (every unit folds each level into C once).  MOA_SPLIT_K forces a factor.
+static int split_k_factor(long tiles, int num_kb, int bk) {
+    static long env = -1;
+    if (env < 0) {
+        const char* e = std::getenv("MOA_SPLIT_K");
+        env = e ? std::max(0L, std::strtol(e, nullptr, 10)) : 0;
+    }
+    long ks = 1;
+    if (env > 0) {
+        ks = env;
+    } else {
+        const long sms = num_sms();
+        if (tiles * 2 <= sms) ks = std::min(sms / tiles, static_cast<long>(num_kb) * bk / 1024);
+    }
+    return static_cast<int>(std::max(1L, std::min({ks, static_cast<long>(num_kb), 64L})));
+}
+
 // Exponent and digit pre-passes of the FP64-accuracy modes for input type T.
 template <typename T>
 static void digit_prepasses(const SplitLayout& L, int64_t m, int64_t n, int64_t p, const T* A,
                             const T* B, int beta, int headroom, int* eA, int* eB, void* cmax,
-                            uint8_t* a_sl, uint8_t* b_sl, int* status, cudaStream_t s) {
+                            uint8_t* a_sl, uint8_t* b_sl, int* status, cudaStream_t s,
+                            void* zero_c, void* zero_cnt) {
     using U = typename Bits<T>::U;
     constexpr int per16 = 16 / sizeof(T);
     const int S = L.S;
@@ -1281,10 +1431,16 @@ static void digit_prepasses(const SplitLayout& L, int64_t m, int64_t n, int64_t 
     const int64_t rblocks = std::min<int64_t>(ceil_div(m, rows_per_block), 16L * num_sms());
     const int64_t chunk = 256;
     const int64_t gx = ceil_div(p, 256);
-    const int64_t eblocks = rblocks + gx * ceil_div(n, chunk);
-    exps_kernel<T><<<static_cast<unsigned>(eblocks), 256, 0, s>>>(
+    const int64_t cblocks = gx * ceil_div(n, chunk);
+    // split K: C (int64 totals, m x p) and the unit counters start at zero
+    const int64_t n0 = zero_c ? m * p : 0;
+    const int64_t n1 = zero_c ? static_cast<int64_t>(L.cnt_bytes / 8) : 0;
+    const int64_t zblocks = zero_c ? std::min<int64_t>(ceil_div(n0 + n1, 256 * 8), 4L * num_sms()) : 0;
+    exps_kernel<T><<<static_cast<unsigned>(rblocks + cblocks + zblocks), 256, 0, s>>>(
         A, m, n, B, p, chunk, headroom, eA, static_cast<U*>(cmax), status,
-        static_cast<int>(rblocks), gx);
+        static_cast<int>(rblocks), gx, static_cast<int>(cblocks),
+        static_cast<unsigned long long*>(zero_c), n0, static_cast<unsigned long long*>(zero_cnt),
+        n1);
     // launch 2: digit planes of A and of B (B's column exponents formed there)
     const int64_t a_plane = m * L.lda;
     const U* cm = static_cast<const U*>(cmax);
@@ -1339,6 +1495,9 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
     a.wait_limit_ns = wait_limit_ns();
     a.status = status;
     a.vec_ok = (p % 4 == 0) && (reinterpret_cast<uintptr_t>(C) % 16 == 0);
+    a.ksplit = dt == MOA_F32_SPLIT ? 1 : split_k_factor(static_cast<long>(a.tiles_m) * a.tiles_n,
+                                                        a.num_kb, bke);
+    a.cnt = a.ksplit > 1 ? reinterpret_cast<int*>(base + L.cnt_off) : nullptr;
 
     if (dt == MOA_F32_SPLIT) {
         auto* a16 = reinterpret_cast<__nv_bfloat16*>(a_sl);
@@ -1369,11 +1528,11 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
         if (dt == MOA_F64_SPLIT_F64IN || dt == MOA_F64_SPLIT_F64IN_E4M3)
             digit_prepasses<double>(L, m, n, p, static_cast<const double*>(A),
                                     static_cast<const double*>(B), beta, h, eA, eB, cmax, a_sl,
-                                    b_sl, status, s);
+                                    b_sl, status, s, a.ksplit > 1 ? C : nullptr, a.cnt);
         else
             digit_prepasses<float>(L, m, n, p, static_cast<const float*>(A),
                                    static_cast<const float*>(B), beta, h, eA, eB, cmax, a_sl, b_sl,
-                                   status, s);
+                                   status, s, a.ksplit > 1 ? C : nullptr, a.cnt);
         kernels += 3;   // the column-max clear, the exponent pass and the digit pass
         a.f64 = 1;
         a.levels = S;
@@ -1415,9 +1574,14 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
                           static_cast<uint64_t>(L.ldb), static_cast<uint64_t>(b_plane), 128,
                           static_cast<uint32_t>(bn));
         if (rc != MOA_OK) return rc;
-        rc = bn == 256   ? launch_split_cfg<256, kModeF64Tmem, kFmtE4M3>(a, tmA, tmB, s, st)
-             : bn == 192 ? launch_split_cfg<192, kModeF64Reg, kFmtE4M3>(a, tmA, tmB, s, st)
-                         : launch_split_cfg<128, kModeF64Reg, kFmtE4M3>(a, tmA, tmB, s, st);
+        if (a.ksplit > 1)
+            rc = bn == 256   ? launch_split_cfg<256, kModeF64Tmem, kFmtE4M3, true>(a, tmA, tmB, s, st)
+                 : bn == 192 ? launch_split_cfg<192, kModeF64Reg, kFmtE4M3, true>(a, tmA, tmB, s, st)
+                             : launch_split_cfg<128, kModeF64Reg, kFmtE4M3, true>(a, tmA, tmB, s, st);
+        else
+            rc = bn == 256   ? launch_split_cfg<256, kModeF64Tmem, kFmtE4M3>(a, tmA, tmB, s, st)
+                 : bn == 192 ? launch_split_cfg<192, kModeF64Reg, kFmtE4M3>(a, tmA, tmB, s, st)
+                             : launch_split_cfg<128, kModeF64Reg, kFmtE4M3>(a, tmA, tmB, s, st);
     } else if (dt == MOA_F32_SPLIT) {
         // kb-major stages: A slices 32 K x 128 rows (64-byte swizzle), B
         // slices 64 columns x 32 K rows per chunk
@@ -1444,9 +1608,14 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
                           static_cast<uint64_t>(L.ldb) * 2, static_cast<uint64_t>(b_plane) * 2, 64,
                           kBK);
         if (rc != MOA_OK) return rc;
-        rc = bn == 256   ? launch_split_cfg<256, kModeF64Tmem, kFmtBF16>(a, tmA, tmB, s, st)
-             : bn == 192 ? launch_split_cfg<192, kModeF64Reg, kFmtBF16>(a, tmA, tmB, s, st)
-                         : launch_split_cfg<128, kModeF64Reg, kFmtBF16>(a, tmA, tmB, s, st);
+        if (a.ksplit > 1)
+            rc = bn == 256   ? launch_split_cfg<256, kModeF64Tmem, kFmtBF16, true>(a, tmA, tmB, s, st)
+                 : bn == 192 ? launch_split_cfg<192, kModeF64Reg, kFmtBF16, true>(a, tmA, tmB, s, st)
+                             : launch_split_cfg<128, kModeF64Reg, kFmtBF16, true>(a, tmA, tmB, s, st);
+        else
+            rc = bn == 256   ? launch_split_cfg<256, kModeF64Tmem, kFmtBF16>(a, tmA, tmB, s, st)
+                 : bn == 192 ? launch_split_cfg<192, kModeF64Reg, kFmtBF16>(a, tmA, tmB, s, st)
+                             : launch_split_cfg<128, kModeF64Reg, kFmtBF16>(a, tmA, tmB, s, st);
     }
     if (st) {
         st->slices = S;

@@ -55,6 +55,8 @@ struct SplitLayout {
                            // when b_trans)
     size_t ea_off, eb_off; // FP64-accuracy: per-row / per-column exponents (int32)
     size_t cmax_off;       // FP64-accuracy: per-column max |B| bit patterns (uint64)
+    size_t cnt_off;        // FP64-accuracy, split K: finished-unit counters (int32,
+    size_t cnt_bytes;      // one per tile and epilogue warp; a multiple of 8 bytes)
     size_t total;
 };
 SplitLayout split_layout(int64_t m, int64_t n, int64_t p, moa_dtype dt, int S);

@@ -106,6 +106,28 @@ def test_f64_split_matches_exact_slice_product(dt, S):
     assert np.all(np.abs(C - exact) <= scale * 2.0 ** -46 + np.abs(exact) * 2.0 ** -52)
 
 
+@pytest.mark.parametrize("dt", [moa.MOA_F64_SPLIT_F64IN, moa.MOA_F64_SPLIT_F64IN_E4M3,
+                                moa.MOA_F64_SPLIT_F32IN], ids=lambda d: NAMES[d])
+@pytest.mark.parametrize("m,n,p", [(70, 4200, 140), (33, 4100, 257), (1, 8192, 3)])
+def test_f64_split_k_exact_and_deterministic(dt, m, n, p):
+    """Few output tiles and a long K: the slice GEMM cuts every tile's K range
+    into slices run on separate SMs whose int64 folds add atomically into C.
+    Integer adds are exact and order-free, so the result is still the exact
+    slice product of the oracle's digits (to the final FP64 rounding and the
+    dropped low bits) and bit-identical from call to call."""
+    beta, h = moa.DIGITS[dt]
+    A, B = inputs.normal_pair(m, n, p, dtype=moa.in_dtype(dt), seed=m + p, scaled="rows")
+    C1 = _run(A, B, dt)
+    C2 = _run(A, B, dt)
+    assert np.array_equal(C1, C2)
+    S = moa.DEFAULT_SLICES[dt]
+    eA, dA = oracle.slice_fixed(A.double().numpy(), 0, beta, S, headroom=h)
+    eB, dB = oracle.slice_fixed(B.double().numpy(), 1, beta, S, headroom=h)
+    exact = oracle.split_gemm_exact(dA, eA, dB, eB, beta, S)
+    scale = np.outer(2.0 ** eA.astype(np.float64), 2.0 ** eB.astype(np.float64))
+    assert np.all(np.abs(C1 - exact) <= scale * 2.0 ** -46 + np.abs(exact) * 2.0 ** -52)
+
+
 def test_f32_split_slices_match_oracle_split():
     """The FP32-accuracy mode's result equals the six-product sum of the
     oracle's BF16 slices up to FP32 accumulation error: each of the 6n terms
