@@ -24,7 +24,10 @@
 // Kernel layout (one persistent CTA per SM): warp 0 issues TMA loads of
 // (A slice, B slice) K blocks; warp 1 issues tcgen05.mma into one of one or
 // two TMEM chunk accumulators; the epilogue warps (one per TMEM lane
-// quadrant and column group) flush chunks and write C.
+// quadrant and column group) flush chunks and write C.  The CTAs walk work
+// units: whole output tiles, or, in the FP64 modes when the tiles fill at
+// most half of the SMs, (tile, K slice) pairs whose int64 totals meet in C by
+// exact atomic adds (split K).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
