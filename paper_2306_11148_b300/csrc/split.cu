@@ -596,6 +596,9 @@ namespace {
 constexpr int kBM = 128, kBK = 64;                // kBK: BF16 elements per K block
 constexpr int kABytes = kBM * 128;                 // 128 rows x 128 bytes of K
 constexpr int kMaxLevels = 12;
+// Largest tile count (at width 128) for which the workspace holds the split-K
+// counters and fine-level sums.
+constexpr int64_t kSplitKMaxTiles = 320;
 // Digit-plane formats of the slice GEMM.  kFmtBF16: kind::f16, B planes
 // MN-major (n x p, read as 64-column chunks).  kFmtE4M3: kind::f8f6f4, B
 // planes hold B^T (p x n, K-major, one box per stage).  A K block is 128
@@ -675,6 +678,10 @@ struct SplitArgs {
     // the units that have finished a warp's region (zeroed before launch).
     int ksplit;
     int* cnt;
+    // split K: levels finer than the total's grid (shift below 0) add their
+    // exact sums, scaled to the finest level, into fine[m x p] instead of
+    // rounding them into C; the region's last unit rounds them in once.
+    long long* fine;
 };
 
 // Work unit u: tile t and the K blocks [kb_lo, kb_hi) of its K slice (SK:
@@ -724,9 +731,11 @@ __device__ __forceinline__ void pair_at(const SplitArgs& a, int L, int q, int& s
 
 // v * 2^sh for sh >= 0; else v / 2^-sh rounded to nearest (ties up): the
 // fixed-point alignment of a level sum to the int64 total.
-__device__ __forceinline__ long long align_level(int v, int sh) {
-    const long long x = v;
+__device__ __forceinline__ long long align_level64(long long x, int sh) {
     return sh >= 0 ? x * (1ll << sh) : (x + (1ll << (-sh - 1))) >> (-sh);
+}
+__device__ __forceinline__ long long align_level(int v, int sh) {
+    return align_level64(static_cast<long long>(v), sh);
 }
 
 // Folds a 32 x 16 block of exact level sums into the int64 fixed-point
@@ -839,10 +848,10 @@ __device__ __forceinline__ void fold_block16(uint8_t* stage, const uint32_t (&v)
 // (32 rows x `cols` columns from (row0, col0), every unit's adds complete)
 // once to FP64, scaled by 2^(eA_i + eB_j + ebias), in place.  Loads bypass
 // L1 (the other units' adds happened in L2).
-__device__ __forceinline__ void convert_region(long long* C64, int64_t ld, int64_t row0,
-                                               int rows_left, int64_t col0, int64_t cols_left,
-                                               int cols, int er, const int* __restrict__ eB,
-                                               int ebias, bool vec) {
+__device__ __forceinline__ void convert_region(long long* C64, const long long* fine, int drop,
+                                               int64_t ld, int64_t row0, int rows_left,
+                                               int64_t col0, int64_t cols_left, int cols, int er,
+                                               const int* __restrict__ eB, int ebias, bool vec) {
     const int lane = threadIdx.x & 31;
     const int r4 = lane >> 3, c2 = lane & 7;
     for (int b = 0; b < cols; b += 16) {
@@ -857,7 +866,8 @@ __device__ __forceinline__ void convert_region(long long* C64, int64_t ld, int64
             const int er_r = __shfl_sync(0xffffffffu, er, rr);
             if (rr >= rows_left || cl <= 0) continue;
             long long* src = C64 + (row0 + rr) * ld + col;
-            long long t0, t1 = 0;
+            const long long* fsrc = fine + (row0 + rr) * ld + col;
+            long long t0, t1 = 0, f0, f1 = 0;
             if (pair) {
                 const longlong2 x = __ldcg(reinterpret_cast<const longlong2*>(src));
                 t0 = x.x;
@@ -866,6 +876,11 @@ __device__ __forceinline__ void convert_region(long long* C64, int64_t ld, int64
                 t0 = __ldcg(src);
                 if (cl > 1) t1 = __ldcg(src + 1);
             }
+            f0 = __ldcg(fsrc);   // 8-byte aligned only: fine is packed m x p
+            if (cl > 1) f1 = __ldcg(fsrc + 1);
+            // the fine levels, rounded once onto the total's grid
+            t0 += align_level64(f0, -drop);
+            t1 += align_level64(f1, -drop);
             const double d0 = ldexp(__ll2double_rn(t0), er_r + eb0 + ebias);
             const double d1 = ldexp(__ll2double_rn(t1), er_r + eb1 + ebias);
             double* dd = reinterpret_cast<double*>(src);
@@ -1221,11 +1236,16 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
                                 for (int i = 0; i < 16; ++i) rv[i] = acc[(b * 16 + i) % kRegs];
                             }
                             const int64_t c0 = col_base + b * 16;
-                            fold_block16(epi_stage, rv, reinterpret_cast<long long*>(args.C),
-                                         args.p, row0, rows_left, c0, args.p - c0, sh, t_init,
-                                         last, er, args.eB,
-                                         args.drop - args.beta * (args.S + 1), args.vec_ok != 0,
-                                         atomic);
+                            // split K: a level finer than the total's grid goes,
+                            // exact, into the fine-level sums
+                            const bool to_fine = atomic && sh < 0;
+                            fold_block16(epi_stage, rv,
+                                         to_fine ? args.fine
+                                                 : reinterpret_cast<long long*>(args.C),
+                                         args.p, row0, rows_left, c0, args.p - c0,
+                                         to_fine ? sh + args.drop : sh, t_init, last, er,
+                                         args.eB, args.drop - args.beta * (args.S + 1),
+                                         args.vec_ok != 0 && !to_fine, atomic);
                         }
                         if (atomic && last) {
                             // this unit's adds to the warp's region are done;
@@ -1241,8 +1261,9 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
                             if (old == args.ksplit - 1) {
                                 __threadfence();
                                 const int64_t left = args.p - col_base;
-                                convert_region(reinterpret_cast<long long*>(args.C), args.p, row0,
-                                               rows_left, col_base, left, kCols, er, args.eB,
+                                convert_region(reinterpret_cast<long long*>(args.C), args.fine,
+                                               args.drop, args.p, row0, rows_left, col_base,
+                                               left, kCols, er, args.eB,
                                                args.drop - args.beta * (args.S + 1),
                                                args.vec_ok != 0);
                             }
@@ -1330,10 +1351,17 @@ SplitLayout split_layout(int64_t m, int64_t n, int64_t p, moa_dtype dt, int S) {
         off += al(static_cast<size_t>(p) * 4);
         L.cmax_off = off;
         off += al(static_cast<size_t>(p) * 8);
-        // split-K counters: at most ceil(m/128) x ceil(p/128) tiles, 16 warps
-        L.cnt_bytes = static_cast<size_t>(ceil_div(m, kBM)) * ceil_div(p, 128) * 16 * 4;
-        L.cnt_off = off;
-        off += al(L.cnt_bytes);
+        // split K (few tiles only): counters for at most ceil(m/128) x
+        // ceil(p/128) tiles of 16 epilogue warps, and the fine-level sums
+        const int64_t tiles128 = ceil_div(m, kBM) * ceil_div(p, 128);
+        if (tiles128 <= kSplitKMaxTiles) {
+            L.cnt_bytes = static_cast<size_t>(tiles128) * 16 * 4;
+            L.cnt_off = off;
+            off += al(L.cnt_bytes);
+            L.fine_bytes = static_cast<size_t>(m) * p * 8;
+            L.fine_off = off;
+            off += al(L.fine_bytes);
+        }
     }
     L.total = off;
     return L;
@@ -1437,7 +1465,9 @@ static void digit_prepasses(const SplitLayout& L, int64_t m, int64_t n, int64_t 
     const int64_t cblocks = gx * ceil_div(n, chunk);
     // split K: C (int64 totals, m x p) and the unit counters start at zero
     const int64_t n0 = zero_c ? m * p : 0;
-    const int64_t n1 = zero_c ? static_cast<int64_t>(L.cnt_bytes / 8) : 0;
+    // (the counters and the fine-level sums are adjacent in the workspace)
+    const int64_t n1 =
+        zero_c ? static_cast<int64_t>((L.fine_off - L.cnt_off + L.fine_bytes) / 8) : 0;
     const int64_t zblocks = zero_c ? std::min<int64_t>(ceil_div(n0 + n1, 256 * 8), 4L * num_sms()) : 0;
     exps_kernel<T><<<static_cast<unsigned>(rblocks + cblocks + zblocks), 256, 0, s>>>(
         A, m, n, B, p, chunk, headroom, eA, static_cast<U*>(cmax), status,
@@ -1498,9 +1528,11 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
     a.wait_limit_ns = wait_limit_ns();
     a.status = status;
     a.vec_ok = (p % 4 == 0) && (reinterpret_cast<uintptr_t>(C) % 16 == 0);
-    a.ksplit = dt == MOA_F32_SPLIT ? 1 : split_k_factor(static_cast<long>(a.tiles_m) * a.tiles_n,
-                                                        a.num_kb, bke);
+    a.ksplit = (dt == MOA_F32_SPLIT || L.fine_bytes == 0)
+                   ? 1
+                   : split_k_factor(static_cast<long>(a.tiles_m) * a.tiles_n, a.num_kb, bke);
     a.cnt = a.ksplit > 1 ? reinterpret_cast<int*>(base + L.cnt_off) : nullptr;
+    a.fine = a.ksplit > 1 ? reinterpret_cast<long long*>(base + L.fine_off) : nullptr;
 
     if (dt == MOA_F32_SPLIT) {
         auto* a16 = reinterpret_cast<__nv_bfloat16*>(a_sl);

@@ -56,7 +56,9 @@ struct SplitLayout {
     size_t ea_off, eb_off; // FP64-accuracy: per-row / per-column exponents (int32)
     size_t cmax_off;       // FP64-accuracy: per-column max |B| bit patterns (uint64)
     size_t cnt_off;        // FP64-accuracy, split K: finished-unit counters (int32,
-    size_t cnt_bytes;      // one per tile and epilogue warp; a multiple of 8 bytes)
+    size_t cnt_bytes;      // one per tile and epilogue warp), then, at fine_off, the
+    size_t fine_off;       // m x p int64 sums of the levels finer than the total's
+    size_t fine_bytes;     // grid; both 0 when the shape cannot take split K
     size_t total;
 };
 SplitLayout split_layout(int64_t m, int64_t n, int64_t p, moa_dtype dt, int S);

@@ -128,6 +128,22 @@ def test_f64_split_k_exact_and_deterministic(dt, m, n, p):
     assert np.all(np.abs(C1 - exact) <= scale * 2.0 ** -46 + np.abs(exact) * 2.0 ** -52)
 
 
+def test_f64_split_k_many_slices_ragged():
+    """Two output tiles and K = 32768: the K range is cut into 32 slices whose
+    int64 folds meet in C; an odd p takes the scalar (non-vector) fold and
+    convert paths.  Exact slice product of the oracle's digits, as above."""
+    dt = moa.MOA_F64_SPLIT_F32IN
+    beta, h = moa.DIGITS[dt]
+    A, B = inputs.normal_pair(200, 32768, 23, dtype=moa.in_dtype(dt), seed=11, scaled="rows")
+    C = _run(A, B, dt)
+    S = moa.DEFAULT_SLICES[dt]
+    eA, dA = oracle.slice_fixed(A.double().numpy(), 0, beta, S, headroom=h)
+    eB, dB = oracle.slice_fixed(B.double().numpy(), 1, beta, S, headroom=h)
+    exact = oracle.split_gemm_exact(dA, eA, dB, eB, beta, S)
+    scale = np.outer(2.0 ** eA.astype(np.float64), 2.0 ** eB.astype(np.float64))
+    assert np.all(np.abs(C - exact) <= scale * 2.0 ** -46 + np.abs(exact) * 2.0 ** -52)
+
+
 def test_f32_split_slices_match_oracle_split():
     """The FP32-accuracy mode's result equals the six-product sum of the
     oracle's BF16 slices up to FP32 accumulation error: each of the 6n terms
