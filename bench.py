@@ -907,6 +907,15 @@ def bench_library_rates(N=8192, reps=10):
                                      out_dtype=torch.bfloat16), reps))
     except Exception as e:  # report, do not hide
         out["cublas_fp8_e4m3"] = f"unavailable: {e}"
+    try:
+        # INT8 x INT8 -> INT32 (cuBLASLt through torch._int_mm): the rate an
+        # integer-digit slice variant would run at
+        ai = torch.randint(-16, 17, (N, N), generator=g, device="cuda", dtype=torch.int8)
+        bi = torch.randint(-16, 17, (N, N), generator=g, device="cuda", dtype=torch.int8)
+        out["cublas_int8"] = rate(N, best_ms(lambda: torch._int_mm(ai, bi), reps))
+        del ai, bi
+    except Exception as e:  # report, do not hide
+        out["cublas_int8"] = f"unavailable: {e}"
     n64 = N // 4
     a64, b64 = a32[:n64, :n64].double(), b32[:n64, :n64].double()
     out["cublas_fp64_n2048"] = rate(n64, best_ms(lambda: a64 @ b64, 3))
