@@ -989,8 +989,7 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
                                 phase ^= 1u;
                             }
                         }
-                        continue;
-                    }
+                    } else {
                     for (int kb = kb_lo; kb < kb_hi && ok; ++kb) {
                         for (int q = 0; q < np; ++q) {
                             int s, u;
@@ -1019,6 +1018,7 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
                             }
                         }
                     }
+                    }   // kb-major or one pair per stage
                 }
             }
             if (!ok) {
@@ -1087,8 +1087,7 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
                                     stage = 0;
                                     phase ^= 1u;
                                 }
-                                continue;
-                            }
+                            } else {
                             for (int q = 0; q < np; ++q) {
                                 if (!mbar_wait(&full[stage], phase, ctl, limit, status)) {
                                     ok = false;
@@ -1119,6 +1118,7 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
                                     phase ^= 1u;
                                 }
                             }
+                            }   // kb-major or one pair per stage
                         }
                         if (!ok) break;
                         mma_commit(&tfull[buf]);
