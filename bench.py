@@ -467,7 +467,7 @@ def cpu_baseline(N, dtype_name, seconds_target=8.0):
     flops = 2.0 * rows * N * N
     return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": int(used), "kind": "oracle",
             "sample": f"{rows} of {N} rows of the N={N} FP64 ONF GEMM (i-k-j loop, OpenMP over "
-                      f"rows), {dt:.2f} s", "host_cores": cores}
+                      f"rows), {dt:.2f} s", "host_cores": cores, "seconds": dt}
 
 
 def bench_grouped(steps, warmup, ws, stream, count=512, compare=True):
@@ -956,6 +956,7 @@ def run_reference(args, ws, rank):
     config["arm"] = "CPU oracle (FP64 i-k-j loop, OpenMP over rows) on sampled rows"
     line = {"impl": "reference", "metric": metric, "value": v, "unit": "TFLOP/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(x["seconds"] for x in per_step) / len(per_step),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config,
             "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": per_step[0]["cores"],
