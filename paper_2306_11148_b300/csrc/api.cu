@@ -175,11 +175,13 @@ size_t moa_gemm_workspace_size(int64_t m, int64_t n, int64_t p, moa_dtype dt, in
 
 int moa_gemm_ex(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const void* B,
                 void* C, int slices, void* ws, size_t ws_bytes, void* stream, moa_stats* stats) {
+    moa::TraceRange tr("moa_gemm_ex");
     return moa::gemm_ex(m, n, p, dt, A, B, C, slices, ws, ws_bytes,
                         static_cast<cudaStream_t>(stream), stats);
 }
 
 int moa_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const void* B, void* C) {
+    moa::TraceRange tr("moa_gemm");
     int rc = moa::validate(m, n, p, dt, A, B, C);
     if (rc != MOA_OK) return rc;
     const size_t need = moa::workspace_bytes(m, n, p, dt, 0);

@@ -335,6 +335,9 @@ int launch_cfg(int64_t m, int64_t n, int64_t p, const void* A, int64_t lda, cons
     cudaError_t e = cudaGetLastError();
     prof_end(s);
     if (e != cudaSuccess) return cuda_fail(e, "dense_tc_kernel launch");
+    log_msg(2, "dense %s m=%lld n=%lld p=%lld tile %dx%d stages %d grid %d tiles %ld",
+            ESIZE == 2 ? "bf16" : "tf32", static_cast<long long>(m), static_cast<long long>(n),
+            static_cast<long long>(p), Cfg::BLOCK_M, BLOCK_N, STAGES, grid, tiles);
     if (st) {
         st->block_m = Cfg::BLOCK_M;
         st->block_n = BLOCK_N;

@@ -425,6 +425,7 @@ int launch_kernel(uint8_t* dev, const Layout& L, int grid, cudaStream_t s) {
     cudaError_t e = cudaGetLastError();
     prof_end(s);
     if (e != cudaSuccess) return cuda_fail(e, "grouped_tc_kernel launch");
+    log_msg(2, "grouped persistent launch: grid %d", grid);
     return MOA_OK;
 }
 
@@ -590,6 +591,7 @@ size_t moa_gemm_grouped_workspace_size(int count, const moa_gemm_desc* d) {
 }
 
 int moa_gemm_grouped(int count, const moa_gemm_desc* d, void* ws, size_t ws_bytes, void* stream) {
+    moa::TraceRange tr("moa_gemm_grouped");
     if (count < 0) return moa::fail(MOA_ERR_ARG, "negative count");
     if (count == 0) return MOA_OK;
     if (d == nullptr) return moa::fail(MOA_ERR_ARG, "descriptor array is NULL");
@@ -647,6 +649,7 @@ size_t moa_gemm_batched_workspace_size(int batch, int64_t m, int64_t n, int64_t 
 int moa_gemm_batched(int batch, int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A,
                      int64_t stride_a, const void* B, int64_t stride_b, void* C, int64_t stride_c,
                      void* ws, size_t ws_bytes, void* stream) {
+    moa::TraceRange tr("moa_gemm_batched");
     std::vector<moa_gemm_desc> d;
     const int rc = moa::batched_descs(batch, m, n, p, dt, A, stride_a, B, stride_b, C, stride_c, d);
     if (rc != MOA_OK) return rc;

@@ -32,6 +32,22 @@ void set_error(const std::string& msg);
 int fail(int status, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 
+// ------------------------------------------------------------------ logging / tracing
+// MOA_LOG=0..3 (default 0): 1 = errors (every fail / cuda_fail message),
+// 2 = the plan of every launch (kernel, tile, grid), 3 = more.  Lines go to
+// stderr prefixed "[moa] ".
+int log_level();
+void log_msg(int level, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+// NVTX ranges (no cost unless a profiler tool is attached).
+void trace_push(const char* name);
+void trace_pop();
+struct TraceRange {
+    explicit TraceRange(const char* name) { trace_push(name); }
+    ~TraceRange() { trace_pop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
+
 // Optional per-thread profiling events (moa_profile_events): recorded on the
 // call's stream immediately before and after the main GEMM kernel.
 void prof_begin(cudaStream_t s);

@@ -88,6 +88,7 @@ extern "C" {
 
 int moa_kronecker(int64_t m, int64_t n, int64_t p, int64_t q, moa_dtype dt, const void* A,
                   const void* B, void* C, void* stream) {
+    moa::TraceRange tr("moa_kronecker");
     int ie, oe;
     int rc = moa::elem_sizes(dt, &ie, &oe);
     if (rc != MOA_OK) return rc;
@@ -124,6 +125,7 @@ int moa_kronecker(int64_t m, int64_t n, int64_t p, int64_t q, moa_dtype dt, cons
 
 int moa_hadamard(int64_t m, int64_t n, moa_dtype dt, const void* A, const void* B, void* C,
                  void* stream) {
+    moa::TraceRange tr("moa_hadamard");
     int ie, oe;
     int rc = moa::elem_sizes(dt, &ie, &oe);
     if (rc != MOA_OK) return rc;

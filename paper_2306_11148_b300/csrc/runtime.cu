@@ -6,6 +6,9 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <nvtx3/nvToolsExt.h>
+
+#include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -51,13 +54,37 @@ void prof_end(cudaStream_t s) {
 
 int fail(int status, const std::string& msg) {
     g_last_error = msg;
+    log_msg(1, "error %d: %s", status, msg.c_str());
     return status;
 }
 
 int cuda_fail(cudaError_t e, const char* what) {
     g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    log_msg(1, "error %d: %s", MOA_ERR_CUDA, g_last_error.c_str());
     return MOA_ERR_CUDA;
 }
+
+int log_level() {
+    static const int level = [] {
+        const char* e = std::getenv("MOA_LOG");
+        const long v = e ? std::strtol(e, nullptr, 10) : 0;
+        return static_cast<int>(v < 0 ? 0 : (v > 3 ? 3 : v));
+    }();
+    return level;
+}
+
+void log_msg(int level, const char* fmt, ...) {
+    if (level > log_level()) return;
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    std::fprintf(stderr, "[moa] %s\n", buf);
+}
+
+void trace_push(const char* name) { nvtxRangePushA(name); }
+void trace_pop() { nvtxRangePop(); }
 
 int* device_status_ptr() {
     const int d = current_device();

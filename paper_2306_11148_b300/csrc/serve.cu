@@ -321,6 +321,8 @@ void scheduler(moa_server* s) {
         s->inflight_peak = std::max<int>(s->inflight_peak, static_cast<int>(s->inflight.size()));
         lk.unlock();
 
+        TraceRange tr("moa_serve batch");
+        log_msg(3, "serve batch of %zu requests, %zu in flight", batch.size(), s->inflight.size());
         std::vector<int> rcs(batch.size(), MOA_OK);
         if (grouped) {
             cudaStream_t gs = s->streams[gstream];

@@ -1391,6 +1391,9 @@ static int launch_split_cfg(const SplitArgs& a, const CUtensorMap& tmA, const CU
     cudaError_t e = cudaGetLastError();
     prof_end(s);
     if (e != cudaSuccess) return cuda_fail(e, "split_gemm_kernel launch");
+    log_msg(2, "split mode %d fmt %d m=%lld n=%lld p=%lld tile %dx%d levels %d K slices %d grid %d "
+            "tiles %ld", MODE, FMT, static_cast<long long>(a.m), static_cast<long long>(a.n),
+            static_cast<long long>(a.p), kBM, BN, a.levels, SK ? a.ksplit : 1, grid, tiles);
     if (st) {
         st->block_m = kBM;
         st->block_n = BN;

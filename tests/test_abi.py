@@ -136,3 +136,21 @@ def test_binding_refuses_mismatched_tensors(L):
         moa.check_tensors(A, B, None, moa.MOA_F32_TF32)
     with pytest.raises(ValueError):
         moa.check_tensors(A, B[:5], None, moa.MOA_F32_TF32)
+
+
+def test_log_level_reports_host_errors(L):
+    """MOA_LOG=1 prints every error message to stderr (argument errors are
+    found on the host, so this needs no GPU); unset, nothing is printed."""
+    import subprocess
+    import sys
+    code = ("import ctypes; from paper_2306_11148_b300 import moa; "
+            "rc = moa.moa_gemm_ex(8, 8, 8, 77, 256, 512, 1024, 0, None, 0, None, None); "
+            "print(rc)")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for level, expect in (("1", True), ("0", False)):
+        env = dict(os.environ, MOA_LOG=level)
+        r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True,
+                           text=True, timeout=300)
+        assert r.returncode == 0, r.stderr
+        assert r.stdout.strip() == str(moa.MOA_ERR_DTYPE)
+        assert ("[moa] error -2:" in r.stderr) == expect, r.stderr
