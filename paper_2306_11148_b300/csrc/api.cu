@@ -91,8 +91,27 @@ size_t workspace_bytes(int64_t m, int64_t n, int64_t p, moa_dtype dt, int slices
     return 0;
 }
 
+int gemm_ex_impl(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const void* B,
+                 void* C, int slices, void* ws, size_t ws_bytes, cudaStream_t s, moa_stats* st);
+
 int gemm_ex(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const void* B, void* C,
             int slices, void* ws, size_t ws_bytes, cudaStream_t s, moa_stats* st) {
+    if (canary_enabled() && ws && m > 0 && n > 0 && p > 0) {
+        const size_t need = (workspace_bytes(m, n, p, dt, slices) + kAlign - 1) / kAlign * kAlign;
+        if (ws_bytes >= need + kCanaryBytes) {
+            void* guard = static_cast<uint8_t*>(ws) + need;
+            int rc = canary_arm(guard, s);
+            if (rc != MOA_OK) return rc;
+            rc = gemm_ex_impl(m, n, p, dt, A, B, C, slices, ws, need, s, st);
+            const int rc2 = canary_check(guard, s);
+            return rc != MOA_OK ? rc : rc2;
+        }
+    }
+    return gemm_ex_impl(m, n, p, dt, A, B, C, slices, ws, ws_bytes, s, st);
+}
+
+int gemm_ex_impl(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const void* B,
+                 void* C, int slices, void* ws, size_t ws_bytes, cudaStream_t s, moa_stats* st) {
     int rc = validate(m, n, p, dt, A, B, C);
     if (rc != MOA_OK) return rc;
     if (st) {
@@ -184,7 +203,10 @@ int moa_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const
     moa::TraceRange tr("moa_gemm");
     int rc = moa::validate(m, n, p, dt, A, B, C);
     if (rc != MOA_OK) return rc;
-    const size_t need = moa::workspace_bytes(m, n, p, dt, 0);
+    size_t need = moa::workspace_bytes(m, n, p, dt, 0);
+    // room for the guard bytes of MOA_DEBUG_CANARY
+    if (need > 0 && moa::canary_enabled())
+        need = (need + moa::kAlign - 1) / moa::kAlign * moa::kAlign + moa::kCanaryBytes;
     void* ws = nullptr;
     if (need > 0) {
         int d = 0;

@@ -38,6 +38,14 @@ int cuda_fail(cudaError_t e, const char* what);
 // stderr prefixed "[moa] ".
 int log_level();
 void log_msg(int level, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+// MOA_DEBUG_CANARY=1: every call with at least kCanaryBytes of workspace past
+// what it needs fills those bytes with a pattern before its kernels and checks
+// them after (a one-block kernel that records kDevCanary in the status word,
+// reported by moa_sync_status), catching writes past the used workspace.
+constexpr size_t kCanaryBytes = 256;
+bool canary_enabled();
+int canary_arm(void* guard, cudaStream_t s);
+int canary_check(const void* guard, cudaStream_t s);
 // NVTX ranges (no cost unless a profiler tool is attached).
 void trace_push(const char* name);
 void trace_pop();

@@ -8,7 +8,7 @@
 namespace moa {
 
 // Device status codes written into the per-device status word.
-enum : int { kDevOk = 0, kDevTimeout = 1, kDevNonFinite = 2 };
+enum : int { kDevOk = 0, kDevTimeout = 1, kDevNonFinite = 2, kDevCanary = 3 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));

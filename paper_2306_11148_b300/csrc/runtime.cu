@@ -83,6 +83,37 @@ void log_msg(int level, const char* fmt, ...) {
     std::fprintf(stderr, "[moa] %s\n", buf);
 }
 
+namespace {
+constexpr unsigned char kCanaryByte = 0xA5;
+__global__ void canary_check_kernel(const unsigned char* guard, int n, int* status) {
+    bool bad = false;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) bad |= guard[i] != kCanaryByte;
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicCAS(status, kDevOk, kDevCanary);
+}
+}  // namespace
+
+bool canary_enabled() {
+    static const bool on = [] {
+        const char* e = std::getenv("MOA_DEBUG_CANARY");
+        return e && std::strtol(e, nullptr, 10) != 0;
+    }();
+    return on;
+}
+
+int canary_arm(void* guard, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(guard, kCanaryByte, kCanaryBytes, s);
+    return e == cudaSuccess ? MOA_OK : cuda_fail(e, "cudaMemsetAsync(canary)");
+}
+
+int canary_check(const void* guard, cudaStream_t s) {
+    int* status = launch_status_ptr();
+    if (!status) return MOA_ERR_CUDA;
+    canary_check_kernel<<<1, 64, 0, s>>>(static_cast<const unsigned char*>(guard),
+                                          static_cast<int>(kCanaryBytes), status);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MOA_OK : cuda_fail(e, "canary_check_kernel launch");
+}
+
 void trace_push(const char* name) { nvtxRangePushA(name); }
 void trace_pop() { nvtxRangePop(); }
 
@@ -377,6 +408,9 @@ int moa_sync_status(void* stream) {
             return moa::fail(MOA_ERR_TIMEOUT, "a device pipeline wait exceeded its time limit");
         if (v == moa::kDevNonFinite)
             return moa::fail(MOA_ERR_NONFINITE, "split pre-pass found a NaN or Inf input");
+        if (v == moa::kDevCanary)
+            return moa::fail(MOA_ERR_CUDA, "workspace guard bytes past the used workspace were "
+                                           "overwritten (MOA_DEBUG_CANARY)");
         return moa::fail(MOA_ERR_CUDA, "unknown device status");
     }
     return MOA_OK;

@@ -40,3 +40,36 @@ def test_selftest_rejects_bad_limits():
     L = moa.lib()
     assert L.moa_selftest_wait_timeout(0, None) == moa.MOA_ERR_ARG
     assert L.moa_selftest_wait_timeout(20_000_000_000, None) == moa.MOA_ERR_ARG
+
+
+@pytest.mark.gpu
+def test_workspace_canary_stays_intact():
+    """MOA_DEBUG_CANARY=1 (read once per process, so in a child process):
+    every mode's plain moa_gemm call guards the bytes past its workspace and
+    checks them after its kernels; none may be overwritten, and the results
+    stay exact on integer inputs."""
+    import os
+    import subprocess
+    import sys
+    code = r'''
+import numpy as np, torch, oracle
+from paper_2306_11148_b300 import inputs, moa
+L = moa.lib()
+for dt in (moa.MOA_F32_TF32, moa.MOA_BF16, moa.MOA_F32_SPLIT, moa.MOA_F64_SPLIT_F32IN,
+           moa.MOA_F64_SPLIT_F64IN_E4M3):
+    for (m, n, p) in ((33, 127, 129), (70, 4200, 140), (257, 1000, 200)):
+        A, B = inputs.integer_pair(m, n, p, dtype=moa.in_dtype(dt), seed=m + n)
+        Ad, Bd = A.cuda(), B.cuda()
+        C = torch.empty((m, p), dtype=moa.out_dtype(dt), device="cuda")
+        moa.check(L.moa_gemm(m, n, p, dt, Ad.data_ptr(), Bd.data_ptr(), C.data_ptr()))
+        moa.check(L.moa_sync_status(None))
+        assert np.array_equal(C.double().cpu().numpy(),
+                              oracle.gemm(A.double().numpy(), B.double().numpy())), (dt, m, n, p)
+print("canary ok")
+'''
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, MOA_DEBUG_CANARY="1", PYTHONPATH=root)
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True,
+                       text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "canary ok" in r.stdout

@@ -69,6 +69,19 @@ def test_integer_inputs_bit_exact(dt, m, n, p):
 
 
 @pytest.mark.parametrize("dt", ALL_MODES, ids=lambda d: NAMES[d])
+def test_small_shape_sweep_bit_exact(dt):
+    """48 shapes drawn (seed 0) from m, n, p in 1..40 -- every tile is ragged
+    in every direction -- on integer inputs: bit-exact against the oracle."""
+    rng = np.random.default_rng(0)
+    for m, n, p in rng.integers(1, 41, size=(48, 3)):
+        m, n, p = int(m), int(n), int(p)
+        A, B = inputs.integer_pair(m, n, p, dtype=moa.in_dtype(dt), seed=m * 1600 + n * 40 + p)
+        C = _run(A, B, dt)
+        ref = oracle.gemm(A.double().numpy(), B.double().numpy())
+        assert np.array_equal(C, ref), f"{m}x{n}x{p}: max diff {np.abs(C - ref).max()}"
+
+
+@pytest.mark.parametrize("dt", ALL_MODES, ids=lambda d: NAMES[d])
 @pytest.mark.parametrize("m,n,p", SHAPES)
 def test_uniform_inputs_within_tolerance(dt, m, n, p):
     A, B = inputs.uniform_pair(m, n, p, dtype=moa.in_dtype(dt), seed=1)
