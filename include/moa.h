@@ -310,7 +310,8 @@ int moa_gemm_f32split_noalloc(int64_t m, int64_t n, int64_t p, const float* A, c
 /* Synchronises `stream`, then returns and clears the current device's
  * status word: MOA_OK, MOA_ERR_TIMEOUT (a kernel gave up on a pipeline
  * wait), MOA_ERR_NONFINITE (a split pre-pass saw NaN/Inf) or MOA_ERR_CUDA
- * (the synchronisation itself failed). */
+ * (the synchronisation itself failed, or, with MOA_DEBUG_CANARY=1 set in
+ * the environment, a call wrote into the guard bytes past its workspace). */
 int moa_sync_status(void* stream);
 
 /* Thread-local message describing the last non-OK status of this thread. */
