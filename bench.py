@@ -465,9 +465,17 @@ def cpu_baseline(N, dtype_name, seconds_target=8.0):
             break
         rows = min(N, rows * 4)
     flops = 2.0 * rows * N * N
+    # the same loop on one thread, on a quarter of the rows (bounded)
+    rows1 = max(1, rows // 4)
+    idx1 = inputs.sample_rows(N, rows1, seed=1)
+    t1 = time.perf_counter()
+    oracle.gemm_omp(A[idx1], B, threads=1)
+    dt1 = time.perf_counter() - t1
     return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": int(used), "kind": "oracle",
             "sample": f"{rows} of {N} rows of the N={N} FP64 ONF GEMM (i-k-j loop, OpenMP over "
-                      f"rows), {dt:.2f} s", "host_cores": cores, "seconds": dt}
+                      f"rows), {dt:.2f} s", "host_cores": cores, "seconds": dt,
+            "single_thread": {"value": 2.0 * rows1 * N * N / dt1 / 1e12, "unit": "TFLOP/s",
+                              "sample": f"{rows1} rows on 1 thread, {dt1:.2f} s"}}
 
 
 def bench_grouped(steps, warmup, ws, stream, count=512, compare=True):
@@ -960,7 +968,8 @@ def run_reference(args, ws, rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config,
             "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": per_step[0]["cores"],
-                             "kind": "oracle", "sample": per_step[0]["sample"]},
+                             "kind": "oracle", "sample": per_step[0]["sample"],
+                             "single_thread": per_step[0].get("single_thread")},
             "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
