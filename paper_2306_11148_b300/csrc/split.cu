@@ -1558,7 +1558,7 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
         int* eB = reinterpret_cast<int*>(base + L.eb_off);
         void* cmax = base + L.cmax_off;
         const int beta = e4m3 ? kBetaE4M3 : kBeta;
-        const int h = e4m3 ? kHeadroomE4M3 : 0;
+        const int h = e4m3 ? kHeadroomE4M3 : kHeadroomBF16;
         if (ceil_div(n, 256) * ceil_div(p, 256) > (1L << 30))
             return fail(MOA_ERR_ARG, "n x p too large for the column-max grid");
         cudaError_t e = cudaMemsetAsync(cmax, 0, static_cast<size_t>(p) * 8, s);

@@ -16,8 +16,14 @@ inline bool is_split(moa_dtype dt) {
 // Digit radix 2^kBeta of the FP64-accuracy mode and its slice-count limits.
 // Base 128 (not 256): each digit product is 4x smaller, so the exact FP32
 // accumulation chunks are 4x longer and their flushes hide behind the MMAs;
-// 7 digits (28 slice products) keep 49 bits per operand.
+// 7 digits (28 slice products) keep 48 bits per operand with one headroom
+// bit: the group exponent is one above the maximum's, so the top digit is at
+// most 64 in magnitude like the others, every per-k product of a level is
+// bounded by (L + 1) 2^12, and the exact chunks are 1.25-4x longer than
+// without it (60 instead of 90 chunk flushes per 128 x 256 tile at n = 8192;
+// each flush converts 32768 FP32 sums to integers).
 constexpr int kBeta = 7;
+constexpr int kHeadroomBF16 = 1;
 constexpr int kMinSlices = 3;
 constexpr int kMaxSlices = 8;
 constexpr int kDefaultSlices = 7;

@@ -53,7 +53,7 @@ MODES = {
 # FP64-accuracy modes (FP64 output) and their digit format: (radix bits, headroom bits)
 F64_ACCURATE = (MOA_F64, MOA_F64_SPLIT_F32IN, MOA_F64_SPLIT_F64IN, MOA_F64_SPLIT_F32IN_E4M3,
                 MOA_F64_SPLIT_F64IN_E4M3)
-DIGITS = {MOA_F64_SPLIT_F32IN: (7, 0), MOA_F64_SPLIT_F64IN: (7, 0),
+DIGITS = {MOA_F64_SPLIT_F32IN: (7, 1), MOA_F64_SPLIT_F64IN: (7, 1),
           MOA_F64_SPLIT_F32IN_E4M3: (5, 1), MOA_F64_SPLIT_F64IN_E4M3: (5, 1)}
 DEFAULT_SLICES = {MOA_F32_SPLIT: 3, MOA_F64_SPLIT_F32IN: 7, MOA_F64_SPLIT_F64IN: 7,
                   MOA_F64_SPLIT_F32IN_E4M3: 10, MOA_F64_SPLIT_F64IN_E4M3: 10}
