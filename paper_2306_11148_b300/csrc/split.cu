@@ -11,10 +11,10 @@
 //   products with t + u <= 2 are summed into one FP32 accumulator.
 // * FP64 accuracy (error-free digit slicing in the manner of Ozaki, Ogita,
 //   Oishi & Rump 2012): each row i of A gets the exponent eA_i with
-//   max_k |A[i,k]| in [2^(eA_i - 1), 2^eA_i), each column j of B likewise eB_j;
-//   x * 2^(7S - e) is rounded once to an integer D and written as S balanced
-//   base-128 digits (|d_0| <= 128, d_s in [-64, 64) for s >= 1), each exactly
-//   a BF16 value.  Level L = s + t of the triangular product (s + t <= S - 1)
+//   max_k |A[i,k]| in [2^(eA_i - 1 - h), 2^(eA_i - h)) (h = 1 headroom bit),
+//   each column j of B likewise eB_j; x * 2^(7S - e) is rounded once to an
+//   integer D and written as S balanced base-128 digits (|d_0| <= 64 with the
+//   headroom bit, d_s in [-64, 64) for s >= 1), each exactly a BF16 value.  Level L = s + t of the triangular product (s + t <= S - 1)
 //   is summed over chunks of K short enough that every FP32 partial sum is an
 //   integer below 2^24, hence exact; each chunk is flushed into an int32
 //   running sum, folded at the level's end into an int64 fixed-point total
