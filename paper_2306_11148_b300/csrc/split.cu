@@ -677,6 +677,10 @@ struct SplitArgs {
     // int64 adds, order-free), and cnt[tile * epilogue warps + warp] counts
     // the units that have finished a warp's region (zeroed before launch).
     int ksplit;
+    // and the levels of a tile into `lgroups` groups (bit L of lmask[g] set:
+    // level L belongs to group g), each run as a separate work unit
+    int lgroups;
+    uint32_t lmask[kMaxLevels];
     int* cnt;
     // split K: levels finer than the total's grid (shift below 0) add their
     // exact sums, scaled to the finest level, into fine[m x p] instead of
@@ -688,16 +692,20 @@ struct SplitArgs {
 // the split-K kernel variant; without it every unit is a whole tile).
 template <bool SK>
 __device__ __forceinline__ void split_unit(const SplitArgs& a, int u, int& t, int& kb_lo,
-                                           int& kb_hi) {
+                                           int& kb_hi, uint32_t& lmask) {
     if constexpr (!SK) {
         t = u;
         kb_lo = 0;
         kb_hi = a.num_kb;
+        lmask = 0xFFFFFFFFu;
         return;
     }
     const int ks = a.ksplit;
-    t = u / ks;
-    const int sl = u - t * ks;
+    const int lg = a.lgroups;
+    t = u / (ks * lg);
+    const int rem = u - t * (ks * lg);
+    const int sl = rem / lg;
+    lmask = a.lmask[rem - sl * lg];
     kb_lo = static_cast<int>(static_cast<long long>(sl) * a.num_kb / ks);
     kb_hi = static_cast<int>(static_cast<long long>(sl + 1) * a.num_kb / ks);
 }
@@ -949,7 +957,7 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
-    const int num_units = args.tiles_m * args.tiles_n * (SK ? args.ksplit : 1);
+    const int num_units = args.tiles_m * args.tiles_n * (SK ? args.ksplit * args.lgroups : 1);
 
     if (warp == 0) {
         if (lane == 0) {
@@ -960,9 +968,12 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
             bool ok = true;
             for (int u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
                 int t, kb_lo, kb_hi, tm, tn;
-                split_unit<SK>(args, u, t, kb_lo, kb_hi);
+                uint32_t lmask;
+                split_unit<SK>(args, u, t, kb_lo, kb_hi, lmask);
                 split_tile_coords(t, args.tiles_m, args.tiles_n, args.group_m, tm, tn);
                 for (int L = 0; L < args.levels && ok; ++L) {
+                    if constexpr (SK)
+                        if (!((lmask >> L) & 1u)) continue;
                     const int np = level_pairs(args, L);
                     if constexpr (Cfg::kKB) {
                         // kb-major: the three slices of A and of B of K block kb
@@ -1042,8 +1053,11 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
             bool ok = true;
             for (int u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
                 int t, kb_lo, kb_hi;
-                split_unit<SK>(args, u, t, kb_lo, kb_hi);
+                uint32_t lmask;
+                split_unit<SK>(args, u, t, kb_lo, kb_hi, lmask);
                 for (int L = 0; L < args.levels && ok; ++L) {
+                    if constexpr (SK)
+                        if (!((lmask >> L) & 1u)) continue;
                     const int np = level_pairs(args, L);
                     const int kc = args.kc[L];
                     for (int kb0 = kb_lo; kb0 < kb_hi && ok; kb0 += kc, ++cnt) {
@@ -1143,7 +1157,12 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
         constexpr bool atomic = SK;
         for (int u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
             int t, kb_lo, kb_hi, tm, tn;
-            split_unit<SK>(args, u, t, kb_lo, kb_hi);
+            uint32_t lmask;
+            split_unit<SK>(args, u, t, kb_lo, kb_hi, lmask);
+            // the unit's last level (its folds end there)
+            const int l_last =
+                SK ? 31 - __clz(static_cast<int>(lmask & ((1u << args.levels) - 1u)))
+                   : args.levels - 1;
             split_tile_coords(t, args.tiles_m, args.tiles_n, args.group_m, tm, tn);
             const int64_t row = static_cast<int64_t>(tm) * kBM + q * 32 + lane;
             const int64_t col_base = static_cast<int64_t>(tn) * BN + h * kCols;
@@ -1161,6 +1180,8 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
             const uint32_t r_base = tmem_base + lane_base + 256u + static_cast<uint32_t>(h * kCols);
             bool r_valid = false;   // kModeF64Tmem: TMEM level sums hold data
             for (int L = 0; L < args.levels && ok; ++L) {
+                if constexpr (SK)
+                    if (!((lmask >> L) & 1u)) continue;
                 const int kc = args.kc[L];
                 int since_fold = 0;
                 for (int kb0 = kb_lo; kb0 < kb_hi; kb0 += kc, ++cnt) {
@@ -1221,7 +1242,7 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
                         // of the tile converts once to FP64 and scales by
                         // 2^(eA_i + eB_j - beta(S+1) + drop).
                         const int sh = args.beta * (args.S - 1 - L) - args.drop;
-                        const bool last = level_end && L == args.levels - 1;
+                        const bool last = level_end && L == l_last;
                         const int64_t row0 = static_cast<int64_t>(tm) * kBM + q * 32;
                         const int64_t rl = args.m - row0;
                         const int rows_left = rl < 0 ? 0 : (rl > 32 ? 32 : static_cast<int>(rl));
@@ -1258,7 +1279,7 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
                                                           (warp - 2)],
                                                 1);
                             old = __shfl_sync(0xffffffffu, old, 0);
-                            if (old == args.ksplit - 1) {
+                            if (old == args.ksplit * args.lgroups - 1) {
                                 __threadfence();
                                 const int64_t left = args.p - col_base;
                                 convert_region(reinterpret_cast<long long*>(args.C), args.fine,
@@ -1385,15 +1406,17 @@ static int launch_split_cfg(const SplitArgs& a, const CUtensorMap& tmA, const CU
         attr_set = true;
     }
     const long tiles = static_cast<long>(a.tiles_m) * a.tiles_n;
-    const int grid = static_cast<int>(std::min<long>(tiles * (SK ? a.ksplit : 1), num_sms()));
+    const int grid =
+        static_cast<int>(std::min<long>(tiles * (SK ? a.ksplit * a.lgroups : 1), num_sms()));
     prof_begin(s);
     split_gemm_kernel<BN, MODE, FMT, SK><<<grid, Cfg::kThreads, Cfg::kSmem, s>>>(tmA, tmB, a);
     cudaError_t e = cudaGetLastError();
     prof_end(s);
     if (e != cudaSuccess) return cuda_fail(e, "split_gemm_kernel launch");
-    log_msg(2, "split mode %d fmt %d m=%lld n=%lld p=%lld tile %dx%d levels %d K slices %d grid %d "
-            "tiles %ld", MODE, FMT, static_cast<long long>(a.m), static_cast<long long>(a.n),
-            static_cast<long long>(a.p), kBM, BN, a.levels, SK ? a.ksplit : 1, grid, tiles);
+    log_msg(2, "split mode %d fmt %d m=%lld n=%lld p=%lld tile %dx%d levels %d K slices %d "
+            "level groups %d grid %d tiles %ld", MODE, FMT, static_cast<long long>(a.m),
+            static_cast<long long>(a.n), static_cast<long long>(a.p), kBM, BN, a.levels,
+            SK ? a.ksplit : 1, SK ? a.lgroups : 1, grid, tiles);
     if (st) {
         st->block_m = kBM;
         st->block_n = BN;
@@ -1448,6 +1471,31 @@ static int split_k_factor(long tiles, int num_kb, int bk) {
         if (tiles * 2 <= sms) ks = std::min(sms / tiles, static_cast<long>(num_kb) * bk / 1024);
     }
     return static_cast<int>(std::max(1L, std::min({ks, static_cast<long>(num_kb), 64L})));
+}
+
+// Level groups of the FP64-accuracy slice GEMM: when the (tile, K slice)
+// units still fill at most half of the SMs, the S levels of a tile (level L
+// holds L + 1 slice products) are dealt longest first onto up to S groups,
+// each a separate work unit, so that the units fill the SMs.  Returns the
+// group count and sets mask[g] (bit L: level L in group g).
+static int split_level_groups(long units, int S, uint32_t* mask) {
+    const long sms = num_sms();
+    int G = 1;
+    if (units * 2 <= sms) G = static_cast<int>(std::min<long>(S, sms / units));
+    if (G <= 1) {
+        mask[0] = 0xFFFFFFFFu;
+        return 1;
+    }
+    int load[kMaxLevels] = {0};
+    for (int g = 0; g < G; ++g) mask[g] = 0;
+    for (int L = S - 1; L >= 0; --L) {   // largest level (L + 1 products) first
+        int best = 0;
+        for (int g = 1; g < G; ++g)
+            if (load[g] < load[best]) best = g;
+        load[best] += L + 1;
+        mask[best] |= 1u << L;
+    }
+    return G;
 }
 
 // Exponent and digit pre-passes of the FP64-accuracy modes for input type T.
@@ -1534,8 +1582,14 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
     a.ksplit = (dt == MOA_F32_SPLIT || L.fine_bytes == 0)
                    ? 1
                    : split_k_factor(static_cast<long>(a.tiles_m) * a.tiles_n, a.num_kb, bke);
-    a.cnt = a.ksplit > 1 ? reinterpret_cast<int*>(base + L.cnt_off) : nullptr;
-    a.fine = a.ksplit > 1 ? reinterpret_cast<long long*>(base + L.fine_off) : nullptr;
+    a.lgroups = 1;
+    a.lmask[0] = 0xFFFFFFFFu;
+    if (dt != MOA_F32_SPLIT && L.fine_bytes > 0)
+        a.lgroups = split_level_groups(static_cast<long>(a.tiles_m) * a.tiles_n * a.ksplit, S,
+                                       a.lmask);
+    const bool split_units = a.ksplit > 1 || a.lgroups > 1;
+    a.cnt = split_units ? reinterpret_cast<int*>(base + L.cnt_off) : nullptr;
+    a.fine = split_units ? reinterpret_cast<long long*>(base + L.fine_off) : nullptr;
 
     if (dt == MOA_F32_SPLIT) {
         auto* a16 = reinterpret_cast<__nv_bfloat16*>(a_sl);
@@ -1566,11 +1620,11 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
         if (dt == MOA_F64_SPLIT_F64IN || dt == MOA_F64_SPLIT_F64IN_E4M3)
             digit_prepasses<double>(L, m, n, p, static_cast<const double*>(A),
                                     static_cast<const double*>(B), beta, h, eA, eB, cmax, a_sl,
-                                    b_sl, status, s, a.ksplit > 1 ? C : nullptr, a.cnt);
+                                    b_sl, status, s, split_units ? C : nullptr, a.cnt);
         else
             digit_prepasses<float>(L, m, n, p, static_cast<const float*>(A),
                                    static_cast<const float*>(B), beta, h, eA, eB, cmax, a_sl, b_sl,
-                                   status, s, a.ksplit > 1 ? C : nullptr, a.cnt);
+                                   status, s, split_units ? C : nullptr, a.cnt);
         kernels += 3;   // the column-max clear, the exponent pass and the digit pass
         a.f64 = 1;
         a.levels = S;
@@ -1612,7 +1666,7 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
                           static_cast<uint64_t>(L.ldb), static_cast<uint64_t>(b_plane), 128,
                           static_cast<uint32_t>(bn));
         if (rc != MOA_OK) return rc;
-        if (a.ksplit > 1)
+        if (split_units)
             rc = bn == 256   ? launch_split_cfg<256, kModeF64Tmem, kFmtE4M3, true>(a, tmA, tmB, s, st)
                  : bn == 192 ? launch_split_cfg<192, kModeF64Reg, kFmtE4M3, true>(a, tmA, tmB, s, st)
                              : launch_split_cfg<128, kModeF64Reg, kFmtE4M3, true>(a, tmA, tmB, s, st);
@@ -1646,7 +1700,7 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
                           static_cast<uint64_t>(L.ldb) * 2, static_cast<uint64_t>(b_plane) * 2, 64,
                           kBK);
         if (rc != MOA_OK) return rc;
-        if (a.ksplit > 1)
+        if (split_units)
             rc = bn == 256   ? launch_split_cfg<256, kModeF64Tmem, kFmtBF16, true>(a, tmA, tmB, s, st)
                  : bn == 192 ? launch_split_cfg<192, kModeF64Reg, kFmtBF16, true>(a, tmA, tmB, s, st)
                              : launch_split_cfg<128, kModeF64Reg, kFmtBF16, true>(a, tmA, tmB, s, st);
