@@ -686,18 +686,21 @@ struct SplitArgs {
     // exact sums, scaled to the finest level, into fine[m x p] instead of
     // rounding them into C; the region's last unit rounds them in once.
     long long* fine;
+    // FP32-accuracy split K: slice s's partial tile at part[s * m * p + i * p + j]
+    float* part;
 };
 
 // Work unit u: tile t and the K blocks [kb_lo, kb_hi) of its K slice (SK:
 // the split-K kernel variant; without it every unit is a whole tile).
 template <bool SK>
 __device__ __forceinline__ void split_unit(const SplitArgs& a, int u, int& t, int& kb_lo,
-                                           int& kb_hi, uint32_t& lmask) {
+                                           int& kb_hi, uint32_t& lmask, int* slice = nullptr) {
     if constexpr (!SK) {
         t = u;
         kb_lo = 0;
         kb_hi = a.num_kb;
         lmask = 0xFFFFFFFFu;
+        if (slice) *slice = 0;
         return;
     }
     const int ks = a.ksplit;
@@ -706,6 +709,7 @@ __device__ __forceinline__ void split_unit(const SplitArgs& a, int u, int& t, in
     const int rem = u - t * (ks * lg);
     const int sl = rem / lg;
     lmask = a.lmask[rem - sl * lg];
+    if (slice) *slice = sl;
     kb_lo = static_cast<int>(static_cast<long long>(sl) * a.num_kb / ks);
     kb_hi = static_cast<int>(static_cast<long long>(sl + 1) * a.num_kb / ks);
 }
@@ -1156,9 +1160,9 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
         bool ok = true;
         constexpr bool atomic = SK;
         for (int u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
-            int t, kb_lo, kb_hi, tm, tn;
+            int t, kb_lo, kb_hi, tm, tn, kslice;
             uint32_t lmask;
-            split_unit<SK>(args, u, t, kb_lo, kb_hi, lmask);
+            split_unit<SK>(args, u, t, kb_lo, kb_hi, lmask, &kslice);
             // the unit's last level (its folds end there)
             const int l_last =
                 SK ? 31 - __clz(static_cast<int>(lmask & ((1u << args.levels) - 1u)))
@@ -1298,6 +1302,55 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
                 }
             }
             if (!ok) break;
+            // ---------------- FP32 mode, split K: this unit's partial tile goes to
+            // the workspace; the last unit of the warp's region sums the slices
+            // in slice order (deterministic) into C
+            if constexpr (!F64 && SK) {
+                const int64_t plane = args.m * args.p;
+                if (row_ok) {   // the lane's row of the partial tile
+                    float* prow = args.part + kslice * plane + row * args.p;
+                    if (args.vec_ok && col_base + 64 <= args.p) {
+                        float4* dst = reinterpret_cast<float4*>(prow + col_base);
+#pragma unroll
+                        for (int v = 0; v < 16; ++v)
+                            dst[v] = make_float4(__uint_as_float(acc[4 * v]),
+                                                 __uint_as_float(acc[4 * v + 1]),
+                                                 __uint_as_float(acc[4 * v + 2]),
+                                                 __uint_as_float(acc[4 * v + 3]));
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 64; ++i)
+                            if (col_base + i < args.p) prow[col_base + i] = __uint_as_float(acc[i]);
+                    }
+                }
+                __threadfence();
+                __syncwarp();
+                int old = 0;
+                if (lane == 0)
+                    old = atomicAdd(&args.cnt[static_cast<int64_t>(t) * Cfg::kEpiWarps + (warp - 2)], 1);
+                old = __shfl_sync(0xffffffffu, old, 0);
+                if (old == args.ksplit - 1) {
+                    // the region's 32 rows x 64 columns, lanes along the columns
+                    // (coalesced), the slices summed in order
+                    __threadfence();
+                    const int64_t row0 = static_cast<int64_t>(tm) * kBM + q * 32;
+#pragma unroll 4
+                    for (int r = 0; r < 32; ++r) {
+                        const int64_t grow = row0 + r;
+                        if (grow >= args.m) break;
+#pragma unroll
+                        for (int hc = 0; hc < 2; ++hc) {
+                            const int64_t col = col_base + hc * 32 + lane;
+                            if (col >= args.p) continue;
+                            const float* src = args.part + grow * args.p + col;
+                            float sum = 0.f;
+                            for (int s2 = 0; s2 < args.ksplit; ++s2) sum += __ldcg(src + s2 * plane);
+                            static_cast<float*>(args.C)[grow * args.p + col] = sum;
+                        }
+                    }
+                }
+                continue;
+            }
             // ---------------- FP32 mode: store the tile
             if (!F64 && row_ok) {
                 float* crow = static_cast<float*>(args.C) + row * args.p;
@@ -1365,6 +1418,21 @@ SplitLayout split_layout(int64_t m, int64_t n, int64_t p, moa_dtype dt, int S) {
     off += al(static_cast<size_t>(S) * m * L.lda * L.esize);
     L.b_off = off;
     off += al(static_cast<size_t>(S) * b_rows * L.ldb * L.esize);
+    if (dt == MOA_F32_SPLIT) {
+        // split K for few tiles (at most 160 SMs' worth of units of 128 x 256)
+        const int64_t tiles256 = ceil_div(m, kBM) * ceil_div(p, 256);
+        const int64_t by_k = std::max<int64_t>(1, ceil_div(n, 32) * 32 / 1024);
+        const int64_t ks = std::min<int64_t>({160 / std::max<int64_t>(1, tiles256), by_k, 64});
+        if (ks >= 2) {
+            L.f32_ks = static_cast<int>(ks);
+            L.cnt_bytes = static_cast<size_t>(ceil_div(m, kBM) * ceil_div(p, 128)) * 16 * 4;
+            L.cnt_off = off;
+            off += al(L.cnt_bytes);
+            L.part_bytes = static_cast<size_t>(ks) * m * p * 4;
+            L.part_off = off;
+            off += al(L.part_bytes);
+        }
+    }
     if (dt != MOA_F32_SPLIT) {
         L.ea_off = off;
         off += al(static_cast<size_t>(m) * 4);
@@ -1579,9 +1647,14 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
     a.wait_limit_ns = wait_limit_ns();
     a.status = status;
     a.vec_ok = (p % 4 == 0) && (reinterpret_cast<uintptr_t>(C) % 16 == 0);
-    a.ksplit = (dt == MOA_F32_SPLIT || L.fine_bytes == 0)
-                   ? 1
-                   : split_k_factor(static_cast<long>(a.tiles_m) * a.tiles_n, a.num_kb, bke);
+    if (dt == MOA_F32_SPLIT)
+        a.ksplit = L.f32_ks >= 2 ? std::min(L.f32_ks, split_k_factor(static_cast<long>(a.tiles_m) *
+                                                                          a.tiles_n, a.num_kb, bke))
+                                 : 1;
+    else
+        a.ksplit = L.fine_bytes == 0
+                       ? 1
+                       : split_k_factor(static_cast<long>(a.tiles_m) * a.tiles_n, a.num_kb, bke);
     a.lgroups = 1;
     a.lmask[0] = 0xFFFFFFFFu;
     if (dt != MOA_F32_SPLIT && L.fine_bytes > 0)
@@ -1589,7 +1662,10 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
                                        a.lmask);
     const bool split_units = a.ksplit > 1 || a.lgroups > 1;
     a.cnt = split_units ? reinterpret_cast<int*>(base + L.cnt_off) : nullptr;
-    a.fine = split_units ? reinterpret_cast<long long*>(base + L.fine_off) : nullptr;
+    a.fine = (split_units && dt != MOA_F32_SPLIT) ? reinterpret_cast<long long*>(base + L.fine_off)
+                                                   : nullptr;
+    a.part = (split_units && dt == MOA_F32_SPLIT) ? reinterpret_cast<float*>(base + L.part_off)
+                                                   : nullptr;
 
     if (dt == MOA_F32_SPLIT) {
         auto* a16 = reinterpret_cast<__nv_bfloat16*>(a_sl);
@@ -1599,6 +1675,11 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
             static_cast<const float*>(A), m, n, L.lda, a16, a_plane, vec_rows(A, n, 4),
             static_cast<const float*>(B), p, L.ldb, b16, b_plane, vec_rows(B, p, 4), status, ga);
         kernels += 1;
+        if (split_units) {
+            cudaError_t e = cudaMemsetAsync(a.cnt, 0, L.cnt_bytes, s);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(split-K counters)");
+            ++kernels;
+        }
         a.f64 = 0;
         a.levels = 1;
         a.beta = 0;
@@ -1687,8 +1768,12 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
                           static_cast<uint64_t>(L.ldb) * 2, static_cast<uint64_t>(b_plane) * 2, 64,
                           bke);
         if (rc != MOA_OK) return rc;
-        rc = bn == 256 ? launch_split_cfg<256, kModeF32, kFmtBF16KB>(a, tmA, tmB, s, st)
-                       : launch_split_cfg<128, kModeF32, kFmtBF16KB>(a, tmA, tmB, s, st);
+        if (split_units)
+            rc = bn == 256 ? launch_split_cfg<256, kModeF32, kFmtBF16KB, true>(a, tmA, tmB, s, st)
+                           : launch_split_cfg<128, kModeF32, kFmtBF16KB, true>(a, tmA, tmB, s, st);
+        else
+            rc = bn == 256 ? launch_split_cfg<256, kModeF32, kFmtBF16KB>(a, tmA, tmB, s, st)
+                           : launch_split_cfg<128, kModeF32, kFmtBF16KB>(a, tmA, tmB, s, st);
     } else {
         rc = make_tmap_3d(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, a_sl, static_cast<uint64_t>(n),
                           static_cast<uint64_t>(m), static_cast<uint64_t>(S),

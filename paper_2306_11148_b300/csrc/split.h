@@ -65,6 +65,10 @@ struct SplitLayout {
     size_t cnt_bytes;      // one per tile and epilogue warp), then, at fine_off, the
     size_t fine_off;       // m x p int64 sums of the levels finer than the total's
     size_t fine_bytes;     // grid; both 0 when the shape cannot take split K
+    // FP32-accuracy split K: at most f32_ks K slices; their FP32 partial tiles
+    // (f32_ks x m x p) at part_off, summed in slice order by the last unit
+    int f32_ks;
+    size_t part_off, part_bytes;
     size_t total;
 };
 SplitLayout split_layout(int64_t m, int64_t n, int64_t p, moa_dtype dt, int S);
