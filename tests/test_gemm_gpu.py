@@ -157,6 +157,23 @@ def test_f64_split_k_many_slices_ragged():
     assert np.all(np.abs(C - exact) <= scale * 2.0 ** -46 + np.abs(exact) * 2.0 ** -52)
 
 
+@pytest.mark.parametrize("m,n,p", [(48, 20000, 40), (130, 9000, 300)])
+def test_f32_split_k_deterministic_and_accurate(m, n, p):
+    """FP32-accuracy split with few tiles and a long K: the K range is cut
+    into slices whose FP32 partial tiles are summed in slice order, so the
+    result is bit-identical from call to call, exact on integer inputs and
+    within the mode's tolerance on normal ones."""
+    dt = moa.MOA_F32_SPLIT
+    A, B = inputs.integer_pair(m, n, p, dtype=torch.float32, seed=m + n)
+    C = _run(A, B, dt)
+    assert np.array_equal(C, oracle.gemm(A.double().numpy(), B.double().numpy()))
+    A, B = inputs.normal_pair(m, n, p, dtype=torch.float32, seed=m + p)
+    C1 = _run(A, B, dt)
+    C2 = _run(A, B, dt)
+    assert np.array_equal(C1, C2)
+    assert _rel(C1, oracle.gemm(A.double().numpy(), B.double().numpy())) <= TOL[dt]
+
+
 def test_f32_split_slices_match_oracle_split():
     """The FP32-accuracy mode's result equals the six-product sum of the
     oracle's BF16 slices up to FP32 accumulation error: each of the 6n terms
