@@ -157,6 +157,35 @@ def test_f64_split_k_many_slices_ragged():
     assert np.all(np.abs(C - exact) <= scale * 2.0 ** -46 + np.abs(exact) * 2.0 ** -52)
 
 
+@pytest.mark.parametrize("dt,m,n,p", [(moa.MOA_F64_SPLIT_F64IN, 300, 700, 520),
+                                      (moa.MOA_F64_SPLIT_F32IN, 129, 1000, 777),
+                                      (moa.MOA_F64_SPLIT_F64IN_E4M3, 300, 700, 520),
+                                      (moa.MOA_F64_SPLIT_F32IN_E4M3, 129, 1000, 777)],
+                         ids=["f64in-300x700x520", "f32in-129x1000x777",
+                              "f64in-e4m3-300x700x520", "f32in-e4m3-129x1000x777"])
+def test_f64_level_groups_exact_and_deterministic(dt, m, n, p):
+    """K too short to cut (n < 1024) and few output tiles: the S levels of
+    every tile are dealt onto separate work units (more units than tiles in
+    the launch) whose int64 folds meet in C by atomic adds.  The result is
+    still the exact slice product of the oracle's digits, to the final FP64
+    rounding and the dropped low bits, and bit-identical from call to call."""
+    beta, h = moa.DIGITS[dt]
+    A, B = inputs.normal_pair(m, n, p, dtype=moa.in_dtype(dt), seed=m + n, scaled="rows")
+    Ad, Bd = A.cuda(), B.cuda()
+    C1, st = moa.gemm(Ad, Bd, dt, stats=True)
+    C2 = moa.gemm(Ad, Bd, dt)
+    moa.sync_status()
+    assert st.grid > st.tiles
+    C1 = C1.cpu().double().numpy()
+    assert np.array_equal(C1, C2.cpu().double().numpy())
+    S = moa.DEFAULT_SLICES[dt]
+    eA, dA = oracle.slice_fixed(A.double().numpy(), 0, beta, S, headroom=h)
+    eB, dB = oracle.slice_fixed(B.double().numpy(), 1, beta, S, headroom=h)
+    exact = oracle.split_gemm_exact(dA, eA, dB, eB, beta, S)
+    scale = np.outer(2.0 ** eA.astype(np.float64), 2.0 ** eB.astype(np.float64))
+    assert np.all(np.abs(C1 - exact) <= scale * 2.0 ** -46 + np.abs(exact) * 2.0 ** -52)
+
+
 @pytest.mark.parametrize("m,n,p", [(48, 20000, 40), (130, 9000, 300)])
 def test_f32_split_k_deterministic_and_accurate(m, n, p):
     """FP32-accuracy split with few tiles and a long K: the K range is cut
