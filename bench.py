@@ -32,6 +32,7 @@ MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}
 # Dense tensor rates relative to BF16 (nominal datasheet figures).
 NOMINAL_RATIO = {"bf16": 1.0, "tf32": 1.1 / 2.25, "fp8": 2.0}
+L2_MB = 126.0   # B300 L2 capacity
 # DRAM traffic (read + write bytes) per launch of the dominant kernel from one
 # ncu capture, keyed by (mode, N); see profiles/.  Remove an entry when its
 # kernel changes.
@@ -941,9 +942,14 @@ def square_metric_config(mode, N, ws):
     """Metric name and config of the square workloads (shared by both arms)."""
     metric = "GEMM TFLOP/s (FP32 ONF GEMM, TF32 tensor path)" if mode == "tf32" else \
         f"GEMM TFLOP/s (ONF GEMM, {mode} path)"
+    # bytes of A and B and of C per element, against the 126 MB L2
+    in_b, out_b = {"bf16": (2, 4), "f64": (8, 8), "f64_split_f32in": (4, 8),
+                   "f64_split_f32in_e4m3": (4, 8)}.get(mode, (4, 4))
+    mb = N * N * (2 * in_b + out_b) / 1e6
+    l2 = (f"inputs larger than L2 (A, B, C: {mb:.0f} MB)" if mb > L2_MB else
+          f"A, B, C fit in L2 ({mb:.1f} MB): not flushed between steps (warm-cache figure)")
     config = {"workload": f"square ONF GEMM m=n=p={N}, row-major, seed 0, mode {mode}",
-              "N": N, "mode": mode, "parallelism": f"replicas x{ws}",
-              "l2": "inputs larger than L2 (3 x N^2 elements)"}
+              "N": N, "mode": mode, "parallelism": f"replicas x{ws}", "l2": l2}
     return metric, config
 
 
