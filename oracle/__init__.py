@@ -19,6 +19,10 @@ Functions and the passages they follow:
 * :func:`split3_bf16` -- FP32-accuracy slicing (not in the paper).
 * :func:`slice_fixed` -- FP64-accuracy integer-digit slicing (not in the paper).
 * :func:`split_gemm_exact` -- the exact value the digit-slice product reaches.
+* :func:`crt_moduli`, :func:`crt_bits`, :func:`scale_int`,
+  :func:`int_gemm_exact` -- FP64 accuracy from modular slices (not in the
+  paper): operands scaled per row / column to integers of at most ``t`` bits,
+  their exact integer product, rounded once.
 * :func:`kronecker`, :func:`hadamard` -- the Appendix's other products of the
   inner/outer-product family.
 """
@@ -78,6 +82,16 @@ def _load():
                                                         _ptr, _ptr, ctypes.c_int,
                                                         ctypes.c_int, _ptr]
             lib.moa_oracle_split_gemm_exact.restype = None
+            lib.moa_oracle_crt_moduli.argtypes = [ctypes.c_int, _ptr]
+            lib.moa_oracle_crt_moduli.restype = None
+            lib.moa_oracle_crt_bits.argtypes = [_i64, ctypes.c_int]
+            lib.moa_oracle_crt_bits.restype = ctypes.c_int
+            lib.moa_oracle_scale_int.argtypes = [_i64, _i64, _ptr, ctypes.c_int, ctypes.c_int,
+                                                 _ptr, _ptr]
+            lib.moa_oracle_scale_int.restype = None
+            lib.moa_oracle_int_gemm_exact.argtypes = [_i64, _i64, _i64, _ptr, _ptr, _ptr, _ptr,
+                                                      ctypes.c_int, _ptr]
+            lib.moa_oracle_int_gemm_exact.restype = None
             lib.moa_oracle_kronecker_f64.argtypes = [_i64, _i64, _i64, _i64, _ptr, _ptr, _ptr]
             lib.moa_oracle_kronecker_f64.restype = None
             lib.moa_oracle_hadamard_f64.argtypes = [_i64, _i64, _ptr, _ptr, _ptr]
@@ -178,6 +192,62 @@ def split_gemm_exact(dA, eA, dB, eB, beta: int, S: int) -> np.ndarray:
     _load().moa_oracle_split_gemm_exact(m, n, p, _p(dA), _p(eA), _p(dB), _p(eB),
                                         int(beta), int(S), _p(C))
     return C
+
+
+def crt_moduli(M: int) -> list:
+    """The first M integers of 256, 255, ... coprime to all taken before."""
+    if not 1 <= M <= 20:
+        raise ValueError("M must lie in [1, 20]")
+    out = np.zeros(M, dtype=np.int32)
+    _load().moa_oracle_crt_moduli(int(M), _p(out))
+    return [int(x) for x in out]
+
+
+def crt_bits(n: int, M: int) -> int:
+    """Largest t <= 62 with n * 2^(2t+1) < (product of the first M moduli)."""
+    if not 1 <= M <= 16 or n < 1:
+        raise ValueError("needs 1 <= M <= 16 and n >= 1")
+    return int(_load().moa_oracle_crt_bits(int(n), int(M)))
+
+
+def scale_int(X, axis: int, t: int):
+    """Per-row (axis 0) or per-column (axis 1) exponents e and the integers
+    rint(x * 2^(t - e)); returns (exps int32[groups], ints int64[rows, cols])."""
+    X = _f64(X)
+    rows, cols = X.shape
+    if not 0 <= t <= 62:
+        raise ValueError("t must lie in [0, 62]")
+    exps = np.empty(rows if axis == 0 else cols, dtype=np.int32)
+    ints = np.empty((rows, cols), dtype=np.int64)
+    _load().moa_oracle_scale_int(rows, cols, _p(X), int(axis), int(t), _p(exps), _p(ints))
+    return exps, ints
+
+
+def int_gemm_exact(Ai, eA, Bi, eB, t: int) -> np.ndarray:
+    """(Ai . Bi)[i,j] * 2^(eA_i + eB_j - 2t), the product exact, rounded once."""
+    Ai = np.ascontiguousarray(Ai, dtype=np.int64)
+    Bi = np.ascontiguousarray(Bi, dtype=np.int64)
+    eA = np.ascontiguousarray(eA, dtype=np.int32)
+    eB = np.ascontiguousarray(eB, dtype=np.int32)
+    m, n = Ai.shape
+    n2, p = Bi.shape
+    if n != n2:
+        raise ValueError("inner dimensions differ")
+    C = np.empty((m, p), dtype=np.float64)
+    _load().moa_oracle_int_gemm_exact(m, n, p, _p(Ai), _p(eA), _p(Bi), _p(eB), int(t), _p(C))
+    return C
+
+
+def crt_gemm(A, B, M: int) -> np.ndarray:
+    """The value the modular-slice method reaches for A . B with M moduli:
+    t = crt_bits(n, M); A scaled per row, B per column; exact product."""
+    A = _f64(A)
+    B = _f64(B)
+    n = A.shape[1]
+    t = crt_bits(max(n, 1), M)
+    eA, Ai = scale_int(A, 0, t)
+    eB, Bi = scale_int(B, 1, t)
+    return int_gemm_exact(Ai, eA, Bi, eB, t)
 
 
 def kronecker(A, B) -> np.ndarray:

@@ -16,6 +16,10 @@
  *   moa_oracle_split3_bf16     precision slicing, FP32-accuracy mode (not in the paper)
  *   moa_oracle_slice_fixed     precision slicing, FP64-accuracy mode (not in the paper)
  *   moa_oracle_split_gemm_exact  the value the FP64-accuracy slice method reaches
+ *   moa_oracle_crt_moduli      moduli of the FP64-accuracy modular-slice mode (not in the paper)
+ *   moa_oracle_crt_bits        operand bits that mode keeps for a given n and modulus count
+ *   moa_oracle_scale_int       per-row / per-column scaling of an operand to integers
+ *   moa_oracle_int_gemm_exact  the value the modular-slice method reaches
  *   moa_oracle_kronecker_f64   Kronecker product (Appendix: outer product, no reduction)
  *   moa_oracle_hadamard_f64    Hadamard product (Appendix: diagonal of the outer product)
  *
@@ -25,7 +29,10 @@
  * library-rounding tests.  moa_oracle_split_gemm_exact is pinned against the
  * GEMM oracle within the slicing error bound.  The Kronecker and Hadamard
  * products are pinned by the mixed-product property, identities and the
- * trace identity on integer inputs.
+ * trace identity on integer inputs.  The modular-slice functions are pinned
+ * by coprimality and maximality of the moduli, the bit bound checked with
+ * big integers, an exact-rational route for the scaling, and brute force,
+ * exact-integer and truncation-bound tests of the exact product.
  */
 #include <stdint.h>
 #include <math.h>
@@ -248,6 +255,118 @@ void moa_oracle_split_gemm_exact(int64_t m, int64_t n, int64_t p,
             C[i * p + j] = neg ? -v : v;
         }
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* FP64 accuracy from modular slices (not in the paper; the residue-number   */
+/* form of error-free slicing, in the manner of Ozaki, Uchino & Imamura's   */
+/* "Ozaki scheme II", 2025).  Each row i of A is scaled by 2^(t - eA_i) and rounded to an        */
+/* integer A'[i,k] (|A'| <= 2^t), each column j of B by 2^(t - eB_j) to      */
+/* B'[k,j]; the integer product C' = A' B' is exact, and                     */
+/*     C[i,j] = C'[i,j] * 2^(eA_i + eB_j - 2t), rounded once to FP64.         */
+/* A GPU forms C' from its residues modulo M pairwise-coprime moduli (one    */
+/* small exact GEMM per modulus) by the Chinese remainder theorem, which     */
+/* recovers C' itself when n * 2^(2t) < P / 2, P the product of the moduli.  */
+/* The functions below state that definition; the residues are the GPU's    */
+/* business, so none is formed here.                                         */
+/* ------------------------------------------------------------------------ */
+
+static int64_t gcd64(int64_t a, int64_t b)
+{
+    while (b != 0) { const int64_t r = a % b; a = b; b = r; }
+    return a;
+}
+
+/* The first M integers of the sequence 256, 255, 254, ... that are coprime
+ * to every integer taken before them (a greedy, descending choice; every
+ * modulus is at most 2^8 so that each symmetric residue is an integer of
+ * magnitude <= 128, exact in BF16).  Requires 1 <= M <= 20. */
+void moa_oracle_crt_moduli(int M, int32_t* out)
+{
+    int taken = 0;
+    for (int64_t c = 256; c >= 2 && taken < M; --c) {
+        int ok = 1;
+        for (int q = 0; q < taken; ++q)
+            if (gcd64(c, out[q]) != 1) { ok = 0; break; }
+        if (ok) out[taken++] = (int32_t)c;
+    }
+}
+
+/* Largest t <= 62 with n * 2^(2t + 1) < P (P the product of the first M
+ * moduli): with |A'|, |B'| <= 2^t every |C'| <= n 2^(2t) < P / 2, so the
+ * symmetric residue class modulo P names C' uniquely.  Requires
+ * 1 <= M <= 16 (P < 2^128) and n >= 1; returns -1 if no t >= 0 fits. */
+int moa_oracle_crt_bits(int64_t n, int M)
+{
+    int32_t mod[16];
+    moa_oracle_crt_moduli(M, mod);
+    unsigned __int128 P = 1;
+    for (int q = 0; q < M; ++q) P *= (unsigned __int128)mod[q];
+    int best = -1;
+    for (int t = 0; t <= 62; ++t) {
+        /* n * 2^(2t+1) < P  <=>  n < P / 2^(2t+1) (exact: compare n with the
+         * ceiling of the quotient) */
+        const int sh = 2 * t + 1;
+        if (sh >= 128) break;
+        const unsigned __int128 q = P >> sh;
+        const int exact = (q << sh) == P;
+        /* n * 2^sh < P  <=>  n < P / 2^sh  <=>  n <= ceil(P / 2^sh) - 1 */
+        const unsigned __int128 lim = exact ? q - 1 : q;
+        if ((unsigned __int128)n <= lim) best = t;
+        else break;
+    }
+    return best;
+}
+
+/* Per-group exponents and scaled integers of X (rows x cols, row-major):
+ * axis 0 scales each row, axis 1 each column.  e_g is the frexp exponent of
+ * the group's largest magnitude (0 for an all-zero group), so that every
+ * |x| < 2^e_g, and ints[r,c] = x * 2^(t - e_g) rounded to the nearest
+ * integer, ties to even: |ints| <= 2^t.  Requires 0 <= t <= 62. */
+void moa_oracle_scale_int(int64_t rows, int64_t cols, const double* X, int axis, int t,
+                          int32_t* exps, int64_t* ints)
+{
+    const int64_t ngroups = axis == 0 ? rows : cols;
+    for (int64_t g = 0; g < ngroups; ++g) {
+        double mu = 0.0;
+        const int64_t len = axis == 0 ? cols : rows;
+        for (int64_t q = 0; q < len; ++q) {
+            const double v = axis == 0 ? X[g * cols + q] : X[q * cols + g];
+            if (fabs(v) > mu) mu = fabs(v);
+        }
+        int f = 0;
+        if (mu != 0.0) (void)frexp(mu, &f);
+        exps[g] = f;
+    }
+    for (int64_t r = 0; r < rows; ++r)
+        for (int64_t c = 0; c < cols; ++c) {
+            const int e = axis == 0 ? exps[r] : exps[c];
+            /* the scaling by a power of two is exact unless the result is
+             * subnormal, and such a result (< 2^-1022) rounds to 0 anyway;
+             * rint rounds half to even in the default rounding mode */
+            ints[r * cols + c] = (int64_t)rint(ldexp(X[r * cols + c], t - e));
+        }
+}
+
+/* C[i,j] = (sum_k Ai[i,k] * Bi[k,j]) * 2^(eA_i + eB_j - 2t), the sum exact in
+ * 128-bit integers, rounded once to FP64.  Requires |Ai|, |Bi| <= 2^62 and
+ * n * max|Ai| * max|Bi| < 2^127. */
+void moa_oracle_int_gemm_exact(int64_t m, int64_t n, int64_t p,
+                               const int64_t* Ai, const int32_t* eA,
+                               const int64_t* Bi, const int32_t* eB,
+                               int t, double* C)
+{
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t j = 0; j < p; ++j) {
+            __int128 acc = 0;
+            for (int64_t k = 0; k < n; ++k)
+                acc += (__int128)Ai[i * n + k] * (__int128)Bi[k * p + j];
+            const int neg = acc < 0;
+            const unsigned __int128 mag = neg ? (unsigned __int128)(-acc)
+                                              : (unsigned __int128)acc;
+            const double v = u128_scaled_to_double(mag, (int)(eA[i] + eB[j]) - 2 * t);
+            C[i * p + j] = neg ? -v : v;
+        }
 }
 
 /* ------------------------------------------------------------------------ */
