@@ -1,12 +1,18 @@
 #!/usr/bin/env python
 """Benchmark of the B300-native MoA ONF GEMM (Eq. eq:dnf).
 
-Default workload: the square FP32 ONF GEMM at N = 8192 (uniform[-1,1) inputs,
-seed 0) on the FP32-via-TF32 tensor-core path, one GEMM per step; the other
-precision modes are measured on the same inputs and reported under "modes".
+Default workload: the FP64-accurate ONF GEMM at m = n = p = 8192 on FP32
+inputs drawn i.i.d. N(0, 1) (seed 0): the FP64-accuracy split mode
+(MOA_F64_SPLIT_F32IN: integer digit slices of A and B as BF16 planes, slice
+products on the tensor cores, exact integer accumulation, one FP64 rounding),
+one GEMM (pre-passes included) per step.  The line carries the oracle's error
+on 64 sampled rows for the plain and the two row-scaled input kinds, the
+roofline of the slice-product kernel, the CPU oracle's rate, the end-to-end
+rate from pinned host memory, joules per GEMM, and the other precision modes
+and a short serving run under "modes".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl moa|reference]
-                  [--workload square|split_f32|split_f64|bf16|f64] [--n N]
+                  [--workload split_f64|square|split_f32|bf16|f64|...] [--n N]
 
 Under torchrun (N > 1) every rank runs its own replica of the workload (the
 GEMM is not sharded: replicas only); timing is the max over ranks and the
@@ -34,9 +40,33 @@ FALLBACK = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1
 NOMINAL_RATIO = {"bf16": 1.0, "tf32": 1.1 / 2.25, "fp8": 2.0}
 L2_MB = 126.0   # B300 L2 capacity
 # DRAM traffic (read + write bytes) per launch of the dominant kernel from one
-# ncu capture, keyed by (mode, N); see profiles/.  Remove an entry when its
-# kernel changes.
-TRAFFIC = {("tf32", 8192): 1.652613e9 + 0.236939e9}
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by (mode,
+# N), with the SHA-256 (first 16 hex digits) of the kernel's source file at
+# capture time: a figure whose source has changed since is reported as null.
+TRAFFIC = {
+    ("tf32", 8192): {"bytes": 1.652613e9 + 0.236939e9, "src": "gemm_tc.cu",
+                     "sha": None},
+}
+
+
+def src_sha(name):
+    import hashlib
+    path = os.path.join(ROOT, "paper_2306_11148_b300", "csrc", name)
+    try:
+        with open(path, "rb") as f:
+            return hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+
+
+def traffic_of(mode, N):
+    """(bytes per launch or None, note) for the dominant kernel of `mode`."""
+    t = TRAFFIC.get((mode, N))
+    if t is None:
+        return None, "no ncu capture of this kernel at this size"
+    if t["sha"] is None or src_sha(t["src"]) != t["sha"]:
+        return None, f"kernel source {t['src']} changed since the ncu capture"
+    return t["bytes"], f"ncu capture of {t['src']} (sha {t['sha']})"
 
 
 def load_peaks():
@@ -279,19 +309,26 @@ def aggregate(flops_per_step, steps, seconds, ws):
 
 
 # ------------------------------------------------------------------ workloads
-MODE_OF = {"square": "tf32", "bf16": "bf16", "split_f32": "f32_split",
-           "split_f64": "f64_split_f32in", "split_f64_e4m3": "f64_split_f32in_e4m3",
+MODE_OF = {"split_f64": "f64_split_f32in", "square": "tf32", "bf16": "bf16",
+           "split_f32": "f32_split",
+           "split_f64_e4m3": "f64_split_f32in_e4m3",
            "f64": "f64", "simt": "f32_simt",
            "grouped": "grouped", "serve": "serve", "energy_n": "energy_n",
            "tiles": "tiles", "peaks": "peaks"}
 
 
-def make_inputs(mode, N):
+SPLIT_F32IN = ("f32_split", "f64_split_f32in", "f64_split_f32in_e4m3")
+
+
+def make_inputs(mode, N, scaled=None):
+    """Seed-0 operands of the square workload: FP32 N(0, 1) for the split
+    modes (optionally row-scaled, `scaled` = "rows" | "rowcol"), uniform[-1, 1)
+    in the mode's input type otherwise."""
     import torch
     from paper_2306_11148_b300 import inputs, moa
     dt = moa.MODES[mode]
-    if mode in ("f32_split", "f64_split_f32in", "f64_split_f32in_e4m3"):
-        A, B = inputs.normal_pair(N, N, N, dtype=torch.float32, seed=0)
+    if mode in SPLIT_F32IN:
+        A, B = inputs.normal_pair(N, N, N, dtype=torch.float32, seed=0, scaled=scaled)
     else:
         A, B = inputs.square_uniform(N, moa.in_dtype(dt), seed=0)
     return dt, A, B
@@ -316,7 +353,9 @@ def time_device(fn, steps, warmup, stream, ws, warm_fn=None):
 
 
 def bench_mode(mode, N, steps, warmup, ws, stream, want_energy=False, energy=None,
-               want_e2e=False, check_rows=True):
+               want_e2e=False, check_rows=True, keep_rows=None):
+    """Times `steps` GEMMs of the square workload of `mode`.  keep_rows: row
+    indices of C returned (on the host) as out["rows_C"]."""
     import torch
     from paper_2306_11148_b300 import moa
     dt, A, B = make_inputs(mode, N)
@@ -375,6 +414,9 @@ def bench_mode(mode, N, steps, warmup, ws, stream, want_energy=False, energy=Non
                              "avg_w": (j1 - j0) / (t1 - t0)}
     if want_e2e:
         out["e2e"] = bench_e2e(dt, A, B, C, N, max(4, min(steps, 8)), 2, stream, ws)
+    if keep_rows is not None:
+        out["rows_C"] = C.index_select(
+            0, torch.as_tensor(keep_rows, dtype=torch.int64, device=C.device)).cpu()
     # spot check of a few rows of the timed output (parity proper is in tests/)
     try:
         if not check_rows:
@@ -443,18 +485,97 @@ def bench_e2e(dt, A, B, C, N, steps, warmup, stream, ws):
             "d2h_bytes_per_step": d2h, "streams": 2}
 
 
-def cpu_baseline(N, dtype_name, seconds_target=8.0):
-    """The oracle, as it stands, on sampled rows of the same N^3 problem, all
-    host cores (OpenMP over rows); TFLOP/s of algorithmic work."""
+def gpu_rows(mode, N, scaled, rows, stream):
+    """Rows `rows` of C for the square workload of `mode` on the input kind
+    `scaled` (None, "rows", "rowcol"), one untimed GEMM through moa_gemm_ex."""
+    import torch
+    from paper_2306_11148_b300 import moa
+    dt, A, B = make_inputs(mode, N, scaled=scaled)
+    Ad, Bd = A.cuda(), B.cuda()
+    C = torch.empty((N, N), dtype=moa.out_dtype(dt), device="cuda")
+    with torch.cuda.stream(stream):
+        moa.gemm(Ad, Bd, dt, C=C, stream=stream)
+    moa.check(moa.moa_sync_status(int(stream.cuda_stream)))
+    out = C.index_select(0, torch.as_tensor(rows, dtype=torch.int64, device="cuda")).cpu()
+    del Ad, Bd, C
+    return out
+
+
+def cpu_baseline_split(mode, N, rows_c, rows, seconds_target=8.0):
+    """CPU leg of the split-mode workloads: the oracle (FP64 i-k-j loop,
+    OpenMP over rows, all host cores), as it stands, timed on a bounded
+    sample of rows of the same N(0, 1) problem, then run on the sampled rows
+    `rows` of each input kind, whose GPU results `rows_c[kind]` it checks
+    (relative Frobenius error over those rows)."""
     import numpy as np
     import torch
 
     import oracle
+    cores = os.cpu_count() or 1
+    errs = {}
+    t_all = 0.0
+    flops_all = 0.0
+    used = 0
+    for kind, got in rows_c.items():
+        _, A, B = make_inputs(mode, N, scaled=None if kind == "plain" else kind)
+        A = A.double().numpy()
+        B = B.double().numpy()
+        t0 = time.perf_counter()
+        ref, used = oracle.gemm_omp(A[rows], B, threads=0)
+        dt = time.perf_counter() - t0
+        t_all += dt
+        flops_all += 2.0 * len(rows) * N * N
+        g = got.double().numpy()
+        errs[kind] = float(np.linalg.norm(g - ref) / max(np.linalg.norm(ref), 1e-300))
+        if kind == "plain":
+            # a longer bounded sample of the same loop for the rate (rows
+            # grown 4x until the sample takes a quarter of the target)
+            extra = len(rows)
+            from paper_2306_11148_b300 import inputs
+            while t_all < seconds_target / 4 and extra < N:
+                extra = min(N, extra * 4)
+                idx = inputs.sample_rows(N, extra, seed=1)
+                t0 = time.perf_counter()
+                oracle.gemm_omp(A[idx], B, threads=0)
+                t_all += time.perf_counter() - t0
+                flops_all += 2.0 * extra * N * N
+            # the same loop on one thread, 8 rows
+            idx1 = inputs.sample_rows(N, 8, seed=1)
+            t1 = time.perf_counter()
+            oracle.gemm_omp(A[idx1], B, threads=1)
+            dt1 = time.perf_counter() - t1
+            single = {"value": 2.0 * 8 * N * N / dt1 / 1e12, "unit": "TFLOP/s",
+                      "sample": f"8 rows on 1 thread, {dt1:.2f} s"}
+        del A, B
+    return {"value": flops_all / t_all / 1e12, "unit": "TFLOP/s", "cores": int(used),
+            "kind": "oracle",
+            "sample": f"sampled rows of the N={N} problem on {len(rows_c)} input kinds "
+                      f"({', '.join(rows_c)}), FP64 i-k-j loop, OpenMP over rows, "
+                      f"{flops_all / (2.0 * N * N):.0f} rows in {t_all:.2f} s",
+            "host_cores": cores, "seconds": t_all, "single_thread": single,
+            "rel_err_vs_oracle": errs, "rows_checked": len(rows)}
+
+
+def cpu_operands(N, dtype_name, mode=None):
+    """The square workload's operands as FP64 numpy arrays (exact
+    conversion): a split mode's N(0, 1) FP32 operands, else uniform[-1, 1)."""
+    import torch
     from paper_2306_11148_b300 import inputs
     tdt = torch.float32 if dtype_name != "f64" else torch.float64
-    A, B = inputs.square_uniform(N, tdt, seed=0)
-    A = A.double().numpy()
-    B = B.double().numpy()
+    if mode in SPLIT_F32IN:
+        _, A, B = make_inputs(mode, N)
+    else:
+        A, B = inputs.square_uniform(N, tdt, seed=0)
+    return A.double().numpy(), B.double().numpy()
+
+
+def cpu_baseline(N, dtype_name, seconds_target=8.0, mode=None, operands=None):
+    """The oracle, as it stands, on sampled rows of the same N^3 problem, all
+    host cores (OpenMP over rows); TFLOP/s of algorithmic work.  `operands`:
+    (A, B) from cpu_operands, else drawn here."""
+    import oracle
+    from paper_2306_11148_b300 import inputs
+    A, B = operands if operands is not None else cpu_operands(N, dtype_name, mode)
     rows = 8
     cores = os.cpu_count() or 1
     while True:
@@ -473,8 +594,8 @@ def cpu_baseline(N, dtype_name, seconds_target=8.0):
     oracle.gemm_omp(A[idx1], B, threads=1)
     dt1 = time.perf_counter() - t1
     return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "cores": int(used), "kind": "oracle",
-            "sample": f"{rows} of {N} rows of the N={N} FP64 ONF GEMM (i-k-j loop, OpenMP over "
-                      f"rows), {dt:.2f} s", "host_cores": cores, "seconds": dt,
+            "sample": f"{rows} of {N} rows of the N={N} ONF GEMM in FP64 (i-k-j loop, OpenMP "
+                      f"over rows), {dt:.2f} s", "host_cores": cores, "seconds": dt,
             "single_thread": {"value": 2.0 * rows1 * N * N / dt1 / 1e12, "unit": "TFLOP/s",
                               "sample": f"{rows1} rows on 1 thread, {dt1:.2f} s"}}
 
@@ -631,22 +752,62 @@ def bench_grouped_e2e(shapes, steps, warmup, ws):
             "d2h_bytes_per_step": 4 * nc, "streams": 2}
 
 
-def serve_run(srv, pool, arrivals, cring):
-    """Submits `arrivals` [(t, pool index)] at their times; returns the
-    completions and the submit results."""
+class ServeOperands:
+    """Device-resident operands of the serving stream, sized for its largest
+    request.  `nbuf` pairs of FP32 N(0, 1) buffers (A: 4096 x 8192, B:
+    8192 x 4096 elements) and `nout` output slots of 4096 x 4096 FP64.
+    Arrival i reads its row-major m x n A and n x p B from pair i % nbuf at an
+    offset that moves with i (256-byte aligned, so that successive requests
+    touch different memory rather than one L2-resident prefix), and writes its
+    m x p C to slot i % nout.  Every arrival thus runs its own shape."""
+
+    MAX_MP, MAX_N = 4096, 8192
+
+    def __init__(self, nbuf=2, nout=256, seed=0):
+        import torch
+        from paper_2306_11148_b300 import inputs
+        self.nbuf, self.nout = nbuf, nout
+        self.A, self.B = [], []
+        for b in range(nbuf):
+            A, B = inputs.normal_pair(self.MAX_MP, self.MAX_N, self.MAX_MP,
+                                      dtype=torch.float32, seed=seed + 100 + b)
+            self.A.append(A.reshape(-1).cuda())
+            self.B.append(B.reshape(-1).cuda())
+        self.C = torch.empty((nout, self.MAX_MP * self.MAX_MP), dtype=torch.float64,
+                             device="cuda")
+
+    def request(self, i, m, n, p, dt):
+        """(A, B, C) views of arrival i with shape (m, n, p) for mode dt."""
+        import torch
+        from paper_2306_11148_b300 import moa
+        size = self.MAX_MP * self.MAX_N
+        b = i % self.nbuf
+        span_a = max(1, (size - m * n) // 64 + 1)
+        span_b = max(1, (size - n * p) // 64 + 1)
+        oa = ((i * 7919) % span_a) * 64
+        ob = ((i * 104729) % span_b) * 64
+        A = self.A[b][oa:oa + m * n].view(m, n)
+        B = self.B[b][ob:ob + n * p].view(n, p)
+        slot = self.C[i % self.nout]
+        C = slot[:m * p].view(m, p) if moa.out_dtype(dt) == torch.float64 else \
+            slot.view(torch.float32)[:m * p].view(m, p)
+        return A, B, C
+
+
+def serve_run(srv, ops, arrivals):
+    """Submits every arrival (t, m, n, p, tag) at its time; returns the submit
+    results [(status, ticket, i, flops)], the completions and the wall time."""
     from paper_2306_11148_b300 import moa
     t0 = time.perf_counter()
     codes = []
-    ring_pos = {}
-    for t, i in arrivals:
+    for i, (t, m, n, p, tag) in enumerate(arrivals):
         delay = t - (time.perf_counter() - t0)
         if delay > 0:
             time.sleep(delay)
-        A, B, dt, flops = pool[i]
-        k = ring_pos.get(i, 0)
-        ring_pos[i] = (k + 1) % len(cring[i])
-        rc, tk = srv.submit(A, B, cring[i][k], dt)
-        codes.append((rc, tk, i))
+        dt = moa.MOA_F32_SPLIT if tag == "f32" else moa.MOA_F64_SPLIT_F32IN
+        A, B, C = ops.request(i, m, n, p, dt)
+        rc, tk = srv.submit(A, B, C, dt)
+        codes.append((rc, tk, i, 2.0 * m * n * p))
     submitted = [c for c in codes if c[0] == moa.MOA_OK]
     got = {}
     deadline = time.perf_counter() + 120
@@ -658,72 +819,52 @@ def serve_run(srv, pool, arrivals, cring):
     return codes, got, wall
 
 
-def serve_pool(pool_size=64, ring=8, seed=0):
-    """Device-resident operands of `pool_size` requests drawn from the serving
-    distribution (m, p log-uniform in [64, 4096], n in [64, 8192], multiples of
-    16; tag FP32-accuracy or FP64-accuracy with probability 1/2; FP32 N(0,1)),
-    each with `ring` output buffers."""
+def bench_serve(ops, rate, seconds, seed=0, energy=None, n_streams=8):
+    """Serving stream: Poisson arrivals at `rate` for `seconds`, each with its
+    own (m, n, p) and precision tag from inputs.serve_arrivals, through one
+    server (64 GB arena, 32 in flight, 8 streams, 2 s queue deadline)."""
     import torch
     from paper_2306_11148_b300 import inputs, moa
-    shapes = inputs.serve_arrivals(rate=pool_size * 2.0, seconds=1.0, seed=seed + 1)[:pool_size]
-    pool, cring = [], []
-    for j, (_, m, n, p, tag) in enumerate(shapes):
-        A, B = inputs.normal_pair(m, n, p, dtype=torch.float32, seed=seed + 100 + j)
-        dt = moa.MOA_F32_SPLIT if tag == "f32" else moa.MOA_F64_SPLIT_F32IN
-        pool.append((A.cuda(), B.cuda(), dt, 2.0 * m * n * p))
-        cring.append([torch.empty((m, p), dtype=moa.out_dtype(dt), device="cuda")
-                      for _ in range(ring)])
-    return pool, cring
-
-
-def bench_serve(pool, cring, rate, seconds, seed=0, energy=None, n_streams=8):
-    """Serving stream: Poisson arrivals at `rate` for `seconds` through one
-    server (64 GB arena, 32 in flight, 8 streams, 2 s queue deadline).
-    Arrival i uses pool entry i % len(pool) and the next of its output
-    buffers."""
-    import torch
-    from paper_2306_11148_b300 import inputs, moa
-    ring = len(cring[0])
-    arr = inputs.serve_arrivals(rate=rate, seconds=seconds, seed=seed)
-    arrivals = [(a[0], i % len(pool)) for i, a in enumerate(arr)]
+    arrivals = inputs.serve_arrivals(rate=rate, seconds=seconds, seed=seed)
+    # a queued or running request owns its output slot until it completes
     srv = moa.Server(arena_bytes=64 << 30, max_inflight=32, n_streams=n_streams,
-                     queue_capacity=len(pool) * ring // 2 - 32, queue_deadline_s=2.0)
+                     queue_capacity=ops.nout - 64, queue_deadline_s=2.0)
     j0 = energy.read_j() if energy else None
     try:
-        codes, got, wall = serve_run(srv, pool, arrivals, cring)
+        codes, got, wall = serve_run(srv, ops, arrivals)
         st = srv.stats()
     finally:
         srv.close()
     j1 = energy.read_j() if energy else None
     done_ok = [c for c in got.values() if c[1] == moa.MOA_OK]
-    flops = sum(pool[i][3] for rc, tk, i in codes if rc == moa.MOA_OK and tk in got
-                and got[tk][1] == moa.MOA_OK)
+    ok_ticket = {c[0] for c in done_ok}
+    flops = sum(f for rc, tk, i, f in codes if rc == moa.MOA_OK and tk in ok_ticket)
     span = (max(c[4] for c in done_ok) - min(c[2] for c in done_ok)) if done_ok else float("nan")
-    # latency split: queue wait (submit -> admission by the scheduler) and
-    # service (admission -> completion callback on the stream)
+
     def pct(xs, q):
         xs = sorted(xs)
         return xs[min(len(xs) - 1, int(q * len(xs)))] * 1e3 if xs else float("nan")
+    # latency split: queue wait (submit -> admission) and service (admission -> done)
     waits = [c[3] - c[2] for c in done_ok]
     service = [c[4] - c[3] for c in done_ok]
-    # alone vs mix: the last output of some pool entries against the same GEMM alone
+    # alone vs mix: arrivals whose output slot no later arrival reused, every
+    # 8th of them, recomputed alone and compared bit for bit
     torch.cuda.synchronize()
     mism = checked = 0
-    uses = {}
-    last_ok = {}
-    for rc, tk, j in codes:
-        uses[j] = uses.get(j, 0) + 1
-        if rc == moa.MOA_OK and tk in got and got[tk][1] == moa.MOA_OK:
-            last_ok[j] = (tk, uses[j] - 1)
-    for i in range(0, len(pool), 8):
-        if i not in last_ok or last_ok[i][1] != uses[i] - 1:
+    last = len(arrivals)
+    for rc, tk, i, _ in codes[max(0, last - ops.nout):]:
+        if i % 8 or rc != moa.MOA_OK or tk not in ok_ticket:
             continue
-        A, B, dt, _ = pool[i]
+        _, m, n, p, tag = arrivals[i]
+        dt = moa.MOA_F32_SPLIT if tag == "f32" else moa.MOA_F64_SPLIT_F32IN
+        A, B, C = ops.request(i, m, n, p, dt)
         alone = moa.gemm(A, B, dt)
         torch.cuda.synchronize()
         checked += 1
-        mism += 0 if torch.equal(alone, cring[i][(uses[i] - 1) % ring]) else 1
+        mism += 0 if torch.equal(alone, C) else 1
+    n_f64 = sum(1 for a in arrivals if a[4] == "f64")
     return {"rate": rate, "seconds": seconds, "offered": len(arrivals),
+            "offered_f64_accuracy": n_f64, "offered_f32_accuracy": len(arrivals) - n_f64,
             "submitted": st["submitted"], "completed": st["completed"],
             "rejected": st["rejected"], "busy": sum(1 for c in codes if c[0] == moa.MOA_ERR_BUSY),
             "failed": st["failed"], "served_per_s": len(done_ok) / span if done_ok else 0.0,
@@ -938,17 +1079,28 @@ def bench_library_rates(N=8192, reps=10):
 
 
 # ------------------------------------------------------------------ reference arm
+METRIC_OF = {
+    "tf32": "GEMM TFLOP/s (FP32 ONF GEMM, TF32 tensor path)",
+    "f64_split_f32in": "GEMM TFLOP/s (FP64-accurate ONF GEMM of FP32 inputs: BF16 integer-digit "
+                       "slices on the tensor cores, exact integer accumulation)",
+    "f64_split_f32in_e4m3": "GEMM TFLOP/s (FP64-accurate ONF GEMM of FP32 inputs: FP8 E4M3 "
+                            "integer-digit slices on the tensor cores)",
+    "f32_split": "GEMM TFLOP/s (FP32-accurate ONF GEMM: three BF16 slices, six products)",
+}
+INPUTS_OF = {m: "FP32 i.i.d. N(0,1), seed 0" for m in SPLIT_F32IN}
+
+
 def square_metric_config(mode, N, ws):
     """Metric name and config of the square workloads (shared by both arms)."""
-    metric = "GEMM TFLOP/s (FP32 ONF GEMM, TF32 tensor path)" if mode == "tf32" else \
-        f"GEMM TFLOP/s (ONF GEMM, {mode} path)"
+    metric = METRIC_OF.get(mode, f"GEMM TFLOP/s (ONF GEMM, {mode} path)")
     # bytes of A and B and of C per element, against the 126 MB L2
     in_b, out_b = {"bf16": (2, 4), "f64": (8, 8), "f64_split_f32in": (4, 8),
                    "f64_split_f32in_e4m3": (4, 8)}.get(mode, (4, 4))
     mb = N * N * (2 * in_b + out_b) / 1e6
     l2 = (f"inputs larger than L2 (A, B, C: {mb:.0f} MB)" if mb > L2_MB else
           f"A, B, C fit in L2 ({mb:.1f} MB): not flushed between steps (warm-cache figure)")
-    config = {"workload": f"square ONF GEMM m=n=p={N}, row-major, seed 0, mode {mode}",
+    config = {"workload": f"square ONF GEMM m=n=p={N}, row-major, "
+                          f"{INPUTS_OF.get(mode, 'uniform[-1,1), seed 0')}, mode {mode}",
               "N": N, "mode": mode, "parallelism": f"replicas x{ws}", "l2": l2}
     return metric, config
 
@@ -959,12 +1111,13 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return
     N = args.n
-    mode = MODE_OF.get(args.workload, "tf32")
+    mode = MODE_OF.get(args.workload, "f64_split_f32in")
     per_step = []
+    ops = cpu_operands(N, "f32", mode)
     for _ in range(args.warmup):
-        cpu_baseline(N, "f32", seconds_target=2.0)
+        cpu_baseline(N, "f32", seconds_target=2.0, operands=ops)
     for _ in range(args.steps):
-        per_step.append(cpu_baseline(N, "f32", seconds_target=4.0))
+        per_step.append(cpu_baseline(N, "f32", seconds_target=4.0, operands=ops))
     v = sum(x["value"] for x in per_step) / len(per_step)
     metric, config = square_metric_config(mode, N, args.gpus)
     config["arm"] = "CPU oracle (FP64 i-k-j loop, OpenMP over rows) on sampled rows"
@@ -988,7 +1141,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="moa", choices=["moa", "reference"])
-    ap.add_argument("--workload", default="square", choices=list(MODE_OF))
+    ap.add_argument("--workload", default="split_f64", choices=list(MODE_OF))
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
@@ -1058,17 +1211,17 @@ def main():
         return
 
     if mode == "serve":
-        pool, cring = serve_pool()
+        ops = ServeOperands(nbuf=4)
         clocks = ClockSampler(pci)
         clocks.start()
-        sat = bench_serve(pool, cring, args.serve_rate, args.serve_seconds, energy=energy)
+        sat = bench_serve(ops, args.serve_rate, args.serve_seconds, energy=energy)
         sweep = []
         for r in args.serve_sweep:
-            sweep.append(bench_serve(pool, cring, r, args.serve_seconds, energy=energy))
+            sweep.append(bench_serve(ops, r, args.serve_seconds, energy=energy))
         clk = clocks.stop()
         # capacity: the highest served rate seen; a run at ~70 % of it
         cap = max([sat["served_per_s"]] + [x["served_per_s"] for x in sweep])
-        light = bench_serve(pool, cring, 0.7 * cap, args.serve_seconds, energy=energy) \
+        light = bench_serve(ops, 0.7 * cap, args.serve_seconds, energy=energy) \
             if args.serve_sweep else None
         if rank == 0:
             line = {"metric": "served GEMM requests/s (continuous batching), p50/p99 latency",
@@ -1076,9 +1229,10 @@ def main():
                     "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak",
                     "vs_baseline": None, "dtype": "bf16-slices", "data": "synthetic",
                     "config": {"workload": f"Poisson arrivals {args.serve_rate}/s for "
-                                           f"{args.serve_seconds} s; m,p logU[64,4096], n "
-                                           "logU[64,8192]; FP32-acc or FP64-acc split requests; "
-                                           "64 GB arena; 32 in flight; 8 streams",
+                                           f"{args.serve_seconds} s, each its own (m, n, p): "
+                                           "m,p logU[64,4096], n logU[64,8192]; FP32-acc or "
+                                           "FP64-acc split requests; 64 GB arena; 32 in "
+                                           "flight; 8 streams",
                                "parallelism": f"replicas x{ws}"},
                     "specified_rate": sat, "rate_sweep": sweep, "capacity_req_s": cap,
                     "at_70pct_capacity": light, "clocks": clk}
@@ -1090,13 +1244,24 @@ def main():
 
     clocks = ClockSampler(pci)
     clocks.start()
+    # the split modes' error check: 64 sampled rows of C on each input kind
+    check_idx = None
+    if mode in SPLIT_F32IN and rank == 0 and not args.no_cpu:
+        from paper_2306_11148_b300 import inputs as _inputs
+        check_idx = _inputs.sample_rows(N, 64, seed=0)
     if mode == "grouped":
         main_res = bench_grouped(args.steps, args.warmup, ws, stream, compare=not args.profile)
     else:
         main_res = bench_mode(mode, N, args.steps, args.warmup, ws, stream,
                               want_energy=not args.profile, energy=energy,
-                              want_e2e=not args.profile, check_rows=not args.profile)
+                              want_e2e=not args.profile, check_rows=not args.profile,
+                              keep_rows=check_idx)
     clk = clocks.stop()
+    rows_c = None
+    if check_idx is not None:
+        rows_c = {"plain": main_res.pop("rows_C")}
+        for kind in ("rows", "rowcol"):
+            rows_c[kind] = gpu_rows(mode, N, kind, check_idx, stream)
 
     value, t_max = aggregate(main_res["flops_per_step"], args.steps, main_res["seconds"], ws)
     ms_per_step = t_max / args.steps * 1e3
@@ -1126,7 +1291,7 @@ def main():
             achieved = main_res["bytes_per_step"] / (kernel_ms / 1e3) / 1e9
             roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"]}
-        roof.update({"traffic": TRAFFIC.get((mode, N)), "kernel_ms": kernel_ms,
+        roof.update({"traffic": traffic_of(mode, N)[0], "kernel_ms": kernel_ms,
                      "kernel": "grouped_tc_kernel",
                      "bound_times_ms": {"tensor": t_tensor * 1e3, "hbm": t_hbm * 1e3},
                      "peak_source": peaks["source"]})
@@ -1140,10 +1305,14 @@ def main():
         # that fraction is reported beside it for such launches only
         peak_s = peaks.get("bf16_tflops_sustained", FALLBACK["bf16_tflops_sustained"]) * \
             NOMINAL_RATIO[kdtype]
+        traffic, tnote = traffic_of(mode, N)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": TRAFFIC.get((mode, N)),
+                "frac": achieved / peak, "traffic": traffic, "traffic_note": tnote,
                 "kernel_ms": kernel_ms,
-                "peak_source": f"{peaks['source']} bf16 x nominal {kdtype}/bf16 ratio",
+                "work_per_launch": f"{max(1, main_res['products'])} slice products x 2N^3 "
+                                   f"= {main_res['flops_per_step'] * max(1, main_res['products']):.4g}"
+                                   " flop" if main_res["products"] > 1 else "2N^3 flop",
+                "peak_source": f"{peaks['source']} bf16 burst x nominal {kdtype}/bf16 ratio",
                 "kernel": "dense_tc_kernel" if mode in ("tf32", "bf16") else "split_gemm_kernel"}
         if kernel_ms >= 10.0:
             roof.update({"peak_sustained": peak_s, "frac_sustained": achieved / peak_s})
@@ -1153,7 +1322,7 @@ def main():
 
     modes = {}
     if not args.no_extras and rank == 0 and ws == 1 and mode != "grouped":
-        for m2, n2 in [("bf16", N), ("f32_split", N), ("f64_split_f32in", N),
+        for m2, n2 in [("tf32", N), ("bf16", N), ("f32_split", N), ("f64_split_f32in", N),
                        ("f64_split_f32in_e4m3", N), ("f32_simt", N // 2),
                        ("f64", N // 4)]:
             if m2 == mode:
@@ -1165,9 +1334,25 @@ def main():
             except Exception as e:  # report, do not hide
                 modes[m2] = {"error": str(e)}
 
+        # a short run of the serving stream (each arrival its own shape)
+        try:
+            ops = ServeOperands(nbuf=2)
+            modes["serve"] = bench_serve(ops, args.serve_rate, min(args.serve_seconds, 5.0),
+                                         energy=energy)
+            modes["serve"]["workload"] = (f"Poisson arrivals {args.serve_rate}/s for "
+                                          f"{min(args.serve_seconds, 5.0)} s, each its own "
+                                          "(m, n, p): m,p logU[64,4096], n logU[64,8192]; "
+                                          "FP32-acc or FP64-acc split requests")
+            del ops
+        except Exception as e:  # report, do not hide
+            modes["serve"] = {"error": str(e)}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu and mode != "grouped":
-        cpu = cpu_baseline(N, "f32")
+        if rows_c is not None:
+            cpu = cpu_baseline_split(mode, N, rows_c, check_idx)
+        else:
+            cpu = cpu_baseline(N, "f32")
 
     if rank == 0:
         if mode == "grouped":
@@ -1185,17 +1370,23 @@ def main():
                       main_res["graph_seconds_per_step"] / 1e12}
         else:
             metric, config = square_metric_config(mode, N, ws)
+        if cpu is not None and "rel_err_vs_oracle" in cpu:
+            tol = 1e-5 if mode == "f32_split" else 1e-12
+            config["error_check"] = (f"relative Frobenius error vs the FP64 oracle on "
+                                     f"{cpu['rows_checked']} sampled rows per input kind, "
+                                     f"tolerance {tol:g}")
         line = {
             "metric": metric,
             "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"tf32": "tf32", "bf16": "bf16", "f32_split": "bf16x6",
-                      "f64_split_f32in": "bf16-digits",
-                      "f64_split_f32in_e4m3": "e4m3-digits", "f64": "f64",
+                      "f64_split_f32in": "f64 via bf16 integer digits (exact int accumulation)",
+                      "f64_split_f32in_e4m3": "f64 via e4m3 integer digits", "f64": "f64",
                       "f32_simt": "f32", "grouped": "bf16"}[mode],
             "data": "synthetic",
             "config": config,
+            "rel_err_vs_oracle": (cpu or {}).get("rel_err_vs_oracle"),
             "rel_err_sampled_rows": main_res.get("rel_err_sampled_rows"),
             "roofline": roof,
             "cpu_baseline": cpu,

@@ -81,7 +81,7 @@ typedef struct {
     int32_t products;                    /* slice products issued per K block, else 1 */
     int32_t grid;                        /* CTAs launched for the main kernel */
     int64_t tiles;                       /* output tiles */
-    int32_t kernels;                     /* kernel launches made by this call */
+    int32_t kernels;                     /* kernel launches made by this call (memsets not counted) */
     int32_t padded;                      /* 1 if operands were copied to padded pitches */
 } moa_stats;
 
@@ -282,24 +282,29 @@ int moa_serve_destroy(moa_server* s);
 /* ---------------------------------------------------------------------- */
 
 /* C := A . B in the FP32-accuracy split mode (as moa_gemm_ex with
- * MOA_F32_SPLIT), for callers that cannot allocate device memory: code inside
- * a graph-capture region that must not allocate, hosts with a fixed start-up
- * memory plan, plugins confined to another runtime's pool.  The paper has no
+ * MOA_F32_SPLIT), for callers that may not allocate device memory at all:
+ * real-time or safety-certified hosts whose device memory is fixed at
+ * start-up (a run-time cudaMalloc can block, synchronise the device or fail
+ * late), plugins inside another runtime's memory pool that are handed no
+ * allocator, and deployments with a static memory plan.  The paper has no
  * counterpart; this is a deployment convenience of this library.
  *
  * A (m x n), B (n x p) and C (m x p) are FP32 row-major device arrays owned by
  * the caller, A and B 16-byte aligned.  The scratch (three BF16 slice planes
- * of A and of B) lives in one static device array of 32 MiB that every GPU
- * loading this library holds until exit; problems whose slices do not fit
+ * of A and of B; for few-tile problems also split-K counters and FP32 partial
+ * tiles) lives in one static device array of 32 MiB that every GPU loading
+ * this library holds until exit; problems whose scratch does not fit
  * (moa_gemm_workspace_size(m, n, p, MOA_F32_SPLIT, 0) > 32 MiB) are rejected
  * with MOA_ERR_WORKSPACE and nothing is launched.  No cudaMalloc, cudaFree or
  * allocating library routine is called.
  *
  * The first call on each device (with that device current) looks up the
  * array's device address with cudaGetSymbolAddress; make that first call
- * before any stream capture begins.  All calls share the array: calls whose
- * work overlaps on the GPU (other streams, unordered host threads) race on
- * it, so serialise them.  Asynchronous on `stream` like moa_gemm_ex. */
+ * before any stream capture begins.  All calls share the array and find the
+ * previous call's contents there; each call clears what must start at zero
+ * (the split-K counters) on its own stream.  Calls whose work overlaps on the
+ * GPU (other streams, unordered host threads) race on the array, so
+ * serialise them.  Asynchronous on `stream` like moa_gemm_ex. */
 int moa_gemm_f32split_noalloc(int64_t m, int64_t n, int64_t p, const float* A, const float* B,
                               float* C, void* stream);
 

@@ -68,7 +68,11 @@ def build(force: bool = False, verbose_ptxas: bool = False, quiet: bool = True) 
     for _, c, out in results:
         if out and (verbose_ptxas or not quiet):
             sys.stdout.write(out)
-    if changed or force or not os.path.exists(LIB):
+    # relink also when an object is newer than the library (an earlier build
+    # compiled it but stopped before linking)
+    stale = not os.path.exists(LIB) or any(
+        os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs)
+    if changed or force or stale:
         tmp = LIB + f".tmp{os.getpid()}"
         cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -84,6 +84,13 @@ size_t g_ws_bytes[kMaxDev] = {0};
 
 }  // namespace
 
+// The host-side argument checks of moa_gemm_ex (mode, sizes, pointers,
+// alignment), for entry points that size their scratch before dispatching.
+int validate_gemm_args(int64_t m, int64_t n, int64_t p, int dt, const void* A, const void* B,
+                       const void* C) {
+    return validate(m, n, p, dt, A, B, C);
+}
+
 size_t workspace_bytes(int64_t m, int64_t n, int64_t p, moa_dtype dt, int slices) {
     if (m <= 0 || p <= 0 || n <= 0) return 0;
     if (is_tc_dense(dt)) return dense_ws(m, n, p, dt).total;
@@ -123,7 +130,7 @@ int gemm_ex_impl(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, c
     if (n == 0) {
         cudaError_t e = cudaMemsetAsync(C, 0, static_cast<size_t>(m) * p * out_size(dt), s);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(C)");
-        if (st) st->kernels = 1;
+        if (st) st->kernels = 0;   // a memset of C, no kernel
         return MOA_OK;
     }
     const size_t need = workspace_bytes(m, n, p, dt, slices);

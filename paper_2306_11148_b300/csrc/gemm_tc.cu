@@ -321,12 +321,11 @@ int launch_cfg(int64_t m, int64_t n, int64_t p, const void* A, int64_t lda, cons
     if (!args.status) return MOA_ERR_CUDA;
 
     auto kern = dense_tc_kernel<ESIZE, BLOCK_N, STAGES, BKM, MT>;
-    static bool attr_set = false;   // per instantiation; the attribute is per device function
-    if (!attr_set) {
-        cudaError_t e =
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(dense_tc)");
-        attr_set = true;
+    static std::atomic<uint64_t> attr_done{0};   // per instantiation, per device
+    {
+        const int rc = smem_attr_once(reinterpret_cast<const void*>(kern), Cfg::SMEM, attr_done,
+                                      "cudaFuncSetAttribute(dense_tc)");
+        if (rc != MOA_OK) return rc;
     }
     const long tiles = static_cast<long>(args.tiles_m) * args.tiles_n;
     const int grid = static_cast<int>(std::min<long>(tiles, num_sms()));

@@ -413,12 +413,11 @@ int launch_kernel(uint8_t* dev, const Layout& L, int grid, cudaStream_t s) {
     a.wait_limit_ns = wait_limit_ns();
     a.status = launch_status_ptr();
     if (!a.status) return MOA_ERR_CUDA;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(grouped_tc_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(grouped)");
-        attr_set = true;
+    static std::atomic<uint64_t> attr_done{0};   // per device
+    {
+        const int rc = smem_attr_once(reinterpret_cast<const void*>(grouped_tc_kernel), kGSmem,
+                                      attr_done, "cudaFuncSetAttribute(grouped)");
+        if (rc != MOA_OK) return rc;
     }
     prof_begin(s);
     grouped_tc_kernel<<<grid, kGThreads, kGSmem, s>>>(a);

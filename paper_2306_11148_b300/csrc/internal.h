@@ -1,6 +1,7 @@
 // internal.h -- declarations shared by the translation units of libmoa.so
 // (not part of the public ABI; see include/moa.h for that).
 #pragma once
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <string>
@@ -70,6 +71,12 @@ int* launch_status_ptr();
 void set_status_override(int* p);
 uint64_t wait_limit_ns();
 int num_sms();
+// Raises `func`'s dynamic shared-memory limit to `bytes` on the current
+// device, once per device (the attribute belongs to the device context, so
+// a process that launches on several GPUs needs it on each).  `done` is the
+// caller's per-kernel record (bit d: device d set); devices numbered 64 and
+// above are set on every call.
+int smem_attr_once(const void* func, int bytes, std::atomic<uint64_t>& done, const char* what);
 
 // ------------------------------------------------------------------ TMA maps
 // 2-D tiled map over a row-major matrix of `outer` rows x `inner` columns with

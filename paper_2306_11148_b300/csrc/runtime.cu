@@ -153,6 +153,16 @@ int num_sms() {
     return g_sms[d];
 }
 
+int smem_attr_once(const void* func, int bytes, std::atomic<uint64_t>& done, const char* what) {
+    const int d = current_device();
+    const uint64_t bit = (d >= 0 && d < 64) ? (1ull << d) : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return MOA_OK;
+    cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    if (bit) done.fetch_or(bit, std::memory_order_acq_rel);
+    return MOA_OK;
+}
+
 uint64_t wait_limit_ns() {
     std::lock_guard<std::mutex> lk(g_mu);
     if (g_wait_limit_ns == 0) {

@@ -36,6 +36,7 @@
 #include <cstdio>
 #include <cstdlib>
 
+#include "fpbits.cuh"
 #include "internal.h"
 #include "ptx.cuh"
 #include "split.h"
@@ -131,69 +132,6 @@ __global__ void split3_pair_kernel(const float* __restrict__ A, int64_t m, int64
     else
         split3_part(B, n, p, ldb, b_out, b_plane, vb, status, blockIdx.x - ga, gridDim.x - ga);
 }
-
-template <typename T>
-struct Bits;
-template <>
-struct Bits<double> {
-    using U = unsigned long long;
-    static constexpr U kAbsMask = 0x7FFFFFFFFFFFFFFFull;
-    static constexpr U kInf = 0x7FF0000000000000ull;
-    __device__ static U abs_bits(double x) {
-        return static_cast<U>(__double_as_longlong(x)) & kAbsMask;
-    }
-    // frexp exponent of the non-negative value with bit pattern M (0 for 0).
-    __device__ static int frexp_exp(U M) {
-        if (M == 0) return 0;
-        const int ex = static_cast<int>(M >> 52);
-        if (ex > 0) return ex - 1022;
-        return (64 - __clzll(static_cast<long long>(M))) - 1074;
-    }
-    // round-half-even(x * 2^k) as an integer; requires |x| * 2^k < 2^62.
-    __device__ static long long round_scaled(double x, int k) {
-        const U b = static_cast<U>(__double_as_longlong(x));
-        const bool neg = (b >> 63) != 0;
-        const int ex = static_cast<int>((b >> 52) & 0x7FF);
-        U mant = b & 0xFFFFFFFFFFFFFull;
-        int E;
-        if (ex == 0) {
-            E = -1074;
-        } else {
-            mant |= 1ull << 52;
-            E = ex - 1075;
-        }
-        if (mant == 0) return 0;
-        const int sh = E + k;
-        U D;
-        if (sh >= 0) {
-            D = mant << sh;
-        } else {
-            const int kk = -sh;
-            if (kk > 54) {
-                D = 0;
-            } else {
-                const U q = mant >> kk;
-                const U rem = mant & ((1ull << kk) - 1);
-                const U half = 1ull << (kk - 1);
-                D = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
-            }
-        }
-        return neg ? -static_cast<long long>(D) : static_cast<long long>(D);
-    }
-};
-template <>
-struct Bits<float> {
-    using U = unsigned int;
-    static constexpr U kAbsMask = 0x7FFFFFFFu;
-    static constexpr U kInf = 0x7F800000u;
-    __device__ static U abs_bits(float x) { return __float_as_uint(x) & kAbsMask; }
-    __device__ static int frexp_exp(U M) {
-        if (M == 0) return 0;
-        const int ex = static_cast<int>(M >> 23);
-        if (ex > 0) return ex - 126;
-        return (32 - __clz(static_cast<int>(M))) - 149;
-    }
-};
 
 // Digit generator of one element: D = round_half_even(x * 2^k) written as
 // balanced radix-2^beta digits from the bottom, d_s for s = S-1 .. 1 in
@@ -1466,12 +1404,12 @@ template <int BN, int MODE, int FMT, bool SK = false>
 static int launch_split_cfg(const SplitArgs& a, const CUtensorMap& tmA, const CUtensorMap& tmB,
                             cudaStream_t s, moa_stats* st) {
     using Cfg = SplitCfg<BN, MODE, FMT>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel<BN, MODE, FMT, SK>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(split_gemm)");
-        attr_set = true;
+    static std::atomic<uint64_t> attr_done{0};   // per instantiation, per device
+    {
+        const int rc = smem_attr_once(
+            reinterpret_cast<const void*>(split_gemm_kernel<BN, MODE, FMT, SK>), Cfg::kSmem,
+            attr_done, "cudaFuncSetAttribute(split_gemm)");
+        if (rc != MOA_OK) return rc;
     }
     const long tiles = static_cast<long>(a.tiles_m) * a.tiles_n;
     const int grid =
@@ -1678,7 +1616,6 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
         if (split_units) {
             cudaError_t e = cudaMemsetAsync(a.cnt, 0, L.cnt_bytes, s);
             if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(split-K counters)");
-            ++kernels;
         }
         a.f64 = 0;
         a.levels = 1;
@@ -1706,7 +1643,7 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
             digit_prepasses<float>(L, m, n, p, static_cast<const float*>(A),
                                    static_cast<const float*>(B), beta, h, eA, eB, cmax, a_sl, b_sl,
                                    status, s, split_units ? C : nullptr, a.cnt);
-        kernels += 3;   // the column-max clear, the exponent pass and the digit pass
+        kernels += 2;   // the exponent pass and the digit pass (the column-max clear is a memset)
         a.f64 = 1;
         a.levels = S;
         a.beta = beta;

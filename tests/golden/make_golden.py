@@ -1,4 +1,4 @@
-"""Writes the oracle regression records of tests/golden (see README.md).
+"""Writes the oracle regression records of tests/golden from the oracle alone.
 Calls only oracle/ and the seeded input generators."""
 import os
 import sys
