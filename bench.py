@@ -311,13 +311,13 @@ def aggregate(flops_per_step, steps, seconds, ws):
 # ------------------------------------------------------------------ workloads
 MODE_OF = {"split_f64": "f64_split_f32in", "square": "tf32", "bf16": "bf16",
            "split_f32": "f32_split",
-           "split_f64_e4m3": "f64_split_f32in_e4m3",
+           "split_f64_e4m3": "f64_split_f32in_e4m3", "crt_f64": "f64_crt_f32in",
            "f64": "f64", "simt": "f32_simt",
            "grouped": "grouped", "serve": "serve", "energy_n": "energy_n",
            "tiles": "tiles", "peaks": "peaks"}
 
 
-SPLIT_F32IN = ("f32_split", "f64_split_f32in", "f64_split_f32in_e4m3")
+SPLIT_F32IN = ("f32_split", "f64_split_f32in", "f64_split_f32in_e4m3", "f64_crt_f32in")
 
 
 def make_inputs(mode, N, scaled=None):
@@ -1086,6 +1086,9 @@ METRIC_OF = {
     "f64_split_f32in_e4m3": "GEMM TFLOP/s (FP64-accurate ONF GEMM of FP32 inputs: FP8 E4M3 "
                             "integer-digit slices on the tensor cores)",
     "f32_split": "GEMM TFLOP/s (FP32-accurate ONF GEMM: three BF16 slices, six products)",
+    "f64_crt_f32in": "GEMM TFLOP/s (FP64-accurate ONF GEMM of FP32 inputs: BF16 modular slices "
+                     "on the tensor cores, exact integer product by the Chinese remainder "
+                     "theorem)",
 }
 INPUTS_OF = {m: "FP32 i.i.d. N(0,1), seed 0" for m in SPLIT_F32IN}
 
@@ -1095,7 +1098,7 @@ def square_metric_config(mode, N, ws):
     metric = METRIC_OF.get(mode, f"GEMM TFLOP/s (ONF GEMM, {mode} path)")
     # bytes of A and B and of C per element, against the 126 MB L2
     in_b, out_b = {"bf16": (2, 4), "f64": (8, 8), "f64_split_f32in": (4, 8),
-                   "f64_split_f32in_e4m3": (4, 8)}.get(mode, (4, 4))
+                   "f64_split_f32in_e4m3": (4, 8), "f64_crt_f32in": (4, 8)}.get(mode, (4, 4))
     mb = N * N * (2 * in_b + out_b) / 1e6
     l2 = (f"inputs larger than L2 (A, B, C: {mb:.0f} MB)" if mb > L2_MB else
           f"A, B, C fit in L2 ({mb:.1f} MB): not flushed between steps (warm-cache figure)")
@@ -1274,7 +1277,7 @@ def main():
     # / that kernel's own CUDA-event duration, recorded by the library on the
     # launching stream.
     kdtype = {"tf32": "tf32", "bf16": "bf16", "f32_split": "bf16",
-              "f64_split_f32in": "bf16", "f64_split_f32in_e4m3": "fp8",
+              "f64_split_f32in": "bf16", "f64_split_f32in_e4m3": "fp8", "f64_crt_f32in": "bf16",
               "grouped": "bf16"}.get(mode)
     kernel_ms = main_res["kernel_seconds"] / args.steps * 1e3
     if mode == "grouped":
@@ -1313,7 +1316,8 @@ def main():
                                    f"= {main_res['flops_per_step'] * max(1, main_res['products']):.4g}"
                                    " flop" if main_res["products"] > 1 else "2N^3 flop",
                 "peak_source": f"{peaks['source']} bf16 burst x nominal {kdtype}/bf16 ratio",
-                "kernel": "dense_tc_kernel" if mode in ("tf32", "bf16") else "split_gemm_kernel"}
+                "kernel": {"tf32": "dense_tc_kernel", "bf16": "dense_tc_kernel",
+                           "f64_crt_f32in": "crt_gemm_kernel"}.get(mode, "split_gemm_kernel")}
         if kernel_ms >= 10.0:
             roof.update({"peak_sustained": peak_s, "frac_sustained": achieved / peak_s})
     else:
@@ -1323,7 +1327,7 @@ def main():
     modes = {}
     if not args.no_extras and rank == 0 and ws == 1 and mode != "grouped":
         for m2, n2 in [("tf32", N), ("bf16", N), ("f32_split", N), ("f64_split_f32in", N),
-                       ("f64_split_f32in_e4m3", N), ("f32_simt", N // 2),
+                       ("f64_crt_f32in", N), ("f64_split_f32in_e4m3", N), ("f32_simt", N // 2),
                        ("f64", N // 4)]:
             if m2 == mode:
                 continue
@@ -1382,7 +1386,9 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": {"tf32": "tf32", "bf16": "bf16", "f32_split": "bf16x6",
                       "f64_split_f32in": "f64 via bf16 integer digits (exact int accumulation)",
-                      "f64_split_f32in_e4m3": "f64 via e4m3 integer digits", "f64": "f64",
+                      "f64_split_f32in_e4m3": "f64 via e4m3 integer digits",
+                      "f64_crt_f32in": "f64 via bf16 modular slices (exact integer CRT)",
+                      "f64": "f64",
                       "f32_simt": "f32", "grouped": "bf16"}[mode],
             "data": "synthetic",
             "config": config,

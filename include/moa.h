@@ -28,7 +28,9 @@
  *
  * Precision modes (moa_dtype): see the enum.  Tolerances the test suite
  * holds each mode to, as relative Frobenius error against the FP64 oracle:
- * MOA_F64 1e-12, MOA_F64_SPLIT_* (both digit formats) 1e-12, MOA_F32_SPLIT 1e-5, MOA_F32_TF32
+ * MOA_F64 1e-12, MOA_F64_SPLIT_* (both digit formats) and MOA_F64_CRT_* 1e-12 (the
+ * latter also bit-exact against the oracle's exact integer product of the
+ * scaled operands), MOA_F32_SPLIT 1e-5, MOA_F32_TF32
  * 5e-3, MOA_BF16 1e-2 (and bit-exact on integer-valued inputs in {-8..8}
  * for every mode).
  */
@@ -71,7 +73,15 @@ typedef enum {
                               /*   [-16, 16], exact in E4M3) on tcgen05 kind::f8f6f4.        */
                               /*   slices: 4..12, default 10 (a 49-bit span per operand);   */
                               /*   55 slice products at twice the BF16 rate.                 */
-    MOA_F64_SPLIT_F64IN_E4M3 = 8  /* A,B,C FP64.  As above with FP64 inputs.                 */
+    MOA_F64_SPLIT_F64IN_E4M3 = 8, /* A,B,C FP64.  As above with FP64 inputs.                 */
+    MOA_F64_CRT_F32IN = 9,    /* A,B FP32, C FP64.  Modular slices: rows of A and columns of  */
+                              /*   B scaled to t-bit integers, their residues modulo M        */
+                              /*   pairwise-coprime moduli <= 256 as BF16 planes, one exact    */
+                              /*   tensor-core GEMM per modulus, the exact integer product    */
+                              /*   recovered by the Chinese remainder theorem and rounded     */
+                              /*   once to FP64.  slices = M: 8..16, default 14 (15 once      */
+                              /*   n > 36639), t the largest with n 2^(2t+1) < prod(moduli).  */
+    MOA_F64_CRT_F64IN = 10    /* A,B,C FP64.  As above with FP64 inputs.                     */
 } moa_dtype;
 
 /* Optional per-call report (may be NULL). */
@@ -101,7 +111,8 @@ int moa_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt,
 /* Bytes of workspace moa_gemm_ex needs for this problem (0 if none).
  * slices: split modes only (0 = default); ignored otherwise.  Allowed slice
  * counts: MOA_F32_SPLIT 3; MOA_F64_SPLIT_F32IN / _F64IN 3..8 (default 7);
- * the _E4M3 forms 4..12 (default 10).  Returns 0 for a count not allowed. */
+ * the _E4M3 forms 4..12 (default 10); MOA_F64_CRT_* 8..16 moduli (default 14,
+ * 15 once n > 36639).  Returns 0 for a count not allowed. */
 size_t moa_gemm_workspace_size(int64_t m, int64_t n, int64_t p, moa_dtype dt, int slices);
 
 /* C := A . B on `stream` with a caller-provided device workspace of at least

@@ -10,6 +10,7 @@
 #include <mutex>
 #include <string>
 
+#include "crt.h"
 #include "internal.h"
 #include "split.h"
 
@@ -71,7 +72,8 @@ int validate(int64_t m, int64_t n, int64_t p, int dt, const void* A, const void*
                     ic = reinterpret_cast<uintptr_t>(C);
     if (ia % in_size(d) || ib % in_size(d) || ic % out_size(d))
         return fail(MOA_ERR_ALIGN, "pointer not aligned to its element size");
-    if ((is_tc_dense(d) || is_split(d)) && m > 0 && n > 0 && p > 0 && (ia % 16 || ib % 16))
+    if ((is_tc_dense(d) || is_split(d) || is_crt(d)) && m > 0 && n > 0 && p > 0 &&
+        (ia % 16 || ib % 16))
         return fail(MOA_ERR_ALIGN, "tensor-core modes need 16-byte aligned A and B");
     return MOA_OK;
 }
@@ -95,6 +97,7 @@ size_t workspace_bytes(int64_t m, int64_t n, int64_t p, moa_dtype dt, int slices
     if (m <= 0 || p <= 0 || n <= 0) return 0;
     if (is_tc_dense(dt)) return dense_ws(m, n, p, dt).total;
     if (is_split(dt)) return split_workspace_bytes(m, n, p, dt, slices);
+    if (is_crt(dt)) return crt_workspace_bytes(m, n, p, dt, slices);
     return 0;
 }
 
@@ -185,6 +188,9 @@ int gemm_ex_impl(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, c
             }
             return rc;
         }
+        case MOA_F64_CRT_F32IN:
+        case MOA_F64_CRT_F64IN:
+            return crt_gemm(m, n, p, dt, A, B, C, slices, ws, ws_bytes, s, st);
         default:
             return split_gemm(m, n, p, dt, A, B, C, slices, ws, ws_bytes, s, st);
     }

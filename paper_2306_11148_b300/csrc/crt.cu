@@ -1,0 +1,913 @@
+// crt.cu -- FP64-accuracy ONF GEMM from modular slices (MOA_F64_CRT_F32IN,
+// MOA_F64_CRT_F64IN).
+//
+// The result is Eq. (eq:dnf) of Sec. 2, C[(i*p)+j] := sum_k A[(i*n)+k] *
+// B[(k*p)+j], to FP64 accuracy; the slicing is not in the paper (it is the
+// residue-number form of error-free slicing, "Ozaki scheme II" of Ozaki,
+// Uchino & Imamura, 2025):
+//
+// * each row i of A is scaled by 2^(t - eA_i) (eA_i the frexp exponent of
+//   max_k |A[i,k]|) and rounded to the nearest integer A'[i,k], |A'| <= 2^t;
+//   each column j of B likewise by 2^(t - eB_j) to B'[k,j];
+// * for M pairwise-coprime moduli q_l <= 256 (product P), the symmetric
+//   residues A' mod q_l and B' mod q_l are integers of magnitude <= 128,
+//   exact in BF16; one BF16 tensor-core GEMM per modulus forms
+//   sum_k (A' mod q_l)(B' mod q_l), exact in FP32 over K chunks of 1024
+//   (1024 * 128^2 = 2^24), reduced modulo q_l after every chunk;
+// * the Chinese remainder theorem recovers C' = A'B' itself from its M
+//   residues, because t is chosen so that n * 2^(2t) < P / 2; C' is rounded
+//   once to FP64 and scaled by 2^(eA_i + eB_j - 2t).
+//
+// The result is therefore exactly fl(2^(eA_i + eB_j - 2t) * (A'B')[i,j]):
+// deterministic, independent of the K order, with M slice GEMMs (14 for
+// n <= 36639 at t >= 47) instead of the S(S+1)/2 = 28 of the integer-digit
+// form.
+//
+// Launches per call: a clear of the column maxima, the exponent pass, the
+// residue pass (A and B in one launch), the residue GEMM (one persistent
+// launch over (modulus, tile, K slice) units, modulus-major so that the L2
+// holds one modulus's planes at a time) and the reconstruction pass.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+
+#include "crt.h"
+#include "fpbits.cuh"
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace moa {
+
+namespace {
+
+// The moduli: 256, 255, 254, ... keeping each integer coprime to every one
+// taken before it (254 = 2 * 127 shares 2 with 256, 252 likewise, 249 = 3 * 83
+// shares 3 with 255, ...).  Every symmetric residue lies in [-128, 128].
+__host__ __device__ constexpr uint32_t crt_mod(int l) {
+    return l == 0 ? 256u : l == 1 ? 255u : l == 2 ? 253u : l == 3 ? 251u : l == 4 ? 247u
+         : l == 5 ? 241u : l == 6 ? 239u : l == 7 ? 233u : l == 8 ? 229u : l == 9 ? 227u
+         : l == 10 ? 223u : l == 11 ? 217u : l == 12 ? 211u : l == 13 ? 199u : l == 14 ? 197u
+         : 193u;
+}
+
+using u128 = unsigned __int128;
+using i128 = __int128;
+
+// Per-call constants of the reconstruction (kernel parameter).
+struct CrtConsts {
+    int M;                               // moduli in use
+    int t;                               // operand bits
+    uint64_t w_lo[kCrtMaxModuli];        // CRT weights W_l = (P / q_l) * ((P / q_l)^-1 mod q_l)
+    uint64_t w_hi[kCrtMaxModuli];        //   mod P, as two 64-bit words
+    uint64_t P_lo, P_hi;                 // P = prod q_l
+    double invP;                         // 1 / P, rounded
+};
+
+// ---------------------------------------------------------------- host arithmetic
+u128 crt_product(int M) {
+    u128 P = 1;
+    for (int l = 0; l < M; ++l) P *= crt_mod(l);
+    return P;
+}
+
+// x^-1 mod q for x coprime to q (extended Euclid on small integers).
+int64_t inv_mod(int64_t x, int64_t q) {
+    int64_t a = ((x % q) + q) % q, b = q, u = 1, v = 0;
+    while (b != 0) {
+        const int64_t k = a / b;
+        a -= k * b;
+        u -= k * v;
+        int64_t tmp = a; a = b; b = tmp;
+        tmp = u; u = v; v = tmp;
+    }
+    return ((u % q) + q) % q;
+}
+
+CrtConsts crt_consts(int M, int t) {
+    CrtConsts c{};
+    c.M = M;
+    c.t = t;
+    const u128 P = crt_product(M);
+    c.P_lo = static_cast<uint64_t>(P);
+    c.P_hi = static_cast<uint64_t>(P >> 64);
+    c.invP = 1.0 / (static_cast<double>(c.P_hi) * 18446744073709551616.0 +
+                    static_cast<double>(c.P_lo));
+    for (int l = 0; l < M; ++l) {
+        const u128 Ml = P / crt_mod(l);
+        const int64_t Ml_mod = static_cast<int64_t>(Ml % crt_mod(l));
+        const int64_t y = inv_mod(Ml_mod, crt_mod(l));
+        const u128 W = (Ml * static_cast<u128>(y)) % P;   // Ml * y < P * 256 < 2^128
+        c.w_lo[l] = static_cast<uint64_t>(W);
+        c.w_hi[l] = static_cast<uint64_t>(W >> 64);
+    }
+    return c;
+}
+
+// ---------------------------------------------------------------- exponent pass
+// One warp per row: eA[r] = frexp exponent of max_k |A[r,k]|.  Flags NaN/Inf.
+template <typename T>
+__device__ void crt_row_exp_part(const T* __restrict__ X, int64_t rows, int64_t cols,
+                                 int* __restrict__ e_out, int* status, int64_t bid, int64_t nblk) {
+    using B = Bits<T>;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = nblk * (blockDim.x >> 5);
+    bool bad = false;
+    for (int64_t r = bid * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
+        typename B::U mx = 0;
+        for (int64_t c = lane; c < cols; c += 32) mx = max(mx, B::abs_bits(X[r * cols + c]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) {
+            bad |= mx >= B::kInf;
+            e_out[r] = B::frexp_exp(mx);
+        }
+    }
+    if (bad) atomicCAS(status, kDevOk, kDevNonFinite);
+}
+
+// Column maxima of |B| (bit patterns) by atomicMax over chunks of rows: block
+// bid covers 256 columns from 256 (bid % gx) and rows chunk * (bid / gx) ..
+template <typename T>
+__device__ void crt_col_max_part(const T* __restrict__ X, int64_t rows, int64_t cols,
+                                 int64_t chunk, typename Bits<T>::U* __restrict__ cmax,
+                                 int64_t bid, int64_t gx) {
+    using B = Bits<T>;
+    const int64_t c = (bid % gx) * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    const int64_t r0 = (bid / gx) * chunk;
+    const int64_t r1 = min(rows, r0 + chunk);
+    typename B::U mx = 0;
+    for (int64_t r = r0; r < r1; ++r) mx = max(mx, B::abs_bits(X[r * cols + c]));
+    if (mx != 0) atomicMax(&cmax[c], mx);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    crt_exps_kernel(const T* __restrict__ A, int64_t m, int64_t n, const T* __restrict__ B,
+                    int64_t p, int64_t chunk, int* __restrict__ eA,
+                    typename Bits<T>::U* __restrict__ cmax, int* status, int rblocks, int64_t gx) {
+    const int b = static_cast<int>(blockIdx.x);
+    if (b < rblocks)
+        crt_row_exp_part(A, m, n, eA, status, b, rblocks);
+    else
+        crt_col_max_part(B, n, p, chunk, cmax, b - rblocks, gx);
+}
+
+// ---------------------------------------------------------------- residue pass
+// |x * 2^k| rounded half-even, as (sign, magnitude); requires the result
+// below 2^63.
+__device__ __forceinline__ uint64_t scaled_mag(float x, int k, bool& neg) {
+    const uint32_t b = __float_as_uint(x);
+    neg = (b >> 31) != 0;
+    const int ex = static_cast<int>((b >> 23) & 0xFF);
+    uint32_t mant = b & 0x7FFFFFu;
+    int E = -149;
+    if (ex != 0) {
+        mant |= 1u << 23;
+        E = ex - 150;
+    }
+    if (mant == 0) return 0;
+    const int sh = E + k;
+    if (sh >= 0) return static_cast<uint64_t>(mant) << sh;
+    const int kk = -sh;
+    if (kk > 25) return 0;
+    const uint32_t q = mant >> kk;
+    const uint32_t rem = mant & ((1u << kk) - 1u);
+    const uint32_t half = 1u << (kk - 1);
+    return q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u);
+}
+__device__ __forceinline__ uint64_t scaled_mag(double x, int k, bool& neg) {
+    const long long D = Bits<double>::round_scaled(x, k);
+    neg = D < 0;
+    return static_cast<uint64_t>(neg ? -D : D);
+}
+
+// Symmetric residue of a signed integer (sign, magnitude v < 2^63) modulo
+// crt_mod(l), in [-128, 128]: v = hi 2^32 + lo, reduced piecewise.  l is a
+// compile-time constant at every call (unrolled loops), so the divisions by
+// the modulus compile to multiplications.
+template <int L>
+__device__ __forceinline__ int sym_residue(uint64_t v, bool neg) {
+    constexpr uint32_t q = crt_mod(L);
+    constexpr uint32_t c32 = static_cast<uint32_t>((uint64_t(1) << 32) % q);
+    const uint32_t hi = static_cast<uint32_t>(v >> 32), lo = static_cast<uint32_t>(v);
+    uint32_t r = ((hi % q) * c32 + lo % q) % q;          // < 2^16 before the last %
+    int s = static_cast<int>(r);
+    if (s > static_cast<int>(q / 2) || (s == static_cast<int>(q / 2) && (q & 1u) == 0u))
+        s -= static_cast<int>(q);                        // [-(q/2), (q-1)/2]
+    return neg ? -s : s;
+}
+
+// BF16 bit patterns of two integers of magnitude <= 256 (exact in BF16),
+// packed low half first: the integer goes into the significand of
+// 1.5 * 2^23 and the offset is subtracted (both exact); the result has at
+// most 9 significant bits with its lowest one zero for |k| = 256, so its
+// upper 16 bits are its BF16 pattern.
+__device__ __forceinline__ uint32_t ints_bf16x2(int lo, int hi) {
+    const uint32_t flo =
+        __float_as_uint(__fsub_rn(__uint_as_float(0x4B400000u + static_cast<uint32_t>(lo)), 12582912.0f));
+    const uint32_t fhi =
+        __float_as_uint(__fsub_rn(__uint_as_float(0x4B400000u + static_cast<uint32_t>(hi)), 12582912.0f));
+    return (flo >> 16) | (fhi & 0xFFFF0000u);
+}
+
+template <typename T>
+__device__ __forceinline__ void load8(const T* __restrict__ X, int64_t r, int64_t cols, int64_t c0,
+                                      bool vec, T (&x)[8]) {
+    const T* src = X + r * cols + c0;
+    if (vec && c0 + 8 <= cols) {
+        if constexpr (sizeof(T) == 4) {
+            const float4 a = reinterpret_cast<const float4*>(src)[0];
+            const float4 b = reinterpret_cast<const float4*>(src)[1];
+            x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+            x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+        } else {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const double2 d = reinterpret_cast<const double2*>(src)[v];
+                x[2 * v] = d.x;
+                x[2 * v + 1] = d.y;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = (c0 + i < cols) ? src[i] : T(0);
+    }
+}
+
+// Writes the residue planes of 8 scaled integers (magnitudes v, signs neg)
+// at element offset o of every plane (one 16-byte store per plane).
+template <int L>
+__device__ __forceinline__ void store_planes(const uint64_t (&v)[8], const bool (&neg)[8], int M,
+                                             __nv_bfloat16* __restrict__ out, int64_t plane,
+                                             int64_t o) {
+    if constexpr (L < kCrtMaxModuli) {
+        if (L >= M) return;
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 8; i += 2)
+            w[i / 2] = ints_bf16x2(sym_residue<L>(v[i], neg[i]), sym_residue<L>(v[i + 1], neg[i + 1]));
+        *reinterpret_cast<uint4*>(out + L * plane + o) = make_uint4(w[0], w[1], w[2], w[3]);
+        store_planes<L + 1>(v, neg, M, out, plane, o);
+    }
+}
+
+// Residue planes of X (rows x cols, row-major) into M BF16 planes of row
+// pitch ld (a multiple of 8; zero pad); 8 consecutive elements per thread.
+// AXIS 0: exponent per row from e[r]; AXIS 1: exponent per column from the
+// column maximum cmax[c] (the threads of row 0 store it to e[c] and flag
+// NaN/Inf).
+template <typename T, int AXIS>
+__device__ void crt_residue_part(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
+                                 int* __restrict__ e, const typename Bits<T>::U* __restrict__ cmax,
+                                 int* status, int t, int M, int vec,
+                                 __nv_bfloat16* __restrict__ out, int64_t plane, int64_t bid,
+                                 int64_t nblk) {
+    const int64_t gpr = ld / 8;
+    const int64_t total = rows * gpr;
+    for (int64_t g = bid * blockDim.x + threadIdx.x; g < total; g += nblk * blockDim.x) {
+        const int64_t r = g / gpr, c0 = (g - r * gpr) * 8;
+        T x[8];
+        load8(X, r, cols, c0, vec != 0, x);
+        uint64_t v[8];
+        bool neg[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int64_t c = c0 + i;
+            int ex = 0;
+            if (c < cols) {
+                if (AXIS == 0) {
+                    ex = e[r];
+                } else {
+                    const typename Bits<T>::U mx = cmax[c];
+                    if (r == 0 && mx >= Bits<T>::kInf) atomicCAS(status, kDevOk, kDevNonFinite);
+                    ex = Bits<T>::frexp_exp(mx);
+                    if (r == 0) e[c] = ex;
+                }
+            }
+            v[i] = scaled_mag(x[i], t - ex, neg[i]);
+        }
+        store_planes<0>(v, neg, M, out, plane, r * ld + c0);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    crt_residue_kernel(const T* __restrict__ A, int64_t m, int64_t n, int64_t lda, int va,
+                       const int* __restrict__ eA, const T* __restrict__ B, int64_t p, int64_t ldb,
+                       int vb, int* __restrict__ eB, const typename Bits<T>::U* __restrict__ cmax,
+                       int* status, int t, int M, __nv_bfloat16* __restrict__ a_out,
+                       int64_t a_plane, __nv_bfloat16* __restrict__ b_out, int64_t b_plane,
+                       int ga) {
+    if (static_cast<int>(blockIdx.x) < ga)
+        crt_residue_part<T, 0>(A, m, n, lda, const_cast<int*>(eA), nullptr, status, t, M, va,
+                               a_out, a_plane, blockIdx.x, ga);
+    else
+        crt_residue_part<T, 1>(B, n, p, ldb, eB, cmax, status, t, M, vb, b_out, b_plane,
+                               blockIdx.x - ga, gridDim.x - ga);
+}
+
+// ---------------------------------------------------------------- residue GEMM
+constexpr int kBM = 128;
+constexpr int kBK = 64;            // BF16 elements per K block (128 bytes)
+constexpr int kChunkKB = 16;       // K blocks per exact FP32 chunk: 1024 * 128^2 = 2^24
+
+template <int BN>
+struct CrtCfg {
+    static constexpr int kAStage = kBM * 128;                // 128 rows x 128 B
+    static constexpr int kBChunk = kBK * 128;                // 64 K rows x 64 columns (MN-major)
+    static constexpr int kBStage = (BN / 64) * kBChunk;
+    static constexpr int kStageBytes = kAStage + kBStage;
+    static constexpr int kStages = BN == 256 ? 4 : 6;
+    static constexpr int kSmem = 1024 + kStages * kStageBytes + 256;
+    static_assert(kSmem <= 227 * 1024, "crt kernel shared memory");
+    static constexpr int kEpiWarps = 4 * (BN / 64);          // 32 rows x 64 columns each
+    static constexpr int kThreads = 64 + 32 * kEpiWarps;
+    static constexpr int kTmemCols = 2 * BN;                 // two chunk accumulators
+    static constexpr uint32_t kIdesc = make_idesc(1u, kBM, BN, 0u, 1u);
+};
+
+struct CrtGemmArgs {
+    uint8_t* R;                   // residue planes: (l * ks + s) x m x ldr bytes
+    int64_t m, n, p, ldr;
+    int tiles_m, tiles_n, num_kb, group_m;
+    int M, ks;
+    float qf[kCrtMaxModuli];      // moduli and their rounded reciprocals
+    float qinv[kCrtMaxModuli];
+    uint64_t wait_limit_ns;
+    int* status;
+};
+
+// Unit u: modulus l (slowest), tile t, K slice s (fastest).
+__device__ __forceinline__ void crt_unit(const CrtGemmArgs& a, int u, int& l, int& t, int& kb_lo,
+                                         int& kb_hi, int& s) {
+    const int per_l = a.tiles_m * a.tiles_n * a.ks;
+    l = u / per_l;
+    const int r = u - l * per_l;
+    t = r / a.ks;
+    s = r - t * a.ks;
+    kb_lo = static_cast<int>(static_cast<long long>(s) * a.num_kb / a.ks);
+    kb_hi = static_cast<int>(static_cast<long long>(s + 1) * a.num_kb / a.ks);
+}
+
+__device__ __forceinline__ void crt_tile_coords(int t, int tiles_m, int tiles_n, int group_m,
+                                                int& tm, int& tn) {
+    const int per_group = group_m * tiles_n;
+    const int g = t / per_group;
+    const int first_m = g * group_m;
+    const int gsize = min(tiles_m - first_m, group_m);
+    const int r = t - g * per_group;
+    tm = first_m + r % gsize;
+    tn = r / gsize;
+}
+
+// x (an integer-valued float, |x| <= 2^24) reduced modulo q to an integer
+// of magnitude <= q / 2 + 1: x - q * rint(x / q), with rint by the
+// magic-number addition (exact for |x / q| < 2^22) and the product
+// subtracted by one fused multiply-add (the result is exact).
+__device__ __forceinline__ float mod_reduce(float x, float q, float qinv) {
+    const float y = __fmul_rn(x, qinv);
+    const float k = __fsub_rn(__fadd_rn(y, 12582912.0f), 12582912.0f);
+    return __fmaf_rn(-k, q, x);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(CrtCfg<BN>::kThreads, 1)
+    crt_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    const CrtGemmArgs args) {
+    using Cfg = CrtCfg<BN>;
+    constexpr int kStages = Cfg::kStages;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                               ~static_cast<uintptr_t>(1023));
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + kStages * Cfg::kAStage;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kStages * Cfg::kBStage);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + kStages;
+    uint64_t* tfull = bars + 2 * kStages;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* drain = tempty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    CtaCtl* ctl = reinterpret_cast<CtaCtl*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const uint64_t limit = args.wait_limit_ns;
+    int* status = args.status;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], Cfg::kEpiWarps);
+        }
+        mbar_init(drain, 1);
+        ctl->abort = 0;
+        fence_barrier_init();
+    }
+    if (warp == 0 && lane == 0) {
+        prefetch_tmap(&tmA);
+        prefetch_tmap(&tmB);
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, Cfg::kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const int num_units = args.M * args.tiles_m * args.tiles_n * args.ks;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer: (unit, K block)
+            int stage = 0;
+            uint32_t phase = 0;
+            long issued = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
+                int l, t, kb_lo, kb_hi, s, tm, tn;
+                crt_unit(args, u, l, t, kb_lo, kb_hi, s);
+                crt_tile_coords(t, args.tiles_m, args.tiles_n, args.group_m, tm, tn);
+                for (int kb = kb_lo; kb < kb_hi; ++kb) {
+                    if (!mbar_wait(&empty[stage], phase ^ 1u, ctl, limit, status)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[stage], Cfg::kStageBytes);
+                    tma_load_3d(sA + stage * Cfg::kAStage, &tmA, &full[stage], kb * kBK, tm * kBM, l);
+#pragma unroll
+                    for (int c = 0; c < BN / 64; ++c)
+                        tma_load_3d(sB + stage * Cfg::kBStage + c * Cfg::kBChunk, &tmB, &full[stage],
+                                    tn * BN + c * 64, kb * kBK, l);
+                    ++issued;
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                // Let the loads already in flight land before the CTA exits.
+                CtaCtl local{0};
+                const long outstanding = issued < kStages ? issued : kStages;
+                for (long q = 1; q <= outstanding; ++q) {
+                    const long idx = issued - q;
+                    mbar_wait(&full[idx % kStages], static_cast<uint32_t>((idx / kStages) & 1),
+                              &local, limit, status);
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer: one TMEM chunk accumulator per chunk
+            int stage = 0;
+            uint32_t phase = 0;
+            long cnt = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
+                int l, t, kb_lo, kb_hi, s;
+                crt_unit(args, u, l, t, kb_lo, kb_hi, s);
+                for (int kb0 = kb_lo; kb0 < kb_hi && ok; kb0 += kChunkKB, ++cnt) {
+                    const int buf = static_cast<int>(cnt & 1);
+                    const uint32_t bph = static_cast<uint32_t>((cnt >> 1) & 1);
+                    if (!mbar_wait(&tempty[buf], bph ^ 1u, ctl, limit, status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d = tmem_base + static_cast<uint32_t>(buf * BN);
+                    const int kb1 = min(kb_hi, kb0 + kChunkKB);
+                    for (int kb = kb0; kb < kb1; ++kb) {
+                        if (!mbar_wait(&full[stage], phase, ctl, limit, status)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint64_t adesc =
+                            smem_desc_sw128(smem_u32(sA + stage * Cfg::kAStage), 16, 1024);
+                        const uint64_t bdesc =
+                            smem_desc_sw128(smem_u32(sB + stage * Cfg::kBStage), Cfg::kBChunk, 1024);
+                        // four MMAs of 16 K elements (32 bytes of A's rows) each
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            mma_f16(d, adesc + static_cast<uint64_t>((k * 32) >> 4),
+                                    bdesc + static_cast<uint64_t>((k * 16 * 128) >> 4), Cfg::kIdesc,
+                                    (kb == kb0 && k == 0) ? 0u : 1u);
+                        mma_commit(&empty[stage]);
+                        if (++stage == kStages) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                    if (!ok) break;
+                    mma_commit(&tfull[buf]);
+                }
+            }
+            // Every MMA issued above must finish before TMEM is released.
+            mma_commit(drain);
+            CtaCtl local{0};
+            mbar_wait(drain, 0, &local, limit, status);
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue: quadrant q = warp % 4 (32 rows), column group h
+        const int q = warp & 3;
+        const int h = (warp - 2) >> 2;
+        const uint32_t lane_base = static_cast<uint32_t>(q * 32) << 16;
+        long cnt = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
+            int l, t, kb_lo, kb_hi, s, tm, tn;
+            crt_unit(args, u, l, t, kb_lo, kb_hi, s);
+            crt_tile_coords(t, args.tiles_m, args.tiles_n, args.group_m, tm, tn);
+            const float qf = args.qf[l], qinv = args.qinv[l];
+            float acc[64];
+#pragma unroll
+            for (int i = 0; i < 64; ++i) acc[i] = 0.f;
+            for (int kb0 = kb_lo; kb0 < kb_hi; kb0 += kChunkKB, ++cnt) {
+                const int buf = static_cast<int>(cnt & 1);
+                const uint32_t bph = static_cast<uint32_t>((cnt >> 1) & 1);
+                ok = mbar_wait(&tfull[buf], bph, ctl, limit, status);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a_base =
+                    tmem_base + lane_base + static_cast<uint32_t>(buf * BN + h * 64);
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    uint32_t r[16];
+                    tmem_ld16(a_base + 16u * g, r);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        acc[g * 16 + i] =
+                            __fadd_rn(acc[g * 16 + i], mod_reduce(__uint_as_float(r[i]), qf, qinv));
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[buf]);
+            }
+            if (!ok) break;
+            // the unit's residues in [0, q) as bytes of plane (l, s)
+            const int64_t row = static_cast<int64_t>(tm) * kBM + q * 32 + lane;
+            const int64_t col0 = static_cast<int64_t>(tn) * BN + h * 64;
+            if (row < args.m && col0 < args.p) {
+                uint32_t w[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    uint32_t word = 0;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        float r = mod_reduce(acc[4 * i + b], qf, qinv);   // |r| <= q/2 + 1
+                        r = r < 0.f ? __fadd_rn(r, qf) : r;
+                        r = r >= qf ? __fsub_rn(r, qf) : r;
+                        word |= (__float_as_uint(__fadd_rn(r, 8388608.0f)) & 0xFFu) << (8 * b);
+                    }
+                    w[i] = word;
+                }
+                uint8_t* dst = args.R + ((static_cast<int64_t>(l) * args.ks + s) * args.m + row) *
+                                            args.ldr + col0;
+                if (col0 + 64 <= args.ldr) {
+#pragma unroll
+                    for (int v = 0; v < 4; ++v)
+                        reinterpret_cast<uint4*>(dst)[v] =
+                            make_uint4(w[4 * v], w[4 * v + 1], w[4 * v + 2], w[4 * v + 3]);
+                } else {
+                    for (int i = 0; i < 64 && col0 + i < args.ldr; ++i)
+                        dst[i] = static_cast<uint8_t>((w[i >> 2] >> (8 * (i & 3))) & 0xFFu);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, Cfg::kTmemCols);
+    }
+}
+
+// ---------------------------------------------------------------- reconstruction
+// mag * 2^e rounded to the nearest FP64 value, ties to even (one rounding
+// unless the result is subnormal).
+__device__ __forceinline__ double u128_to_double_scaled(u128 mag, int e) {
+    if (mag == 0) return 0.0;
+    const uint64_t hi = static_cast<uint64_t>(mag >> 64), lo = static_cast<uint64_t>(mag);
+    const int nbits = hi ? 128 - __clzll(static_cast<long long>(hi))
+                         : 64 - __clzll(static_cast<long long>(lo));
+    if (nbits <= 53) return ldexp(static_cast<double>(lo), e);
+    const int drop = nbits - 53;
+    u128 q = mag >> drop;
+    const u128 rem = mag - (q << drop);
+    const u128 half = static_cast<u128>(1) << (drop - 1);
+    if (rem > half || (rem == half && (static_cast<uint64_t>(q) & 1u))) q += 1;
+    return ldexp(static_cast<double>(static_cast<uint64_t>(q)), e + drop);
+}
+
+// C[i, j] for 4 consecutive j per thread: residues r_l = sum_s R[l, s, i, j]
+// mod q_l, X = sum_l r_l W_l (exact: the low 128 bits and an FP64 estimate
+// of the quotient by P), C' = X mod P in (-P/2, P/2), rounded once and
+// scaled by 2^(eA_i + eB_j - 2t).
+__global__ void __launch_bounds__(256)
+    crt_recon_kernel(const uint8_t* __restrict__ R, int64_t m, int64_t p, int64_t ldr, int ks,
+                     const int* __restrict__ eA, const int* __restrict__ eB, double* __restrict__ C,
+                     int vec, const CrtConsts k) {
+    const int64_t gpr = (p + 3) / 4;
+    const int64_t total = m * gpr;
+    const u128 P = (static_cast<u128>(k.P_hi) << 64) | k.P_lo;
+    const u128 halfP = P >> 1;
+    for (int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < total;
+         g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t i = g / gpr, j0 = (g - i * gpr) * 4;
+        u128 lo[4] = {0, 0, 0, 0}, hi[4] = {0, 0, 0, 0};
+        for (int l = 0; l < k.M; ++l) {
+            const uint32_t q = crt_mod(l);
+            uint32_t r[4] = {0, 0, 0, 0};
+            for (int s = 0; s < ks; ++s) {
+                const uint32_t word = *reinterpret_cast<const uint32_t*>(
+                    R + ((static_cast<int64_t>(l) * ks + s) * m + i) * ldr + j0);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) r[e] += (word >> (8 * e)) & 0xFFu;
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const uint32_t re = r[e] % q;
+                lo[e] += static_cast<u128>(re) * k.w_lo[l];
+                hi[e] += static_cast<u128>(re) * k.w_hi[l];
+            }
+        }
+        const int ea = eA[i] - 2 * k.t;
+        double out[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            // X = lo + hi 2^64 < 2^12 P; its quotient by P from an FP64 estimate
+            // (off by at most one), the remainder exact in 128 bits
+            const double xd = (static_cast<double>(static_cast<uint64_t>(hi[e] >> 64)) *
+                                   18446744073709551616.0 +
+                               static_cast<double>(static_cast<uint64_t>(hi[e]))) *
+                                  18446744073709551616.0 +
+                              (static_cast<double>(static_cast<uint64_t>(lo[e] >> 64)) *
+                                   18446744073709551616.0 +
+                               static_cast<double>(static_cast<uint64_t>(lo[e])));
+            const uint64_t qe = static_cast<uint64_t>(xd * k.invP);
+            const u128 x = lo[e] + (hi[e] << 64);
+            i128 rr = static_cast<i128>(x - static_cast<u128>(qe) * P);
+            if (rr < 0) rr += static_cast<i128>(P);
+            if (rr >= static_cast<i128>(P)) rr -= static_cast<i128>(P);
+            // symmetric: C' in [-P/2, P/2)
+            const bool neg = static_cast<u128>(rr) >= halfP;
+            const u128 mag = neg ? P - static_cast<u128>(rr) : static_cast<u128>(rr);
+            const int64_t j = j0 + e;
+            const double v = j < p ? u128_to_double_scaled(mag, ea + eB[j]) : 0.0;
+            out[e] = neg ? -v : v;
+        }
+        double* crow = C + i * p + j0;
+        if (vec && j0 + 4 <= p) {
+            reinterpret_cast<double2*>(crow)[0] = make_double2(out[0], out[1]);
+            reinterpret_cast<double2*>(crow)[1] = make_double2(out[2], out[3]);
+        } else {
+            for (int e = 0; e < 4 && j0 + e < p; ++e) crow[e] = out[e];
+        }
+    }
+}
+
+int grid_for(int64_t total, int threads) {
+    const int64_t want = ceil_div(total, threads);
+    const int64_t cap = 16L * num_sms();
+    return static_cast<int>(std::max<int64_t>(1, std::min(want, cap)));
+}
+
+int vec_rows(const void* X, int64_t cols, int per16) {
+    return (cols % per16 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
+}
+
+// Most K slices per tile the workspace is sized for.
+constexpr int kCrtMaxKs = 8;
+// Reference SM count of the workspace sizing (the launch uses the device's).
+constexpr int kCrtRefSms = 160;
+
+// K slices for `units` (modulus x tile) units over `sms` SMs: cut K only
+// when the units fill at most half of the SMs, keeping >= 4 chunks a slice.
+int crt_ks(long units, int num_kb, long sms) {
+    if (units * 2 > sms) return 1;
+    const long by_sms = (sms + units - 1) / units;
+    const long by_k = std::max(1L, static_cast<long>(num_kb) / (4 * kChunkKB));
+    return static_cast<int>(std::max(1L, std::min({by_sms, by_k, static_cast<long>(kCrtMaxKs)})));
+}
+
+// Tile width by a wave-count cost model over (modulus, tile) units: the
+// cheapest of ceil(units / SMs) waves of width / efficiency (128-wide tiles
+// at 0.9 of 256-wide ones); moa_set_block_n(128 | 256) forces it.
+int crt_block_n(int64_t m, int64_t p, int M, long sms) {
+    const int ov = tile_override();
+    if (ov == 128 || ov == 256) return ov;
+    auto cost = [&](int bn, double eff) {
+        const long units = M * ceil_div(m, kBM) * ceil_div(p, bn);
+        return static_cast<double>((units + sms - 1) / sms) * bn / eff;
+    };
+    return cost(128, 0.9) < cost(256, 1.0) ? 128 : 256;
+}
+
+template <int BN>
+int launch_crt_gemm(const CrtGemmArgs& a, const CUtensorMap& tmA, const CUtensorMap& tmB,
+                    cudaStream_t s, moa_stats* st) {
+    using Cfg = CrtCfg<BN>;
+    static std::atomic<uint64_t> attr_done{0};
+    int rc = smem_attr_once(reinterpret_cast<const void*>(crt_gemm_kernel<BN>), Cfg::kSmem,
+                            attr_done, "cudaFuncSetAttribute(crt_gemm)");
+    if (rc != MOA_OK) return rc;
+    const long units = static_cast<long>(a.M) * a.tiles_m * a.tiles_n * a.ks;
+    const int grid = static_cast<int>(std::min<long>(units, num_sms()));
+    prof_begin(s);
+    crt_gemm_kernel<BN><<<grid, Cfg::kThreads, Cfg::kSmem, s>>>(tmA, tmB, a);
+    cudaError_t e = cudaGetLastError();
+    prof_end(s);
+    if (e != cudaSuccess) return cuda_fail(e, "crt_gemm_kernel launch");
+    log_msg(2, "crt m=%lld n=%lld p=%lld tile %dx%d moduli %d K slices %d units %ld grid %d",
+            static_cast<long long>(a.m), static_cast<long long>(a.n), static_cast<long long>(a.p),
+            kBM, BN, a.M, a.ks, units, grid);
+    if (st) {
+        st->block_m = kBM;
+        st->block_n = BN;
+        st->block_k = kBK;
+        st->grid = grid;
+        st->tiles = static_cast<int64_t>(a.tiles_m) * a.tiles_n;
+    }
+    return MOA_OK;
+}
+
+}  // namespace
+
+int crt_moduli_for(moa_dtype dt, int64_t n, int slices) {
+    (void)dt;
+    if (slices != 0) return (slices < kCrtMinModuli || slices > kCrtMaxModuli) ? -1 : slices;
+    // the fewest moduli, from 14, that keep t >= 47 bits per operand
+    for (int M = kCrtDefaultModuli; M < kCrtMaxModuli; ++M)
+        if (crt_bits(std::max<int64_t>(n, 1), M) >= 47) return M;
+    return kCrtMaxModuli;
+}
+
+int crt_bits(int64_t n, int M) {
+    const u128 P = crt_product(M);
+    int best = -1;
+    for (int t = 0; t <= 62; ++t) {
+        // n * 2^(2t+1) < P
+        const int sh = 2 * t + 1;
+        if (sh >= 127) break;
+        const u128 lhs = static_cast<u128>(n) << sh;
+        if ((lhs >> sh) != static_cast<u128>(n) || lhs >= P) break;
+        best = t;
+    }
+    return best;
+}
+
+CrtLayout crt_layout(int64_t m, int64_t n, int64_t p, int M) {
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    CrtLayout L{};
+    L.M = M;
+    L.lda = round_up(n, 8);
+    L.ldb = round_up(p, 8);
+    L.ldr = round_up(p, 16);
+    const long tiles128 = static_cast<long>(ceil_div(m, kBM) * ceil_div(p, 128));
+    L.ks_max = crt_ks(static_cast<long>(M) * tiles128, static_cast<int>(ceil_div(n, kBK)),
+                      kCrtRefSms);
+    size_t off = 0;
+    L.a_off = off;
+    off += al(static_cast<size_t>(M) * m * L.lda * 2);
+    L.b_off = off;
+    off += al(static_cast<size_t>(M) * n * L.ldb * 2);
+    L.ea_off = off;
+    off += al(static_cast<size_t>(m) * 4);
+    L.eb_off = off;
+    off += al(static_cast<size_t>(p) * 4);
+    L.cmax_off = off;
+    off += al(static_cast<size_t>(p) * 8);
+    L.r_off = off;
+    off += al(static_cast<size_t>(M) * L.ks_max * m * L.ldr);
+    L.total = off;
+    return L;
+}
+
+size_t crt_workspace_bytes(int64_t m, int64_t n, int64_t p, moa_dtype dt, int slices) {
+    const int M = crt_moduli_for(dt, n, slices);
+    if (M < 0) return 0;
+    return crt_layout(m, n, p, M).total;
+}
+
+int crt_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const void* B, void* C,
+             int slices, void* ws, size_t ws_bytes, cudaStream_t s, moa_stats* st) {
+    const int M = crt_moduli_for(dt, n, slices);
+    if (M < 0) return fail(MOA_ERR_DTYPE, "modulus count not supported (8..16)");
+    const int t = crt_bits(n, M);
+    if (t < 1) return fail(MOA_ERR_ARG, "n too large for this modulus count");
+    const CrtLayout L = crt_layout(m, n, p, M);
+    if (ws_bytes < L.total) return fail(MOA_ERR_WORKSPACE, "workspace too small for crt mode");
+    if (ceil_div(n, 256) * ceil_div(p, 256) > (1L << 30))
+        return fail(MOA_ERR_ARG, "n x p too large for the column-max grid");
+    int* status = launch_status_ptr();
+    if (!status) return MOA_ERR_CUDA;
+    uint8_t* base = static_cast<uint8_t*>(ws);
+    auto* a_pl = reinterpret_cast<__nv_bfloat16*>(base + L.a_off);
+    auto* b_pl = reinterpret_cast<__nv_bfloat16*>(base + L.b_off);
+    int* eA = reinterpret_cast<int*>(base + L.ea_off);
+    int* eB = reinterpret_cast<int*>(base + L.eb_off);
+    void* cmax = base + L.cmax_off;
+    uint8_t* R = base + L.r_off;
+    const int64_t a_plane = m * L.lda;
+    const int64_t b_plane = n * L.ldb;
+    const bool f64in = dt == MOA_F64_CRT_F64IN;
+
+    // launch 1: clear the column maxima; 2: row exponents of A beside the
+    // column maxima of B; 3: residue planes of A and B
+    cudaError_t e = cudaMemsetAsync(cmax, 0, static_cast<size_t>(p) * 8, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(colmax)");
+    const int64_t rblocks = std::min<int64_t>(ceil_div(m, 8), 16L * num_sms());
+    const int64_t chunk = 256;
+    const int64_t gx = ceil_div(p, 256);
+    const int64_t cblocks = gx * ceil_div(n, chunk);
+    const int ga = grid_for(a_plane / 8, 256);
+    const int gb = grid_for(b_plane / 8, 256);
+    if (f64in) {
+        const double* Ad = static_cast<const double*>(A);
+        const double* Bd = static_cast<const double*>(B);
+        auto* cm = static_cast<unsigned long long*>(cmax);
+        crt_exps_kernel<double><<<static_cast<unsigned>(rblocks + cblocks), 256, 0, s>>>(
+            Ad, m, n, Bd, p, chunk, eA, cm, status, static_cast<int>(rblocks), gx);
+        crt_residue_kernel<double><<<ga + gb, 256, 0, s>>>(
+            Ad, m, n, L.lda, vec_rows(Ad, n, 2), eA, Bd, p, L.ldb, vec_rows(Bd, p, 2), eB, cm,
+            status, t, M, a_pl, a_plane, b_pl, b_plane, ga);
+    } else {
+        const float* Af = static_cast<const float*>(A);
+        const float* Bf = static_cast<const float*>(B);
+        auto* cm = static_cast<unsigned int*>(cmax);
+        crt_exps_kernel<float><<<static_cast<unsigned>(rblocks + cblocks), 256, 0, s>>>(
+            Af, m, n, Bf, p, chunk, eA, cm, status, static_cast<int>(rblocks), gx);
+        crt_residue_kernel<float><<<ga + gb, 256, 0, s>>>(
+            Af, m, n, L.lda, vec_rows(Af, n, 4), eA, Bf, p, L.ldb, vec_rows(Bf, p, 4), eB, cm,
+            status, t, M, a_pl, a_plane, b_pl, b_plane, ga);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "crt pre-pass launch");
+
+    // launch 4: the residue GEMM
+    const long sms = num_sms();
+    const int bn = crt_block_n(m, p, M, sms);
+    CrtGemmArgs a{};
+    a.R = R;
+    a.m = m;
+    a.n = n;
+    a.p = p;
+    a.ldr = L.ldr;
+    a.tiles_m = static_cast<int>(ceil_div(m, kBM));
+    a.tiles_n = static_cast<int>(ceil_div(p, bn));
+    a.num_kb = static_cast<int>(ceil_div(n, kBK));
+    a.group_m = split_raster_group(n);
+    a.M = M;
+    a.ks = std::min(L.ks_max, crt_ks(static_cast<long>(M) * a.tiles_m * a.tiles_n, a.num_kb, sms));
+    for (int l = 0; l < M; ++l) {
+        a.qf[l] = static_cast<float>(crt_mod(l));
+        a.qinv[l] = 1.0f / static_cast<float>(crt_mod(l));
+    }
+    a.wait_limit_ns = wait_limit_ns();
+    a.status = status;
+    CUtensorMap tmA, tmB;
+    int rc = make_tmap_3d(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, a_pl, static_cast<uint64_t>(n),
+                          static_cast<uint64_t>(m), static_cast<uint64_t>(M),
+                          static_cast<uint64_t>(L.lda) * 2, static_cast<uint64_t>(a_plane) * 2,
+                          kBK, kBM);
+    if (rc != MOA_OK) return rc;
+    rc = make_tmap_3d(&tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, b_pl, static_cast<uint64_t>(p),
+                      static_cast<uint64_t>(n), static_cast<uint64_t>(M),
+                      static_cast<uint64_t>(L.ldb) * 2, static_cast<uint64_t>(b_plane) * 2, 64, kBK);
+    if (rc != MOA_OK) return rc;
+    rc = bn == 256 ? launch_crt_gemm<256>(a, tmA, tmB, s, st) : launch_crt_gemm<128>(a, tmA, tmB, s, st);
+    if (rc != MOA_OK) return rc;
+
+    // launch 5: reconstruction
+    const CrtConsts k = crt_consts(M, t);
+    const int vec = (p % 2 == 0) && (reinterpret_cast<uintptr_t>(C) % 16 == 0);
+    crt_recon_kernel<<<grid_for(m * ceil_div(p, 4), 256), 256, 0, s>>>(
+        R, m, p, L.ldr, a.ks, eA, eB, static_cast<double*>(C), vec, k);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "crt reconstruction launch");
+    if (st) {
+        st->slices = M;
+        st->products = M;
+        st->kernels = 5;
+    }
+    return MOA_OK;
+}
+
+}  // namespace moa

@@ -1,0 +1,43 @@
+// crt.h -- the FP64-accuracy modular-slice modes (MOA_F64_CRT_F32IN,
+// MOA_F64_CRT_F64IN), internal to libmoa.so.
+#pragma once
+#include "internal.h"
+
+namespace moa {
+
+inline bool is_crt(moa_dtype dt) { return dt == MOA_F64_CRT_F32IN || dt == MOA_F64_CRT_F64IN; }
+
+// Modulus counts: 8..16 accepted (the product of the moduli stays below
+// 2^128); by default the fewest from 14 that keep t >= 47 bits per operand
+// (14 up to n = 36639, 15 up to n = 7218057, 16 beyond).
+constexpr int kCrtMinModuli = 8;
+constexpr int kCrtMaxModuli = 16;
+constexpr int kCrtDefaultModuli = 14;
+
+// Modulus count for a call (slices = 0: the default for this n); -1 if the
+// count is not allowed.
+int crt_moduli_for(moa_dtype dt, int64_t n, int slices);
+// Largest t <= 62 with n * 2^(2t+1) < P (P the product of the first M moduli);
+// -1 if none.
+int crt_bits(int64_t n, int M);
+
+size_t crt_workspace_bytes(int64_t m, int64_t n, int64_t p, moa_dtype dt, int slices);
+
+int crt_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const void* B, void* C,
+             int slices, void* ws, size_t ws_bytes, cudaStream_t s, moa_stats* st);
+
+// Workspace layout of a modular-slice call (byte offsets from the base).
+struct CrtLayout {
+    int M;                  // moduli
+    int ks_max;             // most K slices per tile the residue planes hold
+    int64_t lda, ldb, ldr;  // row pitches: A / B residue planes (BF16 elements),
+                            // output residue planes (bytes)
+    size_t a_off, b_off;    // M x m x lda and M x n x ldb BF16 residues of A' and B'
+    size_t ea_off, eb_off;  // per-row / per-column exponents (int32)
+    size_t cmax_off;        // per-column max |B| bit patterns (8 bytes each)
+    size_t r_off;           // residues of the product: (M * ks_max) x m x ldr bytes
+    size_t total;
+};
+CrtLayout crt_layout(int64_t m, int64_t n, int64_t p, int M);
+
+}  // namespace moa

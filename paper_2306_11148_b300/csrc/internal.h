@@ -14,16 +14,18 @@
 namespace moa {
 
 // ------------------------------------------------------------------ modes
-inline bool valid_dtype(int dt) { return dt >= MOA_F64 && dt <= MOA_F64_SPLIT_F64IN_E4M3; }
+inline bool valid_dtype(int dt) { return dt >= MOA_F64 && dt <= MOA_F64_CRT_F64IN; }
 // Bytes per element of A and B, and of C, for each mode.
 inline int dtype_in_bytes(moa_dtype dt) {
-    return (dt == MOA_F64 || dt == MOA_F64_SPLIT_F64IN || dt == MOA_F64_SPLIT_F64IN_E4M3)
+    return (dt == MOA_F64 || dt == MOA_F64_SPLIT_F64IN || dt == MOA_F64_SPLIT_F64IN_E4M3 ||
+            dt == MOA_F64_CRT_F64IN)
                ? 8
                : (dt == MOA_BF16 ? 2 : 4);
 }
 inline int dtype_out_bytes(moa_dtype dt) {
     return (dt == MOA_F64 || dt == MOA_F64_SPLIT_F32IN || dt == MOA_F64_SPLIT_F64IN ||
-            dt == MOA_F64_SPLIT_F32IN_E4M3 || dt == MOA_F64_SPLIT_F64IN_E4M3)
+            dt == MOA_F64_SPLIT_F32IN_E4M3 || dt == MOA_F64_SPLIT_F64IN_E4M3 ||
+            dt == MOA_F64_CRT_F32IN || dt == MOA_F64_CRT_F64IN)
                ? 8
                : 4;
 }

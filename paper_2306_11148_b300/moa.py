@@ -42,6 +42,8 @@ MOA_F64_SPLIT_F32IN = 5
 MOA_F64_SPLIT_F64IN = 6
 MOA_F64_SPLIT_F32IN_E4M3 = 7
 MOA_F64_SPLIT_F64IN_E4M3 = 8
+MOA_F64_CRT_F32IN = 9
+MOA_F64_CRT_F64IN = 10
 
 MODES = {
     "f64": MOA_F64, "tf32": MOA_F32_TF32, "f32_simt": MOA_F32_SIMT, "bf16": MOA_BF16,
@@ -49,10 +51,13 @@ MODES = {
     "f64_split_f64in": MOA_F64_SPLIT_F64IN,
     "f64_split_f32in_e4m3": MOA_F64_SPLIT_F32IN_E4M3,
     "f64_split_f64in_e4m3": MOA_F64_SPLIT_F64IN_E4M3,
+    "f64_crt_f32in": MOA_F64_CRT_F32IN, "f64_crt_f64in": MOA_F64_CRT_F64IN,
 }
 # FP64-accuracy modes (FP64 output) and their digit format: (radix bits, headroom bits)
 F64_ACCURATE = (MOA_F64, MOA_F64_SPLIT_F32IN, MOA_F64_SPLIT_F64IN, MOA_F64_SPLIT_F32IN_E4M3,
-                MOA_F64_SPLIT_F64IN_E4M3)
+                MOA_F64_SPLIT_F64IN_E4M3, MOA_F64_CRT_F32IN, MOA_F64_CRT_F64IN)
+# modular-slice modes (slices = number of moduli)
+CRT = (MOA_F64_CRT_F32IN, MOA_F64_CRT_F64IN)
 DIGITS = {MOA_F64_SPLIT_F32IN: (7, 1), MOA_F64_SPLIT_F64IN: (7, 1),
           MOA_F64_SPLIT_F32IN_E4M3: (5, 1), MOA_F64_SPLIT_F64IN_E4M3: (5, 1)}
 DEFAULT_SLICES = {MOA_F32_SPLIT: 3, MOA_F64_SPLIT_F32IN: 7, MOA_F64_SPLIT_F64IN: 7,
@@ -226,7 +231,7 @@ def out_dtype(dt: int):
 
 def in_dtype(dt: int):
     import torch
-    if dt in (MOA_F64, MOA_F64_SPLIT_F64IN, MOA_F64_SPLIT_F64IN_E4M3):
+    if dt in (MOA_F64, MOA_F64_SPLIT_F64IN, MOA_F64_SPLIT_F64IN_E4M3, MOA_F64_CRT_F64IN):
         return torch.float64
     if dt == MOA_BF16:
         return torch.bfloat16

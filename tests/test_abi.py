@@ -107,7 +107,16 @@ def test_workspace_sizes(L):
     # a 5-column B is padded to 16-byte rows of its transpose: p rows of round_up(n, 16)
     w = moa.moa_gemm_workspace_size(16, 5, 3, moa.MOA_F64_SPLIT_F32IN_E4M3, 4)
     assert w >= 4 * (16 * 16 + 3 * 16)
-    assert moa.moa_gemm_ex(4, 4, 4, 9, 16, 16, 16, 0, None, 0, None) == moa.MOA_ERR_DTYPE
+    assert moa.moa_gemm_ex(4, 4, 4, 11, 16, 16, 16, 0, None, 0, None) == moa.MOA_ERR_DTYPE
+    # modular slices: M x (A and B residue planes) + the product's residue planes;
+    # 8..16 moduli, default 14 up to n = 36639 and 15 beyond
+    c14 = moa.moa_gemm_workspace_size(256, 256, 256, moa.MOA_F64_CRT_F32IN, 0)
+    assert c14 == moa.moa_gemm_workspace_size(256, 256, 256, moa.MOA_F64_CRT_F32IN, 14)
+    assert c14 >= 14 * 2 * (2 * 256 * 256) + 14 * 256 * 256
+    assert moa.moa_gemm_workspace_size(16, 36640, 16, moa.MOA_F64_CRT_F32IN, 0) == \
+        moa.moa_gemm_workspace_size(16, 36640, 16, moa.MOA_F64_CRT_F32IN, 15)
+    for bad in (7, 17):
+        assert moa.moa_gemm_workspace_size(256, 256, 256, moa.MOA_F64_CRT_F64IN, bad) == 0
 
 
 def test_empty_problems_are_noops(L):
