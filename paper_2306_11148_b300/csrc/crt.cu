@@ -61,10 +61,10 @@ using i128 = __int128;
 struct CrtConsts {
     int M;                               // moduli in use
     int t;                               // operand bits
-    uint64_t w_lo[kCrtMaxModuli];        // CRT weights W_l = (P / q_l) * ((P / q_l)^-1 mod q_l)
-    uint64_t w_hi[kCrtMaxModuli];        //   mod P, as two 64-bit words
+    uint32_t w[kCrtMaxModuli][8];        // CRT weights W_l = (P / q_l) * ((P / q_l)^-1 mod q_l)
+                                         //   mod P, as 16-bit limbs, least significant first
+    float wf[kCrtMaxModuli];             // W_l / P rounded to FP32 (quotient estimate)
     uint64_t P_lo, P_hi;                 // P = prod q_l
-    double invP;                         // 1 / P, rounded
 };
 
 // ---------------------------------------------------------------- host arithmetic
@@ -94,15 +94,17 @@ CrtConsts crt_consts(int M, int t) {
     const u128 P = crt_product(M);
     c.P_lo = static_cast<uint64_t>(P);
     c.P_hi = static_cast<uint64_t>(P >> 64);
-    c.invP = 1.0 / (static_cast<double>(c.P_hi) * 18446744073709551616.0 +
-                    static_cast<double>(c.P_lo));
+    auto as_double = [](u128 v) {
+        return static_cast<double>(static_cast<uint64_t>(v >> 64)) * 18446744073709551616.0 +
+               static_cast<double>(static_cast<uint64_t>(v));
+    };
     for (int l = 0; l < M; ++l) {
         const u128 Ml = P / crt_mod(l);
         const int64_t Ml_mod = static_cast<int64_t>(Ml % crt_mod(l));
         const int64_t y = inv_mod(Ml_mod, crt_mod(l));
         const u128 W = (Ml * static_cast<u128>(y)) % P;   // Ml * y < P * 256 < 2^128
-        c.w_lo[l] = static_cast<uint64_t>(W);
-        c.w_hi[l] = static_cast<uint64_t>(W >> 64);
+        for (int k = 0; k < 8; ++k) c.w[l][k] = static_cast<uint32_t>(W >> (16 * k)) & 0xFFFFu;
+        c.wf[l] = static_cast<float>(as_double(W) / as_double(P));
     }
     return c;
 }
@@ -158,11 +160,47 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---------------------------------------------------------------- residue pass
-// |x * 2^k| rounded half-even, as (sign, magnitude); requires the result
-// below 2^63.
-__device__ __forceinline__ uint64_t scaled_mag(float x, int k, bool& neg) {
+// 2^s mod q_l for s < 128 (kernel parameter; copied to shared memory as FP32).
+constexpr int kPow2Cols = 128;
+struct CrtPow2 {
+    uint8_t v[kCrtMaxModuli][kPow2Cols];
+};
+
+// x (an integer-valued float) minus the nearest multiple of q: rint(x / q)
+// by the magic-number addition (exact for |x / q| < 2^22), the product
+// subtracted by one fused multiply-add (the result is an exact integer).  The
+// quotient comes from x * RN(1/q), off from x / q by at most 2^-23 x / q: for
+// |x| <= 2^24 the result lies within 0.51 q + 1 of zero, and for |x| < 2^21
+// (the estimate's error is then below 1/(2q), the least distance of x / q from
+// a half-integer it is not on) it is the symmetric residue, |result| <= q/2.
+__device__ __forceinline__ float mod_reduce(float x, float q, float qinv) {
+    const float y = __fmul_rn(x, qinv);
+    const float k = __fsub_rn(__fadd_rn(y, 12582912.0f), 12582912.0f);
+    return __fmaf_rn(-k, q, x);
+}
+
+// An integer 0 <= v < 2^23 as an FP32 value (the float with bits 2^23 | v is
+// 2^23 + v exactly).
+__device__ __forceinline__ float small_uint_to_float(uint32_t v) {
+    return __fsub_rn(__uint_as_float(0x4B000000u | v), 8388608.0f);
+}
+
+// The scaled integer D = rint(x * 2^k) of one element as (sign, 12-bit
+// pieces as exact floats, shift): |D| = sum_i p[i] 2^(12 i + s).  FP32
+// inputs: two pieces of the 24-bit significand (or of the rounded D when k
+// shifts it right) and a shift s < 64; FP64 inputs: six pieces of |D| < 2^63
+// and s = 0.
+template <int NP>
+struct ScaledParts {
+    float p[NP];
+    int s;
+    bool neg;
+};
+__device__ __forceinline__ ScaledParts<2> scaled_parts(float x, int k) {
+    ScaledParts<2> r;
     const uint32_t b = __float_as_uint(x);
-    neg = (b >> 31) != 0;
+    r.neg = (b >> 31) != 0;
+    r.s = 0;
     const int ex = static_cast<int>((b >> 23) & 0xFF);
     uint32_t mant = b & 0x7FFFFFu;
     int E = -149;
@@ -170,64 +208,80 @@ __device__ __forceinline__ uint64_t scaled_mag(float x, int k, bool& neg) {
         mant |= 1u << 23;
         E = ex - 150;
     }
-    if (mant == 0) return 0;
     const int sh = E + k;
-    if (sh >= 0) return static_cast<uint64_t>(mant) << sh;
-    const int kk = -sh;
-    if (kk > 25) return 0;
-    const uint32_t q = mant >> kk;
-    const uint32_t rem = mant & ((1u << kk) - 1u);
-    const uint32_t half = 1u << (kk - 1);
-    return q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u);
+    uint32_t base;
+    if (sh >= 0) {
+        base = mant;
+        r.s = sh;
+    } else {
+        const int kk = -sh;
+        if (kk > 25) {
+            base = 0;
+        } else {
+            const uint32_t q = mant >> kk;
+            const uint32_t rem = mant & ((1u << kk) - 1u);
+            const uint32_t half = 1u << (kk - 1);
+            base = q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u);
+        }
+    }
+    r.p[0] = small_uint_to_float(base & 0xFFFu);
+    r.p[1] = small_uint_to_float(base >> 12);   // base <= 2^24
+    return r;
 }
-__device__ __forceinline__ uint64_t scaled_mag(double x, int k, bool& neg) {
+__device__ __forceinline__ ScaledParts<6> scaled_parts(double x, int k) {
+    ScaledParts<6> r;
     const long long D = Bits<double>::round_scaled(x, k);
-    neg = D < 0;
-    return static_cast<uint64_t>(neg ? -D : D);
+    r.neg = D < 0;
+    r.s = 0;
+    const uint64_t v = static_cast<uint64_t>(r.neg ? -D : D);
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        r.p[i] = small_uint_to_float(static_cast<uint32_t>((v >> (12 * i)) & 0xFFFu));
+    return r;
 }
 
-// Symmetric residue of a signed integer (sign, magnitude v < 2^63) modulo
-// crt_mod(l), in [-128, 128]: v = hi 2^32 + lo, reduced piecewise.  l is a
-// compile-time constant at every call (unrolled loops), so the divisions by
-// the modulus compile to multiplications.
-template <int L>
-__device__ __forceinline__ int sym_residue(uint64_t v, bool neg) {
-    constexpr uint32_t q = crt_mod(L);
-    constexpr uint32_t c32 = static_cast<uint32_t>((uint64_t(1) << 32) % q);
-    const uint32_t hi = static_cast<uint32_t>(v >> 32), lo = static_cast<uint32_t>(v);
-    uint32_t r = ((hi % q) * c32 + lo % q) % q;          // < 2^16 before the last %
-    int s = static_cast<int>(r);
-    if (s > static_cast<int>(q / 2) || (s == static_cast<int>(q / 2) && (q & 1u) == 0u))
-        s -= static_cast<int>(q);                        // [-(q/2), (q-1)/2]
-    return neg ? -s : s;
+// Symmetric residue (|r| <= q/2, an integer-valued float with the element's
+// sign applied) of one element modulo q = crt_mod(L); tab: the block's shared
+// table row of 2^s mod q.
+template <int L, int NP>
+__device__ __forceinline__ float residue_of(const ScaledParts<NP>& e, const float* tab) {
+    constexpr float q = static_cast<float>(crt_mod(L));
+    constexpr float qinv = 1.0f / static_cast<float>(crt_mod(L));
+    float r;
+    if constexpr (NP == 2) {
+        // two pieces below 2^12 times 2^s mod q (< 2^8): the sum is below 2^21,
+        // one reduction gives the symmetric residue
+        r = mod_reduce(__fmaf_rn(e.p[1], tab[e.s + 12], __fmul_rn(e.p[0], tab[e.s])), q, qinv);
+    } else {
+        // six pieces: the sum is below 2^23, reduced within 0.51 q + 1, then
+        // reduced once more to the symmetric residue
+        float t = __fmul_rn(e.p[0], tab[0]);
+#pragma unroll
+        for (int i = 1; i < NP; ++i) t = __fmaf_rn(e.p[i], tab[12 * i], t);
+        r = mod_reduce(mod_reduce(t, q, qinv), q, qinv);
+    }
+    return e.neg ? -r : r;
 }
 
-// BF16 bit patterns of two integers of magnitude <= 256 (exact in BF16),
-// packed low half first: the integer goes into the significand of
-// 1.5 * 2^23 and the offset is subtracted (both exact); the result has at
-// most 9 significant bits with its lowest one zero for |k| = 256, so its
-// upper 16 bits are its BF16 pattern.
-__device__ __forceinline__ uint32_t ints_bf16x2(int lo, int hi) {
-    const uint32_t flo =
-        __float_as_uint(__fsub_rn(__uint_as_float(0x4B400000u + static_cast<uint32_t>(lo)), 12582912.0f));
-    const uint32_t fhi =
-        __float_as_uint(__fsub_rn(__uint_as_float(0x4B400000u + static_cast<uint32_t>(hi)), 12582912.0f));
-    return (flo >> 16) | (fhi & 0xFFFF0000u);
+// BF16 patterns of two integer-valued floats of magnitude <= 256 (exact in
+// BF16: at most 8 significant bits, so the upper 16 bits are the pattern),
+// packed low half first.
+__device__ __forceinline__ uint32_t bf16x2_of_ints(float lo, float hi) {
+    return (__float_as_uint(lo) >> 16) | (__float_as_uint(hi) & 0xFFFF0000u);
 }
 
+// Loads X[r, c0 .. c0+3] (zero past `cols`); 16-byte loads when allowed.
 template <typename T>
-__device__ __forceinline__ void load8(const T* __restrict__ X, int64_t r, int64_t cols, int64_t c0,
-                                      bool vec, T (&x)[8]) {
+__device__ __forceinline__ void load4(const T* __restrict__ X, int64_t r, int64_t cols, int64_t c0,
+                                      bool vec, T (&x)[4]) {
     const T* src = X + r * cols + c0;
-    if (vec && c0 + 8 <= cols) {
+    if (vec && c0 + 4 <= cols) {
         if constexpr (sizeof(T) == 4) {
             const float4 a = reinterpret_cast<const float4*>(src)[0];
-            const float4 b = reinterpret_cast<const float4*>(src)[1];
             x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
-            x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
         } else {
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
+            for (int v = 0; v < 2; ++v) {
                 const double2 d = reinterpret_cast<const double2*>(src)[v];
                 x[2 * v] = d.x;
                 x[2 * v + 1] = d.y;
@@ -235,48 +289,46 @@ __device__ __forceinline__ void load8(const T* __restrict__ X, int64_t r, int64_
         }
     } else {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) x[i] = (c0 + i < cols) ? src[i] : T(0);
+        for (int i = 0; i < 4; ++i) x[i] = (c0 + i < cols) ? src[i] : T(0);
     }
 }
 
-// Writes the residue planes of 8 scaled integers (magnitudes v, signs neg)
-// at element offset o of every plane (one 16-byte store per plane).
-template <int L>
-__device__ __forceinline__ void store_planes(const uint64_t (&v)[8], const bool (&neg)[8], int M,
-                                             __nv_bfloat16* __restrict__ out, int64_t plane,
-                                             int64_t o) {
+// Writes the residues of 4 elements at element offset o of planes L .. M-1
+// (one 8-byte store per plane).
+template <int L, int NP>
+__device__ __forceinline__ void store_planes(const ScaledParts<NP> (&v)[4], int M,
+                                             const float* tab, __nv_bfloat16* __restrict__ out,
+                                             int64_t plane, int64_t o) {
     if constexpr (L < kCrtMaxModuli) {
         if (L >= M) return;
-        uint32_t w[4];
-#pragma unroll
-        for (int i = 0; i < 8; i += 2)
-            w[i / 2] = ints_bf16x2(sym_residue<L>(v[i], neg[i]), sym_residue<L>(v[i + 1], neg[i + 1]));
-        *reinterpret_cast<uint4*>(out + L * plane + o) = make_uint4(w[0], w[1], w[2], w[3]);
-        store_planes<L + 1>(v, neg, M, out, plane, o);
+        const float* row = tab + L * kPow2Cols;
+        const uint32_t w0 = bf16x2_of_ints(residue_of<L, NP>(v[0], row), residue_of<L, NP>(v[1], row));
+        const uint32_t w1 = bf16x2_of_ints(residue_of<L, NP>(v[2], row), residue_of<L, NP>(v[3], row));
+        *reinterpret_cast<uint2*>(out + L * plane + o) = make_uint2(w0, w1);
+        store_planes<L + 1, NP>(v, M, tab, out, plane, o);
     }
 }
 
 // Residue planes of X (rows x cols, row-major) into M BF16 planes of row
-// pitch ld (a multiple of 8; zero pad); 8 consecutive elements per thread.
+// pitch ld (a multiple of 8; zero pad); 4 consecutive elements per thread.
 // AXIS 0: exponent per row from e[r]; AXIS 1: exponent per column from the
 // column maximum cmax[c] (the threads of row 0 store it to e[c] and flag
 // NaN/Inf).
 template <typename T, int AXIS>
 __device__ void crt_residue_part(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
                                  int* __restrict__ e, const typename Bits<T>::U* __restrict__ cmax,
-                                 int* status, int t, int M, int vec,
+                                 int* status, int t, int M, int vec, const float* tab,
                                  __nv_bfloat16* __restrict__ out, int64_t plane, int64_t bid,
                                  int64_t nblk) {
-    const int64_t gpr = ld / 8;
+    const int64_t gpr = ld / 4;
     const int64_t total = rows * gpr;
     for (int64_t g = bid * blockDim.x + threadIdx.x; g < total; g += nblk * blockDim.x) {
-        const int64_t r = g / gpr, c0 = (g - r * gpr) * 8;
-        T x[8];
-        load8(X, r, cols, c0, vec != 0, x);
-        uint64_t v[8];
-        bool neg[8];
+        const int64_t r = g / gpr, c0 = (g - r * gpr) * 4;
+        T x[4];
+        load4(X, r, cols, c0, vec != 0, x);
+        ScaledParts<sizeof(T) == 8 ? 6 : 2> v[4];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < 4; ++i) {
             const int64_t c = c0 + i;
             int ex = 0;
             if (c < cols) {
@@ -289,9 +341,9 @@ __device__ void crt_residue_part(const T* __restrict__ X, int64_t rows, int64_t 
                     if (r == 0) e[c] = ex;
                 }
             }
-            v[i] = scaled_mag(x[i], t - ex, neg[i]);
+            v[i] = scaled_parts(x[i], t - ex);
         }
-        store_planes<0>(v, neg, M, out, plane, r * ld + c0);
+        store_planes<0, sizeof(T) == 8 ? 6 : 2>(v, M, tab, out, plane, r * ld + c0);
     }
 }
 
@@ -302,12 +354,18 @@ __global__ void __launch_bounds__(256)
                        int vb, int* __restrict__ eB, const typename Bits<T>::U* __restrict__ cmax,
                        int* status, int t, int M, __nv_bfloat16* __restrict__ a_out,
                        int64_t a_plane, __nv_bfloat16* __restrict__ b_out, int64_t b_plane,
-                       int ga) {
+                       int ga, const CrtPow2 pow2) {
+    // tab[l * 128 + s] = 2^s mod q_l (a row per modulus: threads of a warp that
+    // read different s of one row hit different banks)
+    __shared__ float tab[kCrtMaxModuli * kPow2Cols];
+    for (int i = threadIdx.x; i < kCrtMaxModuli * kPow2Cols; i += blockDim.x)
+        tab[i] = static_cast<float>(pow2.v[i / kPow2Cols][i % kPow2Cols]);
+    __syncthreads();
     if (static_cast<int>(blockIdx.x) < ga)
-        crt_residue_part<T, 0>(A, m, n, lda, const_cast<int*>(eA), nullptr, status, t, M, va,
+        crt_residue_part<T, 0>(A, m, n, lda, const_cast<int*>(eA), nullptr, status, t, M, va, tab,
                                a_out, a_plane, blockIdx.x, ga);
     else
-        crt_residue_part<T, 1>(B, n, p, ldb, eB, cmax, status, t, M, vb, b_out, b_plane,
+        crt_residue_part<T, 1>(B, n, p, ldb, eB, cmax, status, t, M, vb, tab, b_out, b_plane,
                                blockIdx.x - ga, gridDim.x - ga);
 }
 
@@ -363,16 +421,6 @@ __device__ __forceinline__ void crt_tile_coords(int t, int tiles_m, int tiles_n,
     const int r = t - g * per_group;
     tm = first_m + r % gsize;
     tn = r / gsize;
-}
-
-// x (an integer-valued float, |x| <= 2^24) reduced modulo q to an integer
-// of magnitude <= q / 2 + 1: x - q * rint(x / q), with rint by the
-// magic-number addition (exact for |x / q| < 2^22) and the product
-// subtracted by one fused multiply-add (the result is exact).
-__device__ __forceinline__ float mod_reduce(float x, float q, float qinv) {
-    const float y = __fmul_rn(x, qinv);
-    const float k = __fsub_rn(__fadd_rn(y, 12582912.0f), 12582912.0f);
-    return __fmaf_rn(-k, q, x);
 }
 
 template <int BN>
@@ -600,77 +648,143 @@ __global__ void __launch_bounds__(CrtCfg<BN>::kThreads, 1)
 }
 
 // ---------------------------------------------------------------- reconstruction
-// mag * 2^e rounded to the nearest FP64 value, ties to even (one rounding
-// unless the result is subnormal).
-__device__ __forceinline__ double u128_to_double_scaled(u128 mag, int e) {
-    if (mag == 0) return 0.0;
-    const uint64_t hi = static_cast<uint64_t>(mag >> 64), lo = static_cast<uint64_t>(mag);
-    const int nbits = hi ? 128 - __clzll(static_cast<long long>(hi))
-                         : 64 - __clzll(static_cast<long long>(lo));
-    if (nbits <= 53) return ldexp(static_cast<double>(lo), e);
-    const int drop = nbits - 53;
-    u128 q = mag >> drop;
-    const u128 rem = mag - (q << drop);
-    const u128 half = static_cast<u128>(1) << (drop - 1);
-    if (rem > half || (rem == half && (static_cast<uint64_t>(q) & 1u))) q += 1;
-    return ldexp(static_cast<double>(static_cast<uint64_t>(q)), e + drop);
+// mag * 2^e rounded to the nearest FP64 value, ties to even: the top 64 bits
+// normalised, the top 53 of them rounded half to even with the rest (and a
+// sticky bit for anything below), the FP64 pattern assembled directly (no
+// FP64 arithmetic); results outside the normal range go through ldexp (one
+// more rounding when subnormal).
+__device__ __forceinline__ double u128_to_double_scaled(uint64_t hi, uint64_t lo, int e) {
+    uint64_t top;
+    bool sticky;
+    int e0;   // mag = top * 2^(e0 - 63) + (the sticky part)
+    if (hi != 0) {
+        const int sh = __clzll(static_cast<long long>(hi));
+        top = sh ? (hi << sh) | (lo >> (64 - sh)) : hi;
+        sticky = (lo << sh) != 0;
+        e0 = 127 - sh;
+    } else if (lo != 0) {
+        const int sh = __clzll(static_cast<long long>(lo));
+        top = lo << sh;
+        sticky = false;
+        e0 = 63 - sh;
+    } else {
+        return 0.0;
+    }
+    uint64_t m53 = top >> 11;                 // in [2^52, 2^53)
+    const uint32_t rbits = static_cast<uint32_t>(top & 0x7FFu);
+    if (rbits > 0x400u || (rbits == 0x400u && (sticky || (m53 & 1u)))) ++m53;
+    int e2 = e + e0 - 52;                      // value = m53 * 2^e2
+    if (m53 == (uint64_t(1) << 53)) {
+        m53 >>= 1;
+        ++e2;
+    }
+    const int biased = e2 + 52 + 1023;
+    if (biased >= 1 && biased <= 2046)
+        return __longlong_as_double(static_cast<long long>(
+            (static_cast<uint64_t>(biased) << 52) | (m53 & ((uint64_t(1) << 52) - 1))));
+    return ldexp(static_cast<double>(m53), e2);
 }
 
-// C[i, j] for 4 consecutive j per thread: residues r_l = sum_s R[l, s, i, j]
-// mod q_l, X = sum_l r_l W_l (exact: the low 128 bits and an FP64 estimate
-// of the quotient by P), C' = X mod P in (-P/2, P/2), rounded once and
-// scaled by 2^(eA_i + eB_j - 2t).
+// Residues of modulus L for 4 consecutive outputs (w: their bytes, summed
+// over the K slices and reduced when there are several), then X += r W_L as
+// NL 16-bit limbs in 32-bit sums (r < 2^8: each product is below 2^24, a sum
+// of 16 below 2^28) and the quotient estimate qs += r W_L / P.
+template <int L, int NL>
+__device__ __forceinline__ void crt_accumulate(const uint32_t (&w)[kCrtMaxModuli], int M,
+                                               const CrtConsts& k, uint32_t (&acc)[4][NL],
+                                               float (&qs)[4]) {
+    if constexpr (L < kCrtMaxModuli) {
+        if (L >= M) return;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const uint32_t r = (w[L] >> (8 * e)) & 0xFFu;
+#pragma unroll
+            for (int j = 0; j < NL; ++j) acc[e][j] += r * k.w[L][j];
+            qs[e] = __fmaf_rn(small_uint_to_float(r), k.wf[L], qs[e]);
+        }
+        crt_accumulate<L + 1, NL>(w, M, k, acc, qs);
+    }
+}
+
+// The residue bytes of modulus L and its successors, 4 outputs per word:
+// the K slices summed and reduced modulo q_L (a compile-time constant).
+template <int L>
+__device__ __forceinline__ void crt_load(const uint8_t* __restrict__ R, int64_t plane_stride,
+                                         int ks, int M, uint32_t (&w)[kCrtMaxModuli]) {
+    if constexpr (L < kCrtMaxModuli) {
+        if (L >= M) return;
+        const uint8_t* src = R + static_cast<int64_t>(L) * ks * plane_stride;
+        w[L] = __ldg(reinterpret_cast<const uint32_t*>(src));
+        if (ks > 1) {
+            constexpr uint32_t q = crt_mod(L);
+            uint32_t r[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) r[e] = (w[L] >> (8 * e)) & 0xFFu;
+            for (int s = 1; s < ks; ++s) {
+                const uint32_t v = __ldg(reinterpret_cast<const uint32_t*>(src + s * plane_stride));
+#pragma unroll
+                for (int e = 0; e < 4; ++e) r[e] += (v >> (8 * e)) & 0xFFu;
+            }
+            w[L] = (r[0] % q) | ((r[1] % q) << 8) | ((r[2] % q) << 16) | ((r[3] % q) << 24);
+        }
+        crt_load<L + 1>(R, plane_stride, ks, M, w);
+    }
+}
+
+// C[i, j] for 4 consecutive j per thread: r_l = sum_s R[l, s, i, j] mod q_l;
+// X = sum_l r_l W_l kept modulo 2^128 (NL 16-bit limbs summed in 32 bits);
+// the quotient q = floor(X / P) estimated in FP32 from sum_l r_l W_l / P (off
+// by at most one); C' = X - q P corrected into [0, P), then into
+// [-P/2, P/2), rounded once and scaled by 2^(eA_i + eB_j - 2t).  NL = 7
+// covers P < 2^112 (up to 14 moduli), NL = 8 the rest.
+template <int NL>
 __global__ void __launch_bounds__(256)
     crt_recon_kernel(const uint8_t* __restrict__ R, int64_t m, int64_t p, int64_t ldr, int ks,
                      const int* __restrict__ eA, const int* __restrict__ eB, double* __restrict__ C,
                      int vec, const CrtConsts k) {
     const int64_t gpr = (p + 3) / 4;
     const int64_t total = m * gpr;
+    const int64_t plane_stride = m * ldr;
     const u128 P = (static_cast<u128>(k.P_hi) << 64) | k.P_lo;
     const u128 halfP = P >> 1;
     for (int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < total;
          g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int64_t i = g / gpr, j0 = (g - i * gpr) * 4;
-        u128 lo[4] = {0, 0, 0, 0}, hi[4] = {0, 0, 0, 0};
-        for (int l = 0; l < k.M; ++l) {
-            const uint32_t q = crt_mod(l);
-            uint32_t r[4] = {0, 0, 0, 0};
-            for (int s = 0; s < ks; ++s) {
-                const uint32_t word = *reinterpret_cast<const uint32_t*>(
-                    R + ((static_cast<int64_t>(l) * ks + s) * m + i) * ldr + j0);
-#pragma unroll
-                for (int e = 0; e < 4; ++e) r[e] += (word >> (8 * e)) & 0xFFu;
-            }
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const uint32_t re = r[e] % q;
-                lo[e] += static_cast<u128>(re) * k.w_lo[l];
-                hi[e] += static_cast<u128>(re) * k.w_hi[l];
-            }
-        }
+        uint32_t w[kCrtMaxModuli];
+        crt_load<0>(R + i * ldr + j0, plane_stride, ks, k.M, w);
+        uint32_t acc[4][NL] = {};
+        float qs[4] = {0.f, 0.f, 0.f, 0.f};
+        crt_accumulate<0, NL>(w, k.M, k, acc, qs);
         const int ea = eA[i] - 2 * k.t;
         double out[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            // X = lo + hi 2^64 < 2^12 P; its quotient by P from an FP64 estimate
-            // (off by at most one), the remainder exact in 128 bits
-            const double xd = (static_cast<double>(static_cast<uint64_t>(hi[e] >> 64)) *
-                                   18446744073709551616.0 +
-                               static_cast<double>(static_cast<uint64_t>(hi[e]))) *
-                                  18446744073709551616.0 +
-                              (static_cast<double>(static_cast<uint64_t>(lo[e] >> 64)) *
-                                   18446744073709551616.0 +
-                               static_cast<double>(static_cast<uint64_t>(lo[e])));
-            const uint64_t qe = static_cast<uint64_t>(xd * k.invP);
-            const u128 x = lo[e] + (hi[e] << 64);
+            // X mod 2^128 from the limb sums (each < 2^28): 16-bit digits with
+            // carries, packed two to a 32-bit word
+            uint32_t d[8];
+            uint32_t c = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const uint32_t v = (j < NL ? acc[e][j] : 0u) + c;   // < 2^28 + 2^13
+                d[j] = v & 0xFFFFu;
+                c = v >> 16;
+            }
+            const uint64_t lo64 = static_cast<uint64_t>(d[0] | (d[1] << 16)) |
+                                  (static_cast<uint64_t>(d[2] | (d[3] << 16)) << 32);
+            const uint64_t hi64 = static_cast<uint64_t>(d[4] | (d[5] << 16)) |
+                                  (static_cast<uint64_t>(d[6] | (d[7] << 16)) << 32);
+            const u128 x = (static_cast<u128>(hi64) << 64) | lo64;
+            const uint32_t qe = static_cast<uint32_t>(__float2int_rd(qs[e]));
+            // the true remainder lies in [-P, 2P), inside the signed 128-bit range
             i128 rr = static_cast<i128>(x - static_cast<u128>(qe) * P);
             if (rr < 0) rr += static_cast<i128>(P);
             if (rr >= static_cast<i128>(P)) rr -= static_cast<i128>(P);
-            // symmetric: C' in [-P/2, P/2)
             const bool neg = static_cast<u128>(rr) >= halfP;
             const u128 mag = neg ? P - static_cast<u128>(rr) : static_cast<u128>(rr);
             const int64_t j = j0 + e;
-            const double v = j < p ? u128_to_double_scaled(mag, ea + eB[j]) : 0.0;
+            const double v = j < p ? u128_to_double_scaled(static_cast<uint64_t>(mag >> 64),
+                                                           static_cast<uint64_t>(mag), ea + eB[j])
+                                   : 0.0;
             out[e] = neg ? -v : v;
         }
         double* crow = C + i * p + j0;
@@ -829,6 +943,11 @@ int crt_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const
     const int64_t b_plane = n * L.ldb;
     const bool f64in = dt == MOA_F64_CRT_F64IN;
 
+    CrtPow2 pow2{};
+    for (int l = 0; l < kCrtMaxModuli; ++l)
+        for (int e2 = 0; e2 < kPow2Cols; ++e2)
+            pow2.v[l][e2] = static_cast<uint8_t>(
+                (e2 < 128 ? (static_cast<u128>(1) << e2) % crt_mod(l) : 0));
     // launch 1: clear the column maxima; 2: row exponents of A beside the
     // column maxima of B; 3: residue planes of A and B
     cudaError_t e = cudaMemsetAsync(cmax, 0, static_cast<size_t>(p) * 8, s);
@@ -837,8 +956,8 @@ int crt_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const
     const int64_t chunk = 256;
     const int64_t gx = ceil_div(p, 256);
     const int64_t cblocks = gx * ceil_div(n, chunk);
-    const int ga = grid_for(a_plane / 8, 256);
-    const int gb = grid_for(b_plane / 8, 256);
+    const int ga = grid_for(a_plane / 4, 256);
+    const int gb = grid_for(b_plane / 4, 256);
     if (f64in) {
         const double* Ad = static_cast<const double*>(A);
         const double* Bd = static_cast<const double*>(B);
@@ -847,7 +966,7 @@ int crt_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const
             Ad, m, n, Bd, p, chunk, eA, cm, status, static_cast<int>(rblocks), gx);
         crt_residue_kernel<double><<<ga + gb, 256, 0, s>>>(
             Ad, m, n, L.lda, vec_rows(Ad, n, 2), eA, Bd, p, L.ldb, vec_rows(Bd, p, 2), eB, cm,
-            status, t, M, a_pl, a_plane, b_pl, b_plane, ga);
+            status, t, M, a_pl, a_plane, b_pl, b_plane, ga, pow2);
     } else {
         const float* Af = static_cast<const float*>(A);
         const float* Bf = static_cast<const float*>(B);
@@ -856,7 +975,7 @@ int crt_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const
             Af, m, n, Bf, p, chunk, eA, cm, status, static_cast<int>(rblocks), gx);
         crt_residue_kernel<float><<<ga + gb, 256, 0, s>>>(
             Af, m, n, L.lda, vec_rows(Af, n, 4), eA, Bf, p, L.ldb, vec_rows(Bf, p, 4), eB, cm,
-            status, t, M, a_pl, a_plane, b_pl, b_plane, ga);
+            status, t, M, a_pl, a_plane, b_pl, b_plane, ga, pow2);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "crt pre-pass launch");
@@ -898,8 +1017,13 @@ int crt_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const
     // launch 5: reconstruction
     const CrtConsts k = crt_consts(M, t);
     const int vec = (p % 2 == 0) && (reinterpret_cast<uintptr_t>(C) % 16 == 0);
-    crt_recon_kernel<<<grid_for(m * ceil_div(p, 4), 256), 256, 0, s>>>(
-        R, m, p, L.ldr, a.ks, eA, eB, static_cast<double*>(C), vec, k);
+    const int rgrid = grid_for(m * ceil_div(p, 4), 256);
+    if (M <= 14)   // P < 2^112: seven 16-bit limbs
+        crt_recon_kernel<7><<<rgrid, 256, 0, s>>>(R, m, p, L.ldr, a.ks, eA, eB,
+                                                  static_cast<double*>(C), vec, k);
+    else
+        crt_recon_kernel<8><<<rgrid, 256, 0, s>>>(R, m, p, L.ldr, a.ks, eA, eB,
+                                                  static_cast<double*>(C), vec, k);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "crt reconstruction launch");
     if (st) {
