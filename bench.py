@@ -2,17 +2,18 @@
 """Benchmark of the B300-native MoA ONF GEMM (Eq. eq:dnf).
 
 Default workload: the FP64-accurate ONF GEMM at m = n = p = 8192 on FP32
-inputs drawn i.i.d. N(0, 1) (seed 0): the FP64-accuracy split mode
-(MOA_F64_SPLIT_F32IN: integer digit slices of A and B as BF16 planes, slice
-products on the tensor cores, exact integer accumulation, one FP64 rounding),
-one GEMM (pre-passes included) per step.  The line carries the oracle's error
+inputs drawn i.i.d. N(0, 1) (seed 0): the modular-slice mode
+(MOA_F64_CRT_F32IN: rows of A and columns of B scaled to integers, their
+residues modulo 14 small moduli as BF16 planes, one exact tensor-core GEMM
+per modulus, the exact integer product recovered by the Chinese remainder
+theorem and rounded once to FP64), one GEMM (all passes included) per step.  The line carries the oracle's error
 on 64 sampled rows for the plain and the two row-scaled input kinds, the
 roofline of the slice-product kernel, the CPU oracle's rate, the end-to-end
 rate from pinned host memory, joules per GEMM, and the other precision modes
 and a short serving run under "modes".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl moa|reference]
-                  [--workload split_f64|square|split_f32|bf16|f64|...] [--n N]
+                  [--workload crt_f64|split_f64|square|split_f32|bf16|f64|...] [--n N]
 
 Under torchrun (N > 1) every rank runs its own replica of the workload (the
 GEMM is not sharded: replicas only); timing is the max over ranks and the
@@ -46,6 +47,8 @@ L2_MB = 126.0   # B300 L2 capacity
 TRAFFIC = {
     ("tf32", 8192): {"bytes": 1.652613e9 + 0.236939e9, "src": "gemm_tc.cu",
                      "sha": None},
+    ("f64_crt_f32in", 8192): {"bytes": 13867509760 + 986232576, "src": "crt.cu",
+                              "sha": "b5d020389af09e6a"},
 }
 
 
@@ -794,7 +797,16 @@ class ServeOperands:
         return A, B, C
 
 
-def serve_run(srv, ops, arrivals):
+def serve_dtype(tag, f64_mode="crt"):
+    """Mode of a served request: FP32 accuracy -> the three-slice split;
+    FP64 accuracy -> the modular slices ("crt") or the integer digits."""
+    from paper_2306_11148_b300 import moa
+    if tag == "f32":
+        return moa.MOA_F32_SPLIT
+    return moa.MOA_F64_CRT_F32IN if f64_mode == "crt" else moa.MOA_F64_SPLIT_F32IN
+
+
+def serve_run(srv, ops, arrivals, f64_mode="crt"):
     """Submits every arrival (t, m, n, p, tag) at its time; returns the submit
     results [(status, ticket, i, flops)], the completions and the wall time."""
     from paper_2306_11148_b300 import moa
@@ -804,7 +816,7 @@ def serve_run(srv, ops, arrivals):
         delay = t - (time.perf_counter() - t0)
         if delay > 0:
             time.sleep(delay)
-        dt = moa.MOA_F32_SPLIT if tag == "f32" else moa.MOA_F64_SPLIT_F32IN
+        dt = serve_dtype(tag, f64_mode)
         A, B, C = ops.request(i, m, n, p, dt)
         rc, tk = srv.submit(A, B, C, dt)
         codes.append((rc, tk, i, 2.0 * m * n * p))
@@ -819,10 +831,12 @@ def serve_run(srv, ops, arrivals):
     return codes, got, wall
 
 
-def bench_serve(ops, rate, seconds, seed=0, energy=None, n_streams=8):
+def bench_serve(ops, rate, seconds, seed=0, energy=None, n_streams=8, f64_mode="crt"):
     """Serving stream: Poisson arrivals at `rate` for `seconds`, each with its
     own (m, n, p) and precision tag from inputs.serve_arrivals, through one
-    server (64 GB arena, 32 in flight, 8 streams, 2 s queue deadline)."""
+    server (64 GB arena, 32 in flight, 8 streams, 2 s queue deadline).
+    f64_mode: the mode of the FP64-accuracy requests ("crt": modular slices,
+    "digits": integer digits)."""
     import torch
     from paper_2306_11148_b300 import inputs, moa
     arrivals = inputs.serve_arrivals(rate=rate, seconds=seconds, seed=seed)
@@ -831,7 +845,7 @@ def bench_serve(ops, rate, seconds, seed=0, energy=None, n_streams=8):
                      queue_capacity=ops.nout - 64, queue_deadline_s=2.0)
     j0 = energy.read_j() if energy else None
     try:
-        codes, got, wall = serve_run(srv, ops, arrivals)
+        codes, got, wall = serve_run(srv, ops, arrivals, f64_mode)
         st = srv.stats()
     finally:
         srv.close()
@@ -856,7 +870,7 @@ def bench_serve(ops, rate, seconds, seed=0, energy=None, n_streams=8):
         if i % 8 or rc != moa.MOA_OK or tk not in ok_ticket:
             continue
         _, m, n, p, tag = arrivals[i]
-        dt = moa.MOA_F32_SPLIT if tag == "f32" else moa.MOA_F64_SPLIT_F32IN
+        dt = serve_dtype(tag, f64_mode)
         A, B, C = ops.request(i, m, n, p, dt)
         alone = moa.gemm(A, B, dt)
         torch.cuda.synchronize()
@@ -877,7 +891,8 @@ def bench_serve(ops, rate, seconds, seed=0, energy=None, n_streams=8):
             "j_per_request": (j1 - j0) / len(done_ok) if (j0 is not None and j1 is not None
                                                            and done_ok) else None,
             "avg_w": (j1 - j0) / wall if (j0 is not None and j1 is not None) else None,
-            "alone_vs_mix_checked": checked, "alone_vs_mix_mismatch": mism}
+            "alone_vs_mix_checked": checked, "alone_vs_mix_mismatch": mism,
+            "f64_accuracy_mode": f64_mode}
 
 
 def sampled_rows_err(Ad, Bd, C, rows):
@@ -1114,7 +1129,7 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return
     N = args.n
-    mode = MODE_OF.get(args.workload, "f64_split_f32in")
+    mode = MODE_OF.get(args.workload, "f64_crt_f32in")
     per_step = []
     ops = cpu_operands(N, "f32", mode)
     for _ in range(args.warmup):
@@ -1144,12 +1159,14 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="moa", choices=["moa", "reference"])
-    ap.add_argument("--workload", default="split_f64", choices=list(MODE_OF))
+    ap.add_argument("--workload", default="crt_f64", choices=list(MODE_OF))
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-sweep", type=lambda x: [float(v) for v in x.split(",") if v],
                     default=[], help="extra arrival rates (comma list) to find capacity")
+    ap.add_argument("--serve-f64", default="crt", choices=["crt", "digits"],
+                    help="mode of the FP64-accuracy serving requests")
     ap.add_argument("--no-extras", action="store_true", help="skip the other-mode measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--profile", action="store_true",
@@ -1217,14 +1234,17 @@ def main():
         ops = ServeOperands(nbuf=4)
         clocks = ClockSampler(pci)
         clocks.start()
-        sat = bench_serve(ops, args.serve_rate, args.serve_seconds, energy=energy)
+        sat = bench_serve(ops, args.serve_rate, args.serve_seconds, energy=energy,
+                          f64_mode=args.serve_f64)
         sweep = []
         for r in args.serve_sweep:
-            sweep.append(bench_serve(ops, r, args.serve_seconds, energy=energy))
+            sweep.append(bench_serve(ops, r, args.serve_seconds, energy=energy,
+                                     f64_mode=args.serve_f64))
         clk = clocks.stop()
         # capacity: the highest served rate seen; a run at ~70 % of it
         cap = max([sat["served_per_s"]] + [x["served_per_s"] for x in sweep])
-        light = bench_serve(ops, 0.7 * cap, args.serve_seconds, energy=energy) \
+        light = bench_serve(ops, 0.7 * cap, args.serve_seconds, energy=energy,
+                            f64_mode=args.serve_f64) \
             if args.serve_sweep else None
         if rank == 0:
             line = {"metric": "served GEMM requests/s (continuous batching), p50/p99 latency",
@@ -1342,7 +1362,7 @@ def main():
         try:
             ops = ServeOperands(nbuf=2)
             modes["serve"] = bench_serve(ops, args.serve_rate, min(args.serve_seconds, 5.0),
-                                         energy=energy)
+                                         energy=energy, f64_mode=args.serve_f64)
             modes["serve"]["workload"] = (f"Poisson arrivals {args.serve_rate}/s for "
                                           f"{min(args.serve_seconds, 5.0)} s, each its own "
                                           "(m, n, p): m,p logU[64,4096], n logU[64,8192]; "
