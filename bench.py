@@ -680,6 +680,52 @@ def bench_grouped(steps, warmup, ws, stream, count=512, compare=True):
             "products": 1, "tile": [128, 0, 64]}
 
 
+def bench_grouped_crt(stream, count=64, div=1, steps=5, warmup=3, seed=3):
+    """`count` FP64-accuracy GEMMs (modular slices, FP32 N(0,1) inputs) with the
+    serving stream's shapes (m, p log-uniform in [64, 4096], n in [64, 8192],
+    each divided by `div`): one moa_gemm_grouped call per step against the
+    same problems as `count` separate moa_gemm_ex calls (CUDA events)."""
+    import torch
+    from paper_2306_11148_b300 import inputs, moa
+    arr = inputs.serve_arrivals(rate=count * 4.0, seconds=1.0, seed=seed)[:count]
+    probs = []
+    flops = 0.0
+    for i, (_, m, n, p, _) in enumerate(arr):
+        m, n, p = max(1, m // div), max(1, n // div), max(1, p // div)
+        A, B = inputs.normal_pair(m, n, p, dtype=torch.float32, seed=500 + i)
+        probs.append((A.cuda(), B.cuda(), torch.empty((m, p), dtype=torch.float64, device="cuda"),
+                      moa.MOA_F64_CRT_F32IN))
+        flops += 2.0 * m * n * p
+    descs = moa.make_descs(probs)
+    wsp = moa.Workspace(torch.device("cuda"))
+    L = moa.lib()
+    w, wb = wsp.get(int(L.moa_gemm_grouped_workspace_size(len(probs), descs)))
+    sh = int(stream.cuda_stream)
+
+    def grouped():
+        moa.check(L.moa_gemm_grouped(len(probs), descs, w, wb, sh))
+
+    sws = moa.Workspace(torch.device("cuda"))
+    sw, swb = sws.get(max(moa.moa_gemm_workspace_size(A.shape[0], A.shape[1], B.shape[1], dt, 0)
+                          for A, B, _, dt in probs))
+
+    def separate():
+        for A, B, C, dt in probs:
+            moa.check(moa.moa_gemm_ex(A.shape[0], A.shape[1], B.shape[1], dt, A.data_ptr(),
+                                      B.data_ptr(), C.data_ptr(), 0, sw, swb, sh, None))
+
+    with torch.cuda.stream(stream):
+        t_g = time_device(grouped, steps, warmup, stream, 1)
+        t_s = time_device(separate, steps, warmup, stream, 1)
+    moa.check(moa.moa_sync_status(sh))
+    return {"count": count, "shape_divisor": div, "flops_per_step": flops,
+            "grouped_ms": t_g / steps * 1e3, "separate_ms": t_s / steps * 1e3,
+            "grouped_tflops": flops * steps / t_g / 1e12,
+            "separate_tflops": flops * steps / t_s / 1e12,
+            "speedup": t_s / t_g,
+            "workload": f"{count} FP64-accuracy modular-slice GEMMs, serving shapes / {div}"}
+
+
 def bench_grouped_e2e(shapes, steps, warmup, ws):
     """The grouped batch end to end through moa_gemm_grouped with host
     buffers: every step copies all A and B operands from pinned host memory
@@ -1358,6 +1404,12 @@ def main():
             except Exception as e:  # report, do not hide
                 modes[m2] = {"error": str(e)}
 
+        # grouped modular-slice batches against separate launches
+        for div in (1, 4):
+            try:
+                modes[f"grouped_crt_div{div}"] = bench_grouped_crt(stream, count=64, div=div)
+            except Exception as e:  # report, do not hide
+                modes[f"grouped_crt_div{div}"] = {"error": str(e)}
         # a short run of the serving stream (each arrival its own shape)
         try:
             ops = ServeOperands(nbuf=2)

@@ -147,8 +147,13 @@ size_t moa_gemm_grouped_workspace_size(int count, const moa_gemm_desc* descs);
  * BF16 problems with 16-byte row pitches and 16-byte aligned A, B run in ONE
  * persistent tcgen05 launch: each problem gets a tile width from a shape cost
  * model, all output tiles are dealt to the SMs longest-first, and per-problem
- * TMA descriptors live in `ws`.  Other problems (other dtypes, unaligned
- * pitches) run one by one on the same stream.  A call that repeats the
+ * TMA descriptors live in `ws`.  Modular-slice problems (MOA_F64_CRT_*, with
+ * 16-byte aligned A and B) run as one grouped sequence: one exponent and one
+ * residue launch per input type over all of them, ONE persistent residue-GEMM
+ * launch over every (problem, modulus, tile) unit (longest K first), one
+ * reconstruction launch; each result is bit-identical to the problem run
+ * alone.  Other problems (other dtypes, unaligned pitches) run one by one on
+ * the same stream.  A call that repeats the
  * previous call of the same thread (identical descriptors, same `ws`, same
  * device) reuses the tables already in `ws`, so callers must not modify `ws`
  * between such calls.  Host-side tables are staged in pinned host memory
@@ -270,8 +275,8 @@ int moa_serve_create(const moa_serve_config* cfg, moa_server** out);
  * stays resident and valid until the ticket completes).  Non-blocking.  A
  * scheduler thread admits queued requests in FIFO order while fewer than
  * max_inflight run and the request's workspace fits in the free arena; the
- * requests admitted in one pass form a batch (its BF16 requests share one
- * grouped persistent launch) spread over the server's streams, so requests
+ * requests admitted in one pass form a batch (its BF16 and modular-slice
+ * requests share one grouped call) spread over the server's streams, so requests
  * arriving while others run overlap with them on the device.  Returns MOA_OK
  * (queued), MOA_ERR_BUDGET (the workspace alone exceeds the arena),
  * MOA_ERR_BUSY (queue full), MOA_ERR_ARG / MOA_ERR_DTYPE (bad descriptor).

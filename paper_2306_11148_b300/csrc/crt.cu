@@ -34,6 +34,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
+#include <vector>
 
 #include "crt.h"
 #include "fpbits.cuh"
@@ -389,6 +391,15 @@ struct CrtCfg {
     static constexpr uint32_t kIdesc = make_idesc(1u, kBM, BN, 0u, 1u);
 };
 
+// One problem of a grouped residue GEMM (device table).
+struct CrtGProb {
+    uint8_t* R;                   // its residue planes: l x m x ldr bytes (one K slice)
+    int64_t m, p, ldr;
+    int tiles_m, tiles_n, num_kb, group_m;
+    int M, bn;                    // moduli; tile width (128 or 256)
+    int unit_begin, pad;          // first unit of the problem in the work list
+};
+
 struct CrtGemmArgs {
     uint8_t* R;                   // residue planes: (l * ks + s) x m x ldr bytes
     int64_t m, n, p, ldr;
@@ -398,19 +409,13 @@ struct CrtGemmArgs {
     float qinv[kCrtMaxModuli];
     uint64_t wait_limit_ns;
     int* status;
+    // grouped launches: the problems (sorted by unit_begin) and their TMA
+    // descriptors (A, B per problem, global memory, 64-byte aligned)
+    const CrtGProb* probs;
+    const CUtensorMap* maps;
+    int nprob;
+    int num_units;
 };
-
-// Unit u: modulus l (slowest), tile t, K slice s (fastest).
-__device__ __forceinline__ void crt_unit(const CrtGemmArgs& a, int u, int& l, int& t, int& kb_lo,
-                                         int& kb_hi, int& s) {
-    const int per_l = a.tiles_m * a.tiles_n * a.ks;
-    l = u / per_l;
-    const int r = u - l * per_l;
-    t = r / a.ks;
-    s = r - t * a.ks;
-    kb_lo = static_cast<int>(static_cast<long long>(s) * a.num_kb / a.ks);
-    kb_hi = static_cast<int>(static_cast<long long>(s + 1) * a.num_kb / a.ks);
-}
 
 __device__ __forceinline__ void crt_tile_coords(int t, int tiles_m, int tiles_n, int group_m,
                                                 int& tm, int& tn) {
@@ -423,7 +428,65 @@ __device__ __forceinline__ void crt_tile_coords(int t, int tiles_m, int tiles_n,
     tn = r / gsize;
 }
 
-template <int BN>
+// What every role needs to know about work unit u.
+struct CrtUnit {
+    int g;                 // problem (0 for a single GEMM)
+    int l, tm, tn, s;      // modulus, tile, K slice
+    int kb_lo, kb_hi;      // K blocks
+    int bn;                // tile width (the MMA N extent)
+    uint8_t* R;
+    int64_t m, p, ldr;
+    int ks;
+};
+
+// Single GEMM: unit u = modulus l (slowest), tile t, K slice s (fastest).
+// Grouped: the problem by binary search over the units' starts, then modulus
+// and tile within it (one K slice).
+template <bool GROUPED>
+__device__ __forceinline__ CrtUnit crt_resolve(const CrtGemmArgs& a, int u) {
+    CrtUnit x;
+    if constexpr (!GROUPED) {
+        const int per_l = a.tiles_m * a.tiles_n * a.ks;
+        x.g = 0;
+        x.l = u / per_l;
+        const int r = u - x.l * per_l;
+        const int t = r / a.ks;
+        x.s = r - t * a.ks;
+        x.kb_lo = static_cast<int>(static_cast<long long>(x.s) * a.num_kb / a.ks);
+        x.kb_hi = static_cast<int>(static_cast<long long>(x.s + 1) * a.num_kb / a.ks);
+        crt_tile_coords(t, a.tiles_m, a.tiles_n, a.group_m, x.tm, x.tn);
+        x.bn = 0;   // the kernel's BN
+        x.R = a.R;
+        x.m = a.m;
+        x.p = a.p;
+        x.ldr = a.ldr;
+        x.ks = a.ks;
+    } else {
+        int lo = 0, hi = a.nprob - 1;
+        while (lo < hi) {   // last problem with unit_begin <= u
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.probs[mid].unit_begin <= u) lo = mid; else hi = mid - 1;
+        }
+        const CrtGProb& pr = a.probs[lo];
+        x.g = lo;
+        const int r0 = u - pr.unit_begin;
+        const int per_l = pr.tiles_m * pr.tiles_n;
+        x.l = r0 / per_l;
+        crt_tile_coords(r0 - x.l * per_l, pr.tiles_m, pr.tiles_n, pr.group_m, x.tm, x.tn);
+        x.s = 0;
+        x.kb_lo = 0;
+        x.kb_hi = pr.num_kb;
+        x.bn = pr.bn;
+        x.R = pr.R;
+        x.m = pr.m;
+        x.p = pr.p;
+        x.ldr = pr.ldr;
+        x.ks = 1;
+    }
+    return x;
+}
+
+template <int BN, bool GROUPED>
 __global__ void __launch_bounds__(CrtCfg<BN>::kThreads, 1)
     crt_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const CrtGemmArgs args) {
@@ -461,7 +524,7 @@ __global__ void __launch_bounds__(CrtCfg<BN>::kThreads, 1)
         ctl->abort = 0;
         fence_barrier_init();
     }
-    if (warp == 0 && lane == 0) {
+    if (!GROUPED && warp == 0 && lane == 0) {
         prefetch_tmap(&tmA);
         prefetch_tmap(&tmB);
     }
@@ -473,7 +536,8 @@ __global__ void __launch_bounds__(CrtCfg<BN>::kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    const int num_units = args.M * args.tiles_m * args.tiles_n * args.ks;
+    const int num_units =
+        GROUPED ? args.num_units : args.M * args.tiles_m * args.tiles_n * args.ks;
 
     if (warp == 0) {
         if (lane == 0) {
@@ -482,21 +546,29 @@ __global__ void __launch_bounds__(CrtCfg<BN>::kThreads, 1)
             uint32_t phase = 0;
             long issued = 0;
             bool ok = true;
+            int g_prev = -1;
             for (int u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
-                int l, t, kb_lo, kb_hi, s, tm, tn;
-                crt_unit(args, u, l, t, kb_lo, kb_hi, s);
-                crt_tile_coords(t, args.tiles_m, args.tiles_n, args.group_m, tm, tn);
-                for (int kb = kb_lo; kb < kb_hi; ++kb) {
+                const CrtUnit x = crt_resolve<GROUPED>(args, u);
+                const int bn = GROUPED ? x.bn : BN;
+                const CUtensorMap* mA = GROUPED ? args.maps + 2 * x.g : &tmA;
+                const CUtensorMap* mB = GROUPED ? args.maps + 2 * x.g + 1 : &tmB;
+                if (GROUPED && x.g != g_prev) {
+                    prefetch_tmap(mA);
+                    prefetch_tmap(mB);
+                    g_prev = x.g;
+                }
+                const uint32_t bytes = Cfg::kAStage + static_cast<uint32_t>(bn / 64) * Cfg::kBChunk;
+                for (int kb = x.kb_lo; kb < x.kb_hi; ++kb) {
                     if (!mbar_wait(&empty[stage], phase ^ 1u, ctl, limit, status)) {
                         ok = false;
                         break;
                     }
-                    mbar_arrive_expect_tx(&full[stage], Cfg::kStageBytes);
-                    tma_load_3d(sA + stage * Cfg::kAStage, &tmA, &full[stage], kb * kBK, tm * kBM, l);
-#pragma unroll
-                    for (int c = 0; c < BN / 64; ++c)
-                        tma_load_3d(sB + stage * Cfg::kBStage + c * Cfg::kBChunk, &tmB, &full[stage],
-                                    tn * BN + c * 64, kb * kBK, l);
+                    mbar_arrive_expect_tx(&full[stage], bytes);
+                    tma_load_3d(sA + stage * Cfg::kAStage, mA, &full[stage], kb * kBK, x.tm * kBM,
+                                x.l);
+                    for (int c = 0; c < bn / 64; ++c)
+                        tma_load_3d(sB + stage * Cfg::kBStage + c * Cfg::kBChunk, mB, &full[stage],
+                                    x.tn * bn + c * 64, kb * kBK, x.l);
                     ++issued;
                     if (++stage == kStages) {
                         stage = 0;
@@ -524,8 +596,10 @@ __global__ void __launch_bounds__(CrtCfg<BN>::kThreads, 1)
             long cnt = 0;
             bool ok = true;
             for (int u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
-                int l, t, kb_lo, kb_hi, s;
-                crt_unit(args, u, l, t, kb_lo, kb_hi, s);
+                const CrtUnit x = crt_resolve<GROUPED>(args, u);
+                const int kb_lo = x.kb_lo, kb_hi = x.kb_hi;
+                const uint32_t idesc =
+                    GROUPED ? make_idesc(1u, kBM, static_cast<uint32_t>(x.bn), 0u, 1u) : Cfg::kIdesc;
                 for (int kb0 = kb_lo; kb0 < kb_hi && ok; kb0 += kChunkKB, ++cnt) {
                     const int buf = static_cast<int>(cnt & 1);
                     const uint32_t bph = static_cast<uint32_t>((cnt >> 1) & 1);
@@ -550,7 +624,7 @@ __global__ void __launch_bounds__(CrtCfg<BN>::kThreads, 1)
 #pragma unroll
                         for (int k = 0; k < 4; ++k)
                             mma_f16(d, adesc + static_cast<uint64_t>((k * 32) >> 4),
-                                    bdesc + static_cast<uint64_t>((k * 16 * 128) >> 4), Cfg::kIdesc,
+                                    bdesc + static_cast<uint64_t>((k * 16 * 128) >> 4), idesc,
                                     (kb == kb0 && k == 0) ? 0u : 1u);
                         mma_commit(&empty[stage]);
                         if (++stage == kStages) {
@@ -576,14 +650,15 @@ __global__ void __launch_bounds__(CrtCfg<BN>::kThreads, 1)
         long cnt = 0;
         bool ok = true;
         for (int u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
-            int l, t, kb_lo, kb_hi, s, tm, tn;
-            crt_unit(args, u, l, t, kb_lo, kb_hi, s);
-            crt_tile_coords(t, args.tiles_m, args.tiles_n, args.group_m, tm, tn);
+            const CrtUnit x = crt_resolve<GROUPED>(args, u);
+            const int l = x.l, tm = x.tm, tn = x.tn, s = x.s;
+            const int bn = GROUPED ? x.bn : BN;
+            const bool cols_live = h * 64 < bn;   // narrow tiles leave the last warps idle
             const float qf = args.qf[l], qinv = args.qinv[l];
             float acc[64];
 #pragma unroll
             for (int i = 0; i < 64; ++i) acc[i] = 0.f;
-            for (int kb0 = kb_lo; kb0 < kb_hi; kb0 += kChunkKB, ++cnt) {
+            for (int kb0 = x.kb_lo; kb0 < x.kb_hi; kb0 += kChunkKB, ++cnt) {
                 const int buf = static_cast<int>(cnt & 1);
                 const uint32_t bph = static_cast<uint32_t>((cnt >> 1) & 1);
                 ok = mbar_wait(&tfull[buf], bph, ctl, limit, status);
@@ -594,15 +669,17 @@ __global__ void __launch_bounds__(CrtCfg<BN>::kThreads, 1)
                 tc_fence_after();
                 const uint32_t a_base =
                     tmem_base + lane_base + static_cast<uint32_t>(buf * BN + h * 64);
+                if (!GROUPED || cols_live) {
 #pragma unroll
-                for (int g = 0; g < 4; ++g) {
-                    uint32_t r[16];
-                    tmem_ld16(a_base + 16u * g, r);
-                    tmem_ld_wait();
+                    for (int g = 0; g < 4; ++g) {
+                        uint32_t r[16];
+                        tmem_ld16(a_base + 16u * g, r);
+                        tmem_ld_wait();
 #pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        acc[g * 16 + i] =
-                            __fadd_rn(acc[g * 16 + i], mod_reduce(__uint_as_float(r[i]), qf, qinv));
+                        for (int i = 0; i < 16; ++i)
+                            acc[g * 16 + i] = __fadd_rn(acc[g * 16 + i],
+                                                        mod_reduce(__uint_as_float(r[i]), qf, qinv));
+                    }
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -611,8 +688,8 @@ __global__ void __launch_bounds__(CrtCfg<BN>::kThreads, 1)
             if (!ok) break;
             // the unit's residues in [0, q) as bytes of plane (l, s)
             const int64_t row = static_cast<int64_t>(tm) * kBM + q * 32 + lane;
-            const int64_t col0 = static_cast<int64_t>(tn) * BN + h * 64;
-            if (row < args.m && col0 < args.p) {
+            const int64_t col0 = static_cast<int64_t>(tn) * bn + h * 64;
+            if (cols_live && row < x.m && col0 < x.p) {
                 uint32_t w[16];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
@@ -626,15 +703,14 @@ __global__ void __launch_bounds__(CrtCfg<BN>::kThreads, 1)
                     }
                     w[i] = word;
                 }
-                uint8_t* dst = args.R + ((static_cast<int64_t>(l) * args.ks + s) * args.m + row) *
-                                            args.ldr + col0;
-                if (col0 + 64 <= args.ldr) {
+                uint8_t* dst = x.R + ((static_cast<int64_t>(l) * x.ks + s) * x.m + row) * x.ldr + col0;
+                if (col0 + 64 <= x.ldr) {
 #pragma unroll
                     for (int v = 0; v < 4; ++v)
                         reinterpret_cast<uint4*>(dst)[v] =
                             make_uint4(w[4 * v], w[4 * v + 1], w[4 * v + 2], w[4 * v + 3]);
                 } else {
-                    for (int i = 0; i < 64 && col0 + i < args.ldr; ++i)
+                    for (int i = 0; i < 64 && col0 + i < x.ldr; ++i)
                         dst[i] = static_cast<uint8_t>((w[i >> 2] >> (8 * (i & 3))) & 0xFFu);
                 }
             }
@@ -736,26 +812,28 @@ __device__ __forceinline__ void crt_load(const uint8_t* __restrict__ R, int64_t 
 // the quotient q = floor(X / P) estimated in FP32 from sum_l r_l W_l / P (off
 // by at most one); C' = X - q P corrected into [0, P), then into
 // [-P/2, P/2), rounded once and scaled by 2^(eA_i + eB_j - 2t).  NL = 7
-// covers P < 2^112 (up to 14 moduli), NL = 8 the rest.
+// covers P < 2^112 (up to 14 moduli), NL = 8 the rest.  The thread takes
+// the groups of 4 outputs g0, g0 + gstep, ... of the m x ceil(p / 4) groups.
 template <int NL>
-__global__ void __launch_bounds__(256)
-    crt_recon_kernel(const uint8_t* __restrict__ R, int64_t m, int64_t p, int64_t ldr, int ks,
-                     const int* __restrict__ eA, const int* __restrict__ eB, double* __restrict__ C,
-                     int vec, const CrtConsts k) {
+__device__ __forceinline__ void crt_recon_range(const uint8_t* __restrict__ R, int64_t m, int64_t p,
+                                                int64_t ldr, int ks, int t,
+                                                const int* __restrict__ eA,
+                                                const int* __restrict__ eB,
+                                                double* __restrict__ C, int vec,
+                                                const CrtConsts& k, int64_t g0, int64_t gstep) {
     const int64_t gpr = (p + 3) / 4;
     const int64_t total = m * gpr;
     const int64_t plane_stride = m * ldr;
     const u128 P = (static_cast<u128>(k.P_hi) << 64) | k.P_lo;
     const u128 halfP = P >> 1;
-    for (int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g < total;
-         g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    for (int64_t g = g0; g < total; g += gstep) {
         const int64_t i = g / gpr, j0 = (g - i * gpr) * 4;
         uint32_t w[kCrtMaxModuli];
         crt_load<0>(R + i * ldr + j0, plane_stride, ks, k.M, w);
         uint32_t acc[4][NL] = {};
         float qs[4] = {0.f, 0.f, 0.f, 0.f};
         crt_accumulate<0, NL>(w, k.M, k, acc, qs);
-        const int ea = eA[i] - 2 * k.t;
+        const int ea = eA[i] - 2 * t;
         double out[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -797,6 +875,108 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+template <int NL>
+__global__ void __launch_bounds__(256)
+    crt_recon_kernel(const uint8_t* __restrict__ R, int64_t m, int64_t p, int64_t ldr, int ks,
+                     const int* __restrict__ eA, const int* __restrict__ eB, double* __restrict__ C,
+                     int vec, const CrtConsts k) {
+    crt_recon_range<NL>(R, m, p, ldr, ks, k.t, eA, eB, C, vec, k,
+                        static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x,
+                        static_cast<int64_t>(gridDim.x) * blockDim.x);
+}
+
+// ---------------------------------------------------------------- grouped launches
+// One problem of a grouped call, as the pre-pass and reconstruction launches
+// see it: operands, its workspace region, and the block range it owns in
+// each launch (blocks [*_begin, *_begin + *_blocks)).
+struct CrtGPass {
+    const void* A;
+    const void* B;
+    double* C;
+    int64_t m, n, p, lda, ldb, ldr, a_plane, b_plane, gx;
+    __nv_bfloat16* a_pl;
+    __nv_bfloat16* b_pl;
+    int* eA;
+    int* eB;
+    void* cmax;
+    const uint8_t* R;
+    int M, t, va, vb, vec_c, f64in;
+    int exps_begin, rblocks, cblocks;
+    int res_begin, ga, gb;
+    int rec_begin, rec_blocks;
+};
+
+// The problem whose block range of a launch holds block b (begin(i) ascending).
+template <typename F>
+__device__ __forceinline__ int find_owner(int count, int b, F begin) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (begin(mid) <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Grouped exponent pass over the problems of one input type.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    crt_g_exps_kernel(const CrtGPass* __restrict__ pr, int count, int* status) {
+    const int b = static_cast<int>(blockIdx.x);
+    const int g = find_owner(count, b, [&](int i) { return pr[i].exps_begin; });
+    const CrtGPass& x = pr[g];
+    const int local = b - x.exps_begin;
+    using U = typename Bits<T>::U;
+    if (local < x.rblocks)
+        crt_row_exp_part(static_cast<const T*>(x.A), x.m, x.n, x.eA, status, local, x.rblocks);
+    else if (local < x.rblocks + x.cblocks)
+        crt_col_max_part(static_cast<const T*>(x.B), x.n, x.p, 256, static_cast<U*>(x.cmax),
+                         local - x.rblocks, x.gx);
+}
+
+// Grouped residue pass over the problems of one input type.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    crt_g_residue_kernel(const CrtGPass* __restrict__ pr, int count, int* status,
+                         const CrtPow2 pow2) {
+    __shared__ float tab[kCrtMaxModuli * kPow2Cols];
+    for (int i = threadIdx.x; i < kCrtMaxModuli * kPow2Cols; i += blockDim.x)
+        tab[i] = static_cast<float>(pow2.v[i / kPow2Cols][i % kPow2Cols]);
+    __syncthreads();
+    const int b = static_cast<int>(blockIdx.x);
+    const int g = find_owner(count, b, [&](int i) { return pr[i].res_begin; });
+    const CrtGPass& x = pr[g];
+    const int local = b - x.res_begin;
+    using U = typename Bits<T>::U;
+    if (local < x.ga)
+        crt_residue_part<T, 0>(static_cast<const T*>(x.A), x.m, x.n, x.lda, x.eA, nullptr, status,
+                               x.t, x.M, x.va, tab, x.a_pl, x.a_plane, local, x.ga);
+    else if (local < x.ga + x.gb)
+        crt_residue_part<T, 1>(static_cast<const T*>(x.B), x.n, x.p, x.ldb, x.eB,
+                               static_cast<const U*>(x.cmax), status, x.t, x.M, x.vb, tab, x.b_pl,
+                               x.b_plane, local - x.ga, x.gb);
+}
+
+// Grouped reconstruction: each block serves one problem, with that problem's
+// CRT constants (consts[M - kCrtMinModuli]) copied to shared memory.
+__global__ void __launch_bounds__(256)
+    crt_g_recon_kernel(const CrtGPass* __restrict__ pr, int count,
+                       const CrtConsts* __restrict__ consts) {
+    __shared__ CrtConsts k;
+    const int b = static_cast<int>(blockIdx.x);
+    const int g = find_owner(count, b, [&](int i) { return pr[i].rec_begin; });
+    const CrtGPass& x = pr[g];
+    {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(consts + (x.M - kCrtMinModuli));
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&k);
+        for (int i = threadIdx.x; i < static_cast<int>(sizeof(CrtConsts) / 4); i += blockDim.x)
+            dst[i] = src[i];
+    }
+    __syncthreads();
+    crt_recon_range<8>(x.R, x.m, x.p, x.ldr, 1, x.t, x.eA, x.eB, x.C, x.vec_c, k,
+                       static_cast<int64_t>(b - x.rec_begin) * blockDim.x + threadIdx.x,
+                       static_cast<int64_t>(x.rec_blocks) * blockDim.x);
+}
+
 int grid_for(int64_t total, int threads) {
     const int64_t want = ceil_div(total, threads);
     const int64_t cap = 16L * num_sms();
@@ -834,18 +1014,19 @@ int crt_block_n(int64_t m, int64_t p, int M, long sms) {
     return cost(128, 0.9) < cost(256, 1.0) ? 128 : 256;
 }
 
-template <int BN>
+template <int BN, bool GROUPED = false>
 int launch_crt_gemm(const CrtGemmArgs& a, const CUtensorMap& tmA, const CUtensorMap& tmB,
                     cudaStream_t s, moa_stats* st) {
     using Cfg = CrtCfg<BN>;
     static std::atomic<uint64_t> attr_done{0};
-    int rc = smem_attr_once(reinterpret_cast<const void*>(crt_gemm_kernel<BN>), Cfg::kSmem,
+    int rc = smem_attr_once(reinterpret_cast<const void*>(crt_gemm_kernel<BN, GROUPED>), Cfg::kSmem,
                             attr_done, "cudaFuncSetAttribute(crt_gemm)");
     if (rc != MOA_OK) return rc;
-    const long units = static_cast<long>(a.M) * a.tiles_m * a.tiles_n * a.ks;
+    const long units =
+        GROUPED ? a.num_units : static_cast<long>(a.M) * a.tiles_m * a.tiles_n * a.ks;
     const int grid = static_cast<int>(std::min<long>(units, num_sms()));
     prof_begin(s);
-    crt_gemm_kernel<BN><<<grid, Cfg::kThreads, Cfg::kSmem, s>>>(tmA, tmB, a);
+    crt_gemm_kernel<BN, GROUPED><<<grid, Cfg::kThreads, Cfg::kSmem, s>>>(tmA, tmB, a);
     cudaError_t e = cudaGetLastError();
     prof_end(s);
     if (e != cudaSuccess) return cuda_fail(e, "crt_gemm_kernel launch");
@@ -1031,6 +1212,232 @@ int crt_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const
         st->products = M;
         st->kernels = 5;
     }
+    return MOA_OK;
+}
+
+// ---------------------------------------------------------------- grouped host side
+namespace {
+
+struct GroupedPlan {
+    size_t consts_off, pass_off, prob_off, maps_off, head_bytes;   // tables, one upload
+    size_t cmax_off, cmax_bytes;                                     // one memset
+    std::vector<size_t> region;   // per taken problem: its region in the workspace
+    size_t total;
+};
+
+struct Taken {
+    int idx;          // index in the caller's descriptors
+    int M, t, bn;
+    CrtLayout L;      // offsets within the problem's region (cmax unused)
+};
+
+// The problems this path takes, F32-input ones first, and the workspace plan.
+GroupedPlan grouped_plan(int count, const moa_gemm_desc* d, std::vector<Taken>* taken) {
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    std::vector<Taken> tk;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int g = 0; g < count; ++g) {
+            if (!crt_grouped_ok(d[g])) continue;
+            if ((d[g].dt == MOA_F64_CRT_F64IN) != (pass == 1)) continue;
+            Taken x{};
+            x.idx = g;
+            x.M = crt_moduli_for(d[g].dt, d[g].n, 0);
+            x.t = crt_bits(d[g].n, x.M);
+            x.L = crt_layout(d[g].m, d[g].n, d[g].p, x.M);
+            tk.push_back(x);
+        }
+    const size_t G = tk.size();
+    GroupedPlan P{};
+    size_t off = 0;
+    P.consts_off = off;
+    off += al(sizeof(CrtConsts) * (kCrtMaxModuli - kCrtMinModuli + 1));
+    P.pass_off = off;
+    off += al(sizeof(CrtGPass) * G);
+    P.prob_off = off;
+    off += al(sizeof(CrtGProb) * G);
+    P.maps_off = off;
+    off += al(sizeof(CUtensorMap) * 2 * G);
+    P.head_bytes = off;
+    P.cmax_off = off;
+    for (const Taken& x : tk) off += al(static_cast<size_t>(d[x.idx].p) * 8);
+    P.cmax_bytes = off - P.cmax_off;
+    for (const Taken& x : tk) {
+        P.region.push_back(off);
+        // the single-call layout without its column-max block and with one K slice
+        off += al(x.L.r_off + static_cast<size_t>(x.M) * d[x.idx].m * x.L.ldr);
+    }
+    P.total = G ? off : 0;
+    if (taken) *taken = tk;
+    return P;
+}
+
+}  // namespace
+
+bool crt_grouped_ok(const moa_gemm_desc& d) {
+    const int64_t lim = int64_t(1) << 31;
+    return is_crt(d.dt) && d.m > 0 && d.n > 0 && d.p > 0 && d.m < lim && d.n < lim && d.p < lim &&
+           reinterpret_cast<uintptr_t>(d.A) % 16 == 0 && reinterpret_cast<uintptr_t>(d.B) % 16 == 0 &&
+           reinterpret_cast<uintptr_t>(d.C) % 8 == 0 && d.C != nullptr &&
+           crt_moduli_for(d.dt, d.n, 0) > 0 && crt_bits(d.n, crt_moduli_for(d.dt, d.n, 0)) >= 1 &&
+           ceil_div(d.n, 256) * ceil_div(d.p, 256) <= (1L << 30);
+}
+
+size_t crt_grouped_workspace(int count, const moa_gemm_desc* d) {
+    return grouped_plan(count, d, nullptr).total;
+}
+
+int crt_grouped_launch(int count, const moa_gemm_desc* d, void* ws, size_t ws_bytes,
+                       cudaStream_t s) {
+    std::vector<Taken> tk;
+    const GroupedPlan P = grouped_plan(count, d, &tk);
+    const int G = static_cast<int>(tk.size());
+    if (G == 0) return MOA_OK;
+    if (ws == nullptr || ws_bytes < P.total)
+        return fail(MOA_ERR_WORKSPACE, "workspace too small for the grouped modular-slice path");
+    int* status = launch_status_ptr();
+    if (!status) return MOA_ERR_CUDA;
+    const long sms = num_sms();
+    uint8_t* base = static_cast<uint8_t*>(ws);
+    int slot = 0;
+    uint8_t* host = static_cast<uint8_t*>(staging_get(P.head_bytes, &slot));
+    if (!host) return fail(MOA_ERR_CUDA, "pinned staging buffer unavailable");
+    std::memset(host, 0, P.head_bytes);
+    auto* consts = reinterpret_cast<CrtConsts*>(host + P.consts_off);
+    for (int M = kCrtMinModuli; M <= kCrtMaxModuli; ++M) consts[M - kCrtMinModuli] = crt_consts(M, 0);
+    auto* pass = reinterpret_cast<CrtGPass*>(host + P.pass_off);
+    auto* probs = reinterpret_cast<CrtGProb*>(host + P.prob_off);
+    auto* maps = reinterpret_cast<CUtensorMap*>(host + P.maps_off);
+
+    // pre-pass and reconstruction tables (F32-input problems first)
+    int n32 = 0;
+    int exps_pos[2] = {0, 0}, res_pos[2] = {0, 0}, rec_pos = 0;
+    size_t cmax_pos = P.cmax_off;
+    for (int i = 0; i < G; ++i) {
+        const Taken& x = tk[i];
+        const moa_gemm_desc& dd = d[x.idx];
+        const int ty = dd.dt == MOA_F64_CRT_F64IN ? 1 : 0;
+        n32 += ty == 0;
+        uint8_t* r = base + P.region[i];
+        CrtGPass& q = pass[i];
+        q.A = dd.A;
+        q.B = dd.B;
+        q.C = static_cast<double*>(dd.C);
+        q.m = dd.m;
+        q.n = dd.n;
+        q.p = dd.p;
+        q.lda = x.L.lda;
+        q.ldb = x.L.ldb;
+        q.ldr = x.L.ldr;
+        q.a_plane = dd.m * x.L.lda;
+        q.b_plane = dd.n * x.L.ldb;
+        q.gx = ceil_div(dd.p, 256);
+        q.a_pl = reinterpret_cast<__nv_bfloat16*>(r + x.L.a_off);
+        q.b_pl = reinterpret_cast<__nv_bfloat16*>(r + x.L.b_off);
+        q.eA = reinterpret_cast<int*>(r + x.L.ea_off);
+        q.eB = reinterpret_cast<int*>(r + x.L.eb_off);
+        q.cmax = base + cmax_pos;
+        cmax_pos += (static_cast<size_t>(dd.p) * 8 + 255) / 256 * 256;
+        q.R = r + x.L.r_off;
+        q.M = x.M;
+        q.t = x.t;
+        const int per16 = ty ? 2 : 4;
+        q.va = vec_rows(dd.A, dd.n, per16);
+        q.vb = vec_rows(dd.B, dd.p, per16);
+        q.vec_c = (dd.p % 2 == 0) && (reinterpret_cast<uintptr_t>(dd.C) % 16 == 0);
+        q.f64in = ty;
+        q.rblocks = static_cast<int>(std::min<int64_t>(ceil_div(dd.m, 8), 16L * sms));
+        q.cblocks = static_cast<int>(q.gx * ceil_div(dd.n, 256));
+        q.exps_begin = exps_pos[ty];
+        exps_pos[ty] += q.rblocks + q.cblocks;
+        q.ga = grid_for(q.a_plane / 4, 256);
+        q.gb = grid_for(q.b_plane / 4, 256);
+        q.res_begin = res_pos[ty];
+        res_pos[ty] += q.ga + q.gb;
+        q.rec_blocks = grid_for(dd.m * ceil_div(dd.p, 4), 256);
+        q.rec_begin = rec_pos;
+        rec_pos += q.rec_blocks;
+    }
+    // residue-GEMM problems, longest K first, each with its TMA descriptors
+    std::vector<int> order(G);
+    for (int i = 0; i < G; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return d[tk[a].idx].n > d[tk[b].idx].n; });
+    long units = 0;
+    for (int j = 0; j < G; ++j) {
+        const int i = order[j];
+        const Taken& x = tk[i];
+        const moa_gemm_desc& dd = d[x.idx];
+        CrtGProb& g = probs[j];
+        g.R = base + P.region[i] + x.L.r_off;
+        g.m = dd.m;
+        g.p = dd.p;
+        g.ldr = x.L.ldr;
+        g.bn = crt_block_n(dd.m, dd.p, x.M, sms);
+        g.tiles_m = static_cast<int>(ceil_div(dd.m, kBM));
+        g.tiles_n = static_cast<int>(ceil_div(dd.p, g.bn));
+        g.num_kb = static_cast<int>(ceil_div(dd.n, kBK));
+        g.group_m = split_raster_group(dd.n);
+        g.M = x.M;
+        g.unit_begin = static_cast<int>(units);
+        units += static_cast<long>(x.M) * g.tiles_m * g.tiles_n;
+        int rc = make_tmap_3d(&maps[2 * j], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, pass[i].a_pl,
+                              static_cast<uint64_t>(dd.n), static_cast<uint64_t>(dd.m),
+                              static_cast<uint64_t>(x.M), static_cast<uint64_t>(x.L.lda) * 2,
+                              static_cast<uint64_t>(pass[i].a_plane) * 2, kBK, kBM);
+        if (rc == MOA_OK)
+            rc = make_tmap_3d(&maps[2 * j + 1], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, pass[i].b_pl,
+                              static_cast<uint64_t>(dd.p), static_cast<uint64_t>(dd.n),
+                              static_cast<uint64_t>(x.M), static_cast<uint64_t>(x.L.ldb) * 2,
+                              static_cast<uint64_t>(pass[i].b_plane) * 2, 64, kBK);
+        if (rc != MOA_OK) {
+            staging_release(slot, s);
+            return rc;
+        }
+    }
+    if (units > (1L << 30)) {
+        staging_release(slot, s);
+        return fail(MOA_ERR_ARG, "too many units in one grouped call");
+    }
+    cudaError_t e = cudaMemcpyAsync(base, host, P.head_bytes, cudaMemcpyHostToDevice, s);
+    staging_release(slot, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(grouped crt tables)");
+    e = cudaMemsetAsync(base + P.cmax_off, 0, P.cmax_bytes, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(grouped colmax)");
+    const CrtGPass* dpass = reinterpret_cast<const CrtGPass*>(base + P.pass_off);
+    CrtPow2 pow2{};
+    for (int l = 0; l < kCrtMaxModuli; ++l)
+        for (int e2 = 0; e2 < kPow2Cols; ++e2)
+            pow2.v[l][e2] = static_cast<uint8_t>((static_cast<u128>(1) << e2) % crt_mod(l));
+    const int n64 = G - n32;
+    if (n32 > 0) {
+        crt_g_exps_kernel<float><<<exps_pos[0], 256, 0, s>>>(dpass, n32, status);
+        crt_g_residue_kernel<float><<<res_pos[0], 256, 0, s>>>(dpass, n32, status, pow2);
+    }
+    if (n64 > 0) {
+        crt_g_exps_kernel<double><<<exps_pos[1], 256, 0, s>>>(dpass + n32, n64, status);
+        crt_g_residue_kernel<double><<<res_pos[1], 256, 0, s>>>(dpass + n32, n64, status, pow2);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "grouped crt pre-pass launch");
+    CrtGemmArgs a{};
+    for (int l = 0; l < kCrtMaxModuli; ++l) {
+        a.qf[l] = static_cast<float>(crt_mod(l));
+        a.qinv[l] = 1.0f / static_cast<float>(crt_mod(l));
+    }
+    a.wait_limit_ns = wait_limit_ns();
+    a.status = status;
+    a.probs = reinterpret_cast<const CrtGProb*>(base + P.prob_off);
+    a.maps = reinterpret_cast<const CUtensorMap*>(base + P.maps_off);
+    a.nprob = G;
+    a.num_units = static_cast<int>(units);
+    CUtensorMap unused{};
+    int rc = launch_crt_gemm<256, true>(a, unused, unused, s, nullptr);
+    if (rc != MOA_OK) return rc;
+    crt_g_recon_kernel<<<rec_pos, 256, 0, s>>>(
+        dpass, G, reinterpret_cast<const CrtConsts*>(base + P.consts_off));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "grouped crt reconstruction launch");
+    log_msg(2, "grouped crt: %d problems, %ld units", G, units);
     return MOA_OK;
 }
 

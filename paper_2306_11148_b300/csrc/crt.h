@@ -26,6 +26,19 @@ size_t crt_workspace_bytes(int64_t m, int64_t n, int64_t p, moa_dtype dt, int sl
 int crt_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const void* B, void* C,
              int slices, void* ws, size_t ws_bytes, cudaStream_t s, moa_stats* st);
 
+// Grouped calls (moa_gemm_grouped): the modular-slice problems of a call that
+// this path takes (positive sizes, 16-byte aligned A and B, 8-byte aligned C)
+// run as one exponent and one residue launch per input type, ONE persistent
+// residue GEMM launch over every (problem, modulus, tile) unit and one
+// reconstruction launch.  Each problem's result is bit-identical to the same
+// problem run alone.
+bool crt_grouped_ok(const moa_gemm_desc& d);
+size_t crt_grouped_workspace(int count, const moa_gemm_desc* d);
+// Runs the problems of d[] that crt_grouped_ok takes; `ws` must hold
+// crt_grouped_workspace(count, d) bytes.
+int crt_grouped_launch(int count, const moa_gemm_desc* d, void* ws, size_t ws_bytes,
+                       cudaStream_t s);
+
 // Workspace layout of a modular-slice call (byte offsets from the base).
 struct CrtLayout {
     int M;                  // moduli

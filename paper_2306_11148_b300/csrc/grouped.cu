@@ -25,6 +25,7 @@
 #include <queue>
 #include <vector>
 
+#include "crt.h"
 #include "epilogue.cuh"
 #include "internal.h"
 #include "ptx.cuh"
@@ -430,6 +431,9 @@ int launch_kernel(uint8_t* dev, const Layout& L, int grid, cudaStream_t s) {
 
 }  // namespace
 
+void* staging_get(size_t n, int* slot) { return t_staging.get(n, slot); }
+void staging_release(int slot, cudaStream_t s) { t_staging.release(slot, s); }
+
 int grouped_plan_bn(int64_t m, int64_t n, int64_t p) {
     moa_gemm_desc d{};
     d.m = m;
@@ -439,21 +443,27 @@ int grouped_plan_bn(int64_t m, int64_t n, int64_t p) {
     return plan_bn(d);
 }
 
-size_t grouped_workspace(int count, const moa_gemm_desc* d) {
+// Workspace of a grouped call: the persistent BF16 tables, then the grouped
+// modular-slice region, then scratch for the problems run one by one.
+size_t grouped_main_bytes(int count, const moa_gemm_desc* d) {
     int G = 0;
     long T = 0;
-    size_t side = 0;
-    for (int g = 0; g < count; ++g) {
+    for (int g = 0; g < count; ++g)
         if (persistent_ok(d[g])) {
             ++G;
             T += ceil_div(d[g].m, kGBM) * ceil_div(d[g].p, plan_bn(d[g]));
-        } else if (d[g].m >= 0 && d[g].n >= 0 && d[g].p >= 0) {
-            side = std::max(side, workspace_bytes(d[g].m, d[g].n, d[g].p, d[g].dt, 0));
         }
-    }
-    size_t main = 0;
-    if (G > 0) main = layout_for(G, T, static_cast<int>(std::min<long>(T, num_sms()))).total;
-    return main + side;
+    return G > 0 ? layout_for(G, T, static_cast<int>(std::min<long>(T, num_sms()))).total : 0;
+}
+
+size_t grouped_workspace(int count, const moa_gemm_desc* d) {
+    size_t side = 0;
+    for (int g = 0; g < count; ++g)
+        if (!persistent_ok(d[g]) && !crt_grouped_ok(d[g]) && d[g].m >= 0 && d[g].n >= 0 &&
+            d[g].p >= 0)
+            side = std::max(side, workspace_bytes(d[g].m, d[g].n, d[g].p, d[g].dt, 0));
+    const size_t crt = crt_grouped_workspace(count, d);
+    return grouped_main_bytes(count, d) + (crt + 255) / 256 * 256 + side;
 }
 
 int grouped_launch(int count, const moa_gemm_desc* d, void* ws, size_t ws_bytes, cudaStream_t s,
@@ -568,11 +578,18 @@ int grouped_launch(int count, const moa_gemm_desc* d, void* ws, size_t ws_bytes,
             }
         }
     }
-    // problems outside the persistent path, one by one on the same stream
-    uint8_t* side = static_cast<uint8_t*>(ws) + main_bytes;
-    const size_t side_bytes = ws ? ws_bytes - main_bytes : 0;
+    // modular-slice problems: one grouped sequence of launches
+    const size_t crt_bytes = (crt_grouped_workspace(count, d) + 255) / 256 * 256;
+    if (crt_bytes > 0) {
+        const int rc = crt_grouped_launch(count, d, static_cast<uint8_t*>(ws) + main_bytes,
+                                          crt_bytes, s);
+        if (rc != MOA_OK) return rc;
+    }
+    // problems outside the persistent paths, one by one on the same stream
+    uint8_t* side = static_cast<uint8_t*>(ws) + main_bytes + crt_bytes;
+    const size_t side_bytes = ws ? ws_bytes - main_bytes - crt_bytes : 0;
     for (int g = 0; g < count; ++g) {
-        if (persistent_ok(d[g])) continue;
+        if (persistent_ok(d[g]) || crt_grouped_ok(d[g])) continue;
         const int rc = gemm_ex(d[g].m, d[g].n, d[g].p, d[g].dt, d[g].A, d[g].B, d[g].C, 0,
                                side_bytes ? side : nullptr, side_bytes, s, nullptr);
         if (rc != MOA_OK) return rc;

@@ -129,6 +129,13 @@ int transpose_pad_launch(const float* X, int64_t rows, int64_t cols, float* Xt, 
 int pad_copy_launch(const void* src, void* dst, int64_t rows, int64_t cols, int64_t ld,
                     int esize, cudaStream_t s);
 
+// Pinned host staging for per-call device tables (a small ring per host
+// thread): get() returns a buffer of at least n bytes whose previous copy has
+// finished; release() records, on the stream of the copy that reads it, when
+// it may be reused.
+void* staging_get(size_t n, int* slot);
+void staging_release(int slot, cudaStream_t s);
+
 inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 inline int64_t ceil_div(int64_t x, int64_t a) { return (x + a - 1) / a; }
 

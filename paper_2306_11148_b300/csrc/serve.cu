@@ -42,6 +42,7 @@
 #include <thread>
 #include <vector>
 
+#include "crt.h"
 #include "internal.h"
 #include "ptx.cuh"
 
@@ -160,6 +161,10 @@ struct moa_server {
 
 namespace moa {
 namespace {
+
+// Largest modular-slice request (algorithmic flops) that joins a batch's
+// grouped call: about 2 GFLOP, a few tens of microseconds of tensor work.
+constexpr double kServeGroupFlops = 2.0e9;
 
 moa_completion completion_of(const Request& r, int status, double t_done) {
     moa_completion c{};
@@ -295,13 +300,20 @@ void scheduler(moa_server* s) {
         ++s->n_batches;
         s->n_admitted += batch.size();
 
-        // BF16 requests of the batch share one grouped persistent launch; its
-        // tables get their own arena block, released with the lead request
-        // (all of them finish with the same kernel).
+        // BF16 and modular-slice requests of the batch share one grouped call
+        // (one persistent launch per kind); its workspace gets its own arena
+        // block, released with the lead request (all of them finish with the
+        // same kernels).
+        // Only small modular-slice requests join the group: a request grouped
+        // with a large one would complete only when the large one does.
+        auto groupable = [](const moa_gemm_desc& d) {
+            return d.dt == MOA_BF16 ||
+                   (crt_grouped_ok(d) && 2.0 * d.m * d.n * d.p <= kServeGroupFlops);
+        };
         std::vector<moa_gemm_desc> bf;
         std::vector<size_t> bf_idx;
         for (size_t i = 0; i < batch.size(); ++i)
-            if (batch[i].d.dt == MOA_BF16) {
+            if (groupable(batch[i].d)) {
                 bf.push_back(batch[i].d);
                 bf_idx.push_back(i);
             }
@@ -316,7 +328,7 @@ void scheduler(moa_server* s) {
         }
         const bool grouped = toff != SIZE_MAX;
         const int gstream = grouped ? take_stream(s) : 0;
-        for (Request& r : batch) r.stream = (grouped && r.d.dt == MOA_BF16) ? gstream : take_stream(s);
+        for (Request& r : batch) r.stream = (grouped && groupable(r.d)) ? gstream : take_stream(s);
         for (const Request& r : batch) s->inflight[r.ticket] = r;
         s->inflight_peak = std::max<int>(s->inflight_peak, static_cast<int>(s->inflight.size()));
         lk.unlock();
@@ -340,7 +352,7 @@ void scheduler(moa_server* s) {
         std::vector<uint64_t> failed_now;
         for (size_t i = 0; i < batch.size(); ++i) {
             Request& r = batch[i];
-            if (!(grouped && r.d.dt == MOA_BF16)) {
+            if (!(grouped && groupable(r.d))) {
                 cudaStream_t rs = s->streams[r.stream];
                 set_status_override(s->dev_status + r.hidx);
                 rcs[i] = gemm_ex(r.d.m, r.d.n, r.d.p, r.d.dt, r.d.A, r.d.B, r.d.C, 0,
