@@ -317,7 +317,7 @@ MODE_OF = {"split_f64": "f64_split_f32in", "square": "tf32", "bf16": "bf16",
            "split_f64_e4m3": "f64_split_f32in_e4m3", "crt_f64": "f64_crt_f32in",
            "f64": "f64", "simt": "f32_simt",
            "grouped": "grouped", "serve": "serve", "energy_n": "energy_n",
-           "tiles": "tiles", "peaks": "peaks"}
+           "tiles": "tiles", "peaks": "peaks", "products": "products"}
 
 
 SPLIT_F32IN = ("f32_split", "f64_split_f32in", "f64_split_f32in_e4m3", "f64_crt_f32in")
@@ -678,6 +678,42 @@ def bench_grouped(steps, warmup, ws, stream, count=512, compare=True):
             "separate_seconds_per_step": t_sep / nsep,
             "graph_seconds_per_step": t_graph / nsep, "kernels_per_step": 1,
             "products": 1, "tile": [128, 0, 64]}
+
+
+def bench_products(stream, steps=10, warmup=3):
+    """The no-reduction members of the outer-product family through the one
+    kernel (moa_product), FP32: the Kronecker product of 64 x 64 and 128 x 128
+    operands (an 8192 x 8192 output) and the Hadamard product of two
+    8192 x 8192 arrays.  HBM-bound: bytes = output written + operands read once;
+    GB/s against the measured copy bandwidth."""
+    import torch
+    from paper_2306_11148_b300 import inputs, moa
+    out = {}
+    cases = [("kronecker", moa.MOA_PRODUCT_KRONECKER, (64, 64), (128, 128)),
+             ("hadamard", moa.MOA_PRODUCT_HADAMARD, (8192, 8192), (8192, 8192))]
+    for name, kind, sa, sb in cases:
+        A, _ = inputs.uniform_pair(sa[0], sa[1], 1, dtype=torch.float32, seed=1)
+        B, _ = inputs.uniform_pair(sb[0], sb[1], 1, dtype=torch.float32, seed=2)
+        Ad, Bd = A.cuda(), B.cuda()
+        C = moa.product(kind, Ad, Bd, moa.MOA_F32_SIMT, stream=stream)
+        L = moa.lib()
+        m, n = sa
+        p, q = sb
+        sh = int(stream.cuda_stream)
+
+        def step():
+            moa.check(L.moa_product(kind, m, n, p, q, moa.MOA_F32_SIMT, Ad.data_ptr(),
+                                    Bd.data_ptr(), C.data_ptr(), sh))
+
+        with torch.cuda.stream(stream):
+            t = time_device(step, steps, warmup, stream, 1)
+        moa.check(moa.moa_sync_status(sh))
+        nbytes = 4 * (C.numel() + Ad.numel() + Bd.numel())
+        out[name] = {"A": list(sa), "B": list(sb), "C": list(C.shape), "ms": t / steps * 1e3,
+                     "bytes_per_launch": nbytes, "gbs": nbytes * steps / t / 1e9,
+                     "kernel": "ipophp_kernel<float, float>"}
+        del Ad, Bd, C
+    return out
 
 
 def bench_grouped_crt(stream, count=64, div=1, steps=5, warmup=3, seed=3):
@@ -1245,10 +1281,17 @@ def main():
     mode = MODE_OF[args.workload]
     N = args.n
 
-    if mode in ("energy_n", "tiles", "peaks"):
+    if mode in ("energy_n", "tiles", "peaks", "products"):
         clocks = ClockSampler(pci)
         clocks.start()
-        if mode == "peaks":
+        if mode == "products":
+            res = bench_products(stream, steps=args.steps, warmup=args.warmup)
+            for v in res.values():
+                v["frac_of_hbm"] = v["gbs"] / peaks["hbm_gbs"]
+            metric = "GB/s of the outer-product family's no-reduction members (one kernel)"
+            value = res["kronecker"]["gbs"]
+            unit = "GB/s (Kronecker product, FP32, 8192 x 8192 output)"
+        elif mode == "peaks":
             res = bench_library_rates(args.n)
             metric = "dense GEMM TFLOP/s per dtype: vendor library vs this library"
             value = res["moa_tf32"]
@@ -1404,6 +1447,14 @@ def main():
             except Exception as e:  # report, do not hide
                 modes[m2] = {"error": str(e)}
 
+        # the outer-product family's no-reduction members (HBM roofline)
+        try:
+            pr = bench_products(stream)
+            for v in pr.values():
+                v["frac_of_hbm"] = v["gbs"] / peaks["hbm_gbs"]
+            modes["products"] = pr
+        except Exception as e:  # report, do not hide
+            modes["products"] = {"error": str(e)}
         # grouped modular-slice batches against separate launches
         for div in (1, 4):
             try:

@@ -163,19 +163,47 @@ int moa_gemm_grouped(int count, const moa_gemm_desc* descs,
                      void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------------------------------------------------------------- */
-/* The other products of the inner/outer-product family (paper's Appendix) */
+/* The inner/outer-product family as one algorithm (paper's Appendix)       */
 /* ---------------------------------------------------------------------- */
+
+/* With the outer product T[i,j,k,l] = A[i,j] * B[k,l] (A is m x n, B is
+ * p x q, row-major), the Hadamard, Kronecker and matrix products are one
+ * index map over the output C (R x Q, row-major):
+ *     C[r, c] = sum_{s < S} A[r / ra, c / ca + s] * B[r % rb + s, c % cb]
+ *   MOA_PRODUCT_HADAMARD   C[i,j] = T[i,j,i,j]       m = p, n = q; R x Q = m x n, S = 1
+ *   MOA_PRODUCT_KRONECKER  C[(i*p)+k, (j*q)+l] = T[i,j,k,l]; R x Q = mp x nq, S = 1
+ *   MOA_PRODUCT_MATMUL     C[i,l] = sum_j T[i,j,j,l]  n = p; R x Q = m x q, S = n */
+typedef enum {
+    MOA_PRODUCT_HADAMARD = 0,
+    MOA_PRODUCT_KRONECKER = 1,
+    MOA_PRODUCT_MATMUL = 2
+} moa_product_kind;
+
+/* C := the product `kind` of A and B by the single outer-product kernel:
+ * each output element is its sum of S products, each product rounded and the
+ * sums added in s order (no fused multiply-add), so MOA_PRODUCT_MATMUL in
+ * FP64 follows the oracle's i-k-j order element for element.  dt: MOA_F64
+ * (FP64 in/out), MOA_F32_TF32 or MOA_F32_SIMT (FP32 in/out, FP32
+ * arithmetic), MOA_BF16 (BF16 in, FP32 out).  The matrix product here is the
+ * algebra's reference form on CUDA cores; moa_gemm_ex is its tensor-core
+ * specialisation.  Asynchronous on `stream`; MOA_ERR_ARG for mismatched
+ * shapes, MOA_ERR_DTYPE for other modes. */
+int moa_product(moa_product_kind kind, int64_t m, int64_t n, int64_t p, int64_t q, moa_dtype dt,
+                const void* A, const void* B, void* C, void* stream);
+
 
 /* Kronecker product C := A (x) B: A is m x n, B is p x q, C is (m*p) x (n*q),
  * all row-major, C[(i*p)+k, (j*q)+l] = A[i,j] * B[k,l] (one rounding per
- * element).  dt: MOA_F64 (FP64 in/out), MOA_F32_TF32 or MOA_F32_SIMT (FP32
- * in/out, plain FP32 products), MOA_BF16 (BF16 in, FP32 out, exact).
- * Asynchronous on `stream`.  MOA_ERR_DTYPE for other modes. */
+ * element); moa_product(MOA_PRODUCT_KRONECKER, ...).  dt: MOA_F64 (FP64
+ * in/out), MOA_F32_TF32 or MOA_F32_SIMT (FP32 in/out, plain FP32 products),
+ * MOA_BF16 (BF16 in, FP32 out, exact).  Asynchronous on `stream`.
+ * MOA_ERR_DTYPE for other modes. */
 int moa_kronecker(int64_t m, int64_t n, int64_t p, int64_t q, moa_dtype dt, const void* A,
                   const void* B, void* C, void* stream);
 
-/* Hadamard product C := A o B of two m x n arrays: C[i,j] = A[i,j] * B[i,j];
- * dtypes as for moa_kronecker.  Asynchronous on `stream`. */
+/* Hadamard product C := A o B of two m x n arrays: C[i,j] = A[i,j] * B[i,j]
+ * (moa_product(MOA_PRODUCT_HADAMARD, m, n, m, n, ...)); dtypes as for
+ * moa_kronecker.  Asynchronous on `stream`. */
 int moa_hadamard(int64_t m, int64_t n, moa_dtype dt, const void* A, const void* B, void* C,
                  void* stream);
 

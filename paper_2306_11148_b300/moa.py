@@ -64,6 +64,12 @@ DEFAULT_SLICES = {MOA_F32_SPLIT: 3, MOA_F64_SPLIT_F32IN: 7, MOA_F64_SPLIT_F64IN:
                   MOA_F64_SPLIT_F32IN_E4M3: 10, MOA_F64_SPLIT_F64IN_E4M3: 10}
 
 
+# moa_product_kind
+MOA_PRODUCT_HADAMARD = 0
+MOA_PRODUCT_KRONECKER = 1
+MOA_PRODUCT_MATMUL = 2
+
+
 class moa_stats(ctypes.Structure):
     _fields_ = [("block_m", ctypes.c_int32), ("block_n", ctypes.c_int32),
                 ("block_k", ctypes.c_int32), ("slices", ctypes.c_int32),
@@ -145,6 +151,8 @@ EXPORTS = {
     "moa_set_block_n": (ctypes.c_int, [ctypes.c_int]),
     "moa_kronecker": (ctypes.c_int, [_i64, _i64, _i64, _i64, ctypes.c_int, _vp, _vp, _vp, _vp]),
     "moa_hadamard": (ctypes.c_int, [_i64, _i64, ctypes.c_int, _vp, _vp, _vp, _vp]),
+    "moa_product": (ctypes.c_int, [ctypes.c_int, _i64, _i64, _i64, _i64, ctypes.c_int, _vp, _vp,
+                                   _vp, _vp]),
     "moa_gemm_batched_workspace_size": (_sz, [ctypes.c_int, _i64, _i64, _i64, ctypes.c_int, _i64,
                                               _i64, _i64]),
     "moa_gemm_batched": (ctypes.c_int, [ctypes.c_int, _i64, _i64, _i64, ctypes.c_int, _vp, _i64,
@@ -422,6 +430,23 @@ def kronecker(A, B, dt: int, stream=None):
     p, q = B.shape
     C = torch.empty((m * p, n * q), dtype=out_dtype(dt), device=A.device)
     check(lib().moa_kronecker(m, n, p, q, dt, _ptr(A), _ptr(B), _ptr(C), _stream_handle(stream)))
+    return C
+
+
+def product(kind: int, A, B, dt: int, stream=None):
+    """C := the product `kind` (MOA_PRODUCT_HADAMARD / _KRONECKER / _MATMUL) of
+    A and B through moa_product, the single outer-product kernel."""
+    import torch
+    for t, name in ((A, "A"), (B, "B")):
+        if t.dtype != in_dtype(dt) or t.dim() != 2 or not t.is_contiguous() or t.device.type != "cuda":
+            raise TypeError(f"{name} must be a contiguous 2-D CUDA {in_dtype(dt)} tensor")
+    m, n = A.shape
+    p, q = B.shape
+    shape = {MOA_PRODUCT_HADAMARD: (m, n), MOA_PRODUCT_KRONECKER: (m * p, n * q),
+             MOA_PRODUCT_MATMUL: (m, q)}[kind]
+    C = torch.empty(shape, dtype=out_dtype(dt), device=A.device)
+    check(lib().moa_product(kind, m, n, p, q, dt, _ptr(A), _ptr(B), _ptr(C),
+                            _stream_handle(stream)))
     return C
 
 
