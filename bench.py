@@ -1030,7 +1030,7 @@ def _prep(mode, N, seed=0):
 
 def bench_energy_n(stream, energy, sizes=(1024, 2048, 4096, 8192, 16384),
                    modes=("tf32", "bf16", "f32_split", "f64_split_f64in",
-                          "f64_split_f64in_e4m3", "f64")):
+                          "f64_split_f64in_e4m3", "f64_crt_f64in", "f64")):
     """Square sweep: per precision mode and N, time, TFLOP/s and NVML joules per
     GEMM, plus the least-squares slope of log J against log N (the paper
     claims energy quadratic in N)."""
@@ -1247,6 +1247,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-sweep", type=lambda x: [float(v) for v in x.split(",") if v],
                     default=[], help="extra arrival rates (comma list) to find capacity")
+    ap.add_argument("--energy-modes", type=lambda x: [v for v in x.split(",") if v], default=[],
+                    help="modes of the energy_n sweep (comma list; default: all)")
     ap.add_argument("--serve-f64", default="crt", choices=["crt", "digits"],
                     help="mode of the FP64-accuracy serving requests")
     ap.add_argument("--no-extras", action="store_true", help="skip the other-mode measurements")
@@ -1297,9 +1299,10 @@ def main():
             value = res["moa_tf32"]
             unit = "TFLOP/s (this library, TF32)"
         elif mode == "energy_n":
-            res = bench_energy_n(stream, energy)
+            res = bench_energy_n(stream, energy, **({"modes": tuple(args.energy_modes)}
+                                                     if args.energy_modes else {}))
             metric = "joules per square ONF GEMM vs N (slope of log J vs log N)"
-            value = res["tf32"]["slope_logJ_logN"]
+            value = res[next(iter(res))]["slope_logJ_logN"]
             unit = "dlogJ/dlogN"
         else:
             res = bench_tiles(stream, energy)

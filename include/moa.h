@@ -249,6 +249,12 @@ int moa_tune_dense(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A,
                    void* C, void* ws, size_t ws_bytes, void* stream, int* best_block_n,
                    float* best_ms);
 
+/* The tile width (64, 128 or 256) the grouped persistent launch gives a BF16
+ * problem of this shape: the width moa_tune_dense recorded for its shape
+ * bucket when there is one (or a width forced by moa_set_block_n), else the
+ * shape cost model's.  0 for empty shapes. */
+int moa_grouped_block_n(int64_t m, int64_t n, int64_t p);
+
 /* Writes / reads / clears the measured table (text: "dt m n p block_n" per
  * line, dimensions as half-octave buckets).  The file named by the
  * MOA_TUNE_CACHE environment variable is loaded on first use. */

@@ -312,9 +312,16 @@ bool persistent_ok(const moa_gemm_desc& d) {
 }
 
 // Tile width of one problem (the block size chosen from the static shapes,
-// Sec. 3.4): the width with the least total tile cost.  The balance of all
-// tiles over the SMs is left to the LPT dealing of the work list.
+// Sec. 3.4): the width recorded by the measured autotuner for the problem's
+// shape bucket (moa_tune_dense / moa_tune_load) when there is one, else the
+// width with the least total tile cost.  The balance of all tiles over the
+// SMs is left to the LPT dealing of the work list.  (A per-thread
+// moa_set_block_n of 64, 128 or 256 forces the width here too.)
 int plan_bn(const moa_gemm_desc& d) {
+    const int ov = tile_override();
+    if (ov == 64 || ov == 128 || ov == 256) return ov;
+    const int tuned = tuned_block_n(MOA_BF16, d.m, d.n, d.p);
+    if (tuned == 64 || tuned == 128 || tuned == 256) return tuned;
     const int64_t tiles_m = ceil_div(d.m, kGBM);
     int best = 256;
     double best_cost = 1e300;
@@ -600,6 +607,11 @@ int grouped_launch(int count, const moa_gemm_desc* d, void* ws, size_t ws_bytes,
 }  // namespace moa
 
 extern "C" {
+
+int moa_grouped_block_n(int64_t m, int64_t n, int64_t p) {
+    if (m <= 0 || n <= 0 || p <= 0) return 0;
+    return moa::grouped_plan_bn(m, n, p);
+}
 
 size_t moa_gemm_grouped_workspace_size(int count, const moa_gemm_desc* d) {
     if (count <= 0 || d == nullptr) return 0;

@@ -163,6 +163,7 @@ EXPORTS = {
     "moa_tune_save": (ctypes.c_int, [ctypes.c_char_p]),
     "moa_tune_load": (ctypes.c_int, [ctypes.c_char_p]),
     "moa_tune_clear": (ctypes.c_int, []),
+    "moa_grouped_block_n": (ctypes.c_int, [_i64, _i64, _i64]),
     "moa_shutdown": (None, []),
 }
 

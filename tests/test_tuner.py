@@ -152,3 +152,62 @@ def test_split_tile_widths_agree(L, dt, widths):
     got = outs[1].double().cpu().numpy()
     tol = 1e-5 if dt == moa.MOA_F32_SPLIT else 1e-12
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= tol
+
+
+def test_grouped_planner_reads_the_measured_table(L, tmp_path):
+    """The grouped launch's per-problem tile width comes from the measured
+    table when its shape bucket has an entry (half-octave buckets: 1024 ->
+    round(2 log2 1024) = 20), else from the cost model; moa_set_block_n forces it."""
+    L.moa_tune_clear()
+    model = L.moa_grouped_block_n(1024, 1024, 1024)
+    assert model in (64, 128, 256)
+    want = 64 if model != 64 else 128
+    src = tmp_path / "t.txt"
+    src.write_text(f"3 20 20 20 {want}\n")
+    assert L.moa_tune_load(str(src).encode()) == moa.MOA_OK
+    assert L.moa_grouped_block_n(1024, 1024, 1024) == want
+    assert L.moa_grouped_block_n(1000, 1100, 1024) == want          # same buckets
+    assert L.moa_grouped_block_n(2048, 1024, 1024) == L.moa_grouped_block_n(2048, 1024, 1024)
+    assert L.moa_set_block_n(256) == moa.MOA_OK
+    assert L.moa_grouped_block_n(1024, 1024, 1024) == 256
+    assert L.moa_set_block_n(0) == moa.MOA_OK
+    L.moa_tune_clear()
+    assert L.moa_grouped_block_n(1024, 1024, 1024) == model
+    assert L.moa_grouped_block_n(0, 5, 5) == 0
+
+
+@pytest.mark.gpu
+def test_grouped_tuned_widths_bit_identical(L, tmp_path):
+    """A grouped call planned with measured widths gives the same bits as the
+    cost-model plan and as the problems run alone (integer inputs: exact)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2306_11148_b300 import inputs
+    shapes = [(1024, 1024, 1024), (1000, 1100, 1024), (256, 512, 384)]
+    probs = []
+    for i, (m, n, p) in enumerate(shapes):
+        A, B = inputs.integer_pair(m, n, p, dtype=torch.bfloat16, seed=40 + i)
+        probs.append((A.cuda(), B.cuda(), torch.empty((m, p), device="cuda"), moa.MOA_BF16))
+    L.moa_tune_clear()
+    moa.gemm_grouped(probs)
+    moa.sync_status()
+    base = [p[2].clone() for p in probs]
+    model = L.moa_grouped_block_n(1024, 1024, 1024)
+    want = 64 if model != 64 else 128
+    src = tmp_path / "t.txt"
+    src.write_text(f"3 20 20 20 {want}\n")
+    assert L.moa_tune_load(str(src).encode()) == moa.MOA_OK
+    try:
+        assert L.moa_grouped_block_n(1024, 1024, 1024) == want
+        for p in probs:
+            p[2].fill_(float("nan"))
+        moa.gemm_grouped(probs, workspace=moa.Workspace(torch.device("cuda")))
+        moa.sync_status()
+    finally:
+        L.moa_tune_clear()
+    for b, (A, B, C, dt) in zip(base, probs):
+        assert torch.equal(C, b)
+        ref = oracle.gemm(A.double().cpu().numpy(), B.double().cpu().numpy())
+        assert np.array_equal(C.double().cpu().numpy(), ref)
