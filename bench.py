@@ -315,6 +315,7 @@ def aggregate(flops_per_step, steps, seconds, ws):
 MODE_OF = {"split_f64": "f64_split_f32in", "square": "tf32", "bf16": "bf16",
            "split_f32": "f32_split",
            "split_f64_e4m3": "f64_split_f32in_e4m3", "crt_f64": "f64_crt_f32in",
+           "crt_f64in": "f64_crt_f64in",
            "f64": "f64", "simt": "f32_simt",
            "grouped": "grouped", "serve": "serve", "energy_n": "energy_n",
            "tiles": "tiles", "peaks": "peaks", "products": "products"}
@@ -1195,7 +1196,8 @@ def square_metric_config(mode, N, ws):
     metric = METRIC_OF.get(mode, f"GEMM TFLOP/s (ONF GEMM, {mode} path)")
     # bytes of A and B and of C per element, against the 126 MB L2
     in_b, out_b = {"bf16": (2, 4), "f64": (8, 8), "f64_split_f32in": (4, 8),
-                   "f64_split_f32in_e4m3": (4, 8), "f64_crt_f32in": (4, 8)}.get(mode, (4, 4))
+                   "f64_split_f32in_e4m3": (4, 8), "f64_crt_f32in": (4, 8),
+                   "f64_crt_f64in": (8, 8)}.get(mode, (4, 4))
     mb = N * N * (2 * in_b + out_b) / 1e6
     l2 = (f"inputs larger than L2 (A, B, C: {mb:.0f} MB)" if mb > L2_MB else
           f"A, B, C fit in L2 ({mb:.1f} MB): not flushed between steps (warm-cache figure)")
@@ -1390,6 +1392,7 @@ def main():
     # launching stream.
     kdtype = {"tf32": "tf32", "bf16": "bf16", "f32_split": "bf16",
               "f64_split_f32in": "bf16", "f64_split_f32in_e4m3": "fp8", "f64_crt_f32in": "bf16",
+              "f64_crt_f64in": "bf16",
               "grouped": "bf16"}.get(mode)
     kernel_ms = main_res["kernel_seconds"] / args.steps * 1e3
     if mode == "grouped":
@@ -1429,7 +1432,8 @@ def main():
                                    " flop" if main_res["products"] > 1 else "2N^3 flop",
                 "peak_source": f"{peaks['source']} bf16 burst x nominal {kdtype}/bf16 ratio",
                 "kernel": {"tf32": "dense_tc_kernel", "bf16": "dense_tc_kernel",
-                           "f64_crt_f32in": "crt_gemm_kernel"}.get(mode, "split_gemm_kernel")}
+                           "f64_crt_f32in": "crt_gemm_kernel",
+                           "f64_crt_f64in": "crt_gemm_kernel"}.get(mode, "split_gemm_kernel")}
         if kernel_ms >= 10.0:
             roof.update({"peak_sustained": peak_s, "frac_sustained": achieved / peak_s})
     else:
@@ -1514,6 +1518,7 @@ def main():
                       "f64_split_f32in": "f64 via bf16 integer digits (exact int accumulation)",
                       "f64_split_f32in_e4m3": "f64 via e4m3 integer digits",
                       "f64_crt_f32in": "f64 via bf16 modular slices (exact integer CRT)",
+                      "f64_crt_f64in": "f64 via bf16 modular slices (exact integer CRT)",
                       "f64": "f64",
                       "f32_simt": "f32", "grouped": "bf16"}[mode],
             "data": "synthetic",
