@@ -38,6 +38,7 @@
 #include <vector>
 
 #include "crt.h"
+#include "fastdiv.cuh"
 #include "fpbits.cuh"
 #include "internal.h"
 #include "ptx.cuh"
@@ -65,8 +66,9 @@ struct CrtConsts {
     int t;                               // operand bits
     uint32_t w[kCrtMaxModuli][8];        // CRT weights W_l = (P / q_l) * ((P / q_l)^-1 mod q_l)
                                          //   mod P, as 16-bit limbs, least significant first
-    float wf[kCrtMaxModuli];             // W_l / P rounded to FP32 (quotient estimate)
     uint64_t P_lo, P_hi;                 // P = prod q_l
+    int sP;                              // quotient estimate: floor(X / 2^sP) * kq ~ X / P,
+    float kq;                            //   sP = bit length of P - 32, kq = 2^sP / P rounded
 };
 
 // ---------------------------------------------------------------- host arithmetic
@@ -106,8 +108,11 @@ CrtConsts crt_consts(int M, int t) {
         const int64_t y = inv_mod(Ml_mod, crt_mod(l));
         const u128 W = (Ml * static_cast<u128>(y)) % P;   // Ml * y < P * 256 < 2^128
         for (int k = 0; k < 8; ++k) c.w[l][k] = static_cast<uint32_t>(W >> (16 * k)) & 0xFFFFu;
-        c.wf[l] = static_cast<float>(as_double(W) / as_double(P));
     }
+    int bits = 0;
+    while (bits < 128 && (P >> bits) != 0) ++bits;
+    c.sP = bits > 32 ? bits - 32 : 0;
+    c.kq = static_cast<float>(std::ldexp(1.0, c.sP) / as_double(P));
     return c;
 }
 
@@ -226,8 +231,10 @@ __device__ __forceinline__ ScaledParts<2> scaled_parts(float x, int k) {
             base = q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u);
         }
     }
-    r.p[0] = small_uint_to_float(base & 0xFFFu);
-    r.p[1] = small_uint_to_float(base >> 12);   // base <= 2^24
+    // the pieces carry the sign, so every residue comes out signed
+    const uint32_t sgn = r.neg ? 0x80000000u : 0u;
+    r.p[0] = __uint_as_float(__float_as_uint(small_uint_to_float(base & 0xFFFu)) ^ sgn);
+    r.p[1] = __uint_as_float(__float_as_uint(small_uint_to_float(base >> 12)) ^ sgn);   // base <= 2^24
     return r;
 }
 __device__ __forceinline__ ScaledParts<6> scaled_parts(double x, int k) {
@@ -236,33 +243,39 @@ __device__ __forceinline__ ScaledParts<6> scaled_parts(double x, int k) {
     r.neg = D < 0;
     r.s = 0;
     const uint64_t v = static_cast<uint64_t>(r.neg ? -D : D);
+    const uint32_t sgn = r.neg ? 0x80000000u : 0u;
 #pragma unroll
     for (int i = 0; i < 6; ++i)
-        r.p[i] = small_uint_to_float(static_cast<uint32_t>((v >> (12 * i)) & 0xFFFu));
+        r.p[i] = __uint_as_float(
+            __float_as_uint(small_uint_to_float(static_cast<uint32_t>((v >> (12 * i)) & 0xFFFu))) ^ sgn);
     return r;
 }
 
 // Symmetric residue (|r| <= q/2, an integer-valued float with the element's
 // sign applied) of one element modulo q = crt_mod(L); tab: the block's shared
 // table row of 2^s mod q.
+// tab: the block's shared table row of modulus L, tab[s] = (2^s mod q,
+// 2^(s+12) mod q) for s < 64.  The pieces carry the element's sign.
 template <int L, int NP>
-__device__ __forceinline__ float residue_of(const ScaledParts<NP>& e, const float* tab) {
+__device__ __forceinline__ float residue_of(const ScaledParts<NP>& e, const float2* tab) {
     constexpr float q = static_cast<float>(crt_mod(L));
     constexpr float qinv = 1.0f / static_cast<float>(crt_mod(L));
-    float r;
     if constexpr (NP == 2) {
         // two pieces below 2^12 times 2^s mod q (< 2^8): the sum is below 2^21,
         // one reduction gives the symmetric residue
-        r = mod_reduce(__fmaf_rn(e.p[1], tab[e.s + 12], __fmul_rn(e.p[0], tab[e.s])), q, qinv);
+        const float2 c = tab[e.s];
+        return mod_reduce(__fmaf_rn(e.p[1], c.y, __fmul_rn(e.p[0], c.x)), q, qinv);
     } else {
-        // six pieces: the sum is below 2^23, reduced within 0.51 q + 1, then
-        // reduced once more to the symmetric residue
-        float t = __fmul_rn(e.p[0], tab[0]);
-#pragma unroll
-        for (int i = 1; i < NP; ++i) t = __fmaf_rn(e.p[i], tab[12 * i], t);
-        r = mod_reduce(mod_reduce(t, q, qinv), q, qinv);
+        // six pieces at 2^0, 2^12, ..., 2^60: the sum is below 2^23, reduced
+        // within 0.51 q + 1, then reduced once more to the symmetric residue
+        float t = __fmul_rn(e.p[0], tab[0].x);
+        t = __fmaf_rn(e.p[1], tab[0].y, t);
+        t = __fmaf_rn(e.p[2], tab[24].x, t);
+        t = __fmaf_rn(e.p[3], tab[24].y, t);
+        t = __fmaf_rn(e.p[4], tab[48].x, t);
+        t = __fmaf_rn(e.p[5], tab[48].y, t);
+        return mod_reduce(mod_reduce(t, q, qinv), q, qinv);
     }
-    return e.neg ? -r : r;
 }
 
 // BF16 patterns of two integer-valued floats of magnitude <= 256 (exact in
@@ -299,11 +312,11 @@ __device__ __forceinline__ void load4(const T* __restrict__ X, int64_t r, int64_
 // (one 8-byte store per plane).
 template <int L, int NP>
 __device__ __forceinline__ void store_planes(const ScaledParts<NP> (&v)[4], int M,
-                                             const float* tab, __nv_bfloat16* __restrict__ out,
+                                             const float2* tab, __nv_bfloat16* __restrict__ out,
                                              int64_t plane, int64_t o) {
     if constexpr (L < kCrtMaxModuli) {
         if (L >= M) return;
-        const float* row = tab + L * kPow2Cols;
+        const float2* row = tab + L * 64;
         const uint32_t w0 = bf16x2_of_ints(residue_of<L, NP>(v[0], row), residue_of<L, NP>(v[1], row));
         const uint32_t w1 = bf16x2_of_ints(residue_of<L, NP>(v[2], row), residue_of<L, NP>(v[3], row));
         *reinterpret_cast<uint2*>(out + L * plane + o) = make_uint2(w0, w1);
@@ -319,13 +332,25 @@ __device__ __forceinline__ void store_planes(const ScaledParts<NP> (&v)[4], int 
 template <typename T, int AXIS>
 __device__ void crt_residue_part(const T* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
                                  int* __restrict__ e, const typename Bits<T>::U* __restrict__ cmax,
-                                 int* status, int t, int M, int vec, const float* tab,
+                                 int* status, int t, int M, int vec, const float2* tab,
                                  __nv_bfloat16* __restrict__ out, int64_t plane, int64_t bid,
                                  int64_t nblk) {
     const int64_t gpr = ld / 4;
     const int64_t total = rows * gpr;
-    for (int64_t g = bid * blockDim.x + threadIdx.x; g < total; g += nblk * blockDim.x) {
-        const int64_t r = g / gpr, c0 = (g - r * gpr) * 4;
+    const int64_t step = nblk * blockDim.x;
+    const bool small = total + step < (int64_t(1) << 31);
+    const FastDiv fd{static_cast<uint32_t>(gpr),
+                     gpr <= 1 ? 0xFFFFFFFFu : static_cast<uint32_t>((uint64_t(1) << 32) / gpr)};
+    for (int64_t g = bid * blockDim.x + threadIdx.x; g < total; g += step) {
+        int64_t r, c0;
+        if (small) {
+            uint32_t rem;
+            r = fdiv(static_cast<uint32_t>(g), fd, rem);
+            c0 = static_cast<int64_t>(rem) * 4;
+        } else {
+            r = g / gpr;
+            c0 = (g - r * gpr) * 4;
+        }
         T x[4];
         load4(X, r, cols, c0, vec != 0, x);
         ScaledParts<sizeof(T) == 8 ? 6 : 2> v[4];
@@ -357,11 +382,12 @@ __global__ void __launch_bounds__(256)
                        int* status, int t, int M, __nv_bfloat16* __restrict__ a_out,
                        int64_t a_plane, __nv_bfloat16* __restrict__ b_out, int64_t b_plane,
                        int ga, const CrtPow2 pow2) {
-    // tab[l * 128 + s] = 2^s mod q_l (a row per modulus: threads of a warp that
-    // read different s of one row hit different banks)
-    __shared__ float tab[kCrtMaxModuli * kPow2Cols];
-    for (int i = threadIdx.x; i < kCrtMaxModuli * kPow2Cols; i += blockDim.x)
-        tab[i] = static_cast<float>(pow2.v[i / kPow2Cols][i % kPow2Cols]);
+    // tab[l * 64 + s] = (2^s mod q_l, 2^(s+12) mod q_l): a row per modulus, so
+    // threads of a warp that read different s of one row mostly hit different banks
+    __shared__ float2 tab[kCrtMaxModuli * 64];
+    for (int i = threadIdx.x; i < kCrtMaxModuli * 64; i += blockDim.x)
+        tab[i] = make_float2(static_cast<float>(pow2.v[i / 64][i % 64]),
+                             static_cast<float>(pow2.v[i / 64][i % 64 + 12]));
     __syncthreads();
     if (static_cast<int>(blockIdx.x) < ga)
         crt_residue_part<T, 0>(A, m, n, lda, const_cast<int*>(eA), nullptr, status, t, M, va, tab,
@@ -764,11 +790,10 @@ __device__ __forceinline__ double u128_to_double_scaled(uint64_t hi, uint64_t lo
 // Residues of modulus L for 4 consecutive outputs (w: their bytes, summed
 // over the K slices and reduced when there are several), then X += r W_L as
 // NL 16-bit limbs in 32-bit sums (r < 2^8: each product is below 2^24, a sum
-// of 16 below 2^28) and the quotient estimate qs += r W_L / P.
+// of 16 below 2^28).
 template <int L, int NL>
 __device__ __forceinline__ void crt_accumulate(const uint32_t (&w)[kCrtMaxModuli], int M,
-                                               const CrtConsts& k, uint32_t (&acc)[4][NL],
-                                               float (&qs)[4]) {
+                                               const CrtConsts& k, uint32_t (&acc)[4][NL]) {
     if constexpr (L < kCrtMaxModuli) {
         if (L >= M) return;
 #pragma unroll
@@ -776,9 +801,8 @@ __device__ __forceinline__ void crt_accumulate(const uint32_t (&w)[kCrtMaxModuli
             const uint32_t r = (w[L] >> (8 * e)) & 0xFFu;
 #pragma unroll
             for (int j = 0; j < NL; ++j) acc[e][j] += r * k.w[L][j];
-            qs[e] = __fmaf_rn(small_uint_to_float(r), k.wf[L], qs[e]);
         }
-        crt_accumulate<L + 1, NL>(w, M, k, acc, qs);
+        crt_accumulate<L + 1, NL>(w, M, k, acc);
     }
 }
 
@@ -808,12 +832,16 @@ __device__ __forceinline__ void crt_load(const uint8_t* __restrict__ R, int64_t 
 }
 
 // C[i, j] for 4 consecutive j per thread: r_l = sum_s R[l, s, i, j] mod q_l;
-// X = sum_l r_l W_l kept modulo 2^128 (NL 16-bit limbs summed in 32 bits);
-// the quotient q = floor(X / P) estimated in FP32 from sum_l r_l W_l / P (off
-// by at most one); C' = X - q P corrected into [0, P), then into
-// [-P/2, P/2), rounded once and scaled by 2^(eA_i + eB_j - 2t).  NL = 7
-// covers P < 2^112 (up to 14 moduli), NL = 8 the rest.  The thread takes
-// the groups of 4 outputs g0, g0 + gstep, ... of the m x ceil(p / 4) groups.
+// X = sum_l r_l W_l (NL 16-bit limbs summed in 32 bits, carried into 16-bit
+// digits; X < 2^12 P and P < 2^126, so X has at most 138 bits: digits 0..7
+// hold X mod 2^128 and the carry out of digit 7 its top bits); the quotient
+// q = floor(X / P) estimated in FP32 from floor(X / 2^sP) (off by at most
+// one); C' = X - q P (exact modulo 2^128, and within (-P, 2P)) corrected into
+// [0, P), then into [-P/2, P/2), rounded once and scaled by
+// 2^(eA_i + eB_j - 2t); the FP64 pattern is assembled with integer
+// operations only.  NL = 7 covers P < 2^112 (up to 14 moduli), NL = 8 the
+// rest.  The thread takes the groups of 4 outputs g0, g0 + gstep, ... of the
+// m x ceil(p / 4) groups.
 template <int NL>
 __device__ __forceinline__ void crt_recon_range(const uint8_t* __restrict__ R, int64_t m, int64_t p,
                                                 int64_t ldr, int ks, int t,
@@ -826,19 +854,30 @@ __device__ __forceinline__ void crt_recon_range(const uint8_t* __restrict__ R, i
     const int64_t plane_stride = m * ldr;
     const u128 P = (static_cast<u128>(k.P_hi) << 64) | k.P_lo;
     const u128 halfP = P >> 1;
+    // 32-bit index arithmetic by reciprocal when the group count allows
+    const bool small = total + gstep < (int64_t(1) << 31);
+    const FastDiv fd{static_cast<uint32_t>(gpr),
+                     gpr <= 1 ? 0xFFFFFFFFu : static_cast<uint32_t>((uint64_t(1) << 32) / gpr)};
     for (int64_t g = g0; g < total; g += gstep) {
-        const int64_t i = g / gpr, j0 = (g - i * gpr) * 4;
+        int64_t i, j0;
+        if (small) {
+            uint32_t rem;
+            i = fdiv(static_cast<uint32_t>(g), fd, rem);
+            j0 = static_cast<int64_t>(rem) * 4;
+        } else {
+            i = g / gpr;
+            j0 = (g - i * gpr) * 4;
+        }
         uint32_t w[kCrtMaxModuli];
         crt_load<0>(R + i * ldr + j0, plane_stride, ks, k.M, w);
         uint32_t acc[4][NL] = {};
-        float qs[4] = {0.f, 0.f, 0.f, 0.f};
-        crt_accumulate<0, NL>(w, k.M, k, acc, qs);
+        crt_accumulate<0, NL>(w, k.M, k, acc);
         const int ea = eA[i] - 2 * t;
-        double out[4];
+        uint64_t out[4];   // FP64 bit patterns
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            // X mod 2^128 from the limb sums (each < 2^28): 16-bit digits with
-            // carries, packed two to a 32-bit word
+            // 16-bit digits with carries, packed two to a 32-bit word; the
+            // final carry holds X's bits from 128 up
             uint32_t d[8];
             uint32_t c = 0;
 #pragma unroll
@@ -851,24 +890,36 @@ __device__ __forceinline__ void crt_recon_range(const uint8_t* __restrict__ R, i
                                   (static_cast<uint64_t>(d[2] | (d[3] << 16)) << 32);
             const uint64_t hi64 = static_cast<uint64_t>(d[4] | (d[5] << 16)) |
                                   (static_cast<uint64_t>(d[6] | (d[7] << 16)) << 32);
+            // floor(X / 2^sP) < 2^44 (sP >= 64 when P >= 2^96; the carry c is X >> 128)
+            uint64_t top;
+            if (k.sP >= 64) {
+                const int sh = k.sP - 64;
+                top = sh == 0 ? hi64 : ((hi64 >> sh) | (static_cast<uint64_t>(c) << (64 - sh)));
+            } else {
+                top = (hi64 << (64 - k.sP)) | (lo64 >> k.sP);   // X < 2^76 here: no carry
+            }
+            const uint32_t qe = static_cast<uint32_t>(__float2int_rd(__fmul_rn(__ull2float_rn(top), k.kq)));
+            // X - qe P modulo 2^128: the true value lies in (-P, 2P), inside the
+            // signed 128-bit range
+            const uint64_t ql = qe * k.P_lo;
+            const uint64_t qh = __umul64hi(static_cast<uint64_t>(qe), k.P_lo) + qe * k.P_hi;
             const u128 x = (static_cast<u128>(hi64) << 64) | lo64;
-            const uint32_t qe = static_cast<uint32_t>(__float2int_rd(qs[e]));
-            // the true remainder lies in [-P, 2P), inside the signed 128-bit range
-            i128 rr = static_cast<i128>(x - static_cast<u128>(qe) * P);
+            i128 rr = static_cast<i128>(x - ((static_cast<u128>(qh) << 64) | ql));
             if (rr < 0) rr += static_cast<i128>(P);
             if (rr >= static_cast<i128>(P)) rr -= static_cast<i128>(P);
             const bool neg = static_cast<u128>(rr) >= halfP;
             const u128 mag = neg ? P - static_cast<u128>(rr) : static_cast<u128>(rr);
             const int64_t j = j0 + e;
-            const double v = j < p ? u128_to_double_scaled(static_cast<uint64_t>(mag >> 64),
-                                                           static_cast<uint64_t>(mag), ea + eB[j])
-                                   : 0.0;
-            out[e] = neg ? -v : v;
+            const uint64_t vb =
+                j < p ? static_cast<uint64_t>(__double_as_longlong(u128_to_double_scaled(
+                            static_cast<uint64_t>(mag >> 64), static_cast<uint64_t>(mag), ea + eB[j])))
+                      : 0ull;
+            out[e] = vb | (neg ? 0x8000000000000000ull : 0ull);
         }
-        double* crow = C + i * p + j0;
+        uint64_t* crow = reinterpret_cast<uint64_t*>(C + i * p + j0);
         if (vec && j0 + 4 <= p) {
-            reinterpret_cast<double2*>(crow)[0] = make_double2(out[0], out[1]);
-            reinterpret_cast<double2*>(crow)[1] = make_double2(out[2], out[3]);
+            reinterpret_cast<ulonglong2*>(crow)[0] = make_ulonglong2(out[0], out[1]);
+            reinterpret_cast<ulonglong2*>(crow)[1] = make_ulonglong2(out[2], out[3]);
         } else {
             for (int e = 0; e < 4 && j0 + e < p; ++e) crow[e] = out[e];
         }
@@ -938,9 +989,12 @@ template <typename T>
 __global__ void __launch_bounds__(256)
     crt_g_residue_kernel(const CrtGPass* __restrict__ pr, int count, int* status,
                          const CrtPow2 pow2) {
-    __shared__ float tab[kCrtMaxModuli * kPow2Cols];
-    for (int i = threadIdx.x; i < kCrtMaxModuli * kPow2Cols; i += blockDim.x)
-        tab[i] = static_cast<float>(pow2.v[i / kPow2Cols][i % kPow2Cols]);
+    // tab[l * 64 + s] = (2^s mod q_l, 2^(s+12) mod q_l): a row per modulus, so
+    // threads of a warp that read different s of one row mostly hit different banks
+    __shared__ float2 tab[kCrtMaxModuli * 64];
+    for (int i = threadIdx.x; i < kCrtMaxModuli * 64; i += blockDim.x)
+        tab[i] = make_float2(static_cast<float>(pow2.v[i / 64][i % 64]),
+                             static_cast<float>(pow2.v[i / 64][i % 64 + 12]));
     __syncthreads();
     const int b = static_cast<int>(blockIdx.x);
     const int g = find_owner(count, b, [&](int i) { return pr[i].res_begin; });

@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "fastdiv.cuh"
 #include "internal.h"
 
 namespace moa {
@@ -167,26 +168,6 @@ __device__ __forceinline__ void load4_at(const TI* __restrict__ row, uint32_t c,
     }
 #pragma unroll
     for (int e = 0; e < 4; ++e) x[e] = widen<TI, TO>(row[c + e]);
-}
-
-// n / d and n % d for n < 2^31 by a precomputed reciprocal: m = floor(2^32 /
-// d) (2^32 - 1 for d = 1) gives floor(n m / 2^32) in {q - 1, q}, and one
-// correction step makes it exact.
-struct FastDiv {
-    uint32_t d, m;
-};
-inline FastDiv make_fastdiv(uint32_t d) {
-    return FastDiv{d, d <= 1 ? 0xFFFFFFFFu : static_cast<uint32_t>((uint64_t(1) << 32) / d)};
-}
-__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f, uint32_t& rem) {
-    uint32_t q = __umulhi(n, f.m);
-    uint32_t r = n - q * f.d;
-    if (r >= f.d) {
-        ++q;
-        r -= f.d;
-    }
-    rem = r;
-    return q;
 }
 
 struct OuterMap {
