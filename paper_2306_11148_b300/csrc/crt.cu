@@ -944,7 +944,7 @@ struct CrtGPass {
     const void* A;
     const void* B;
     double* C;
-    int64_t m, n, p, lda, ldb, ldr, a_plane, b_plane, gx;
+    int64_t m, n, p, lda, ldb, ldr, a_plane, b_plane, gx, chunk;
     __nv_bfloat16* a_pl;
     __nv_bfloat16* b_pl;
     int* eA;
@@ -980,7 +980,7 @@ __global__ void __launch_bounds__(256)
     if (local < x.rblocks)
         crt_row_exp_part(static_cast<const T*>(x.A), x.m, x.n, x.eA, status, local, x.rblocks);
     else if (local < x.rblocks + x.cblocks)
-        crt_col_max_part(static_cast<const T*>(x.B), x.n, x.p, 256, static_cast<U*>(x.cmax),
+        crt_col_max_part(static_cast<const T*>(x.B), x.n, x.p, x.chunk, static_cast<U*>(x.cmax),
                          local - x.rblocks, x.gx);
 }
 
@@ -1029,6 +1029,14 @@ __global__ void __launch_bounds__(256)
     crt_recon_range<8>(x.R, x.m, x.p, x.ldr, 1, x.t, x.eA, x.eB, x.C, x.vec_c, k,
                        static_cast<int64_t>(b - x.rec_begin) * blockDim.x + threadIdx.x,
                        static_cast<int64_t>(x.rec_blocks) * blockDim.x);
+}
+
+// Rows per block of the column-maximum pass: enough blocks to spread over
+// the SMs (about 8 per SM), 16 .. 256 rows each.
+int64_t colmax_chunk(int64_t n, int64_t p, long sms) {
+    const int64_t gx = ceil_div(p, 256);
+    const int64_t want = ceil_div(n * gx, 8 * sms);
+    return std::max<int64_t>(16, std::min<int64_t>(256, want));
 }
 
 int grid_for(int64_t total, int threads) {
@@ -1188,7 +1196,7 @@ int crt_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const
     cudaError_t e = cudaMemsetAsync(cmax, 0, static_cast<size_t>(p) * 8, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(colmax)");
     const int64_t rblocks = std::min<int64_t>(ceil_div(m, 8), 16L * num_sms());
-    const int64_t chunk = 256;
+    const int64_t chunk = colmax_chunk(n, p, num_sms());
     const int64_t gx = ceil_div(p, 256);
     const int64_t cblocks = gx * ceil_div(n, chunk);
     const int ga = grid_for(a_plane / 4, 256);
@@ -1400,7 +1408,8 @@ int crt_grouped_launch(int count, const moa_gemm_desc* d, void* ws, size_t ws_by
         q.vec_c = (dd.p % 2 == 0) && (reinterpret_cast<uintptr_t>(dd.C) % 16 == 0);
         q.f64in = ty;
         q.rblocks = static_cast<int>(std::min<int64_t>(ceil_div(dd.m, 8), 16L * sms));
-        q.cblocks = static_cast<int>(q.gx * ceil_div(dd.n, 256));
+        q.chunk = colmax_chunk(dd.n, dd.p, sms);
+        q.cblocks = static_cast<int>(q.gx * ceil_div(dd.n, q.chunk));
         q.exps_begin = exps_pos[ty];
         exps_pos[ty] += q.rblocks + q.cblocks;
         q.ga = grid_for(q.a_plane / 4, 256);
