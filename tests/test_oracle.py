@@ -510,3 +510,38 @@ def test_oracle_reproduces_golden_records():
     eB, dB = oracle.slice_fixed(r["B"], 1, 7, 4)
     assert np.array_equal(oracle.split_gemm_exact(dA, eA, dB, eB, 7, 4), r["C"])
 
+
+
+def _triangle_by_fractions(dA, eA, dB, eB, beta, S, width):
+    """Exact-rational route of the digit-slice product over the levels
+    s + t <= width (the method keeps width = S - 1), rounded once (Python's
+    float of a Fraction rounds to nearest, ties to even)."""
+    _, m, n = dA.shape
+    p = dB.shape[2]
+    C = np.empty((m, p))
+    for i in range(m):
+        for j in range(p):
+            acc = Fraction(0)
+            for s in range(S):
+                for t in range(S):
+                    if s + t > width:
+                        continue
+                    dot = sum(int(dA[s, i, k]) * int(dB[t, k, j]) for k in range(n))
+                    acc += Fraction(dot) * Fraction(2) ** (-beta * (s + t + 2))
+            C[i, j] = float(acc * Fraction(2) ** (int(eA[i]) + int(eB[j])))
+    return C
+
+
+@pytest.mark.parametrize("beta,S,h", [(7, 4, 1), (5, 5, 1), (8, 3, 0)])
+def test_split_gemm_exact_keeps_exactly_the_triangle(beta, S, h):
+    """Two-sided pin of the level set: the oracle equals the exact-rational sum
+    over s + t <= S - 1 and differs from the sums over one level fewer and one
+    level more (row-scaled inputs, where the dropped levels are visible)."""
+    A, B = inputs.normal_pair(3, 7, 4, dtype=torch.float64, seed=13, scaled="rows")
+    A, B = A.numpy(), B.numpy()
+    eA, dA = oracle.slice_fixed(A, 0, beta, S, headroom=h)
+    eB, dB = oracle.slice_fixed(B, 1, beta, S, headroom=h)
+    C = oracle.split_gemm_exact(dA, eA, dB, eB, beta, S)
+    assert np.array_equal(C, _triangle_by_fractions(dA, eA, dB, eB, beta, S, S - 1))
+    assert not np.array_equal(C, _triangle_by_fractions(dA, eA, dB, eB, beta, S, S - 2))
+    assert not np.array_equal(C, _triangle_by_fractions(dA, eA, dB, eB, beta, S, S))
