@@ -951,6 +951,7 @@ struct CrtGPass {
     int* eB;
     void* cmax;
     const uint8_t* R;
+    int* status;   // where this problem's non-finite inputs are recorded
     int M, t, va, vb, vec_c, f64in;
     int exps_begin, rblocks, cblocks;
     int res_begin, ga, gb;
@@ -971,14 +972,14 @@ __device__ __forceinline__ int find_owner(int count, int b, F begin) {
 // Grouped exponent pass over the problems of one input type.
 template <typename T>
 __global__ void __launch_bounds__(256)
-    crt_g_exps_kernel(const CrtGPass* __restrict__ pr, int count, int* status) {
+    crt_g_exps_kernel(const CrtGPass* __restrict__ pr, int count) {
     const int b = static_cast<int>(blockIdx.x);
     const int g = find_owner(count, b, [&](int i) { return pr[i].exps_begin; });
     const CrtGPass& x = pr[g];
     const int local = b - x.exps_begin;
     using U = typename Bits<T>::U;
     if (local < x.rblocks)
-        crt_row_exp_part(static_cast<const T*>(x.A), x.m, x.n, x.eA, status, local, x.rblocks);
+        crt_row_exp_part(static_cast<const T*>(x.A), x.m, x.n, x.eA, x.status, local, x.rblocks);
     else if (local < x.rblocks + x.cblocks)
         crt_col_max_part(static_cast<const T*>(x.B), x.n, x.p, x.chunk, static_cast<U*>(x.cmax),
                          local - x.rblocks, x.gx);
@@ -987,8 +988,7 @@ __global__ void __launch_bounds__(256)
 // Grouped residue pass over the problems of one input type.
 template <typename T>
 __global__ void __launch_bounds__(256)
-    crt_g_residue_kernel(const CrtGPass* __restrict__ pr, int count, int* status,
-                         const CrtPow2 pow2) {
+    crt_g_residue_kernel(const CrtGPass* __restrict__ pr, int count, const CrtPow2 pow2) {
     // tab[l * 64 + s] = (2^s mod q_l, 2^(s+12) mod q_l): a row per modulus, so
     // threads of a warp that read different s of one row mostly hit different banks
     __shared__ float2 tab[kCrtMaxModuli * 64];
@@ -1002,12 +1002,12 @@ __global__ void __launch_bounds__(256)
     const int local = b - x.res_begin;
     using U = typename Bits<T>::U;
     if (local < x.ga)
-        crt_residue_part<T, 0>(static_cast<const T*>(x.A), x.m, x.n, x.lda, x.eA, nullptr, status,
-                               x.t, x.M, x.va, tab, x.a_pl, x.a_plane, local, x.ga);
+        crt_residue_part<T, 0>(static_cast<const T*>(x.A), x.m, x.n, x.lda, x.eA, nullptr,
+                               x.status, x.t, x.M, x.va, tab, x.a_pl, x.a_plane, local, x.ga);
     else if (local < x.ga + x.gb)
         crt_residue_part<T, 1>(static_cast<const T*>(x.B), x.n, x.p, x.ldb, x.eB,
-                               static_cast<const U*>(x.cmax), status, x.t, x.M, x.vb, tab, x.b_pl,
-                               x.b_plane, local - x.ga, x.gb);
+                               static_cast<const U*>(x.cmax), x.status, x.t, x.M, x.vb, tab,
+                               x.b_pl, x.b_plane, local - x.ga, x.gb);
 }
 
 // Grouped reconstruction: each block serves one problem, with that problem's
@@ -1272,7 +1272,7 @@ int crt_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const
     if (st) {
         st->slices = M;
         st->products = M;
-        st->kernels = 5;
+        st->kernels = 4;   // the column-maximum clear is a memset
     }
     return MOA_OK;
 }
@@ -1349,7 +1349,7 @@ size_t crt_grouped_workspace(int count, const moa_gemm_desc* d) {
 }
 
 int crt_grouped_launch(int count, const moa_gemm_desc* d, void* ws, size_t ws_bytes,
-                       cudaStream_t s) {
+                       cudaStream_t s, int* const* status_of) {
     std::vector<Taken> tk;
     const GroupedPlan P = grouped_plan(count, d, &tk);
     const int G = static_cast<int>(tk.size());
@@ -1400,6 +1400,7 @@ int crt_grouped_launch(int count, const moa_gemm_desc* d, void* ws, size_t ws_by
         q.cmax = base + cmax_pos;
         cmax_pos += (static_cast<size_t>(dd.p) * 8 + 255) / 256 * 256;
         q.R = r + x.L.r_off;
+        q.status = (status_of && status_of[x.idx]) ? status_of[x.idx] : status;
         q.M = x.M;
         q.t = x.t;
         const int per16 = ty ? 2 : 4;
@@ -1473,12 +1474,12 @@ int crt_grouped_launch(int count, const moa_gemm_desc* d, void* ws, size_t ws_by
             pow2.v[l][e2] = static_cast<uint8_t>((static_cast<u128>(1) << e2) % crt_mod(l));
     const int n64 = G - n32;
     if (n32 > 0) {
-        crt_g_exps_kernel<float><<<exps_pos[0], 256, 0, s>>>(dpass, n32, status);
-        crt_g_residue_kernel<float><<<res_pos[0], 256, 0, s>>>(dpass, n32, status, pow2);
+        crt_g_exps_kernel<float><<<exps_pos[0], 256, 0, s>>>(dpass, n32);
+        crt_g_residue_kernel<float><<<res_pos[0], 256, 0, s>>>(dpass, n32, pow2);
     }
     if (n64 > 0) {
-        crt_g_exps_kernel<double><<<exps_pos[1], 256, 0, s>>>(dpass + n32, n64, status);
-        crt_g_residue_kernel<double><<<res_pos[1], 256, 0, s>>>(dpass + n32, n64, status, pow2);
+        crt_g_exps_kernel<double><<<exps_pos[1], 256, 0, s>>>(dpass + n32, n64);
+        crt_g_residue_kernel<double><<<res_pos[1], 256, 0, s>>>(dpass + n32, n64, pow2);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "grouped crt pre-pass launch");

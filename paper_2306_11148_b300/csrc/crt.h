@@ -35,9 +35,12 @@ int crt_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const
 bool crt_grouped_ok(const moa_gemm_desc& d);
 size_t crt_grouped_workspace(int count, const moa_gemm_desc* d);
 // Runs the problems of d[] that crt_grouped_ok takes; `ws` must hold
-// crt_grouped_workspace(count, d) bytes.
+// crt_grouped_workspace(count, d) bytes.  status (may be NULL): a device
+// status word per descriptor, where that problem's non-finite inputs are
+// recorded (pipeline timeouts, which belong to the shared launch, go to the
+// launch's word).
 int crt_grouped_launch(int count, const moa_gemm_desc* d, void* ws, size_t ws_bytes,
-                       cudaStream_t s);
+                       cudaStream_t s, int* const* status = nullptr);
 
 // Workspace layout of a modular-slice call (byte offsets from the base).
 struct CrtLayout {

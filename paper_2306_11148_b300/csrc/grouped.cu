@@ -474,7 +474,7 @@ size_t grouped_workspace(int count, const moa_gemm_desc* d) {
 }
 
 int grouped_launch(int count, const moa_gemm_desc* d, void* ws, size_t ws_bytes, cudaStream_t s,
-                   bool allow_cache) {
+                   bool allow_cache, int* const* status_of) {
     const int sms = num_sms();
     std::vector<int> idx;
     std::vector<int> bn;
@@ -589,7 +589,7 @@ int grouped_launch(int count, const moa_gemm_desc* d, void* ws, size_t ws_bytes,
     const size_t crt_bytes = (crt_grouped_workspace(count, d) + 255) / 256 * 256;
     if (crt_bytes > 0) {
         const int rc = crt_grouped_launch(count, d, static_cast<uint8_t*>(ws) + main_bytes,
-                                          crt_bytes, s);
+                                          crt_bytes, s, status_of);
         if (rc != MOA_OK) return rc;
     }
     // problems outside the persistent paths, one by one on the same stream
@@ -623,7 +623,8 @@ int moa_gemm_grouped(int count, const moa_gemm_desc* d, void* ws, size_t ws_byte
     if (count < 0) return moa::fail(MOA_ERR_ARG, "negative count");
     if (count == 0) return MOA_OK;
     if (d == nullptr) return moa::fail(MOA_ERR_ARG, "descriptor array is NULL");
-    return moa::grouped_launch(count, d, ws, ws_bytes, static_cast<cudaStream_t>(stream), true);
+    return moa::grouped_launch(count, d, ws, ws_bytes, static_cast<cudaStream_t>(stream), true,
+                               nullptr);
 }
 
 }  // extern "C"
@@ -683,7 +684,7 @@ int moa_gemm_batched(int batch, int64_t m, int64_t n, int64_t p, moa_dtype dt, c
     if (rc != MOA_OK) return rc;
     if (batch == 0) return MOA_OK;
     return moa::grouped_launch(batch, d.data(), ws, ws_bytes, static_cast<cudaStream_t>(stream),
-                               true);
+                               true, nullptr);
 }
 
 }  // extern "C"

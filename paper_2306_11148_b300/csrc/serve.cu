@@ -52,7 +52,7 @@ int gemm_ex(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const 
 size_t workspace_bytes(int64_t m, int64_t n, int64_t p, moa_dtype dt, int slices);
 size_t grouped_workspace(int count, const moa_gemm_desc* d);
 int grouped_launch(int count, const moa_gemm_desc* d, void* ws, size_t ws_bytes, cudaStream_t s,
-                   bool allow_cache);
+                   bool allow_cache, int* const* status_of);
 
 namespace {
 
@@ -182,17 +182,24 @@ moa_completion completion_of(const Request& r, int status, double t_done) {
 
 size_t block_bytes(size_t ws) { return Arena::granule(ws); }
 
-// Publishes a request's device status word to the host (mapped pinned
-// memory); `reset` clears the word for the slot's next request.
-__global__ void publish_status_kernel(int* dev_word, int* host_word, int reset) {
-    const int v = *reinterpret_cast<volatile int*>(dev_word);
+// Publishes a request's status to the host (mapped pinned memory): its own
+// device word if that records a failure, else the word of the launch it ran
+// in (`shared`; the same word for a request launched alone).  reset_own /
+// reset_shared clear the words for the slots' next requests.
+__global__ void publish_status_kernel(int* own, int* shared, int* host_word, int reset_own,
+                                      int reset_shared) {
+    const int o = *reinterpret_cast<volatile int*>(own);
+    const int v = o != kDevOk ? o : *reinterpret_cast<volatile int*>(shared);
     *reinterpret_cast<volatile int*>(host_word) = v;
-    if (reset) *dev_word = kDevOk;
+    if (reset_own) *own = kDevOk;
+    if (reset_shared) *shared = kDevOk;
 }
 
-int publish_status(moa_server* s, int dev_slot, int host_slot, bool reset, cudaStream_t st) {
-    publish_status_kernel<<<1, 1, 0, st>>>(s->dev_status + dev_slot,
-                                           s->host_status_dev + host_slot, reset ? 1 : 0);
+int publish_status(moa_server* s, int own_slot, int shared_slot, int host_slot, bool reset_own,
+                   bool reset_shared, cudaStream_t st) {
+    publish_status_kernel<<<1, 1, 0, st>>>(s->dev_status + own_slot, s->dev_status + shared_slot,
+                                           s->host_status_dev + host_slot, reset_own ? 1 : 0,
+                                           reset_shared ? 1 : 0);
     return cudaGetLastError() == cudaSuccess ? MOA_OK : MOA_ERR_CUDA;
 }
 
@@ -338,14 +345,21 @@ void scheduler(moa_server* s) {
         std::vector<int> rcs(batch.size(), MOA_OK);
         if (grouped) {
             cudaStream_t gs = s->streams[gstream];
-            const int lead = batch[bf_idx[0]].hidx;   // the batch shares the lead's status word
+            // Failures of the shared launch (a pipeline timeout) go to the
+            // lead's status word; a modular-slice request's non-finite inputs
+            // go to its own word, so one bad request does not fail the rest.
+            const int lead = batch[bf_idx[0]].hidx;
+            std::vector<int*> own(bf.size());
+            for (size_t k = 0; k < bf_idx.size(); ++k) own[k] = s->dev_status + batch[bf_idx[k]].hidx;
             set_status_override(s->dev_status + lead);
             const int rc = grouped_launch(static_cast<int>(bf.size()), bf.data(), s->arena.ptr(toff),
-                                          tbytes, gs, false);
+                                          tbytes, gs, false, own.data());
             set_status_override(nullptr);
             for (size_t k = 0; k < bf_idx.size(); ++k) {
                 const size_t i = bf_idx[k];
-                const int prc = publish_status(s, lead, batch[i].hidx, k + 1 == bf_idx.size(), gs);
+                const bool last = k + 1 == bf_idx.size();
+                const int prc = publish_status(s, batch[i].hidx, lead, batch[i].hidx,
+                                               batch[i].hidx != lead, last, gs);
                 rcs[i] = rc != MOA_OK ? rc : prc;
             }
         }
@@ -359,7 +373,7 @@ void scheduler(moa_server* s) {
                                  r.ws_bytes ? s->arena.ptr(r.ws_off) : nullptr, r.ws_bytes, rs,
                                  nullptr);
                 set_status_override(nullptr);
-                const int prc = publish_status(s, r.hidx, r.hidx, true, rs);
+                const int prc = publish_status(s, r.hidx, r.hidx, r.hidx, true, true, rs);
                 if (rcs[i] == MOA_OK) rcs[i] = prc;
             }
             if (cudaEventRecord(s->done_ev[r.hidx], s->streams[r.stream]) != cudaSuccess) {

@@ -56,7 +56,7 @@ import numpy as np, torch, oracle
 from paper_2306_11148_b300 import inputs, moa
 L = moa.lib()
 for dt in (moa.MOA_F32_TF32, moa.MOA_BF16, moa.MOA_F32_SPLIT, moa.MOA_F64_SPLIT_F32IN,
-           moa.MOA_F64_SPLIT_F64IN_E4M3):
+           moa.MOA_F64_SPLIT_F64IN_E4M3, moa.MOA_F64_CRT_F32IN, moa.MOA_F64_CRT_F64IN):
     for (m, n, p) in ((33, 127, 129), (70, 4200, 140), (257, 1000, 200)):
         A, B = inputs.integer_pair(m, n, p, dtype=moa.in_dtype(dt), seed=m + n)
         Ad, Bd = A.cuda(), B.cuda()

@@ -1,8 +1,9 @@
 """The continuous-batching server (moa_serve_*).
 
 * Each result is the same alone and in the mix: every request of a mixed
-  batch (FP32-accuracy and FP64-accuracy split requests, plus BF16 requests
-  that share grouped launches) equals, bit for bit, the same GEMM computed
+  batch (FP32-accuracy and FP64-accuracy split requests, plus BF16 and
+  modular-slice requests that share grouped launches) equals, bit for bit,
+  the same GEMM computed
   alone through moa_gemm_ex, and a sample also matches the FP64 oracle within
   the mode's tolerance.
 * Admission: a request whose workspace exceeds the arena is refused
@@ -23,7 +24,7 @@ import oracle
 from paper_2306_11148_b300 import inputs, moa
 
 TOL = {moa.MOA_F32_SPLIT: 1e-5, moa.MOA_F64_SPLIT_F32IN: 1e-12, moa.MOA_BF16: 1e-5,
-       moa.MOA_F64_SPLIT_F32IN_E4M3: 1e-12}
+       moa.MOA_F64_SPLIT_F32IN_E4M3: 1e-12, moa.MOA_F64_CRT_F32IN: 1e-12}
 
 
 def _req(m, n, p, dt, seed):
@@ -48,11 +49,11 @@ def _drain(srv, want, timeout=60.0):
 def test_results_same_alone_and_in_the_mix():
     rng = np.random.default_rng(0)
     reqs = []
-    for i in range(36):
+    for i in range(40):
         m, p = (int(x) for x in rng.integers(1, 40, 2) * 16)
         n = int(rng.integers(1, 80)) * 16
         dt = [moa.MOA_F32_SPLIT, moa.MOA_F64_SPLIT_F32IN, moa.MOA_BF16,
-              moa.MOA_F64_SPLIT_F32IN_E4M3][i % 4]
+              moa.MOA_F64_SPLIT_F32IN_E4M3, moa.MOA_F64_CRT_F32IN][i % 5]
         reqs.append(_req(m, n, p, dt, seed=i))
     alone = [moa.gemm(A, B, dt) for A, B, C, dt in reqs]
     torch.cuda.synchronize()
@@ -183,4 +184,36 @@ def test_per_request_device_status():
     assert got[tb][1] == moa.MOA_ERR_NONFINITE
     assert all(got[t][1] == moa.MOA_OK for t in tg)
     assert st["failed"] == 1 and st["completed"] == 3
+    assert moa.moa_sync_status(moa._stream_handle(None)) == moa.MOA_OK
+
+
+@pytest.mark.gpu
+def test_grouped_modular_slice_requests_keep_their_own_status():
+    """Small modular-slice requests share grouped launches in the server; one
+    with a NaN input completes as MOA_ERR_NONFINITE while the others, grouped
+    with it or not, complete normally and equal their alone results bit for
+    bit."""
+    reqs = [_req(96 + 16 * i, 320, 80 + 16 * i, moa.MOA_F64_CRT_F32IN, seed=90 + i)
+            for i in range(6)]
+    bad = 2
+    reqs[bad][0][3, 11] = float("nan")
+    alone = {i: moa.gemm(A, B, dt) for i, (A, B, C, dt) in enumerate(reqs) if i != bad}
+    torch.cuda.synchronize()
+    moa.check(moa.moa_sync_status(moa._stream_handle(None)))
+    srv = moa.Server(arena_bytes=1 << 28, max_inflight=8, n_streams=2)
+    try:
+        tickets = {srv.submit(*r)[1]: i for i, r in enumerate(reqs)}
+        got = _drain(srv, len(reqs))
+        st = srv.stats()
+    finally:
+        srv.close()
+    torch.cuda.synchronize()
+    assert set(got) == set(tickets)
+    for t, i in tickets.items():
+        if i == bad:
+            assert got[t][1] == moa.MOA_ERR_NONFINITE
+        else:
+            assert got[t][1] == moa.MOA_OK, f"request {i}"
+            assert torch.equal(reqs[i][2], alone[i]), f"request {i} differs from its alone result"
+    assert st["failed"] == 1 and st["completed"] == len(reqs) - 1
     assert moa.moa_sync_status(moa._stream_handle(None)) == moa.MOA_OK
