@@ -238,6 +238,16 @@ int moa_gemm_batched(int batch, int64_t m, int64_t n, int64_t p, moa_dtype dt, c
  * restores the planners.  MOA_ERR_ARG for values outside {0,64,128,192,256}. */
 int moa_set_block_n(int block_n);
 
+/* Tile height of the modular-slice modes (MOA_F64_CRT_*): 128-row tiles on
+ * one SM, or 256 x 256 tiles on a pair of SMs (a cluster of two CTAs whose
+ * tensor-core MMAs span both: each SM stages half of the operands, so more
+ * K blocks are in flight per SM).  The planner picks one by a wave-count
+ * cost model; moa_set_block_m(128 | 256) forces it for the calling thread's
+ * later calls (256 implies block_n 256; a forced block_n of 128 implies
+ * 128 rows), 0 restores the planner.  Results are identical either way.
+ * MOA_ERR_ARG for values outside {0, 128, 256}. */
+int moa_set_block_m(int block_m);
+
 /* Measured refinement of the planner: times C := A . B with every block_n on
  * the caller's buffers (1 warm-up + 3 timed calls each, CUDA events on
  * `stream`, synchronous), records the fastest for the shape bucket of

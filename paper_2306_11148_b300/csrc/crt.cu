@@ -749,6 +749,288 @@ __global__ void __launch_bounds__(CrtCfg<BN>::kThreads, 1)
     }
 }
 
+// ---------------------------------------------------------------- residue GEMM, CTA pairs
+// The same units over 256 x 256 output tiles, each computed by a cluster of
+// two CTAs (CTA r: rows 128 r .. 128 r + 127 of the tile) with cta_group::2
+// MMAs of M = 256, N = 256.  Each CTA stages its 128 rows of A and its half
+// (128 columns) of B: 32 KB a K block instead of 48 KB, so six stages are in
+// flight, and the L2 serves a third less operand traffic per product.
+//   * producer (warp 0 of each CTA): its own halves into its own stages; the
+//     loads of both CTAs complete on the even CTA's `full` barrier (which
+//     the even CTA's producer arms for both: 64 KB a stage);
+//   * the even CTA's warp 1 issues the MMAs; its commits release the stage
+//     in both CTAs (`empty`) and hand each chunk accumulator to both CTAs'
+//     epilogues (`tfull`);
+//   * epilogue (16 warps of each CTA): its 128 x 256 accumulator, as in the
+//     one-CTA kernel; both CTAs' warps report the drain to the even CTA's
+//     `tempty` barrier.
+// Every wait is bounded; both CTAs pass a cluster barrier before TMEM is
+// released and before either exits, so neither leaves while the other's MMAs
+// or arrivals may still reach it.
+struct CrtPairCfg {
+    static constexpr int kAStage = kBM * 128;                 // this CTA's 128 rows x 128 B
+    static constexpr int kBChunk = kBK * 128;                 // 64 K rows x 64 columns
+    static constexpr int kBStage = 2 * kBChunk;               // this CTA's 128 columns
+    static constexpr int kStageBytes = kAStage + kBStage;
+    static constexpr int kStages = 6;
+    static constexpr int kSmem = 1024 + kStages * kStageBytes + 256;
+    static_assert(kSmem <= 227 * 1024, "crt pair kernel shared memory");
+    static constexpr int kEpiWarps = 16;                      // 32 rows x 64 columns each
+    static constexpr int kThreads = 64 + 32 * kEpiWarps;
+    static constexpr int kTmemCols = 512;                     // two 256-column accumulators
+    static constexpr uint32_t kIdesc = make_idesc(1u, 2 * kBM, 256, 0u, 1u);
+};
+constexpr int kPairRows = 2 * kBM;
+
+// Unit u of the pair kernel: modulus l (slowest), then the 256 x 256 tile.
+__device__ __forceinline__ void crt_pair_unit(const CrtGemmArgs& a, int u, int& l, int& tm,
+                                              int& tn) {
+    const int per_l = a.tiles_m * a.tiles_n;
+    l = u / per_l;
+    crt_tile_coords(u - l * per_l, a.tiles_m, a.tiles_n, a.group_m, tm, tn);
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(CrtPairCfg::kThreads, 1)
+    crt_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA,
+                         const __grid_constant__ CUtensorMap tmB, const CrtGemmArgs args) {
+    using Cfg = CrtPairCfg;
+    constexpr int kStages = Cfg::kStages;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                               ~static_cast<uintptr_t>(1023));
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + kStages * Cfg::kAStage;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kStages * Cfg::kBStage);
+    uint64_t* full = bars;                   // (even CTA) both CTAs' stage has landed
+    uint64_t* empty = bars + kStages;        // the pair's MMAs are done with the stage
+    uint64_t* tfull = bars + 2 * kStages;    // a chunk accumulator is complete
+    uint64_t* tempty = tfull + 2;            // (even CTA) both epilogues drained it
+    uint64_t* drain = tempty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    CtaCtl* ctl = reinterpret_cast<CtaCtl*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_ctarank();
+    const uint64_t limit = args.wait_limit_ns;
+    int* status = args.status;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 2 * Cfg::kEpiWarps);
+        }
+        mbar_init(drain, 1);
+        ctl->abort = 0;
+        fence_barrier_init();
+    }
+    if (warp == 0 && lane == 0) {
+        prefetch_tmap(&tmA);
+        prefetch_tmap(&tmB);
+    }
+    if (warp == 1) {
+        tmem_alloc_pair(tmem_slot, Cfg::kTmemCols);
+        tmem_relinquish_pair();
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();   // both CTAs' barriers exist before any arrival crosses over
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const int cid = static_cast<int>(blockIdx.x) >> 1;
+    const int ncl = static_cast<int>(gridDim.x) >> 1;
+    const int num_units = args.M * args.tiles_m * args.tiles_n;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer: this CTA's rows of A, columns of B,
+            // completing on the even CTA's full barrier
+            const uint32_t full0 = mapa_shared(smem_u32(full), 0);
+            int stage = 0;
+            uint32_t phase = 0;
+            long issued = 0;
+            bool ok = true;
+            for (int u = cid; u < num_units && ok; u += ncl) {
+                int l, tm, tn;
+                crt_pair_unit(args, u, l, tm, tn);
+                const int row0 = tm * kPairRows + static_cast<int>(rank) * kBM;
+                const int col0 = tn * 256 + static_cast<int>(rank) * 128;
+                for (int kb = 0; kb < args.num_kb; ++kb) {
+                    if (!mbar_wait(&empty[stage], phase ^ 1u, ctl, limit, status)) {
+                        ok = false;
+                        break;
+                    }
+                    if (rank == 0) mbar_arrive_expect_tx(&full[stage], 2 * Cfg::kStageBytes);
+                    const uint32_t fb = full0 + 8u * static_cast<uint32_t>(stage);
+                    tma_load_3d_pair(sA + stage * Cfg::kAStage, &tmA, fb, kb * kBK, row0, l);
+                    for (int c = 0; c < 2; ++c)
+                        tma_load_3d_pair(sB + stage * Cfg::kBStage + c * Cfg::kBChunk, &tmB, fb,
+                                         col0 + c * 64, kb * kBK, l);
+                    ++issued;
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                // Let the loads already in flight land before the CTA exits:
+                // the even CTA waits on its full barriers (which count both
+                // CTAs' loads); the odd CTA, which cannot see them, gives its
+                // own at most kStages loads a millisecond.
+                CtaCtl local{0};
+                if (rank == 0) {
+                    const long outstanding = issued < kStages ? issued : kStages;
+                    for (long q = 1; q <= outstanding; ++q) {
+                        const long idx = issued - q;
+                        mbar_wait(&full[idx % kStages], static_cast<uint32_t>((idx / kStages) & 1),
+                                  &local, limit, status);
+                    }
+                } else {
+                    const uint64_t t0 = global_timer_ns();
+                    while (global_timer_ns() - t0 < 1000000ull) {
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0 && rank == 0) {
+            // ---------------- even CTA: MMA issuer for the pair
+            int stage = 0;
+            uint32_t phase = 0;
+            long cnt = 0;
+            bool ok = true;
+            for (int u = cid; u < num_units && ok; u += ncl) {
+                for (int kb0 = 0; kb0 < args.num_kb && ok; kb0 += kChunkKB, ++cnt) {
+                    const int buf = static_cast<int>(cnt & 1);
+                    const uint32_t bph = static_cast<uint32_t>((cnt >> 1) & 1);
+                    if (!mbar_wait(&tempty[buf], bph ^ 1u, ctl, limit, status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d = tmem_base + static_cast<uint32_t>(buf * 256);
+                    const int kb1 = min(args.num_kb, kb0 + kChunkKB);
+                    for (int kb = kb0; kb < kb1; ++kb) {
+                        if (!mbar_wait(&full[stage], phase, ctl, limit, status)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint64_t adesc =
+                            smem_desc_sw128(smem_u32(sA + stage * Cfg::kAStage), 16, 1024);
+                        const uint64_t bdesc =
+                            smem_desc_sw128(smem_u32(sB + stage * Cfg::kBStage), Cfg::kBChunk, 1024);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            mma_f16_pair(d, adesc + static_cast<uint64_t>((k * 32) >> 4),
+                                         bdesc + static_cast<uint64_t>((k * 16 * 128) >> 4),
+                                         Cfg::kIdesc, (kb == kb0 && k == 0) ? 0u : 1u);
+                        mma_commit_pair_mc(&empty[stage], 0x3);
+                        if (++stage == kStages) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                    if (!ok) break;
+                    mma_commit_pair_mc(&tfull[buf], 0x3);
+                }
+            }
+            // Every MMA issued above must finish before either CTA releases
+            // TMEM or exits.
+            mma_commit_pair(drain);
+            CtaCtl local{0};
+            mbar_wait(drain, 0, &local, limit, status);
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue: quadrant q = warp % 4 (32 rows), column group h
+        const int q = warp & 3;
+        const int h = (warp - 2) >> 2;
+        const uint32_t lane_base = static_cast<uint32_t>(q * 32) << 16;
+        const uint32_t tempty0 = rank == 0 ? 0u : mapa_shared(smem_u32(tempty), 0);
+        long cnt = 0;
+        bool ok = true;
+        for (int u = cid; u < num_units && ok; u += ncl) {
+            int l, tm, tn;
+            crt_pair_unit(args, u, l, tm, tn);
+            const float qf = args.qf[l], qinv = args.qinv[l];
+            float acc[64];
+#pragma unroll
+            for (int i = 0; i < 64; ++i) acc[i] = 0.f;
+            for (int kb0 = 0; kb0 < args.num_kb; kb0 += kChunkKB, ++cnt) {
+                const int buf = static_cast<int>(cnt & 1);
+                const uint32_t bph = static_cast<uint32_t>((cnt >> 1) & 1);
+                ok = mbar_wait(&tfull[buf], bph, ctl, limit, status);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a_base = tmem_base + lane_base + static_cast<uint32_t>(buf * 256 + h * 64);
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    uint32_t r[16];
+                    tmem_ld16(a_base + 16u * g, r);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        acc[g * 16 + i] =
+                            __fadd_rn(acc[g * 16 + i], mod_reduce(__uint_as_float(r[i]), qf, qinv));
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) {
+                    if (rank == 0)
+                        mbar_arrive(&tempty[buf]);
+                    else
+                        mbar_arrive_remote(tempty0 + 8u * static_cast<uint32_t>(buf));
+                }
+            }
+            if (!ok) break;
+            // the unit's residues in [0, q) as bytes of plane l
+            const int64_t row = static_cast<int64_t>(tm) * kPairRows + rank * kBM + q * 32 + lane;
+            const int64_t col0 = static_cast<int64_t>(tn) * 256 + h * 64;
+            if (row < args.m && col0 < args.p) {
+                uint32_t w[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    uint32_t word = 0;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        float r = mod_reduce(acc[4 * i + b], qf, qinv);   // |r| <= q/2 + 1
+                        r = r < 0.f ? __fadd_rn(r, qf) : r;
+                        r = r >= qf ? __fsub_rn(r, qf) : r;
+                        word |= (__float_as_uint(__fadd_rn(r, 8388608.0f)) & 0xFFu) << (8 * b);
+                    }
+                    w[i] = word;
+                }
+                uint8_t* dst = args.R + (static_cast<int64_t>(l) * args.m + row) * args.ldr + col0;
+                if (col0 + 64 <= args.ldr) {
+#pragma unroll
+                    for (int v = 0; v < 4; ++v)
+                        reinterpret_cast<uint4*>(dst)[v] =
+                            make_uint4(w[4 * v], w[4 * v + 1], w[4 * v + 2], w[4 * v + 3]);
+                } else {
+                    for (int i = 0; i < 64 && col0 + i < args.ldr; ++i)
+                        dst[i] = static_cast<uint8_t>((w[i >> 2] >> (8 * (i & 3))) & 0xFFu);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    cluster_sync_all();   // the pair's MMAs and cross-CTA arrivals are over
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc_pair(tmem_base, Cfg::kTmemCols);
+    }
+}
+
 // ---------------------------------------------------------------- reconstruction
 // mag * 2^e rounded to the nearest FP64 value, ties to even: the top 64 bits
 // normalised, the top 53 of them rounded half to even with the rest (and a
@@ -1076,6 +1358,101 @@ int crt_block_n(int64_t m, int64_t p, int M, long sms) {
     return cost(128, 0.9) < cost(256, 1.0) ? 128 : 256;
 }
 
+// Tile shape of a single modular-slice GEMM: 128-row tiles of width 128 or
+// 256 on one SM, or 256 x 256 tiles on a CTA pair.  Wave-count cost model:
+// ceil(units / slots) waves, each as long as one SM's share of a unit (a
+// 128 x bn block) divided by the shape's efficiency (measured: 128 x 256 at
+// 0.9 of the pair's rate, 128 x 128 at 0.9 of that).  Pair tiles only while
+// one modulus plane of A (m x n) and of B (n x p) each fit in the L2: beyond
+// that the pair kernel reads more from DRAM and, under the power cap, runs
+// slower (measured, FP32 inputs, square N: pair 0.362 vs 0.386 ms at 2048,
+// 5.66 vs 5.76 ms at 6144, even at 8192, 47-48 vs 44 ms at 12288).  K-sliced
+// launches (few units) stay on one SM.  moa_set_block_m / moa_set_block_n
+// force it.
+struct CrtTiles {
+    int rows, bn;
+};
+CrtTiles crt_tile_plan(int64_t m, int64_t n, int64_t p, int M, int ks, long sms, long clusters,
+                       int64_t l2_bytes) {
+    const int ov_m = tile_m_override(), ov_n = tile_override();
+    const int bn1 = crt_block_n(m, p, M, sms);
+    if (ks != 1 || ov_n == 128 || ov_m == 128 || clusters < 1) return {kBM, bn1};
+    if (ov_m == 256) return {2 * kBM, 256};
+    if (2 * std::max(m, p) * n > l2_bytes) return {kBM, bn1};
+    const long units2 = M * ceil_div(m, 2 * kBM) * ceil_div(p, 256);
+    const double c_pair = static_cast<double>((units2 + clusters - 1) / clusters) * 256.0;
+    const long units1 = M * ceil_div(m, kBM) * ceil_div(p, bn1);
+    const double eff1 = bn1 == 256 ? 0.9 : 0.81;
+    const double c_one = static_cast<double>((units1 + sms - 1) / sms) * bn1 / eff1;
+    return c_pair <= c_one ? CrtTiles{2 * kBM, 256} : CrtTiles{kBM, bn1};
+}
+
+// The device's L2 size in bytes (cached per device).
+int64_t l2_bytes() {
+    static std::atomic<int64_t> cache[64];
+    int d = -1;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) return 0;
+    int64_t v = cache[d].load(std::memory_order_acquire);
+    if (v == 0) {
+        int b = 0;
+        if (cudaDeviceGetAttribute(&b, cudaDevAttrL2CacheSize, d) != cudaSuccess || b <= 0) return 0;
+        v = b;
+        cache[d].store(v, std::memory_order_release);
+    }
+    return v;
+}
+
+// Clusters of the pair kernel that fit on the device at once (0 when the
+// query fails: the one-SM kernels are used).
+long crt_pair_clusters() {
+    static std::atomic<long> cache[64];
+    int d = -1;
+    if (cudaGetDevice(&d) != cudaSuccess) d = -1;
+    if (d >= 0 && d < 64 && cache[d].load(std::memory_order_acquire) != 0)
+        return cache[d].load(std::memory_order_acquire);
+    static std::atomic<uint64_t> attr_done{0};
+    if (smem_attr_once(reinterpret_cast<const void*>(crt_gemm_pair_kernel), CrtPairCfg::kSmem,
+                       attr_done, "cudaFuncSetAttribute(crt_gemm_pair)") != MOA_OK)
+        return 0;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(2 * static_cast<unsigned>(num_sms()), 1, 1);
+    cfg.blockDim = dim3(CrtPairCfg::kThreads, 1, 1);
+    cfg.dynamicSmemBytes = CrtPairCfg::kSmem;
+    int n = 0;
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&n, crt_gemm_pair_kernel, &cfg);
+    if (e != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        log_msg(1, "crt pair kernel: cluster occupancy query failed (%s); one-SM tiles only",
+                e != cudaSuccess ? cudaGetErrorString(e) : "no cluster fits");
+        return 0;
+    }
+    if (d >= 0 && d < 64) cache[d].store(n, std::memory_order_release);
+    return n;
+}
+
+int launch_crt_pair(const CrtGemmArgs& a, const CUtensorMap& tmA, const CUtensorMap& tmB,
+                    long clusters, cudaStream_t s, moa_stats* st) {
+    using Cfg = CrtPairCfg;
+    const long units = static_cast<long>(a.M) * a.tiles_m * a.tiles_n;
+    const int grid = 2 * static_cast<int>(std::min<long>(units, clusters));
+    prof_begin(s);
+    crt_gemm_pair_kernel<<<grid, Cfg::kThreads, Cfg::kSmem, s>>>(tmA, tmB, a);
+    cudaError_t e = cudaGetLastError();
+    prof_end(s);
+    if (e != cudaSuccess) return cuda_fail(e, "crt_gemm_pair_kernel launch");
+    log_msg(2, "crt m=%lld n=%lld p=%lld tile 256x256 (CTA pairs) moduli %d units %ld grid %d",
+            static_cast<long long>(a.m), static_cast<long long>(a.n), static_cast<long long>(a.p),
+            a.M, units, grid);
+    if (st) {
+        st->block_m = 2 * kBM;
+        st->block_n = 256;
+        st->block_k = kBK;
+        st->grid = grid;
+        st->tiles = static_cast<int64_t>(a.tiles_m) * a.tiles_n;
+    }
+    return MOA_OK;
+}
+
 template <int BN, bool GROUPED = false>
 int launch_crt_gemm(const CrtGemmArgs& a, const CUtensorMap& tmA, const CUtensorMap& tmB,
                     cudaStream_t s, moa_stats* st) {
@@ -1225,19 +1602,29 @@ int crt_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const
 
     // launch 4: the residue GEMM
     const long sms = num_sms();
-    const int bn = crt_block_n(m, p, M, sms);
+    const int bn1 = crt_block_n(m, p, M, sms);
+    const int ks = std::min(L.ks_max, crt_ks(static_cast<long>(M) * ceil_div(m, kBM) *
+                                                 ceil_div(p, bn1),
+                                             static_cast<int>(ceil_div(n, kBK)), sms));
+    const long clusters = ks == 1 ? crt_pair_clusters() : 0;
+    const CrtTiles tiles = crt_tile_plan(m, n, p, M, ks, sms, clusters, l2_bytes());
+    const bool pair = tiles.rows == 2 * kBM;
+    const int bn = tiles.bn;
     CrtGemmArgs a{};
     a.R = R;
     a.m = m;
     a.n = n;
     a.p = p;
     a.ldr = L.ldr;
-    a.tiles_m = static_cast<int>(ceil_div(m, kBM));
+    a.tiles_m = static_cast<int>(ceil_div(m, tiles.rows));
     a.tiles_n = static_cast<int>(ceil_div(p, bn));
     a.num_kb = static_cast<int>(ceil_div(n, kBK));
+    // the same number of tile rows a raster group either way: twice the
+    // output rows for pair tiles (measured: 16 pair rows a group hold their
+    // own against 16 one-SM rows at 8192^2 under the power cap; 8 lose ~2%)
     a.group_m = split_raster_group(n);
     a.M = M;
-    a.ks = std::min(L.ks_max, crt_ks(static_cast<long>(M) * a.tiles_m * a.tiles_n, a.num_kb, sms));
+    a.ks = ks;
     for (int l = 0; l < M; ++l) {
         a.qf[l] = static_cast<float>(crt_mod(l));
         a.qinv[l] = 1.0f / static_cast<float>(crt_mod(l));
@@ -1254,7 +1641,9 @@ int crt_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const
                       static_cast<uint64_t>(n), static_cast<uint64_t>(M),
                       static_cast<uint64_t>(L.ldb) * 2, static_cast<uint64_t>(b_plane) * 2, 64, kBK);
     if (rc != MOA_OK) return rc;
-    rc = bn == 256 ? launch_crt_gemm<256>(a, tmA, tmB, s, st) : launch_crt_gemm<128>(a, tmA, tmB, s, st);
+    rc = pair ? launch_crt_pair(a, tmA, tmB, clusters, s, st)
+         : bn == 256 ? launch_crt_gemm<256>(a, tmA, tmB, s, st)
+                     : launch_crt_gemm<128>(a, tmA, tmB, s, st);
     if (rc != MOA_OK) return rc;
 
     // launch 5: reconstruction

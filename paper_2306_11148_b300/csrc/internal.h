@@ -104,6 +104,9 @@ int dense_tc_launch(bool in_bf16, int64_t m, int64_t n, int64_t p, const void* A
 // Tile-width choice of the dense kernels (tuner.cu): per-thread override
 // (0 = none) and the measured width for a shape bucket (0 = none).
 int tile_override();
+// Tile-height override of the modular-slice GEMM (0 = none, 128 = one CTA a
+// tile, 256 = a CTA pair a tile).
+int tile_m_override();
 // Tile rows per raster group of the persistent kernels (the L2-level lift):
 // MOA_RASTER_GROUP, default 16.
 int raster_group();

@@ -26,6 +26,7 @@ int gemm_ex(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const 
 
 namespace {
 thread_local int t_override = 0;
+thread_local int t_override_m = 0;
 std::mutex g_mu;
 using Key = std::tuple<int, int, int, int>;
 std::map<Key, int> g_table;
@@ -52,6 +53,7 @@ int load_locked(const char* path) {
 }  // namespace
 
 int tile_override() { return t_override; }
+int tile_m_override() { return t_override_m; }
 
 // MOA_RASTER_GROUP if set (1..1024), else 0.
 static int raster_env() {
@@ -92,6 +94,13 @@ int moa_set_block_n(int block_n) {
     if (block_n != 0 && block_n != 64 && block_n != 128 && block_n != 192 && block_n != 256)
         return moa::fail(MOA_ERR_ARG, "block_n must be 0, 64, 128, 192 or 256");
     moa::t_override = block_n;
+    return MOA_OK;
+}
+
+int moa_set_block_m(int block_m) {
+    if (block_m != 0 && block_m != 128 && block_m != 256)
+        return moa::fail(MOA_ERR_ARG, "block_m must be 0, 128 or 256");
+    moa::t_override_m = block_m;
     return MOA_OK;
 }
 

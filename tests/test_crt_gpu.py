@@ -87,6 +87,77 @@ def test_both_tile_widths_bit_exact(bn):
                           oracle.crt_gemm(A.double().numpy(), B.double().numpy(), 14))
 
 
+def _run_tiles(A, B, dt, block_m, slices=0, block_n=0):
+    L = moa.lib()
+    moa.check(L.moa_set_block_m(block_m))
+    moa.check(L.moa_set_block_n(block_n))
+    try:
+        C, st = moa.gemm(A.cuda(), B.cuda(), dt, slices=slices, stats=True)
+        moa.sync_status()
+    finally:
+        moa.check(L.moa_set_block_m(0))
+        moa.check(L.moa_set_block_n(0))
+    return C.cpu().numpy(), st
+
+
+# ragged rows (the odd CTA's rows partly or wholly past m), ragged columns
+# (its B half past p), one and several K chunks, 7- and 8-limb moduli counts
+PAIR_CASES = [((1, 1, 1), 14), ((3, 17, 5), 14), ((129, 3000, 385), 14), ((257, 1030, 260), 16),
+              ((300, 2100, 520), 15), ((640, 700, 900), 8), ((1000, 64, 3000), 14)]
+
+
+@pytest.mark.parametrize("dt", MODES, ids=lambda d: NAMES[d])
+@pytest.mark.parametrize("case", PAIR_CASES, ids=lambda c: "x".join(map(str, c[0])))
+def test_pair_tiles_bit_exact(dt, case):
+    """256 x 256 tiles on CTA pairs (moa_set_block_m(256)) equal the exact
+    integer product bit for bit."""
+    (m, n, p), M = case
+    A, B = _pair(m, n, p, dt, "rowcol", seed=m + 2 * n + p)
+    got, st = _run_tiles(A, B, dt, 256, slices=M)
+    assert st.block_m == 256 and st.block_n == 256 and st.grid % 2 == 0
+    assert np.array_equal(got, oracle.crt_gemm(A.double().numpy(), B.double().numpy(), M))
+
+
+def test_pair_and_one_sm_tiles_agree_on_many_tiles():
+    """3000 x 1500 x 5000 (12 x 20 pair tiles x 14 moduli, several units per
+    cluster): CTA-pair tiles, 128 x 256 and 128 x 128 tiles give the same
+    bits, and sampled rows equal the exact integer product."""
+    m, n, p = 3000, 1500, 5000
+    A, B = _pair(m, n, p, moa.MOA_F64_CRT_F32IN, "rows", seed=21)
+    pair, st2 = _run_tiles(A, B, moa.MOA_F64_CRT_F32IN, 256)
+    one, st1 = _run_tiles(A, B, moa.MOA_F64_CRT_F32IN, 128, block_n=256)
+    narrow, st0 = _run_tiles(A, B, moa.MOA_F64_CRT_F32IN, 128, block_n=128)
+    assert (st2.block_m, st1.block_m, st1.block_n, st0.block_n) == (256, 128, 256, 128)
+    assert np.array_equal(pair, one) and np.array_equal(pair, narrow)
+    rows = inputs.sample_rows(m, 6, seed=4)
+    want = oracle.crt_gemm(A.double().numpy()[rows], B.double().numpy(), 14)
+    assert np.array_equal(pair[rows], want)
+
+
+def test_planner_pair_tiles_only_while_planes_fit_l2():
+    """The planner takes CTA-pair tiles while one modulus plane of A and of B
+    fits in the L2 (1024^3), one-SM tiles once a plane does not (8192 x 8192
+    x 256: A's plane is 128 MiB); both give the forced other shape's bits."""
+    small = _pair(1024, 1024, 1024, moa.MOA_F64_CRT_F32IN, "rows", seed=31)
+    got, st = _run_tiles(*small, moa.MOA_F64_CRT_F32IN, 0)
+    forced, _ = _run_tiles(*small, moa.MOA_F64_CRT_F32IN, 128)
+    assert st.block_m == 256 and np.array_equal(got, forced)
+    A, B = _pair(8192, 8192, 256, moa.MOA_F64_CRT_F32IN, "rows", seed=32)
+    got, st = _run_tiles(A, B, moa.MOA_F64_CRT_F32IN, 0)
+    forced, st2 = _run_tiles(A, B, moa.MOA_F64_CRT_F32IN, 256)
+    assert st.block_m == 128 and st2.block_m == 256 and np.array_equal(got, forced)
+    rows = inputs.sample_rows(8192, 4, seed=5)
+    want = oracle.crt_gemm(A.double().numpy()[rows], B.double().numpy(), 14)
+    assert np.array_equal(got[rows], want)
+
+
+def test_block_m_setter_rejects_bad_values():
+    L = moa.lib()
+    assert L.moa_set_block_m(64) == moa.MOA_ERR_ARG
+    assert L.moa_set_block_m(512) == moa.MOA_ERR_ARG
+    assert L.moa_set_block_m(0) == moa.MOA_OK
+
+
 @pytest.mark.parametrize("dt", MODES, ids=lambda d: NAMES[d])
 def test_integer_inputs_bit_exact_against_gemm_oracle(dt):
     A, B = inputs.integer_pair(257, 1000, 200, dtype=moa.in_dtype(dt), seed=3)
