@@ -318,7 +318,7 @@ MODE_OF = {"split_f64": "f64_split_f32in", "square": "tf32", "bf16": "bf16",
            "crt_f64in": "f64_crt_f64in",
            "f64": "f64", "simt": "f32_simt",
            "grouped": "grouped", "serve": "serve", "energy_n": "energy_n",
-           "tiles": "tiles", "peaks": "peaks", "products": "products"}
+           "tiles": "tiles", "peaks": "peaks", "products": "products", "crt_tiles": "crt_tiles"}
 
 
 SPLIT_F32IN = ("f32_split", "f64_split_f32in", "f64_split_f32in_e4m3", "f64_crt_f32in")
@@ -1107,6 +1107,45 @@ def bench_tiles(stream, energy, sizes=(2048, 4096, 8192), modes=("bf16", "tf32")
     return out
 
 
+def bench_crt_tiles(stream, energy, sizes=(2048, 4096, 6144, 8192, 12288), rounds=2):
+    """Tile shapes of the modular-slice mode (FP32 inputs) under sustained
+    load: 128 x 256 tiles on one SM against 256 x 256 tiles on CTA pairs,
+    alternating, each a >= 1.5 s window of back-to-back GEMMs (seconds per
+    GEMM by CUDA events, joules by the NVML counter): the data behind the
+    planner's choice."""
+    import torch
+    from paper_2306_11148_b300 import moa
+    L = moa.lib()
+    out = []
+    for N in sizes:
+        dt, A, B, Ad, Bd, C, ws, w, wb = _prep("f64_crt_f32in", N)
+        sh = int(stream.cuda_stream)
+        for r in range(rounds):
+            for bm, bn in ((128, 256), (256, 256)):
+                moa.check(L.moa_set_block_m(bm))
+                moa.check(L.moa_set_block_n(bn))
+
+                def step():
+                    moa.check(moa.moa_gemm_ex(N, N, N, dt, Ad.data_ptr(), Bd.data_ptr(),
+                                              C.data_ptr(), 0, w, wb, sh, None))
+                with torch.cuda.stream(stream):
+                    step()
+                    t0 = time.perf_counter()
+                    step()
+                    torch.cuda.synchronize()
+                    t_est = time.perf_counter() - t0
+                m = measure_window(step, energy, stream, t_est, min_window=1.5)
+                m.update({"N": N, "block_m": bm, "block_n": bn, "round": r,
+                          "tflops": 2.0 * N ** 3 / m["s_per_gemm"] / 1e12})
+                out.append(m)
+        moa.check(L.moa_set_block_m(0))
+        moa.check(L.moa_set_block_n(0))
+        moa.check(moa.moa_sync_status(sh))
+        del Ad, Bd, C, ws
+        torch.cuda.empty_cache()
+    return out
+
+
 def bench_library_rates(N=8192, reps=10):
     """Dense GEMM rates of the vendor library (cuBLAS through torch) per data
     type on this GPU, next to this library's dense kernels: context for the
@@ -1255,6 +1294,8 @@ def main():
                     help="mode of the FP64-accuracy serving requests")
     ap.add_argument("--no-extras", action="store_true", help="skip the other-mode measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--block-m", type=int, default=0, choices=[0, 128, 256],
+                    help="force the modular-slice tile height (moa_set_block_m)")
     ap.add_argument("--profile", action="store_true",
                     help="timed GEMM steps only (no energy window, e2e, extras, CPU baseline)")
     args = ap.parse_args()
@@ -1285,7 +1326,10 @@ def main():
     mode = MODE_OF[args.workload]
     N = args.n
 
-    if mode in ("energy_n", "tiles", "peaks", "products"):
+    if args.block_m:
+        moa.check(moa.lib().moa_set_block_m(args.block_m))
+
+    if mode in ("energy_n", "tiles", "peaks", "products", "crt_tiles"):
         clocks = ClockSampler(pci)
         clocks.start()
         if mode == "products":
@@ -1300,6 +1344,12 @@ def main():
             metric = "dense GEMM TFLOP/s per dtype: vendor library vs this library"
             value = res["moa_tf32"]
             unit = "TFLOP/s (this library, TF32)"
+        elif mode == "crt_tiles":
+            res = bench_crt_tiles(stream, energy)
+            metric = "modular-slice GEMM time and energy: one-SM vs CTA-pair tiles vs N"
+            best = max(res, key=lambda r: r["tflops"])
+            value = best["tflops"]
+            unit = "TFLOP/s (best cell)"
         elif mode == "energy_n":
             res = bench_energy_n(stream, energy, **({"modes": tuple(args.energy_modes)}
                                                      if args.energy_modes else {}))
@@ -1434,6 +1484,8 @@ def main():
                 "kernel": {"tf32": "dense_tc_kernel", "bf16": "dense_tc_kernel",
                            "f64_crt_f32in": "crt_gemm_kernel",
                            "f64_crt_f64in": "crt_gemm_kernel"}.get(mode, "split_gemm_kernel")}
+        if roof["kernel"] == "crt_gemm_kernel" and main_res["tile"][0] == 256:
+            roof["kernel"] = "crt_gemm_pair_kernel"   # 256 x 256 tiles on CTA pairs
         if kernel_ms >= 10.0:
             roof.update({"peak_sustained": peak_s, "frac_sustained": achieved / peak_s})
     else:
