@@ -417,7 +417,7 @@ def bench_mode(mode, N, steps, warmup, ws, stream, want_energy=False, energy=Non
             out["energy"] = {"j_per_gemm": (j1 - j0) / reps, "window_s": t1 - t0, "reps": reps,
                              "avg_w": (j1 - j0) / (t1 - t0)}
     if want_e2e:
-        out["e2e"] = bench_e2e(dt, A, B, C, N, max(4, min(steps, 8)), 2, stream, ws)
+        out["e2e"] = bench_e2e(dt, A, B, C, N, max(6, steps), 3, stream, ws)
     if keep_rows is not None:
         out["rows_C"] = C.index_select(
             0, torch.as_tensor(keep_rows, dtype=torch.int64, device=C.device)).cpu()
@@ -432,38 +432,33 @@ def bench_mode(mode, N, steps, warmup, ws, stream, want_energy=False, energy=Non
     return out
 
 
-def bench_e2e(dt, A, B, C, N, steps, warmup, stream, ws):
-    """Same GEMM through the C ABI with host buffers: every step copies its A
-    and B from pinned host memory to the device, runs the GEMM and copies C
-    back to pinned host memory, all inside the timed region.  Independent
-    steps alternate between two streams with their own device buffers, so one
-    step's host-to-device copy overlaps the previous step's GEMM and
-    device-to-host copy (separate copy engines)."""
+def bench_e2e(dt, A, B, C, N, steps, warmup, stream, ws, lanes_n=3):
+    """The same GEMM through the library's host-buffer entry (moa_gemm_host):
+    every step the library copies that step's A and B from pinned host memory
+    to the device, runs the GEMM and copies C back to pinned host memory, all
+    inside the timed region.  Independent steps rotate over `lanes_n` streams,
+    each with its own workspace and host C, so one step's copies overlap
+    another's GEMM (the copy engines and the SMs work at once); with three
+    lanes a lane's in-order upload, GEMM and download span three steps."""
     import torch
     from paper_2306_11148_b300 import moa
     Ah = A.pin_memory()
     Bh = B.pin_memory()
+    need = moa.moa_gemm_host_workspace_size(N, N, N, dt, 0)
     lanes = []
-    for _ in range(2):
+    for _ in range(lanes_n):
         st = torch.cuda.Stream()
-        Ad = torch.empty_like(A, device="cuda")
-        Bd = torch.empty_like(B, device="cuda")
-        Cd = torch.empty_like(C)
         Ch = torch.empty(C.shape, dtype=C.dtype, pin_memory=True)
         wsp = moa.Workspace(torch.device("cuda"))
-        w, wb = wsp.get(moa.moa_gemm_workspace_size(N, N, N, dt, 0))
-        lanes.append((st, Ad, Bd, Cd, Ch, wsp, w, wb))
+        w, wb = wsp.get(need)
+        lanes.append((st, Ch, wsp, w, wb))
     idx = [0]
 
     def step():
-        st, Ad, Bd, Cd, Ch, _, w, wb = lanes[idx[0] % 2]
+        st, Ch, _, w, wb = lanes[idx[0] % lanes_n]
         idx[0] += 1
-        with torch.cuda.stream(st):
-            Ad.copy_(Ah, non_blocking=True)
-            Bd.copy_(Bh, non_blocking=True)
-            moa.check(moa.moa_gemm_ex(N, N, N, dt, Ad.data_ptr(), Bd.data_ptr(), Cd.data_ptr(), 0,
-                                      w, wb, int(st.cuda_stream), None))
-            Ch.copy_(Cd, non_blocking=True)
+        moa.check(moa.moa_gemm_host(N, N, N, dt, Ah.data_ptr(), Bh.data_ptr(), Ch.data_ptr(), 0,
+                                    w, wb, int(st.cuda_stream), None))
 
     for _ in range(warmup):
         step()
@@ -472,21 +467,25 @@ def bench_e2e(dt, A, B, C, N, steps, warmup, stream, ws):
     t0 = time.perf_counter()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev0.record(lanes[0][0])
-    lanes[1][0].wait_event(ev0)
+    for ln in lanes[1:]:
+        ln[0].wait_event(ev0)
     for _ in range(steps):
         step()
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev2 = torch.cuda.Event(enable_timing=True)
-    ev1.record(lanes[0][0])
-    ev2.record(lanes[1][0])
+    ends = []
+    for ln in lanes:
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(ln[0])
+        ends.append(e)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t0
-    t = max(ev0.elapsed_time(ev1), ev0.elapsed_time(ev2)) / 1000.0
+    t = max(ev0.elapsed_time(e) for e in ends) / 1000.0
+    for ln in lanes:
+        moa.check(moa.moa_sync_status(int(ln[0].cuda_stream)))
     barrier(ws)
     h2d = A.numel() * A.element_size() + B.numel() * B.element_size()
     d2h = C.numel() * C.element_size()
     return {"seconds": t, "wall_seconds": t_wall, "steps": steps, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "streams": 2}
+            "d2h_bytes_per_step": d2h, "streams": lanes_n, "api": "moa_gemm_host"}
 
 
 def gpu_rows(mode, N, scaled, rows, stream):
@@ -1581,7 +1580,9 @@ def main():
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val if math.isfinite(e2e_val) else None, "unit": "TFLOP/s",
                     "h2d_bytes_per_step": e2e.get("h2d_bytes_per_step"),
-                    "d2h_bytes_per_step": e2e.get("d2h_bytes_per_step")},
+                    "d2h_bytes_per_step": e2e.get("d2h_bytes_per_step"),
+                    "api": e2e.get("api"), "streams": e2e.get("streams"),
+                    "steps": e2e.get("steps")},
             "gpu_launches": main_res["kernels_per_step"] * args.steps,
             "clocks": clk,
             "energy": main_res.get("energy") or {"unavailable": energy.why},

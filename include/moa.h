@@ -126,6 +126,32 @@ int moa_gemm_ex(int64_t m, int64_t n, int64_t p, moa_dtype dt,
                 const void* A, const void* B, void* C, int slices,
                 void* ws, size_t ws_bytes, void* stream, moa_stats* stats);
 
+/* C := A . B with A, B and C in HOST memory (row-major, contiguous), the
+ * call a user without device buffers makes.  On `stream`, in order: A and B
+ * are copied to device buffers inside `ws`, the GEMM runs there exactly as
+ * moa_gemm_ex would run it (same kernels, same bits), and C is copied back to
+ * hC.  ws: a device buffer of at least moa_gemm_host_workspace_size(...)
+ * bytes, 256-byte aligned, owned by the caller (the call allocates nothing);
+ * it must not be in use by another call until this one's stream work is
+ * done.  Asynchronous like moa_gemm_ex: hC holds the result once `stream` has
+ * been synchronised (moa_sync_status(stream) also reports the device
+ * status).  The copies overlap other streams' work only from page-locked
+ * host memory (cudaHostAlloc / cudaHostRegister); from pageable memory they
+ * are staged by the driver and the call may return only after them.
+ * Independent calls on different streams with different workspaces overlap
+ * one call's copies with another's GEMM.  stats may be NULL.  Errors as
+ * moa_gemm_ex, plus MOA_ERR_WORKSPACE / MOA_ERR_ALIGN for the workspace;
+ * host pointers need only their element alignment.
+ * m == 0 or p == 0: MOA_OK, nothing enqueued.  n == 0: hC := 0. */
+int moa_gemm_host(int64_t m, int64_t n, int64_t p, moa_dtype dt,
+                  const void* hA, const void* hB, void* hC, int slices,
+                  void* ws, size_t ws_bytes, void* stream, moa_stats* stats);
+
+/* Bytes of device workspace moa_gemm_host needs: device copies of A, B and C
+ * (each rounded up to 256 bytes) plus moa_gemm_workspace_size(...).  0 for
+ * an unknown mode or a negative dimension. */
+size_t moa_gemm_host_workspace_size(int64_t m, int64_t n, int64_t p, moa_dtype dt, int slices);
+
 /* ---------------------------------------------------------------------- */
 /* Grouped GEMM: `count` independent problems of any shapes in one          */
 /* persistent launch (the batching pattern).                                */

@@ -212,6 +212,76 @@ int moa_gemm_ex(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, co
                         static_cast<cudaStream_t>(stream), stats);
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------- host buffers
+// Workspace of moa_gemm_host: device copies of A, B and C, then the mode's
+// own workspace (each region 256-byte aligned).
+namespace moa {
+namespace {
+struct HostLayout {
+    size_t a_bytes, b_bytes, c_bytes;
+    size_t a_off, b_off, c_off, g_off, total;
+};
+HostLayout host_layout(int64_t m, int64_t n, int64_t p, moa_dtype dt, int slices) {
+    auto al = [](size_t x) { return (x + kAlign - 1) / kAlign * kAlign; };
+    HostLayout L{};
+    L.a_bytes = static_cast<size_t>(m) * n * in_size(dt);
+    L.b_bytes = static_cast<size_t>(n) * p * in_size(dt);
+    L.c_bytes = static_cast<size_t>(m) * p * out_size(dt);
+    L.a_off = 0;
+    L.b_off = al(L.a_bytes);
+    L.c_off = L.b_off + al(L.b_bytes);
+    L.g_off = L.c_off + al(L.c_bytes);
+    L.total = L.g_off + workspace_bytes(m, n, p, dt, slices);
+    return L;
+}
+}  // namespace
+}  // namespace moa
+
+extern "C" {
+
+size_t moa_gemm_host_workspace_size(int64_t m, int64_t n, int64_t p, moa_dtype dt, int slices) {
+    if (!moa::valid_dtype(dt) || m < 0 || n < 0 || p < 0) return 0;
+    if (m > (int64_t(1) << 31) || n > (int64_t(1) << 31) || p > (int64_t(1) << 31)) return 0;
+    return moa::host_layout(m, n, p, dt, slices).total;
+}
+
+int moa_gemm_host(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* hA, const void* hB,
+                  void* hC, int slices, void* ws, size_t ws_bytes, void* stream,
+                  moa_stats* stats) {
+    moa::TraceRange tr("moa_gemm_host");
+    if (!moa::valid_dtype(dt)) return moa::fail(MOA_ERR_DTYPE, "unknown moa_dtype");
+    if (m < 0 || n < 0 || p < 0) return moa::fail(MOA_ERR_ARG, "negative dimension");
+    if (m > (int64_t(1) << 31) || n > (int64_t(1) << 31) || p > (int64_t(1) << 31))
+        return moa::fail(MOA_ERR_ARG, "dimension above 2^31");
+    if (m > 0 && p > 0 && hC == nullptr) return moa::fail(MOA_ERR_ARG, "C is NULL");
+    if (m > 0 && p > 0 && n > 0 && (hA == nullptr || hB == nullptr))
+        return moa::fail(MOA_ERR_ARG, "A or B is NULL");
+    if (stats) *stats = moa_stats{};
+    if (m == 0 || p == 0) return MOA_OK;
+    const moa::HostLayout L = moa::host_layout(m, n, p, dt, slices);
+    if (ws_bytes < L.total || ws == nullptr)
+        return moa::fail(MOA_ERR_WORKSPACE, "workspace smaller than moa_gemm_host_workspace_size");
+    if (reinterpret_cast<uintptr_t>(ws) % moa::kAlign)
+        return moa::fail(MOA_ERR_ALIGN, "workspace not 256-byte aligned");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint8_t* base = static_cast<uint8_t*>(ws);
+    void* dA = base + L.a_off;
+    void* dB = base + L.b_off;
+    void* dC = base + L.c_off;
+    cudaError_t e = cudaSuccess;
+    if (L.a_bytes) e = cudaMemcpyAsync(dA, hA, L.a_bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && L.b_bytes) e = cudaMemcpyAsync(dB, hB, L.b_bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return moa::cuda_fail(e, "cudaMemcpyAsync(A, B to the device)");
+    const int rc = moa::gemm_ex(m, n, p, dt, n ? dA : nullptr, n ? dB : nullptr, dC, slices,
+                                base + L.g_off, ws_bytes - L.g_off, s, stats);
+    if (rc != MOA_OK) return rc;
+    e = cudaMemcpyAsync(hC, dC, L.c_bytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return moa::cuda_fail(e, "cudaMemcpyAsync(C to the host)");
+    return MOA_OK;
+}
+
 int moa_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const void* B, void* C) {
     moa::TraceRange tr("moa_gemm");
     int rc = moa::validate(m, n, p, dt, A, B, C);

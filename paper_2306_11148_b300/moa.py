@@ -128,6 +128,9 @@ _sz = ctypes.c_size_t
 EXPORTS = {
     "moa_gemm": (ctypes.c_int, [_i64, _i64, _i64, ctypes.c_int, _vp, _vp, _vp]),
     "moa_gemm_workspace_size": (_sz, [_i64, _i64, _i64, ctypes.c_int, ctypes.c_int]),
+    "moa_gemm_host_workspace_size": (_sz, [_i64, _i64, _i64, ctypes.c_int, ctypes.c_int]),
+    "moa_gemm_host": (ctypes.c_int, [_i64, _i64, _i64, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int,
+                                     _vp, _sz, _vp, ctypes.POINTER(moa_stats)]),
     "moa_gemm_ex": (ctypes.c_int, [_i64, _i64, _i64, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int,
                                    _vp, _sz, _vp, ctypes.POINTER(moa_stats)]),
     "moa_gemm_grouped_workspace_size": (_sz, [ctypes.c_int, ctypes.POINTER(moa_gemm_desc)]),
@@ -221,6 +224,15 @@ def moa_gemm_ex(m, n, p, dt, A, B, C, slices, ws, ws_bytes, stream, stats=None) 
                              ctypes.byref(stats) if stats is not None else None)
 
 
+def moa_gemm_host_workspace_size(m, n, p, dt, slices=0) -> int:
+    return int(lib().moa_gemm_host_workspace_size(m, n, p, dt, slices))
+
+
+def moa_gemm_host(m, n, p, dt, hA, hB, hC, slices, ws, ws_bytes, stream, stats=None) -> int:
+    return lib().moa_gemm_host(m, n, p, dt, hA, hB, hC, slices, ws, ws_bytes, stream,
+                               ctypes.byref(stats) if stats is not None else None)
+
+
 def moa_sync_status(stream=0) -> int:
     return lib().moa_sync_status(stream)
 
@@ -309,6 +321,42 @@ def gemm(A, B, dt: int, C=None, slices: int = 0, stream=None, workspace: Workspa
     st = moa_stats() if stats else None
     check(moa_gemm_ex(m, n, p, dt, _ptr(A), _ptr(B), _ptr(C), slices, ws, wsb,
                       _stream_handle(stream), st))
+    return (C, st) if stats else C
+
+
+def gemm_host(A, B, dt: int, C=None, slices: int = 0, stream=None,
+              workspace: Workspace | None = None, stats: bool = False):
+    """C := A . B through moa_gemm_host on torch CPU tensors (row-major,
+    contiguous; page-locked ones let the copies overlap other streams' work).
+    The library copies A and B to the device, runs the GEMM and copies C back;
+    C holds the result once ``stream`` is synchronised."""
+    import torch
+    ind, outd = in_dtype(dt), out_dtype(dt)
+    if A.dtype != ind or B.dtype != ind:
+        raise TypeError(f"mode {dt} needs {ind} A and B, got {A.dtype} and {B.dtype}")
+    for name, t in (("A", A), ("B", B), ("C", C)):
+        if t is None:
+            continue
+        if t.device.type != "cpu":
+            raise ValueError(f"{name} must be a CPU tensor")
+        if t.dim() != 2 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous row-major matrix")
+    if A.shape[1] != B.shape[0]:
+        raise ValueError("A must be m x n and B n x p")
+    m, n = A.shape
+    p = B.shape[1]
+    if C is None:
+        C = torch.empty((m, p), dtype=outd, pin_memory=A.is_pinned())
+    elif C.dtype != outd or tuple(C.shape) != (m, p):
+        raise ValueError(f"C must be an m x p {outd} tensor")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if workspace is None:
+        workspace = _default_ws.setdefault(("host", dev), Workspace(dev))
+    ws, wsb = workspace.get(moa_gemm_host_workspace_size(m, n, p, dt, slices))
+    st = moa_stats() if stats else None
+    check(moa_gemm_host(m, n, p, dt, A.data_ptr() if A.numel() else None,
+                        B.data_ptr() if B.numel() else None, C.data_ptr() if C.numel() else None,
+                        slices, ws, wsb, _stream_handle(stream), st))
     return (C, st) if stats else C
 
 

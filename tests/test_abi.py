@@ -119,6 +119,39 @@ def test_workspace_sizes(L):
         assert moa.moa_gemm_workspace_size(256, 256, 256, moa.MOA_F64_CRT_F64IN, bad) == 0
 
 
+def test_host_entry_workspace_and_argument_errors(L):
+    """moa_gemm_host: the workspace holds device copies of A, B, C (each
+    rounded to 256 bytes) plus the mode's own; bad arguments are refused on
+    the host before any copy or launch."""
+    for dt in (moa.MOA_BF16, moa.MOA_F32_TF32, moa.MOA_F32_SPLIT, moa.MOA_F64_CRT_F32IN,
+               moa.MOA_F64_CRT_F64IN, moa.MOA_F64):
+        m, n, p = 100, 70, 30
+        ib = 2 if dt == moa.MOA_BF16 else (8 if dt in (moa.MOA_F64, moa.MOA_F64_CRT_F64IN) else 4)
+        ob = 8 if dt in moa.F64_ACCURATE else 4
+        al = lambda x: (x + 255) // 256 * 256  # noqa: E731
+        want = al(m * n * ib) + al(n * p * ib) + al(m * p * ob) + \
+            moa.moa_gemm_workspace_size(m, n, p, dt, 0)
+        assert moa.moa_gemm_host_workspace_size(m, n, p, dt, 0) == want
+    assert moa.moa_gemm_host_workspace_size(4, 4, 4, 11, 0) == 0
+    assert moa.moa_gemm_host_workspace_size(-1, 4, 4, moa.MOA_BF16, 0) == 0
+    a = (ctypes.c_float * 64)()
+    c = (ctypes.c_double * 64)()
+    pa, pc = ctypes.addressof(a), ctypes.addressof(c)
+    need = moa.moa_gemm_host_workspace_size(8, 8, 8, moa.MOA_F64_CRT_F32IN, 0)
+    f = moa.moa_gemm_host
+    assert f(8, 8, 8, 11, pa, pa, pc, 0, 256, need, None) == moa.MOA_ERR_DTYPE
+    assert f(-8, 8, 8, moa.MOA_F64_CRT_F32IN, pa, pa, pc, 0, 256, need, None) == moa.MOA_ERR_ARG
+    assert f(8, 8, 8, moa.MOA_F64_CRT_F32IN, None, pa, pc, 0, 256, need, None) == moa.MOA_ERR_ARG
+    assert f(8, 8, 8, moa.MOA_F64_CRT_F32IN, pa, pa, None, 0, 256, need, None) == moa.MOA_ERR_ARG
+    assert f(8, 8, 8, moa.MOA_F64_CRT_F32IN, pa, pa, pc, 0, 256, need - 1,
+             None) == moa.MOA_ERR_WORKSPACE
+    assert f(8, 8, 8, moa.MOA_F64_CRT_F32IN, pa, pa, pc, 0, None, need,
+             None) == moa.MOA_ERR_WORKSPACE
+    assert f(8, 8, 8, moa.MOA_F64_CRT_F32IN, pa, pa, pc, 0, 128, need,
+             None) == moa.MOA_ERR_ALIGN
+    assert f(0, 8, 8, moa.MOA_F64_CRT_F32IN, None, None, None, 0, None, 0, None) == moa.MOA_OK
+
+
 def test_empty_problems_are_noops(L):
     # m == 0 or p == 0: nothing to do, nothing launched (works without a GPU)
     assert moa.moa_gemm_ex(0, 5, 5, moa.MOA_F64, None, None, None, 0, None, 0, None) == moa.MOA_OK
