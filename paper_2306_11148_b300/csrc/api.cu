@@ -270,6 +270,11 @@ int moa_gemm_host(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* hA,
     void* dA = base + L.a_off;
     void* dB = base + L.b_off;
     void* dC = base + L.c_off;
+    // modular slices: B once, then A in bands whose uploads, GEMMs and
+    // downloads overlap
+    if (moa::is_crt(dt) && n > 0)
+        return moa::crt_gemm_host(m, n, p, dt, hA, hB, hC, slices, dA, dB, dC, base + L.g_off,
+                                  ws_bytes - L.g_off, s, stats);
     cudaError_t e = cudaSuccess;
     if (L.a_bytes) e = cudaMemcpyAsync(dA, hA, L.a_bytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && L.b_bytes) e = cudaMemcpyAsync(dB, hB, L.b_bytes, cudaMemcpyHostToDevice, s);

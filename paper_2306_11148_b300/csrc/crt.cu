@@ -427,8 +427,9 @@ struct CrtGProb {
 };
 
 struct CrtGemmArgs {
-    uint8_t* R;                   // residue planes: (l * ks + s) x m x ldr bytes
+    uint8_t* R;                   // residue planes: (l * ks + s) x r_rows x ldr bytes
     int64_t m, n, p, ldr;
+    int64_t r_rows;               // rows a residue plane holds (m, or more for a band of rows)
     int tiles_m, tiles_n, num_kb, group_m;
     int M, ks;
     float qf[kCrtMaxModuli];      // moduli and their rounded reciprocals
@@ -461,7 +462,7 @@ struct CrtUnit {
     int kb_lo, kb_hi;      // K blocks
     int bn;                // tile width (the MMA N extent)
     uint8_t* R;
-    int64_t m, p, ldr;
+    int64_t m, p, ldr, r_rows;
     int ks;
 };
 
@@ -486,6 +487,7 @@ __device__ __forceinline__ CrtUnit crt_resolve(const CrtGemmArgs& a, int u) {
         x.m = a.m;
         x.p = a.p;
         x.ldr = a.ldr;
+        x.r_rows = a.r_rows;
         x.ks = a.ks;
     } else {
         int lo = 0, hi = a.nprob - 1;
@@ -507,6 +509,7 @@ __device__ __forceinline__ CrtUnit crt_resolve(const CrtGemmArgs& a, int u) {
         x.m = pr.m;
         x.p = pr.p;
         x.ldr = pr.ldr;
+        x.r_rows = pr.m;
         x.ks = 1;
     }
     return x;
@@ -729,7 +732,8 @@ __global__ void __launch_bounds__(CrtCfg<BN>::kThreads, 1)
                     }
                     w[i] = word;
                 }
-                uint8_t* dst = x.R + ((static_cast<int64_t>(l) * x.ks + s) * x.m + row) * x.ldr + col0;
+                uint8_t* dst =
+                    x.R + ((static_cast<int64_t>(l) * x.ks + s) * x.r_rows + row) * x.ldr + col0;
                 if (col0 + 64 <= x.ldr) {
 #pragma unroll
                     for (int v = 0; v < 4; ++v)
@@ -1010,7 +1014,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(CrtPairCfg::kThreads
                     }
                     w[i] = word;
                 }
-                uint8_t* dst = args.R + (static_cast<int64_t>(l) * args.m + row) * args.ldr + col0;
+                uint8_t* dst = args.R + (static_cast<int64_t>(l) * args.r_rows + row) * args.ldr + col0;
                 if (col0 + 64 <= args.ldr) {
 #pragma unroll
                     for (int v = 0; v < 4; ++v)
@@ -1123,17 +1127,17 @@ __device__ __forceinline__ void crt_load(const uint8_t* __restrict__ R, int64_t 
 // 2^(eA_i + eB_j - 2t); the FP64 pattern is assembled with integer
 // operations only.  NL = 7 covers P < 2^112 (up to 14 moduli), NL = 8 the
 // rest.  The thread takes the groups of 4 outputs g0, g0 + gstep, ... of the
-// m x ceil(p / 4) groups.
+// m x ceil(p / 4) groups.  A residue plane holds r_rows >= m rows of ldr bytes.
 template <int NL>
 __device__ __forceinline__ void crt_recon_range(const uint8_t* __restrict__ R, int64_t m, int64_t p,
-                                                int64_t ldr, int ks, int t,
+                                                int64_t ldr, int64_t r_rows, int ks, int t,
                                                 const int* __restrict__ eA,
                                                 const int* __restrict__ eB,
                                                 double* __restrict__ C, int vec,
                                                 const CrtConsts& k, int64_t g0, int64_t gstep) {
     const int64_t gpr = (p + 3) / 4;
     const int64_t total = m * gpr;
-    const int64_t plane_stride = m * ldr;
+    const int64_t plane_stride = r_rows * ldr;
     const u128 P = (static_cast<u128>(k.P_hi) << 64) | k.P_lo;
     const u128 halfP = P >> 1;
     // 32-bit index arithmetic by reciprocal when the group count allows
@@ -1210,10 +1214,11 @@ __device__ __forceinline__ void crt_recon_range(const uint8_t* __restrict__ R, i
 
 template <int NL>
 __global__ void __launch_bounds__(256)
-    crt_recon_kernel(const uint8_t* __restrict__ R, int64_t m, int64_t p, int64_t ldr, int ks,
+    crt_recon_kernel(const uint8_t* __restrict__ R, int64_t m, int64_t p, int64_t ldr,
+                     int64_t r_rows, int ks,
                      const int* __restrict__ eA, const int* __restrict__ eB, double* __restrict__ C,
                      int vec, const CrtConsts k) {
-    crt_recon_range<NL>(R, m, p, ldr, ks, k.t, eA, eB, C, vec, k,
+    crt_recon_range<NL>(R, m, p, ldr, r_rows, ks, k.t, eA, eB, C, vec, k,
                         static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x,
                         static_cast<int64_t>(gridDim.x) * blockDim.x);
 }
@@ -1308,7 +1313,7 @@ __global__ void __launch_bounds__(256)
             dst[i] = src[i];
     }
     __syncthreads();
-    crt_recon_range<8>(x.R, x.m, x.p, x.ldr, 1, x.t, x.eA, x.eB, x.C, x.vec_c, k,
+    crt_recon_range<8>(x.R, x.m, x.p, x.ldr, x.m, 1, x.t, x.eA, x.eB, x.C, x.vec_c, k,
                        static_cast<int64_t>(b - x.rec_begin) * blockDim.x + threadIdx.x,
                        static_cast<int64_t>(x.rec_blocks) * blockDim.x);
 }
@@ -1540,83 +1545,126 @@ size_t crt_workspace_bytes(int64_t m, int64_t n, int64_t p, moa_dtype dt, int sl
     return crt_layout(m, n, p, M).total;
 }
 
-int crt_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const void* B, void* C,
-             int slices, void* ws, size_t ws_bytes, cudaStream_t s, moa_stats* st) {
-    const int M = crt_moduli_for(dt, n, slices);
-    if (M < 0) return fail(MOA_ERR_DTYPE, "modulus count not supported (8..16)");
-    const int t = crt_bits(n, M);
-    if (t < 1) return fail(MOA_ERR_ARG, "n too large for this modulus count");
-    const CrtLayout L = crt_layout(m, n, p, M);
-    if (ws_bytes < L.total) return fail(MOA_ERR_WORKSPACE, "workspace too small for crt mode");
+namespace {
+
+// One modular-slice GEMM's constants and workspace regions.
+struct CrtCall {
+    int64_t m, n, p;
+    int M, t;
+    bool f64in;
+    CrtLayout L;
+    __nv_bfloat16* a_pl;
+    __nv_bfloat16* b_pl;
+    int* eA;
+    int* eB;
+    void* cmax;
+    uint8_t* R;
+    int64_t a_plane, b_plane;   // elements a residue plane of A (m rows) and of B
+    int* status;
+    CrtPow2 pow2;
+};
+
+int crt_setup(int64_t m, int64_t n, int64_t p, moa_dtype dt, int slices, void* ws,
+              size_t ws_bytes, CrtCall& c) {
+    c.m = m;
+    c.n = n;
+    c.p = p;
+    c.M = crt_moduli_for(dt, n, slices);
+    if (c.M < 0) return fail(MOA_ERR_DTYPE, "modulus count not supported (8..16)");
+    c.t = crt_bits(n, c.M);
+    if (c.t < 1) return fail(MOA_ERR_ARG, "n too large for this modulus count");
+    c.L = crt_layout(m, n, p, c.M);
+    if (ws_bytes < c.L.total) return fail(MOA_ERR_WORKSPACE, "workspace too small for crt mode");
     if (ceil_div(n, 256) * ceil_div(p, 256) > (1L << 30))
         return fail(MOA_ERR_ARG, "n x p too large for the column-max grid");
-    int* status = launch_status_ptr();
-    if (!status) return MOA_ERR_CUDA;
+    c.status = launch_status_ptr();
+    if (!c.status) return MOA_ERR_CUDA;
     uint8_t* base = static_cast<uint8_t*>(ws);
-    auto* a_pl = reinterpret_cast<__nv_bfloat16*>(base + L.a_off);
-    auto* b_pl = reinterpret_cast<__nv_bfloat16*>(base + L.b_off);
-    int* eA = reinterpret_cast<int*>(base + L.ea_off);
-    int* eB = reinterpret_cast<int*>(base + L.eb_off);
-    void* cmax = base + L.cmax_off;
-    uint8_t* R = base + L.r_off;
-    const int64_t a_plane = m * L.lda;
-    const int64_t b_plane = n * L.ldb;
-    const bool f64in = dt == MOA_F64_CRT_F64IN;
-
-    CrtPow2 pow2{};
+    c.a_pl = reinterpret_cast<__nv_bfloat16*>(base + c.L.a_off);
+    c.b_pl = reinterpret_cast<__nv_bfloat16*>(base + c.L.b_off);
+    c.eA = reinterpret_cast<int*>(base + c.L.ea_off);
+    c.eB = reinterpret_cast<int*>(base + c.L.eb_off);
+    c.cmax = base + c.L.cmax_off;
+    c.R = base + c.L.r_off;
+    c.a_plane = m * c.L.lda;
+    c.b_plane = n * c.L.ldb;
+    c.f64in = dt == MOA_F64_CRT_F64IN;
     for (int l = 0; l < kCrtMaxModuli; ++l)
         for (int e2 = 0; e2 < kPow2Cols; ++e2)
-            pow2.v[l][e2] = static_cast<uint8_t>(
+            c.pow2.v[l][e2] = static_cast<uint8_t>(
                 (e2 < 128 ? (static_cast<u128>(1) << e2) % crt_mod(l) : 0));
-    // launch 1: clear the column maxima; 2: row exponents of A beside the
-    // column maxima of B; 3: residue planes of A and B
-    cudaError_t e = cudaMemsetAsync(cmax, 0, static_cast<size_t>(p) * 8, s);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(colmax)");
-    const int64_t rblocks = std::min<int64_t>(ceil_div(m, 8), 16L * num_sms());
+    return MOA_OK;
+}
+
+// Exponents and residue planes of rows [r0, r0 + mb) of A (A0: A's row r0;
+// mb = 0: none) and, when B is not NULL, of all of B (its column maxima
+// cleared first).  Two launches (a memset before them when B is taken).
+int crt_passes(const CrtCall& c, const void* A0, int64_t r0, int64_t mb, const void* B,
+               cudaStream_t s) {
+    const int64_t n = c.n, p = c.p;
+    if (B) {
+        cudaError_t e = cudaMemsetAsync(c.cmax, 0, static_cast<size_t>(p) * 8, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(colmax)");
+    }
+    const int64_t rblocks = mb > 0 ? std::min<int64_t>(ceil_div(mb, 8), 16L * num_sms()) : 0;
     const int64_t chunk = colmax_chunk(n, p, num_sms());
     const int64_t gx = ceil_div(p, 256);
-    const int64_t cblocks = gx * ceil_div(n, chunk);
-    const int ga = grid_for(a_plane / 4, 256);
-    const int gb = grid_for(b_plane / 4, 256);
-    if (f64in) {
-        const double* Ad = static_cast<const double*>(A);
+    const int64_t cblocks = B ? gx * ceil_div(n, chunk) : 0;
+    const int ga = mb > 0 ? grid_for(mb * c.L.lda / 4, 256) : 0;
+    const int gb = B ? grid_for(c.b_plane / 4, 256) : 0;
+    if (rblocks + cblocks == 0) return MOA_OK;
+    int* eA = c.eA + r0;
+    __nv_bfloat16* a_out = c.a_pl + r0 * c.L.lda;
+    if (c.f64in) {
+        const double* Ad = static_cast<const double*>(A0);
         const double* Bd = static_cast<const double*>(B);
-        auto* cm = static_cast<unsigned long long*>(cmax);
+        auto* cm = static_cast<unsigned long long*>(c.cmax);
         crt_exps_kernel<double><<<static_cast<unsigned>(rblocks + cblocks), 256, 0, s>>>(
-            Ad, m, n, Bd, p, chunk, eA, cm, status, static_cast<int>(rblocks), gx);
+            Ad, mb, n, Bd, p, chunk, eA, cm, c.status, static_cast<int>(rblocks), gx);
         crt_residue_kernel<double><<<ga + gb, 256, 0, s>>>(
-            Ad, m, n, L.lda, vec_rows(Ad, n, 2), eA, Bd, p, L.ldb, vec_rows(Bd, p, 2), eB, cm,
-            status, t, M, a_pl, a_plane, b_pl, b_plane, ga, pow2);
+            Ad, mb, n, c.L.lda, mb > 0 ? vec_rows(Ad, n, 2) : 0, eA, Bd, p, c.L.ldb,
+            B ? vec_rows(Bd, p, 2) : 0, c.eB, cm, c.status, c.t, c.M, a_out, c.a_plane, c.b_pl,
+            c.b_plane, ga, c.pow2);
     } else {
-        const float* Af = static_cast<const float*>(A);
+        const float* Af = static_cast<const float*>(A0);
         const float* Bf = static_cast<const float*>(B);
-        auto* cm = static_cast<unsigned int*>(cmax);
+        auto* cm = static_cast<unsigned int*>(c.cmax);
         crt_exps_kernel<float><<<static_cast<unsigned>(rblocks + cblocks), 256, 0, s>>>(
-            Af, m, n, Bf, p, chunk, eA, cm, status, static_cast<int>(rblocks), gx);
+            Af, mb, n, Bf, p, chunk, eA, cm, c.status, static_cast<int>(rblocks), gx);
         crt_residue_kernel<float><<<ga + gb, 256, 0, s>>>(
-            Af, m, n, L.lda, vec_rows(Af, n, 4), eA, Bf, p, L.ldb, vec_rows(Bf, p, 4), eB, cm,
-            status, t, M, a_pl, a_plane, b_pl, b_plane, ga, pow2);
+            Af, mb, n, c.L.lda, mb > 0 ? vec_rows(Af, n, 4) : 0, eA, Bf, p, c.L.ldb,
+            B ? vec_rows(Bf, p, 4) : 0, c.eB, cm, c.status, c.t, c.M, a_out, c.a_plane, c.b_pl,
+            c.b_plane, ga, c.pow2);
     }
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "crt pre-pass launch");
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MOA_OK : cuda_fail(e, "crt pre-pass launch");
+}
 
-    // launch 4: the residue GEMM
+// The residue GEMM and the reconstruction of rows [r0, r0 + mb) into C0
+// (C's row r0), from residue planes that crt_passes wrote.  Two launches.
+int crt_product(const CrtCall& c, int64_t r0, int64_t mb, double* C0, cudaStream_t s,
+                moa_stats* st) {
+    const int64_t n = c.n, p = c.p;
+    const int M = c.M;
+    const CrtLayout& L = c.L;
     const long sms = num_sms();
-    const int bn1 = crt_block_n(m, p, M, sms);
-    const int ks = std::min(L.ks_max, crt_ks(static_cast<long>(M) * ceil_div(m, kBM) *
+    const int bn1 = crt_block_n(mb, p, M, sms);
+    const int ks = std::min(L.ks_max, crt_ks(static_cast<long>(M) * ceil_div(mb, kBM) *
                                                  ceil_div(p, bn1),
                                              static_cast<int>(ceil_div(n, kBK)), sms));
     const long clusters = ks == 1 ? crt_pair_clusters() : 0;
-    const CrtTiles tiles = crt_tile_plan(m, n, p, M, ks, sms, clusters, l2_bytes());
+    const CrtTiles tiles = crt_tile_plan(mb, n, p, M, ks, sms, clusters, l2_bytes());
     const bool pair = tiles.rows == 2 * kBM;
     const int bn = tiles.bn;
+    uint8_t* R0 = c.R + r0 * L.ldr;
     CrtGemmArgs a{};
-    a.R = R;
-    a.m = m;
+    a.R = R0;
+    a.m = mb;
     a.n = n;
     a.p = p;
     a.ldr = L.ldr;
-    a.tiles_m = static_cast<int>(ceil_div(m, tiles.rows));
+    a.r_rows = c.m;
+    a.tiles_m = static_cast<int>(ceil_div(mb, tiles.rows));
     a.tiles_n = static_cast<int>(ceil_div(p, bn));
     a.num_kb = static_cast<int>(ceil_div(n, kBK));
     // the same number of tile rows a raster group either way: twice the
@@ -1630,40 +1678,149 @@ int crt_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const
         a.qinv[l] = 1.0f / static_cast<float>(crt_mod(l));
     }
     a.wait_limit_ns = wait_limit_ns();
-    a.status = status;
+    a.status = c.status;
     CUtensorMap tmA, tmB;
-    int rc = make_tmap_3d(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, a_pl, static_cast<uint64_t>(n),
-                          static_cast<uint64_t>(m), static_cast<uint64_t>(M),
-                          static_cast<uint64_t>(L.lda) * 2, static_cast<uint64_t>(a_plane) * 2,
-                          kBK, kBM);
+    int rc = make_tmap_3d(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, c.a_pl + r0 * L.lda,
+                          static_cast<uint64_t>(n), static_cast<uint64_t>(mb),
+                          static_cast<uint64_t>(M), static_cast<uint64_t>(L.lda) * 2,
+                          static_cast<uint64_t>(c.a_plane) * 2, kBK, kBM);
     if (rc != MOA_OK) return rc;
-    rc = make_tmap_3d(&tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, b_pl, static_cast<uint64_t>(p),
+    rc = make_tmap_3d(&tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, c.b_pl, static_cast<uint64_t>(p),
                       static_cast<uint64_t>(n), static_cast<uint64_t>(M),
-                      static_cast<uint64_t>(L.ldb) * 2, static_cast<uint64_t>(b_plane) * 2, 64, kBK);
+                      static_cast<uint64_t>(L.ldb) * 2, static_cast<uint64_t>(c.b_plane) * 2, 64,
+                      kBK);
     if (rc != MOA_OK) return rc;
     rc = pair ? launch_crt_pair(a, tmA, tmB, clusters, s, st)
          : bn == 256 ? launch_crt_gemm<256>(a, tmA, tmB, s, st)
                      : launch_crt_gemm<128>(a, tmA, tmB, s, st);
     if (rc != MOA_OK) return rc;
 
-    // launch 5: reconstruction
-    const CrtConsts k = crt_consts(M, t);
-    const int vec = (p % 2 == 0) && (reinterpret_cast<uintptr_t>(C) % 16 == 0);
-    const int rgrid = grid_for(m * ceil_div(p, 4), 256);
+    const CrtConsts k = crt_consts(M, c.t);
+    const int vec = (p % 2 == 0) && (reinterpret_cast<uintptr_t>(C0) % 16 == 0);
+    const int rgrid = grid_for(mb * ceil_div(p, 4), 256);
     if (M <= 14)   // P < 2^112: seven 16-bit limbs
-        crt_recon_kernel<7><<<rgrid, 256, 0, s>>>(R, m, p, L.ldr, a.ks, eA, eB,
-                                                  static_cast<double*>(C), vec, k);
+        crt_recon_kernel<7><<<rgrid, 256, 0, s>>>(R0, mb, p, L.ldr, c.m, a.ks, c.eA + r0, c.eB,
+                                                  C0, vec, k);
     else
-        crt_recon_kernel<8><<<rgrid, 256, 0, s>>>(R, m, p, L.ldr, a.ks, eA, eB,
-                                                  static_cast<double*>(C), vec, k);
-    e = cudaGetLastError();
+        crt_recon_kernel<8><<<rgrid, 256, 0, s>>>(R0, mb, p, L.ldr, c.m, a.ks, c.eA + r0, c.eB,
+                                                  C0, vec, k);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "crt reconstruction launch");
     if (st) {
         st->slices = M;
         st->products = M;
-        st->kernels = 4;   // the column-maximum clear is a memset
     }
     return MOA_OK;
+}
+
+}  // namespace
+
+int crt_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const void* B, void* C,
+             int slices, void* ws, size_t ws_bytes, cudaStream_t s, moa_stats* st) {
+    CrtCall c;
+    int rc = crt_setup(m, n, p, dt, slices, ws, ws_bytes, c);
+    if (rc != MOA_OK) return rc;
+    // launches: clear the column maxima (a memset), row exponents of A beside
+    // the column maxima of B, residue planes of A and B, the residue GEMM,
+    // the reconstruction
+    rc = crt_passes(c, A, 0, m, B, s);
+    if (rc != MOA_OK) return rc;
+    rc = crt_product(c, 0, m, static_cast<double*>(C), s, st);
+    if (rc != MOA_OK) return rc;
+    if (st) st->kernels = 4;
+    return MOA_OK;
+}
+
+int crt_gemm_host(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* hA, const void* hB,
+                  void* hC, int slices, void* dA, void* dB, void* dC, void* ws, size_t ws_bytes,
+                  cudaStream_t s, moa_stats* st) {
+    CrtCall c;
+    int rc = crt_setup(m, n, p, dt, slices, ws, ws_bytes, c);
+    if (rc != MOA_OK) return rc;
+    const size_t in_b = c.f64in ? 8 : 4;
+    // bands of about 2048 rows (at most 8), 256-row multiples
+    const int64_t want = std::min<int64_t>(8, std::max<int64_t>(1, ceil_div(m, 2048)));
+    const int64_t mb = round_up(ceil_div(m, want), 256);
+    const int64_t nb = ceil_div(m, mb);
+    cudaStream_t up = nullptr, down = nullptr;
+    std::vector<cudaEvent_t> ev;   // start, b_ready, a_ready[nb], c_ready[nb], up_done, down_done
+    auto mk = [&]() {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return false;
+        ev.push_back(e);
+        return true;
+    };
+    bool ok = cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&down, cudaStreamNonBlocking) == cudaSuccess;
+    for (int64_t i = 0; ok && i < 2 * nb + 4; ++i) ok = mk();
+    // Whatever happens below, the caller's stream ends after both helper
+    // streams' work, so the workspace and host buffers stay in use until then.
+    auto finish = [&](int status) {
+        if (up && ev.size() == static_cast<size_t>(2 * nb + 4)) {
+            cudaEventRecord(ev[2 * nb + 2], up);
+            cudaEventRecord(ev[2 * nb + 3], down);
+            cudaStreamWaitEvent(s, ev[2 * nb + 2], 0);
+            cudaStreamWaitEvent(s, ev[2 * nb + 3], 0);
+        }
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        if (up) cudaStreamDestroy(up);
+        if (down) cudaStreamDestroy(down);
+        return status;
+    };
+    if (!ok) return finish(fail(MOA_ERR_CUDA, "stream / event creation for moa_gemm_host"));
+    cudaEvent_t start = ev[0], b_ready = ev[1];
+    cudaEvent_t* a_ready = ev.data() + 2;
+    cudaEvent_t* c_ready = ev.data() + 2 + nb;
+    if (cudaEventRecord(start, s) != cudaSuccess || cudaStreamWaitEvent(up, start, 0) != cudaSuccess ||
+        cudaStreamWaitEvent(down, start, 0) != cudaSuccess)
+        return finish(fail(MOA_ERR_CUDA, "moa_gemm_host stream order"));
+    // uploads: all of B, then A band by band
+    if (cudaMemcpyAsync(dB, hB, static_cast<size_t>(n) * p * in_b, cudaMemcpyHostToDevice, up) !=
+            cudaSuccess ||
+        cudaEventRecord(b_ready, up) != cudaSuccess)
+        return finish(fail(MOA_ERR_CUDA, "cudaMemcpyAsync(B to the device)"));
+    for (int64_t i = 0; i < nb; ++i) {
+        const int64_t r0 = i * mb, rows = std::min(mb, m - r0);
+        const size_t off = static_cast<size_t>(r0) * n * in_b;
+        if (cudaMemcpyAsync(static_cast<uint8_t*>(dA) + off, static_cast<const uint8_t*>(hA) + off,
+                            static_cast<size_t>(rows) * n * in_b, cudaMemcpyHostToDevice,
+                            up) != cudaSuccess ||
+            cudaEventRecord(a_ready[i], up) != cudaSuccess)
+            return finish(fail(MOA_ERR_CUDA, "cudaMemcpyAsync(A band to the device)"));
+    }
+    // compute on the caller's stream: B's passes once, then band by band
+    int kernels = 0;
+    if (cudaStreamWaitEvent(s, b_ready, 0) != cudaSuccess)
+        return finish(fail(MOA_ERR_CUDA, "moa_gemm_host stream order"));
+    rc = crt_passes(c, nullptr, 0, 0, dB, s);
+    if (rc != MOA_OK) return finish(rc);
+    kernels += 2;
+    for (int64_t i = 0; i < nb; ++i) {
+        const int64_t r0 = i * mb, rows = std::min(mb, m - r0);
+        if (cudaStreamWaitEvent(s, a_ready[i], 0) != cudaSuccess)
+            return finish(fail(MOA_ERR_CUDA, "moa_gemm_host stream order"));
+        rc = crt_passes(c, static_cast<const uint8_t*>(dA) + static_cast<size_t>(r0) * n * in_b,
+                        r0, rows, nullptr, s);
+        if (rc != MOA_OK) return finish(rc);
+        double* C0 = static_cast<double*>(dC) + r0 * p;
+        rc = crt_product(c, r0, rows, C0, s, st);
+        if (rc != MOA_OK) return finish(rc);
+        kernels += 4;
+        if (cudaEventRecord(c_ready[i], s) != cudaSuccess)
+            return finish(fail(MOA_ERR_CUDA, "moa_gemm_host stream order"));
+        // download of the band as soon as it is reconstructed
+        if (cudaStreamWaitEvent(down, c_ready[i], 0) != cudaSuccess ||
+            cudaMemcpyAsync(static_cast<double*>(hC) + r0 * p, C0,
+                            static_cast<size_t>(rows) * p * 8, cudaMemcpyDeviceToHost,
+                            down) != cudaSuccess)
+            return finish(fail(MOA_ERR_CUDA, "cudaMemcpyAsync(C band to the host)"));
+    }
+    if (st) {
+        st->kernels = kernels;
+        st->slices = c.M;
+        st->products = c.M;
+    }
+    return finish(MOA_OK);
 }
 
 // ---------------------------------------------------------------- grouped host side

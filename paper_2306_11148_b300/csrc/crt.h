@@ -26,6 +26,16 @@ size_t crt_workspace_bytes(int64_t m, int64_t n, int64_t p, moa_dtype dt, int sl
 int crt_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const void* B, void* C,
              int slices, void* ws, size_t ws_bytes, cudaStream_t s, moa_stats* st);
 
+// moa_gemm_host for the modular-slice modes (m, n, p > 0): host A, B, C;
+// device copies dA, dB, dC; ws / ws_bytes as for crt_gemm.  B is uploaded
+// and its passes run once; then A's rows go through in bands of about 2048
+// rows, each band's upload, passes + GEMM + reconstruction and download on
+// their own streams, so that they overlap; `s` ends after all of it.  The
+// result equals crt_gemm's bit for bit.
+int crt_gemm_host(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* hA, const void* hB,
+                  void* hC, int slices, void* dA, void* dB, void* dC, void* ws, size_t ws_bytes,
+                  cudaStream_t s, moa_stats* st);
+
 // Grouped calls (moa_gemm_grouped): the modular-slice problems of a call that
 // this path takes (positive sizes, 16-byte aligned A and B, 8-byte aligned C)
 // run as one exponent and one residue launch per input type, ONE persistent

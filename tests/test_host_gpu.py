@@ -48,6 +48,29 @@ def test_host_entry_modular_slices_match_the_oracle():
     assert np.array_equal(C.numpy(), oracle.crt_gemm(A.double().numpy(), B.double().numpy(), 14))
 
 
+@pytest.mark.parametrize("shape", [(5000, 700, 300), (2049, 1030, 514), (4100, 3000, 64)],
+                         ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("dt", [moa.MOA_F64_CRT_F32IN, moa.MOA_F64_CRT_F64IN],
+                         ids=lambda d: NAMES[d])
+def test_host_entry_bands_equal_device_entry(dt, shape):
+    """Modular slices with host buffers run A in bands of about 2048 rows
+    (uploads, band GEMMs and downloads overlapping on their own streams):
+    3, 2 and 2 bands here, the last one ragged; the result equals the
+    device-side call bit for bit, and sampled rows equal the exact integer
+    product."""
+    m, n, p = shape
+    A, B = _host_pair(m, n, p, dt, seed=m + p, pinned=True)
+    C, st = moa.gemm_host(A, B, dt, stats=True)
+    moa.sync_status()
+    assert st.kernels > 4
+    want = moa.gemm(A.cuda(), B.cuda(), dt)
+    moa.sync_status()
+    assert torch.equal(C, want.cpu())
+    rows = inputs.sample_rows(m, 4, seed=3)
+    exact = oracle.crt_gemm(A.double().numpy()[rows], B.double().numpy(), 14)
+    assert np.array_equal(C.numpy()[rows], exact)
+
+
 def test_host_entry_k_zero_gives_zeros():
     A = torch.zeros((5, 0), dtype=torch.float32)
     B = torch.zeros((0, 7), dtype=torch.float32)
