@@ -1145,6 +1145,20 @@ def bench_crt_tiles(stream, energy, sizes=(2048, 4096, 6144, 8192, 12288), round
     return out
 
 
+def fp64_rates(stream):
+    """This device's FP64 rates (TFLOP/s) from the library's diagnostic:
+    independent fused multiply-adds on the CUDA cores, and independent
+    warp-level FP64 MMAs (the FP64 tensor path)."""
+    import ctypes
+    from paper_2306_11148_b300 import moa
+    out = []
+    for kind in (0, 1):
+        v = ctypes.c_double(0.0)
+        moa.check(moa.lib().moa_measure_fp64_rate(kind, int(stream.cuda_stream), ctypes.byref(v)))
+        out.append(v.value)
+    return tuple(out)
+
+
 def bench_library_rates(N=8192, reps=10):
     """Dense GEMM rates of the vendor library (cuBLAS through torch) per data
     type on this GPU, next to this library's dense kernels: context for the
@@ -1211,6 +1225,10 @@ def bench_library_rates(N=8192, reps=10):
     out["moa_bf16"] = rate(N, best_ms(lambda: moa.gemm(a16, b16, moa.MOA_BF16, C=c32), reps))
     c64 = torch.empty((n64, n64), dtype=torch.float64, device="cuda")
     out["moa_fp64_n2048"] = rate(n64, best_ms(lambda: moa.gemm(a64, b64, moa.MOA_F64, C=c64), 3))
+    # the device's own FP64 rates (library diagnostic kernels)
+    fma, mma = fp64_rates(torch.cuda.current_stream())
+    out["measured_fp64_fma"] = fma
+    out["measured_fp64_mma"] = mma
     return out
 
 
@@ -1504,6 +1522,15 @@ def main():
                 modes[m2] = r
             except Exception as e:  # report, do not hide
                 modes[m2] = {"error": str(e)}
+        # the native FP64 GEMM against this device's measured FP64 rates
+        if "tflops" in modes.get("f64", {}):
+            try:
+                fma, mma = fp64_rates(stream)
+                modes["f64"].update({"fp64_fma_tflops_measured": fma,
+                                     "fp64_mma_tflops_measured": mma,
+                                     "frac_of_measured_fp64_fma": modes["f64"]["tflops"] / fma})
+            except Exception as e:  # report, do not hide
+                modes["f64"]["fp64_rates"] = {"error": str(e)}
 
         # the outer-product family's no-reduction members (HBM roofline)
         try:

@@ -428,6 +428,16 @@ int moa_profile_events(void* start_event, void* stop_event);
  * Diagnostic only; the paper has no counterpart. */
 int moa_selftest_wait_timeout(uint64_t limit_ns, void* stream);
 
+/* Measured FP64 rate of this device (the roofline denominator of the native
+ * FP64 mode): kind 0 = independent fused multiply-adds on the CUDA cores,
+ * kind 1 = independent warp-level FP64 MMAs (mma.sync m16n8k4, the FP64
+ * tensor path).  Runs a short warm-up launch and five launches of about
+ * 1.5e10 flops (a GEMM kernel's length) on `stream`, each timed with CUDA
+ * events (synchronous: returns after them), and writes the best rate in
+ * TFLOP/s to *tflops.  Allocates nothing.  MOA_ERR_ARG for another kind or a
+ * NULL tflops.  Diagnostic only. */
+int moa_measure_fp64_rate(int kind, void* stream, double* tflops);
+
 /* Library version string. */
 const char* moa_version(void);
 

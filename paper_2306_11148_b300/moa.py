@@ -153,6 +153,7 @@ EXPORTS = {
     "moa_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_uint64, _vp]),
     "moa_set_block_n": (ctypes.c_int, [ctypes.c_int]),
     "moa_set_block_m": (ctypes.c_int, [ctypes.c_int]),
+    "moa_measure_fp64_rate": (ctypes.c_int, [ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_double)]),
     "moa_kronecker": (ctypes.c_int, [_i64, _i64, _i64, _i64, ctypes.c_int, _vp, _vp, _vp, _vp]),
     "moa_hadamard": (ctypes.c_int, [_i64, _i64, ctypes.c_int, _vp, _vp, _vp, _vp]),
     "moa_product": (ctypes.c_int, [ctypes.c_int, _i64, _i64, _i64, _i64, ctypes.c_int, _vp, _vp,

@@ -152,6 +152,12 @@ def test_host_entry_workspace_and_argument_errors(L):
     assert f(0, 8, 8, moa.MOA_F64_CRT_F32IN, None, None, None, 0, None, 0, None) == moa.MOA_OK
 
 
+def test_fp64_rate_argument_errors(L):
+    out = ctypes.c_double(0.0)
+    assert L.moa_measure_fp64_rate(2, None, ctypes.byref(out)) == moa.MOA_ERR_ARG
+    assert L.moa_measure_fp64_rate(0, None, None) == moa.MOA_ERR_ARG
+
+
 def test_empty_problems_are_noops(L):
     # m == 0 or p == 0: nothing to do, nothing launched (works without a GPU)
     assert moa.moa_gemm_ex(0, 5, 5, moa.MOA_F64, None, None, None, 0, None, 0, None) == moa.MOA_OK
