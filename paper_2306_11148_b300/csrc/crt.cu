@@ -64,8 +64,8 @@ using i128 = __int128;
 struct CrtConsts {
     int M;                               // moduli in use
     int t;                               // operand bits
-    uint32_t w[kCrtMaxModuli][8];        // CRT weights W_l = (P / q_l) * ((P / q_l)^-1 mod q_l)
-                                         //   mod P, as 16-bit limbs, least significant first
+    uint32_t w[kCrtMaxModuli][4];        // CRT weights W_l = (P / q_l) * ((P / q_l)^-1 mod q_l)
+                                         //   mod P, as 32-bit limbs, least significant first
     uint64_t P_lo, P_hi;                 // P = prod q_l
     int sP;                              // quotient estimate: floor(X / 2^sP) * kq ~ X / P,
     float kq;                            //   sP = bit length of P - 32, kq = 2^sP / P rounded
@@ -107,7 +107,7 @@ CrtConsts crt_consts(int M, int t) {
         const int64_t Ml_mod = static_cast<int64_t>(Ml % crt_mod(l));
         const int64_t y = inv_mod(Ml_mod, crt_mod(l));
         const u128 W = (Ml * static_cast<u128>(y)) % P;   // Ml * y < P * 256 < 2^128
-        for (int k = 0; k < 8; ++k) c.w[l][k] = static_cast<uint32_t>(W >> (16 * k)) & 0xFFFFu;
+        for (int k = 0; k < 4; ++k) c.w[l][k] = static_cast<uint32_t>(W >> (32 * k));
     }
     int bits = 0;
     while (bits < 128 && (P >> bits) != 0) ++bits;
@@ -1075,20 +1075,20 @@ __device__ __forceinline__ double u128_to_double_scaled(uint64_t hi, uint64_t lo
 
 // Residues of modulus L for 4 consecutive outputs (w: their bytes, summed
 // over the K slices and reduced when there are several), then X += r W_L as
-// NL 16-bit limbs in 32-bit sums (r < 2^8: each product is below 2^24, a sum
-// of 16 below 2^28).
-template <int L, int NL>
+// four 32-bit limbs, each product (r < 2^8 times a limb < 2^32) added in a
+// 64-bit sum by one wide multiply-add (16 of them stay below 2^44).
+template <int L>
 __device__ __forceinline__ void crt_accumulate(const uint32_t (&w)[kCrtMaxModuli], int M,
-                                               const CrtConsts& k, uint32_t (&acc)[4][NL]) {
+                                               const CrtConsts& k, uint64_t (&acc)[4][4]) {
     if constexpr (L < kCrtMaxModuli) {
         if (L >= M) return;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const uint32_t r = (w[L] >> (8 * e)) & 0xFFu;
 #pragma unroll
-            for (int j = 0; j < NL; ++j) acc[e][j] += r * k.w[L][j];
+            for (int j = 0; j < 4; ++j) acc[e][j] += static_cast<uint64_t>(r) * k.w[L][j];
         }
-        crt_accumulate<L + 1, NL>(w, M, k, acc);
+        crt_accumulate<L + 1>(w, M, k, acc);
     }
 }
 
@@ -1118,17 +1118,16 @@ __device__ __forceinline__ void crt_load(const uint8_t* __restrict__ R, int64_t 
 }
 
 // C[i, j] for 4 consecutive j per thread: r_l = sum_s R[l, s, i, j] mod q_l;
-// X = sum_l r_l W_l (NL 16-bit limbs summed in 32 bits, carried into 16-bit
-// digits; X < 2^12 P and P < 2^126, so X has at most 138 bits: digits 0..7
-// hold X mod 2^128 and the carry out of digit 7 its top bits); the quotient
-// q = floor(X / P) estimated in FP32 from floor(X / 2^sP) (off by at most
-// one); C' = X - q P (exact modulo 2^128, and within (-P, 2P)) corrected into
+// X = sum_l r_l W_l (four 64-bit limb sums, then carried into 32-bit words;
+// X < 2^12 P and P < 2^126, so X has at most 138 bits: words 0..3 hold X mod
+// 2^128 and the carry out of word 3 its top bits); the quotient q =
+// floor(X / P) estimated in FP32 from floor(X / 2^sP) (off by at most one);
+// C' = X - q P (exact modulo 2^128, and within (-P, 2P)) corrected into
 // [0, P), then into [-P/2, P/2), rounded once and scaled by
 // 2^(eA_i + eB_j - 2t); the FP64 pattern is assembled with integer
-// operations only.  NL = 7 covers P < 2^112 (up to 14 moduli), NL = 8 the
-// rest.  The thread takes the groups of 4 outputs g0, g0 + gstep, ... of the
-// m x ceil(p / 4) groups.  A residue plane holds r_rows >= m rows of ldr bytes.
-template <int NL>
+// operations only.  The thread takes the groups of 4 outputs g0, g0 + gstep,
+// ... of the m x ceil(p / 4) groups.  A residue plane holds r_rows >= m rows
+// of ldr bytes.
 __device__ __forceinline__ void crt_recon_range(const uint8_t* __restrict__ R, int64_t m, int64_t p,
                                                 int64_t ldr, int64_t r_rows, int ks, int t,
                                                 const int* __restrict__ eA,
@@ -1156,26 +1155,22 @@ __device__ __forceinline__ void crt_recon_range(const uint8_t* __restrict__ R, i
         }
         uint32_t w[kCrtMaxModuli];
         crt_load<0>(R + i * ldr + j0, plane_stride, ks, k.M, w);
-        uint32_t acc[4][NL] = {};
-        crt_accumulate<0, NL>(w, k.M, k, acc);
+        uint64_t acc[4][4] = {};
+        crt_accumulate<0>(w, k.M, k, acc);
         const int ea = eA[i] - 2 * t;
         uint64_t out[4];   // FP64 bit patterns
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            // 16-bit digits with carries, packed two to a 32-bit word; the
-            // final carry holds X's bits from 128 up
-            uint32_t d[8];
-            uint32_t c = 0;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const uint32_t v = (j < NL ? acc[e][j] : 0u) + c;   // < 2^28 + 2^13
-                d[j] = v & 0xFFFFu;
-                c = v >> 16;
-            }
-            const uint64_t lo64 = static_cast<uint64_t>(d[0] | (d[1] << 16)) |
-                                  (static_cast<uint64_t>(d[2] | (d[3] << 16)) << 32);
-            const uint64_t hi64 = static_cast<uint64_t>(d[4] | (d[5] << 16)) |
-                                  (static_cast<uint64_t>(d[6] | (d[7] << 16)) << 32);
+            // X = a0 + a1 2^32 + a2 2^64 + a3 2^96 carried into 32-bit words
+            // (every partial sum below 2^45); c holds X's bits from 128 up
+            const uint64_t a0 = acc[e][0], a1 = acc[e][1], a2 = acc[e][2], a3 = acc[e][3];
+            uint64_t v = (a0 >> 32) + (a1 & 0xFFFFFFFFull);
+            const uint64_t lo64 = (a0 & 0xFFFFFFFFull) | (v << 32);
+            v = (v >> 32) + (a1 >> 32) + (a2 & 0xFFFFFFFFull);
+            const uint32_t w2 = static_cast<uint32_t>(v);
+            v = (v >> 32) + (a2 >> 32) + (a3 & 0xFFFFFFFFull);
+            const uint64_t hi64 = w2 | (v << 32);
+            const uint32_t c = static_cast<uint32_t>((v >> 32) + (a3 >> 32));
             // floor(X / 2^sP) < 2^44 (sP >= 64 when P >= 2^96; the carry c is X >> 128)
             uint64_t top;
             if (k.sP >= 64) {
@@ -1184,7 +1179,13 @@ __device__ __forceinline__ void crt_recon_range(const uint8_t* __restrict__ R, i
             } else {
                 top = (hi64 << (64 - k.sP)) | (lo64 >> k.sP);   // X < 2^76 here: no carry
             }
-            const uint32_t qe = static_cast<uint32_t>(__float2int_rd(__fmul_rn(__ull2float_rn(top), k.kq)));
+            // fl(top) without a 64-bit conversion (those run on the FP64
+            // pipe): top < 2^44 = hi 2^21 + lo with hi < 2^23, lo < 2^21,
+            // both exact as floats, joined by one rounding
+            const float top_f = __fmaf_rn(small_uint_to_float(static_cast<uint32_t>(top >> 21)),
+                                          2097152.0f,
+                                          small_uint_to_float(static_cast<uint32_t>(top) & 0x1FFFFFu));
+            const uint32_t qe = static_cast<uint32_t>(__float2int_rd(__fmul_rn(top_f, k.kq)));
             // X - qe P modulo 2^128: the true value lies in (-P, 2P), inside the
             // signed 128-bit range
             const uint64_t ql = qe * k.P_lo;
@@ -1212,13 +1213,12 @@ __device__ __forceinline__ void crt_recon_range(const uint8_t* __restrict__ R, i
     }
 }
 
-template <int NL>
 __global__ void __launch_bounds__(256)
     crt_recon_kernel(const uint8_t* __restrict__ R, int64_t m, int64_t p, int64_t ldr,
                      int64_t r_rows, int ks,
                      const int* __restrict__ eA, const int* __restrict__ eB, double* __restrict__ C,
                      int vec, const CrtConsts k) {
-    crt_recon_range<NL>(R, m, p, ldr, r_rows, ks, k.t, eA, eB, C, vec, k,
+    crt_recon_range(R, m, p, ldr, r_rows, ks, k.t, eA, eB, C, vec, k,
                         static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x,
                         static_cast<int64_t>(gridDim.x) * blockDim.x);
 }
@@ -1313,7 +1313,7 @@ __global__ void __launch_bounds__(256)
             dst[i] = src[i];
     }
     __syncthreads();
-    crt_recon_range<8>(x.R, x.m, x.p, x.ldr, x.m, 1, x.t, x.eA, x.eB, x.C, x.vec_c, k,
+    crt_recon_range(x.R, x.m, x.p, x.ldr, x.m, 1, x.t, x.eA, x.eB, x.C, x.vec_c, k,
                        static_cast<int64_t>(b - x.rec_begin) * blockDim.x + threadIdx.x,
                        static_cast<int64_t>(x.rec_blocks) * blockDim.x);
 }
@@ -1698,12 +1698,8 @@ int crt_product(const CrtCall& c, int64_t r0, int64_t mb, double* C0, cudaStream
     const CrtConsts k = crt_consts(M, c.t);
     const int vec = (p % 2 == 0) && (reinterpret_cast<uintptr_t>(C0) % 16 == 0);
     const int rgrid = grid_for(mb * ceil_div(p, 4), 256);
-    if (M <= 14)   // P < 2^112: seven 16-bit limbs
-        crt_recon_kernel<7><<<rgrid, 256, 0, s>>>(R0, mb, p, L.ldr, c.m, a.ks, c.eA + r0, c.eB,
-                                                  C0, vec, k);
-    else
-        crt_recon_kernel<8><<<rgrid, 256, 0, s>>>(R0, mb, p, L.ldr, c.m, a.ks, c.eA + r0, c.eB,
-                                                  C0, vec, k);
+    crt_recon_kernel<<<rgrid, 256, 0, s>>>(R0, mb, p, L.ldr, c.m, a.ks, c.eA + r0, c.eB, C0, vec,
+                                           k);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "crt reconstruction launch");
     if (st) {
