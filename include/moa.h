@@ -178,7 +178,12 @@ size_t moa_gemm_grouped_workspace_size(int count, const moa_gemm_desc* descs);
  * residue launch per input type over all of them, ONE persistent residue-GEMM
  * launch over every (problem, modulus, tile) unit (longest K first), one
  * reconstruction launch; each result is bit-identical to the problem run
- * alone.  Other problems (other dtypes, unaligned pitches) run one by one on
+ * alone.  FP32-accuracy split problems (MOA_F32_SPLIT, 16-byte aligned A and
+ * B) that a lone call would run without split K (enough tiles for the SMs)
+ * share one slice pre-pass launch and ONE persistent slice-GEMM launch over
+ * all their tiles (longest K first, each problem at its lone call's tile
+ * width), bit-identical to the lone calls.  Other problems (other dtypes,
+ * unaligned pitches, few-tile long-K FP32-accuracy problems) run one by one on
  * the same stream.  A call that repeats the
  * previous call of the same thread (identical descriptors, same `ws`, same
  * device) reuses the tables already in `ws`, so callers must not modify `ws`
@@ -187,6 +192,15 @@ size_t moa_gemm_grouped_workspace_size(int count, const moa_gemm_desc* descs);
  * bad descriptor (nothing launched), MOA_ERR_WORKSPACE if ws is too small. */
 int moa_gemm_grouped(int count, const moa_gemm_desc* descs,
                      void* ws, size_t ws_bytes, void* stream);
+
+/* The path a problem takes in moa_gemm_grouped (and in the server's grouped
+ * calls): MOA_GROUPED_BF16 (the persistent BF16 launch), MOA_GROUPED_CRT (the
+ * grouped modular-slice launches), MOA_GROUPED_F32_SPLIT (the grouped
+ * FP32-accuracy split launches) or MOA_GROUPED_ALONE (its own launches on the
+ * same stream).  Host-side only.  MOA_ERR_ARG for a NULL descriptor. */
+enum { MOA_GROUPED_ALONE = 0, MOA_GROUPED_BF16 = 1, MOA_GROUPED_CRT = 2,
+       MOA_GROUPED_F32_SPLIT = 3 };
+int moa_grouped_path(const moa_gemm_desc* d);
 
 /* ---------------------------------------------------------------------- */
 /* The inner/outer-product family as one algorithm (paper's Appendix)       */
@@ -345,8 +359,9 @@ int moa_serve_create(const moa_serve_config* cfg, moa_server** out);
  * stays resident and valid until the ticket completes).  Non-blocking.  A
  * scheduler thread admits queued requests in FIFO order while fewer than
  * max_inflight run and the request's workspace fits in the free arena; the
- * requests admitted in one pass form a batch (its BF16 and modular-slice
- * requests share one grouped call) spread over the server's streams, so requests
+ * requests admitted in one pass form a batch (its BF16 requests and its
+ * modular-slice and FP32-accuracy split requests of at most 2 GFLOP share one
+ * grouped call) spread over the server's streams, so requests
  * arriving while others run overlap with them on the device.  Returns MOA_OK
  * (queued), MOA_ERR_BUDGET (the workspace alone exceeds the arena),
  * MOA_ERR_BUSY (queue full), MOA_ERR_ARG / MOA_ERR_DTYPE (bad descriptor).

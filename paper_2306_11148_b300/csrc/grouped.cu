@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "crt.h"
+#include "split.h"
 #include "epilogue.cuh"
 #include "internal.h"
 #include "ptx.cuh"
@@ -466,11 +467,12 @@ size_t grouped_main_bytes(int count, const moa_gemm_desc* d) {
 size_t grouped_workspace(int count, const moa_gemm_desc* d) {
     size_t side = 0;
     for (int g = 0; g < count; ++g)
-        if (!persistent_ok(d[g]) && !crt_grouped_ok(d[g]) && d[g].m >= 0 && d[g].n >= 0 &&
-            d[g].p >= 0)
+        if (!persistent_ok(d[g]) && !crt_grouped_ok(d[g]) && !split_grouped_ok(d[g]) &&
+            d[g].m >= 0 && d[g].n >= 0 && d[g].p >= 0)
             side = std::max(side, workspace_bytes(d[g].m, d[g].n, d[g].p, d[g].dt, 0));
     const size_t crt = crt_grouped_workspace(count, d);
-    return grouped_main_bytes(count, d) + (crt + 255) / 256 * 256 + side;
+    const size_t spl = split_grouped_workspace(count, d);
+    return grouped_main_bytes(count, d) + (crt + 255) / 256 * 256 + (spl + 255) / 256 * 256 + side;
 }
 
 int grouped_launch(int count, const moa_gemm_desc* d, void* ws, size_t ws_bytes, cudaStream_t s,
@@ -592,11 +594,19 @@ int grouped_launch(int count, const moa_gemm_desc* d, void* ws, size_t ws_bytes,
                                           crt_bytes, s, status_of);
         if (rc != MOA_OK) return rc;
     }
+    // FP32-accuracy split problems: one pre-pass launch and one persistent GEMM
+    const size_t spl_bytes = (split_grouped_workspace(count, d) + 255) / 256 * 256;
+    if (spl_bytes > 0) {
+        const int rc = split_grouped_launch(count, d,
+                                            static_cast<uint8_t*>(ws) + main_bytes + crt_bytes,
+                                            spl_bytes, s, status_of);
+        if (rc != MOA_OK) return rc;
+    }
     // problems outside the persistent paths, one by one on the same stream
-    uint8_t* side = static_cast<uint8_t*>(ws) + main_bytes + crt_bytes;
-    const size_t side_bytes = ws ? ws_bytes - main_bytes - crt_bytes : 0;
+    uint8_t* side = static_cast<uint8_t*>(ws) + main_bytes + crt_bytes + spl_bytes;
+    const size_t side_bytes = ws ? ws_bytes - main_bytes - crt_bytes - spl_bytes : 0;
     for (int g = 0; g < count; ++g) {
-        if (persistent_ok(d[g]) || crt_grouped_ok(d[g])) continue;
+        if (persistent_ok(d[g]) || crt_grouped_ok(d[g]) || split_grouped_ok(d[g])) continue;
         const int rc = gemm_ex(d[g].m, d[g].n, d[g].p, d[g].dt, d[g].A, d[g].B, d[g].C, 0,
                                side_bytes ? side : nullptr, side_bytes, s, nullptr);
         if (rc != MOA_OK) return rc;
@@ -611,6 +621,14 @@ extern "C" {
 int moa_grouped_block_n(int64_t m, int64_t n, int64_t p) {
     if (m <= 0 || n <= 0 || p <= 0) return 0;
     return moa::grouped_plan_bn(m, n, p);
+}
+
+int moa_grouped_path(const moa_gemm_desc* d) {
+    if (d == nullptr) return moa::fail(MOA_ERR_ARG, "descriptor is NULL");
+    if (moa::persistent_ok(*d)) return MOA_GROUPED_BF16;
+    if (moa::crt_grouped_ok(*d)) return MOA_GROUPED_CRT;
+    if (moa::split_grouped_ok(*d)) return MOA_GROUPED_F32_SPLIT;
+    return MOA_GROUPED_ALONE;
 }
 
 size_t moa_gemm_grouped_workspace_size(int count, const moa_gemm_desc* d) {

@@ -43,6 +43,7 @@
 #include <vector>
 
 #include "crt.h"
+#include "split.h"
 #include "internal.h"
 #include "ptx.cuh"
 
@@ -307,15 +308,16 @@ void scheduler(moa_server* s) {
         ++s->n_batches;
         s->n_admitted += batch.size();
 
-        // BF16 and modular-slice requests of the batch share one grouped call
-        // (one persistent launch per kind); its workspace gets its own arena
-        // block, released with the lead request (all of them finish with the
-        // same kernels).
-        // Only small modular-slice requests join the group: a request grouped
+        // BF16, modular-slice and FP32-accuracy split requests of the batch
+        // share one grouped call (one persistent launch per kind); its
+        // workspace gets its own arena block, released with the lead request
+        // (all of them finish with the same kernels).
+        // Only small split-precision requests join the group: a request grouped
         // with a large one would complete only when the large one does.
         auto groupable = [](const moa_gemm_desc& d) {
             return d.dt == MOA_BF16 ||
-                   (crt_grouped_ok(d) && 2.0 * d.m * d.n * d.p <= kServeGroupFlops);
+                   ((crt_grouped_ok(d) || split_grouped_ok(d)) &&
+                    2.0 * d.m * d.n * d.p <= kServeGroupFlops);
         };
         std::vector<moa_gemm_desc> bf;
         std::vector<size_t> bf_idx;

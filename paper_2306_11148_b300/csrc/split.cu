@@ -35,6 +35,8 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
+#include <vector>
 
 #include "fpbits.cuh"
 #include "internal.h"
@@ -131,6 +133,37 @@ __global__ void split3_pair_kernel(const float* __restrict__ A, int64_t m, int64
         split3_part(A, m, n, lda, a_out, a_plane, va, status, blockIdx.x, ga);
     else
         split3_part(B, n, p, ldb, b_out, b_plane, vb, status, blockIdx.x - ga, gridDim.x - ga);
+}
+
+// One problem of a grouped FP32-accuracy split call, as the pre-pass sees it:
+// its operands, slice planes and the blocks [begin, begin + ga + gb) of the
+// launch (the first ga split A, the rest B).
+struct SplitGPass {
+    const float* A;
+    const float* B;
+    __nv_bfloat16* a_sl;
+    __nv_bfloat16* b_sl;
+    int64_t m, n, p, lda, ldb, a_plane, b_plane;
+    int* status;   // where this problem's non-finite inputs are recorded
+    int va, vb, ga, gb, begin, pad;
+};
+
+// The slice pre-pass of every problem of a grouped call in one launch (the
+// problem of block b by binary search over the problems' first blocks).
+__global__ void __launch_bounds__(256)
+    split3_g_kernel(const SplitGPass* __restrict__ pr, int count) {
+    const int b = static_cast<int>(blockIdx.x);
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pr[mid].begin <= b) lo = mid; else hi = mid - 1;
+    }
+    const SplitGPass& x = pr[lo];
+    const int local = b - x.begin;
+    if (local < x.ga)
+        split3_part(x.A, x.m, x.n, x.lda, x.a_sl, x.a_plane, x.va, x.status, local, x.ga);
+    else if (local < x.ga + x.gb)
+        split3_part(x.B, x.n, x.p, x.ldb, x.b_sl, x.b_plane, x.vb, x.status, local - x.ga, x.gb);
 }
 
 // Digit generator of one element: D = round_half_even(x * 2^k) written as
@@ -626,7 +659,55 @@ struct SplitArgs {
     long long* fine;
     // FP32-accuracy split K: slice s's partial tile at part[s * m * p + i * p + j]
     float* part;
+    // grouped FP32-accuracy launches: the problems (sorted by unit_begin) and
+    // their TMA descriptors (A slices, B slices per problem, global memory)
+    const struct SplitGProb* probs;
+    const CUtensorMap* maps;
+    int nprob;
+    int num_units;
 };
+
+// One problem of a grouped FP32-accuracy split GEMM (device table).
+struct SplitGProb {
+    float* C;
+    int64_t m, p;
+    int tiles_m, tiles_n, num_kb, group_m;
+    int bn;                 // tile width (the MMA N extent): 128 or 256
+    int vec_ok;             // C rows allow 16-byte stores
+    int unit_begin, pad;    // first unit (tile) of the problem in the work list
+};
+
+// What the roles need about a unit of a grouped launch: the problem and the
+// tile (one K slice, every level).
+struct SplitGUnit {
+    int g, tm, tn, bn, vec_ok;
+    int64_t m, p;
+    float* C;
+};
+__device__ __forceinline__ SplitGUnit split_gresolve(const SplitArgs& a, int u) {
+    int lo = 0, hi = a.nprob - 1;
+    while (lo < hi) {   // last problem with unit_begin <= u
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.probs[mid].unit_begin <= u) lo = mid; else hi = mid - 1;
+    }
+    const SplitGProb& pr = a.probs[lo];
+    SplitGUnit x;
+    x.g = lo;
+    const int t = u - pr.unit_begin;
+    const int per_group = pr.group_m * pr.tiles_n;
+    const int gi = t / per_group;
+    const int first_m = gi * pr.group_m;
+    const int gsize = min(pr.tiles_m - first_m, pr.group_m);
+    const int r = t - gi * per_group;
+    x.tm = first_m + r % gsize;
+    x.tn = r / gsize;
+    x.bn = pr.bn;
+    x.vec_ok = pr.vec_ok;
+    x.m = pr.m;
+    x.p = pr.p;
+    x.C = pr.C;
+    return x;
+}
 
 // Work unit u: tile t and the K blocks [kb_lo, kb_hi) of its K slice (SK:
 // the split-K kernel variant; without it every unit is a whole tile).
@@ -844,10 +925,15 @@ __device__ __forceinline__ void convert_region(long long* C64, const long long* 
     }
 }
 
-template <int BN, int MODE, int FMT, bool SK>
+// GROUPED (FP32 mode, kb-major stages, no split K only): units are the tiles
+// of all problems of args.probs, each with its own TMA descriptors, C and
+// tile width (runtime MMA N; narrow tiles leave the last epilogue warps idle).
+template <int BN, int MODE, int FMT, bool SK, bool GROUPED = false>
 __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
     split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       const SplitArgs args) {
+    static_assert(!GROUPED || (MODE == kModeF32 && FMT == kFmtBF16KB && !SK),
+                  "grouped split launches take FP32-accuracy problems without split K");
     using Cfg = SplitCfg<BN, MODE, FMT>;
     constexpr int kBKe = Cfg::kBKe;
     constexpr bool F64 = MODE != kModeF32;
@@ -886,7 +972,7 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
         ctl->abort = 0;
         fence_barrier_init();
     }
-    if (warp == 0 && lane == 0) {
+    if (!GROUPED && warp == 0 && lane == 0) {
         prefetch_tmap(&tmA);
         prefetch_tmap(&tmB);
     }
@@ -899,7 +985,8 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
-    const int num_units = args.tiles_m * args.tiles_n * (SK ? args.ksplit * args.lgroups : 1);
+    const int num_units = GROUPED ? args.num_units
+                                  : args.tiles_m * args.tiles_n * (SK ? args.ksplit * args.lgroups : 1);
 
     if (warp == 0) {
         if (lane == 0) {
@@ -908,33 +995,59 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
             uint32_t phase = 0;
             long issued = 0;
             bool ok = true;
+            int g_prev = -1;
             for (int u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
                 int t, kb_lo, kb_hi, tm, tn;
                 uint32_t lmask;
-                split_unit<SK>(args, u, t, kb_lo, kb_hi, lmask);
-                split_tile_coords(t, args.tiles_m, args.tiles_n, args.group_m, tm, tn);
+                int bn = BN;
+                const CUtensorMap* mA = &tmA;
+                const CUtensorMap* mB = &tmB;
+                if constexpr (GROUPED) {
+                    const SplitGUnit x = split_gresolve(args, u);
+                    tm = x.tm;
+                    tn = x.tn;
+                    bn = x.bn;
+                    kb_lo = 0;
+                    kb_hi = args.probs[x.g].num_kb;
+                    lmask = 0xFFFFFFFFu;
+                    t = 0;
+                    mA = args.maps + 2 * x.g;
+                    mB = args.maps + 2 * x.g + 1;
+                    if (x.g != g_prev) {
+                        prefetch_tmap(mA);
+                        prefetch_tmap(mB);
+                        g_prev = x.g;
+                    }
+                } else {
+                    split_unit<SK>(args, u, t, kb_lo, kb_hi, lmask);
+                    split_tile_coords(t, args.tiles_m, args.tiles_n, args.group_m, tm, tn);
+                }
                 for (int L = 0; L < args.levels && ok; ++L) {
                     if constexpr (SK)
                         if (!((lmask >> L) & 1u)) continue;
                     const int np = level_pairs(args, L);
                     if constexpr (Cfg::kKB) {
                         // kb-major: the three slices of A and of B of K block kb
+                        const uint32_t bytes =
+                            GROUPED ? 3u * (Cfg::kASlice + static_cast<uint32_t>(bn / 64) * Cfg::kBChunk)
+                                    : static_cast<uint32_t>(Cfg::kStageBytes);
                         for (int kb = kb_lo; kb < kb_hi && ok; ++kb) {
                             if (!mbar_wait(&empty[stage], phase ^ 1u, ctl, limit, status)) {
                                 ok = false;
                                 break;
                             }
-                            mbar_arrive_expect_tx(&full[stage], Cfg::kStageBytes);
+                            mbar_arrive_expect_tx(&full[stage], bytes);
                             uint8_t* a_st = sA + stage * Cfg::kAStage;
                             uint8_t* b_st = sB + stage * Cfg::kBBytes;
 #pragma unroll
                             for (int sl = 0; sl < 3; ++sl) {
-                                tma_load_3d(a_st + sl * Cfg::kASlice, &tmA, &full[stage],
+                                tma_load_3d(a_st + sl * Cfg::kASlice, mA, &full[stage],
                                             kb * kBKe, tm * kBM, sl);
 #pragma unroll
                                 for (int c = 0; c < BN / 64; ++c)
-                                    tma_load_3d(b_st + sl * Cfg::kBSlice + c * Cfg::kBChunk, &tmB,
-                                                &full[stage], tn * BN + c * 64, kb * kBKe, sl);
+                                    if (!GROUPED || c < bn / 64)
+                                        tma_load_3d(b_st + sl * Cfg::kBSlice + c * Cfg::kBChunk, mB,
+                                                    &full[stage], tn * bn + c * 64, kb * kBKe, sl);
                             }
                             ++issued;
                             if (++stage == kStages) {
@@ -996,7 +1109,18 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
             for (int u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
                 int t, kb_lo, kb_hi;
                 uint32_t lmask;
-                split_unit<SK>(args, u, t, kb_lo, kb_hi, lmask);
+                uint32_t idesc = Cfg::kIdesc;
+                if constexpr (GROUPED) {
+                    const SplitGUnit x = split_gresolve(args, u);
+                    kb_lo = 0;
+                    kb_hi = args.probs[x.g].num_kb;
+                    lmask = 0xFFFFFFFFu;
+                    t = 0;
+                    idesc = make_idesc(1u, kBM, static_cast<uint32_t>(x.bn), 0u, 1u);
+                } else {
+                    split_unit<SK>(args, u, t, kb_lo, kb_hi, lmask);
+                }
+                (void)t;
                 for (int L = 0; L < args.levels && ok; ++L) {
                     if constexpr (SK)
                         if (!((lmask >> L) & 1u)) continue;
@@ -1035,7 +1159,7 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
                                     for (int k = 0; k < kBKe / 16; ++k)
                                         mma_f16(d, adesc + static_cast<uint64_t>((k * 32) >> 4),
                                                 bdesc + static_cast<uint64_t>((k * 16 * 128) >> 4),
-                                                Cfg::kIdesc, (first && q == 0 && k == 0) ? 0u : 1u);
+                                                idesc, (first && q == 0 && k == 0) ? 0u : 1u);
                                 }
                                 first = false;
                                 mma_commit(&empty[stage]);
@@ -1100,15 +1224,37 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
         for (int u = blockIdx.x; u < num_units && ok; u += gridDim.x) {
             int t, kb_lo, kb_hi, tm, tn, kslice;
             uint32_t lmask;
-            split_unit<SK>(args, u, t, kb_lo, kb_hi, lmask, &kslice);
+            // the unit's problem: its C, sizes and tile width
+            int64_t um = args.m, up = args.p;
+            float* uC = static_cast<float*>(args.C);
+            int uvec = args.vec_ok, bn = BN;
+            if constexpr (GROUPED) {
+                const SplitGUnit x = split_gresolve(args, u);
+                tm = x.tm;
+                tn = x.tn;
+                kb_lo = 0;
+                kb_hi = args.probs[x.g].num_kb;
+                lmask = 0xFFFFFFFFu;
+                kslice = 0;
+                t = 0;
+                um = x.m;
+                up = x.p;
+                uC = x.C;
+                uvec = x.vec_ok;
+                bn = x.bn;
+            } else {
+                split_unit<SK>(args, u, t, kb_lo, kb_hi, lmask, &kslice);
+                split_tile_coords(t, args.tiles_m, args.tiles_n, args.group_m, tm, tn);
+            }
+            // narrow tiles of a grouped launch leave the last column warps idle
+            const bool cols_live = !GROUPED || h * kCols < bn;
             // the unit's last level (its folds end there)
             const int l_last =
                 SK ? 31 - __clz(static_cast<int>(lmask & ((1u << args.levels) - 1u)))
                    : args.levels - 1;
-            split_tile_coords(t, args.tiles_m, args.tiles_n, args.group_m, tm, tn);
             const int64_t row = static_cast<int64_t>(tm) * kBM + q * 32 + lane;
-            const int64_t col_base = static_cast<int64_t>(tn) * BN + h * kCols;
-            const bool row_ok = row < args.m;
+            const int64_t col_base = static_cast<int64_t>(tn) * bn + h * kCols;
+            const bool row_ok = row < um;
             // FP64 modes keep the tile's int64 fixed-point total T in C itself
             // (same 8 bytes per element as the final FP64 value).
             const int er = (F64 && row_ok) ? args.eA[row] : 0;
@@ -1153,7 +1299,7 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
                         }
                         tmem_st_wait();
                         r_valid = true;
-                    } else {
+                    } else if (cols_live) {
 #pragma unroll
                         for (int g = 0; g < 4; ++g) {
                             uint32_t r[16];
@@ -1290,9 +1436,9 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
                 continue;
             }
             // ---------------- FP32 mode: store the tile
-            if (!F64 && row_ok) {
-                float* crow = static_cast<float*>(args.C) + row * args.p;
-                if (args.vec_ok && col_base + 64 <= args.p) {
+            if (!F64 && row_ok && cols_live) {
+                float* crow = uC + row * up;
+                if (uvec && col_base + 64 <= up) {
                     float4* dst = reinterpret_cast<float4*>(crow + col_base);
 #pragma unroll
                     for (int v = 0; v < 16; ++v)
@@ -1303,7 +1449,7 @@ __global__ void __launch_bounds__(SplitCfg<BN, MODE, FMT>::kThreads, 1)
                 } else {
 #pragma unroll
                     for (int i = 0; i < 64; ++i)
-                        if (col_base + i < args.p) crow[col_base + i] = __uint_as_float(acc[i % kRegs]);
+                        if (col_base + i < up) crow[col_base + i] = __uint_as_float(acc[i % kRegs]);
                 }
             }
         }
@@ -1400,22 +1546,23 @@ size_t split_workspace_bytes(int64_t m, int64_t n, int64_t p, moa_dtype dt, int 
     return split_layout(m, n, p, dt, S).total;
 }
 
-template <int BN, int MODE, int FMT, bool SK = false>
+template <int BN, int MODE, int FMT, bool SK = false, bool GROUPED = false>
 static int launch_split_cfg(const SplitArgs& a, const CUtensorMap& tmA, const CUtensorMap& tmB,
                             cudaStream_t s, moa_stats* st) {
     using Cfg = SplitCfg<BN, MODE, FMT>;
     static std::atomic<uint64_t> attr_done{0};   // per instantiation, per device
     {
         const int rc = smem_attr_once(
-            reinterpret_cast<const void*>(split_gemm_kernel<BN, MODE, FMT, SK>), Cfg::kSmem,
-            attr_done, "cudaFuncSetAttribute(split_gemm)");
+            reinterpret_cast<const void*>(split_gemm_kernel<BN, MODE, FMT, SK, GROUPED>),
+            Cfg::kSmem, attr_done, "cudaFuncSetAttribute(split_gemm)");
         if (rc != MOA_OK) return rc;
     }
-    const long tiles = static_cast<long>(a.tiles_m) * a.tiles_n;
+    const long tiles = GROUPED ? a.num_units : static_cast<long>(a.tiles_m) * a.tiles_n;
     const int grid =
         static_cast<int>(std::min<long>(tiles * (SK ? a.ksplit * a.lgroups : 1), num_sms()));
     prof_begin(s);
-    split_gemm_kernel<BN, MODE, FMT, SK><<<grid, Cfg::kThreads, Cfg::kSmem, s>>>(tmA, tmB, a);
+    split_gemm_kernel<BN, MODE, FMT, SK, GROUPED><<<grid, Cfg::kThreads, Cfg::kSmem, s>>>(tmA, tmB,
+                                                                                         a);
     cudaError_t e = cudaGetLastError();
     prof_end(s);
     if (e != cudaSuccess) return cuda_fail(e, "split_gemm_kernel launch");
@@ -1553,6 +1700,15 @@ static void digit_prepasses(const SplitLayout& L, int64_t m, int64_t n, int64_t 
     }
 }
 
+// K slices of an FP32-accuracy split GEMM of tile width bn (1: no split K),
+// as split_gemm plans it.
+static int f32_split_ks(const SplitLayout& L, int64_t m, int64_t n, int64_t p, int bn) {
+    const int bke = block_k<kFmtBF16KB>();
+    if (L.f32_ks < 2) return 1;
+    const long tiles = static_cast<long>(ceil_div(m, kBM)) * ceil_div(p, bn);
+    return std::min(L.f32_ks, split_k_factor(tiles, static_cast<int>(ceil_div(n, bke)), bke));
+}
+
 int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const void* B,
                void* C, int slices, void* ws, size_t ws_bytes, cudaStream_t s, moa_stats* st) {
     const int S = split_slices(dt, slices);
@@ -1586,9 +1742,7 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
     a.status = status;
     a.vec_ok = (p % 4 == 0) && (reinterpret_cast<uintptr_t>(C) % 16 == 0);
     if (dt == MOA_F32_SPLIT)
-        a.ksplit = L.f32_ks >= 2 ? std::min(L.f32_ks, split_k_factor(static_cast<long>(a.tiles_m) *
-                                                                          a.tiles_n, a.num_kb, bke))
-                                 : 1;
+        a.ksplit = f32_split_ks(L, m, n, p, bn);
     else
         a.ksplit = L.fine_bytes == 0
                        ? 1
@@ -1737,6 +1891,183 @@ int split_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, con
         st->kernels = kernels + 1;
     }
     return rc;
+}
+
+
+// ---------------------------------------------------------------- grouped FP32-accuracy
+namespace {
+
+struct SplitGPlan {
+    size_t pass_off, prob_off, maps_off, head_bytes;   // tables, one upload
+    std::vector<size_t> region;                         // per taken problem: its slice planes
+    size_t total;
+};
+
+struct STaken {
+    int idx;        // index in the caller's descriptors
+    int bn;         // the lone call's tile width
+    SplitLayout L;  // offsets within the problem's region (slice planes only)
+};
+
+SplitGPlan split_grouped_plan(int count, const moa_gemm_desc* d, std::vector<STaken>* taken) {
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    std::vector<STaken> tk;
+    for (int g = 0; g < count; ++g) {
+        if (!split_grouped_ok(d[g])) continue;
+        STaken x{};
+        x.idx = g;
+        x.bn = split_block_n(d[g].m, d[g].p, false);
+        x.L = split_layout(d[g].m, d[g].n, d[g].p, MOA_F32_SPLIT, 3);
+        tk.push_back(x);
+    }
+    const size_t G = tk.size();
+    SplitGPlan P{};
+    size_t off = 0;
+    P.pass_off = off;
+    off += al(sizeof(SplitGPass) * G);
+    P.prob_off = off;
+    off += al(sizeof(SplitGProb) * G);
+    P.maps_off = off;
+    off += al(sizeof(CUtensorMap) * 2 * G);
+    P.head_bytes = off;
+    for (const STaken& x : tk) {
+        P.region.push_back(off);
+        off += al(x.L.b_off + static_cast<size_t>(3) * d[x.idx].n * x.L.ldb * 2);
+    }
+    P.total = G ? off : 0;
+    if (taken) *taken = tk;
+    return P;
+}
+
+}  // namespace
+
+bool split_grouped_ok(const moa_gemm_desc& d) {
+    const int64_t lim = int64_t(1) << 31;
+    if (d.dt != MOA_F32_SPLIT || d.m <= 0 || d.n <= 0 || d.p <= 0 || d.m >= lim || d.n >= lim ||
+        d.p >= lim || d.C == nullptr || reinterpret_cast<uintptr_t>(d.A) % 16 != 0 ||
+        reinterpret_cast<uintptr_t>(d.B) % 16 != 0 || reinterpret_cast<uintptr_t>(d.C) % 4 != 0)
+        return false;
+    // only what the lone call would run without split K: the same sums in
+    // the same order, so a grouped result equals the lone one bit for bit
+    const int bn = split_block_n(d.m, d.p, false);
+    return f32_split_ks(split_layout(d.m, d.n, d.p, MOA_F32_SPLIT, 3), d.m, d.n, d.p, bn) == 1;
+}
+
+size_t split_grouped_workspace(int count, const moa_gemm_desc* d) {
+    return split_grouped_plan(count, d, nullptr).total;
+}
+
+int split_grouped_launch(int count, const moa_gemm_desc* d, void* ws, size_t ws_bytes,
+                         cudaStream_t s, int* const* status_of) {
+    std::vector<STaken> tk;
+    const SplitGPlan P = split_grouped_plan(count, d, &tk);
+    const int G = static_cast<int>(tk.size());
+    if (G == 0) return MOA_OK;
+    if (ws == nullptr || ws_bytes < P.total)
+        return fail(MOA_ERR_WORKSPACE, "workspace too small for the grouped split path");
+    int* status = launch_status_ptr();
+    if (!status) return MOA_ERR_CUDA;
+    const int bke = block_k<kFmtBF16KB>();
+    uint8_t* base = static_cast<uint8_t*>(ws);
+    int slot = 0;
+    uint8_t* host = static_cast<uint8_t*>(staging_get(P.head_bytes, &slot));
+    if (!host) return fail(MOA_ERR_CUDA, "pinned staging buffer unavailable");
+    std::memset(host, 0, P.head_bytes);
+    auto* pass = reinterpret_cast<SplitGPass*>(host + P.pass_off);
+    auto* probs = reinterpret_cast<SplitGProb*>(host + P.prob_off);
+    auto* maps = reinterpret_cast<CUtensorMap*>(host + P.maps_off);
+    int pre_blocks = 0;
+    for (int i = 0; i < G; ++i) {
+        const STaken& x = tk[i];
+        const moa_gemm_desc& dd = d[x.idx];
+        uint8_t* r = base + P.region[i];
+        SplitGPass& q = pass[i];
+        q.A = static_cast<const float*>(dd.A);
+        q.B = static_cast<const float*>(dd.B);
+        q.a_sl = reinterpret_cast<__nv_bfloat16*>(r + x.L.a_off);
+        q.b_sl = reinterpret_cast<__nv_bfloat16*>(r + x.L.b_off);
+        q.m = dd.m;
+        q.n = dd.n;
+        q.p = dd.p;
+        q.lda = x.L.lda;
+        q.ldb = x.L.ldb;
+        q.a_plane = dd.m * x.L.lda;
+        q.b_plane = dd.n * x.L.ldb;
+        q.status = (status_of && status_of[x.idx]) ? status_of[x.idx] : status;
+        q.va = vec_rows(dd.A, dd.n, 4);
+        q.vb = vec_rows(dd.B, dd.p, 4);
+        q.ga = grid_for(q.a_plane / 8, 256);
+        q.gb = grid_for(q.b_plane / 8, 256);
+        q.begin = pre_blocks;
+        pre_blocks += q.ga + q.gb;
+    }
+    // GEMM problems, longest K first, each with its TMA descriptors
+    std::vector<int> order(G);
+    for (int i = 0; i < G; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return d[tk[a].idx].n > d[tk[b].idx].n; });
+    long units = 0;
+    for (int j = 0; j < G; ++j) {
+        const int i = order[j];
+        const STaken& x = tk[i];
+        const moa_gemm_desc& dd = d[x.idx];
+        SplitGProb& g = probs[j];
+        g.C = static_cast<float*>(dd.C);
+        g.m = dd.m;
+        g.p = dd.p;
+        g.bn = x.bn;
+        g.tiles_m = static_cast<int>(ceil_div(dd.m, kBM));
+        g.tiles_n = static_cast<int>(ceil_div(dd.p, x.bn));
+        g.num_kb = static_cast<int>(ceil_div(dd.n, bke));
+        g.group_m = split_raster_group(dd.n);
+        g.vec_ok = (dd.p % 4 == 0) && (reinterpret_cast<uintptr_t>(dd.C) % 16 == 0);
+        g.unit_begin = static_cast<int>(units);
+        units += static_cast<long>(g.tiles_m) * g.tiles_n;
+        int rc = make_tmap_3d(&maps[2 * j], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, pass[i].a_sl,
+                              static_cast<uint64_t>(dd.n), static_cast<uint64_t>(dd.m), 3,
+                              static_cast<uint64_t>(x.L.lda) * 2,
+                              static_cast<uint64_t>(pass[i].a_plane) * 2, bke, kBM, 64);
+        if (rc == MOA_OK)
+            rc = make_tmap_3d(&maps[2 * j + 1], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, pass[i].b_sl,
+                              static_cast<uint64_t>(dd.p), static_cast<uint64_t>(dd.n), 3,
+                              static_cast<uint64_t>(x.L.ldb) * 2,
+                              static_cast<uint64_t>(pass[i].b_plane) * 2, 64, bke);
+        if (rc != MOA_OK) {
+            staging_release(slot, s);
+            return rc;
+        }
+    }
+    if (units > (1L << 30)) {
+        staging_release(slot, s);
+        return fail(MOA_ERR_ARG, "too many tiles in one grouped call");
+    }
+    cudaError_t e = cudaMemcpyAsync(base, host, P.head_bytes, cudaMemcpyHostToDevice, s);
+    staging_release(slot, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(grouped split tables)");
+    split3_g_kernel<<<pre_blocks, 256, 0, s>>>(reinterpret_cast<const SplitGPass*>(base + P.pass_off),
+                                               G);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "grouped split pre-pass launch");
+    SplitArgs a{};
+    a.f64 = 0;
+    a.levels = 1;
+    a.S = 3;
+    a.kc[0] = f32_split_chunk_kb(bke);
+    a.ksplit = 1;
+    a.lgroups = 1;
+    a.lmask[0] = 0xFFFFFFFFu;
+    a.wait_limit_ns = wait_limit_ns();
+    a.status = status;
+    a.probs = reinterpret_cast<const SplitGProb*>(base + P.prob_off);
+    a.maps = reinterpret_cast<const CUtensorMap*>(base + P.maps_off);
+    a.nprob = G;
+    a.num_units = static_cast<int>(units);
+    CUtensorMap unused{};
+    const int rc = launch_split_cfg<256, kModeF32, kFmtBF16KB, false, true>(a, unused, unused, s,
+                                                                            nullptr);
+    if (rc != MOA_OK) return rc;
+    log_msg(2, "grouped split: %d problems, %ld tiles", G, units);
+    return MOA_OK;
 }
 
 }  // namespace moa

@@ -73,4 +73,14 @@ struct SplitLayout {
 };
 SplitLayout split_layout(int64_t m, int64_t n, int64_t p, moa_dtype dt, int S);
 
+// Grouped calls (moa_gemm_grouped): FP32-accuracy split problems that the
+// lone call would run without split K share one slice pre-pass launch and
+// one persistent GEMM launch (per-problem TMA descriptors and tile widths);
+// each result equals its lone call's bit for bit.  status_of (may be NULL):
+// a device status word per descriptor for non-finite inputs.
+bool split_grouped_ok(const moa_gemm_desc& d);
+size_t split_grouped_workspace(int count, const moa_gemm_desc* d);
+int split_grouped_launch(int count, const moa_gemm_desc* d, void* ws, size_t ws_bytes,
+                         cudaStream_t s, int* const* status_of = nullptr);
+
 }  // namespace moa

@@ -65,6 +65,7 @@ DEFAULT_SLICES = {MOA_F32_SPLIT: 3, MOA_F64_SPLIT_F32IN: 7, MOA_F64_SPLIT_F64IN:
 
 
 # moa_product_kind
+MOA_GROUPED_ALONE, MOA_GROUPED_BF16, MOA_GROUPED_CRT, MOA_GROUPED_F32_SPLIT = 0, 1, 2, 3
 MOA_PRODUCT_HADAMARD = 0
 MOA_PRODUCT_KRONECKER = 1
 MOA_PRODUCT_MATMUL = 2
@@ -153,6 +154,7 @@ EXPORTS = {
     "moa_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_uint64, _vp]),
     "moa_set_block_n": (ctypes.c_int, [ctypes.c_int]),
     "moa_set_block_m": (ctypes.c_int, [ctypes.c_int]),
+    "moa_grouped_path": (ctypes.c_int, [ctypes.POINTER(moa_gemm_desc)]),
     "moa_measure_fp64_rate": (ctypes.c_int, [ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_double)]),
     "moa_kronecker": (ctypes.c_int, [_i64, _i64, _i64, _i64, ctypes.c_int, _vp, _vp, _vp, _vp]),
     "moa_hadamard": (ctypes.c_int, [_i64, _i64, ctypes.c_int, _vp, _vp, _vp, _vp]),
@@ -377,6 +379,12 @@ def make_descs(problems):
         arr[i].B = _ptr(B)
         arr[i].C = _ptr(C)
     return arr
+
+
+def grouped_path(A, B, C, dt) -> int:
+    """The path (MOA_GROUPED_*) the problem C := A . B takes in a grouped call."""
+    d = make_descs([(A, B, C, dt)])
+    return int(lib().moa_grouped_path(d))
 
 
 def gemm_grouped(problems, stream=None, workspace: Workspace | None = None, descs=None):

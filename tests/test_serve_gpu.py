@@ -1,9 +1,9 @@
 """The continuous-batching server (moa_serve_*).
 
 * Each result is the same alone and in the mix: every request of a mixed
-  batch (FP32-accuracy and FP64-accuracy split requests, plus BF16 and
-  modular-slice requests that share grouped launches) equals, bit for bit,
-  the same GEMM computed
+  batch (FP32-accuracy and FP64-accuracy split requests, BF16 and
+  modular-slice requests; the small split-precision and BF16 ones share
+  grouped launches) equals, bit for bit, the same GEMM computed
   alone through moa_gemm_ex, and a sample also matches the FP64 oracle within
   the mode's tolerance.
 * Admission: a request whose workspace exceeds the arena is refused
@@ -188,13 +188,16 @@ def test_per_request_device_status():
 
 
 @pytest.mark.gpu
-def test_grouped_modular_slice_requests_keep_their_own_status():
-    """Small modular-slice requests share grouped launches in the server; one
-    with a NaN input completes as MOA_ERR_NONFINITE while the others, grouped
-    with it or not, complete normally and equal their alone results bit for
-    bit."""
-    reqs = [_req(96 + 16 * i, 320, 80 + 16 * i, moa.MOA_F64_CRT_F32IN, seed=90 + i)
-            for i in range(6)]
+@pytest.mark.parametrize("dt", [moa.MOA_F64_CRT_F32IN, moa.MOA_F32_SPLIT],
+                         ids=["modular_slices", "f32_split"])
+def test_grouped_split_requests_keep_their_own_status(dt):
+    """Small modular-slice and FP32-accuracy split requests share grouped
+    launches in the server; one with a NaN input completes as
+    MOA_ERR_NONFINITE while the others, grouped with it or not, complete
+    normally and equal their alone results bit for bit."""
+    reqs = [_req(96 + 16 * i, 320, 80 + 16 * i, dt, seed=90 + i) for i in range(6)]
+    assert all(moa.grouped_path(*r) in (moa.MOA_GROUPED_CRT, moa.MOA_GROUPED_F32_SPLIT)
+               for r in reqs)
     bad = 2
     reqs[bad][0][3, 11] = float("nan")
     alone = {i: moa.gemm(A, B, dt) for i, (A, B, C, dt) in enumerate(reqs) if i != bad}
