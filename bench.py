@@ -716,22 +716,25 @@ def bench_products(stream, steps=10, warmup=3):
     return out
 
 
-def bench_grouped_crt(stream, count=64, div=1, steps=5, warmup=3, seed=3):
-    """`count` FP64-accuracy GEMMs (modular slices, FP32 N(0,1) inputs) with the
-    serving stream's shapes (m, p log-uniform in [64, 4096], n in [64, 8192],
-    each divided by `div`): one moa_gemm_grouped call per step against the
-    same problems as `count` separate moa_gemm_ex calls (CUDA events)."""
+def bench_grouped_crt(stream, count=64, div=1, steps=5, warmup=3, seed=3, mode="f64_crt_f32in"):
+    """`count` split-precision GEMMs (FP32 N(0,1) inputs; `mode`: FP64-accuracy
+    modular slices or FP32-accuracy split) with the serving stream's shapes
+    (m, p log-uniform in [64, 4096], n in [64, 8192], each divided by `div`):
+    one moa_gemm_grouped call per step against the same problems as `count`
+    separate moa_gemm_ex calls (CUDA events)."""
     import torch
     from paper_2306_11148_b300 import inputs, moa
+    dt = moa.MODES[mode]
     arr = inputs.serve_arrivals(rate=count * 4.0, seconds=1.0, seed=seed)[:count]
     probs = []
     flops = 0.0
     for i, (_, m, n, p, _) in enumerate(arr):
         m, n, p = max(1, m // div), max(1, n // div), max(1, p // div)
         A, B = inputs.normal_pair(m, n, p, dtype=torch.float32, seed=500 + i)
-        probs.append((A.cuda(), B.cuda(), torch.empty((m, p), dtype=torch.float64, device="cuda"),
-                      moa.MOA_F64_CRT_F32IN))
+        probs.append((A.cuda(), B.cuda(), torch.empty((m, p), dtype=moa.out_dtype(dt),
+                                                      device="cuda"), dt))
         flops += 2.0 * m * n * p
+    paths = [moa.grouped_path(*pr) for pr in probs]
     descs = moa.make_descs(probs)
     wsp = moa.Workspace(torch.device("cuda"))
     L = moa.lib()
@@ -754,12 +757,15 @@ def bench_grouped_crt(stream, count=64, div=1, steps=5, warmup=3, seed=3):
         t_g = time_device(grouped, steps, warmup, stream, 1)
         t_s = time_device(separate, steps, warmup, stream, 1)
     moa.check(moa.moa_sync_status(sh))
+    what = {"f64_crt_f32in": "FP64-accuracy modular-slice",
+            "f32_split": "FP32-accuracy split"}.get(mode, mode)
     return {"count": count, "shape_divisor": div, "flops_per_step": flops,
             "grouped_ms": t_g / steps * 1e3, "separate_ms": t_s / steps * 1e3,
             "grouped_tflops": flops * steps / t_g / 1e12,
             "separate_tflops": flops * steps / t_s / 1e12,
             "speedup": t_s / t_g,
-            "workload": f"{count} FP64-accuracy modular-slice GEMMs, serving shapes / {div}"}
+            "on_grouped_path": sum(1 for x in paths if x != moa.MOA_GROUPED_ALONE),
+            "workload": f"{count} {what} GEMMs, serving shapes / {div}"}
 
 
 def bench_grouped_e2e(shapes, steps, warmup, ws):
@@ -1546,6 +1552,11 @@ def main():
                 modes[f"grouped_crt_div{div}"] = bench_grouped_crt(stream, count=64, div=div)
             except Exception as e:  # report, do not hide
                 modes[f"grouped_crt_div{div}"] = {"error": str(e)}
+            try:
+                modes[f"grouped_f32_split_div{div}"] = bench_grouped_crt(stream, count=64, div=div,
+                                                                         mode="f32_split")
+            except Exception as e:  # report, do not hide
+                modes[f"grouped_f32_split_div{div}"] = {"error": str(e)}
         # a short run of the serving stream (each arrival its own shape)
         try:
             ops = ServeOperands(nbuf=2)
