@@ -716,7 +716,7 @@ def bench_products(stream, steps=10, warmup=3):
     return out
 
 
-def bench_grouped_crt(stream, count=64, div=1, steps=5, warmup=3, seed=3, mode="f64_crt_f32in"):
+def bench_grouped_split(stream, count=64, div=1, steps=5, warmup=3, seed=3, mode="f64_crt_f32in"):
     """`count` split-precision GEMMs (FP32 N(0,1) inputs; `mode`: FP64-accuracy
     modular slices or FP32-accuracy split) with the serving stream's shapes
     (m, p log-uniform in [64, 4096], n in [64, 8192], each divided by `div`):
@@ -1549,11 +1549,11 @@ def main():
         # grouped modular-slice batches against separate launches
         for div in (1, 4):
             try:
-                modes[f"grouped_crt_div{div}"] = bench_grouped_crt(stream, count=64, div=div)
+                modes[f"grouped_crt_div{div}"] = bench_grouped_split(stream, count=64, div=div)
             except Exception as e:  # report, do not hide
                 modes[f"grouped_crt_div{div}"] = {"error": str(e)}
             try:
-                modes[f"grouped_f32_split_div{div}"] = bench_grouped_crt(stream, count=64, div=div,
+                modes[f"grouped_f32_split_div{div}"] = bench_grouped_split(stream, count=64, div=div,
                                                                          mode="f32_split")
             except Exception as e:  # report, do not hide
                 modes[f"grouped_f32_split_div{div}"] = {"error": str(e)}

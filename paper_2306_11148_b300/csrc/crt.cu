@@ -1738,6 +1738,22 @@ int crt_gemm_host(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* hA,
     const int64_t want = std::min<int64_t>(8, std::max<int64_t>(1, ceil_div(m, 2048)));
     const int64_t mb = round_up(ceil_div(m, want), 256);
     const int64_t nb = ceil_div(m, mb);
+    if (nb == 1) {
+        // one band: nothing to overlap within the call; upload, compute and
+        // download in order on the caller's stream (no helper streams)
+        cudaError_t e = cudaMemcpyAsync(dA, hA, static_cast<size_t>(m) * n * in_b,
+                                        cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dB, hB, static_cast<size_t>(n) * p * in_b, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(A, B to the device)");
+        rc = crt_passes(c, dA, 0, m, dB, s);
+        if (rc == MOA_OK) rc = crt_product(c, 0, m, static_cast<double*>(dC), s, st);
+        if (rc != MOA_OK) return rc;
+        e = cudaMemcpyAsync(hC, dC, static_cast<size_t>(m) * p * 8, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(C to the host)");
+        if (st) st->kernels = 4;
+        return MOA_OK;
+    }
     cudaStream_t up = nullptr, down = nullptr;
     std::vector<cudaEvent_t> ev;   // start, b_ready, a_ready[nb], c_ready[nb], up_done, down_done
     auto mk = [&]() {

@@ -30,8 +30,9 @@ int crt_gemm(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* A, const
 // device copies dA, dB, dC; ws / ws_bytes as for crt_gemm.  B is uploaded
 // and its passes run once; then A's rows go through in bands of about 2048
 // rows, each band's upload, passes + GEMM + reconstruction and download on
-// their own streams, so that they overlap; `s` ends after all of it.  The
-// result equals crt_gemm's bit for bit.
+// their own streams, so that they overlap; `s` ends after all of it (a
+// problem of one band runs in order on `s` alone).  The result equals
+// crt_gemm's bit for bit.
 int crt_gemm_host(int64_t m, int64_t n, int64_t p, moa_dtype dt, const void* hA, const void* hB,
                   void* hC, int slices, void* dA, void* dB, void* dC, void* ws, size_t ws_bytes,
                   cudaStream_t s, moa_stats* st);
