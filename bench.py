@@ -47,8 +47,8 @@ L2_MB = 126.0   # B300 L2 capacity
 TRAFFIC = {
     ("tf32", 8192): {"bytes": 1.652613e9 + 0.236939e9, "src": "gemm_tc.cu",
                      "sha": None},
-    ("f64_crt_f32in", 8192): {"bytes": 13939213568 + 983858176, "src": "crt.cu",
-                              "sha": "b2b2e87ca68a9058"},
+    ("f64_crt_f32in", 8192): {"bytes": 14224164864 + 984522496, "src": "crt.cu",
+                              "sha": "33b7df3c3e06828b"},
 }
 
 
