@@ -278,14 +278,17 @@ int moa_gemm_batched(int batch, int64_t m, int64_t n, int64_t p, moa_dtype dt, c
  * restores the planners.  MOA_ERR_ARG for values outside {0,64,128,192,256}. */
 int moa_set_block_n(int block_n);
 
-/* Tile height of the modular-slice modes (MOA_F64_CRT_*): 128-row tiles on
- * one SM, or 256 x 256 tiles on a pair of SMs (a cluster of two CTAs whose
- * tensor-core MMAs span both: each SM stages half of the operands, so more
- * K blocks are in flight per SM).  The planner picks one by a wave-count
- * cost model; moa_set_block_m(128 | 256) forces it for the calling thread's
- * later calls (256 implies block_n 256; a forced block_n of 128 implies
- * 128 rows), 0 restores the planner.  Results are identical either way.
- * MOA_ERR_ARG for values outside {0, 128, 256}. */
+/* Tile height: 128-row tiles on one SM, or 256 x 256 tiles on a pair of SMs
+ * (a cluster of two CTAs whose tensor-core MMAs span both: each SM stages
+ * half of the operands).  Modular-slice modes (MOA_F64_CRT_*): the planner
+ * picks one by a wave-count cost model while the operand planes fit in the
+ * L2.  Dense modes (MOA_BF16, MOA_F32_TF32): the planner chooses among
+ * 128-row tiles and 256 x 256 tiles on one SM; pair tiles (each SM with a
+ * double-buffered accumulator) are available but measured no faster.
+ * moa_set_block_m(128 | 256) forces 128-row tiles or pair tiles for the
+ * calling thread's later calls (256 implies block_n 256; a forced block_n of
+ * 128 implies 128 rows), 0 restores the planners.  Results are identical
+ * either way.  MOA_ERR_ARG for values outside {0, 128, 256}. */
 int moa_set_block_m(int block_m);
 
 /* Measured refinement of the planner: times C := A . B with every block_n on
