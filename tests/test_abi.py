@@ -152,6 +152,25 @@ def test_host_entry_workspace_and_argument_errors(L):
     assert f(0, 8, 8, moa.MOA_F64_CRT_F32IN, None, None, None, 0, None, 0, None) == moa.MOA_OK
 
 
+def test_grouped_path_host_query(L):
+    """moa_grouped_path on the host: aligned BF16 problems take the persistent
+    launch, modular-slice ones the grouped modular-slice launches, small
+    FP32-accuracy split ones the grouped split launches, other modes (and
+    unaligned operands) their own launches."""
+    def path(m, n, p, dt, a=4096, b=8192, c=16384):
+        d = moa.moa_gemm_desc()
+        d.m, d.n, d.p, d.dt, d.A, d.B, d.C = m, n, p, dt, a, b, c
+        return L.moa_grouped_path(ctypes.byref(d))
+    assert path(128, 256, 192, moa.MOA_BF16) == moa.MOA_GROUPED_BF16
+    assert path(128, 256, 192, moa.MOA_F64_CRT_F32IN) == moa.MOA_GROUPED_CRT
+    assert path(128, 256, 192, moa.MOA_F32_SPLIT) == moa.MOA_GROUPED_F32_SPLIT
+    assert path(128, 256, 192, moa.MOA_F64) == moa.MOA_GROUPED_ALONE
+    assert path(128, 256, 192, moa.MOA_F64_SPLIT_F32IN) == moa.MOA_GROUPED_ALONE
+    assert path(128, 256, 192, moa.MOA_F32_SPLIT, a=4100) == moa.MOA_GROUPED_ALONE
+    assert path(0, 256, 192, moa.MOA_BF16) == moa.MOA_GROUPED_ALONE
+    assert L.moa_grouped_path(None) == moa.MOA_ERR_ARG
+
+
 def test_fp64_rate_argument_errors(L):
     out = ctypes.c_double(0.0)
     assert L.moa_measure_fp64_rate(2, None, ctypes.byref(out)) == moa.MOA_ERR_ARG
